@@ -1,0 +1,304 @@
+"""Benchmark: atom-steps/s of velocity-Verlet MD with the Tersoff potential, fp64 path and
+mixed-precision path, on one GB300 (the paper's speed metric, Sec. 3: N x steps / time).
+
+Workload (default): Tersoff-1989 carbon honeycomb sheet, 500 x 500 rectangular cells =
+1,000,000 atoms, bond 1.42 A, periodic in-plane, 20 A periodic length along z, jitter
++-0.02 A, Maxwell-Boltzmann 300 K, NVE, dt = 0.5 fs.  A "step" is one full velocity-Verlet
+step: kick/drift, conditional neighbour rebuild, pair pass, gather (F, W, J), half-kick
+and the per-step fp64 totals (U, K, J).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints ONE JSON line.  Timing: W untimed warm-up steps, then K steps between CUDA events
+on the library's stream, bracketed by a barrier and a device synchronise; the per-step
+working set (~0.5 GB) exceeds the 129 MB L2, so no flush is needed between steps.
+Multi-GPU (torchrun): every rank runs its own independent replica of the workload
+("replicas only" -- one MD system does not shard without a halo exchange), the job
+value is the sum over ranks divided by the max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1610_03343_gb300 import inputs as I  # noqa: E402
+
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+# FP64 vector peak of a GB300 from the unit counts and clock (recipe's nominal figure).
+FP64_NOMINAL_TFLOPS = 1.25
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        d["_source"] = "measured"
+        return d
+    d = dict(PEAKS_FALLBACK)
+    d["_source"] = "fallback"
+    return d
+
+
+def workload(name: str, scale: int = 1):
+    if name == "tersoff_c_graphene_1M":
+        return I.c_graphene_tersoff(nx=500 // scale, ny=500 // scale), 0.5
+    if name == "sw_si_512k":
+        return I.si_diamond_sw(n=40 // scale), 1.0
+    if name == "tersoff_si_1728":
+        return I.si_diamond_tersoff(n=6), 1.0
+    raise ValueError(name)
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _loop(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=5).stdout.strip()
+                if out:
+                    self.rows.append([c.strip() for c in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._loop, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if len(r) > 5 + k and r[5 + k] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# FP64 operations per atom-step of the pair pass, counted from its expressions (see
+# DESIGN.md, "roofline"): per in-cutoff bond and per unordered bond pair (triplet).
+def pair_flops(kind: int, bonds: float, triplets: float) -> float:
+    if kind == I.MD_TERSOFF:
+        return 62.0 * bonds + 75.0 * triplets
+    return 60.0 * bonds + 50.0 * triplets
+
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_1610_03343_gb300 import md
+
+    torch.cuda.set_device(0 if world == 1 else int(os.environ.get("LOCAL_RANK", rank)))
+    sysm, dt = workload(args.workload)
+    n = sysm.n
+    stream = torch.cuda.Stream()
+    res = {}
+    for prec, tag in ((md.MD_FP64, "fp64"), (md.MD_MIXED, "mixed")):
+        g = md.System(sysm.box, sysm.pbc, n, sysm.kind, sysm.params, sysm.mass, precision=prec,
+                      stream=stream.cuda_stream)
+        g.set_positions(sysm.pos)
+        g.set_velocities(sysm.vel)
+        f0 = g.compute(want=("f",))["F"].copy()
+        g.run(args.warmup, dt, record=False)
+        md.md_set_profiling(g.ctx, True)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        clocks = ClockSampler(torch.cuda.current_device())
+        with clocks:
+            e0.record(stream)
+            g.run(args.steps, dt, record=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        ms = e0.elapsed_time(e1)
+        kt = md.md_kernel_times(g.ctx)
+        md.md_set_profiling(g.ctx, False)
+        st = g.stats()
+        res[tag] = dict(ms=ms, kt=kt, f0=f0, clocks=clocks.summary(), stats=st, sys=g)
+    # end-to-end through the public API with host buffers (pinned), copies inside the
+    # timed region: upload x, v; run K steps; read back the series and the final state
+    import torch as _t
+    g = res["fp64"]["sys"]
+    xs = _t.tensor(np.ascontiguousarray(sysm.pos.T), dtype=_t.float64).pin_memory()
+    vs = _t.tensor(np.ascontiguousarray(sysm.vel.T), dtype=_t.float64).pin_memory()
+    ser = _t.zeros((args.steps, 5), dtype=_t.float64).pin_memory()
+    xo = _t.zeros(3 * n, dtype=_t.float64).pin_memory()
+    vo = _t.zeros(3 * n, dtype=_t.float64).pin_memory()
+    g.run(args.warmup, dt, record=False)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    md.md_set_positions(g.ctx, xs[0], xs[1], xs[2])
+    md.md_set_velocities(g.ctx, vs[0], vs[1], vs[2])
+    md.md_run(g.ctx, args.steps, dt, ser)
+    md.md_get_state(g.ctx, xo, vo)
+    t_e2e = time.perf_counter() - t0
+    h2d = 6 * 8 * n
+    d2h = 6 * 8 * n + 5 * 8 * args.steps
+    mixed_err = float(np.abs(res["mixed"]["f0"] - res["fp64"]["f0"]).max() / np.abs(res["fp64"]["f0"]).max())
+    for tag in res:
+        res[tag]["sys"].close()
+    return n, dt, res, t_e2e, h2d, d2h, mixed_err
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="tersoff_c_graphene_1M")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend=backend)
+        if backend == "nccl":
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", rank)))
+
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(reference_arm(args)))
+        return
+
+    n, dt, res, t_e2e, h2d, d2h, mixed_err = run_ours(args, rank, world)
+    ms = res["fp64"]["ms"]
+    ms_mixed = res["mixed"]["ms"]
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms, ms_mixed, t_e2e], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, ms_mixed, t_e2e = (float(v) for v in t.tolist())
+    value = world * n * args.steps / (ms / 1e3)
+    value_mixed = world * n * args.steps / (ms_mixed / 1e3)
+    e2e_value = world * n * args.steps / t_e2e
+    if rank != 0:
+        return
+    peaks = load_peaks()
+    kt = res["fp64"]["kt"]
+    pair_n, pair_ms = kt["pair"]
+    gat_n, gat_ms = kt["gather"]
+    st = res["fp64"]["stats"]
+    sysm, _ = workload(args.workload)
+    bonds = 3.0 if sysm.kind == I.MD_TERSOFF and "graphene" in args.workload else 4.0
+    trip = bonds * (bonds - 1) / 2
+    flops = pair_flops(sysm.kind, bonds, trip) * n
+    pair_avg_s = pair_ms / max(pair_n, 1) / 1e3
+    achieved_tf = flops / pair_avg_s / 1e12
+    kernel_launches = res["fp64"]["stats"].kernel_launches_per_step * args.steps
+    out = {
+        "metric": "atom-steps/s Tersoff FP64 vs mixed on 1 GB300",
+        "value": value,
+        "unit": "atom-steps/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "n_atoms": n, "dt_fs": dt, "ensemble": "NVE",
+                   "potential": "Tersoff 1989 C", "l2": "working set > L2 (no flush)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "mixed": {"value": value_mixed, "ms_per_step": ms_mixed / args.steps, "dtype": "f32+f64",
+                  "force_err_vs_fp64": mixed_err},
+        "roofline": {"bound": "alu", "kernel": "pair (fp64)", "achieved": achieved_tf,
+                     "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved_tf / FP64_NOMINAL_TFLOPS, "traffic": None,
+                     "peak_source": "nominal GB300 FP64 (recipe unit counts x clock)"},
+        "kernel_ms_per_step": {k: (v[1] / max(v[0], 1)) for k, v in kt.items()},
+        "e2e": {"value": e2e_value, "unit": "atom-steps/s", "h2d_bytes_per_step": h2d / args.steps,
+                "d2h_bytes_per_step": d2h / args.steps},
+        "gpu_launches": kernel_launches,
+        "rebuilds": int(st.n_rebuilds),
+        "clocks": res["fp64"]["clocks"],
+    }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args)
+    print(json.dumps(out))
+
+
+def _oracle_rate(sysm, dt, steps):
+    import oracle
+    t0 = time.perf_counter()
+    oracle.run(sysm.pos, sysm.vel, sysm.mass, sysm.box, sysm.pbc, sysm.kind, sysm.params, steps, dt)
+    t = time.perf_counter() - t0
+    return sysm.n * steps / t, t
+
+
+def cpu_baseline(args):
+    """The oracle as it stands, single-threaded on a host core, on a bounded sample of the
+    same workload: a 100 x 100-cell patch (40,000 atoms) of the same sheet, 5 steps."""
+    import oracle
+    oracle.build()
+    sysm = I.c_graphene_tersoff(nx=100, ny=100) if "graphene" in args.workload else workload(args.workload, 4)[0]
+    _, dt = workload(args.workload)
+    rate, t = _oracle_rate(sysm, dt, 5)
+    return {"value": rate, "unit": "atom-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{sysm.n} atoms of the same lattice, 5 steps, {t:.1f} s"}
+
+
+def reference_arm(args):
+    """The oracle timed on the host as the reference arm: each step a bounded sample
+    (40,000-atom patch of the same workload, one velocity-Verlet step)."""
+    import oracle
+    oracle.build()
+    sysm = I.c_graphene_tersoff(nx=100, ny=100) if "graphene" in args.workload else workload(args.workload, 4)[0]
+    _, dt = workload(args.workload)
+    steps = max(1, min(args.steps, 20))
+    for _ in range(min(args.warmup, 1)):
+        _oracle_rate(sysm, dt, 1)
+    rate, t = _oracle_rate(sysm, dt, steps)
+    return {"impl": "reference", "metric": "atom-steps/s Tersoff FP64 vs mixed on 1 GB300", "value": rate,
+            "unit": "atom-steps/s", "n_gpus": 1, "steps": steps, "warmup": min(args.warmup, 1),
+            "ms_per_step": t / steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "sample_atoms": sysm.n, "dt_fs": dt},
+            "cpu_baseline": {"value": rate, "unit": "atom-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{sysm.n} atoms x {steps} steps"},
+            "e2e": {"value": rate, "unit": "atom-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,159 @@
+/*
+ * md.h -- C ABI of the GB300 many-body MD library (libmd.so).
+ *
+ * Computes, for the Tersoff (Tersoff 1989) and Stillinger-Weber (Stillinger & Weber 1985)
+ * potentials, the per-atom force, energy, virial and heat current in the explicit
+ * pairwise-force form of Fan, Chen, Vierimaa, Harju, "Efficient molecular dynamics
+ * simulations with many-body potentials on graphics processing units", CPC 2017
+ * (arXiv:1610.03343), and integrates the motion with velocity Verlet (Sec. 3):
+ *
+ *   F_i = sum_j (dU_i/dr_ij - dU_j/dr_ji)                      (Eq. 28; Eqs. 12-14)
+ *   W_i = -1/2 sum_j r_ij (x) (dU_i/dr_ij - dU_j/dr_ji)         (Eq. 29; Eq. 21)
+ *   J_i = sum_j r_ij (dU_j/dr_ji . v_i)                        (Eq. 30; Eqs. 26-27)
+ *   U_i = 1/2 sum_j U_ij                                       (Eqs. 1-2)
+ *
+ * with r_ij = r_j - r_i (Sec. 2.1, below Eq. 6), minimum image on periodic axes, and
+ * (u (x) w)_ab = u_a w_b.  Units: Angstrom, eV, amu, fs; J in eV Angstrom/fs.
+ *
+ * Conventions for every call:
+ *   - Every function returns md_status.  On failure the context keeps a message,
+ *     readable with md_last_error(); the failing call leaves outputs undefined.
+ *   - Input arrays are copied; the caller keeps ownership of every pointer it passes.
+ *     Outputs are written into caller-owned buffers.
+ *   - Pointers are host pointers unless md_options.io == MD_IO_DEVICE, in which case
+ *     every array argument (positions, velocities, outputs; not box/pbc/params/totals/
+ *     series) is a device pointer on the context's GPU.
+ *   - Calls run on the context's CUDA stream and return after the results are in the
+ *     caller's buffers (host I/O) or after the work is enqueued and synchronised
+ *     (device I/O).
+ *   - Arrays are SoA: a 3-vector field is 3N doubles (all x, then all y, then all z);
+ *     a per-atom tensor is 9N doubles, component (a,b) at [(3a+b) N + i].
+ *   - The box is orthorhombic with edges box[0..2]; a periodic axis needs
+ *     box >= 2 (cutoff + skin), else MD_ERR_BOX (each pair then has one image).
+ */
+#ifndef MD_H
+#define MD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct md_ctx md_ctx; /* opaque; owns all of its device memory */
+
+typedef enum {
+    MD_OK = 0,
+    MD_ERR_ARG = -1,            /* bad argument (NULL where required, negative size, ...) */
+    MD_ERR_BOX = -2,            /* periodic box shorter than 2 (cutoff + skin)            */
+    MD_ERR_NEIGH_OVERFLOW = -3, /* an atom had more neighbours than max_neigh / max_active */
+    MD_ERR_OOM = -4,            /* device allocation failed or exceeded hbm_budget        */
+    MD_ERR_CUDA = -5,           /* a CUDA runtime call failed                             */
+    MD_ERR_TIMEOUT = -6,        /* a bounded device-side wait gave up                    */
+    MD_ERR_NAN = -7,            /* a non-finite force appeared                            */
+    MD_ERR_STATE = -8           /* call out of order (e.g. run before positions are set)  */
+} md_status;
+
+enum { MD_TERSOFF = 1, MD_SW = 2 };      /* md_params.kind */
+enum { MD_FP64 = 0, MD_MIXED = 1 };      /* md_options.precision */
+enum { MD_IO_HOST = 0, MD_IO_DEVICE = 1 }; /* md_options.io */
+
+/* Potential parameters (single element; n_types must be 1).
+ *   MD_TERSOFF: p[11] = A (eV), B (eV), lambda (1/A), mu (1/A), beta, n, c, d, h, R (A), S (A)
+ *               Eqs. 2-6 with f_R = A exp(-lambda r), f_A = B exp(-mu r), and
+ *               f_C = 1 (r < R), 1/2 + 1/2 cos(pi (r-R)/(S-R)) (R <= r < S), 0 (r >= S).
+ *   MD_SW:      p[9]  = epsilon (eV), sigma (A), a, lambda, gamma, A, B, p, q
+ *               U_i = 1/2 sum_j phi2(r_ij) + sum_{j<k} phi3(r_ij, r_ik, theta_jik),
+ *               the three-body term belonging to its vertex atom i.
+ * The array is copied at md_create. */
+typedef struct {
+    int kind;
+    int n_types;
+    const double *p;
+} md_params;
+
+/* Options; fill with md_default_options() and override. */
+typedef struct {
+    int precision;     /* MD_FP64: all arithmetic in fp64.  MD_MIXED: per-pair bond-order
+                          and derivative arithmetic in fp32; positions, velocities,
+                          minimum-image displacements and system totals in fp64. */
+    double skin;       /* Verlet skin (A); the list is rebuilt when an atom has moved more
+                          than skin/2 since the last build (0 = default, 0.15 x cutoff). */
+    int max_neigh;     /* list capacity per atom, <= 32 (default 32)                    */
+    int max_active;    /* capacity of in-cutoff neighbours per atom, <= 16 (0 = default:
+                          8 for Tersoff, 16 for SW, whose second shell in diamond Si sits
+                          only 0.07 A outside the cutoff)                                 */
+    int io;            /* MD_IO_HOST (default) or MD_IO_DEVICE                           */
+    void *cuda_stream; /* cudaStream_t to run on, or NULL: the context creates its own  */
+    size_t hbm_budget; /* bytes the context may allocate; 0 = unlimited                 */
+    int device;        /* CUDA device ordinal (default 0)                               */
+} md_options;
+
+/* Fill *opt with defaults (precision MD_FP64, skin 0 = default, max_neigh 32,
+ * max_active 0 = default, host I/O, own stream, no budget, device 0). */
+md_status md_default_options(md_options *opt);
+
+/* Create a context for n_atoms atoms (n_atoms >= 0).
+ *   box[3]  orthorhombic edge lengths (A), each > 0
+ *   pbc[3]  1 = periodic along that axis, 0 = open
+ *   types   n_atoms element indices (all 0 for a single element) -- host pointer always
+ *   masses_by_type  n_types masses (amu), host pointer
+ * Positions and velocities start at zero; set them before computing. */
+md_status md_create(md_ctx **out, const double box[3], const int pbc[3], int64_t n_atoms,
+                    const int32_t *types, const double *masses_by_type,
+                    const md_params *params, const md_options *opt);
+
+/* Positions, SoA (x[N], y[N], z[N]), A.  Coordinates on periodic axes are wrapped into
+ * [0, L).  Invalidates the neighbour list and forces. */
+md_status md_set_positions(md_ctx *ctx, const double *x, const double *y, const double *z);
+
+/* Velocities, SoA, A/fs. */
+md_status md_set_velocities(md_ctx *ctx, const double *vx, const double *vy, const double *vz);
+
+/* One force evaluation at the current positions and velocities (Algorithm 2's outputs):
+ *   f [3N] forces (eV/A), u [N] per-atom energies (eV), w [9N] per-atom virials (eV),
+ *   j [3N] per-atom potential heat currents (eV A/fs),
+ *   totals[13] = U, W (9 components), J (3), summed in fp64 in a fixed order.
+ * Any output pointer may be NULL (not requested).  totals is always a host pointer. */
+md_status md_compute(md_ctx *ctx, double *f, double *u, double *w, double *j, double *totals);
+
+/* Advance n_steps velocity-Verlet steps of dt_fs (NVE):
+ *   v += F/m dt/2; x += v dt (wrapped); [rebuild list if needed]; F = F(x);
+ *   v += F/m dt/2; record U, K, J with x(t+dt), v(t+dt).
+ * series: NULL or n_steps x 5 doubles (U, K, Jx, Jy, Jz per step; host pointer, or a
+ * device pointer under MD_IO_DEVICE).  Steps are replayed from a CUDA graph; the host
+ * is not involved between steps. */
+md_status md_run(md_ctx *ctx, int64_t n_steps, double dt_fs, double *series);
+
+/* Current positions and velocities, each 3N SoA; either may be NULL. */
+md_status md_get_state(md_ctx *ctx, double *x, double *v);
+
+/* Counters for tests and benchmarks. */
+typedef struct {
+    int64_t n_atoms;
+    int64_t steps_done;      /* MD steps since creation                               */
+    int64_t n_rebuilds;      /* neighbour-list builds since creation                  */
+    int max_neigh_seen;      /* largest list length at the last build                 */
+    int kernel_launches_per_step; /* kernels one md_run step launches                 */
+    size_t device_bytes;     /* bytes the context has allocated on the device         */
+} md_stats;
+md_status md_get_stats(md_ctx *ctx, md_stats *out);
+
+/* Per-kernel timing.  While enabled, md_run records CUDA events around each kernel
+ * class of every step and accumulates their elapsed times; md_kernel_times returns, for
+ * up to max_k classes, the name, the number of timed launches and the total ms. */
+md_status md_set_profiling(md_ctx *ctx, int enable);
+md_status md_kernel_times(md_ctx *ctx, int max_k, const char **names, int64_t *launches,
+                          double *total_ms, int *n_out);
+
+/* Message of the last failing call (empty string if none).  Never NULL. */
+const char *md_last_error(const md_ctx *ctx);
+
+/* Free the context and all of its device memory.  NULL is accepted. */
+void md_destroy(md_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MD_H */

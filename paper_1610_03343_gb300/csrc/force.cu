@@ -1,0 +1,611 @@
+// force.cu -- the force hot path in the paper's explicit pairwise-force form.
+//
+// Pass A, "pair pass" (one thread per atom i, Algorithm 3 and the dU_i/dr_ij part of
+// Algorithm 2 fused): for every list neighbour j the fp64 minimum-image bond r_ij
+// (Algorithm 2's minimum-image step); the in-cutoff ones are staged in shared memory
+// (SoA across the block's threads), then
+//   Tersoff: zeta_ij (Eq. 4) for every bond, b_ij and db/dzeta (Eq. 3), U_i (Eq. 2) and
+//            dU_i/dr_ij, whose chain rule runs through b_ij and every b_ik (k != j);
+//   SW:      the two-body and vertex three-body sums in one pass (no precompute, as
+//            the paper notes for SW in Sec. 2.3).
+// Every bond order is computed once per bond: the paper's force kernel recomputes
+// dU_j/dr_ji inside atom i's thread (Algorithm 2, the loop over j's neighbours); here
+// each atom writes its own dU_i/dr_ij once and the gather reads the partner's value.
+//
+// Pass B, "gather" (one thread per atom i, Eqs. 28-30): F_i = sum_j (d_ij - d_ji),
+// W_i = -1/2 sum_j r_ij (x) (d_ij - d_ji), J_i = (sum_j r_ij (x) d_ji) . v_i, where
+// d_ji is found through the reverse-slot index.  Each atom's sums live in one thread:
+// no atomics, fixed summation order, bitwise-reproducible results.  The gather also
+// applies the second velocity-Verlet half-kick and writes per-block fp64 partial sums
+// of U, K, J and W; a one-block kernel adds them in a fixed order.
+#include "md_plan.cuh"
+
+namespace mdk {
+
+const char *kKernelClassNames[KC_COUNT] = {"kick_drift", "rebuild", "pair", "gather", "reduce"};
+
+namespace {
+
+// ---------------------------------------------------------------- precision
+template <typename T> struct M;
+template <> struct M<double> {
+    static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+    static __device__ __forceinline__ double exp_(double x) { return exp(x); }
+    static __device__ __forceinline__ double log_(double x) { return log(x); }
+    static __device__ __forceinline__ double log1p_(double x) { return log1p(x); }
+    static __device__ __forceinline__ void sincos_(double x, double *s, double *c) { sincos(x, s, c); }
+    static __device__ __forceinline__ double pow_(double x, double y) { return pow(x, y); }
+};
+template <> struct M<float> {
+    static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+    static __device__ __forceinline__ float exp_(float x) { return expf(x); }
+    static __device__ __forceinline__ float log_(float x) { return logf(x); }
+    static __device__ __forceinline__ float log1p_(float x) { return log1pf(x); }
+    static __device__ __forceinline__ void sincos_(float x, float *s, float *c) { sincosf(x, s, c); }
+    static __device__ __forceinline__ float pow_(float x, float y) { return powf(x, y); }
+};
+
+template <typename T>
+__device__ __forceinline__ T ipow(T x, int n)
+{
+    T r = T(1);
+    for (int k = 0; k < n; ++k) r *= x;
+    return r;
+}
+
+// Shared-memory staging of atom i's in-cutoff neighbours: field f of neighbour k of
+// thread t lives at s[(f MAXA + k) BLOCK + t] (consecutive threads, consecutive words).
+template <typename T, int MAXA, int BLOCK>
+struct Stage {
+    T *s;
+    int t;
+    __device__ __forceinline__ T &operator()(int f, int k) const { return s[(f * MAXA + k) * BLOCK + t]; }
+};
+
+// ------------------------------------------------------- neighbour staging
+// Computes the fp64 minimum-image r_ij for each list slot, keeps the slots with
+// |r_ij|^2 < rc^2, writes their bond vectors (compact row k) to global memory and
+// stages (x, y, z, r^2) in the shared fields fx, fy, fz, fr2.  Returns the count and
+// the active-slot mask.
+template <typename T, int MAXA, int BLOCK>
+__device__ __forceinline__ int collect_bonds(const PairArgs<T> &a, int64_t i, uint32_t &mask,
+                                             const Stage<T, MAXA, BLOCK> &S, int fx, int fy, int fz,
+                                             int fr2)
+{
+    const int64_t N = a.N;
+    const double xi = a.pos[i], yi = a.pos[N + i], zi = a.pos[2 * N + i];
+    const int nn = a.nn[i];
+    int na = 0;
+    mask = 0u;
+    for (int m = 0; m < nn; ++m) {
+        const int j = a.nl[(int64_t)m * N + i];
+        const double dx = min_image(a.pos[j] - xi, a.box.L[0], a.box.invL[0], a.box.pbc[0]);
+        const double dy = min_image(a.pos[N + j] - yi, a.box.L[1], a.box.invL[1], a.box.pbc[1]);
+        const double dz = min_image(a.pos[2 * N + j] - zi, a.box.L[2], a.box.invL[2], a.box.pbc[2]);
+        const T tx = T(dx), ty = T(dy), tz = T(dz);
+        const T r2 = tx * tx + ty * ty + tz * tz;
+        if (r2 < a.rc2) {
+            if (na < MAXA) {
+                S(fx, na) = tx; S(fy, na) = ty; S(fz, na) = tz; S(fr2, na) = r2;
+                a.r[(0 * MAXA + na) * N + i] = tx;
+                a.r[(1 * MAXA + na) * N + i] = ty;
+                a.r[(2 * MAXA + na) * N + i] = tz;
+            }
+            mask |= 1u << m;
+            ++na;
+        }
+    }
+    if (na > MAXA) {
+        a.flags->active_overflow = 1;
+        na = MAXA;
+    }
+    return na;
+}
+
+// ------------------------------------------------------------------ Tersoff
+enum { TF_UX, TF_UY, TF_UZ, TF_IR, TF_FC, TF_DFC, TF_FR, TF_FA, TF_Z, TF_DX, TF_DY, TF_DZ, TF_NF };
+
+// g(cos) of Eq. 5 written as 1 + c^2 (h-cos)^2 / (d^2 (d^2 + (h-cos)^2)): the same
+// function as printed, without the cancellation of c^2/d^2 - c^2/(d^2+(h-cos)^2)
+// (about 4e7 - 4e7 for silicon), so that it stays accurate in fp32.  Also dg/dcos.
+template <typename T>
+__device__ __forceinline__ void tersoff_g(const TersoffP &p, T cs, T &g, T &dg)
+{
+    const T hc = T(p.h) - cs;
+    const T den = T(p.d2) + hc * hc;
+    const T inv = T(1) / den;
+    g = T(1) + T(p.c2) * hc * hc * inv / T(p.d2);
+    dg = T(-2) * T(p.c2) * hc * inv * inv;
+}
+
+// b = (1 + (beta zeta)^n)^(-1/(2n)) (Eq. 3) and db/dzeta = -1/2 b x / (zeta (1 + x)),
+// x = (beta zeta)^n.  b = 1, db = 0 at zeta = 0 (every dzeta/dr it multiplies is 0).
+template <typename T>
+__device__ __forceinline__ void tersoff_b(const TersoffP &p, T zeta, T &b, T &db)
+{
+    if (!(zeta > T(0)) || p.beta_zero) {
+        b = T(1);
+        db = T(0);
+        return;
+    }
+    const T x = M<T>::exp_(T(p.n) * (M<T>::log_(zeta) + T(p.ln_beta)));
+    b = M<T>::exp_(-T(p.inv2n) * M<T>::log1p_(x));
+    db = T(-0.5) * b * x / (zeta * (T(1) + x));
+}
+
+template <typename T, int MAXA, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_pair_tersoff(PairArgs<T> a, TersoffP p)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
+    if (i >= a.N) return;
+    const int64_t N = a.N;
+    Stage<T, MAXA, BLOCK> S{reinterpret_cast<T *>(smem), (int)threadIdx.x};
+
+    uint32_t mask;
+    const int na = collect_bonds<T, MAXA, BLOCK>(a, i, mask, S, TF_UX, TF_UY, TF_UZ, TF_IR);
+
+    // per-bond radial functions (the staged vectors become unit vectors, r^2 -> 1/r)
+    for (int k = 0; k < na; ++k) {
+        const T r = M<T>::sqrt_(S(TF_IR, k));
+        const T ir = T(1) / r;
+        S(TF_UX, k) *= ir;
+        S(TF_UY, k) *= ir;
+        S(TF_UZ, k) *= ir;
+        S(TF_IR, k) = ir;
+        T fc = T(1), dfc = T(0);
+        if (r >= T(p.R)) {
+            T sn, cn;
+            M<T>::sincos_(T(p.pi_SR) * (r - T(p.R)), &sn, &cn);
+            fc = T(0.5) + T(0.5) * cn;
+            dfc = T(-0.5) * T(p.pi_SR) * sn;
+        }
+        S(TF_FC, k) = fc;
+        S(TF_DFC, k) = dfc;
+        S(TF_FR, k) = T(p.A) * M<T>::exp_(-T(p.lam) * r);
+        S(TF_FA, k) = T(p.B) * M<T>::exp_(-T(p.mu) * r);
+        S(TF_Z, k) = T(0);
+    }
+    // zeta_ij = sum_{k != j} f_C(r_ik) g(theta_ijk), each unordered pair once
+    for (int j = 0; j < na; ++j) {
+        const T ujx = S(TF_UX, j), ujy = S(TF_UY, j), ujz = S(TF_UZ, j), fcj = S(TF_FC, j);
+        T zj = S(TF_Z, j);
+        for (int k = j + 1; k < na; ++k) {
+            const T cs = ujx * S(TF_UX, k) + ujy * S(TF_UY, k) + ujz * S(TF_UZ, k);
+            T g, dg;
+            tersoff_g(p, cs, g, dg);
+            zj += S(TF_FC, k) * g;
+            S(TF_Z, k) += fcj * g;
+        }
+        S(TF_Z, j) = zj;
+    }
+    // bond orders, U_i, radial part of dU_i/dr_ij; P_k = -1/2 f_C f_A b'_k kept in TF_Z
+    T ui = T(0);
+    for (int k = 0; k < na; ++k) {
+        T b, db;
+        tersoff_b(p, S(TF_Z, k), b, db);
+        const T fc = S(TF_FC, k), dfc = S(TF_DFC, k), fr = S(TF_FR, k), fa = S(TF_FA, k);
+        ui += T(0.5) * fc * (fr - b * fa);
+        const T dR = dfc * fr - T(p.lam) * fc * fr;   // (f_C f_R)'
+        const T dA = dfc * fa - T(p.mu) * fc * fa;    // (f_C f_A)'
+        const T radial = T(0.5) * (dR - b * dA);
+        S(TF_DX, k) = radial * S(TF_UX, k);
+        S(TF_DY, k) = radial * S(TF_UY, k);
+        S(TF_DZ, k) = radial * S(TF_UZ, k);
+        S(TF_Z, k) = T(-0.5) * fc * fa * db;
+    }
+    // angular part: for each unordered pair (j,k), with dcos_j = (u_k - cos u_j)/r_ij,
+    //   d_j += (P_j fc_k + P_k fc_j) g' dcos_j + P_k fc'_j g u_j   (and j <-> k)
+    for (int j = 0; j < na; ++j) {
+        const T ujx = S(TF_UX, j), ujy = S(TF_UY, j), ujz = S(TF_UZ, j);
+        const T irj = S(TF_IR, j), fcj = S(TF_FC, j), dfcj = S(TF_DFC, j), Pj = S(TF_Z, j);
+        T djx = S(TF_DX, j), djy = S(TF_DY, j), djz = S(TF_DZ, j);
+        for (int k = j + 1; k < na; ++k) {
+            const T ukx = S(TF_UX, k), uky = S(TF_UY, k), ukz = S(TF_UZ, k);
+            const T irk = S(TF_IR, k), fck = S(TF_FC, k), dfck = S(TF_DFC, k), Pk = S(TF_Z, k);
+            const T cs = ujx * ukx + ujy * uky + ujz * ukz;
+            T g, dg;
+            tersoff_g(p, cs, g, dg);
+            const T Q = (Pj * fck + Pk * fcj) * dg;
+            const T cj = Pk * dfcj * g, ck = Pj * dfck * g;
+            const T qj = Q * irj, qk = Q * irk;
+            djx += qj * (ukx - cs * ujx) + cj * ujx;
+            djy += qj * (uky - cs * ujy) + cj * ujy;
+            djz += qj * (ukz - cs * ujz) + cj * ujz;
+            S(TF_DX, k) += qk * (ujx - cs * ukx) + ck * ukx;
+            S(TF_DY, k) += qk * (ujy - cs * uky) + ck * uky;
+            S(TF_DZ, k) += qk * (ujz - cs * ukz) + ck * ukz;
+        }
+        a.d[(0 * MAXA + j) * N + i] = djx;
+        a.d[(1 * MAXA + j) * N + i] = djy;
+        a.d[(2 * MAXA + j) * N + i] = djz;
+    }
+    a.mask[i] = mask;
+    a.u[i] = double(ui);
+}
+
+// ---------------------------------------------------------- Stillinger-Weber
+enum { SW_UX, SW_UY, SW_UZ, SW_IR, SW_E, SW_DE, SW_DX, SW_DY, SW_DZ, SW_NF };
+
+template <typename T, int MAXA, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_pair_sw(PairArgs<T> a, SWP p)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
+    if (i >= a.N) return;
+    const int64_t N = a.N;
+    Stage<T, MAXA, BLOCK> S{reinterpret_cast<T *>(smem), (int)threadIdx.x};
+    uint32_t mask;
+    const int na = collect_bonds<T, MAXA, BLOCK>(a, i, mask, S, SW_UX, SW_UY, SW_UZ, SW_IR);
+
+    T ui = T(0);
+    const T rc = T(p.rc), sig = T(p.sig);
+    for (int k = 0; k < na; ++k) {
+        const T r = M<T>::sqrt_(S(SW_IR, k));
+        const T ir = T(1) / r;
+        const T ux = S(SW_UX, k) * ir, uy = S(SW_UY, k) * ir, uz = S(SW_UZ, k) * ir;
+        S(SW_UX, k) = ux; S(SW_UY, k) = uy; S(SW_UZ, k) = uz; S(SW_IR, k) = ir;
+        const T irc = T(1) / (r - rc);                 // 1/(r - a sigma) < 0
+        const T e2 = M<T>::exp_(sig * irc);
+        const T E = M<T>::exp_(T(p.gamsig) * irc);
+        S(SW_E, k) = E;
+        S(SW_DE, k) = -T(p.gamsig) * irc * irc * E;
+        // phi2 = A eps [B (sigma/r)^p - (sigma/r)^q] exp(sigma/(r - a sigma))
+        const T sr = sig * ir;
+        T sp, sq;
+        if (p.p_int >= 0) sp = ipow(sr, p.p_int); else sp = M<T>::pow_(sr, T(p.p));
+        if (p.q_int >= 0) sq = ipow(sr, p.q_int); else sq = M<T>::pow_(sr, T(p.q));
+        const T poly = T(p.B) * sp - sq;
+        const T dpoly = (-T(p.p) * T(p.B) * sp + T(p.q) * sq) * ir;
+        ui += T(0.5) * T(p.Aeps) * poly * e2;
+        const T dphi = T(p.Aeps) * (dpoly * e2 - poly * sig * irc * irc * e2);
+        S(SW_DX, k) = T(0.5) * dphi * ux;
+        S(SW_DY, k) = T(0.5) * dphi * uy;
+        S(SW_DZ, k) = T(0.5) * dphi * uz;
+    }
+    // phi3 = lambda eps (cos + 1/3)^2 E(r_ij) E(r_ik), vertex i, each unordered pair once
+    for (int j = 0; j < na; ++j) {
+        const T ujx = S(SW_UX, j), ujy = S(SW_UY, j), ujz = S(SW_UZ, j);
+        const T irj = S(SW_IR, j), Ej = S(SW_E, j), dEj = S(SW_DE, j);
+        T djx = S(SW_DX, j), djy = S(SW_DY, j), djz = S(SW_DZ, j);
+        for (int k = j + 1; k < na; ++k) {
+            const T ukx = S(SW_UX, k), uky = S(SW_UY, k), ukz = S(SW_UZ, k);
+            const T irk = S(SW_IR, k), Ek = S(SW_E, k), dEk = S(SW_DE, k);
+            const T cs = ujx * ukx + ujy * uky + ujz * ukz;
+            const T t = cs + T(1.0 / 3.0);
+            const T EE = Ej * Ek;
+            ui += T(p.lameps) * t * t * EE;
+            const T c1 = T(2) * T(p.lameps) * t * EE;
+            const T cj = T(p.lameps) * t * t * dEj * Ek, ck = T(p.lameps) * t * t * Ej * dEk;
+            const T qj = c1 * irj, qk = c1 * irk;
+            djx += qj * (ukx - cs * ujx) + cj * ujx;
+            djy += qj * (uky - cs * ujy) + cj * ujy;
+            djz += qj * (ukz - cs * ujz) + cj * ujz;
+            S(SW_DX, k) += qk * (ujx - cs * ukx) + ck * ukx;
+            S(SW_DY, k) += qk * (ujy - cs * uky) + ck * uky;
+            S(SW_DZ, k) += qk * (ujz - cs * ukz) + ck * ukz;
+        }
+        a.d[(0 * MAXA + j) * N + i] = djx;
+        a.d[(1 * MAXA + j) * N + i] = djy;
+        a.d[(2 * MAXA + j) * N + i] = djz;
+    }
+    a.mask[i] = mask;
+    a.u[i] = double(ui);
+}
+
+// ------------------------------------------------------------------ gather
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int BLOCK>
+__device__ __forceinline__ void block_partials(double (&vals)[kNumPartials], double *out)
+{
+    __shared__ double red[BLOCK / 32][kNumPartials];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < kNumPartials; ++c) {
+        double v = warp_sum(vals[c]);
+        if (lane == 0) red[wid][c] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kNumPartials) {
+        double s = 0.0;
+        for (int w = 0; w < BLOCK / 32; ++w) s += red[w][threadIdx.x];
+        out[(int64_t)blockIdx.x * kNumPartials + threadIdx.x] = s;
+    }
+}
+
+template <typename T, int MAXA, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_gather(GatherArgs<T> a)
+{
+    const int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
+    const int64_t N = a.N;
+    double vals[kNumPartials];
+#pragma unroll
+    for (int c = 0; c < kNumPartials; ++c) vals[c] = 0.0;
+    if (i < N) {
+        uint32_t mask = a.mask[i];
+        T f0 = 0, f1 = 0, f2 = 0;
+        T w[9], mj[9];
+#pragma unroll
+        for (int c = 0; c < 9; ++c) { w[c] = 0; mj[c] = 0; }
+        int k = 0;
+        while (mask != 0u && k < MAXA) {
+            const int m = __ffs(mask) - 1;
+            mask &= mask - 1u;
+            const int j = a.nl[(int64_t)m * N + i];
+            const int mr = a.rev[(int64_t)m * N + i];
+            const uint32_t maskj = a.mask[j];
+            const int kr = __popc(maskj & ((1u << mr) - 1u));
+            if (kr < MAXA) {
+                const T dx = a.d[(0 * MAXA + k) * N + i], dy = a.d[(1 * MAXA + k) * N + i],
+                        dz = a.d[(2 * MAXA + k) * N + i];
+                const T ex = a.d[(0 * MAXA + kr) * N + j], ey = a.d[(1 * MAXA + kr) * N + j],
+                        ez = a.d[(2 * MAXA + kr) * N + j];
+                const T rx = a.r[(0 * MAXA + k) * N + i], ry = a.r[(1 * MAXA + k) * N + i],
+                        rz = a.r[(2 * MAXA + k) * N + i];
+                const T gx = dx - ex, gy = dy - ey, gz = dz - ez;   // F_ij = d_ij - d_ji
+                f0 += gx; f1 += gy; f2 += gz;
+                w[0] += rx * gx; w[1] += rx * gy; w[2] += rx * gz;
+                w[3] += ry * gx; w[4] += ry * gy; w[5] += ry * gz;
+                w[6] += rz * gx; w[7] += rz * gy; w[8] += rz * gz;
+                mj[0] += rx * ex; mj[1] += rx * ey; mj[2] += rx * ez;
+                mj[3] += ry * ex; mj[4] += ry * ey; mj[5] += ry * ez;
+                mj[6] += rz * ex; mj[7] += rz * ey; mj[8] += rz * ez;
+            }
+            ++k;
+        }
+        const double F[3] = {double(f0), double(f1), double(f2)};
+        if (!(isfinite(F[0]) && isfinite(F[1]) && isfinite(F[2]))) a.flags->nonfinite = 1;
+        a.force[i] = F[0];
+        a.force[N + i] = F[1];
+        a.force[2 * N + i] = F[2];
+        const int t = a.type[i];
+        double v[3] = {a.vel[i], a.vel[N + i], a.vel[2 * N + i]};
+        if (a.kick) {
+            const double h = a.hk[t];
+            v[0] = fma(h, F[0], v[0]);
+            v[1] = fma(h, F[1], v[1]);
+            v[2] = fma(h, F[2], v[2]);
+            a.vel[i] = v[0];
+            a.vel[N + i] = v[1];
+            a.vel[2 * N + i] = v[2];
+        }
+        double J[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+            J[r] = double(mj[3 * r]) * v[0] + double(mj[3 * r + 1]) * v[1] + double(mj[3 * r + 2]) * v[2];
+        const double ke = 0.5 * a.mass[t] * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) / kAccUnit;
+        vals[0] = a.u[i];
+        vals[1] = ke;
+        vals[2] = J[0]; vals[3] = J[1]; vals[4] = J[2];
+#pragma unroll
+        for (int c = 0; c < 9; ++c) vals[5 + c] = -0.5 * double(w[c]);
+        if (a.w_out) {
+#pragma unroll
+            for (int c = 0; c < 9; ++c) a.w_out[c * N + i] = vals[5 + c];
+        }
+        if (a.j_out) {
+            a.j_out[i] = J[0];
+            a.j_out[N + i] = J[1];
+            a.j_out[2 * N + i] = J[2];
+        }
+    }
+    block_partials<BLOCK>(vals, a.partials);
+}
+
+// One block: partial sums in a fixed order -> totals (U, K, J, W) and a series row.
+constexpr int kReduceThreads = 256;
+__global__ void __launch_bounds__(kReduceThreads)
+k_reduce(const double *partials, int nb, double *totals, double *series, Flags *flags, bool record)
+{
+    __shared__ double red[kReduceThreads / 32][kNumPartials];
+    double acc[kNumPartials];
+#pragma unroll
+    for (int c = 0; c < kNumPartials; ++c) acc[c] = 0.0;
+    for (int b = threadIdx.x; b < nb; b += kReduceThreads)
+#pragma unroll
+        for (int c = 0; c < kNumPartials; ++c) acc[c] += partials[(int64_t)b * kNumPartials + c];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < kNumPartials; ++c) {
+        double v = warp_sum(acc[c]);
+        if (lane == 0) red[wid][c] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kNumPartials) {
+        double s = 0.0;
+        for (int w = 0; w < kReduceThreads / 32; ++w) s += red[w][threadIdx.x];
+        totals[threadIdx.x] = s;
+        if (record && threadIdx.x < 5) series[flags->step * 5 + threadIdx.x] = s;
+    }
+    __syncthreads();
+    if (record && threadIdx.x == 0) flags->step += 1;
+}
+
+// ------------------------------------------------------------------ integrator
+struct KickDriftArgs {
+    int64_t N;
+    Box box;
+    double *pos, *vel;
+    const double *force, *pos_build;
+    const int *type;
+    double hk[kMaxTypes];   // dt/2 * acc / m per type
+    double dt;
+    double half_skin2;
+    Flags *flags;
+};
+
+__global__ void k_kick_drift(KickDriftArgs a)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.N) return;
+    const int64_t N = a.N;
+    const double h = a.hk[a.type[i]];
+    double d2 = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        double v = fma(h, a.force[c * N + i], a.vel[c * N + i]);
+        double x = fma(a.dt, v, a.pos[c * N + i]);
+        if (a.box.pbc[c]) {
+            if (x >= a.box.L[c]) x -= a.box.L[c];
+            else if (x < 0.0) x += a.box.L[c];
+        }
+        a.vel[c * N + i] = v;
+        a.pos[c * N + i] = x;
+        const double d = min_image(x - a.pos_build[c * N + i], a.box.L[c], a.box.invL[c], a.box.pbc[c]);
+        d2 = fma(d, d, d2);
+    }
+    if (!(d2 <= a.half_skin2)) a.flags->rebuild = 1;
+}
+
+inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+constexpr int kPairBlockF64 = 64;
+constexpr int kPairBlockF32 = 128;
+constexpr int kGatherBlock = 128;
+
+template <typename T> constexpr int pair_block();
+template <> constexpr int pair_block<double>() { return kPairBlockF64; }
+template <> constexpr int pair_block<float>() { return kPairBlockF32; }
+
+template <typename T, int MAXA>
+size_t smem_for(int kind)
+{
+    const int nf = kind == 1 ? TF_NF : SW_NF;
+    return (size_t)nf * MAXA * pair_block<T>() * sizeof(T);
+}
+
+template <typename T, int MAXA>
+void configure_one()
+{
+    constexpr int B = pair_block<T>();
+    cudaFuncSetAttribute(k_pair_tersoff<T, MAXA, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem_for<T, MAXA>(1));
+    cudaFuncSetAttribute(k_pair_sw<T, MAXA, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem_for<T, MAXA>(2));
+}
+
+template <typename T, int MAXA>
+void pair_launch(const Plan &p, cudaStream_t s)
+{
+    constexpr int B = pair_block<T>();
+    PairArgs<T> a;
+    a.N = p.N;
+    a.box = p.box;
+    a.pos = p.pos;
+    a.nn = p.nn;
+    a.nl = p.nl;
+    a.cap = p.cap;
+    a.rc2 = T(p.rc * p.rc);
+    a.d = static_cast<T *>(p.pd);
+    a.r = static_cast<T *>(p.pr);
+    a.mask = p.mask;
+    a.u = p.u;
+    a.flags = p.flags;
+    if (p.kind == 1)
+        k_pair_tersoff<T, MAXA, B><<<blocks_for(p.N, B), B, smem_for<T, MAXA>(1), s>>>(a, p.tp);
+    else
+        k_pair_sw<T, MAXA, B><<<blocks_for(p.N, B), B, smem_for<T, MAXA>(2), s>>>(a, p.sp);
+}
+
+template <typename T, int MAXA>
+void gather_launch(const Plan &p, cudaStream_t s, const double *hk, bool store_wj)
+{
+    GatherArgs<T> a;
+    a.N = p.N;
+    a.nl = p.nl;
+    a.rev = p.rev;
+    a.mask = p.mask;
+    a.d = static_cast<const T *>(p.pd);
+    a.r = static_cast<const T *>(p.pr);
+    a.u = p.u;
+    a.type = p.type;
+    for (int t = 0; t < kMaxTypes; ++t) {
+        a.mass[t] = p.mass[t];
+        a.hk[t] = hk ? hk[t] : 0.0;
+    }
+    a.kick = hk != nullptr;
+    a.vel = p.vel;
+    a.force = p.force;
+    a.w_out = store_wj ? p.w : nullptr;
+    a.j_out = store_wj ? p.j : nullptr;
+    a.partials = p.partials;
+    a.flags = p.flags;
+    k_gather<T, MAXA, kGatherBlock><<<blocks_for(p.N, kGatherBlock), kGatherBlock, 0, s>>>(a);
+}
+
+}  // namespace
+
+size_t pair_smem_bytes(const Plan &p)
+{
+    if (p.precision == 0) return p.maxa <= 8 ? smem_for<double, 8>(p.kind) : smem_for<double, 16>(p.kind);
+    return p.maxa <= 8 ? smem_for<float, 8>(p.kind) : smem_for<float, 16>(p.kind);
+}
+
+void configure_kernels(const Plan &)
+{
+    static bool done = false;
+    if (done) return;
+    configure_one<double, 8>();
+    configure_one<double, 16>();
+    configure_one<float, 8>();
+    configure_one<float, 16>();
+    done = true;
+}
+
+void launch_kick_drift(const Plan &p, cudaStream_t s, const double *hk, double dt)
+{
+    if (p.N == 0) return;
+    KickDriftArgs a;
+    a.N = p.N;
+    a.box = p.box;
+    a.pos = p.pos;
+    a.vel = p.vel;
+    a.force = p.force;
+    a.pos_build = p.pos_build;
+    a.type = p.type;
+    for (int t = 0; t < kMaxTypes; ++t) a.hk[t] = hk[t];
+    a.dt = dt;
+    const double hs = 0.5 * p.skin;
+    a.half_skin2 = hs * hs;
+    a.flags = p.flags;
+    k_kick_drift<<<blocks_for(p.N, 256), 256, 0, s>>>(a);
+}
+
+void launch_pair(const Plan &p, cudaStream_t s)
+{
+    if (p.N == 0) return;
+    if (p.precision == 0) {
+        if (p.maxa <= 8) pair_launch<double, 8>(p, s); else pair_launch<double, 16>(p, s);
+    } else {
+        if (p.maxa <= 8) pair_launch<float, 8>(p, s); else pair_launch<float, 16>(p, s);
+    }
+}
+
+void launch_gather(const Plan &p, cudaStream_t s, const double *hk, bool store_wj)
+{
+    if (p.N == 0) return;
+    if (p.precision == 0) {
+        if (p.maxa <= 8) gather_launch<double, 8>(p, s, hk, store_wj);
+        else gather_launch<double, 16>(p, s, hk, store_wj);
+    } else {
+        if (p.maxa <= 8) gather_launch<float, 8>(p, s, hk, store_wj);
+        else gather_launch<float, 16>(p, s, hk, store_wj);
+    }
+}
+
+void launch_reduce(const Plan &p, cudaStream_t s, bool record_series)
+{
+    const int nb = p.N == 0 ? 0 : (int)blocks_for(p.N, kGatherBlock);
+    k_reduce<<<1, kReduceThreads, 0, s>>>(p.partials, nb, p.totals, p.series, p.flags,
+                                          record_series && p.series != nullptr);
+}
+
+int gather_blocks(int64_t N) { return N == 0 ? 1 : (int)blocks_for(N, kGatherBlock); }
+
+}  // namespace mdk

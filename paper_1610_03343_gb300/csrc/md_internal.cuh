@@ -1,0 +1,102 @@
+// md_internal.cuh -- device-side structures and helpers shared by the CUDA translation
+// units of libmd (neighbour build, force passes, integrator, C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mdk {
+
+// eV/(A amu) -> A/fs^2 (exact elementary charge, CODATA-2018 atomic mass constant)
+constexpr double kAccUnit = 9.648533215665328e-3;
+constexpr int kMaxTypes = 4;
+constexpr int kMaxListCap = 32;   // list slots per atom (active mask is 32 bits)
+
+// Orthorhombic box with per-axis periodicity.
+struct Box {
+    double L[3];
+    double invL[3];
+    int pbc[3];
+};
+
+// Device status words written by kernels and read by the host after a call.
+struct Flags {
+    int rebuild;          // 1: list must be rebuilt before the next force pass
+    int list_overflow;    // an atom found more than max_neigh neighbours
+    int active_overflow;  // an atom had more than max_active neighbours inside the cutoff
+    int nonfinite;        // a non-finite force appeared
+    int asym;             // a pair was missing from the partner's list
+    int max_nn;           // longest list at the last build
+    int n_rebuilds;       // builds since creation
+    int pad;
+    long long step;       // index of the next series row
+};
+
+// Tersoff (single element).  Eqs. 2-6 with Tersoff-1989 f_R, f_A, f_C.
+struct TersoffP {
+    double A, B, lam, mu, beta, n, c, d, h, R, S;
+    double c2, d2, c2d2;        // c^2, d^2, c^2/d^2
+    double pi_SR;               // pi / (S - R)
+    double ln_beta;             // log(beta)   (beta > 0), used in (beta zeta)^n
+    double inv2n;               // 1 / (2 n)
+    int beta_zero;              // beta == 0: b = 1 (pair limit)
+};
+
+// Stillinger-Weber (single element), U_i = 1/2 sum_j phi2 + sum_{j<k} phi3 (vertex i).
+struct SWP {
+    double eps, sig, a, lam, gam, A, B, p, q;
+    double rc;                  // a * sigma
+    double Aeps, lameps, gamsig;
+    int p_int, q_int;           // exponents as integers when they are (4 and 0 in SW 1985)
+};
+
+// Arguments of the per-atom pair pass (one thread per atom i; computes U_i and
+// dU_i/dr_ij for every in-cutoff neighbour j of i, Eqs. 14 / 28-30's building block).
+template <typename T>
+struct PairArgs {
+    int64_t N;
+    Box box;
+    const double *pos;      // 3N SoA
+    const int *nn;          // N list lengths
+    const int *nl;          // cap x N, column-major: nl[m N + i]
+    int cap;                // list capacity
+    T rc2;                  // cutoff^2 in T
+    // outputs, "compact active" layout: row k = k-th in-cutoff neighbour of i
+    T *d;                   // 3 x MAXA x N : d[(c MAXA + k) N + i] = dU_i/dr_ij (component c)
+    T *r;                   // 3 x MAXA x N : r_ij
+    uint32_t *mask;         // N : bit m set <=> list slot m is inside the cutoff
+    double *u;              // N : U_i
+    Flags *flags;
+};
+
+// Arguments of the per-atom gather (one thread per atom i; Eqs. 28-30 + half-kick).
+template <typename T>
+struct GatherArgs {
+    int64_t N;
+    const int *nl;
+    const uint8_t *rev;     // cap x N: slot of i in j's list
+    const uint32_t *mask;
+    const T *d;
+    const T *r;
+    const double *u;
+    const int *type;
+    double mass[kMaxTypes];
+    double hk[kMaxTypes];   // half-kick factor dt/2 * acc / m per type
+    int kick;               // apply the half-kick v += hk F
+    double *vel;            // 3N, updated in place when kicking
+    double *force;          // 3N, written
+    double *w_out;          // 9N or nullptr
+    double *j_out;          // 3N or nullptr
+    double *partials;       // gridDim.x x kNumPartials
+    Flags *flags;
+};
+
+// per-block partial sums: U, K, J(3), W(9)
+constexpr int kNumPartials = 14;
+
+__device__ __forceinline__ double min_image(double d, double L, double invL, int periodic)
+{
+    return periodic ? fma(-L, rint(d * invL), d) : d;
+}
+
+}  // namespace mdk

@@ -1,0 +1,320 @@
+"""Thin Python binding of libmd.so (include/md.h) -- argument marshalling only.
+
+Every computation runs in the CUDA library.  The functions below carry the C names
+(md_create, md_set_positions, md_compute, md_run, md_get_state, ...) and take numpy
+arrays (host I/O) or torch CUDA tensors (device I/O); `System` is a small convenience
+wrapper over one context.  Loading fails loudly if the library has not been built:
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+MD_OK = 0
+MD_TERSOFF = 1
+MD_SW = 2
+MD_FP64 = 0
+MD_MIXED = 1
+MD_IO_HOST = 0
+MD_IO_DEVICE = 1
+
+STATUS = {0: "MD_OK", -1: "MD_ERR_ARG", -2: "MD_ERR_BOX", -3: "MD_ERR_NEIGH_OVERFLOW",
+          -4: "MD_ERR_OOM", -5: "MD_ERR_CUDA", -6: "MD_ERR_TIMEOUT", -7: "MD_ERR_NAN",
+          -8: "MD_ERR_STATE"}
+
+
+class MDError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+
+
+class md_params(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("n_types", ctypes.c_int), ("p", ctypes.POINTER(ctypes.c_double))]
+
+
+class md_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("skin", ctypes.c_double), ("max_neigh", ctypes.c_int),
+                ("max_active", ctypes.c_int), ("io", ctypes.c_int), ("cuda_stream", ctypes.c_void_p),
+                ("hbm_budget", ctypes.c_size_t), ("device", ctypes.c_int)]
+
+
+class md_stats(ctypes.Structure):
+    _fields_ = [("n_atoms", ctypes.c_int64), ("steps_done", ctypes.c_int64), ("n_rebuilds", ctypes.c_int64),
+                ("max_neigh_seen", ctypes.c_int), ("kernel_launches_per_step", ctypes.c_int),
+                ("device_bytes", ctypes.c_size_t)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+EXPORTS = ["md_default_options", "md_create", "md_set_positions", "md_set_velocities", "md_compute",
+           "md_run", "md_get_state", "md_get_stats", "md_set_profiling", "md_kernel_times",
+           "md_last_error", "md_destroy"]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libmd.so.  Raises if it is missing (build it with __graft_entry__.build())."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_build.LIB):
+            if not build_if_missing:
+                raise RuntimeError(f"libmd.so not built ({_build.LIB}); run __graft_entry__.build()")
+            _build.build()
+        lib = ctypes.CDLL(_build.LIB)
+        P = ctypes.c_void_p
+        S = ctypes.c_int
+        lib.md_default_options.argtypes = [ctypes.POINTER(md_options)]
+        lib.md_create.argtypes = [ctypes.POINTER(P), P, P, ctypes.c_int64, P, P,
+                                  ctypes.POINTER(md_params), ctypes.POINTER(md_options)]
+        lib.md_set_positions.argtypes = [P, P, P, P]
+        lib.md_set_velocities.argtypes = [P, P, P, P]
+        lib.md_compute.argtypes = [P, P, P, P, P, P]
+        lib.md_run.argtypes = [P, ctypes.c_int64, ctypes.c_double, P]
+        lib.md_get_state.argtypes = [P, P, P]
+        lib.md_get_stats.argtypes = [P, ctypes.POINTER(md_stats)]
+        lib.md_set_profiling.argtypes = [P, ctypes.c_int]
+        lib.md_kernel_times.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
+                                        ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_int)]
+        lib.md_last_error.argtypes = [P]
+        lib.md_last_error.restype = ctypes.c_char_p
+        lib.md_destroy.argtypes = [P]
+        lib.md_destroy.restype = None
+        for f in EXPORTS:
+            if f not in ("md_last_error", "md_destroy"):
+                getattr(lib, f).restype = S
+        _lib = lib
+        return lib
+
+
+def _ptr(a):
+    """Address of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    if isinstance(a, int):
+        return a
+    raise TypeError(type(a))
+
+
+def _check(lib, ctx, status):
+    if status != MD_OK:
+        msg = lib.md_last_error(ctx).decode() if ctx else ""
+        raise MDError(status, msg)
+
+
+# ----------------------------------------------------------------- C names
+def md_default_options() -> md_options:
+    lib = load()
+    o = md_options()
+    _check(lib, None, lib.md_default_options(ctypes.byref(o)))
+    return o
+
+
+def md_create(box, pbc, n_atoms, types, masses_by_type, kind, params, opt: md_options | None = None):
+    lib = load()
+    box = np.ascontiguousarray(box, dtype=np.float64)
+    pbc = np.ascontiguousarray(pbc, dtype=np.int32)
+    types = np.ascontiguousarray(types, dtype=np.int32)
+    masses = np.ascontiguousarray(masses_by_type, dtype=np.float64)
+    prm_arr = np.ascontiguousarray(params, dtype=np.float64)
+    prm = md_params(int(kind), 1, prm_arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    ctx = ctypes.c_void_p()
+    st = lib.md_create(ctypes.byref(ctx), _ptr(box), _ptr(pbc), int(n_atoms), _ptr(types), _ptr(masses),
+                       ctypes.byref(prm), ctypes.byref(opt) if opt is not None else None)
+    if st != MD_OK:
+        raise MDError(st, "md_create failed")
+    return ctx
+
+
+def md_set_positions(ctx, x, y, z):
+    lib = load()
+    _check(lib, ctx, lib.md_set_positions(ctx, _ptr(x), _ptr(y), _ptr(z)))
+
+
+def md_set_velocities(ctx, vx, vy, vz):
+    lib = load()
+    _check(lib, ctx, lib.md_set_velocities(ctx, _ptr(vx), _ptr(vy), _ptr(vz)))
+
+
+def md_compute(ctx, f=None, u=None, w=None, j=None, totals=None):
+    lib = load()
+    _check(lib, ctx, lib.md_compute(ctx, _ptr(f), _ptr(u), _ptr(w), _ptr(j), _ptr(totals)))
+
+
+def md_run(ctx, n_steps, dt_fs, series=None):
+    lib = load()
+    _check(lib, ctx, lib.md_run(ctx, int(n_steps), float(dt_fs), _ptr(series)))
+
+
+def md_get_state(ctx, x=None, v=None):
+    lib = load()
+    _check(lib, ctx, lib.md_get_state(ctx, _ptr(x), _ptr(v)))
+
+
+def md_get_stats(ctx) -> md_stats:
+    lib = load()
+    s = md_stats()
+    _check(lib, ctx, lib.md_get_stats(ctx, ctypes.byref(s)))
+    return s
+
+
+def md_set_profiling(ctx, enable: bool):
+    lib = load()
+    _check(lib, ctx, lib.md_set_profiling(ctx, 1 if enable else 0))
+
+
+def md_kernel_times(ctx):
+    lib = load()
+    k = 8
+    names = (ctypes.c_char_p * k)()
+    n = (ctypes.c_int64 * k)()
+    ms = (ctypes.c_double * k)()
+    nout = ctypes.c_int()
+    _check(lib, ctx, lib.md_kernel_times(ctx, k, names, n, ms, ctypes.byref(nout)))
+    return {names[i].decode(): (int(n[i]), float(ms[i])) for i in range(nout.value)}
+
+
+def md_last_error(ctx) -> str:
+    return load().md_last_error(ctx).decode()
+
+
+def md_destroy(ctx):
+    if ctx:
+        load().md_destroy(ctx)
+
+
+# ----------------------------------------------------------------- convenience
+class System:
+    """One context with host (numpy) I/O, or device (torch CUDA tensor) I/O when
+    io=MD_IO_DEVICE.  Arrays are (N,3) row-major on the Python side and SoA in the
+    library; the transposes below are the marshalling."""
+
+    def __init__(self, box, pbc, n_atoms, kind, params, mass, precision=MD_FP64, skin=0.0,
+                 max_neigh=32, max_active=0, io=MD_IO_HOST, stream=None, hbm_budget=0):
+        self.n = int(n_atoms)
+        self.io = io
+        opt = md_default_options()
+        opt.precision = precision
+        opt.skin = skin
+        opt.max_neigh = max_neigh
+        opt.max_active = max_active
+        opt.io = io
+        opt.cuda_stream = stream
+        opt.hbm_budget = hbm_budget
+        self.ctx = md_create(box, pbc, self.n, np.zeros(self.n, np.int32), [mass], kind, params, opt)
+
+    def close(self):
+        if self.ctx:
+            md_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # host <-> SoA helpers
+    @staticmethod
+    def _soa(a):
+        a = np.asarray(a, dtype=np.float64)
+        return np.ascontiguousarray(a.T)
+
+    @staticmethod
+    def _device_soa(a):
+        # the library runs on its own stream: make torch's producer work visible first
+        import torch
+        t = a.t().contiguous()
+        torch.cuda.current_stream().synchronize()
+        return t
+
+    def set_positions(self, pos):
+        if self.io == MD_IO_DEVICE:
+            t = self._device_soa(pos)
+            md_set_positions(self.ctx, t[0], t[1], t[2])
+        else:
+            s = self._soa(pos)
+            md_set_positions(self.ctx, s[0], s[1], s[2])
+
+    def set_velocities(self, vel):
+        if self.io == MD_IO_DEVICE:
+            t = self._device_soa(vel)
+            md_set_velocities(self.ctx, t[0], t[1], t[2])
+        else:
+            s = self._soa(vel)
+            md_set_velocities(self.ctx, s[0], s[1], s[2])
+
+    def compute(self, want=("f", "u", "w", "j")):
+        n = self.n
+        if self.io == MD_IO_DEVICE:
+            import torch
+            mk = lambda c: torch.empty(c * max(n, 1), dtype=torch.float64, device="cuda")
+        else:
+            mk = lambda c: np.empty(c * max(n, 1), dtype=np.float64)
+        f = mk(3) if "f" in want else None
+        u = mk(1) if "u" in want else None
+        w = mk(9) if "w" in want else None
+        j = mk(3) if "j" in want else None
+        tot = np.zeros(13)
+        md_compute(self.ctx, f, u, w, j, tot)
+        out = {"totals": tot}
+        if f is not None:
+            out["F"] = f[:3 * n].reshape(3, n).T
+        if u is not None:
+            out["U"] = u[:n]
+        if w is not None:
+            out["W"] = w[:9 * n].reshape(9, n).T
+        if j is not None:
+            out["J"] = j[:3 * n].reshape(3, n).T
+        return out
+
+    def run(self, n_steps, dt, record=True):
+        series = np.zeros((max(n_steps, 1), 5)) if record else None
+        md_run(self.ctx, n_steps, dt, series)
+        return series[:n_steps] if record else None
+
+    def state(self):
+        x = np.empty(3 * max(self.n, 1))
+        v = np.empty(3 * max(self.n, 1))
+        md_get_state(self.ctx, x, v)
+        n = self.n
+        return x[:3 * n].reshape(3, n).T.copy(), v[:3 * n].reshape(3, n).T.copy()
+
+    def stats(self):
+        return md_get_stats(self.ctx)
+
+
+def from_inputs(sysm, precision=MD_FP64, **kw) -> System:
+    """Context for an inputs.System, with its positions and velocities uploaded."""
+    s = System(sysm.box, sysm.pbc, sysm.n, sysm.kind, sysm.params, sysm.mass, precision=precision, **kw)
+    s.set_positions(sysm.pos)
+    if sysm.vel is not None:
+        s.set_velocities(sysm.vel)
+    return s

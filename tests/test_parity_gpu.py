@@ -1,0 +1,186 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle, element by
+element, on the same seeded inputs.
+
+Error metric (per-atom fields): max_i |a_i - b_i|_inf / max_i |b_i|_inf; scalars |a-b|/|b|.
+Bounds: fp64 path 1e-12 on F, U_i, W_i, J_i and totals; trajectories 1e-10 after 50
+steps; mixed path (fp32 pair arithmetic) 1e-5 on forces.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1610_03343_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+TRAJ_TOL = 1e-10
+MIXED_TOL = 1e-5
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64); b = np.asarray(b, dtype=np.float64)
+    if b.size == 0:
+        return 0.0
+    den = np.abs(b).max()
+    if den == 0.0:
+        return float(np.abs(a).max())
+    return float(np.abs(a - b).max() / den)
+
+
+@pytest.fixture(scope="module")
+def md():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1610_03343_gb300 import _build, md as M
+    _build.build()
+    M.load()
+    return M
+
+
+def compare_compute(md, sysm, tol=FP64_TOL, precision=0, **kw):
+    ref = O.compute(sysm.pos, sysm.box, sysm.pbc, sysm.kind, sysm.params, sysm.vel)
+    with md.from_inputs(sysm, precision=precision, **kw) as g:
+        out = g.compute()
+    errs = {k: rel(out[k], ref[k]) for k in ("F", "U", "W", "J")}
+    errs["totals"] = rel(out["totals"], ref["totals"])
+    for k, e in errs.items():
+        assert e < tol, (sysm.name, k, e, errs)
+    return errs
+
+
+CASES = [
+    ("tersoff_si_1728", lambda: I.si_diamond_tersoff(n=6)),
+    ("tersoff_si_1000_ragged", lambda: I.si_diamond_tersoff(n=5, jitter_amp=0.1, seed_pos=3)),
+    ("sw_si_216", lambda: I.si_diamond_sw(n=3, jitter_amp=0.1)),
+    ("sw_si_4096_300K", lambda: I.si_diamond_sw(n=8, jitter_amp=0.08)),
+    ("tersoff_c_graphene_960", lambda: I.c_graphene_tersoff(nx=10, ny=24)),
+    ("tersoff_c_diamond_512", lambda: I.c_diamond_tersoff(n=4)),
+    ("tersoff_cluster", lambda: I.cluster(I.si_diamond_tersoff(n=4, jitter_amp=0.1), 7.0)),
+    ("sw_cluster", lambda: I.cluster(I.si_diamond_sw(n=4, jitter_amp=0.1), 7.0)),
+    ("tersoff_tight_box", lambda: I.random_cell(14, [6.95, 7.0, 7.05], 2.0, I.MD_TERSOFF,
+                                                I.TERSOFF_SI_1989, I.MASS_SI, 31)),
+    ("sw_tight_box", lambda: I.random_cell(20, [8.7, 8.8, 8.9], 2.0, I.MD_SW, I.SW_SI_1985,
+                                           I.MASS_SI, 33)),
+]
+
+
+@pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])
+def test_compute_fp64_matches_oracle(md, name, make):
+    compare_compute(md, make())
+
+
+@pytest.mark.parametrize("name,make", CASES[:6], ids=[c[0] for c in CASES[:6]])
+def test_compute_mixed_force_error(md, name, make):
+    sysm = make()
+    ref = O.compute(sysm.pos, sysm.box, sysm.pbc, sysm.kind, sysm.params, sysm.vel)
+    with md.from_inputs(sysm, precision=md.MD_MIXED) as g:
+        out = g.compute()
+    assert rel(out["F"], ref["F"]) < MIXED_TOL
+    assert rel(out["U"], ref["U"]) < MIXED_TOL
+    assert rel(out["W"], ref["W"]) < 1e-4
+    assert rel(out["J"], ref["J"]) < 1e-4
+    assert rel(out["totals"][:1], ref["totals"][:1]) < 1e-6
+
+
+def test_empty_system(md):
+    box = np.array([20.0, 20.0, 20.0])
+    g = md.System(box, [1, 1, 1], 0, I.MD_TERSOFF, I.TERSOFF_SI_1989, I.MASS_SI)
+    g.set_positions(np.zeros((0, 3)))
+    g.set_velocities(np.zeros((0, 3)))
+    out = g.compute()
+    assert np.all(out["totals"] == 0.0)
+    ser = g.run(3, 1.0)
+    assert ser.shape == (3, 5) and np.all(ser == 0.0)
+    g.close()
+
+
+def test_single_atom_and_dimer(md):
+    box = np.array([20.0, 20.0, 20.0])
+    for pos in (np.array([[5.0, 5.0, 5.0]]), np.array([[5.0, 5.0, 5.0], [5.0, 5.0, 7.35]]),
+                np.array([[5.0, 5.0, 5.0], [5.0, 5.0, 7.85]])):   # inside the f_C switch
+        sysm = I.System("few", pos, box, np.array([0, 0, 0], np.int32), I.MD_TERSOFF,
+                        I.TERSOFF_SI_1989, I.MASS_SI, np.zeros_like(pos))
+        compare_compute(md, sysm)
+
+
+def test_bitwise_deterministic(md):
+    s = I.si_diamond_sw(n=5, jitter_amp=0.08)
+    outs = []
+    for _ in range(2):
+        with md.from_inputs(s) as g:
+            o = g.compute()
+            ser = g.run(20, 1.0)
+            outs.append((o["F"].copy(), o["W"].copy(), ser.copy(), g.state()[0]))
+    for a, b in zip(outs[0], outs[1]):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("make,steps,dt", [
+    (lambda: I.si_diamond_tersoff(n=6), 50, 1.0),
+    (lambda: I.si_diamond_sw(n=4, jitter_amp=0.05), 50, 1.0),
+    (lambda: I.c_graphene_tersoff(nx=8, ny=14, jitter_amp=0.02), 40, 0.5),
+], ids=["tersoff_si_1728", "sw_si_512", "graphene_448"])
+def test_trajectory_matches_oracle(md, make, steps, dt):
+    """50 NVE velocity-Verlet steps (the GPU keeps a skin list and rebuilds on the
+    skin/2 rule; the oracle rebuilds from scratch every step)."""
+    s = make()
+    with md.from_inputs(s) as g:
+        ser = g.run(steps, dt)
+        pos, vel = g.state()
+        st = g.stats()
+    p2, v2, ser2 = O.run(s.pos, s.vel, s.mass, s.box, s.pbc, s.kind, s.params, steps, dt)
+    d = pos - p2
+    d -= np.round(d / s.box) * s.box * s.pbc
+    assert np.abs(d).max() < TRAJ_TOL
+    assert rel(vel, v2) < TRAJ_TOL
+    for c in range(5):
+        assert rel(ser[:, c], ser2[:, c]) < TRAJ_TOL, c
+    assert st.steps_done == steps
+
+
+def test_rebuilds_happen_and_stay_exact(md):
+    """A hot, small-skin run forces several list rebuilds; results still match."""
+    s = I.si_diamond_tersoff(n=3, jitter_amp=0.05, temperature=1500.0)
+    with md.from_inputs(s, skin=0.1) as g:
+        ser = g.run(60, 1.0)
+        pos, _ = g.state()
+        st = g.stats()
+    assert st.n_rebuilds >= 3
+    p2, _, ser2 = O.run(s.pos, s.vel, s.mass, s.box, s.pbc, s.kind, s.params, 60, 1.0)
+    d = pos - p2
+    d -= np.round(d / s.box) * s.box
+    assert np.abs(d).max() < TRAJ_TOL
+    assert rel(ser, ser2) < TRAJ_TOL
+
+
+def test_list_overflow_is_reported(md):
+    s = I.si_diamond_sw(n=3)
+    with md.from_inputs(s, max_neigh=8) as g:     # SW lists hold 16 (4 + 12 second nbrs)
+        with pytest.raises(md.MDError) as e:
+            g.compute()
+        assert e.value.status == -3
+
+
+def test_device_io_matches_host_io(md):
+    import torch
+    s = I.si_diamond_tersoff(n=4)
+    with md.from_inputs(s) as g:
+        host = g.compute()
+    g = md.System(s.box, s.pbc, s.n, s.kind, s.params, s.mass, io=md.MD_IO_DEVICE)
+    g.set_positions(torch.tensor(s.pos, device="cuda"))
+    g.set_velocities(torch.tensor(s.vel, device="cuda"))
+    dev = g.compute()
+    for k in ("F", "U", "W", "J"):
+        assert np.array_equal(dev[k].cpu().numpy(), host[k])
+    g.close()
+
+
+@pytest.mark.parametrize("name,make", [
+    ("sw_si_512000", lambda: I.si_diamond_sw(n=40)),
+    ("tersoff_c_graphene_1M", lambda: I.c_graphene_tersoff()),
+], ids=["sw_si_512000", "tersoff_c_graphene_1M"])
+def test_full_size_compute(md, name, make):
+    """Full-size workloads, in the same launch configuration the benchmark uses."""
+    compare_compute(md, make())
