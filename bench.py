@@ -121,13 +121,19 @@ def run_ours(args, rank, world):
     n = sysm.n
     stream = torch.cuda.Stream()
     res = {}
-    for prec, tag in ((md.MD_FP64, "fp64"), (md.MD_MIXED, "mixed")):
+    precs = [(md.MD_FP64, "fp64"), (md.MD_MIXED, "mixed")]
+    if args.precision != "both":
+        precs = [p for p in precs if p[1] == args.precision]
+    for prec, tag in precs:
         g = md.System(sysm.box, sysm.pbc, n, sysm.kind, sysm.params, sysm.mass, precision=prec,
                       stream=stream.cuda_stream)
         g.set_positions(sysm.pos)
         g.set_velocities(sysm.vel)
+        if args.eager:
+            md.md_set_graph_mode(g.ctx, False)
         f0 = g.compute(want=("f",))["F"].copy()
         g.run(args.warmup, dt, record=False)
+        rebuilds0 = g.stats().n_rebuilds
         md.md_set_profiling(g.ctx, True)
         if world > 1:
             torch.distributed.barrier()
@@ -146,11 +152,19 @@ def run_ours(args, rank, world):
         kt = md.md_kernel_times(g.ctx)
         md.md_set_profiling(g.ctx, False)
         st = g.stats()
-        res[tag] = dict(ms=ms, kt=kt, f0=f0, clocks=clocks.summary(), stats=st, sys=g)
+        res[tag] = dict(ms=ms, kt=kt, f0=f0, clocks=clocks.summary(), stats=st, sys=g,
+                        rebuilds=int(st.n_rebuilds - rebuilds0),
+                        launches=int(st.kernel_launches_per_step) * args.steps
+                        + int(st.kernel_launches_per_rebuild) * int(st.n_rebuilds - rebuilds0))
     # end-to-end through the public API with host buffers (pinned), copies inside the
     # timed region: upload x, v; run K steps; read back the series and the final state
     import torch as _t
-    g = res["fp64"]["sys"]
+    first = next(iter(res))
+    if args.no_e2e:
+        for tag in res:
+            res[tag]["sys"].close()
+        return n, dt, res, None, 0, 0, None
+    g = res[first]["sys"]
     xs = _t.tensor(np.ascontiguousarray(sysm.pos.T), dtype=_t.float64).pin_memory()
     vs = _t.tensor(np.ascontiguousarray(sysm.vel.T), dtype=_t.float64).pin_memory()
     ser = _t.zeros((args.steps, 5), dtype=_t.float64).pin_memory()
@@ -168,7 +182,9 @@ def run_ours(args, rank, world):
     t_e2e = time.perf_counter() - t0
     h2d = 6 * 8 * n
     d2h = 6 * 8 * n + 5 * 8 * args.steps
-    mixed_err = float(np.abs(res["mixed"]["f0"] - res["fp64"]["f0"]).max() / np.abs(res["fp64"]["f0"]).max())
+    mixed_err = None
+    if "mixed" in res and "fp64" in res:
+        mixed_err = float(np.abs(res["mixed"]["f0"] - res["fp64"]["f0"]).max() / np.abs(res["fp64"]["f0"]).max())
     for tag in res:
         res[tag]["sys"].close()
     return n, dt, res, t_e2e, h2d, d2h, mixed_err
@@ -182,6 +198,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="tersoff_c_graphene_1M")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--precision", default="both", choices=["both", "fp64", "mixed"])
+    ap.add_argument("--eager", action="store_true",
+                    help="launch each kernel eagerly instead of replaying graphs (for profilers)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -200,31 +220,28 @@ def main():
         return
 
     n, dt, res, t_e2e, h2d, d2h, mixed_err = run_ours(args, rank, world)
-    ms = res["fp64"]["ms"]
-    ms_mixed = res["mixed"]["ms"]
+    primary = "fp64" if "fp64" in res else "mixed"
+    ms = res[primary]["ms"]
+    ms_mixed = res["mixed"]["ms"] if "mixed" in res else 0.0
     if world > 1:
         import torch
         import torch.distributed as dist
-        t = torch.tensor([ms, ms_mixed, t_e2e], device="cuda", dtype=torch.float64)
+        t = torch.tensor([ms, ms_mixed, t_e2e or 0.0], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, ms_mixed, t_e2e = (float(v) for v in t.tolist())
+        ms, ms_mixed, t_e2e_max = (float(v) for v in t.tolist())
+        t_e2e = t_e2e_max if t_e2e is not None else None
     value = world * n * args.steps / (ms / 1e3)
-    value_mixed = world * n * args.steps / (ms_mixed / 1e3)
-    e2e_value = world * n * args.steps / t_e2e
     if rank != 0:
         return
-    peaks = load_peaks()
-    kt = res["fp64"]["kt"]
-    pair_n, pair_ms = kt["pair"]
-    gat_n, gat_ms = kt["gather"]
-    st = res["fp64"]["stats"]
+    kt = res[primary]["kt"]
+    pair_n, pair_ms = kt.get("pair", (0, 0.0))
+    st = res[primary]["stats"]
     sysm, _ = workload(args.workload)
     bonds = 3.0 if sysm.kind == I.MD_TERSOFF and "graphene" in args.workload else 4.0
     trip = bonds * (bonds - 1) / 2
     flops = pair_flops(sysm.kind, bonds, trip) * n
-    pair_avg_s = pair_ms / max(pair_n, 1) / 1e3
-    achieved_tf = flops / pair_avg_s / 1e12
-    kernel_launches = res["fp64"]["stats"].kernel_launches_per_step * args.steps
+    pair_avg_s = pair_ms / pair_n / 1e3 if pair_n > 0 and pair_ms > 0 else None
+    achieved_tf = flops / pair_avg_s / 1e12 if pair_avg_s else None
     out = {
         "metric": "atom-steps/s Tersoff FP64 vs mixed on 1 GB300",
         "value": value,
@@ -236,24 +253,28 @@ def main():
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64",
+        "dtype": "f64" if primary == "fp64" else "f32+f64",
         "data": "synthetic",
         "config": {"workload": args.workload, "n_atoms": n, "dt_fs": dt, "ensemble": "NVE",
-                   "potential": "Tersoff 1989 C", "l2": "working set > L2 (no flush)",
+                   "l2": "working set > L2 (no flush)", "launch": "eager" if args.eager else "graphs",
                    "parallelism": "replicas" if world > 1 else "single"},
-        "mixed": {"value": value_mixed, "ms_per_step": ms_mixed / args.steps, "dtype": "f32+f64",
-                  "force_err_vs_fp64": mixed_err},
-        "roofline": {"bound": "alu", "kernel": "pair (fp64)", "achieved": achieved_tf,
+        "roofline": {"bound": "alu", "kernel": f"pair ({primary})", "achieved": achieved_tf,
                      "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved_tf / FP64_NOMINAL_TFLOPS, "traffic": None,
+                     "frac": achieved_tf / FP64_NOMINAL_TFLOPS if achieved_tf else None, "traffic": None,
                      "peak_source": "nominal GB300 FP64 (recipe unit counts x clock)"},
-        "kernel_ms_per_step": {k: (v[1] / max(v[0], 1)) for k, v in kt.items()},
-        "e2e": {"value": e2e_value, "unit": "atom-steps/s", "h2d_bytes_per_step": h2d / args.steps,
-                "d2h_bytes_per_step": d2h / args.steps},
-        "gpu_launches": kernel_launches,
-        "rebuilds": int(st.n_rebuilds),
-        "clocks": res["fp64"]["clocks"],
+        "kernel_ms_per_step": {k: (v[1] / v[0] if v[0] else None) for k, v in kt.items()},
+        "gpu_launches": res[primary]["launches"],
+        "rebuilds": res[primary]["rebuilds"],
+        "clocks": res[primary]["clocks"],
     }
+    if "mixed" in res and primary != "mixed":
+        out["mixed"] = {"value": world * n * args.steps / (ms_mixed / 1e3), "ms_per_step": ms_mixed / args.steps,
+                        "dtype": "f32+f64", "force_err_vs_fp64": mixed_err,
+                        "kernel_ms_per_step": {k: (v[1] / v[0] if v[0] else None)
+                                               for k, v in res["mixed"]["kt"].items()}}
+    if t_e2e is not None:
+        out["e2e"] = {"value": world * n * args.steps / t_e2e, "unit": "atom-steps/s",
+                      "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps}
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args)
     print(json.dumps(out))

@@ -135,10 +135,18 @@ typedef struct {
     int64_t steps_done;      /* MD steps since creation                               */
     int64_t n_rebuilds;      /* neighbour-list builds since creation                  */
     int max_neigh_seen;      /* largest list length at the last build                 */
-    int kernel_launches_per_step; /* kernels one md_run step launches                 */
+    int kernel_launches_per_step; /* kernels every md_run step launches               */
+    int kernel_launches_per_rebuild; /* extra kernels of a step that rebuilds the list */
     size_t device_bytes;     /* bytes the context has allocated on the device         */
 } md_stats;
 md_status md_get_stats(md_ctx *ctx, md_stats *out);
+
+/* Launch mode of md_run.  use_graphs = 1 (default): steps are replayed from captured
+ * CUDA graphs whose list rebuild is a conditional node decided on the device.
+ * use_graphs = 0: the same kernels launched one by one, the rebuild decided on the host
+ * after each drift (one small device-to-host copy per step); profilers that cannot
+ * look inside graphs with conditional nodes see every kernel this way. */
+md_status md_set_graph_mode(md_ctx *ctx, int use_graphs);
 
 /* Per-kernel timing.  While enabled, md_run records CUDA events around each kernel
  * class of every step and accumulates their elapsed times; md_kernel_times returns, for

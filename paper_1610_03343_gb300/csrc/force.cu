@@ -1,9 +1,9 @@
 // force.cu -- the force hot path in the paper's explicit pairwise-force form.
 //
-// Pass A, "pair pass" (one thread per atom i, Algorithm 3 and the dU_i/dr_ij part of
-// Algorithm 2 fused): for every list neighbour j the fp64 minimum-image bond r_ij
-// (Algorithm 2's minimum-image step); the in-cutoff ones are staged in shared memory
-// (SoA across the block's threads), then
+// Pass A, "pair pass" (one thread per atom i; Algorithm 3 and the dU_i/dr_ij part of
+// Algorithm 2 fused): for every list neighbour j the fp64 bond r_ij (the list entry
+// carries the periodic image, so this is three subtractions); the in-cutoff bonds are
+// staged in shared memory (SoA across the block's threads), then
 //   Tersoff: zeta_ij (Eq. 4) for every bond, b_ij and db/dzeta (Eq. 3), U_i (Eq. 2) and
 //            dU_i/dr_ij, whose chain rule runs through b_ij and every b_ik (k != j);
 //   SW:      the two-body and vertex three-body sums in one pass (no precompute, as
@@ -17,7 +17,11 @@
 // d_ji is found through the reverse-slot index.  Each atom's sums live in one thread:
 // no atomics, fixed summation order, bitwise-reproducible results.  The gather also
 // applies the second velocity-Verlet half-kick and writes per-block fp64 partial sums
-// of U, K, J and W; a one-block kernel adds them in a fixed order.
+// of U, K, J (and W for a force evaluation); a small kernel adds them in fixed order.
+//
+// Precision: T = double (fp64 path) or float (mixed path: per-pair arithmetic and
+// per-atom sums in fp32; bond vectors from fp64 positions; velocities, positions and
+// the block / system totals in fp64).
 #include "md_plan.cuh"
 
 namespace mdk {
@@ -29,7 +33,7 @@ namespace {
 // ---------------------------------------------------------------- precision
 template <typename T> struct M;
 template <> struct M<double> {
-    static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+    static __device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
     static __device__ __forceinline__ double exp_(double x) { return exp(x); }
     static __device__ __forceinline__ double log_(double x) { return log(x); }
     static __device__ __forceinline__ double log1p_(double x) { return log1p(x); }
@@ -37,7 +41,7 @@ template <> struct M<double> {
     static __device__ __forceinline__ double pow_(double x, double y) { return pow(x, y); }
 };
 template <> struct M<float> {
-    static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+    static __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
     static __device__ __forceinline__ float exp_(float x) { return expf(x); }
     static __device__ __forceinline__ float log_(float x) { return logf(x); }
     static __device__ __forceinline__ float log1p_(float x) { return log1pf(x); }
@@ -63,10 +67,11 @@ struct Stage {
 };
 
 // ------------------------------------------------------- neighbour staging
-// Computes the fp64 minimum-image r_ij for each list slot, keeps the slots with
-// |r_ij|^2 < rc^2, writes their bond vectors (compact row k) to global memory and
-// stages (x, y, z, r^2) in the shared fields fx, fy, fz, fr2.  Returns the count and
-// the active-slot mask.
+// For each list slot, the fp64 bond r_ij (image shift from the entry); keeps the slots
+// with |r_ij|^2 < rc^2, writes their bond vectors (compact row k) to global memory and
+// stages (x, y, z, r^2) in the shared fields fx, fy, fz, fr2.  Returns the count and the
+// active-slot mask.  The cutoff decision is symmetric in i and j: the two fp64
+// differences are exact negatives of each other, and so are their conversions.
 template <typename T, int MAXA, int BLOCK>
 __device__ __forceinline__ int collect_bonds(const PairArgs<T> &a, int64_t i, uint32_t &mask,
                                              const Stage<T, MAXA, BLOCK> &S, int fx, int fy, int fz,
@@ -78,10 +83,8 @@ __device__ __forceinline__ int collect_bonds(const PairArgs<T> &a, int64_t i, ui
     int na = 0;
     mask = 0u;
     for (int m = 0; m < nn; ++m) {
-        const int j = a.nl[(int64_t)m * N + i];
-        const double dx = min_image(a.pos[j] - xi, a.box.L[0], a.box.invL[0], a.box.pbc[0]);
-        const double dy = min_image(a.pos[N + j] - yi, a.box.L[1], a.box.invL[1], a.box.pbc[1]);
-        const double dz = min_image(a.pos[2 * N + j] - zi, a.box.L[2], a.box.invL[2], a.box.pbc[2]);
+        double dx, dy, dz;
+        bond_vector(a.pos, N, i, a.nl[(int64_t)m * N + i], a.box, xi, yi, zi, dx, dy, dz);
         const T tx = T(dx), ty = T(dy), tz = T(dz);
         const T r2 = tx * tx + ty * ty + tz * tz;
         if (r2 < a.rc2) {
@@ -105,16 +108,21 @@ __device__ __forceinline__ int collect_bonds(const PairArgs<T> &a, int64_t i, ui
 // ------------------------------------------------------------------ Tersoff
 enum { TF_UX, TF_UY, TF_UZ, TF_IR, TF_FC, TF_DFC, TF_FR, TF_FA, TF_Z, TF_DX, TF_DY, TF_DZ, TF_NF };
 
-// g(cos) of Eq. 5 written as 1 + c^2 (h-cos)^2 / (d^2 (d^2 + (h-cos)^2)): the same
+// g(cos) of Eq. 5 written as 1 + (c^2/d^2) (h-cos)^2 / (d^2 + (h-cos)^2): the same
 // function as printed, without the cancellation of c^2/d^2 - c^2/(d^2+(h-cos)^2)
-// (about 4e7 - 4e7 for silicon), so that it stays accurate in fp32.  Also dg/dcos.
+// (about 4e7 - 4e7 for silicon), so that it stays accurate in fp32.  inv = 1/den is
+// returned so the derivative loop can reuse it; dg = dg/dcos.
 template <typename T>
-__device__ __forceinline__ void tersoff_g(const TersoffP &p, T cs, T &g, T &dg)
+__device__ __forceinline__ T tersoff_inv_den(const TersoffP &p, T cs)
 {
     const T hc = T(p.h) - cs;
-    const T den = T(p.d2) + hc * hc;
-    const T inv = T(1) / den;
-    g = T(1) + T(p.c2) * hc * hc * inv / T(p.d2);
+    return T(1) / (T(p.d2) + hc * hc);
+}
+template <typename T>
+__device__ __forceinline__ void tersoff_g(const TersoffP &p, T cs, T inv, T &g, T &dg)
+{
+    const T hc = T(p.h) - cs;
+    g = T(1) + T(p.c2d2) * hc * hc * inv;
     dg = T(-2) * T(p.c2) * hc * inv * inv;
 }
 
@@ -133,6 +141,12 @@ __device__ __forceinline__ void tersoff_b(const TersoffP &p, T zeta, T &b, T &db
     db = T(-0.5) * b * x / (zeta * (T(1) + x));
 }
 
+// index of the unordered bond pair (j, k), j < k
+__device__ __forceinline__ int tri(int j, int k) { return k * (k - 1) / 2 + j; }
+
+template <typename T, int MAXA>
+constexpr int tersoff_smem_fields() { return TF_NF * MAXA + MAXA * (MAXA - 1) / 2; }
+
 template <typename T, int MAXA, int BLOCK>
 __global__ void __launch_bounds__(BLOCK) k_pair_tersoff(PairArgs<T> a, TersoffP p)
 {
@@ -140,15 +154,19 @@ __global__ void __launch_bounds__(BLOCK) k_pair_tersoff(PairArgs<T> a, TersoffP 
     const int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
     if (i >= a.N) return;
     const int64_t N = a.N;
-    Stage<T, MAXA, BLOCK> S{reinterpret_cast<T *>(smem), (int)threadIdx.x};
+    T *base = reinterpret_cast<T *>(smem);
+    Stage<T, MAXA, BLOCK> S{base, (int)threadIdx.x};
+    T *sinv = base + TF_NF * MAXA * BLOCK;   // per bond pair: 1/(d^2 + (h - cos)^2)
+    auto INV = [&](int q) -> T & { return sinv[q * BLOCK + threadIdx.x]; };
 
     uint32_t mask;
     const int na = collect_bonds<T, MAXA, BLOCK>(a, i, mask, S, TF_UX, TF_UY, TF_UZ, TF_IR);
 
     // per-bond radial functions (the staged vectors become unit vectors, r^2 -> 1/r)
     for (int k = 0; k < na; ++k) {
-        const T r = M<T>::sqrt_(S(TF_IR, k));
-        const T ir = T(1) / r;
+        const T r2 = S(TF_IR, k);
+        const T ir = M<T>::rsqrt_(r2);
+        const T r = r2 * ir;
         S(TF_UX, k) *= ir;
         S(TF_UY, k) *= ir;
         S(TF_UZ, k) *= ir;
@@ -172,8 +190,10 @@ __global__ void __launch_bounds__(BLOCK) k_pair_tersoff(PairArgs<T> a, TersoffP 
         T zj = S(TF_Z, j);
         for (int k = j + 1; k < na; ++k) {
             const T cs = ujx * S(TF_UX, k) + ujy * S(TF_UY, k) + ujz * S(TF_UZ, k);
+            const T inv = tersoff_inv_den(p, cs);
+            INV(tri(j, k)) = inv;
             T g, dg;
-            tersoff_g(p, cs, g, dg);
+            tersoff_g(p, cs, inv, g, dg);
             zj += S(TF_FC, k) * g;
             S(TF_Z, k) += fcj * g;
         }
@@ -205,7 +225,7 @@ __global__ void __launch_bounds__(BLOCK) k_pair_tersoff(PairArgs<T> a, TersoffP 
             const T irk = S(TF_IR, k), fck = S(TF_FC, k), dfck = S(TF_DFC, k), Pk = S(TF_Z, k);
             const T cs = ujx * ukx + ujy * uky + ujz * ukz;
             T g, dg;
-            tersoff_g(p, cs, g, dg);
+            tersoff_g(p, cs, INV(tri(j, k)), g, dg);
             const T Q = (Pj * fck + Pk * fcj) * dg;
             const T cj = Pk * dfcj * g, ck = Pj * dfck * g;
             const T qj = Q * irj, qk = Q * irk;
@@ -241,8 +261,9 @@ __global__ void __launch_bounds__(BLOCK) k_pair_sw(PairArgs<T> a, SWP p)
     T ui = T(0);
     const T rc = T(p.rc), sig = T(p.sig);
     for (int k = 0; k < na; ++k) {
-        const T r = M<T>::sqrt_(S(SW_IR, k));
-        const T ir = T(1) / r;
+        const T r2 = S(SW_IR, k);
+        const T ir = M<T>::rsqrt_(r2);
+        const T r = r2 * ir;
         const T ux = S(SW_UX, k) * ir, uy = S(SW_UY, k) * ir, uz = S(SW_UZ, k) * ir;
         S(SW_UX, k) = ux; S(SW_UY, k) = uy; S(SW_UZ, k) = uz; S(SW_IR, k) = ir;
         const T irc = T(1) / (r - rc);                 // 1/(r - a sigma) < 0
@@ -294,39 +315,41 @@ __global__ void __launch_bounds__(BLOCK) k_pair_sw(PairArgs<T> a, SWP p)
 }
 
 // ------------------------------------------------------------------ gather
-__device__ __forceinline__ double warp_sum(double v)
+// Block sums of NC per-thread fp64 values, in a fixed order: transpose through shared
+// memory, then 8 threads per component add 16 values each and combine by shuffles.
+template <int BLOCK, int NC>
+__device__ __forceinline__ void block_partials(const double (&vals)[NC], double *out, int nb)
 {
+    static_assert(BLOCK == 128, "block_partials assumes 128 threads");
+    __shared__ double red[NC][BLOCK];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
-
-template <int BLOCK>
-__device__ __forceinline__ void block_partials(double (&vals)[kNumPartials], double *out)
-{
-    __shared__ double red[BLOCK / 32][kNumPartials];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int c = 0; c < kNumPartials; ++c) {
-        double v = warp_sum(vals[c]);
-        if (lane == 0) red[wid][c] = v;
-    }
+    for (int c = 0; c < NC; ++c) red[c][threadIdx.x] = vals[c];
     __syncthreads();
-    if (threadIdx.x < kNumPartials) {
+    const int t = threadIdx.x;
+    if (t < NC * 8) {
+        const int c = t >> 3, sub = t & 7;
         double s = 0.0;
-        for (int w = 0; w < BLOCK / 32; ++w) s += red[w][threadIdx.x];
-        out[(int64_t)blockIdx.x * kNumPartials + threadIdx.x] = s;
+#pragma unroll
+        for (int q = 0; q < BLOCK / 8; ++q) s += red[c][sub + 8 * q];
+        const unsigned grp = 0xffu << (t & 24);
+        s += __shfl_xor_sync(grp, s, 4, 8);
+        s += __shfl_xor_sync(grp, s, 2, 8);
+        s += __shfl_xor_sync(grp, s, 1, 8);
+        if (sub == 0) out[(int64_t)c * nb + blockIdx.x] = s;
     }
 }
 
-template <typename T, int MAXA, int BLOCK>
+// FULL: a force evaluation (per-atom F, W, J stored; U, K, J, W partials) or a
+// velocity-Verlet step (F and the kick only; U, K, J partials).
+template <typename T, int MAXA, int BLOCK, bool FULL>
 __global__ void __launch_bounds__(BLOCK) k_gather(GatherArgs<T> a)
 {
+    constexpr int NC = FULL ? kNumPartials : kStepPartials;
     const int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
     const int64_t N = a.N;
-    double vals[kNumPartials];
+    double vals[NC];
 #pragma unroll
-    for (int c = 0; c < kNumPartials; ++c) vals[c] = 0.0;
+    for (int c = 0; c < NC; ++c) vals[c] = 0.0;
     if (i < N) {
         uint32_t mask = a.mask[i];
         T f0 = 0, f1 = 0, f2 = 0;
@@ -337,7 +360,7 @@ __global__ void __launch_bounds__(BLOCK) k_gather(GatherArgs<T> a)
         while (mask != 0u && k < MAXA) {
             const int m = __ffs(mask) - 1;
             mask &= mask - 1u;
-            const int j = a.nl[(int64_t)m * N + i];
+            const int j = list_atom(a.nl[(int64_t)m * N + i]);
             const int mr = a.rev[(int64_t)m * N + i];
             const uint32_t maskj = a.mask[j];
             const int kr = __popc(maskj & ((1u << mr) - 1u));
@@ -350,9 +373,11 @@ __global__ void __launch_bounds__(BLOCK) k_gather(GatherArgs<T> a)
                         rz = a.r[(2 * MAXA + k) * N + i];
                 const T gx = dx - ex, gy = dy - ey, gz = dz - ez;   // F_ij = d_ij - d_ji
                 f0 += gx; f1 += gy; f2 += gz;
-                w[0] += rx * gx; w[1] += rx * gy; w[2] += rx * gz;
-                w[3] += ry * gx; w[4] += ry * gy; w[5] += ry * gz;
-                w[6] += rz * gx; w[7] += rz * gy; w[8] += rz * gz;
+                if (FULL) {
+                    w[0] += rx * gx; w[1] += rx * gy; w[2] += rx * gz;
+                    w[3] += ry * gx; w[4] += ry * gy; w[5] += ry * gz;
+                    w[6] += rz * gx; w[7] += rz * gy; w[8] += rz * gz;
+                }
                 mj[0] += rx * ex; mj[1] += rx * ey; mj[2] += rx * ez;
                 mj[3] += ry * ex; mj[4] += ry * ey; mj[5] += ry * ez;
                 mj[6] += rz * ex; mj[7] += rz * ey; mj[8] += rz * ez;
@@ -375,92 +400,95 @@ __global__ void __launch_bounds__(BLOCK) k_gather(GatherArgs<T> a)
             a.vel[N + i] = v[1];
             a.vel[2 * N + i] = v[2];
         }
-        double J[3];
-#pragma unroll
-        for (int r = 0; r < 3; ++r)
-            J[r] = double(mj[3 * r]) * v[0] + double(mj[3 * r + 1]) * v[1] + double(mj[3 * r + 2]) * v[2];
-        const double ke = 0.5 * a.mass[t] * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) / kAccUnit;
+        // J_i = M_i . v_i and K_i = m v^2 / 2 in T (the fp32 per-atom value of the mixed
+        // path feeds an fp64 total)
+        const T vx = T(v[0]), vy = T(v[1]), vz = T(v[2]);
+        const T J0 = mj[0] * vx + mj[1] * vy + mj[2] * vz;
+        const T J1 = mj[3] * vx + mj[4] * vy + mj[5] * vz;
+        const T J2 = mj[6] * vx + mj[7] * vy + mj[8] * vz;
+        const T ke = T(0.5 / kAccUnit) * T(a.mass[t]) * (vx * vx + vy * vy + vz * vz);
         vals[0] = a.u[i];
-        vals[1] = ke;
-        vals[2] = J[0]; vals[3] = J[1]; vals[4] = J[2];
+        vals[1] = double(ke);
+        vals[2] = double(J0);
+        vals[3] = double(J1);
+        vals[4] = double(J2);
+        if (FULL) {
 #pragma unroll
-        for (int c = 0; c < 9; ++c) vals[5 + c] = -0.5 * double(w[c]);
-        if (a.w_out) {
+            for (int c = 0; c < 9; ++c) vals[5 + c] = -0.5 * double(w[c]);
+            if (a.w_out) {
 #pragma unroll
-            for (int c = 0; c < 9; ++c) a.w_out[c * N + i] = vals[5 + c];
-        }
-        if (a.j_out) {
-            a.j_out[i] = J[0];
-            a.j_out[N + i] = J[1];
-            a.j_out[2 * N + i] = J[2];
+                for (int c = 0; c < 9; ++c) a.w_out[c * N + i] = vals[5 + c];
+            }
+            if (a.j_out) {
+                a.j_out[i] = vals[2];
+                a.j_out[N + i] = vals[3];
+                a.j_out[2 * N + i] = vals[4];
+            }
         }
     }
-    block_partials<BLOCK>(vals, a.partials);
+    block_partials<BLOCK, NC>(vals, a.partials, gridDim.x);
 }
 
-// One block: partial sums in a fixed order -> totals (U, K, J, W) and a series row.
+// One block per component: that component's block partials added in a fixed order.
 constexpr int kReduceThreads = 256;
 __global__ void __launch_bounds__(kReduceThreads)
 k_reduce(const double *partials, int nb, double *totals, double *series, Flags *flags, bool record)
 {
-    __shared__ double red[kReduceThreads / 32][kNumPartials];
-    double acc[kNumPartials];
+    __shared__ double red[kReduceThreads / 32];
+    const int c = blockIdx.x;
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < nb; b += kReduceThreads) acc += partials[(int64_t)c * nb + b];
 #pragma unroll
-    for (int c = 0; c < kNumPartials; ++c) acc[c] = 0.0;
-    for (int b = threadIdx.x; b < nb; b += kReduceThreads)
-#pragma unroll
-        for (int c = 0; c < kNumPartials; ++c) acc[c] += partials[(int64_t)b * kNumPartials + c];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int c = 0; c < kNumPartials; ++c) {
-        double v = warp_sum(acc[c]);
-        if (lane == 0) red[wid][c] = v;
-    }
+    if (lane == 0) red[wid] = acc;
     __syncthreads();
-    if (threadIdx.x < kNumPartials) {
+    if (threadIdx.x == 0) {
         double s = 0.0;
-        for (int w = 0; w < kReduceThreads / 32; ++w) s += red[w][threadIdx.x];
-        totals[threadIdx.x] = s;
-        if (record && threadIdx.x < 5) series[flags->step * 5 + threadIdx.x] = s;
+        for (int w = 0; w < kReduceThreads / 32; ++w) s += red[w];
+        totals[c] = s;
+        if (record && c < kStepPartials) series[flags->row * kStepPartials + c] = s;
     }
-    __syncthreads();
-    if (record && threadIdx.x == 0) flags->step += 1;
 }
 
 // ------------------------------------------------------------------ integrator
 struct KickDriftArgs {
     int64_t N;
-    Box box;
     double *pos, *vel;
     const double *force, *pos_build;
     const int *type;
     double hk[kMaxTypes];   // dt/2 * acc / m per type
     double dt;
-    double half_skin2;
+    float half_skin2;
     Flags *flags;
 };
 
+// v += F/m dt/2; x += v dt (no wrap: positions are wrapped when the list is rebuilt);
+// request a rebuild when an atom has moved more than skin/2 since the last build.
 __global__ void k_kick_drift(KickDriftArgs a)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.N) return;
     const int64_t N = a.N;
     const double h = a.hk[a.type[i]];
-    double d2 = 0.0;
+    float d2 = 0.f;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        double v = fma(h, a.force[c * N + i], a.vel[c * N + i]);
-        double x = fma(a.dt, v, a.pos[c * N + i]);
-        if (a.box.pbc[c]) {
-            if (x >= a.box.L[c]) x -= a.box.L[c];
-            else if (x < 0.0) x += a.box.L[c];
-        }
+        const double v = fma(h, a.force[c * N + i], a.vel[c * N + i]);
+        const double x = fma(a.dt, v, a.pos[c * N + i]);
         a.vel[c * N + i] = v;
         a.pos[c * N + i] = x;
-        const double d = min_image(x - a.pos_build[c * N + i], a.box.L[c], a.box.invL[c], a.box.pbc[c]);
-        d2 = fma(d, d, d2);
+        const float d = (float)(x - a.pos_build[c * N + i]);
+        d2 = fmaf(d, d, d2);
     }
     if (!(d2 <= a.half_skin2)) a.flags->rebuild = 1;
+}
+
+__global__ void k_step_begin(Flags *flags, cudaGraphConditionalHandle h, int has_cond)
+{
+    flags->row = flags->step;
+    flags->step += 1;
+    if (has_cond) cudaGraphSetConditional(h, flags->rebuild != 0 ? 1u : 0u);
 }
 
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -476,8 +504,8 @@ template <> constexpr int pair_block<float>() { return kPairBlockF32; }
 template <typename T, int MAXA>
 size_t smem_for(int kind)
 {
-    const int nf = kind == 1 ? TF_NF : SW_NF;
-    return (size_t)nf * MAXA * pair_block<T>() * sizeof(T);
+    const int nf = kind == 1 ? tersoff_smem_fields<T, MAXA>() : SW_NF * MAXA;
+    return (size_t)nf * pair_block<T>() * sizeof(T);
 }
 
 template <typename T, int MAXA>
@@ -502,6 +530,7 @@ void pair_launch(const Plan &p, cudaStream_t s)
     a.nl = p.nl;
     a.cap = p.cap;
     a.rc2 = T(p.rc * p.rc);
+    for (int c = 0; c < 3; ++c) a.shift[c] = p.box.L[c];
     a.d = static_cast<T *>(p.pd);
     a.r = static_cast<T *>(p.pr);
     a.mask = p.mask;
@@ -514,7 +543,7 @@ void pair_launch(const Plan &p, cudaStream_t s)
 }
 
 template <typename T, int MAXA>
-void gather_launch(const Plan &p, cudaStream_t s, const double *hk, bool store_wj)
+void gather_launch(const Plan &p, cudaStream_t s, const double *hk, bool full)
 {
     GatherArgs<T> a;
     a.N = p.N;
@@ -532,11 +561,15 @@ void gather_launch(const Plan &p, cudaStream_t s, const double *hk, bool store_w
     a.kick = hk != nullptr;
     a.vel = p.vel;
     a.force = p.force;
-    a.w_out = store_wj ? p.w : nullptr;
-    a.j_out = store_wj ? p.j : nullptr;
+    a.w_out = full ? p.w : nullptr;
+    a.j_out = full ? p.j : nullptr;
     a.partials = p.partials;
     a.flags = p.flags;
-    k_gather<T, MAXA, kGatherBlock><<<blocks_for(p.N, kGatherBlock), kGatherBlock, 0, s>>>(a);
+    const unsigned nb = blocks_for(p.N, kGatherBlock);
+    if (full)
+        k_gather<T, MAXA, kGatherBlock, true><<<nb, kGatherBlock, 0, s>>>(a);
+    else
+        k_gather<T, MAXA, kGatherBlock, false><<<nb, kGatherBlock, 0, s>>>(a);
 }
 
 }  // namespace
@@ -563,7 +596,6 @@ void launch_kick_drift(const Plan &p, cudaStream_t s, const double *hk, double d
     if (p.N == 0) return;
     KickDriftArgs a;
     a.N = p.N;
-    a.box = p.box;
     a.pos = p.pos;
     a.vel = p.vel;
     a.force = p.force;
@@ -572,9 +604,14 @@ void launch_kick_drift(const Plan &p, cudaStream_t s, const double *hk, double d
     for (int t = 0; t < kMaxTypes; ++t) a.hk[t] = hk[t];
     a.dt = dt;
     const double hs = 0.5 * p.skin;
-    a.half_skin2 = hs * hs;
+    a.half_skin2 = (float)(hs * hs);
     a.flags = p.flags;
     k_kick_drift<<<blocks_for(p.N, 256), 256, 0, s>>>(a);
+}
+
+void launch_step_begin(const Plan &p, cudaStream_t s, const cudaGraphConditionalHandle *h)
+{
+    k_step_begin<<<1, 1, 0, s>>>(p.flags, h ? *h : cudaGraphConditionalHandle(0), h ? 1 : 0);
 }
 
 void launch_pair(const Plan &p, cudaStream_t s)
@@ -587,23 +624,24 @@ void launch_pair(const Plan &p, cudaStream_t s)
     }
 }
 
-void launch_gather(const Plan &p, cudaStream_t s, const double *hk, bool store_wj)
+void launch_gather(const Plan &p, cudaStream_t s, const double *hk, bool full)
 {
     if (p.N == 0) return;
     if (p.precision == 0) {
-        if (p.maxa <= 8) gather_launch<double, 8>(p, s, hk, store_wj);
-        else gather_launch<double, 16>(p, s, hk, store_wj);
+        if (p.maxa <= 8) gather_launch<double, 8>(p, s, hk, full);
+        else gather_launch<double, 16>(p, s, hk, full);
     } else {
-        if (p.maxa <= 8) gather_launch<float, 8>(p, s, hk, store_wj);
-        else gather_launch<float, 16>(p, s, hk, store_wj);
+        if (p.maxa <= 8) gather_launch<float, 8>(p, s, hk, full);
+        else gather_launch<float, 16>(p, s, hk, full);
     }
 }
 
-void launch_reduce(const Plan &p, cudaStream_t s, bool record_series)
+void launch_reduce(const Plan &p, cudaStream_t s, bool full, bool record_series)
 {
     const int nb = p.N == 0 ? 0 : (int)blocks_for(p.N, kGatherBlock);
-    k_reduce<<<1, kReduceThreads, 0, s>>>(p.partials, nb, p.totals, p.series, p.flags,
-                                          record_series && p.series != nullptr);
+    const int nc = full ? kNumPartials : kStepPartials;
+    k_reduce<<<nc, kReduceThreads, 0, s>>>(p.partials, nb, p.totals, p.series, p.flags,
+                                           record_series && p.series != nullptr);
 }
 
 int gather_blocks(int64_t N) { return N == 0 ? 1 : (int)blocks_for(N, kGatherBlock); }

@@ -34,11 +34,14 @@ struct md_ctx {
     bool pos_set = false, forces_valid = false, have_wj = false;
     int64_t steps_done = 0;
     int kernels_per_step = 0;
-    // graph cache
-    cudaGraphExec_t gexec = nullptr;
+    int kernels_per_rebuild = 0;
+    // graph cache: an 8-step and a 1-step graph of the velocity-Verlet step
+    cudaGraphExec_t gexec = nullptr, gexec1 = nullptr;
     double g_dt = 0.0;
     double *g_series = nullptr;
     bool g_prof = false;
+    cudaStream_t side = nullptr;   // stream used to capture conditional bodies
+    bool use_graphs = true;        // false: eager launches, rebuild decided on the host
     // profiling
     bool profiling = false;
     std::vector<Timing> ev;        // [steps_per_graph * KC_COUNT]
@@ -94,7 +97,9 @@ md_status dalloc_t(md_ctx *ctx, P **ptr, size_t count)
 void destroy_graph(md_ctx *ctx)
 {
     if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    if (ctx->gexec1) cudaGraphExecDestroy(ctx->gexec1);
     ctx->gexec = nullptr;
+    ctx->gexec1 = nullptr;
 }
 
 // copy a 3-vector SoA field given as three pointers into dst[3N]
@@ -163,42 +168,120 @@ void half_kick(const md_ctx *ctx, double dt, double *hk)
 
 struct Recorder {
     md_ctx *ctx;
-    int step;   // index of the step inside the graph (profiling events)
+    int step;         // index of the step inside the graph (profiling events)
+    bool capturing;   // enqueued under stream capture
+    // Under capture the records must be "external" to become event-record nodes of the
+    // graph (a plain record only marks a capture dependency); outside capture the flag
+    // is not allowed, so a plain record is used there.
+    void rec(cudaEvent_t e) const
+    {
+        if (capturing) cudaEventRecordWithFlags(e, ctx->stream, cudaEventRecordExternal);
+        else cudaEventRecord(e, ctx->stream);
+    }
     void begin(int kc) const
     {
-        if (ctx->profiling) cudaEventRecord(ctx->ev[step * KC_COUNT + kc].ev[0], ctx->stream);
+        if (ctx->profiling) rec(ctx->ev[step * KC_COUNT + kc].ev[0]);
     }
     void end(int kc) const
     {
-        if (ctx->profiling) cudaEventRecord(ctx->ev[step * KC_COUNT + kc].ev[1], ctx->stream);
+        if (ctx->profiling) rec(ctx->ev[step * KC_COUNT + kc].ev[1]);
     }
 };
 
-// force evaluation: [rebuild if flagged] -> pair pass -> gather -> reduce
-int enqueue_forces(md_ctx *ctx, const Recorder &rec, const double *hk, bool store_wj, bool record)
+// Inside a capture on ctx->stream: a conditional IF node whose body is the list
+// rebuild, taken when the handle's value is non-zero.  The body is captured on the
+// side stream.  Returns the number of kernels in the body.
+md_status add_conditional_rebuild(md_ctx *ctx, cudaGraphConditionalHandle h)
 {
-    int n = 0;
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    const cudaGraphEdgeData *edges = nullptr;
+    size_t nd = 0;
+    CK(cudaStreamGetCaptureInfo(ctx->stream, &cs, nullptr, &g, &deps, &edges, &nd));
+    if (cs != cudaStreamCaptureStatusActive) return fail(ctx, MD_ERR_CUDA, "stream is not capturing");
+    // the parameter union has no usable default constructor: zero a raw buffer instead
+    alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
+    std::memset(raw, 0, sizeof(raw));
+    cudaGraphNodeParams &np = *reinterpret_cast<cudaGraphNodeParams *>(raw);
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeIf;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, g, deps, edges, nd, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    CK(cudaStreamUpdateCaptureDependencies(ctx->stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    CK(cudaStreamBeginCaptureToGraph(ctx->side, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    ctx->kernels_per_rebuild = launch_rebuild(ctx->p, ctx->side);
+    cudaGraph_t out = nullptr;
+    CK(cudaStreamEndCapture(ctx->side, &out));
+    return MD_OK;
+}
+
+// One velocity-Verlet step inside a capture:
+//   kick/drift -> [step begin: series row, rebuild condition] -> IF(rebuild) ->
+//   pair pass -> gather (+ half-kick) -> reduce (series row)
+md_status enqueue_step(md_ctx *ctx, const Recorder &rec, const double *hk, double dt, int *n_kernels)
+{
+    rec.begin(KC_KICK_DRIFT);
+    launch_kick_drift(ctx->p, ctx->stream, hk, dt);
+    rec.end(KC_KICK_DRIFT);
     rec.begin(KC_REBUILD);
-    n += launch_rebuild(ctx->p, ctx->stream, true);
+    if (ctx->p.N > 0) {
+        cudaGraphConditionalHandle h;
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamGetCaptureInfo(ctx->stream, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+        CK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+        launch_step_begin(ctx->p, ctx->stream, &h);
+        md_status s = add_conditional_rebuild(ctx, h);
+        if (s != MD_OK) return s;
+    } else {
+        launch_step_begin(ctx->p, ctx->stream, nullptr);   // no atoms: nothing to rebuild
+    }
     rec.end(KC_REBUILD);
     rec.begin(KC_PAIR);
     launch_pair(ctx->p, ctx->stream);
     rec.end(KC_PAIR);
     rec.begin(KC_GATHER);
-    launch_gather(ctx->p, ctx->stream, hk, store_wj);
+    launch_gather(ctx->p, ctx->stream, hk, false);
     rec.end(KC_GATHER);
     rec.begin(KC_REDUCE);
-    launch_reduce(ctx->p, ctx->stream, record);
+    launch_reduce(ctx->p, ctx->stream, false, true);
     rec.end(KC_REDUCE);
-    return n + 3;
+    // kernels launched every step; a taken rebuild adds the body's kernels
+    *n_kernels = ctx->p.N > 0 ? 5 : 2;
+    return MD_OK;
 }
 
-int enqueue_step(md_ctx *ctx, const Recorder &rec, const double *hk, double dt)
+// The same step with eager launches: the rebuild decision is read back to the host
+// (one small copy and a synchronisation per step).  Kernels and arguments are those of
+// the graph path; this mode exists so that profilers can see every kernel.
+md_status eager_step(md_ctx *ctx, const double *hk, double dt)
 {
+    Recorder rec{ctx, 0, false};
     rec.begin(KC_KICK_DRIFT);
     launch_kick_drift(ctx->p, ctx->stream, hk, dt);
     rec.end(KC_KICK_DRIFT);
-    return 1 + enqueue_forces(ctx, rec, hk, false, true);
+    launch_step_begin(ctx->p, ctx->stream, nullptr);
+    int rebuild = 0;
+    CK(cudaMemcpyAsync(&rebuild, &ctx->p.flags->rebuild, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    rec.begin(KC_REBUILD);
+    if (rebuild) launch_rebuild(ctx->p, ctx->stream);
+    rec.end(KC_REBUILD);
+    rec.begin(KC_PAIR);
+    launch_pair(ctx->p, ctx->stream);
+    rec.end(KC_PAIR);
+    rec.begin(KC_GATHER);
+    launch_gather(ctx->p, ctx->stream, hk, false);
+    rec.end(KC_GATHER);
+    rec.begin(KC_REDUCE);
+    launch_reduce(ctx->p, ctx->stream, false, true);
+    rec.end(KC_REDUCE);
+    CK(cudaGetLastError());
+    return MD_OK;
 }
 
 md_status ensure_events(md_ctx *ctx)
@@ -256,20 +339,25 @@ md_status ensure_wj(md_ctx *ctx)
     return MD_OK;
 }
 
-md_status force_eval(md_ctx *ctx, bool store_wj)
+// One force evaluation (not a time step): rebuild the list if any atom moved more than
+// skin/2 (checked on the host here; md_run decides on the device), then the pair pass,
+// the full gather (F, W, J per atom) and the totals.
+md_status force_eval(md_ctx *ctx, bool full)
 {
-    if (store_wj) {
+    if (full) {
         md_status s = ensure_wj(ctx);
         if (s != MD_OK) return s;
     }
     md_status s0 = clear_error_flags(ctx);
     if (s0 != MD_OK) return s0;
     launch_displacement_check(ctx->p, ctx->stream);
-    Recorder rec{ctx, 0};
-    const bool prof = ctx->profiling;
-    ctx->profiling = false;
-    enqueue_forces(ctx, rec, nullptr, store_wj, false);
-    ctx->profiling = prof;
+    int rebuild = 0;
+    CK(cudaMemcpyAsync(&rebuild, &ctx->p.flags->rebuild, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (rebuild) launch_rebuild(ctx->p, ctx->stream);
+    launch_pair(ctx->p, ctx->stream);
+    launch_gather(ctx->p, ctx->stream, nullptr, full);
+    launch_reduce(ctx->p, ctx->stream, full, false);
     CK(cudaGetLastError());
     md_status s = check_flags(ctx);
     if (s != MD_OK) return s;
@@ -277,22 +365,38 @@ md_status force_eval(md_ctx *ctx, bool store_wj)
     return MD_OK;
 }
 
-md_status capture_graph(md_ctx *ctx, const double *hk, double dt)
+md_status capture_one(md_ctx *ctx, const double *hk, double dt, int steps, cudaGraphExec_t *out)
 {
-    destroy_graph(ctx);
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
     int per_step = 0;
-    for (int s = 0; s < kStepsPerGraph; ++s) per_step = enqueue_step(ctx, Recorder{ctx, s}, hk, dt);
+    for (int st = 0; st < steps; ++st) {
+        md_status s = enqueue_step(ctx, Recorder{ctx, st, true}, hk, dt, &per_step);
+        if (s != MD_OK) {
+            cudaStreamEndCapture(ctx->stream, &g);
+            if (g) cudaGraphDestroy(g);
+            return s;
+        }
+    }
     cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&ctx->gexec, g, 0);
+    e = cudaGraphInstantiate(out, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
+    ctx->kernels_per_step = per_step;
+    return MD_OK;
+}
+
+md_status capture_graph(md_ctx *ctx, const double *hk, double dt)
+{
+    destroy_graph(ctx);
+    md_status s = capture_one(ctx, hk, dt, kStepsPerGraph, &ctx->gexec);
+    if (s != MD_OK) return s;
+    s = capture_one(ctx, hk, dt, 1, &ctx->gexec1);
+    if (s != MD_OK) return s;
     ctx->g_dt = dt;
     ctx->g_series = ctx->p.series;
     ctx->g_prof = ctx->profiling;
-    ctx->kernels_per_step = per_step;
     return MD_OK;
 }
 
@@ -323,7 +427,7 @@ md_status md_create(md_ctx **out, const double box[3], const int pbc[3], int64_t
     *out = nullptr;
     if (!box || !pbc || n_atoms < 0 || (n_atoms > 0 && !types) || !masses_by_type || !params || !params->p)
         return MD_ERR_ARG;
-    if (n_atoms > (int64_t)0x7fffffff) return MD_ERR_ARG;
+    if (n_atoms > kMaxAtoms) return MD_ERR_ARG;   // list entries hold 26-bit atom indices
     md_options opt;
     if (opt_in) opt = *opt_in; else md_default_options(&opt);
     if (params->kind != MD_TERSOFF && params->kind != MD_SW) return MD_ERR_ARG;
@@ -391,7 +495,7 @@ md_status md_create(md_ctx **out, const double box[3], const int pbc[3], int64_t
         p.box.L[a] = box[a];
         p.box.invL[a] = 1.0 / box[a];
         p.box.pbc[a] = pbc[a] ? 1 : 0;
-        if (p.box.pbc[a] && box[a] < 2.0 * p.rl) {
+        if (p.box.pbc[a] && box[a] < 2.0 * p.rl + 0.01) {
             delete ctx;
             return MD_ERR_BOX;
         }
@@ -418,6 +522,13 @@ md_status md_create(md_ctx **out, const double box[3], const int pbc[3], int64_t
         }
         ctx->own_stream = true;
     }
+    e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+        delete ctx;
+        return MD_ERR_CUDA;
+    }
     configure_kernels(p);
 
     const size_t N1 = (size_t)(p.N > 0 ? p.N : 1);
@@ -432,6 +543,8 @@ md_status md_create(md_ctx **out, const double box[3], const int pbc[3], int64_t
     AL(p.force, 3 * N1);
     AL(p.pos_build, 3 * N1);
     AL(p.u, N1);
+    AL(p.posf, 3 * N1);
+    AL(p.stage, 3 * N1);
     AL(p.type, N1);
     AL(p.nn, N1);
     AL(p.nl, (size_t)p.cap * N1);
@@ -484,7 +597,6 @@ md_status md_set_positions(md_ctx *ctx, const double *x, const double *y, const 
     if (ctx->p.N > 0) {
         md_status s = upload3(ctx, ctx->p.pos, x, y, z);
         if (s != MD_OK) return s;
-        launch_wrap(ctx->p, ctx->stream);
     }
     md_status s = set_flag_rebuild(ctx);
     if (s != MD_OK) return s;
@@ -552,26 +664,37 @@ md_status md_run(md_ctx *ctx, int64_t n_steps, double dt_fs, double *series)
         const long long zero = 0;
         CK(cudaMemcpyAsync(&ctx->p.flags->step, &zero, sizeof(zero), cudaMemcpyHostToDevice, ctx->stream));
     }
-    if (!ctx->gexec || ctx->g_dt != dt_fs || ctx->g_series != ctx->p.series || ctx->g_prof != ctx->profiling) {
-        s = capture_graph(ctx, hk, dt_fs);
-        if (s != MD_OK) return s;
-    }
-    int64_t done = 0;
-    while (n_steps - done >= kStepsPerGraph) {
-        CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
-        if (ctx->profiling) {
-            s = accumulate_times(ctx, kStepsPerGraph);
+    if (!ctx->use_graphs) {
+        for (int64_t done = 0; done < n_steps; ++done) {
+            s = eager_step(ctx, hk, dt_fs);
+            if (s != MD_OK) return s;
+            if (ctx->profiling) {
+                s = accumulate_times(ctx, 1);
+                if (s != MD_OK) return s;
+            }
+        }
+    } else {
+        if (!ctx->gexec || !ctx->gexec1 || ctx->g_dt != dt_fs || ctx->g_series != ctx->p.series ||
+            ctx->g_prof != ctx->profiling) {
+            s = capture_graph(ctx, hk, dt_fs);
             if (s != MD_OK) return s;
         }
-        done += kStepsPerGraph;
-    }
-    for (int r = 0; done < n_steps; ++done, ++r) {
-        enqueue_step(ctx, Recorder{ctx, r}, hk, dt_fs);
-        CK(cudaGetLastError());
-    }
-    if (ctx->profiling) {
-        s = accumulate_times(ctx, (int)(n_steps % kStepsPerGraph));
-        if (s != MD_OK) return s;
+        int64_t done = 0;
+        while (n_steps - done >= kStepsPerGraph) {
+            CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
+            if (ctx->profiling) {
+                s = accumulate_times(ctx, kStepsPerGraph);
+                if (s != MD_OK) return s;
+            }
+            done += kStepsPerGraph;
+        }
+        for (; done < n_steps; ++done) {
+            CK(cudaGraphLaunch(ctx->gexec1, ctx->stream));
+            if (ctx->profiling) {
+                s = accumulate_times(ctx, 1);
+                if (s != MD_OK) return s;
+            }
+        }
     }
     if (series) {
         const cudaMemcpyKind k = ctx->io == MD_IO_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
@@ -590,7 +713,11 @@ md_status md_get_state(md_ctx *ctx, double *x, double *v)
 {
     if (!ctx) return MD_ERR_ARG;
     md_status s;
-    if ((s = download(ctx, x, ctx->p.pos, 3 * ctx->p.N)) != MD_OK) return s;
+    if (x && ctx->p.N > 0) {
+        // positions move unwrapped between list builds; report them wrapped into the box
+        launch_wrap_copy(ctx->p, ctx->stream, ctx->p.stage);
+        if ((s = download(ctx, x, ctx->p.stage, 3 * ctx->p.N)) != MD_OK) return s;
+    }
     if ((s = download(ctx, v, ctx->p.vel, 3 * ctx->p.N)) != MD_OK) return s;
     CK(cudaStreamSynchronize(ctx->stream));
     return MD_OK;
@@ -607,7 +734,15 @@ md_status md_get_stats(md_ctx *ctx, md_stats *out)
     out->n_rebuilds = f.n_rebuilds;
     out->max_neigh_seen = f.max_nn;
     out->kernel_launches_per_step = ctx->kernels_per_step;
+    out->kernel_launches_per_rebuild = ctx->kernels_per_rebuild;
     out->device_bytes = ctx->allocated;
+    return MD_OK;
+}
+
+md_status md_set_graph_mode(md_ctx *ctx, int use_graphs)
+{
+    if (!ctx) return MD_ERR_ARG;
+    ctx->use_graphs = use_graphs != 0;
     return MD_OK;
 }
 
@@ -653,6 +788,7 @@ void md_destroy(md_ctx *ctx)
     for (void *a : ctx->allocs)
         if (a) cudaFree(a);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
     delete ctx;
 }
 

@@ -12,6 +12,22 @@ constexpr double kAccUnit = 9.648533215665328e-3;
 constexpr int kMaxTypes = 4;
 constexpr int kMaxListCap = 32;   // list slots per atom (active mask is 32 bits)
 
+// List entries.  A neighbour-list entry packs the neighbour's index (low 26 bits, so a
+// context holds at most 2^26 atoms) with the periodic image it was found at when the
+// list was built: code = (sx+1) + 3 (sy+1) + 9 (sz+1) in bits 26..30, s in {-1, 0, 1},
+// and r_ij = r_j - r_i + (sx Lx, sy Ly, sz Lz).  Code 13 means no shift.
+constexpr int kAtomBits = 26;
+constexpr int kAtomMask = (1 << kAtomBits) - 1;
+constexpr int kNoShift = 13;
+constexpr int64_t kMaxAtoms = (int64_t)1 << kAtomBits;
+
+__host__ __device__ __forceinline__ int list_entry(int j, int sx, int sy, int sz)
+{
+    return j | (((sx + 1) + 3 * (sy + 1) + 9 * (sz + 1)) << kAtomBits);
+}
+__host__ __device__ __forceinline__ int list_atom(int e) { return e & kAtomMask; }
+__host__ __device__ __forceinline__ int list_code(int e) { return (int)((unsigned)e >> kAtomBits); }
+
 // Orthorhombic box with per-axis periodicity.
 struct Box {
     double L[3];
@@ -30,6 +46,7 @@ struct Flags {
     int n_rebuilds;       // builds since creation
     int pad;
     long long step;       // index of the next series row
+    long long row;        // series row of the step in flight
 };
 
 // Tersoff (single element).  Eqs. 2-6 with Tersoff-1989 f_R, f_A, f_C.
@@ -61,6 +78,7 @@ struct PairArgs {
     const int *nl;          // cap x N, column-major: nl[m N + i]
     int cap;                // list capacity
     T rc2;                  // cutoff^2 in T
+    double shift[3];        // box lengths, for the per-entry image shifts
     // outputs, "compact active" layout: row k = k-th in-cutoff neighbour of i
     T *d;                   // 3 x MAXA x N : d[(c MAXA + k) N + i] = dU_i/dr_ij (component c)
     T *r;                   // 3 x MAXA x N : r_ij
@@ -87,16 +105,32 @@ struct GatherArgs {
     double *force;          // 3N, written
     double *w_out;          // 9N or nullptr
     double *j_out;          // 3N or nullptr
-    double *partials;       // gridDim.x x kNumPartials
+    double *partials;       // component-major: partials[c * gridDim.x + block]
     Flags *flags;
 };
 
-// per-block partial sums: U, K, J(3), W(9)
+// per-block partial sums: U, K, J(3), W(9); a velocity-Verlet step needs the first 5
 constexpr int kNumPartials = 14;
+constexpr int kStepPartials = 5;
 
-__device__ __forceinline__ double min_image(double d, double L, double invL, int periodic)
+// r_ij from positions and a list entry's image code (three fp64 subtractions, plus
+// one addition per shifted axis).
+__device__ __forceinline__ void bond_vector(const double *pos, int64_t N, int64_t i, int e, const Box &box,
+                                            double xi, double yi, double zi, double &dx, double &dy,
+                                            double &dz)
 {
-    return periodic ? fma(-L, rint(d * invL), d) : d;
+    const int j = list_atom(e);
+    dx = pos[j] - xi;
+    dy = pos[N + j] - yi;
+    dz = pos[2 * N + j] - zi;
+    const int code = list_code(e);
+    if (code != kNoShift) {
+        const int sx = code % 3 - 1, sy = (code / 3) % 3 - 1, sz = code / 9 - 1;
+        if (sx) dx += sx > 0 ? box.L[0] : -box.L[0];
+        if (sy) dy += sy > 0 ? box.L[1] : -box.L[1];
+        if (sz) dz += sz > 0 ? box.L[2] : -box.L[2];
+    }
+    (void)i;
 }
 
 }  // namespace mdk

@@ -23,6 +23,8 @@ struct Plan {
     // per-atom state (fp64)
     double *pos = nullptr, *vel = nullptr, *force = nullptr, *pos_build = nullptr;
     double *u = nullptr, *w = nullptr, *j = nullptr;
+    float *posf = nullptr;      // fp32 positions for the list build
+    double *stage = nullptr;    // 3N scratch for wrapped output positions
     int *type = nullptr;
     // neighbour list
     int *nn = nullptr, *nl = nullptr;
@@ -50,27 +52,32 @@ extern const char *kKernelClassNames[KC_COUNT];
 
 // neigh.cu
 int scan_block_elems();
-// Build the cell list, the sorted Verlet list (cutoff rl) and the reverse-slot index.
-// With `conditional`, every kernel first reads flags->rebuild and returns at once when
-// it is 0, so the chain can sit unconditionally inside a captured CUDA graph.
-// Returns the number of kernels launched.
-int launch_rebuild(const Plan &p, cudaStream_t s, bool conditional);
+// fp32 safety margin added to rl in the list build (covers coordinate rounding).
+float list_margin(const Plan &p);
+// Wrap positions, build the cell list, the sorted Verlet list (cutoff rl, entries with
+// image shifts) and the reverse-slot index; clears flags->rebuild.  Returns the number
+// of kernels launched.
+int launch_rebuild(const Plan &p, cudaStream_t s);
 // Set flags->rebuild if any atom moved more than skin/2 since the last build.
 void launch_displacement_check(const Plan &p, cudaStream_t s);
-// Wrap coordinates on periodic axes into [0, L).
-void launch_wrap(const Plan &p, cudaStream_t s);
+// dst[3N] = positions wrapped into [0, L) on periodic axes.
+void launch_wrap_copy(const Plan &p, cudaStream_t s, double *dst);
 
 // force.cu
 size_t pair_smem_bytes(const Plan &p);
 void configure_kernels(const Plan &p);
-// Half-kick + drift + wrap + displacement check (first half of a velocity-Verlet step).
+// Half-kick + drift + displacement check (first half of a velocity-Verlet step).
 void launch_kick_drift(const Plan &p, cudaStream_t s, const double *half_kick, double dt);
+// Start of a graph step: claim the series row and set the rebuild conditional from
+// flags->rebuild (h may be null when the graph has no rebuild node).
+void launch_step_begin(const Plan &p, cudaStream_t s, const cudaGraphConditionalHandle *h);
 // Per-atom pair pass: U_i and dU_i/dr_ij for every in-cutoff neighbour.
 void launch_pair(const Plan &p, cudaStream_t s);
-// Per-atom gather: F_i, W_i, J_i (Eqs. 28-30), optional half-kick, block partial sums.
-void launch_gather(const Plan &p, cudaStream_t s, const double *half_kick, bool store_wj);
+// Per-atom gather: F_i (Eq. 28), J_i (Eq. 30) and, for a force evaluation, W_i (Eq. 29)
+// and per-atom outputs; optional half-kick; block partial sums.
+void launch_gather(const Plan &p, cudaStream_t s, const double *half_kick, bool full_outputs);
 int gather_blocks(int64_t N);
 // Fixed-order reduction of the gather's block partials into totals (and a series row).
-void launch_reduce(const Plan &p, cudaStream_t s, bool record_series);
+void launch_reduce(const Plan &p, cudaStream_t s, bool full_outputs, bool record_series);
 
 }  // namespace mdk

@@ -2,13 +2,20 @@
 // built with the standard cell-list method for a uniform cutoff), the reverse-slot
 // index the atomic-free gather needs, and the skin/2 displacement check.
 //
-// Pipeline (all on the device, one thread per atom or per cell):
-//   clear counts -> bin atoms (cell id + rank in cell via atomicAdd) -> exclusive scan
-//   of cell counts -> scatter atoms into cell order -> per-atom list search over the
-//   distinct neighbouring cells, kept sorted by atom index -> reverse slot of i in j's
-//   list -> done (clear the rebuild flag).
-// The order of atoms inside a cell depends on atomic timing, but every list is sorted
-// by index, so the lists are deterministic.
+// Build pipeline (one thread per atom or per cell):
+//   zero cell counts -> wrap positions into the box, fp32 copy, cell id and rank in
+//   cell (atomicAdd) -> exclusive scan of cell counts -> scatter atoms into cell order
+//   -> per-atom search over the distinct neighbouring cells -> reverse slots -> done.
+// Positions are wrapped only here: between builds they move freely, so every listed
+// pair keeps the periodic image it was found with.  Each list entry therefore carries
+// that image shift (see md_internal.cuh, "list entries") and a step computes r_ij with
+// three fp64 subtractions instead of a minimum-image reduction.
+//
+// The candidate test runs in fp32 with a margin that covers the fp32 rounding of the
+// coordinates, so the list is a superset of the exact fp64 list at rl; the force passes
+// apply the exact cutoff.  fp32 negation is exact, so the test is symmetric in i and j
+// and the lists stay symmetric.  Atom order inside a cell depends on atomic timing, but
+// each list is sorted by atom index, so the lists are deterministic.
 #include "md_plan.cuh"
 
 namespace mdk {
@@ -19,44 +26,41 @@ constexpr int kScanThreads = 256;
 constexpr int kScanPerThread = 4;
 constexpr int kScanElems = kScanThreads * kScanPerThread;  // per block
 
-__device__ __forceinline__ bool skip(const Flags *f, bool conditional)
-{
-    return conditional && (*(volatile const int *)&f->rebuild) == 0;
-}
-
 __device__ __forceinline__ int cell_coord(double x, int nc, double invL)
 {
     int c = (int)floor(x * invL * (double)nc);
     return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
 }
 
-__global__ void k_cell_clear(int64_t ncell, int *count, Flags *flags, bool cond)
+// Wrap coordinates on periodic axes into [0, L), keep an fp32 copy, bin into cells.
+__global__ void k_cell_count(int64_t N, double *pos, float *posf, Box box, int nc0, int nc1, int nc2,
+                             int *atom_cell, int *atom_rank, int *count)
 {
-    if (skip(flags, cond)) return;
-    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c == 0) flags->max_nn = 0;
-    if (c < ncell) count[c] = 0;
-}
-
-__global__ void k_cell_count(int64_t N, const double *pos, Box box, int nc0, int nc1, int nc2,
-                             int *atom_cell, int *atom_rank, int *count, Flags *flags, bool cond)
-{
-    if (skip(flags, cond)) return;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    int cx = cell_coord(pos[i], nc0, box.invL[0]);
-    int cy = cell_coord(pos[N + i], nc1, box.invL[1]);
-    int cz = cell_coord(pos[2 * N + i], nc2, box.invL[2]);
-    int c = (cx * nc1 + cy) * nc2 + cz;
+    int cc[3];
+    const int nc[3] = {nc0, nc1, nc2};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double x = pos[a * N + i];
+        if (box.pbc[a]) {
+            x -= box.L[a] * floor(x * box.invL[a]);
+            if (x >= box.L[a]) x -= box.L[a];
+            if (x < 0.0) x += box.L[a];
+            pos[a * N + i] = x;
+        }
+        posf[a * N + i] = (float)x;
+        cc[a] = cell_coord(x, nc[a], box.invL[a]);
+    }
+    const int c = (cc[0] * nc1 + cc[1]) * nc2 + cc[2];
     atom_cell[i] = c;
     atom_rank[i] = atomicAdd(&count[c], 1);
 }
 
 // Exclusive scan, pass 1: scan each block's kScanElems counts, store block totals.
 __global__ void __launch_bounds__(kScanThreads)
-k_scan_blocks(int64_t n, const int *in, int *out, int *block_sums, Flags *flags, bool cond)
+k_scan_blocks(int64_t n, const int *in, int *out, int *block_sums)
 {
-    if (skip(flags, cond)) return;
     __shared__ int warp_tot[kScanThreads / 32];
     const int64_t base = (int64_t)blockIdx.x * kScanElems + (int64_t)threadIdx.x * kScanPerThread;
     int v[kScanPerThread];
@@ -96,10 +100,8 @@ k_scan_blocks(int64_t n, const int *in, int *out, int *block_sums, Flags *flags,
 }
 
 // Pass 2: exclusive scan of the block totals by one block, in chunks, with a carry.
-__global__ void __launch_bounds__(kScanThreads)
-k_scan_sums(int64_t nb, int *block_sums, Flags *flags, bool cond)
+__global__ void __launch_bounds__(kScanThreads) k_scan_sums(int64_t nb, int *block_sums)
 {
-    if (skip(flags, cond)) return;
     __shared__ int warp_tot[kScanThreads / 32];
     __shared__ int carry;
     if (threadIdx.x == 0) carry = 0;
@@ -136,17 +138,15 @@ k_scan_sums(int64_t nb, int *block_sums, Flags *flags, bool cond)
 }
 
 // Pass 3: add each block's offset.
-__global__ void k_scan_add(int64_t n, int *out, const int *block_sums, Flags *flags, bool cond)
+__global__ void k_scan_add(int64_t n, int *out, const int *block_sums)
 {
-    if (skip(flags, cond)) return;
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx < n) out[idx] += block_sums[idx / kScanElems];
 }
 
 __global__ void k_cell_fill(int64_t N, const int *atom_cell, const int *atom_rank,
-                            const int *cell_start, int *cell_atoms, Flags *flags, bool cond)
+                            const int *cell_start, int *cell_atoms)
 {
-    if (skip(flags, cond)) return;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     cell_atoms[cell_start[atom_cell[i]] + atom_rank[i]] = (int)i;
@@ -171,21 +171,22 @@ __device__ __forceinline__ int stencil_axis(int c, int nc, int periodic, int *ou
     return n;
 }
 
-// One thread per atom: search the distinct neighbouring cells, keep every j != i with
-// |r_ij| < rl (minimum image) in ascending index order.  Also snapshots the build
-// positions for the skin/2 test.
-__global__ void k_build_list(int64_t N, const double *pos, Box box, int nc0, int nc1, int nc2,
-                             const int *atom_cell, const int *cell_start, const int *cell_count,
-                             const int *cell_atoms, double rl2, int cap, int *nn, int *nl,
-                             double *pos_build, Flags *flags, bool cond)
+// One thread per atom: search the distinct neighbouring cells and keep every j != i
+// with |r_ij| < rl + margin (fp32, minimum image), in ascending index order, each with
+// the image shift it was found at.  Snapshots the build positions for the skin test.
+__global__ void k_build_list(int64_t N, const double *pos, const float *posf, Box box, int nc0, int nc1,
+                             int nc2, const int *atom_cell, const int *cell_start, const int *cell_count,
+                             const int *cell_atoms, float rlm2, int cap, int *nn, int *nl,
+                             double *pos_build, Flags *flags)
 {
-    if (skip(flags, cond)) return;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    const double xi = pos[i], yi = pos[N + i], zi = pos[2 * N + i];
-    pos_build[i] = xi;
-    pos_build[N + i] = yi;
-    pos_build[2 * N + i] = zi;
+    pos_build[i] = pos[i];
+    pos_build[N + i] = pos[N + i];
+    pos_build[2 * N + i] = pos[2 * N + i];
+    const float xi = posf[i], yi = posf[N + i], zi = posf[2 * N + i];
+    const float L0 = (float)box.L[0], L1 = (float)box.L[1], L2 = (float)box.L[2];
+    const float iL0 = (float)box.invL[0], iL1 = (float)box.invL[1], iL2 = (float)box.invL[2];
     const int c = atom_cell[i];
     const int cz = c % nc2, cy = (c / nc2) % nc1, cx = c / (nc1 * nc2);
     int ox[3], oy[3], oz[3];
@@ -202,17 +203,23 @@ __global__ void k_build_list(int64_t N, const double *pos, Box box, int nc0, int
                 for (int q = s0; q < s1; ++q) {
                     const int j = cell_atoms[q];
                     if (j == (int)i) continue;
-                    const double dx = min_image(pos[j] - xi, box.L[0], box.invL[0], box.pbc[0]);
-                    const double dy = min_image(pos[N + j] - yi, box.L[1], box.invL[1], box.pbc[1]);
-                    const double dz = min_image(pos[2 * N + j] - zi, box.L[2], box.invL[2], box.pbc[2]);
-                    if (dx * dx + dy * dy + dz * dz < rl2) {
-                        if (cnt < cap) {       // insertion into the sorted prefix
+                    float dx = posf[j] - xi, dy = posf[N + j] - yi, dz = posf[2 * N + j] - zi;
+                    // image shift s in {-1, 0, 1}: r_ij = x_j - x_i + s L
+                    const float sx = box.pbc[0] ? -rintf(dx * iL0) : 0.f;
+                    const float sy = box.pbc[1] ? -rintf(dy * iL1) : 0.f;
+                    const float sz = box.pbc[2] ? -rintf(dz * iL2) : 0.f;
+                    dx = fmaf(sx, L0, dx);
+                    dy = fmaf(sy, L1, dy);
+                    dz = fmaf(sz, L2, dz);
+                    if (dx * dx + dy * dy + dz * dz < rlm2) {
+                        const int e_ = list_entry(j, (int)sx, (int)sy, (int)sz);
+                        if (cnt < cap) {       // insertion into the index-sorted prefix
                             int m = cnt;
-                            while (m > 0 && loc[m - 1] > j) {
+                            while (m > 0 && list_atom(loc[m - 1]) > j) {
                                 loc[m] = loc[m - 1];
                                 --m;
                             }
-                            loc[m] = j;
+                            loc[m] = e_;
                         }
                         ++cnt;
                     }
@@ -225,58 +232,59 @@ __global__ void k_build_list(int64_t N, const double *pos, Box box, int nc0, int
     atomicMax(&flags->max_nn, cnt);
 }
 
-// rev[m N + i] = slot of i in the list of j = nl[m N + i] (lists are symmetric).
-__global__ void k_build_rev(int64_t N, const int *nn, const int *nl, uint8_t *rev, Flags *flags,
-                            bool cond)
+// rev[m N + i] = slot of i in the list of j = atom of nl[m N + i] (lists are symmetric).
+__global__ void k_build_rev(int64_t N, const int *nn, const int *nl, uint8_t *rev, Flags *flags)
 {
-    if (skip(flags, cond)) return;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const int n = nn[i];
     for (int m = 0; m < n; ++m) {
-        const int j = nl[(int64_t)m * N + i];
+        const int j = list_atom(nl[(int64_t)m * N + i]);
         const int nj = nn[j];
         int found = -1;
         for (int q = 0; q < nj; ++q)
-            if (nl[(int64_t)q * N + j] == (int)i) { found = q; break; }
+            if (list_atom(nl[(int64_t)q * N + j]) == (int)i) { found = q; break; }
         if (found < 0) { flags->asym = 1; found = 0; }
         rev[(int64_t)m * N + i] = (uint8_t)found;
     }
 }
 
-__global__ void k_build_done(Flags *flags, bool cond)
+__global__ void k_build_done(Flags *flags)
 {
-    if (skip(flags, cond)) return;
     flags->rebuild = 0;
     flags->n_rebuilds += 1;
 }
 
-__global__ void k_displacement(int64_t N, const double *pos, const double *pos_build, Box box,
-                               double half_skin2, Flags *flags)
+// skin/2 test.  Positions are not wrapped between builds, so x - x_build is the true
+// displacement; the difference is taken in fp64 and squared in fp32.
+__global__ void k_displacement(int64_t N, const double *pos, const double *pos_build, float half_skin2,
+                               Flags *flags)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    double d2 = 0.0;
+    float d2 = 0.f;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        double d = min_image(pos[a * N + i] - pos_build[a * N + i], box.L[a], box.invL[a], box.pbc[a]);
-        d2 = fma(d, d, d2);
+        const float d = (float)(pos[a * N + i] - pos_build[a * N + i]);
+        d2 = fmaf(d, d, d2);
     }
     if (!(d2 <= half_skin2)) flags->rebuild = 1;
 }
 
-__global__ void k_wrap(int64_t N, double *pos, Box box)
+// Wrapped copy of the positions (for output): dst[3N] = pos wrapped into [0, L).
+__global__ void k_wrap_copy(int64_t N, const double *pos, double *dst, Box box)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        if (!box.pbc[a]) continue;
         double x = pos[a * N + i];
-        x -= box.L[a] * floor(x * box.invL[a]);
-        if (x >= box.L[a]) x -= box.L[a];
-        if (x < 0.0) x += box.L[a];
-        pos[a * N + i] = x;
+        if (box.pbc[a]) {
+            x -= box.L[a] * floor(x * box.invL[a]);
+            if (x >= box.L[a]) x -= box.L[a];
+            if (x < 0.0) x += box.L[a];
+        }
+        dst[a * N + i] = x;
     }
 }
 
@@ -286,27 +294,38 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 
 int scan_block_elems() { return kScanElems; }
 
-int launch_rebuild(const Plan &p, cudaStream_t s, bool cond)
+float list_margin(const Plan &p)
+{
+    // Bound on the fp32 error of a listed separation: coordinates below 2^e carry an
+    // absolute rounding error of at most 2^(e-24); a difference, a shift by L and the
+    // squared norm stay within a few of those units per component.
+    double lmax = 1.0;
+    for (int a = 0; a < 3; ++a) lmax = p.box.L[a] > lmax ? p.box.L[a] : lmax;
+    const double ulp = std::ldexp(1.0, std::ilogb(lmax) + 1 - 24);
+    return (float)(16.0 * ulp + 1e-6 * p.rl);
+}
+
+int launch_rebuild(const Plan &p, cudaStream_t s)
 {
     if (p.N == 0) return 0;
     const int T = 256;
-    k_cell_clear<<<blocks_for(p.ncell, T), T, 0, s>>>(p.ncell, p.cell_count, p.flags, cond);
-    k_cell_count<<<blocks_for(p.N, T), T, 0, s>>>(p.N, p.pos, p.box, p.nc[0], p.nc[1], p.nc[2],
-                                                 p.atom_cell, p.atom_rank, p.cell_count, p.flags, cond);
+    cudaMemsetAsync(p.cell_count, 0, sizeof(int) * p.ncell, s);
+    cudaMemsetAsync(&p.flags->max_nn, 0, sizeof(int), s);
+    k_cell_count<<<blocks_for(p.N, T), T, 0, s>>>(p.N, p.pos, p.posf, p.box, p.nc[0], p.nc[1], p.nc[2],
+                                                 p.atom_cell, p.atom_rank, p.cell_count);
     const int64_t nb = (p.ncell + kScanElems - 1) / kScanElems;
-    k_scan_blocks<<<(unsigned)nb, kScanThreads, 0, s>>>(p.ncell, p.cell_count, p.cell_start,
-                                                        p.scan_blocks, p.flags, cond);
-    k_scan_sums<<<1, kScanThreads, 0, s>>>(nb, p.scan_blocks, p.flags, cond);
-    k_scan_add<<<blocks_for(p.ncell, T), T, 0, s>>>(p.ncell, p.cell_start, p.scan_blocks, p.flags, cond);
-    k_cell_fill<<<blocks_for(p.N, T), T, 0, s>>>(p.N, p.atom_cell, p.atom_rank, p.cell_start,
-                                                p.cell_atoms, p.flags, cond);
+    k_scan_blocks<<<(unsigned)nb, kScanThreads, 0, s>>>(p.ncell, p.cell_count, p.cell_start, p.scan_blocks);
+    k_scan_sums<<<1, kScanThreads, 0, s>>>(nb, p.scan_blocks);
+    k_scan_add<<<blocks_for(p.ncell, T), T, 0, s>>>(p.ncell, p.cell_start, p.scan_blocks);
+    k_cell_fill<<<blocks_for(p.N, T), T, 0, s>>>(p.N, p.atom_cell, p.atom_rank, p.cell_start, p.cell_atoms);
     const int TB = 128;
-    k_build_list<<<blocks_for(p.N, TB), TB, 0, s>>>(p.N, p.pos, p.box, p.nc[0], p.nc[1], p.nc[2],
+    const float rlm = (float)p.rl + list_margin(p);
+    k_build_list<<<blocks_for(p.N, TB), TB, 0, s>>>(p.N, p.pos, p.posf, p.box, p.nc[0], p.nc[1], p.nc[2],
                                                    p.atom_cell, p.cell_start, p.cell_count, p.cell_atoms,
-                                                   p.rl * p.rl, p.cap, p.nn, p.nl, p.pos_build, p.flags, cond);
-    k_build_rev<<<blocks_for(p.N, T), T, 0, s>>>(p.N, p.nn, p.nl, p.rev, p.flags, cond);
-    k_build_done<<<1, 1, 0, s>>>(p.flags, cond);
-    return 9;
+                                                   rlm * rlm, p.cap, p.nn, p.nl, p.pos_build, p.flags);
+    k_build_rev<<<blocks_for(p.N, T), T, 0, s>>>(p.N, p.nn, p.nl, p.rev, p.flags);
+    k_build_done<<<1, 1, 0, s>>>(p.flags);
+    return 8;
 }
 
 void launch_displacement_check(const Plan &p, cudaStream_t s)
@@ -314,14 +333,14 @@ void launch_displacement_check(const Plan &p, cudaStream_t s)
     if (p.N == 0) return;
     const int T = 256;
     const double hs = 0.5 * p.skin;
-    k_displacement<<<blocks_for(p.N, T), T, 0, s>>>(p.N, p.pos, p.pos_build, p.box, hs * hs, p.flags);
+    k_displacement<<<blocks_for(p.N, T), T, 0, s>>>(p.N, p.pos, p.pos_build, (float)(hs * hs), p.flags);
 }
 
-void launch_wrap(const Plan &p, cudaStream_t s)
+void launch_wrap_copy(const Plan &p, cudaStream_t s, double *dst)
 {
     if (p.N == 0) return;
     const int T = 256;
-    k_wrap<<<blocks_for(p.N, T), T, 0, s>>>(p.N, p.pos, p.box);
+    k_wrap_copy<<<blocks_for(p.N, T), T, 0, s>>>(p.N, p.pos, dst, p.box);
 }
 
 }  // namespace mdk

@@ -48,15 +48,15 @@ class md_options(ctypes.Structure):
 class md_stats(ctypes.Structure):
     _fields_ = [("n_atoms", ctypes.c_int64), ("steps_done", ctypes.c_int64), ("n_rebuilds", ctypes.c_int64),
                 ("max_neigh_seen", ctypes.c_int), ("kernel_launches_per_step", ctypes.c_int),
-                ("device_bytes", ctypes.c_size_t)]
+                ("kernel_launches_per_rebuild", ctypes.c_int), ("device_bytes", ctypes.c_size_t)]
 
 
 _lock = threading.Lock()
 _lib = None
 
 EXPORTS = ["md_default_options", "md_create", "md_set_positions", "md_set_velocities", "md_compute",
-           "md_run", "md_get_state", "md_get_stats", "md_set_profiling", "md_kernel_times",
-           "md_last_error", "md_destroy"]
+           "md_run", "md_get_state", "md_get_stats", "md_set_graph_mode", "md_set_profiling",
+           "md_kernel_times", "md_last_error", "md_destroy"]
 
 
 def library_path() -> str:
@@ -85,6 +85,7 @@ def load(build_if_missing: bool = False):
         lib.md_run.argtypes = [P, ctypes.c_int64, ctypes.c_double, P]
         lib.md_get_state.argtypes = [P, P, P]
         lib.md_get_stats.argtypes = [P, ctypes.POINTER(md_stats)]
+        lib.md_set_graph_mode.argtypes = [P, ctypes.c_int]
         lib.md_set_profiling.argtypes = [P, ctypes.c_int]
         lib.md_kernel_times.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
                                         ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double),
@@ -177,6 +178,11 @@ def md_get_stats(ctx) -> md_stats:
     s = md_stats()
     _check(lib, ctx, lib.md_get_stats(ctx, ctypes.byref(s)))
     return s
+
+
+def md_set_graph_mode(ctx, use_graphs: bool):
+    lib = load()
+    _check(lib, ctx, lib.md_set_graph_mode(ctx, 1 if use_graphs else 0))
 
 
 def md_set_profiling(ctx, enable: bool):

@@ -148,11 +148,25 @@ def test_rebuilds_happen_and_stay_exact(md):
         pos, _ = g.state()
         st = g.stats()
     assert st.n_rebuilds >= 3
-    p2, _, ser2 = O.run(s.pos, s.vel, s.mass, s.box, s.pbc, s.kind, s.params, 60, 1.0)
+    p2, v2, ser2 = O.run(s.pos, s.vel, s.mass, s.box, s.pbc, s.kind, s.params, 60, 1.0)
     d = pos - p2
     d -= np.round(d / s.box) * s.box
     assert np.abs(d).max() < TRAJ_TOL
     assert rel(ser, ser2) < TRAJ_TOL
+
+
+def test_compute_after_run_continues_the_trajectory(md):
+    """md_compute after md_run evaluates the state the run reached (graph-replayed steps
+    leave positions unwrapped between list builds): compare with the oracle's own
+    end state of the same trajectory."""
+    s = I.si_diamond_tersoff(n=4, jitter_amp=0.05, temperature=900.0)
+    with md.from_inputs(s, skin=0.2) as g:
+        g.run(37, 1.0)
+        out = g.compute()
+    p2, v2, _ = O.run(s.pos, s.vel, s.mass, s.box, s.pbc, s.kind, s.params, 37, 1.0)
+    ref = O.compute(p2, s.box, s.pbc, s.kind, s.params, v2)
+    for k in ("F", "U", "W", "J"):
+        assert rel(out[k], ref[k]) < 1e-9, k
 
 
 def test_list_overflow_is_reported(md):
@@ -177,10 +191,72 @@ def test_device_io_matches_host_io(md):
     g.close()
 
 
-@pytest.mark.parametrize("name,make", [
-    ("sw_si_512000", lambda: I.si_diamond_sw(n=40)),
-    ("tersoff_c_graphene_1M", lambda: I.c_graphene_tersoff()),
-], ids=["sw_si_512000", "tersoff_c_graphene_1M"])
-def test_full_size_compute(md, name, make):
-    """Full-size workloads, in the same launch configuration the benchmark uses."""
-    compare_compute(md, make())
+FULL = [
+    ("sw_si_512000", lambda j: I.si_diamond_sw(n=40, jitter_amp=j), 1.0),
+    ("tersoff_c_graphene_1M", lambda j: I.c_graphene_tersoff(jitter_amp=j), 0.5),
+]
+
+
+@pytest.mark.parametrize("name,make,dt", FULL, ids=[f[0] for f in FULL])
+def test_full_size_compute(md, name, make, dt):
+    """Full-size workloads in the benchmark's launch configuration, jittered by
+    +-0.02 A so that every per-atom field is non-trivial."""
+    compare_compute(md, make(0.02))
+
+
+def test_full_size_perfect_lattice_sw(md):
+    """The unjittered 512,000-atom SW crystal at a = 5.431 A sits at the energy minimum:
+    U_i = -2 epsilon to 1e-12 on both sides and every force vanishes to round-off."""
+    s = I.si_diamond_sw(n=40)
+    ref = O.compute(s.pos, s.box, s.pbc, s.kind, s.params, s.vel)
+    with md.from_inputs(s) as g:
+        out = g.compute()
+    assert rel(out["U"], ref["U"]) < FP64_TOL
+    assert np.abs(out["F"]).max() < 1e-10 and np.abs(ref["F"]).max() < 1e-10
+
+
+@pytest.mark.parametrize("name,make,dt", FULL, ids=[f[0] for f in FULL])
+def test_full_size_trajectory(md, name, make, dt):
+    """10 velocity-Verlet steps of the full-size benchmark workload, GPU (graph-replayed
+    steps, skin list) against the oracle (list rebuilt every step)."""
+    s = make(0.0 if name.startswith("sw") else 0.02)
+    steps = 10
+    with md.from_inputs(s) as g:
+        ser = g.run(steps, dt)
+        pos, vel = g.state()
+    p2, v2, ser2 = O.run(s.pos, s.vel, s.mass, s.box, s.pbc, s.kind, s.params, steps, dt)
+    d = pos - p2
+    d -= np.round(d / s.box) * s.box * s.pbc
+    assert np.abs(d).max() < TRAJ_TOL
+    assert rel(vel, v2) < TRAJ_TOL
+    for c in range(5):
+        assert rel(ser[:, c], ser2[:, c]) < TRAJ_TOL, c
+
+
+def test_profiling_records_every_kernel_class(md):
+    """Per-kernel CUDA-event timing over graph-replayed (8) and eager (2) steps."""
+    s = I.si_diamond_tersoff(n=4)
+    with md.from_inputs(s) as g:
+        md.md_set_profiling(g.ctx, True)
+        g.run(10, 1.0)
+        kt = md.md_kernel_times(g.ctx)
+        st = g.stats()
+    assert set(kt) == {"kick_drift", "rebuild", "pair", "gather", "reduce"}
+    for name, (n, ms) in kt.items():
+        assert n == 10 and ms > 0.0, (name, n, ms)
+    assert st.kernel_launches_per_step >= 5
+
+
+def test_eager_launches_match_graph_replay_bitwise(md):
+    s = I.si_diamond_tersoff(n=4, jitter_amp=0.05, temperature=900.0)
+    outs = []
+    for graphs in (True, False):
+        with md.from_inputs(s, skin=0.2) as g:
+            md.md_set_graph_mode(g.ctx, graphs)
+            ser = g.run(21, 1.0)
+            pos, vel = g.state()
+            st = g.stats()
+            outs.append((ser, pos, vel, st.n_rebuilds))
+    assert outs[0][3] == outs[1][3] and outs[0][3] >= 2
+    for a, b in zip(outs[0][:3], outs[1][:3]):
+        assert np.array_equal(a, b)
