@@ -105,7 +105,8 @@ md_status md_create(md_ctx **out, const double box[3], const int pbc[3], int64_t
                     const md_params *params, const md_options *opt);
 
 /* Positions, SoA (x[N], y[N], z[N]), A.  Coordinates on periodic axes are wrapped into
- * [0, L).  Invalidates the neighbour list and forces. */
+ * [0, L).  Invalidates the neighbour list and forces.  (Pools: MD_ERR_STATE; systems
+ * bring their positions to md_batch_add.) */
 md_status md_set_positions(md_ctx *ctx, const double *x, const double *y, const double *z);
 
 /* Velocities, SoA, A/fs. */
@@ -121,8 +122,9 @@ md_status md_compute(md_ctx *ctx, double *f, double *u, double *w, double *j, do
 /* Advance n_steps velocity-Verlet steps of dt_fs (NVE):
  *   v += F/m dt/2; x += v dt (wrapped); [rebuild list if needed]; F = F(x);
  *   v += F/m dt/2; record U, K, J with x(t+dt), v(t+dt).
- * series: NULL or n_steps x 5 doubles (U, K, Jx, Jy, Jz per step; host pointer, or a
- * device pointer under MD_IO_DEVICE).  Steps are replayed from a CUDA graph; the host
+ * series: NULL or n_steps x n_systems x 5 doubles (U, K, Jx, Jy, Jz per step and
+ * system; n_systems = 1 for md_create contexts, max_systems for pools; host pointer, or
+ * a device pointer under MD_IO_DEVICE).  Steps are replayed from CUDA graphs; the host
  * is not involved between steps. */
 md_status md_run(md_ctx *ctx, int64_t n_steps, double dt_fs, double *series);
 
@@ -137,6 +139,8 @@ typedef struct {
     int max_neigh_seen;      /* largest list length at the last build                 */
     int kernel_launches_per_step; /* kernels every md_run step launches               */
     int kernel_launches_per_rebuild; /* extra kernels of a step that rebuilds the list */
+    int pair_deferred;       /* atoms with more than 4 in-cutoff bonds at the last pair pass
+                                (handled by the full-capacity pass)                      */
     size_t device_bytes;     /* bytes the context has allocated on the device         */
 } md_stats;
 md_status md_get_stats(md_ctx *ctx, md_stats *out);
@@ -154,6 +158,56 @@ md_status md_set_graph_mode(md_ctx *ctx, int use_graphs);
 md_status md_set_profiling(md_ctx *ctx, int enable);
 md_status md_kernel_times(md_ctx *ctx, int max_k, const char **names, int64_t *launches,
                           double *total_ms, int *n_out);
+
+/* ---------------------------------------------------------------- pools ----------
+ * A pool holds many independent systems (up to max_systems) over one flattened atom
+ * index of `atom_capacity` atoms, stepped together by md_run: every kernel of a step
+ * covers the whole pool in one launch, each atom using its system's box, cell grid and
+ * parameter set; per-system totals are reduced separately.  Systems are added and
+ * removed between calls (continuous batching), each with its own step budget: a
+ * system stops on the device when its budget reaches zero, so systems of different
+ * lengths share the same graph-replayed steps.  A system's results are those it would
+ * have alone (same kernels, same per-atom arithmetic and summation order).
+ * All systems of a pool use one potential kind (Tersoff or SW); n_sets parameter sets
+ * (elements) of that kind, one per system; per-atom types index masses_by_type.
+ * Each system's atom range starts on a 128-atom boundary (a gather block never mixes
+ * systems). */
+typedef struct {
+    double max_box;         /* largest box edge any system will have (A); 0 = 4096        */
+    int64_t cell_capacity;  /* cells shared by all systems' grids; 0 = 4 x atom_capacity   */
+} md_batch_options;
+
+typedef struct {
+    double box[3];          /* orthorhombic edges (A)                                   */
+    int pbc[3];             /* periodic axes                                            */
+    int64_t n_atoms;        /* >= 1                                                     */
+    const int32_t *types;   /* n_atoms element indices < n_types (host pointer)          */
+    int param_set;          /* index into the pool's parameter sets                     */
+    const double *x, *y, *z;      /* positions, SoA (host or device per options.io)     */
+    const double *vx, *vy, *vz;   /* velocities, or NULL for zero                        */
+    int64_t n_steps;        /* steps to run before stopping (< 0: until removed)         */
+    double damp;            /* damped-MD friction gamma (1/fs): v <- v (1 - gamma dt)
+                               after each step (0 = NVE)                                 */
+} md_system;
+
+md_status md_batch_create(md_ctx **out, int64_t atom_capacity, int max_systems, int n_sets,
+                          const md_params *param_sets, int n_types, const double *masses_by_type,
+                          const md_batch_options *bopt, const md_options *opt);
+
+/* Add a system (copies its arrays); *id receives its slot.  MD_ERR_OOM when the pool has
+ * no free slot, atom range or cell range (admission can retry after removals). */
+md_status md_batch_add(md_ctx *ctx, const md_system *sys, int *id);
+
+/* Remove a system and free its slot, atoms and cells. */
+md_status md_batch_remove(md_ctx *ctx, int id);
+
+/* Per slot (max_systems entries each, any pointer may be NULL): active (1 running, 0
+ * stopped, -1 empty slot), steps left, and totals (13 per slot: U, W(9), J(3) of the
+ * last step or force evaluation). */
+md_status md_batch_status(md_ctx *ctx, int *active, int64_t *steps_left, double *totals);
+
+/* Positions (wrapped) and velocities of one system, each 3 n_atoms SoA. */
+md_status md_batch_get_state(md_ctx *ctx, int id, double *x, double *v);
 
 /* Message of the last failing call (empty string if none).  Never NULL. */
 const char *md_last_error(const md_ctx *ctx);

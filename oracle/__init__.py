@@ -61,7 +61,7 @@ def _load():
         lib.oracle_sw_conventional.argtypes = [I64, P, P, P, P, P, P, P, P, P, P, P]
         lib.oracle_sw_dUdr.argtypes = [I64, P, P, P, P, P, P, I, P, P, P, P]
         lib.oracle_manybody_fwj.argtypes = [I64, P, P, P, P, P, I, P, P, P, P, P, P, P, P, P]
-        lib.oracle_run.argtypes = [I64, P, P, P, P, P, P, P, P, P, I, P, I, I64, D, P]
+        lib.oracle_run.argtypes = [I64, P, P, P, P, P, P, P, P, P, I, P, I, I64, D, D, P]
         for f in ("oracle_neighbors_brute", "oracle_neighbors_cells", "oracle_tersoff_conventional",
                   "oracle_tersoff_dUdr", "oracle_sw_conventional", "oracle_sw_dUdr",
                   "oracle_manybody_fwj", "oracle_run"):
@@ -205,8 +205,9 @@ def compute(pos, box, pbc, kind, params, vel=None, cap=32):
     return out
 
 
-def run(pos, vel, masses, box, pbc, kind, params, n_steps, dt, cap=32):
-    """Velocity Verlet for n_steps: returns (pos, vel, series[n_steps, 5] = U, K, Jx, Jy, Jz)."""
+def run(pos, vel, masses, box, pbc, kind, params, n_steps, dt, cap=32, damp=0.0):
+    """Velocity Verlet for n_steps (optionally damped, v *= 1 - damp dt after each step):
+    returns (pos, vel, series[n_steps, 5] = U, K, Jx, Jy, Jz)."""
     lib = _load()
     x, y, z = _soa(pos)
     vx, vy, vz = _soa(vel)
@@ -216,7 +217,7 @@ def run(pos, vel, masses, box, pbc, kind, params, n_steps, dt, cap=32):
     prm = np.ascontiguousarray(params, dtype=np.float64)
     series = np.zeros(5 * max(n_steps, 1))
     rc = lib.oracle_run(n, _p(x), _p(y), _p(z), _p(vx), _p(vy), _p(vz), _p(m), _p(b), _p(p),
-                        int(kind), _p(prm), int(cap), int(n_steps), float(dt), _p(series))
+                        int(kind), _p(prm), int(cap), int(n_steps), float(dt), float(damp), _p(series))
     if rc != 0:
         raise RuntimeError(f"oracle_run failed: {rc}")
     return (np.stack([x, y, z], axis=1), np.stack([vx, vy, vz], axis=1),

@@ -622,13 +622,14 @@ static void conventional_forces(int kind, int64_t N, const double *x, const doub
 /* Velocity Verlet (Sec. 3): per step
  *   v += F/m dt/2;  x += v dt (wrapped into [0, L) on periodic axes);
  *   neighbour list rebuilt from scratch at the potential cutoff; F(x) by Algorithm 1;
- *   v += F/m dt/2;  heat current J = sum_i J_i (Eq. 30) from x(t+dt), v(t+dt).
+ *   v += F/m dt/2;  [damped relaxation: v *= (1 - damp dt)];
+ *   heat current J = sum_i J_i (Eq. 30) from x(t+dt), v(t+dt).
  * series (n_steps x 5, or NULL) receives U, K, Jx, Jy, Jz after every step.
  * masses: per-atom masses (amu).  x, y, z, vx, vy, vz are updated in place.
  * Returns 0, -1 on allocation failure, -3 on neighbour overflow. */
 int oracle_run(int64_t N, double *x, double *y, double *z, double *vx, double *vy, double *vz,
                const double *masses, const double *box, const int *pbc, int kind,
-               const double *params, int cap, int64_t n_steps, double dt, double *series)
+               const double *params, int cap, int64_t n_steps, double dt, double damp, double *series)
 {
     double rc = pot_cutoff(kind, params);
     int *NN = (int *)malloc(sizeof(int) * (size_t)(N > 0 ? N : 1));
@@ -660,6 +661,10 @@ int oracle_run(int64_t N, double *x, double *y, double *z, double *vx, double *v
         for (int64_t i = 0; i < N; ++i) {
             double h = 0.5 * dt * ACC_UNIT / masses[i];
             vx[i] += h * F[i]; vy[i] += h * F[N + i]; vz[i] += h * F[2 * N + i];
+            if (damp > 0.0) {
+                double f = 1.0 - damp * dt;
+                vx[i] *= f; vy[i] *= f; vz[i] *= f;
+            }
             Ut += U[i];
             K += 0.5 * masses[i] * (vx[i] * vx[i] + vy[i] * vy[i] + vz[i] * vz[i]) / ACC_UNIT;
         }

@@ -58,49 +58,113 @@ __device__ __forceinline__ T ipow(T x, int n)
 }
 
 // Shared-memory staging of atom i's in-cutoff neighbours: field f of neighbour k of
-// thread t lives at s[(f MAXA + k) BLOCK + t] (consecutive threads, consecutive words).
-template <typename T, int MAXA, int BLOCK>
+// thread t lives at s[(f CAP + k) BLOCK + t] (consecutive threads, consecutive words).
+template <typename T, int CAP, int BLOCK>
 struct Stage {
     T *s;
     int t;
-    __device__ __forceinline__ T &operator()(int f, int k) const { return s[(f * MAXA + k) * BLOCK + t]; }
+    __device__ __forceinline__ T &operator()(int f, int k) const { return s[(f * CAP + k) * BLOCK + t]; }
 };
+
+// Potential constants in the pair pass's arithmetic type (no conversions in the loops).
+template <typename T>
+struct TersoffC {
+    T A, B, lam, mu, n, c2, d2, c2d2, h, R, pi_SR, ln_beta, inv2n;
+    T rc2;   // S^2
+    int beta_zero;
+};
+template <typename T>
+TersoffC<T> tersoff_const(const TersoffP &p)
+{
+    TersoffC<T> c;
+    c.A = T(p.A); c.B = T(p.B); c.lam = T(p.lam); c.mu = T(p.mu); c.n = T(p.n);
+    c.c2 = T(p.c2); c.d2 = T(p.d2); c.c2d2 = T(p.c2d2); c.h = T(p.h); c.R = T(p.R);
+    c.pi_SR = T(p.pi_SR); c.ln_beta = T(p.ln_beta); c.inv2n = T(p.inv2n);
+    c.rc2 = T(p.S * p.S);
+    c.beta_zero = p.beta_zero;
+    return c;
+}
+template <typename T>
+struct SWC {
+    T Aeps, B, p, q, sig, rc, gamsig, lameps;
+    T rc2;   // (a sigma)^2
+    int p_int, q_int;
+};
+template <typename T>
+SWC<T> sw_const(const SWP &p)
+{
+    SWC<T> c;
+    c.Aeps = T(p.Aeps); c.B = T(p.B); c.p = T(p.p); c.q = T(p.q); c.sig = T(p.sig);
+    c.rc = T(p.rc); c.gamsig = T(p.gamsig); c.lameps = T(p.lameps);
+    c.rc2 = T(p.rc * p.rc);
+    c.p_int = p.p_int; c.q_int = p.q_int;
+    return c;
+}
 
 // ------------------------------------------------------- neighbour staging
 // For each list slot, the fp64 bond r_ij (image shift from the entry); keeps the slots
 // with |r_ij|^2 < rc^2, writes their bond vectors (compact row k) to global memory and
-// stages (x, y, z, r^2) in the shared fields fx, fy, fz, fr2.  Returns the count and the
-// active-slot mask.  The cutoff decision is symmetric in i and j: the two fp64
-// differences are exact negatives of each other, and so are their conversions.
-template <typename T, int MAXA, int BLOCK>
-__device__ __forceinline__ int collect_bonds(const PairArgs<T> &a, int64_t i, uint32_t &mask,
-                                             const Stage<T, MAXA, BLOCK> &S, int fx, int fy, int fz,
-                                             int fr2)
+// stages (x, y, z, r^2) in the shared fields fx, fy, fz, fr2.  Slots are fetched four at a
+// time so that their index and position loads are in flight together.  Returns the
+// in-cutoff count (and mask), or -1 when the count exceeds CAP in the small-capacity
+// pass: the atom is then appended to the deferred list and left to the full pass.
+// The cutoff decision is symmetric in i and j: the two fp64 differences are exact
+// negatives of each other, and so are their conversions.
+template <typename T, int CAP, int BLOCK, bool FULL_CAP>
+__device__ __forceinline__ int collect_bonds(const PairArgs<T> &a, int64_t i, const Box &box, T rc2,
+                                             uint32_t &mask, const Stage<T, CAP, BLOCK> &S, int fx, int fy,
+                                             int fz, int fr2)
 {
     const int64_t N = a.N;
+    const int S_ = a.stride;
     const double xi = a.pos[i], yi = a.pos[N + i], zi = a.pos[2 * N + i];
     const int nn = a.nn[i];
     int na = 0;
     mask = 0u;
-    for (int m = 0; m < nn; ++m) {
-        double dx, dy, dz;
-        bond_vector(a.pos, N, i, a.nl[(int64_t)m * N + i], a.box, xi, yi, zi, dx, dy, dz);
-        const T tx = T(dx), ty = T(dy), tz = T(dz);
-        const T r2 = tx * tx + ty * ty + tz * tz;
-        if (r2 < a.rc2) {
-            if (na < MAXA) {
-                S(fx, na) = tx; S(fy, na) = ty; S(fz, na) = tz; S(fr2, na) = r2;
-                a.r[(0 * MAXA + na) * N + i] = tx;
-                a.r[(1 * MAXA + na) * N + i] = ty;
-                a.r[(2 * MAXA + na) * N + i] = tz;
+    for (int m0 = 0; m0 < nn; m0 += 4) {
+        int e[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) e[q] = (m0 + q < nn) ? a.nl[(int64_t)(m0 + q) * N + i] : 0;
+        double px[4], py[4], pz[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int j = list_atom(e[q]);
+            px[q] = a.pos[j];
+            py[q] = a.pos[N + j];
+            pz[q] = a.pos[2 * N + j];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (m0 + q >= nn) break;
+            double dx = px[q] - xi, dy = py[q] - yi, dz = pz[q] - zi;
+            const int code = list_code(e[q]);
+            if (code != kNoShift) {
+                const int sx = code % 3 - 1, sy = (code / 3) % 3 - 1, sz = code / 9 - 1;
+                if (sx) dx += sx > 0 ? box.L[0] : -box.L[0];
+                if (sy) dy += sy > 0 ? box.L[1] : -box.L[1];
+                if (sz) dz += sz > 0 ? box.L[2] : -box.L[2];
             }
-            mask |= 1u << m;
-            ++na;
+            const T tx = T(dx), ty = T(dy), tz = T(dz);
+            const T r2 = tx * tx + ty * ty + tz * tz;
+            if (r2 < rc2) {
+                if (na < CAP) {
+                    S(fx, na) = tx; S(fy, na) = ty; S(fz, na) = tz; S(fr2, na) = r2;
+                    a.r[(int64_t)(0 * S_ + na) * N + i] = tx;
+                    a.r[(int64_t)(1 * S_ + na) * N + i] = ty;
+                    a.r[(int64_t)(2 * S_ + na) * N + i] = tz;
+                }
+                mask |= 1u << (m0 + q);
+                ++na;
+            }
         }
     }
-    if (na > MAXA) {
+    if (na > CAP) {
+        if (!FULL_CAP) {
+            a.ovf_list[atomicAdd(a.ovf_count, 1)] = (int)i;
+            return -1;
+        }
         a.flags->active_overflow = 1;
-        na = MAXA;
+        na = CAP;
     }
     return na;
 }
@@ -111,56 +175,56 @@ enum { TF_UX, TF_UY, TF_UZ, TF_IR, TF_FC, TF_DFC, TF_FR, TF_FA, TF_Z, TF_DX, TF_
 // g(cos) of Eq. 5 written as 1 + (c^2/d^2) (h-cos)^2 / (d^2 + (h-cos)^2): the same
 // function as printed, without the cancellation of c^2/d^2 - c^2/(d^2+(h-cos)^2)
 // (about 4e7 - 4e7 for silicon), so that it stays accurate in fp32.  inv = 1/den is
-// returned so the derivative loop can reuse it; dg = dg/dcos.
+// kept so the derivative loop can reuse it; dg = dg/dcos.
 template <typename T>
-__device__ __forceinline__ T tersoff_inv_den(const TersoffP &p, T cs)
+__device__ __forceinline__ T tersoff_inv_den(const TersoffC<T> &p, T cs)
 {
-    const T hc = T(p.h) - cs;
-    return T(1) / (T(p.d2) + hc * hc);
+    const T hc = p.h - cs;
+    return T(1) / (p.d2 + hc * hc);
 }
 template <typename T>
-__device__ __forceinline__ void tersoff_g(const TersoffP &p, T cs, T inv, T &g, T &dg)
+__device__ __forceinline__ void tersoff_g(const TersoffC<T> &p, T cs, T inv, T &g, T &dg)
 {
-    const T hc = T(p.h) - cs;
-    g = T(1) + T(p.c2d2) * hc * hc * inv;
-    dg = T(-2) * T(p.c2) * hc * inv * inv;
+    const T hc = p.h - cs;
+    g = T(1) + p.c2d2 * hc * hc * inv;
+    dg = T(-2) * p.c2 * hc * inv * inv;
 }
 
 // b = (1 + (beta zeta)^n)^(-1/(2n)) (Eq. 3) and db/dzeta = -1/2 b x / (zeta (1 + x)),
 // x = (beta zeta)^n.  b = 1, db = 0 at zeta = 0 (every dzeta/dr it multiplies is 0).
 template <typename T>
-__device__ __forceinline__ void tersoff_b(const TersoffP &p, T zeta, T &b, T &db)
+__device__ __forceinline__ void tersoff_b(const TersoffC<T> &p, T zeta, T &b, T &db)
 {
     if (!(zeta > T(0)) || p.beta_zero) {
         b = T(1);
         db = T(0);
         return;
     }
-    const T x = M<T>::exp_(T(p.n) * (M<T>::log_(zeta) + T(p.ln_beta)));
-    b = M<T>::exp_(-T(p.inv2n) * M<T>::log1p_(x));
+    const T x = M<T>::exp_(p.n * (M<T>::log_(zeta) + p.ln_beta));
+    b = M<T>::exp_(-p.inv2n * M<T>::log1p_(x));
     db = T(-0.5) * b * x / (zeta * (T(1) + x));
 }
 
 // index of the unordered bond pair (j, k), j < k
 __device__ __forceinline__ int tri(int j, int k) { return k * (k - 1) / 2 + j; }
 
-template <typename T, int MAXA>
-constexpr int tersoff_smem_fields() { return TF_NF * MAXA + MAXA * (MAXA - 1) / 2; }
+template <int CAP>
+constexpr int tersoff_smem_fields() { return TF_NF * CAP + CAP * (CAP - 1) / 2; }
 
-template <typename T, int MAXA, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_pair_tersoff(PairArgs<T> a, TersoffP p)
+// Pair pass for one atom (Tersoff).
+template <typename T, int CAP, int BLOCK, bool FULL_CAP>
+__device__ __forceinline__ void tersoff_atom(const PairArgs<T> &a, const TersoffC<T> &p, const Box &box, T *base,
+                                             int64_t i)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
-    if (i >= a.N) return;
     const int64_t N = a.N;
-    T *base = reinterpret_cast<T *>(smem);
-    Stage<T, MAXA, BLOCK> S{base, (int)threadIdx.x};
-    T *sinv = base + TF_NF * MAXA * BLOCK;   // per bond pair: 1/(d^2 + (h - cos)^2)
+    const int S_ = a.stride;
+    Stage<T, CAP, BLOCK> S{base, (int)threadIdx.x};
+    T *sinv = base + TF_NF * CAP * BLOCK;   // per bond pair: 1/(d^2 + (h - cos)^2)
     auto INV = [&](int q) -> T & { return sinv[q * BLOCK + threadIdx.x]; };
 
     uint32_t mask;
-    const int na = collect_bonds<T, MAXA, BLOCK>(a, i, mask, S, TF_UX, TF_UY, TF_UZ, TF_IR);
+    const int na = collect_bonds<T, CAP, BLOCK, FULL_CAP>(a, i, box, p.rc2, mask, S, TF_UX, TF_UY, TF_UZ, TF_IR);
+    if (na < 0) return;   // deferred to the full-capacity pass
 
     // per-bond radial functions (the staged vectors become unit vectors, r^2 -> 1/r)
     for (int k = 0; k < na; ++k) {
@@ -172,16 +236,16 @@ __global__ void __launch_bounds__(BLOCK) k_pair_tersoff(PairArgs<T> a, TersoffP 
         S(TF_UZ, k) *= ir;
         S(TF_IR, k) = ir;
         T fc = T(1), dfc = T(0);
-        if (r >= T(p.R)) {
+        if (r >= p.R) {
             T sn, cn;
-            M<T>::sincos_(T(p.pi_SR) * (r - T(p.R)), &sn, &cn);
+            M<T>::sincos_(p.pi_SR * (r - p.R), &sn, &cn);
             fc = T(0.5) + T(0.5) * cn;
-            dfc = T(-0.5) * T(p.pi_SR) * sn;
+            dfc = T(-0.5) * p.pi_SR * sn;
         }
         S(TF_FC, k) = fc;
         S(TF_DFC, k) = dfc;
-        S(TF_FR, k) = T(p.A) * M<T>::exp_(-T(p.lam) * r);
-        S(TF_FA, k) = T(p.B) * M<T>::exp_(-T(p.mu) * r);
+        S(TF_FR, k) = p.A * M<T>::exp_(-p.lam * r);
+        S(TF_FA, k) = p.B * M<T>::exp_(-p.mu * r);
         S(TF_Z, k) = T(0);
     }
     // zeta_ij = sum_{k != j} f_C(r_ik) g(theta_ijk), each unordered pair once
@@ -206,8 +270,8 @@ __global__ void __launch_bounds__(BLOCK) k_pair_tersoff(PairArgs<T> a, TersoffP 
         tersoff_b(p, S(TF_Z, k), b, db);
         const T fc = S(TF_FC, k), dfc = S(TF_DFC, k), fr = S(TF_FR, k), fa = S(TF_FA, k);
         ui += T(0.5) * fc * (fr - b * fa);
-        const T dR = dfc * fr - T(p.lam) * fc * fr;   // (f_C f_R)'
-        const T dA = dfc * fa - T(p.mu) * fc * fa;    // (f_C f_A)'
+        const T dR = dfc * fr - p.lam * fc * fr;   // (f_C f_R)'
+        const T dA = dfc * fa - p.mu * fc * fa;    // (f_C f_A)'
         const T radial = T(0.5) * (dR - b * dA);
         S(TF_DX, k) = radial * S(TF_UX, k);
         S(TF_DY, k) = radial * S(TF_UY, k);
@@ -236,9 +300,9 @@ __global__ void __launch_bounds__(BLOCK) k_pair_tersoff(PairArgs<T> a, TersoffP 
             S(TF_DY, k) += qk * (ujy - cs * uky) + ck * uky;
             S(TF_DZ, k) += qk * (ujz - cs * ukz) + ck * ukz;
         }
-        a.d[(0 * MAXA + j) * N + i] = djx;
-        a.d[(1 * MAXA + j) * N + i] = djy;
-        a.d[(2 * MAXA + j) * N + i] = djz;
+        a.d[(int64_t)(0 * S_ + j) * N + i] = djx;
+        a.d[(int64_t)(1 * S_ + j) * N + i] = djy;
+        a.d[(int64_t)(2 * S_ + j) * N + i] = djz;
     }
     a.mask[i] = mask;
     a.u[i] = double(ui);
@@ -247,39 +311,41 @@ __global__ void __launch_bounds__(BLOCK) k_pair_tersoff(PairArgs<T> a, TersoffP 
 // ---------------------------------------------------------- Stillinger-Weber
 enum { SW_UX, SW_UY, SW_UZ, SW_IR, SW_E, SW_DE, SW_DX, SW_DY, SW_DZ, SW_NF };
 
-template <typename T, int MAXA, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_pair_sw(PairArgs<T> a, SWP p)
+template <int CAP>
+constexpr int sw_smem_fields() { return SW_NF * CAP; }
+
+// Pair pass for one atom (SW): two-body and vertex three-body terms.
+template <typename T, int CAP, int BLOCK, bool FULL_CAP>
+__device__ __forceinline__ void sw_atom(const PairArgs<T> &a, const SWC<T> &p, const Box &box, T *base, int64_t i)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
-    if (i >= a.N) return;
     const int64_t N = a.N;
-    Stage<T, MAXA, BLOCK> S{reinterpret_cast<T *>(smem), (int)threadIdx.x};
+    const int S_ = a.stride;
+    Stage<T, CAP, BLOCK> S{base, (int)threadIdx.x};
     uint32_t mask;
-    const int na = collect_bonds<T, MAXA, BLOCK>(a, i, mask, S, SW_UX, SW_UY, SW_UZ, SW_IR);
+    const int na = collect_bonds<T, CAP, BLOCK, FULL_CAP>(a, i, box, p.rc2, mask, S, SW_UX, SW_UY, SW_UZ, SW_IR);
+    if (na < 0) return;
 
     T ui = T(0);
-    const T rc = T(p.rc), sig = T(p.sig);
     for (int k = 0; k < na; ++k) {
         const T r2 = S(SW_IR, k);
         const T ir = M<T>::rsqrt_(r2);
         const T r = r2 * ir;
         const T ux = S(SW_UX, k) * ir, uy = S(SW_UY, k) * ir, uz = S(SW_UZ, k) * ir;
         S(SW_UX, k) = ux; S(SW_UY, k) = uy; S(SW_UZ, k) = uz; S(SW_IR, k) = ir;
-        const T irc = T(1) / (r - rc);                 // 1/(r - a sigma) < 0
-        const T e2 = M<T>::exp_(sig * irc);
-        const T E = M<T>::exp_(T(p.gamsig) * irc);
+        const T irc = T(1) / (r - p.rc);                 // 1/(r - a sigma) < 0
+        const T e2 = M<T>::exp_(p.sig * irc);
+        const T E = M<T>::exp_(p.gamsig * irc);
         S(SW_E, k) = E;
-        S(SW_DE, k) = -T(p.gamsig) * irc * irc * E;
+        S(SW_DE, k) = -p.gamsig * irc * irc * E;
         // phi2 = A eps [B (sigma/r)^p - (sigma/r)^q] exp(sigma/(r - a sigma))
-        const T sr = sig * ir;
+        const T sr = p.sig * ir;
         T sp, sq;
-        if (p.p_int >= 0) sp = ipow(sr, p.p_int); else sp = M<T>::pow_(sr, T(p.p));
-        if (p.q_int >= 0) sq = ipow(sr, p.q_int); else sq = M<T>::pow_(sr, T(p.q));
-        const T poly = T(p.B) * sp - sq;
-        const T dpoly = (-T(p.p) * T(p.B) * sp + T(p.q) * sq) * ir;
-        ui += T(0.5) * T(p.Aeps) * poly * e2;
-        const T dphi = T(p.Aeps) * (dpoly * e2 - poly * sig * irc * irc * e2);
+        if (p.p_int >= 0) sp = ipow(sr, p.p_int); else sp = M<T>::pow_(sr, p.p);
+        if (p.q_int >= 0) sq = ipow(sr, p.q_int); else sq = M<T>::pow_(sr, p.q);
+        const T poly = p.B * sp - sq;
+        const T dpoly = (-p.p * p.B * sp + p.q * sq) * ir;
+        ui += T(0.5) * p.Aeps * poly * e2;
+        const T dphi = p.Aeps * (dpoly * e2 - poly * p.sig * irc * irc * e2);
         S(SW_DX, k) = T(0.5) * dphi * ux;
         S(SW_DY, k) = T(0.5) * dphi * uy;
         S(SW_DZ, k) = T(0.5) * dphi * uz;
@@ -295,9 +361,9 @@ __global__ void __launch_bounds__(BLOCK) k_pair_sw(PairArgs<T> a, SWP p)
             const T cs = ujx * ukx + ujy * uky + ujz * ukz;
             const T t = cs + T(1.0 / 3.0);
             const T EE = Ej * Ek;
-            ui += T(p.lameps) * t * t * EE;
-            const T c1 = T(2) * T(p.lameps) * t * EE;
-            const T cj = T(p.lameps) * t * t * dEj * Ek, ck = T(p.lameps) * t * t * Ej * dEk;
+            ui += p.lameps * t * t * EE;
+            const T c1 = T(2) * p.lameps * t * EE;
+            const T cj = p.lameps * t * t * dEj * Ek, ck = p.lameps * t * t * Ej * dEk;
             const T qj = c1 * irj, qk = c1 * irk;
             djx += qj * (ukx - cs * ujx) + cj * ujx;
             djy += qj * (uky - cs * ujy) + cj * ujy;
@@ -306,42 +372,109 @@ __global__ void __launch_bounds__(BLOCK) k_pair_sw(PairArgs<T> a, SWP p)
             S(SW_DY, k) += qk * (ujy - cs * uky) + ck * uky;
             S(SW_DZ, k) += qk * (ujz - cs * ukz) + ck * ukz;
         }
-        a.d[(0 * MAXA + j) * N + i] = djx;
-        a.d[(1 * MAXA + j) * N + i] = djy;
-        a.d[(2 * MAXA + j) * N + i] = djz;
+        a.d[(int64_t)(0 * S_ + j) * N + i] = djx;
+        a.d[(int64_t)(1 * S_ + j) * N + i] = djy;
+        a.d[(int64_t)(2 * S_ + j) * N + i] = djz;
     }
     a.mask[i] = mask;
     a.u[i] = double(ui);
 }
 
+template <typename T>
+struct TersoffSets {
+    TersoffC<T> s[kMaxSets];
+};
+template <typename T>
+struct SWSets {
+    SWC<T> s[kMaxSets];
+};
+
+// Kernels: the small-capacity pass (one thread per atom, CAP = 4) and the full-capacity
+// pass over the deferred atoms (grid-stride over the deferred list).  Pools (BATCH):
+// each atom uses its system's box and parameter set; atoms of stopped systems are
+// skipped.
+template <typename T, int CAP, int BLOCK, bool FULL_CAP, bool BATCH, typename Sets, typename Fn>
+__device__ __forceinline__ void pair_dispatch(const PairArgs<T> &a, const Sets &ps, T *base, Fn fn)
+{
+    auto one = [&](int64_t i) {
+        if (BATCH) {
+            const SysDev &sd = a.sys[a.sys_of[i]];
+            if (!sd.active) return;
+            fn(ps.s[sd.pset], sd.box, i);
+        } else {
+            fn(ps.s[0], a.box, i);
+        }
+    };
+    if (!FULL_CAP) {
+        const int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
+        if (i < a.N) one(i);
+    } else {
+        const int cnt = *a.ovf_count;
+        for (int64_t q = (int64_t)blockIdx.x * BLOCK + threadIdx.x; q < cnt; q += (int64_t)gridDim.x * BLOCK)
+            one(a.ovf_list[q]);
+    }
+}
+
+template <typename T, int CAP, int BLOCK, bool FULL_CAP, bool BATCH>
+__global__ void __launch_bounds__(BLOCK) k_pair_tersoff(PairArgs<T> a, TersoffSets<T> ps)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    T *base = reinterpret_cast<T *>(smem);
+    pair_dispatch<T, CAP, BLOCK, FULL_CAP, BATCH>(a, ps, base, [&](const TersoffC<T> &p, const Box &box, int64_t i) {
+        tersoff_atom<T, CAP, BLOCK, FULL_CAP>(a, p, box, base, i);
+    });
+}
+
+template <typename T, int CAP, int BLOCK, bool FULL_CAP, bool BATCH>
+__global__ void __launch_bounds__(BLOCK) k_pair_sw(PairArgs<T> a, SWSets<T> ps)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    T *base = reinterpret_cast<T *>(smem);
+    pair_dispatch<T, CAP, BLOCK, FULL_CAP, BATCH>(a, ps, base, [&](const SWC<T> &p, const Box &box, int64_t i) {
+        sw_atom<T, CAP, BLOCK, FULL_CAP>(a, p, box, base, i);
+    });
+}
+
+__global__ void k_pair_reset(int *ovf_count) { *ovf_count = 0; }
+
 // ------------------------------------------------------------------ gather
-// Block sums of NC per-thread fp64 values, in a fixed order: transpose through shared
-// memory, then 8 threads per component add 16 values each and combine by shuffles.
+// Block sums of NC per-thread fp64 values per system segment, in a fixed order:
+// transpose through shared memory, then 8 threads per component add 16 values each and
+// combine by shuffles.  A block of a pool can hold atoms of several systems (segment =
+// system - system of the block's first atom); a single system has one segment.
 template <int BLOCK, int NC>
-__device__ __forceinline__ void block_partials(const double (&vals)[NC], double *out, int nb)
+__device__ __forceinline__ void block_partials(const double (&vals)[NC], int seg, int nseg, int seg_max,
+                                               double *out)
 {
     static_assert(BLOCK == 128, "block_partials assumes 128 threads");
     __shared__ double red[NC][BLOCK];
+    __shared__ int sseg[BLOCK];
 #pragma unroll
     for (int c = 0; c < NC; ++c) red[c][threadIdx.x] = vals[c];
+    sseg[threadIdx.x] = seg;
     __syncthreads();
     const int t = threadIdx.x;
     if (t < NC * 8) {
         const int c = t >> 3, sub = t & 7;
-        double s = 0.0;
-#pragma unroll
-        for (int q = 0; q < BLOCK / 8; ++q) s += red[c][sub + 8 * q];
         const unsigned grp = 0xffu << (t & 24);
-        s += __shfl_xor_sync(grp, s, 4, 8);
-        s += __shfl_xor_sync(grp, s, 2, 8);
-        s += __shfl_xor_sync(grp, s, 1, 8);
-        if (sub == 0) out[(int64_t)c * nb + blockIdx.x] = s;
+        for (int g = 0; g < nseg; ++g) {
+            double s = 0.0;
+#pragma unroll
+            for (int q = 0; q < BLOCK / 8; ++q) {
+                const int k = sub + 8 * q;
+                if (nseg == 1 || sseg[k] == g) s += red[c][k];
+            }
+            s += __shfl_xor_sync(grp, s, 4, 8);
+            s += __shfl_xor_sync(grp, s, 2, 8);
+            s += __shfl_xor_sync(grp, s, 1, 8);
+            if (sub == 0) out[((int64_t)blockIdx.x * seg_max + g) * NC + c] = s;
+        }
     }
 }
 
 // FULL: a force evaluation (per-atom F, W, J stored; U, K, J, W partials) or a
 // velocity-Verlet step (F and the kick only; U, K, J partials).
-template <typename T, int MAXA, int BLOCK, bool FULL>
+template <typename T, int MAXA, int BLOCK, bool FULL, bool BATCH>
 __global__ void __launch_bounds__(BLOCK) k_gather(GatherArgs<T> a)
 {
     constexpr int NC = FULL ? kNumPartials : kStepPartials;
@@ -350,7 +483,17 @@ __global__ void __launch_bounds__(BLOCK) k_gather(GatherArgs<T> a)
     double vals[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) vals[c] = 0.0;
-    if (i < N) {
+    // Pools place every system on a block boundary, so a block holds one system plus
+    // inactive padding atoms (which contribute zeros): one segment per block.
+    const int seg = 0, nseg = 1;
+    bool live = i < N;
+    double damp = 0.0;
+    if (BATCH && live) {
+        const SysDev &sd = a.sys[a.sys_of[i]];
+        live = sd.active != 0;
+        damp = sd.damp;
+    }
+    if (live) {
         uint32_t mask = a.mask[i];
         T f0 = 0, f1 = 0, f2 = 0;
         T w[9], mj[9];
@@ -365,12 +508,12 @@ __global__ void __launch_bounds__(BLOCK) k_gather(GatherArgs<T> a)
             const uint32_t maskj = a.mask[j];
             const int kr = __popc(maskj & ((1u << mr) - 1u));
             if (kr < MAXA) {
-                const T dx = a.d[(0 * MAXA + k) * N + i], dy = a.d[(1 * MAXA + k) * N + i],
-                        dz = a.d[(2 * MAXA + k) * N + i];
-                const T ex = a.d[(0 * MAXA + kr) * N + j], ey = a.d[(1 * MAXA + kr) * N + j],
-                        ez = a.d[(2 * MAXA + kr) * N + j];
-                const T rx = a.r[(0 * MAXA + k) * N + i], ry = a.r[(1 * MAXA + k) * N + i],
-                        rz = a.r[(2 * MAXA + k) * N + i];
+                const T dx = a.d[(int64_t)(0 * MAXA + k) * N + i], dy = a.d[(int64_t)(1 * MAXA + k) * N + i],
+                        dz = a.d[(int64_t)(2 * MAXA + k) * N + i];
+                const T ex = a.d[(int64_t)(0 * MAXA + kr) * N + j], ey = a.d[(int64_t)(1 * MAXA + kr) * N + j],
+                        ez = a.d[(int64_t)(2 * MAXA + kr) * N + j];
+                const T rx = a.r[(int64_t)(0 * MAXA + k) * N + i], ry = a.r[(int64_t)(1 * MAXA + k) * N + i],
+                        rz = a.r[(int64_t)(2 * MAXA + k) * N + i];
                 const T gx = dx - ex, gy = dy - ey, gz = dz - ez;   // F_ij = d_ij - d_ji
                 f0 += gx; f1 += gy; f2 += gz;
                 if (FULL) {
@@ -384,8 +527,8 @@ __global__ void __launch_bounds__(BLOCK) k_gather(GatherArgs<T> a)
             }
             ++k;
         }
+        if (!(isfinite(f0) && isfinite(f1) && isfinite(f2))) a.flags->nonfinite = 1;
         const double F[3] = {double(f0), double(f1), double(f2)};
-        if (!(isfinite(F[0]) && isfinite(F[1]) && isfinite(F[2]))) a.flags->nonfinite = 1;
         a.force[i] = F[0];
         a.force[N + i] = F[1];
         a.force[2 * N + i] = F[2];
@@ -396,6 +539,10 @@ __global__ void __launch_bounds__(BLOCK) k_gather(GatherArgs<T> a)
             v[0] = fma(h, F[0], v[0]);
             v[1] = fma(h, F[1], v[1]);
             v[2] = fma(h, F[2], v[2]);
+            if (BATCH && damp > 0.0) {   // damped-MD relaxation: v <- v (1 - gamma dt)
+                const double f = 1.0 - damp * a.dt;
+                v[0] *= f; v[1] *= f; v[2] *= f;
+            }
             a.vel[i] = v[0];
             a.vel[N + i] = v[1];
             a.vel[2 * N + i] = v[2];
@@ -426,34 +573,57 @@ __global__ void __launch_bounds__(BLOCK) k_gather(GatherArgs<T> a)
             }
         }
     }
-    block_partials<BLOCK, NC>(vals, a.partials, gridDim.x);
+    block_partials<BLOCK, NC>(vals, seg, nseg, a.seg_max, a.partials);
 }
 
-// One block per component: that component's block partials added in a fixed order.
-constexpr int kReduceThreads = 256;
+// One block per (system, component): that system's block partials of that component
+// added in a fixed order; totals[s NC_ALL + c] and, when recording,
+// series[(row n_sys + s) 5 + c].  Pools: a system that ran this step counts down its
+// step budget (component-0 block) and stops at zero.
+constexpr int kReduceThreads = 512;
+template <bool BATCH>
 __global__ void __launch_bounds__(kReduceThreads)
-k_reduce(const double *partials, int nb, double *totals, double *series, Flags *flags, bool record)
+k_reduce(const double *partials, int nc, int seg_max, int64_t N, int block, const int *sys_of, SysDev *sys,
+         int n_sys, double *totals, double *series, Flags *flags, bool record)
 {
     __shared__ double red[kReduceThreads / 32];
-    const int c = blockIdx.x;
+    const int s = blockIdx.x, c = blockIdx.y;
+    int64_t a0 = 0, na = N;
+    bool ran = true;
+    if (BATCH) {
+        a0 = sys[s].atom_start;
+        na = sys[s].n_atoms;
+        ran = sys[s].active != 0 && na > 0;
+        if (!ran) return;
+    }
+    const int64_t b0 = na > 0 ? a0 / block : 0, b1 = na > 0 ? (a0 + na - 1) / block : -1;
     double acc = 0.0;
-    for (int b = threadIdx.x; b < nb; b += kReduceThreads) acc += partials[(int64_t)c * nb + b];
+    for (int64_t b = b0 + threadIdx.x; b <= b1; b += kReduceThreads) {
+        const int seg = BATCH ? s - sys_of[b * block] : 0;
+        acc += partials[(b * seg_max + seg) * nc + c];
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) red[wid] = acc;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int w = 0; w < kReduceThreads / 32; ++w) s += red[w];
-        totals[c] = s;
-        if (record && c < kStepPartials) series[flags->row * kStepPartials + c] = s;
+        double t = 0.0;
+        for (int w = 0; w < kReduceThreads / 32; ++w) t += red[w];
+        totals[(int64_t)s * kNumPartials + c] = t;
+        if (record && c < kStepPartials) series[(flags->row * n_sys + s) * kStepPartials + c] = t;
+        if (BATCH && record && c == 0 && sys[s].steps_left > 0) {
+            sys[s].steps_left -= 1;
+            if (sys[s].steps_left == 0) sys[s].active = 0;
+        }
     }
 }
 
 // ------------------------------------------------------------------ integrator
 struct KickDriftArgs {
     int64_t N;
+    const int *sys_of;
+    SysDev *sys;
     double *pos, *vel;
     const double *force, *pos_build;
     const int *type;
@@ -465,10 +635,12 @@ struct KickDriftArgs {
 
 // v += F/m dt/2; x += v dt (no wrap: positions are wrapped when the list is rebuilt);
 // request a rebuild when an atom has moved more than skin/2 since the last build.
+template <bool BATCH>
 __global__ void k_kick_drift(KickDriftArgs a)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.N) return;
+    if (BATCH && !a.sys[a.sys_of[i]].active) return;
     const int64_t N = a.N;
     const double h = a.hk[a.type[i]];
     float d2 = 0.f;
@@ -481,11 +653,16 @@ __global__ void k_kick_drift(KickDriftArgs a)
         const float d = (float)(x - a.pos_build[c * N + i]);
         d2 = fmaf(d, d, d2);
     }
-    if (!(d2 <= a.half_skin2)) a.flags->rebuild = 1;
+    const float hs2 = BATCH ? a.sys[a.sys_of[i]].half_skin2 : a.half_skin2;
+    if (!(d2 <= hs2)) {
+        a.flags->rebuild = 1;
+        if (BATCH) a.sys[a.sys_of[i]].rebuild = 1;
+    }
 }
 
-__global__ void k_step_begin(Flags *flags, cudaGraphConditionalHandle h, int has_cond)
+__global__ void k_step_begin(Flags *flags, int *ovf_count, cudaGraphConditionalHandle h, int has_cond)
 {
+    *ovf_count = 0;
     flags->row = flags->step;
     flags->step += 1;
     if (has_cond) cudaGraphSetConditional(h, flags->rebuild != 0 ? 1u : 0u);
@@ -495,30 +672,39 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 
 constexpr int kPairBlockF64 = 64;
 constexpr int kPairBlockF32 = 128;
+constexpr int kPairCapSmall = 4;     // bonds staged per atom in the common-case pass
+constexpr int kPairBlockFull = 32;   // full-capacity pass over the deferred atoms
 constexpr int kGatherBlock = 128;
 
 template <typename T> constexpr int pair_block();
 template <> constexpr int pair_block<double>() { return kPairBlockF64; }
 template <> constexpr int pair_block<float>() { return kPairBlockF32; }
 
-template <typename T, int MAXA>
+template <typename T, int CAP, int BLOCK>
 size_t smem_for(int kind)
 {
-    const int nf = kind == 1 ? tersoff_smem_fields<T, MAXA>() : SW_NF * MAXA;
-    return (size_t)nf * pair_block<T>() * sizeof(T);
+    const int nf = kind == 1 ? tersoff_smem_fields<CAP>() : sw_smem_fields<CAP>();
+    return (size_t)nf * BLOCK * sizeof(T);
 }
 
-template <typename T, int MAXA>
-void configure_one()
+template <typename T, int CAP, int BLOCK, bool FULL_CAP, bool BATCH>
+void set_smem()
 {
-    constexpr int B = pair_block<T>();
-    cudaFuncSetAttribute(k_pair_tersoff<T, MAXA, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem_for<T, MAXA>(1));
-    cudaFuncSetAttribute(k_pair_sw<T, MAXA, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem_for<T, MAXA>(2));
+    cudaFuncSetAttribute(k_pair_tersoff<T, CAP, BLOCK, FULL_CAP, BATCH>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_for<T, CAP, BLOCK>(1));
+    cudaFuncSetAttribute(k_pair_sw<T, CAP, BLOCK, FULL_CAP, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem_for<T, CAP, BLOCK>(2));
 }
 
-template <typename T, int MAXA>
+template <typename T, bool BATCH>
+void configure_type()
+{
+    set_smem<T, kPairCapSmall, pair_block<T>(), false, BATCH>();
+    set_smem<T, 8, kPairBlockFull, true, BATCH>();
+    set_smem<T, 16, kPairBlockFull, true, BATCH>();
+}
+
+template <typename T, int FULL, bool BATCH>
 void pair_launch(const Plan &p, cudaStream_t s)
 {
     constexpr int B = pair_block<T>();
@@ -530,20 +716,36 @@ void pair_launch(const Plan &p, cudaStream_t s)
     a.nl = p.nl;
     a.cap = p.cap;
     a.rc2 = T(p.rc * p.rc);
-    for (int c = 0; c < 3; ++c) a.shift[c] = p.box.L[c];
+    a.stride = p.maxa;
     a.d = static_cast<T *>(p.pd);
     a.r = static_cast<T *>(p.pr);
+    a.sys_of = p.sys_of;
+    a.sys = p.sys;
+    a.ovf_count = p.ovf_count;
+    a.ovf_list = p.ovf_list;
     a.mask = p.mask;
     a.u = p.u;
     a.flags = p.flags;
-    if (p.kind == 1)
-        k_pair_tersoff<T, MAXA, B><<<blocks_for(p.N, B), B, smem_for<T, MAXA>(1), s>>>(a, p.tp);
-    else
-        k_pair_sw<T, MAXA, B><<<blocks_for(p.N, B), B, smem_for<T, MAXA>(2), s>>>(a, p.sp);
+    const unsigned nb = blocks_for(p.N, B);
+    int64_t nbf = (p.N + kPairBlockFull - 1) / kPairBlockFull;
+    if (nbf > 4 * 152) nbf = 4 * 152;
+    if (p.kind == 1) {
+        TersoffSets<T> c;
+        for (int k = 0; k < kMaxSets; ++k) c.s[k] = tersoff_const<T>(p.tp[k < p.n_sets ? k : 0]);
+        k_pair_tersoff<T, kPairCapSmall, B, false, BATCH><<<nb, B, smem_for<T, kPairCapSmall, B>(1), s>>>(a, c);
+        k_pair_tersoff<T, FULL, kPairBlockFull, true, BATCH>
+            <<<(unsigned)nbf, kPairBlockFull, smem_for<T, FULL, kPairBlockFull>(1), s>>>(a, c);
+    } else {
+        SWSets<T> c;
+        for (int k = 0; k < kMaxSets; ++k) c.s[k] = sw_const<T>(p.sp[k < p.n_sets ? k : 0]);
+        k_pair_sw<T, kPairCapSmall, B, false, BATCH><<<nb, B, smem_for<T, kPairCapSmall, B>(2), s>>>(a, c);
+        k_pair_sw<T, FULL, kPairBlockFull, true, BATCH>
+            <<<(unsigned)nbf, kPairBlockFull, smem_for<T, FULL, kPairBlockFull>(2), s>>>(a, c);
+    }
 }
 
-template <typename T, int MAXA>
-void gather_launch(const Plan &p, cudaStream_t s, const double *hk, bool full)
+template <typename T, int MAXA, bool BATCH>
+void gather_launch(const Plan &p, cudaStream_t s, const double *hk, double dt, bool full)
 {
     GatherArgs<T> a;
     a.N = p.N;
@@ -564,30 +766,34 @@ void gather_launch(const Plan &p, cudaStream_t s, const double *hk, bool full)
     a.w_out = full ? p.w : nullptr;
     a.j_out = full ? p.j : nullptr;
     a.partials = p.partials;
+    a.seg_max = p.seg_max;
+    a.sys_of = p.sys_of;
+    a.sys = p.sys;
+    a.dt = dt;
     a.flags = p.flags;
     const unsigned nb = blocks_for(p.N, kGatherBlock);
     if (full)
-        k_gather<T, MAXA, kGatherBlock, true><<<nb, kGatherBlock, 0, s>>>(a);
+        k_gather<T, MAXA, kGatherBlock, true, BATCH><<<nb, kGatherBlock, 0, s>>>(a);
     else
-        k_gather<T, MAXA, kGatherBlock, false><<<nb, kGatherBlock, 0, s>>>(a);
+        k_gather<T, MAXA, kGatherBlock, false, BATCH><<<nb, kGatherBlock, 0, s>>>(a);
 }
 
 }  // namespace
 
 size_t pair_smem_bytes(const Plan &p)
 {
-    if (p.precision == 0) return p.maxa <= 8 ? smem_for<double, 8>(p.kind) : smem_for<double, 16>(p.kind);
-    return p.maxa <= 8 ? smem_for<float, 8>(p.kind) : smem_for<float, 16>(p.kind);
+    if (p.precision == 0) return smem_for<double, kPairCapSmall, kPairBlockF64>(p.kind);
+    return smem_for<float, kPairCapSmall, kPairBlockF32>(p.kind);
 }
 
 void configure_kernels(const Plan &)
 {
     static bool done = false;
     if (done) return;
-    configure_one<double, 8>();
-    configure_one<double, 16>();
-    configure_one<float, 8>();
-    configure_one<float, 16>();
+    configure_type<double, false>();
+    configure_type<float, false>();
+    configure_type<double, true>();
+    configure_type<float, true>();
     done = true;
 }
 
@@ -596,6 +802,8 @@ void launch_kick_drift(const Plan &p, cudaStream_t s, const double *hk, double d
     if (p.N == 0) return;
     KickDriftArgs a;
     a.N = p.N;
+    a.sys_of = p.sys_of;
+    a.sys = p.sys;
     a.pos = p.pos;
     a.vel = p.vel;
     a.force = p.force;
@@ -606,44 +814,67 @@ void launch_kick_drift(const Plan &p, cudaStream_t s, const double *hk, double d
     const double hs = 0.5 * p.skin;
     a.half_skin2 = (float)(hs * hs);
     a.flags = p.flags;
-    k_kick_drift<<<blocks_for(p.N, 256), 256, 0, s>>>(a);
+    if (p.batch) k_kick_drift<true><<<blocks_for(p.N, 256), 256, 0, s>>>(a);
+    else k_kick_drift<false><<<blocks_for(p.N, 256), 256, 0, s>>>(a);
 }
 
 void launch_step_begin(const Plan &p, cudaStream_t s, const cudaGraphConditionalHandle *h)
 {
-    k_step_begin<<<1, 1, 0, s>>>(p.flags, h ? *h : cudaGraphConditionalHandle(0), h ? 1 : 0);
+    k_step_begin<<<1, 1, 0, s>>>(p.flags, p.ovf_count, h ? *h : cudaGraphConditionalHandle(0), h ? 1 : 0);
 }
 
-void launch_pair(const Plan &p, cudaStream_t s)
+void launch_pair_reset(const Plan &p, cudaStream_t s) { k_pair_reset<<<1, 1, 0, s>>>(p.ovf_count); }
+
+template <bool BATCH>
+void pair_dispatch_launch(const Plan &p, cudaStream_t s)
 {
-    if (p.N == 0) return;
     if (p.precision == 0) {
-        if (p.maxa <= 8) pair_launch<double, 8>(p, s); else pair_launch<double, 16>(p, s);
+        if (p.maxa <= 8) pair_launch<double, 8, BATCH>(p, s); else pair_launch<double, 16, BATCH>(p, s);
     } else {
-        if (p.maxa <= 8) pair_launch<float, 8>(p, s); else pair_launch<float, 16>(p, s);
+        if (p.maxa <= 8) pair_launch<float, 8, BATCH>(p, s); else pair_launch<float, 16, BATCH>(p, s);
     }
 }
 
-void launch_gather(const Plan &p, cudaStream_t s, const double *hk, bool full)
+int launch_pair(const Plan &p, cudaStream_t s)
+{
+    if (p.N == 0) return 0;
+    if (p.batch) pair_dispatch_launch<true>(p, s); else pair_dispatch_launch<false>(p, s);
+    return 2;
+}
+
+template <bool BATCH>
+void gather_dispatch(const Plan &p, cudaStream_t s, const double *hk, double dt, bool full)
+{
+    if (p.precision == 0) {
+        if (p.maxa <= 8) gather_launch<double, 8, BATCH>(p, s, hk, dt, full);
+        else gather_launch<double, 16, BATCH>(p, s, hk, dt, full);
+    } else {
+        if (p.maxa <= 8) gather_launch<float, 8, BATCH>(p, s, hk, dt, full);
+        else gather_launch<float, 16, BATCH>(p, s, hk, dt, full);
+    }
+}
+
+void launch_gather(const Plan &p, cudaStream_t s, const double *hk, double dt, bool full)
 {
     if (p.N == 0) return;
-    if (p.precision == 0) {
-        if (p.maxa <= 8) gather_launch<double, 8>(p, s, hk, full);
-        else gather_launch<double, 16>(p, s, hk, full);
-    } else {
-        if (p.maxa <= 8) gather_launch<float, 8>(p, s, hk, full);
-        else gather_launch<float, 16>(p, s, hk, full);
-    }
+    if (p.batch) gather_dispatch<true>(p, s, hk, dt, full); else gather_dispatch<false>(p, s, hk, dt, full);
 }
 
 void launch_reduce(const Plan &p, cudaStream_t s, bool full, bool record_series)
 {
-    const int nb = p.N == 0 ? 0 : (int)blocks_for(p.N, kGatherBlock);
     const int nc = full ? kNumPartials : kStepPartials;
-    k_reduce<<<nc, kReduceThreads, 0, s>>>(p.partials, nb, p.totals, p.series, p.flags,
-                                           record_series && p.series != nullptr);
+    const bool rec = record_series && p.series != nullptr;
+    if (p.batch)
+        k_reduce<true><<<dim3(p.n_sys, nc), kReduceThreads, 0, s>>>(p.partials, nc, p.seg_max, p.N, kGatherBlock,
+                                                                    p.sys_of, p.sys, p.n_sys, p.totals, p.series,
+                                                                    p.flags, rec);
+    else
+        k_reduce<false><<<dim3(1, nc), kReduceThreads, 0, s>>>(p.partials, nc, p.seg_max, p.N, kGatherBlock,
+                                                               p.sys_of, p.sys, 1, p.totals, p.series, p.flags,
+                                                               rec);
 }
 
+int gather_block() { return kGatherBlock; }
 int gather_blocks(int64_t N) { return N == 0 ? 1 : (int)blocks_for(N, kGatherBlock); }
 
 }  // namespace mdk

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -18,6 +19,45 @@ constexpr int kStepsPerGraph = 8;
 
 struct Timing {
     cudaEvent_t ev[2];
+};
+
+// First-fit allocator of [start, start + len) ranges over [0, capacity).
+struct RangeAlloc {
+    std::map<int64_t, int64_t> free_;   // start -> length
+    void init(int64_t capacity)
+    {
+        free_.clear();
+        if (capacity > 0) free_[0] = capacity;
+    }
+    int64_t alloc(int64_t len)
+    {
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= len) {
+                const int64_t start = it->first, rest = it->second - len;
+                free_.erase(it);
+                if (rest > 0) free_[start + len] = rest;
+                return start;
+            }
+        }
+        return -1;
+    }
+    void release(int64_t start, int64_t len)
+    {
+        if (len <= 0) return;
+        auto it = free_.emplace(start, len).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
 };
 
 }  // namespace
@@ -47,6 +87,14 @@ struct md_ctx {
     std::vector<Timing> ev;        // [steps_per_graph * KC_COUNT]
     double kt_ms[KC_COUNT] = {0, 0, 0, 0, 0};
     int64_t kt_n[KC_COUNT] = {0, 0, 0, 0, 0};
+    // pools
+    bool is_pool = false;
+    std::vector<SysDev> sys_host;   // n_sys + 1 (the last: inactive sentinel for free atoms)
+    std::vector<char> sys_used;
+    RangeAlloc atoms_free, cells_free;
+    int64_t cell_capacity = 0;
+    int64_t min_atoms = 1;
+    double skin_option = 0.0;
     std::string err;
 };
 
@@ -159,6 +207,68 @@ md_status check_flags(md_ctx *ctx)
     return MD_OK;
 }
 
+// Unpack one packed parameter set into set `idx` of the plan; returns its cutoff in rc.
+md_status parse_params(const md_params *params, Plan &p, int idx, double *rc)
+{
+    if (!params || !params->p) return MD_ERR_ARG;
+    const double *q = params->p;
+    if (params->kind == MD_TERSOFF) {
+        TersoffP &t = p.tp[idx];
+        t.A = q[0]; t.B = q[1]; t.lam = q[2]; t.mu = q[3]; t.beta = q[4]; t.n = q[5];
+        t.c = q[6]; t.d = q[7]; t.h = q[8]; t.R = q[9]; t.S = q[10];
+        if (!(t.S > t.R) || !(t.R > 0) || !(t.n > 0) || t.beta < 0 || !(t.d != 0)) return MD_ERR_ARG;
+        t.c2 = t.c * t.c;
+        t.d2 = t.d * t.d;
+        t.c2d2 = t.c2 / t.d2;
+        t.pi_SR = M_PI / (t.S - t.R);
+        t.beta_zero = t.beta == 0.0;
+        t.ln_beta = t.beta > 0 ? std::log(t.beta) : 0.0;
+        t.inv2n = 1.0 / (2.0 * t.n);
+        *rc = t.S;
+    } else if (params->kind == MD_SW) {
+        SWP &w = p.sp[idx];
+        w.eps = q[0]; w.sig = q[1]; w.a = q[2]; w.lam = q[3]; w.gam = q[4]; w.A = q[5]; w.B = q[6];
+        w.p = q[7]; w.q = q[8];
+        if (!(w.sig > 0) || !(w.a > 0)) return MD_ERR_ARG;
+        w.rc = w.a * w.sig;
+        w.Aeps = w.A * w.eps;
+        w.lameps = w.lam * w.eps;
+        w.gamsig = w.gam * w.sig;
+        w.p_int = (w.p == std::floor(w.p) && w.p >= 0 && w.p <= 16) ? (int)w.p : -1;
+        w.q_int = (w.q == std::floor(w.q) && w.q >= 0 && w.q <= 16) ? (int)w.q : -1;
+        *rc = w.rc;
+    } else {
+        return MD_ERR_ARG;
+    }
+    return MD_OK;
+}
+
+// Box and cell grid of one system: periodic edges must exceed 2 (rl + margin); cells
+// have edge >= rl + margin; a grid larger than `max_cells` is coarsened (coarser cells
+// are still correct, only slower).
+md_status system_box(const Plan &p, double rl, const double box[3], const int pbc[3], int64_t max_cells, Box *out,
+                     int nc[3])
+{
+    const double edge = rl + p.list_margin;
+    for (int a = 0; a < 3; ++a) {
+        if (!(box[a] > 0) || !std::isfinite(box[a])) return MD_ERR_ARG;
+        out->L[a] = box[a];
+        out->invL[a] = 1.0 / box[a];
+        out->pbc[a] = pbc[a] ? 1 : 0;
+        if (out->pbc[a] && box[a] < 2.0 * edge + 0.01) return MD_ERR_BOX;
+        const int n = (int)std::floor(box[a] / edge);
+        nc[a] = n < 1 ? 1 : n;
+    }
+    while ((int64_t)nc[0] * nc[1] * nc[2] > max_cells) {
+        int a = 0;
+        if (nc[1] > nc[a]) a = 1;
+        if (nc[2] > nc[a]) a = 2;
+        if (nc[a] == 1) break;
+        nc[a] = (nc[a] + 1) / 2;
+    }
+    return MD_OK;
+}
+
 // half-kick factors dt/2 * acc / m per type (same expression order as the oracle)
 void half_kick(const md_ctx *ctx, double dt, double *hk)
 {
@@ -245,13 +355,13 @@ md_status enqueue_step(md_ctx *ctx, const Recorder &rec, const double *hk, doubl
     launch_pair(ctx->p, ctx->stream);
     rec.end(KC_PAIR);
     rec.begin(KC_GATHER);
-    launch_gather(ctx->p, ctx->stream, hk, false);
+    launch_gather(ctx->p, ctx->stream, hk, dt, false);
     rec.end(KC_GATHER);
     rec.begin(KC_REDUCE);
     launch_reduce(ctx->p, ctx->stream, false, true);
     rec.end(KC_REDUCE);
     // kernels launched every step; a taken rebuild adds the body's kernels
-    *n_kernels = ctx->p.N > 0 ? 5 : 2;
+    *n_kernels = ctx->p.N > 0 ? 6 : 2;
     return MD_OK;
 }
 
@@ -275,7 +385,7 @@ md_status eager_step(md_ctx *ctx, const double *hk, double dt)
     launch_pair(ctx->p, ctx->stream);
     rec.end(KC_PAIR);
     rec.begin(KC_GATHER);
-    launch_gather(ctx->p, ctx->stream, hk, false);
+    launch_gather(ctx->p, ctx->stream, hk, dt, false);
     rec.end(KC_GATHER);
     rec.begin(KC_REDUCE);
     launch_reduce(ctx->p, ctx->stream, false, true);
@@ -312,6 +422,7 @@ md_status accumulate_times(md_ctx *ctx, int steps)
 
 md_status ensure_series(md_ctx *ctx, int64_t rows)
 {
+    rows *= ctx->p.n_sys;
     if (rows <= ctx->series_cap) return MD_OK;
     if (ctx->p.series) {
         cudaFree(ctx->p.series);
@@ -355,8 +466,9 @@ md_status force_eval(md_ctx *ctx, bool full)
     CK(cudaMemcpyAsync(&rebuild, &ctx->p.flags->rebuild, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     if (rebuild) launch_rebuild(ctx->p, ctx->stream);
+    launch_pair_reset(ctx->p, ctx->stream);
     launch_pair(ctx->p, ctx->stream);
-    launch_gather(ctx->p, ctx->stream, nullptr, full);
+    launch_gather(ctx->p, ctx->stream, nullptr, 0.0, full);
     launch_reduce(ctx->p, ctx->stream, full, false);
     CK(cudaGetLastError());
     md_status s = check_flags(ctx);
@@ -419,96 +531,19 @@ md_status md_default_options(md_options *opt)
     return MD_OK;
 }
 
-md_status md_create(md_ctx **out, const double box[3], const int pbc[3], int64_t n_atoms,
-                    const int32_t *types, const double *masses_by_type, const md_params *params,
-                    const md_options *opt_in)
-{
-    if (!out) return MD_ERR_ARG;
-    *out = nullptr;
-    if (!box || !pbc || n_atoms < 0 || (n_atoms > 0 && !types) || !masses_by_type || !params || !params->p)
-        return MD_ERR_ARG;
-    if (n_atoms > kMaxAtoms) return MD_ERR_ARG;   // list entries hold 26-bit atom indices
-    md_options opt;
-    if (opt_in) opt = *opt_in; else md_default_options(&opt);
-    if (params->kind != MD_TERSOFF && params->kind != MD_SW) return MD_ERR_ARG;
-    if (params->n_types != 1) return MD_ERR_ARG;
-    if (opt.precision != MD_FP64 && opt.precision != MD_MIXED) return MD_ERR_ARG;
-    if (opt.max_neigh < 1 || opt.max_neigh > kMaxListCap) return MD_ERR_ARG;
-    if (opt.max_active < 0 || opt.max_active > 16) return MD_ERR_ARG;
-    if (opt.skin < 0) return MD_ERR_ARG;
-    for (int a = 0; a < 3; ++a)
-        if (!(box[a] > 0) || !std::isfinite(box[a])) return MD_ERR_ARG;
-    if (!(masses_by_type[0] > 0)) return MD_ERR_ARG;
-    for (int64_t i = 0; i < n_atoms; ++i)
-        if (types[i] != 0) return MD_ERR_ARG;   // single element
+}  // extern "C"
 
-    md_ctx *ctx = new md_ctx();
-    Plan &p = ctx->p;
+namespace {
+
+// Options common to single systems and pools; device, streams, kernel attributes.
+md_status ctx_init(md_ctx *ctx, const md_options &opt)
+{
     ctx->device = opt.device;
     ctx->io = opt.io;
     ctx->budget = opt.hbm_budget;
-    p.N = n_atoms;
-    p.kind = params->kind;
-    p.precision = opt.precision;
-    p.cap = opt.max_neigh;
-    const int want_active = opt.max_active > 0 ? opt.max_active : (params->kind == MD_SW ? 16 : 8);
-    p.maxa = want_active <= 8 ? 8 : 16;
-    p.ntypes = params->n_types;
-    p.mass[0] = masses_by_type[0];
-    p.inv_mass[0] = 1.0 / masses_by_type[0];
-    const double *q = params->p;
-    if (p.kind == MD_TERSOFF) {
-        TersoffP &t = p.tp;
-        t.A = q[0]; t.B = q[1]; t.lam = q[2]; t.mu = q[3]; t.beta = q[4]; t.n = q[5];
-        t.c = q[6]; t.d = q[7]; t.h = q[8]; t.R = q[9]; t.S = q[10];
-        if (!(t.S > t.R) || !(t.R > 0) || !(t.n > 0) || t.beta < 0 || !(t.d != 0)) {
-            delete ctx;
-            return MD_ERR_ARG;
-        }
-        t.c2 = t.c * t.c;
-        t.d2 = t.d * t.d;
-        t.c2d2 = t.c2 / t.d2;
-        t.pi_SR = M_PI / (t.S - t.R);
-        t.beta_zero = t.beta == 0.0;
-        t.ln_beta = t.beta > 0 ? std::log(t.beta) : 0.0;
-        t.inv2n = 1.0 / (2.0 * t.n);
-        p.rc = t.S;
-    } else {
-        SWP &s = p.sp;
-        s.eps = q[0]; s.sig = q[1]; s.a = q[2]; s.lam = q[3]; s.gam = q[4]; s.A = q[5]; s.B = q[6];
-        s.p = q[7]; s.q = q[8];
-        if (!(s.sig > 0) || !(s.a > 0)) {
-            delete ctx;
-            return MD_ERR_ARG;
-        }
-        s.rc = s.a * s.sig;
-        s.Aeps = s.A * s.eps;
-        s.lameps = s.lam * s.eps;
-        s.gamsig = s.gam * s.sig;
-        s.p_int = (s.p == std::floor(s.p) && s.p >= 0 && s.p <= 16) ? (int)s.p : -1;
-        s.q_int = (s.q == std::floor(s.q) && s.q >= 0 && s.q <= 16) ? (int)s.q : -1;
-        p.rc = s.rc;
-    }
-    p.skin = opt.skin > 0 ? opt.skin : 0.15 * p.rc;
-    p.rl = p.rc + p.skin;
-    for (int a = 0; a < 3; ++a) {
-        p.box.L[a] = box[a];
-        p.box.invL[a] = 1.0 / box[a];
-        p.box.pbc[a] = pbc[a] ? 1 : 0;
-        if (p.box.pbc[a] && box[a] < 2.0 * p.rl + 0.01) {
-            delete ctx;
-            return MD_ERR_BOX;
-        }
-        int n = (int)std::floor(box[a] / p.rl);
-        p.nc[a] = n < 1 ? 1 : n;
-    }
-    p.ncell = (int64_t)p.nc[0] * p.nc[1] * p.nc[2];
-
-    md_status st = MD_OK;
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        delete ctx;
         return MD_ERR_CUDA;
     }
     if (opt.cuda_stream) {
@@ -517,7 +552,6 @@ md_status md_create(md_ctx **out, const double box[3], const int pbc[3], int64_t
         e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
         if (e != cudaSuccess) {
             cudaGetLastError();
-            delete ctx;
             return MD_ERR_CUDA;
         }
         ctx->own_stream = true;
@@ -525,18 +559,44 @@ md_status md_create(md_ctx **out, const double box[3], const int pbc[3], int64_t
     e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
-        delete ctx;
         return MD_ERR_CUDA;
     }
-    configure_kernels(p);
+    configure_kernels(ctx->p);
+    return MD_OK;
+}
 
+md_status check_options(const md_options &opt)
+{
+    if (opt.precision != MD_FP64 && opt.precision != MD_MIXED) return MD_ERR_ARG;
+    if (opt.max_neigh < 1 || opt.max_neigh > kMaxListCap) return MD_ERR_ARG;
+    if (opt.max_active < 0 || opt.max_active > 16) return MD_ERR_ARG;
+    if (opt.skin < 0) return MD_ERR_ARG;
+    return MD_OK;
+}
+
+void apply_options(Plan &p, const md_options &opt, int kind, double rc)
+{
+    p.kind = kind;
+    p.precision = opt.precision;
+    p.cap = opt.max_neigh;
+    const int want_active = opt.max_active > 0 ? opt.max_active : (kind == MD_SW ? 16 : 8);
+    p.maxa = want_active <= 8 ? 8 : 16;
+    p.rc = rc;
+    p.skin = opt.skin > 0 ? opt.skin : 0.15 * rc;
+    p.rl = p.rc + p.skin;
+}
+
+// Device arrays for p.N atoms, p.ncell cells, p.n_sys systems.
+md_status ctx_alloc(md_ctx *ctx)
+{
+    Plan &p = ctx->p;
+    md_status st = MD_OK;
     const size_t N1 = (size_t)(p.N > 0 ? p.N : 1);
     const size_t esz = p.precision == MD_FP64 ? sizeof(double) : sizeof(float);
 #define AL(ptr, count)                                      \
     do {                                                    \
         st = dalloc_t(ctx, &(ptr), (size_t)(count));        \
-        if (st != MD_OK) { md_destroy(ctx); return st; }    \
+        if (st != MD_OK) return st;                         \
     } while (0)
     AL(p.pos, 3 * N1);
     AL(p.vel, 3 * N1);
@@ -550,13 +610,17 @@ md_status md_create(md_ctx **out, const double box[3], const int pbc[3], int64_t
     AL(p.nl, (size_t)p.cap * N1);
     AL(p.rev, (size_t)p.cap * N1);
     AL(p.mask, N1);
+    AL(p.ovf_count, 1);
+    AL(p.ovf_list, N1);
+    AL(p.sys_of, p.batch ? N1 : 1);
+    AL(p.sys, (size_t)p.n_sys + 1);
     {
         void *v = nullptr;
         st = dalloc(ctx, &v, 3 * (size_t)p.maxa * N1 * esz);
-        if (st != MD_OK) { md_destroy(ctx); return st; }
+        if (st != MD_OK) return st;
         p.pd = v;
         st = dalloc(ctx, &v, 3 * (size_t)p.maxa * N1 * esz);
-        if (st != MD_OK) { md_destroy(ctx); return st; }
+        if (st != MD_OK) return st;
         p.pr = v;
     }
     AL(p.cell_count, p.ncell);
@@ -567,22 +631,106 @@ md_status md_create(md_ctx **out, const double box[3], const int pbc[3], int64_t
     p.nscanb = (p.ncell + scan_block_elems() - 1) / scan_block_elems();
     AL(p.scan_blocks, p.nscanb + 1);
     p.nb_gather = gather_blocks(p.N);
+    p.seg_max = 1;
     AL(p.partials, (size_t)p.nb_gather * kNumPartials);
-    AL(p.totals, kNumPartials);
+    AL(p.totals, (size_t)p.n_sys * kNumPartials);
     AL(p.flags, 1);
 #undef AL
     st = ensure_series(ctx, 1024);
-    if (st != MD_OK) { md_destroy(ctx); return st; }
-
-    // zero state; types from the host
+    if (st != MD_OK) return st;
     cudaMemsetAsync(p.pos, 0, sizeof(double) * 3 * N1, ctx->stream);
     cudaMemsetAsync(p.vel, 0, sizeof(double) * 3 * N1, ctx->stream);
     cudaMemsetAsync(p.force, 0, sizeof(double) * 3 * N1, ctx->stream);
+    cudaMemsetAsync(p.pos_build, 0, sizeof(double) * 3 * N1, ctx->stream);
     cudaMemsetAsync(p.flags, 0, sizeof(Flags), ctx->stream);
     cudaMemsetAsync(p.nn, 0, sizeof(int) * N1, ctx->stream);
+    cudaMemsetAsync(p.mask, 0, sizeof(uint32_t) * N1, ctx->stream);
+    cudaMemsetAsync(p.type, 0, sizeof(int) * N1, ctx->stream);
+    cudaMemsetAsync(p.totals, 0, sizeof(double) * p.n_sys * kNumPartials, ctx->stream);
+    return MD_OK;
+}
+
+md_status upload_sys_table(md_ctx *ctx)
+{
+    CK(cudaMemcpyAsync(ctx->p.sys, ctx->sys_host.data(), sizeof(SysDev) * ctx->sys_host.size(),
+                       cudaMemcpyHostToDevice, ctx->stream));
+    return MD_OK;
+}
+
+// Refresh the host copy of the system table (active flags, step budgets, rebuilds).
+md_status download_sys_table(md_ctx *ctx)
+{
+    CK(cudaMemcpyAsync(ctx->sys_host.data(), ctx->p.sys, sizeof(SysDev) * ctx->sys_host.size(),
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return MD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+md_status md_create(md_ctx **out, const double box[3], const int pbc[3], int64_t n_atoms,
+                    const int32_t *types, const double *masses_by_type, const md_params *params,
+                    const md_options *opt_in)
+{
+    if (!out) return MD_ERR_ARG;
+    *out = nullptr;
+    if (!box || !pbc || n_atoms < 0 || (n_atoms > 0 && !types) || !masses_by_type || !params || !params->p)
+        return MD_ERR_ARG;
+    if (n_atoms > kMaxAtoms) return MD_ERR_ARG;   // list entries hold 26-bit atom indices
+    md_options opt;
+    if (opt_in) opt = *opt_in; else md_default_options(&opt);
+    if (check_options(opt) != MD_OK) return MD_ERR_ARG;
+    if (params->n_types != 1) return MD_ERR_ARG;
+    if (!(masses_by_type[0] > 0)) return MD_ERR_ARG;
+    for (int64_t i = 0; i < n_atoms; ++i)
+        if (types[i] != 0) return MD_ERR_ARG;   // single element
+
+    md_ctx *ctx = new md_ctx();
+    Plan &p = ctx->p;
+    double rc = 0;
+    if (parse_params(params, p, 0, &rc) != MD_OK) {
+        delete ctx;
+        return MD_ERR_ARG;
+    }
+    apply_options(p, opt, params->kind, rc);
+    p.N = n_atoms;
+    p.ntypes = 1;
+    p.n_sets = 1;
+    p.mass[0] = masses_by_type[0];
+    p.inv_mass[0] = 1.0 / masses_by_type[0];
+    double lmax = std::max(box[0], std::max(box[1], box[2]));
+    p.list_margin = list_margin_for(lmax, p.rl);
+    md_status st = system_box(p, p.rl, box, pbc, INT64_MAX, &p.box, p.nc);
+    if (st != MD_OK) {
+        delete ctx;
+        return st;
+    }
+    p.ncell = (int64_t)p.nc[0] * p.nc[1] * p.nc[2];
+    p.batch = false;
+    p.n_sys = 1;
+    if ((st = ctx_init(ctx, opt)) != MD_OK || (st = ctx_alloc(ctx)) != MD_OK) {
+        md_destroy(ctx);
+        return st;
+    }
+    // the one system, for the per-system reduce
+    SysDev sd;
+    std::memset(&sd, 0, sizeof(sd));
+    sd.box = p.box;
+    sd.nc[0] = p.nc[0]; sd.nc[1] = p.nc[1]; sd.nc[2] = p.nc[2];
+    sd.n_atoms = p.N;
+    sd.steps_left = -1;
+    sd.active = 1;
+    ctx->sys_host.assign(2, SysDev{});
+    ctx->sys_host[0] = sd;
+    if ((st = upload_sys_table(ctx)) != MD_OK) {
+        md_destroy(ctx);
+        return st;
+    }
     if (p.N > 0) cudaMemcpyAsync(p.type, types, sizeof(int32_t) * p.N, cudaMemcpyHostToDevice, ctx->stream);
-    e = cudaStreamSynchronize(ctx->stream);
-    if (e != cudaSuccess) {
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+        cudaGetLastError();
         md_destroy(ctx);
         return MD_ERR_CUDA;
     }
@@ -590,9 +738,234 @@ md_status md_create(md_ctx **out, const double box[3], const int pbc[3], int64_t
     return MD_OK;
 }
 
+md_status md_batch_create(md_ctx **out, int64_t atom_capacity, int max_systems, int n_sets,
+                          const md_params *param_sets, int n_types, const double *masses_by_type,
+                          const md_batch_options *bopt, const md_options *opt_in)
+{
+    if (!out) return MD_ERR_ARG;
+    *out = nullptr;
+    if (atom_capacity < 1 || max_systems < 1 || n_sets < 1 || n_sets > kMaxSets || !param_sets ||
+        n_types < 1 || n_types > kMaxTypes || !masses_by_type)
+        return MD_ERR_ARG;
+    md_options opt;
+    if (opt_in) opt = *opt_in; else md_default_options(&opt);
+    if (check_options(opt) != MD_OK) return MD_ERR_ARG;
+    for (int t = 0; t < n_types; ++t)
+        if (!(masses_by_type[t] > 0)) return MD_ERR_ARG;
+    const int block = gather_block();
+    const int64_t cap_atoms = (atom_capacity + block - 1) / block * block;
+    if (cap_atoms > kMaxAtoms) return MD_ERR_ARG;
+
+    md_ctx *ctx = new md_ctx();
+    Plan &p = ctx->p;
+    double rcmax = 0;
+    for (int k = 0; k < n_sets; ++k) {
+        double rc = 0;
+        if (param_sets[k].kind != param_sets[0].kind || parse_params(&param_sets[k], p, k, &rc) != MD_OK) {
+            delete ctx;
+            return MD_ERR_ARG;
+        }
+        rcmax = std::max(rcmax, rc);
+    }
+    apply_options(p, opt, param_sets[0].kind, rcmax);
+    ctx->skin_option = opt.skin;
+    p.n_sets = n_sets;
+    p.ntypes = n_types;
+    for (int t = 0; t < n_types; ++t) {
+        p.mass[t] = masses_by_type[t];
+        p.inv_mass[t] = 1.0 / masses_by_type[t];
+    }
+    const double max_box = bopt && bopt->max_box > 0 ? bopt->max_box : 4096.0;
+    p.list_margin = list_margin_for(max_box, p.rl);
+    p.N = cap_atoms;
+    p.batch = true;
+    p.n_sys = max_systems;
+    ctx->is_pool = true;
+    ctx->min_atoms = 1;
+    ctx->cell_capacity = bopt && bopt->cell_capacity > 0 ? bopt->cell_capacity : 4 * cap_atoms + 64;
+    p.ncell = ctx->cell_capacity;
+    md_status st;
+    if ((st = ctx_init(ctx, opt)) != MD_OK || (st = ctx_alloc(ctx)) != MD_OK) {
+        md_destroy(ctx);
+        return st;
+    }
+    ctx->sys_host.assign((size_t)max_systems + 1, SysDev{});
+    for (auto &sd : ctx->sys_host) {
+        std::memset(&sd, 0, sizeof(sd));
+        sd.steps_left = -1;
+        for (int a = 0; a < 3; ++a) {
+            sd.box.L[a] = 1.0;
+            sd.box.invL[a] = 1.0;
+            sd.nc[a] = 1;
+        }
+    }
+    ctx->sys_used.assign((size_t)max_systems, 0);
+    ctx->atoms_free.init(cap_atoms);
+    ctx->cells_free.init(ctx->cell_capacity);
+    // every atom starts free: it belongs to the inactive sentinel system max_systems
+    std::vector<int> sentinel((size_t)cap_atoms, max_systems);
+    cudaMemcpyAsync(p.sys_of, sentinel.data(), sizeof(int) * cap_atoms, cudaMemcpyHostToDevice, ctx->stream);
+    if ((st = upload_sys_table(ctx)) != MD_OK) {
+        md_destroy(ctx);
+        return st;
+    }
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+        cudaGetLastError();
+        md_destroy(ctx);
+        return MD_ERR_CUDA;
+    }
+    ctx->pos_set = true;
+    ctx->forces_valid = true;
+    *out = ctx;
+    return MD_OK;
+}
+
+md_status md_batch_add(md_ctx *ctx, const md_system *sysd, int *id_out)
+{
+    if (!ctx || !sysd || !id_out) return MD_ERR_ARG;
+    if (!ctx->is_pool) return fail(ctx, MD_ERR_STATE, "not a pool");
+    Plan &p = ctx->p;
+    const int64_t n = sysd->n_atoms;
+    if (n < 1 || !sysd->types || !sysd->x || !sysd->y || !sysd->z) return fail(ctx, MD_ERR_ARG, "bad system");
+    if (sysd->param_set < 0 || sysd->param_set >= p.n_sets) return fail(ctx, MD_ERR_ARG, "bad parameter set");
+    if (!(sysd->damp >= 0)) return fail(ctx, MD_ERR_ARG, "bad damping");
+    for (int64_t i = 0; i < n; ++i)
+        if (sysd->types[i] < 0 || sysd->types[i] >= p.ntypes) return fail(ctx, MD_ERR_ARG, "bad type");
+    SysDev sd;
+    std::memset(&sd, 0, sizeof(sd));
+    // cutoff, skin and list radius of this system's parameter set
+    const double rc = p.kind == MD_TERSOFF ? p.tp[sysd->param_set].S : p.sp[sysd->param_set].rc;
+    const double skin = ctx->skin_option > 0 ? ctx->skin_option : 0.15 * rc;
+    const double rl = rc + skin;
+    sd.rlm2 = (float)((rl + p.list_margin) * (rl + p.list_margin));
+    sd.half_skin2 = (float)(0.25 * skin * skin);
+    const int64_t max_cells = std::max<int64_t>(64, 4 * n);
+    md_status st = system_box(p, rl, sysd->box, sysd->pbc, max_cells, &sd.box, sd.nc);
+    if (st != MD_OK) return fail(ctx, st, "box too small for the cutoff");
+    int id = -1;
+    for (int k = 0; k < p.n_sys; ++k)
+        if (!ctx->sys_used[k]) { id = k; break; }
+    if (id < 0) return fail(ctx, MD_ERR_OOM, "no free system slot");
+    const int block = gather_block();
+    const int64_t len = (n + block - 1) / block * block;   // block-aligned: one system per gather block
+    const int64_t a0 = ctx->atoms_free.alloc(len);
+    if (a0 < 0) return fail(ctx, MD_ERR_OOM, "no room for the atoms");
+    const int64_t ncell = (int64_t)sd.nc[0] * sd.nc[1] * sd.nc[2];
+    const int64_t c0 = ctx->cells_free.alloc(ncell);
+    if (c0 < 0) {
+        ctx->atoms_free.release(a0, len);
+        return fail(ctx, MD_ERR_OOM, "no room for the cell grid");
+    }
+    sd.pset = sysd->param_set;
+    sd.cell_off = c0;
+    sd.atom_start = a0;
+    sd.n_atoms = n;
+    sd.steps_left = sysd->n_steps < 0 ? -1 : sysd->n_steps;
+    sd.damp = sysd->damp;
+    sd.active = sysd->n_steps == 0 ? 0 : 1;
+    sd.rebuild = 1;
+    ctx->sys_host[id] = sd;
+    ctx->sys_used[id] = 1;
+    const cudaMemcpyKind k = ctx->io == MD_IO_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const int64_t N = p.N;
+    const double *src[6] = {sysd->x, sysd->y, sysd->z, sysd->vx, sysd->vy, sysd->vz};
+    for (int c = 0; c < 3; ++c) {
+        CK(cudaMemcpyAsync(p.pos + c * N + a0, src[c], sizeof(double) * n, k, ctx->stream));
+        if (src[3 + c]) CK(cudaMemcpyAsync(p.vel + c * N + a0, src[3 + c], sizeof(double) * n, k, ctx->stream));
+        else CK(cudaMemsetAsync(p.vel + c * N + a0, 0, sizeof(double) * n, ctx->stream));
+        CK(cudaMemsetAsync(p.force + c * N + a0, 0, sizeof(double) * len, ctx->stream));
+    }
+    CK(cudaMemcpyAsync(p.type + a0, sysd->types, sizeof(int32_t) * n, cudaMemcpyHostToDevice, ctx->stream));
+    std::vector<int> ids((size_t)n, id);
+    CK(cudaMemcpyAsync(p.sys_of + a0, ids.data(), sizeof(int) * n, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(&p.sys[id], &ctx->sys_host[id], sizeof(SysDev), cudaMemcpyHostToDevice, ctx->stream));
+    static const int one = 1;
+    CK(cudaMemcpyAsync(&p.flags->rebuild, &one, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->forces_valid = false;   // the new system needs forces before its first kick
+    *id_out = id;
+    return MD_OK;
+}
+
+md_status md_batch_remove(md_ctx *ctx, int id)
+{
+    if (!ctx) return MD_ERR_ARG;
+    if (!ctx->is_pool || id < 0 || id >= ctx->p.n_sys || !ctx->sys_used[id])
+        return fail(ctx, MD_ERR_ARG, "no such system");
+    Plan &p = ctx->p;
+    const SysDev sd = ctx->sys_host[id];
+    const int block = gather_block();
+    const int64_t len = (sd.n_atoms + block - 1) / block * block;
+    std::vector<int> ids((size_t)sd.n_atoms, p.n_sys);
+    CK(cudaMemcpyAsync(p.sys_of + sd.atom_start, ids.data(), sizeof(int) * sd.n_atoms, cudaMemcpyHostToDevice,
+                       ctx->stream));
+    SysDev off;
+    std::memset(&off, 0, sizeof(off));
+    off.steps_left = -1;
+    for (int a = 0; a < 3; ++a) {
+        off.box.L[a] = 1.0;
+        off.box.invL[a] = 1.0;
+        off.nc[a] = 1;
+    }
+    ctx->sys_host[id] = off;
+    CK(cudaMemcpyAsync(&p.sys[id], &ctx->sys_host[id], sizeof(SysDev), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->atoms_free.release(sd.atom_start, len);
+    ctx->cells_free.release(sd.cell_off, (int64_t)sd.nc[0] * sd.nc[1] * sd.nc[2]);
+    ctx->sys_used[id] = 0;
+    return MD_OK;
+}
+
+md_status md_batch_status(md_ctx *ctx, int *active, int64_t *steps_left, double *totals)
+{
+    if (!ctx) return MD_ERR_ARG;
+    if (!ctx->is_pool) return fail(ctx, MD_ERR_STATE, "not a pool");
+    md_status s = download_sys_table(ctx);
+    if (s != MD_OK) return s;
+    const int n = ctx->p.n_sys;
+    std::vector<double> t((size_t)n * kNumPartials);
+    CK(cudaMemcpy(t.data(), ctx->p.totals, sizeof(double) * t.size(), cudaMemcpyDeviceToHost));
+    for (int k = 0; k < n; ++k) {
+        const bool used = ctx->sys_used[k] != 0;
+        if (active) active[k] = used ? (ctx->sys_host[k].active ? 1 : 0) : -1;
+        if (steps_left) steps_left[k] = used ? ctx->sys_host[k].steps_left : 0;
+        if (totals) {
+            double *o = totals + (size_t)k * 13;
+            const double *q = t.data() + (size_t)k * kNumPartials;
+            o[0] = q[0];
+            for (int c = 0; c < 9; ++c) o[1 + c] = q[5 + c];
+            for (int c = 0; c < 3; ++c) o[10 + c] = q[2 + c];
+        }
+    }
+    return MD_OK;
+}
+
+md_status md_batch_get_state(md_ctx *ctx, int id, double *x, double *v)
+{
+    if (!ctx) return MD_ERR_ARG;
+    if (!ctx->is_pool || id < 0 || id >= ctx->p.n_sys || !ctx->sys_used[id])
+        return fail(ctx, MD_ERR_ARG, "no such system");
+    const Plan &p = ctx->p;
+    const SysDev &sd = ctx->sys_host[id];
+    const cudaMemcpyKind k = ctx->io == MD_IO_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (x) {
+        launch_wrap_copy(p, ctx->stream, p.stage);
+        for (int c = 0; c < 3; ++c)
+            CK(cudaMemcpyAsync(x + c * sd.n_atoms, p.stage + c * p.N + sd.atom_start, sizeof(double) * sd.n_atoms, k,
+                               ctx->stream));
+    }
+    if (v)
+        for (int c = 0; c < 3; ++c)
+            CK(cudaMemcpyAsync(v + c * sd.n_atoms, p.vel + c * p.N + sd.atom_start, sizeof(double) * sd.n_atoms, k,
+                               ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return MD_OK;
+}
+
 md_status md_set_positions(md_ctx *ctx, const double *x, const double *y, const double *z)
 {
     if (!ctx) return MD_ERR_ARG;
+    if (ctx->is_pool) return fail(ctx, MD_ERR_STATE, "pools take positions through md_batch_add");
     if (ctx->p.N > 0 && (!x || !y || !z)) return fail(ctx, MD_ERR_ARG, "NULL position array");
     if (ctx->p.N > 0) {
         md_status s = upload3(ctx, ctx->p.pos, x, y, z);
@@ -609,6 +982,7 @@ md_status md_set_positions(md_ctx *ctx, const double *x, const double *y, const 
 md_status md_set_velocities(md_ctx *ctx, const double *vx, const double *vy, const double *vz)
 {
     if (!ctx) return MD_ERR_ARG;
+    if (ctx->is_pool) return fail(ctx, MD_ERR_STATE, "pools take velocities through md_batch_add");
     if (ctx->p.N > 0 && (!vx || !vy || !vz)) return fail(ctx, MD_ERR_ARG, "NULL velocity array");
     if (ctx->p.N > 0) {
         md_status s = upload3(ctx, ctx->p.vel, vx, vy, vz);
@@ -629,11 +1003,15 @@ md_status md_compute(md_ctx *ctx, double *f, double *u, double *w, double *j, do
     if ((s = download(ctx, u, ctx->p.u, N)) != MD_OK) return s;
     if ((s = download(ctx, w, ctx->p.w, 9 * N)) != MD_OK) return s;
     if ((s = download(ctx, j, ctx->p.j, 3 * N)) != MD_OK) return s;
-    double t[kNumPartials];
-    CK(cudaMemcpyAsync(t, ctx->p.totals, sizeof(t), cudaMemcpyDeviceToHost, ctx->stream));
+    std::vector<double> all((size_t)ctx->p.n_sys * kNumPartials);
+    CK(cudaMemcpyAsync(all.data(), ctx->p.totals, sizeof(double) * all.size(), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     if (totals) {
-        totals[0] = t[0];                                  // U
+        double t[kNumPartials] = {0};
+        for (int k = 0; k < ctx->p.n_sys; ++k)   // systems in index order
+            if (!ctx->is_pool || ctx->sys_used[k])
+                for (int c = 0; c < kNumPartials; ++c) t[c] += all[(size_t)k * kNumPartials + c];
+        totals[0] = t[0];                                       // U
         for (int c = 0; c < 9; ++c) totals[1 + c] = t[5 + c];   // W
         for (int c = 0; c < 3; ++c) totals[10 + c] = t[2 + c];  // J
     }
@@ -698,7 +1076,7 @@ md_status md_run(md_ctx *ctx, int64_t n_steps, double dt_fs, double *series)
     }
     if (series) {
         const cudaMemcpyKind k = ctx->io == MD_IO_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-        CK(cudaMemcpyAsync(series, ctx->p.series, sizeof(double) * 5 * n_steps, k, ctx->stream));
+        CK(cudaMemcpyAsync(series, ctx->p.series, sizeof(double) * 5 * n_steps * ctx->p.n_sys, k, ctx->stream));
     }
     s = check_flags(ctx);
     ctx->steps_done += n_steps;
@@ -735,6 +1113,9 @@ md_status md_get_stats(md_ctx *ctx, md_stats *out)
     out->max_neigh_seen = f.max_nn;
     out->kernel_launches_per_step = ctx->kernels_per_step;
     out->kernel_launches_per_rebuild = ctx->kernels_per_rebuild;
+    int deferred = 0;
+    CK(cudaMemcpy(&deferred, ctx->p.ovf_count, sizeof(int), cudaMemcpyDeviceToHost));
+    out->pair_deferred = deferred;
     out->device_bytes = ctx->allocated;
     return MD_OK;
 }

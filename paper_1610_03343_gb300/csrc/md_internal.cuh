@@ -35,6 +35,28 @@ struct Box {
     int pbc[3];
 };
 
+// Systems of a pool.  A context holds up to max_systems independent systems over one
+// flattened atom index; each owns the contiguous atom range [atom_start, atom_start +
+// n_atoms), its own box, cell grid (cells [cell_off, cell_off + nc0 nc1 nc2)) and
+// parameter set.  The table lives in device memory; the host edits it between calls.
+constexpr int kMaxSets = 4;
+struct SysDev {
+    Box box;
+    int nc[3];
+    int pset;                 // parameter set index
+    long long cell_off;       // first cell of this system's grid
+    long long atom_start;     // first atom
+    long long n_atoms;
+    long long steps_left;     // steps still to run (< 0: unlimited); 0 stops the system
+    double damp;              // velocity damping gamma (1/fs) after each step; 0 = NVE
+    float rlm2;               // (list cutoff + fp32 margin)^2 of this system's parameter set
+    float half_skin2;         // (skin/2)^2
+    int active;               // 1 while the system is stepped
+    int rebuild;              // 1: rebuild this system's lists at the next rebuild
+    int built;                // 1 once its lists exist
+    int pad;
+};
+
 // Device status words written by kernels and read by the host after a call.
 struct Flags {
     int rebuild;          // 1: list must be rebuilt before the next force pass
@@ -78,10 +100,15 @@ struct PairArgs {
     const int *nl;          // cap x N, column-major: nl[m N + i]
     int cap;                // list capacity
     T rc2;                  // cutoff^2 in T
-    double shift[3];        // box lengths, for the per-entry image shifts
-    // outputs, "compact active" layout: row k = k-th in-cutoff neighbour of i
-    T *d;                   // 3 x MAXA x N : d[(c MAXA + k) N + i] = dU_i/dr_ij (component c)
-    T *r;                   // 3 x MAXA x N : r_ij
+    // outputs, "compact active" layout: row k = k-th in-cutoff neighbour of i, with a row
+    // stride of S = allocated rows (the staging capacity of a kernel may be smaller)
+    int stride;             // S
+    T *d;                   // 3 x S x N : d[(c S + k) N + i] = dU_i/dr_ij (component c)
+    T *r;                   // 3 x S x N : r_ij
+    const int *sys_of;      // N: system of each atom (pools)
+    const SysDev *sys;      // system table (pools)
+    int *ovf_count;         // atoms deferred by the small-capacity pass ...
+    int *ovf_list;          // ... and their indices (capacity N)
     uint32_t *mask;         // N : bit m set <=> list slot m is inside the cutoff
     double *u;              // N : U_i
     Flags *flags;
@@ -105,7 +132,11 @@ struct GatherArgs {
     double *force;          // 3N, written
     double *w_out;          // 9N or nullptr
     double *j_out;          // 3N or nullptr
-    double *partials;       // component-major: partials[c * gridDim.x + block]
+    double *partials;       // per (block, system segment): partials[(b seg_max + seg) NC + c]
+    int seg_max;            // system segments a block may hold
+    const int *sys_of;      // N: system of each atom (pools)
+    const SysDev *sys;      // system table (pools)
+    double dt;              // time step (damping)
     Flags *flags;
 };
 

@@ -7,18 +7,28 @@
 namespace mdk {
 
 struct Plan {
-    int64_t N = 0;
-    Box box{};
+    int64_t N = 0;         // atoms (a pool: its atom capacity)
+    Box box{};             // box of the single system (pools: per-system boxes in `sys`)
     int kind = 0;          // 1 Tersoff, 2 SW
     int precision = 0;     // 0 fp64, 1 mixed
     int cap = 32;          // list capacity
     int maxa = 8;          // in-cutoff capacity (compact pair rows)
     double rc = 0, rl = 0, skin = 0;
-    TersoffP tp{};
-    SWP sp{};
+    float list_margin = 0.f;   // fp32 margin of the list build
+    // parameter sets (a single system uses set 0)
+    int n_sets = 1;
+    TersoffP tp[kMaxSets]{};
+    SWP sp[kMaxSets]{};
     int ntypes = 1;
     double mass[kMaxTypes] = {0, 0, 0, 0};
     double inv_mass[kMaxTypes] = {0, 0, 0, 0};
+
+    // pools: many systems over one flattened atom index
+    bool batch = false;        // kernels look up each atom's system
+    int n_sys = 1;             // system slots
+    int seg_max = 1;           // system segments one gather block can hold
+    int *sys_of = nullptr;     // N
+    SysDev *sys = nullptr;     // n_sys (device)
 
     // per-atom state (fp64)
     double *pos = nullptr, *vel = nullptr, *force = nullptr, *pos_build = nullptr;
@@ -30,9 +40,10 @@ struct Plan {
     int *nn = nullptr, *nl = nullptr;
     uint8_t *rev = nullptr;
     uint32_t *mask = nullptr;
+    int *ovf_count = nullptr, *ovf_list = nullptr;   // deferred atoms of the pair pass
     // pair arrays, element type double (fp64) or float (mixed)
     void *pd = nullptr, *pr = nullptr;
-    // cells
+    // cells (single system: nc; pools: per-system grids in `sys`)
     int nc[3] = {1, 1, 1};
     int64_t ncell = 1;
     int *cell_count = nullptr, *cell_start = nullptr, *cell_atoms = nullptr;
@@ -41,8 +52,8 @@ struct Plan {
     // reductions
     double *partials = nullptr;
     int nb_gather = 1;
-    double *totals = nullptr;   // kNumPartials
-    double *series = nullptr;   // rows of 5
+    double *totals = nullptr;   // n_sys x kNumPartials
+    double *series = nullptr;   // rows x n_sys x 5
     Flags *flags = nullptr;
 };
 
@@ -52,13 +63,15 @@ extern const char *kKernelClassNames[KC_COUNT];
 
 // neigh.cu
 int scan_block_elems();
-// fp32 safety margin added to rl in the list build (covers coordinate rounding).
-float list_margin(const Plan &p);
+// fp32 safety margin added to rl in the list build (covers coordinate rounding) for
+// coordinates up to lmax.
+float list_margin_for(double lmax, double rl);
 // Wrap positions, build the cell list, the sorted Verlet list (cutoff rl, entries with
-// image shifts) and the reverse-slot index; clears flags->rebuild.  Returns the number
-// of kernels launched.
+// image shifts) and the reverse-slot index, for every system whose rebuild is
+// requested (a single system: always); clears the requests.  Returns the number of
+// kernels launched.
 int launch_rebuild(const Plan &p, cudaStream_t s);
-// Set flags->rebuild if any atom moved more than skin/2 since the last build.
+// Request a rebuild where an atom moved more than skin/2 since the last build.
 void launch_displacement_check(const Plan &p, cudaStream_t s);
 // dst[3N] = positions wrapped into [0, L) on periodic axes.
 void launch_wrap_copy(const Plan &p, cudaStream_t s, double *dst);
@@ -68,16 +81,24 @@ size_t pair_smem_bytes(const Plan &p);
 void configure_kernels(const Plan &p);
 // Half-kick + drift + displacement check (first half of a velocity-Verlet step).
 void launch_kick_drift(const Plan &p, cudaStream_t s, const double *half_kick, double dt);
-// Start of a graph step: claim the series row and set the rebuild conditional from
+// Start of a step: claim the series row, reset the pair pass's deferred count, count
+// down per-system step budgets (pools) and set the rebuild conditional from
 // flags->rebuild (h may be null when the graph has no rebuild node).
 void launch_step_begin(const Plan &p, cudaStream_t s, const cudaGraphConditionalHandle *h);
-// Per-atom pair pass: U_i and dU_i/dr_ij for every in-cutoff neighbour.
-void launch_pair(const Plan &p, cudaStream_t s);
+// Zero the pair pass's deferred-atom count (force evaluations outside a step).
+void launch_pair_reset(const Plan &p, cudaStream_t s);
+// Per-atom pair pass: U_i and dU_i/dr_ij for every in-cutoff neighbour.  Two launches:
+// a pass whose shared-memory staging holds 4 bonds per atom (the crystals' common case),
+// which defers any atom with more to a list, and a pass over that list with the full
+// capacity.  Returns the number of kernels launched.
+int launch_pair(const Plan &p, cudaStream_t s);
 // Per-atom gather: F_i (Eq. 28), J_i (Eq. 30) and, for a force evaluation, W_i (Eq. 29)
-// and per-atom outputs; optional half-kick; block partial sums.
-void launch_gather(const Plan &p, cudaStream_t s, const double *half_kick, bool full_outputs);
+// and per-atom outputs; optional half-kick (and per-system damping); block partials.
+void launch_gather(const Plan &p, cudaStream_t s, const double *half_kick, double dt, bool full_outputs);
+int gather_block();
 int gather_blocks(int64_t N);
-// Fixed-order reduction of the gather's block partials into totals (and a series row).
+// Fixed-order reduction of the gather's block partials into per-system totals (and a
+// series row).
 void launch_reduce(const Plan &p, cudaStream_t s, bool full_outputs, bool record_series);
 
 }  // namespace mdk

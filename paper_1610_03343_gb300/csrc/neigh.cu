@@ -33,13 +33,26 @@ __device__ __forceinline__ int cell_coord(double x, int nc, double invL)
 }
 
 // Wrap coordinates on periodic axes into [0, L), keep an fp32 copy, bin into cells.
-__global__ void k_cell_count(int64_t N, double *pos, float *posf, Box box, int nc0, int nc1, int nc2,
-                             int *atom_cell, int *atom_rank, int *count)
+// Pools (BATCH): only atoms of systems with a rebuild request, each in its own grid.
+template <bool BATCH>
+__global__ void k_cell_count(int64_t N, double *pos, float *posf, Box box0, int nc0, int nc1, int nc2,
+                             const int *sys_of, const SysDev *sys, int *atom_cell, int *atom_rank,
+                             int *count)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
+    const Box *bp = &box0;
+    int nc[3] = {nc0, nc1, nc2};
+    long long off = 0;
+    if (BATCH) {
+        const SysDev &sd = sys[sys_of[i]];
+        if (!sd.rebuild) return;
+        bp = &sd.box;
+        nc[0] = sd.nc[0]; nc[1] = sd.nc[1]; nc[2] = sd.nc[2];
+        off = sd.cell_off;
+    }
+    const Box &box = *bp;
     int cc[3];
-    const int nc[3] = {nc0, nc1, nc2};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         double x = pos[a * N + i];
@@ -52,8 +65,8 @@ __global__ void k_cell_count(int64_t N, double *pos, float *posf, Box box, int n
         posf[a * N + i] = (float)x;
         cc[a] = cell_coord(x, nc[a], box.invL[a]);
     }
-    const int c = (cc[0] * nc1 + cc[1]) * nc2 + cc[2];
-    atom_cell[i] = c;
+    const long long c = off + (cc[0] * nc[1] + cc[1]) * nc[2] + cc[2];
+    atom_cell[i] = (int)c;
     atom_rank[i] = atomicAdd(&count[c], 1);
 }
 
@@ -144,11 +157,13 @@ __global__ void k_scan_add(int64_t n, int *out, const int *block_sums)
     if (idx < n) out[idx] += block_sums[idx / kScanElems];
 }
 
-__global__ void k_cell_fill(int64_t N, const int *atom_cell, const int *atom_rank,
-                            const int *cell_start, int *cell_atoms)
+template <bool BATCH>
+__global__ void k_cell_fill(int64_t N, const int *atom_cell, const int *atom_rank, const int *cell_start,
+                            int *cell_atoms, const int *sys_of, const SysDev *sys)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
+    if (BATCH && !sys[sys_of[i]].rebuild) return;
     cell_atoms[cell_start[atom_cell[i]] + atom_rank[i]] = (int)i;
 }
 
@@ -174,31 +189,44 @@ __device__ __forceinline__ int stencil_axis(int c, int nc, int periodic, int *ou
 // One thread per atom: search the distinct neighbouring cells and keep every j != i
 // with |r_ij| < rl + margin (fp32, minimum image), in ascending index order, each with
 // the image shift it was found at.  Snapshots the build positions for the skin test.
-__global__ void k_build_list(int64_t N, const double *pos, const float *posf, Box box, int nc0, int nc1,
-                             int nc2, const int *atom_cell, const int *cell_start, const int *cell_count,
-                             const int *cell_atoms, float rlm2, int cap, int *nn, int *nl,
-                             double *pos_build, Flags *flags)
+template <bool BATCH>
+__global__ void k_build_list(int64_t N, const double *pos, const float *posf, Box box0, int nc0, int nc1,
+                             int nc2, const int *sys_of, const SysDev *sys, const int *atom_cell,
+                             const int *cell_start, const int *cell_count, const int *cell_atoms, float rlm2,
+                             int cap, int *nn, int *nl, double *pos_build, Flags *flags)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
+    const Box *bp = &box0;
+    int nc[3] = {nc0, nc1, nc2};
+    long long off = 0;
+    if (BATCH) {
+        const SysDev &sd = sys[sys_of[i]];
+        if (!sd.rebuild) return;
+        bp = &sd.box;
+        nc[0] = sd.nc[0]; nc[1] = sd.nc[1]; nc[2] = sd.nc[2];
+        off = sd.cell_off;
+        rlm2 = sd.rlm2;
+    }
+    const Box &box = *bp;
     pos_build[i] = pos[i];
     pos_build[N + i] = pos[N + i];
     pos_build[2 * N + i] = pos[2 * N + i];
     const float xi = posf[i], yi = posf[N + i], zi = posf[2 * N + i];
     const float L0 = (float)box.L[0], L1 = (float)box.L[1], L2 = (float)box.L[2];
     const float iL0 = (float)box.invL[0], iL1 = (float)box.invL[1], iL2 = (float)box.invL[2];
-    const int c = atom_cell[i];
-    const int cz = c % nc2, cy = (c / nc2) % nc1, cx = c / (nc1 * nc2);
+    const int c = (int)(atom_cell[i] - off);
+    const int cz = c % nc[2], cy = (c / nc[2]) % nc[1], cx = c / (nc[1] * nc[2]);
     int ox[3], oy[3], oz[3];
-    const int nx = stencil_axis(cx, nc0, box.pbc[0], ox);
-    const int ny = stencil_axis(cy, nc1, box.pbc[1], oy);
-    const int nz = stencil_axis(cz, nc2, box.pbc[2], oz);
+    const int nx = stencil_axis(cx, nc[0], box.pbc[0], ox);
+    const int ny = stencil_axis(cy, nc[1], box.pbc[1], oy);
+    const int nz = stencil_axis(cz, nc[2], box.pbc[2], oz);
     int loc[kMaxListCap];
     int cnt = 0;
     for (int a = 0; a < nx; ++a)
         for (int b = 0; b < ny; ++b)
             for (int e = 0; e < nz; ++e) {
-                const int cc = (ox[a] * nc1 + oy[b]) * nc2 + oz[e];
+                const long long cc = off + (ox[a] * nc[1] + oy[b]) * nc[2] + oz[e];
                 const int s0 = cell_start[cc], s1 = s0 + cell_count[cc];
                 for (int q = s0; q < s1; ++q) {
                     const int j = cell_atoms[q];
@@ -233,10 +261,13 @@ __global__ void k_build_list(int64_t N, const double *pos, const float *posf, Bo
 }
 
 // rev[m N + i] = slot of i in the list of j = atom of nl[m N + i] (lists are symmetric).
-__global__ void k_build_rev(int64_t N, const int *nn, const int *nl, uint8_t *rev, Flags *flags)
+template <bool BATCH>
+__global__ void k_build_rev(int64_t N, const int *nn, const int *nl, uint8_t *rev, const int *sys_of,
+                            const SysDev *sys, Flags *flags)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
+    if (BATCH && !sys[sys_of[i]].rebuild) return;
     const int n = nn[i];
     for (int m = 0; m < n; ++m) {
         const int j = list_atom(nl[(int64_t)m * N + i]);
@@ -249,33 +280,51 @@ __global__ void k_build_rev(int64_t N, const int *nn, const int *nl, uint8_t *re
     }
 }
 
-__global__ void k_build_done(Flags *flags)
+// Clear the rebuild requests (pools: every system's, then the global one).
+template <bool BATCH>
+__global__ void k_build_done(int n_sys, SysDev *sys, Flags *flags)
 {
-    flags->rebuild = 0;
-    flags->n_rebuilds += 1;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (BATCH && s < n_sys && sys[s].rebuild) {
+        sys[s].rebuild = 0;
+        sys[s].built = 1;
+    }
+    if (s == 0) {
+        flags->rebuild = 0;
+        flags->n_rebuilds += 1;
+    }
 }
 
 // skin/2 test.  Positions are not wrapped between builds, so x - x_build is the true
 // displacement; the difference is taken in fp64 and squared in fp32.
+template <bool BATCH>
 __global__ void k_displacement(int64_t N, const double *pos, const double *pos_build, float half_skin2,
-                               Flags *flags)
+                               const int *sys_of, SysDev *sys, Flags *flags)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
+    if (BATCH && !sys[sys_of[i]].active) return;
+    if (BATCH) half_skin2 = sys[sys_of[i]].half_skin2;
     float d2 = 0.f;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const float d = (float)(pos[a * N + i] - pos_build[a * N + i]);
         d2 = fmaf(d, d, d2);
     }
-    if (!(d2 <= half_skin2)) flags->rebuild = 1;
+    if (!(d2 <= half_skin2)) {
+        flags->rebuild = 1;
+        if (BATCH) sys[sys_of[i]].rebuild = 1;
+    }
 }
 
 // Wrapped copy of the positions (for output): dst[3N] = pos wrapped into [0, L).
-__global__ void k_wrap_copy(int64_t N, const double *pos, double *dst, Box box)
+template <bool BATCH>
+__global__ void k_wrap_copy(int64_t N, const double *pos, double *dst, Box box0, const int *sys_of,
+                            const SysDev *sys)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
+    const Box &box = BATCH ? sys[sys_of[i]].box : box0;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         double x = pos[a * N + i];
@@ -294,38 +343,45 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 
 int scan_block_elems() { return kScanElems; }
 
-float list_margin(const Plan &p)
+float list_margin_for(double lmax, double rl)
 {
     // Bound on the fp32 error of a listed separation: coordinates below 2^e carry an
     // absolute rounding error of at most 2^(e-24); a difference, a shift by L and the
     // squared norm stay within a few of those units per component.
-    double lmax = 1.0;
-    for (int a = 0; a < 3; ++a) lmax = p.box.L[a] > lmax ? p.box.L[a] : lmax;
+    if (lmax < 1.0) lmax = 1.0;
     const double ulp = std::ldexp(1.0, std::ilogb(lmax) + 1 - 24);
-    return (float)(16.0 * ulp + 1e-6 * p.rl);
+    return (float)(16.0 * ulp + 1e-6 * rl);
+}
+
+template <bool B>
+int rebuild_impl(const Plan &p, cudaStream_t s)
+{
+    const int T = 256;
+    cudaMemsetAsync(p.cell_count, 0, sizeof(int) * p.ncell, s);
+    cudaMemsetAsync(&p.flags->max_nn, 0, sizeof(int), s);
+    k_cell_count<B><<<blocks_for(p.N, T), T, 0, s>>>(p.N, p.pos, p.posf, p.box, p.nc[0], p.nc[1], p.nc[2],
+                                                    p.sys_of, p.sys, p.atom_cell, p.atom_rank, p.cell_count);
+    const int64_t nb = (p.ncell + kScanElems - 1) / kScanElems;
+    k_scan_blocks<<<(unsigned)nb, kScanThreads, 0, s>>>(p.ncell, p.cell_count, p.cell_start, p.scan_blocks);
+    k_scan_sums<<<1, kScanThreads, 0, s>>>(nb, p.scan_blocks);
+    k_scan_add<<<blocks_for(p.ncell, T), T, 0, s>>>(p.ncell, p.cell_start, p.scan_blocks);
+    k_cell_fill<B><<<blocks_for(p.N, T), T, 0, s>>>(p.N, p.atom_cell, p.atom_rank, p.cell_start, p.cell_atoms,
+                                                   p.sys_of, p.sys);
+    const int TB = 128;
+    const float rlm = (float)p.rl + p.list_margin;
+    k_build_list<B><<<blocks_for(p.N, TB), TB, 0, s>>>(p.N, p.pos, p.posf, p.box, p.nc[0], p.nc[1], p.nc[2],
+                                                      p.sys_of, p.sys, p.atom_cell, p.cell_start,
+                                                      p.cell_count, p.cell_atoms, rlm * rlm, p.cap, p.nn,
+                                                      p.nl, p.pos_build, p.flags);
+    k_build_rev<B><<<blocks_for(p.N, T), T, 0, s>>>(p.N, p.nn, p.nl, p.rev, p.sys_of, p.sys, p.flags);
+    k_build_done<B><<<blocks_for(p.n_sys, T), T, 0, s>>>(p.n_sys, p.sys, p.flags);
+    return 8;
 }
 
 int launch_rebuild(const Plan &p, cudaStream_t s)
 {
     if (p.N == 0) return 0;
-    const int T = 256;
-    cudaMemsetAsync(p.cell_count, 0, sizeof(int) * p.ncell, s);
-    cudaMemsetAsync(&p.flags->max_nn, 0, sizeof(int), s);
-    k_cell_count<<<blocks_for(p.N, T), T, 0, s>>>(p.N, p.pos, p.posf, p.box, p.nc[0], p.nc[1], p.nc[2],
-                                                 p.atom_cell, p.atom_rank, p.cell_count);
-    const int64_t nb = (p.ncell + kScanElems - 1) / kScanElems;
-    k_scan_blocks<<<(unsigned)nb, kScanThreads, 0, s>>>(p.ncell, p.cell_count, p.cell_start, p.scan_blocks);
-    k_scan_sums<<<1, kScanThreads, 0, s>>>(nb, p.scan_blocks);
-    k_scan_add<<<blocks_for(p.ncell, T), T, 0, s>>>(p.ncell, p.cell_start, p.scan_blocks);
-    k_cell_fill<<<blocks_for(p.N, T), T, 0, s>>>(p.N, p.atom_cell, p.atom_rank, p.cell_start, p.cell_atoms);
-    const int TB = 128;
-    const float rlm = (float)p.rl + list_margin(p);
-    k_build_list<<<blocks_for(p.N, TB), TB, 0, s>>>(p.N, p.pos, p.posf, p.box, p.nc[0], p.nc[1], p.nc[2],
-                                                   p.atom_cell, p.cell_start, p.cell_count, p.cell_atoms,
-                                                   rlm * rlm, p.cap, p.nn, p.nl, p.pos_build, p.flags);
-    k_build_rev<<<blocks_for(p.N, T), T, 0, s>>>(p.N, p.nn, p.nl, p.rev, p.flags);
-    k_build_done<<<1, 1, 0, s>>>(p.flags);
-    return 8;
+    return p.batch ? rebuild_impl<true>(p, s) : rebuild_impl<false>(p, s);
 }
 
 void launch_displacement_check(const Plan &p, cudaStream_t s)
@@ -333,14 +389,22 @@ void launch_displacement_check(const Plan &p, cudaStream_t s)
     if (p.N == 0) return;
     const int T = 256;
     const double hs = 0.5 * p.skin;
-    k_displacement<<<blocks_for(p.N, T), T, 0, s>>>(p.N, p.pos, p.pos_build, (float)(hs * hs), p.flags);
+    if (p.batch)
+        k_displacement<true><<<blocks_for(p.N, T), T, 0, s>>>(p.N, p.pos, p.pos_build, (float)(hs * hs),
+                                                             p.sys_of, p.sys, p.flags);
+    else
+        k_displacement<false><<<blocks_for(p.N, T), T, 0, s>>>(p.N, p.pos, p.pos_build, (float)(hs * hs),
+                                                              p.sys_of, p.sys, p.flags);
 }
 
 void launch_wrap_copy(const Plan &p, cudaStream_t s, double *dst)
 {
     if (p.N == 0) return;
     const int T = 256;
-    k_wrap_copy<<<blocks_for(p.N, T), T, 0, s>>>(p.N, p.pos, dst, p.box);
+    if (p.batch)
+        k_wrap_copy<true><<<blocks_for(p.N, T), T, 0, s>>>(p.N, p.pos, dst, p.box, p.sys_of, p.sys);
+    else
+        k_wrap_copy<false><<<blocks_for(p.N, T), T, 0, s>>>(p.N, p.pos, dst, p.box, p.sys_of, p.sys);
 }
 
 }  // namespace mdk

@@ -45,10 +45,23 @@ class md_options(ctypes.Structure):
                 ("hbm_budget", ctypes.c_size_t), ("device", ctypes.c_int)]
 
 
+class md_batch_options(ctypes.Structure):
+    _fields_ = [("max_box", ctypes.c_double), ("cell_capacity", ctypes.c_int64)]
+
+
+class md_system(ctypes.Structure):
+    _fields_ = [("box", ctypes.c_double * 3), ("pbc", ctypes.c_int * 3), ("n_atoms", ctypes.c_int64),
+                ("types", ctypes.c_void_p), ("param_set", ctypes.c_int),
+                ("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("z", ctypes.c_void_p),
+                ("vx", ctypes.c_void_p), ("vy", ctypes.c_void_p), ("vz", ctypes.c_void_p),
+                ("n_steps", ctypes.c_int64), ("damp", ctypes.c_double)]
+
+
 class md_stats(ctypes.Structure):
     _fields_ = [("n_atoms", ctypes.c_int64), ("steps_done", ctypes.c_int64), ("n_rebuilds", ctypes.c_int64),
                 ("max_neigh_seen", ctypes.c_int), ("kernel_launches_per_step", ctypes.c_int),
-                ("kernel_launches_per_rebuild", ctypes.c_int), ("device_bytes", ctypes.c_size_t)]
+                ("kernel_launches_per_rebuild", ctypes.c_int), ("pair_deferred", ctypes.c_int),
+                ("device_bytes", ctypes.c_size_t)]
 
 
 _lock = threading.Lock()
@@ -56,7 +69,8 @@ _lib = None
 
 EXPORTS = ["md_default_options", "md_create", "md_set_positions", "md_set_velocities", "md_compute",
            "md_run", "md_get_state", "md_get_stats", "md_set_graph_mode", "md_set_profiling",
-           "md_kernel_times", "md_last_error", "md_destroy"]
+           "md_kernel_times", "md_batch_create", "md_batch_add", "md_batch_remove", "md_batch_status",
+           "md_batch_get_state", "md_last_error", "md_destroy"]
 
 
 def library_path() -> str:
@@ -90,6 +104,13 @@ def load(build_if_missing: bool = False):
         lib.md_kernel_times.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
                                         ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_int)]
+        lib.md_batch_create.argtypes = [ctypes.POINTER(P), ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                        ctypes.POINTER(md_params), ctypes.c_int, P,
+                                        ctypes.POINTER(md_batch_options), ctypes.POINTER(md_options)]
+        lib.md_batch_add.argtypes = [P, ctypes.POINTER(md_system), ctypes.POINTER(ctypes.c_int)]
+        lib.md_batch_remove.argtypes = [P, ctypes.c_int]
+        lib.md_batch_status.argtypes = [P, P, P, P]
+        lib.md_batch_get_state.argtypes = [P, ctypes.c_int, P, P]
         lib.md_last_error.argtypes = [P]
         lib.md_last_error.restype = ctypes.c_char_p
         lib.md_destroy.argtypes = [P]
@@ -199,6 +220,49 @@ def md_kernel_times(ctx):
     nout = ctypes.c_int()
     _check(lib, ctx, lib.md_kernel_times(ctx, k, names, n, ms, ctypes.byref(nout)))
     return {names[i].decode(): (int(n[i]), float(ms[i])) for i in range(nout.value)}
+
+
+def md_batch_create(atom_capacity, max_systems, kind, param_sets, masses_by_type,
+                    opt: md_options | None = None, max_box=0.0, cell_capacity=0):
+    lib = load()
+    arrs = [np.ascontiguousarray(p, dtype=np.float64) for p in param_sets]
+    sets = (md_params * len(arrs))(*[md_params(int(kind), 1, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+                                      for a in arrs])
+    masses = np.ascontiguousarray(masses_by_type, dtype=np.float64)
+    bo = md_batch_options(float(max_box), int(cell_capacity))
+    ctx = ctypes.c_void_p()
+    st = lib.md_batch_create(ctypes.byref(ctx), int(atom_capacity), int(max_systems), len(arrs), sets,
+                             len(masses), _ptr(masses), ctypes.byref(bo),
+                             ctypes.byref(opt) if opt is not None else None)
+    if st != MD_OK:
+        raise MDError(st, "md_batch_create failed")
+    return ctx
+
+
+def md_batch_add(ctx, system: md_system) -> int:
+    lib = load()
+    out = ctypes.c_int(-1)
+    _check(lib, ctx, lib.md_batch_add(ctx, ctypes.byref(system), ctypes.byref(out)))
+    return out.value
+
+
+def md_batch_remove(ctx, sys_id):
+    lib = load()
+    _check(lib, ctx, lib.md_batch_remove(ctx, int(sys_id)))
+
+
+def md_batch_status(ctx, max_systems):
+    lib = load()
+    active = np.zeros(max_systems, dtype=np.int32)
+    left = np.zeros(max_systems, dtype=np.int64)
+    tot = np.zeros((max_systems, 13))
+    _check(lib, ctx, lib.md_batch_status(ctx, _ptr(active), _ptr(left), _ptr(tot)))
+    return active, left, tot
+
+
+def md_batch_get_state(ctx, sys_id, x=None, v=None):
+    lib = load()
+    _check(lib, ctx, lib.md_batch_get_state(ctx, int(sys_id), _ptr(x), _ptr(v)))
 
 
 def md_last_error(ctx) -> str:
@@ -324,3 +388,76 @@ def from_inputs(sysm, precision=MD_FP64, **kw) -> System:
     if sysm.vel is not None:
         s.set_velocities(sysm.vel)
     return s
+
+
+class Pool:
+    """A pool context (many systems stepped together) with host I/O."""
+
+    def __init__(self, atom_capacity, max_systems, kind, param_sets, masses_by_type, precision=MD_FP64,
+                 skin=0.0, max_neigh=32, max_active=0, stream=None, max_box=0.0, cell_capacity=0):
+        opt = md_default_options()
+        opt.precision = precision
+        opt.skin = skin
+        opt.max_neigh = max_neigh
+        opt.max_active = max_active
+        opt.cuda_stream = stream
+        self.max_systems = int(max_systems)
+        self.ctx = md_batch_create(atom_capacity, max_systems, kind, param_sets, masses_by_type, opt,
+                                   max_box, cell_capacity)
+        self.n_atoms = {}
+
+    def add(self, pos, vel, box, pbc, param_set=0, types=None, n_steps=-1, damp=0.0) -> int:
+        pos = np.asarray(pos, dtype=np.float64)
+        n = pos.shape[0]
+        soa = np.ascontiguousarray(pos.T)
+        v = np.ascontiguousarray(np.zeros_like(pos).T if vel is None else np.asarray(vel, dtype=np.float64).T)
+        t = np.ascontiguousarray(np.zeros(n, np.int32) if types is None else types, dtype=np.int32)
+        sd = md_system()
+        sd.box = (ctypes.c_double * 3)(*[float(b) for b in box])
+        sd.pbc = (ctypes.c_int * 3)(*[int(b) for b in pbc])
+        sd.n_atoms = n
+        sd.types = t.ctypes.data
+        sd.param_set = int(param_set)
+        sd.x, sd.y, sd.z = soa[0].ctypes.data, soa[1].ctypes.data, soa[2].ctypes.data
+        sd.vx, sd.vy, sd.vz = v[0].ctypes.data, v[1].ctypes.data, v[2].ctypes.data
+        sd.n_steps = int(n_steps)
+        sd.damp = float(damp)
+        sid = md_batch_add(self.ctx, sd)
+        self.n_atoms[sid] = n
+        return sid
+
+    def remove(self, sid):
+        md_batch_remove(self.ctx, sid)
+        self.n_atoms.pop(sid, None)
+
+    def run(self, n_steps, dt, record=False):
+        series = np.zeros((max(n_steps, 1), self.max_systems, 5)) if record else None
+        md_run(self.ctx, n_steps, dt, series)
+        return series[:n_steps] if record else None
+
+    def status(self):
+        return md_batch_status(self.ctx, self.max_systems)
+
+    def state(self, sid):
+        n = self.n_atoms[sid]
+        x = np.empty(3 * n)
+        v = np.empty(3 * n)
+        md_batch_get_state(self.ctx, sid, x, v)
+        return x.reshape(3, n).T.copy(), v.reshape(3, n).T.copy()
+
+    def close(self):
+        if self.ctx:
+            md_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -415,3 +415,16 @@ def test_per_atom_force_virial_heat_current_brute_force(oracle, kind, params):
     # the per-atom virial is genuinely non-symmetric here, so orientation is pinned
     Wo = r["W"].reshape(n, 3, 3)
     assert np.abs(Wo - Wo.transpose(0, 2, 1)).max() > 1e-4 * np.abs(Wo).max()
+
+
+def test_damped_step_scales_velocities_after_the_second_half_kick(oracle):
+    """Damped relaxation (reading: v <- v (1 - gamma dt) after the second half-kick):
+    one damped step leaves positions unchanged and scales the undamped velocities."""
+    s = I.si_diamond_tersoff(n=2, jitter_amp=0.05)
+    p0, v0, _ = oracle.run(s.pos, s.vel, s.mass, s.box, s.pbc, s.kind, s.params, 1, 1.0)
+    p1, v1, _ = oracle.run(s.pos, s.vel, s.mass, s.box, s.pbc, s.kind, s.params, 1, 1.0, damp=0.01)
+    assert np.array_equal(p0, p1)
+    assert np.array_equal(v1, v0 * (1.0 - 0.01 * 1.0))
+    _, _, ser = oracle.run(s.pos, s.vel, s.mass, s.box, s.pbc, s.kind, s.params, 200, 1.0, damp=0.01)
+    e = ser[:, 0] + ser[:, 1]
+    assert e[-1] < e[0] - 0.5 * ser[0, 1]      # most of the kinetic energy is removed

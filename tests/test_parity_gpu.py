@@ -71,6 +71,20 @@ def test_compute_fp64_matches_oracle(md, name, make):
     compare_compute(md, make())
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_atoms_with_many_bonds_take_the_full_capacity_pass(md, precision):
+    """Jittered SW silicon puts up to 10 neighbours inside the cutoff: those atoms are
+    deferred by the 4-bond pass and computed by the full-capacity pass."""
+    s = I.si_diamond_sw(n=5, jitter_amp=0.1)
+    ref = O.compute(s.pos, s.box, s.pbc, s.kind, s.params, s.vel)
+    with md.from_inputs(s, precision=precision) as g:
+        out = g.compute()
+        st = g.stats()
+    assert st.pair_deferred > 10
+    tol = FP64_TOL if precision == 0 else MIXED_TOL
+    assert rel(out["F"], ref["F"]) < tol and rel(out["U"], ref["U"]) < tol
+
+
 @pytest.mark.parametrize("name,make", CASES[:6], ids=[c[0] for c in CASES[:6]])
 def test_compute_mixed_force_error(md, name, make):
     sysm = make()
