@@ -202,12 +202,77 @@ md_status md_batch_add(md_ctx *ctx, const md_system *sys, int *id);
 md_status md_batch_remove(md_ctx *ctx, int id);
 
 /* Per slot (max_systems entries each, any pointer may be NULL): active (1 running, 0
- * stopped, -1 empty slot), steps left, and totals (13 per slot: U, W(9), J(3) of the
- * last step or force evaluation). */
-md_status md_batch_status(md_ctx *ctx, int *active, int64_t *steps_left, double *totals);
+ * stopped, -1 empty slot), steps left, totals (13 per slot: U, W(9), J(3) of the last
+ * step or force evaluation) and kinetic energy K of the last step. */
+md_status md_batch_status(md_ctx *ctx, int *active, int64_t *steps_left, double *totals, double *kinetic);
 
 /* Positions (wrapped) and velocities of one system, each 3 n_atoms SoA. */
 md_status md_batch_get_state(md_ctx *ctx, int id, double *x, double *v);
+
+/* ---------------------------------------------------------------- serving -------
+ * A request loop over pools (continuous batching).  Jobs are submitted from any
+ * thread at any time; each potential kind has a pool driven by its own host thread,
+ * which admits queued jobs (first fit into the pool's free atom and cell ranges: the
+ * job's device footprint), steps all admitted jobs together in graph-replayed chunks,
+ * and harvests jobs whose step budget ran out on the device (final state copied into
+ * the job's output buffers, slot freed).  Jobs arriving while others run are admitted
+ * as slots free up; the pools of different kinds run on their own streams and overlap
+ * on the device.  A job's result equals that of the same system run alone. */
+typedef struct md_server md_server;
+
+typedef struct {
+    int precision;              /* MD_FP64 or MD_MIXED                                     */
+    int64_t tersoff_atoms;      /* atom capacity of the Tersoff pool (0: no Tersoff jobs)   */
+    int64_t sw_atoms;           /* atom capacity of the SW pool (0: no SW jobs)             */
+    int max_jobs_per_pool;      /* system slots per pool                                   */
+    double tersoff_dt, sw_dt;   /* time step of each pool (fs)                             */
+    int chunk_steps;            /* steps per scheduling round (default 8)                  */
+    int device;
+} md_server_options;
+
+typedef struct {
+    int kind;                   /* MD_TERSOFF or MD_SW                                     */
+    int param_set;              /* Tersoff: 0 = Si, 1 = C (md_server_create's sets); SW: 0  */
+    double box[3];
+    int pbc[3];
+    int64_t n_atoms;
+    const int32_t *types;       /* element indices (Tersoff: 0 Si, 1 C), copied at submit  */
+    const double *x, *y, *z, *vx, *vy, *vz;  /* host SoA arrays, copied at submit         */
+    int64_t n_steps;            /* >= 1                                                    */
+    double damp;                /* 0: NVE; > 0: damped relaxation                          */
+    double *x_out, *v_out;      /* host 3 n_atoms SoA buffers for the final state, or NULL;
+                                   must stay valid until the job is done                  */
+} md_job;
+
+typedef struct {
+    int done;                   /* 1 when finished (results written)                       */
+    int status;                 /* MD_OK, or the error that failed the job                 */
+    double t_submit, t_admit, t_done;  /* seconds on the server's monotonic clock          */
+    double U, K;                /* final potential and kinetic energy (eV)                 */
+} md_job_result;
+
+typedef struct {
+    int64_t submitted, admitted, completed, failed;
+    double atom_steps;          /* atom-steps of completed jobs                            */
+    double busy_seconds;        /* wall time with at least one job admitted                */
+} md_server_stats;
+
+/* tersoff_sets: 2 parameter sets (Si, C) and masses (Si, C); sw_set: 1 set, its mass. */
+md_status md_server_create(md_server **out, const md_server_options *opt, const md_params *tersoff_sets,
+                           const double *tersoff_masses, const md_params *sw_set, const double *sw_mass);
+/* Queue a job (thread-safe, returns at once); *job_id identifies it. */
+md_status md_server_submit(md_server *srv, const md_job *job, int64_t *job_id);
+/* Current state of a job (done = 0 while queued or running). */
+md_status md_server_poll(md_server *srv, int64_t job_id, md_job_result *out);
+/* Block until the job is done. */
+md_status md_server_wait(md_server *srv, int64_t job_id, md_job_result *out);
+/* Block until every submitted job is done. */
+md_status md_server_drain(md_server *srv);
+md_status md_server_stats_get(md_server *srv, md_server_stats *out);
+/* Seconds since md_server_create on the server's monotonic clock (the job timestamps). */
+double md_server_clock(const md_server *srv);
+/* Finishes the jobs already submitted, stops the pool threads and frees the pools. */
+void md_server_destroy(md_server *srv);
 
 /* Message of the last failing call (empty string if none).  Never NULL. */
 const char *md_last_error(const md_ctx *ctx);

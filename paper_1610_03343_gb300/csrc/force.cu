@@ -399,7 +399,7 @@ __device__ __forceinline__ void pair_dispatch(const PairArgs<T> &a, const Sets &
     auto one = [&](int64_t i) {
         if (BATCH) {
             const SysDev &sd = a.sys[a.sys_of[i]];
-            if (!sd.active) return;
+            if (!system_live(sd, a.flags)) return;
             fn(ps.s[sd.pset], sd.box, i);
         } else {
             fn(ps.s[0], a.box, i);
@@ -436,6 +436,15 @@ __global__ void __launch_bounds__(BLOCK) k_pair_sw(PairArgs<T> a, SWSets<T> ps)
 }
 
 __global__ void k_pair_reset(int *ovf_count) { *ovf_count = 0; }
+
+// End of the force evaluation that follows admissions: the new systems are no longer
+// fresh, and later evaluations cover every running system again.
+__global__ void k_clear_fresh(int n_sys, SysDev *sys, Flags *flags)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < n_sys) sys[s].fresh = 0;
+    if (s == 0) flags->fresh_only = 0;
+}
 
 // ------------------------------------------------------------------ gather
 // Block sums of NC per-thread fp64 values per system segment, in a fixed order:
@@ -490,7 +499,7 @@ __global__ void __launch_bounds__(BLOCK) k_gather(GatherArgs<T> a)
     double damp = 0.0;
     if (BATCH && live) {
         const SysDev &sd = a.sys[a.sys_of[i]];
-        live = sd.active != 0;
+        live = system_live(sd, a.flags);
         damp = sd.damp;
     }
     if (live) {
@@ -593,7 +602,7 @@ k_reduce(const double *partials, int nc, int seg_max, int64_t N, int block, cons
     if (BATCH) {
         a0 = sys[s].atom_start;
         na = sys[s].n_atoms;
-        ran = sys[s].active != 0 && na > 0;
+        ran = system_live(sys[s], flags) && na > 0;
         if (!ran) return;
     }
     const int64_t b0 = na > 0 ? a0 / block : 0, b1 = na > 0 ? (a0 + na - 1) / block : -1;
@@ -824,6 +833,11 @@ void launch_step_begin(const Plan &p, cudaStream_t s, const cudaGraphConditional
 }
 
 void launch_pair_reset(const Plan &p, cudaStream_t s) { k_pair_reset<<<1, 1, 0, s>>>(p.ovf_count); }
+
+void launch_clear_fresh(const Plan &p, cudaStream_t s)
+{
+    k_clear_fresh<<<(unsigned)((p.n_sys + 255) / 256), 256, 0, s>>>(p.n_sys, p.sys, p.flags);
+}
 
 template <bool BATCH>
 void pair_dispatch_launch(const Plan &p, cudaStream_t s)

@@ -453,7 +453,7 @@ md_status ensure_wj(md_ctx *ctx)
 // One force evaluation (not a time step): rebuild the list if any atom moved more than
 // skin/2 (checked on the host here; md_run decides on the device), then the pair pass,
 // the full gather (F, W, J per atom) and the totals.
-md_status force_eval(md_ctx *ctx, bool full)
+md_status force_eval(md_ctx *ctx, bool full, bool fresh_only = false)
 {
     if (full) {
         md_status s = ensure_wj(ctx);
@@ -461,6 +461,10 @@ md_status force_eval(md_ctx *ctx, bool full)
     }
     md_status s0 = clear_error_flags(ctx);
     if (s0 != MD_OK) return s0;
+    if (fresh_only) {
+        static const int one = 1;
+        CK(cudaMemcpyAsync(&ctx->p.flags->fresh_only, &one, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    }
     launch_displacement_check(ctx->p, ctx->stream);
     int rebuild = 0;
     CK(cudaMemcpyAsync(&rebuild, &ctx->p.flags->rebuild, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
@@ -470,6 +474,7 @@ md_status force_eval(md_ctx *ctx, bool full)
     launch_pair(ctx->p, ctx->stream);
     launch_gather(ctx->p, ctx->stream, nullptr, 0.0, full);
     launch_reduce(ctx->p, ctx->stream, full, false);
+    if (ctx->is_pool) launch_clear_fresh(ctx->p, ctx->stream);
     CK(cudaGetLastError());
     md_status s = check_flags(ctx);
     if (s != MD_OK) return s;
@@ -864,6 +869,7 @@ md_status md_batch_add(md_ctx *ctx, const md_system *sysd, int *id_out)
     sd.damp = sysd->damp;
     sd.active = sysd->n_steps == 0 ? 0 : 1;
     sd.rebuild = 1;
+    sd.fresh = 1;
     ctx->sys_host[id] = sd;
     ctx->sys_used[id] = 1;
     const cudaMemcpyKind k = ctx->io == MD_IO_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -916,7 +922,7 @@ md_status md_batch_remove(md_ctx *ctx, int id)
     return MD_OK;
 }
 
-md_status md_batch_status(md_ctx *ctx, int *active, int64_t *steps_left, double *totals)
+md_status md_batch_status(md_ctx *ctx, int *active, int64_t *steps_left, double *totals, double *kinetic)
 {
     if (!ctx) return MD_ERR_ARG;
     if (!ctx->is_pool) return fail(ctx, MD_ERR_STATE, "not a pool");
@@ -929,6 +935,7 @@ md_status md_batch_status(md_ctx *ctx, int *active, int64_t *steps_left, double 
         const bool used = ctx->sys_used[k] != 0;
         if (active) active[k] = used ? (ctx->sys_host[k].active ? 1 : 0) : -1;
         if (steps_left) steps_left[k] = used ? ctx->sys_host[k].steps_left : 0;
+        if (kinetic) kinetic[k] = t[(size_t)k * kNumPartials + 1];
         if (totals) {
             double *o = totals + (size_t)k * 13;
             const double *q = t.data() + (size_t)k * kNumPartials;
@@ -1026,8 +1033,8 @@ md_status md_run(md_ctx *ctx, int64_t n_steps, double dt_fs, double *series)
     if (n_steps == 0) return MD_OK;
     md_status s = ensure_series(ctx, n_steps);
     if (s != MD_OK) return s;
-    if (!ctx->forces_valid) {
-        s = force_eval(ctx, false);
+    if (!ctx->forces_valid) {   // pools: forces for the systems admitted since the last call
+        s = force_eval(ctx, false, ctx->is_pool);
         if (s != MD_OK) return s;
     }
     if (ctx->profiling) {

@@ -54,7 +54,7 @@ struct SysDev {
     int active;               // 1 while the system is stepped
     int rebuild;              // 1: rebuild this system's lists at the next rebuild
     int built;                // 1 once its lists exist
-    int pad;
+    int fresh;                // 1 until its first force evaluation (just admitted)
 };
 
 // Device status words written by kernels and read by the host after a call.
@@ -69,7 +69,16 @@ struct Flags {
     int pad;
     long long step;       // index of the next series row
     long long row;        // series row of the step in flight
+    int fresh_only;       // pools: the force evaluation in flight covers admitted systems only
+    int pad2;
 };
+
+// Pools: does atom work of system `sd` run now?  Stopped systems never; during the
+// force evaluation that follows admissions, only the newly admitted systems.
+__device__ __forceinline__ bool system_live(const SysDev &sd, const Flags *f)
+{
+    return sd.active != 0 && (f->fresh_only == 0 || sd.fresh != 0);
+}
 
 // Tersoff (single element).  Eqs. 2-6 with Tersoff-1989 f_R, f_A, f_C.
 struct TersoffP {

@@ -87,6 +87,8 @@ void launch_kick_drift(const Plan &p, cudaStream_t s, const double *half_kick, d
 void launch_step_begin(const Plan &p, cudaStream_t s, const cudaGraphConditionalHandle *h);
 // Zero the pair pass's deferred-atom count (force evaluations outside a step).
 void launch_pair_reset(const Plan &p, cudaStream_t s);
+// Pools: mark every system as no longer fresh and end a fresh-only evaluation.
+void launch_clear_fresh(const Plan &p, cudaStream_t s);
 // Per-atom pair pass: U_i and dU_i/dr_ij for every in-cutoff neighbour.  Two launches:
 // a pass whose shared-memory staging holds 4 bonds per atom (the crystals' common case),
 // which defers any atom with more to a list, and a pass over that list with the full

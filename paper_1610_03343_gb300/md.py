@@ -57,6 +57,32 @@ class md_system(ctypes.Structure):
                 ("n_steps", ctypes.c_int64), ("damp", ctypes.c_double)]
 
 
+class md_server_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("tersoff_atoms", ctypes.c_int64), ("sw_atoms", ctypes.c_int64),
+                ("max_jobs_per_pool", ctypes.c_int), ("tersoff_dt", ctypes.c_double), ("sw_dt", ctypes.c_double),
+                ("chunk_steps", ctypes.c_int), ("device", ctypes.c_int)]
+
+
+class md_job(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("param_set", ctypes.c_int), ("box", ctypes.c_double * 3),
+                ("pbc", ctypes.c_int * 3), ("n_atoms", ctypes.c_int64), ("types", ctypes.c_void_p),
+                ("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("z", ctypes.c_void_p),
+                ("vx", ctypes.c_void_p), ("vy", ctypes.c_void_p), ("vz", ctypes.c_void_p),
+                ("n_steps", ctypes.c_int64), ("damp", ctypes.c_double),
+                ("x_out", ctypes.c_void_p), ("v_out", ctypes.c_void_p)]
+
+
+class md_job_result(ctypes.Structure):
+    _fields_ = [("done", ctypes.c_int), ("status", ctypes.c_int), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double), ("U", ctypes.c_double),
+                ("K", ctypes.c_double)]
+
+
+class md_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("failed", ctypes.c_int64), ("atom_steps", ctypes.c_double), ("busy_seconds", ctypes.c_double)]
+
+
 class md_stats(ctypes.Structure):
     _fields_ = [("n_atoms", ctypes.c_int64), ("steps_done", ctypes.c_int64), ("n_rebuilds", ctypes.c_int64),
                 ("max_neigh_seen", ctypes.c_int), ("kernel_launches_per_step", ctypes.c_int),
@@ -70,7 +96,9 @@ _lib = None
 EXPORTS = ["md_default_options", "md_create", "md_set_positions", "md_set_velocities", "md_compute",
            "md_run", "md_get_state", "md_get_stats", "md_set_graph_mode", "md_set_profiling",
            "md_kernel_times", "md_batch_create", "md_batch_add", "md_batch_remove", "md_batch_status",
-           "md_batch_get_state", "md_last_error", "md_destroy"]
+           "md_batch_get_state", "md_server_create", "md_server_submit", "md_server_poll", "md_server_wait",
+           "md_server_drain", "md_server_stats_get", "md_server_clock", "md_server_destroy",
+           "md_last_error", "md_destroy"]
 
 
 def library_path() -> str:
@@ -109,14 +137,25 @@ def load(build_if_missing: bool = False):
                                         ctypes.POINTER(md_batch_options), ctypes.POINTER(md_options)]
         lib.md_batch_add.argtypes = [P, ctypes.POINTER(md_system), ctypes.POINTER(ctypes.c_int)]
         lib.md_batch_remove.argtypes = [P, ctypes.c_int]
-        lib.md_batch_status.argtypes = [P, P, P, P]
+        lib.md_batch_status.argtypes = [P, P, P, P, P]
         lib.md_batch_get_state.argtypes = [P, ctypes.c_int, P, P]
+        lib.md_server_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(md_server_options),
+                                         ctypes.POINTER(md_params), P, ctypes.POINTER(md_params), P]
+        lib.md_server_submit.argtypes = [P, ctypes.POINTER(md_job), ctypes.POINTER(ctypes.c_int64)]
+        lib.md_server_poll.argtypes = [P, ctypes.c_int64, ctypes.POINTER(md_job_result)]
+        lib.md_server_wait.argtypes = [P, ctypes.c_int64, ctypes.POINTER(md_job_result)]
+        lib.md_server_drain.argtypes = [P]
+        lib.md_server_stats_get.argtypes = [P, ctypes.POINTER(md_server_stats)]
+        lib.md_server_clock.argtypes = [P]
+        lib.md_server_clock.restype = ctypes.c_double
+        lib.md_server_destroy.argtypes = [P]
+        lib.md_server_destroy.restype = None
         lib.md_last_error.argtypes = [P]
         lib.md_last_error.restype = ctypes.c_char_p
         lib.md_destroy.argtypes = [P]
         lib.md_destroy.restype = None
         for f in EXPORTS:
-            if f not in ("md_last_error", "md_destroy"):
+            if f not in ("md_last_error", "md_destroy", "md_server_clock", "md_server_destroy"):
                 getattr(lib, f).restype = S
         _lib = lib
         return lib
@@ -256,13 +295,82 @@ def md_batch_status(ctx, max_systems):
     active = np.zeros(max_systems, dtype=np.int32)
     left = np.zeros(max_systems, dtype=np.int64)
     tot = np.zeros((max_systems, 13))
-    _check(lib, ctx, lib.md_batch_status(ctx, _ptr(active), _ptr(left), _ptr(tot)))
-    return active, left, tot
+    kin = np.zeros(max_systems)
+    _check(lib, ctx, lib.md_batch_status(ctx, _ptr(active), _ptr(left), _ptr(tot), _ptr(kin)))
+    return active, left, tot, kin
 
 
 def md_batch_get_state(ctx, sys_id, x=None, v=None):
     lib = load()
     _check(lib, ctx, lib.md_batch_get_state(ctx, int(sys_id), _ptr(x), _ptr(v)))
+
+
+def md_server_create(opt: md_server_options, tersoff_sets=None, tersoff_masses=None, sw_set=None, sw_mass=None):
+    lib = load()
+    keep = []
+
+    def sets(arrs, kind):
+        if arrs is None:
+            return None
+        a = [np.ascontiguousarray(p, dtype=np.float64) for p in arrs]
+        keep.extend(a)
+        return (md_params * len(a))(*[md_params(kind, 1, x.ctypes.data_as(ctypes.POINTER(ctypes.c_double))) for x in a])
+
+    ts = sets(tersoff_sets, MD_TERSOFF)
+    ss = sets(sw_set, MD_SW)
+    tm = None if tersoff_masses is None else np.ascontiguousarray(tersoff_masses, dtype=np.float64)
+    sm = None if sw_mass is None else np.ascontiguousarray(sw_mass, dtype=np.float64)
+    srv = ctypes.c_void_p()
+    st = lib.md_server_create(ctypes.byref(srv), ctypes.byref(opt), ts, _ptr(tm), ss, _ptr(sm))
+    if st != MD_OK:
+        raise MDError(st, "md_server_create failed")
+    return srv
+
+
+def md_server_submit(srv, job: md_job) -> int:
+    lib = load()
+    jid = ctypes.c_int64()
+    st = lib.md_server_submit(srv, ctypes.byref(job), ctypes.byref(jid))
+    if st != MD_OK:
+        raise MDError(st, "md_server_submit failed")
+    return jid.value
+
+
+def md_server_poll(srv, job_id) -> md_job_result:
+    r = md_job_result()
+    st = load().md_server_poll(srv, int(job_id), ctypes.byref(r))
+    if st != MD_OK:
+        raise MDError(st, "md_server_poll failed")
+    return r
+
+
+def md_server_wait(srv, job_id) -> md_job_result:
+    r = md_job_result()
+    st = load().md_server_wait(srv, int(job_id), ctypes.byref(r))
+    if st != MD_OK:
+        raise MDError(st, "md_server_wait failed")
+    return r
+
+
+def md_server_drain(srv):
+    st = load().md_server_drain(srv)
+    if st != MD_OK:
+        raise MDError(st, "md_server_drain failed")
+
+
+def md_server_stats_get(srv) -> md_server_stats:
+    s = md_server_stats()
+    load().md_server_stats_get(srv, ctypes.byref(s))
+    return s
+
+
+def md_server_clock(srv) -> float:
+    return load().md_server_clock(srv)
+
+
+def md_server_destroy(srv):
+    if srv:
+        load().md_server_destroy(srv)
 
 
 def md_last_error(ctx) -> str:
@@ -449,6 +557,72 @@ class Pool:
         if self.ctx:
             md_destroy(self.ctx)
             self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request loop (md_server_*) with host I/O."""
+
+    def __init__(self, precision=MD_MIXED, tersoff_atoms=0, sw_atoms=0, max_jobs_per_pool=512,
+                 tersoff_dt=0.5, sw_dt=1.0, chunk_steps=8, tersoff_sets=None, tersoff_masses=None,
+                 sw_set=None, sw_mass=None):
+        opt = md_server_options(int(precision), int(tersoff_atoms), int(sw_atoms), int(max_jobs_per_pool),
+                                float(tersoff_dt), float(sw_dt), int(chunk_steps), 0)
+        self.srv = md_server_create(opt, tersoff_sets, tersoff_masses, sw_set, sw_mass)
+        self._keep = {}
+
+    def submit(self, kind, pos, vel, box, pbc, n_steps, param_set=0, types=None, damp=0.0, want_state=True):
+        pos = np.asarray(pos, dtype=np.float64)
+        n = pos.shape[0]
+        soa = np.ascontiguousarray(pos.T)
+        v = np.ascontiguousarray(np.zeros_like(pos).T if vel is None else np.asarray(vel, dtype=np.float64).T)
+        t = np.ascontiguousarray(np.zeros(n, np.int32) if types is None else types, dtype=np.int32)
+        xo = np.empty(3 * n) if want_state else None
+        vo = np.empty(3 * n) if want_state else None
+        j = md_job()
+        j.kind, j.param_set = int(kind), int(param_set)
+        j.box = (ctypes.c_double * 3)(*[float(b) for b in box])
+        j.pbc = (ctypes.c_int * 3)(*[int(b) for b in pbc])
+        j.n_atoms, j.types = n, t.ctypes.data
+        j.x, j.y, j.z = soa[0].ctypes.data, soa[1].ctypes.data, soa[2].ctypes.data
+        j.vx, j.vy, j.vz = v[0].ctypes.data, v[1].ctypes.data, v[2].ctypes.data
+        j.n_steps, j.damp = int(n_steps), float(damp)
+        j.x_out = None if xo is None else xo.ctypes.data
+        j.v_out = None if vo is None else vo.ctypes.data
+        jid = md_server_submit(self.srv, j)
+        self._keep[jid] = (xo, vo, n)
+        return jid
+
+    def wait(self, jid):
+        r = md_server_wait(self.srv, jid)
+        xo, vo, n = self._keep.pop(jid)
+        state = None if xo is None else (xo.reshape(3, n).T.copy(), vo.reshape(3, n).T.copy())
+        return r, state
+
+    def drain(self):
+        md_server_drain(self.srv)
+
+    def stats(self):
+        return md_server_stats_get(self.srv)
+
+    def clock(self):
+        return md_server_clock(self.srv)
+
+    def close(self):
+        if self.srv:
+            md_server_destroy(self.srv)
+            self.srv = None
 
     def __enter__(self):
         return self

@@ -92,7 +92,7 @@ def test_step_budgets_stop_each_system_on_the_device(md):
         ids = [pool.add(s.pos, s.vel, s.box, s.pbc, pset, types_for(s), n_steps=b)
                for (s, pset, _), b in zip(mix, budgets)]
         pool.run(24, dt)
-        active, left, _ = pool.status()
+        active, left, _, _ = pool.status()
         for (s, pset, _), sid, b in zip(mix, ids, budgets):
             assert active[sid] == 0 and left[sid] == 0
             (p1, v1), _ = standalone(md, s, b, dt)
