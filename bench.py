@@ -190,6 +190,152 @@ def run_ours(args, rank, world):
     return n, dt, res, t_e2e, h2d, d2h, mixed_err
 
 
+# ---------------------------------------------------------------- batched pool
+def batch_systems(n_sys=512, lo=64, hi=20000, seed=11):
+    """512 Si diamond / C graphene cells, atom counts log-uniform in [64, 20000] snapped to
+    admissible lattices (total ~1.8M atoms), 300 K."""
+    out = []
+    for k, (kind, a, b, n) in enumerate(I.batch_sizes(n_sys, lo, hi, seed)):
+        if kind == "si_diamond":
+            s = I.si_diamond_tersoff(n=a, jitter_amp=0.05, seed_pos=1000 + k, seed_vel=2000 + k)
+            out.append((s, 0))
+        else:
+            s = I.c_graphene_tersoff(nx=a, ny=b, jitter_amp=0.02, seed_pos=1000 + k, seed_vel=2000 + k)
+            out.append((s, 1))
+    return out
+
+
+def run_batch(args, steps, warmup):
+    import torch
+    from paper_1610_03343_gb300 import md
+    systems = batch_systems()
+    cap = sum((s.n + 127) // 128 * 128 for s, _ in systems)
+    n_tot = sum(s.n for s, _ in systems)
+    out = {"n_systems": len(systems), "n_atoms": n_tot, "dt_fs": 0.5, "steps": steps}
+    stream = torch.cuda.Stream()
+    for prec, tag in ((md.MD_FP64, "fp64"), (md.MD_MIXED, "mixed")):
+        pool = md.Pool(cap, len(systems), I.MD_TERSOFF, [I.TERSOFF_SI_1989, I.TERSOFF_C_1989],
+                       [I.MASS_SI, I.MASS_C], precision=prec, stream=stream.cuda_stream)
+        for s, pset in systems:
+            pool.add(s.pos, s.vel, s.box, s.pbc, pset, np.full(s.n, pset, np.int32))
+        pool.run(warmup, 0.5)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pool.run(steps, 0.5)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[tag] = {"value": n_tot * steps / (ms / 1e3), "unit": "atom-steps/s", "ms_per_step": ms / steps}
+        pool.close()
+    return out
+
+
+# ---------------------------------------------------------------- serving
+class JobFactory:
+    """Serving jobs: Tersoff (Si or C) or SW (Si) cells, atom count log-uniform in
+    [64, 200000] snapped to a lattice, steps uniform in [100, 2000], NVE or damped
+    relaxation (gamma = 0.01 / fs), 300 K, seeded.  Lattices are cached by shape; every
+    job draws its own jitter and velocities."""
+
+    def __init__(self, seed=21):
+        self.rng = np.random.Generator(np.random.PCG64(seed))
+        self.cache = {}
+
+    def lattice(self, key):
+        if key not in self.cache:
+            kind, a, b = key
+            if kind == "gr":
+                self.cache[key] = I.graphene_positions(a, b, 1.42, 20.0)
+            else:
+                self.cache[key] = I.diamond_positions(a, 5.432 if kind == "si_t" else 5.431)
+        return self.cache[key]
+
+    def make(self, k):
+        r = self.rng
+        kind = I.MD_TERSOFF if r.random() < 0.5 else I.MD_SW
+        elem = (0 if r.random() < 0.5 else 1) if kind == I.MD_TERSOFF else 0
+        target = math.exp(r.uniform(math.log(64), math.log(200000)))
+        if elem == 1:
+            nx = max(3, int(round(math.sqrt(target / 4.0 / 1.732))))
+            ny = max(3, int(round(1.732 * nx)))
+            key = ("gr", nx, ny)
+        else:
+            n = max(2, int(round((target / 8.0) ** (1.0 / 3.0))))
+            key = ("si_t" if kind == I.MD_TERSOFF else "si_s", n, n)
+        pos0, box = self.lattice(key)
+        pbc = np.array([1, 1, 1], np.int32)
+        amp = 0.02 if elem == 1 else 0.05
+        pos = I.wrap(pos0 + r.uniform(-amp, amp, size=pos0.shape), box, pbc)
+        mass = I.MASS_C if elem == 1 else I.MASS_SI
+        vel = I.maxwell_boltzmann(pos.shape[0], mass, 300.0, int(r.integers(1 << 30)))
+        steps = int(r.integers(100, 2001))
+        damp = 0.01 if r.random() < 0.5 else 0.0
+        return dict(kind=kind, pset=elem, pos=pos, vel=vel, box=box, pbc=pbc, steps=steps, damp=damp,
+                    types=np.full(pos.shape[0], elem, np.int32))
+
+
+def run_serve(args):
+    """Poisson arrivals into the serving loop; a waiter thread collects results in
+    submission order (and releases each job's output buffers) while submission goes on."""
+    import queue
+    from paper_1610_03343_gb300 import md
+    rng = np.random.Generator(np.random.PCG64(31))
+    fac = JobFactory()
+    jobs = [fac.make(k) for k in range(args.serve_requests)]
+    sizes = [(j["pos"].shape[0], j["steps"]) for j in jobs]
+    gaps = rng.exponential(1.0 / args.serve_rate, size=len(jobs))
+    results = []
+    with md.Server(precision=md.MD_MIXED, tersoff_atoms=12_000_000, sw_atoms=6_000_000, max_jobs_per_pool=1024,
+                   tersoff_dt=0.5, sw_dt=1.0, chunk_steps=8, tersoff_sets=[I.TERSOFF_SI_1989, I.TERSOFF_C_1989],
+                   tersoff_masses=[I.MASS_SI, I.MASS_C], sw_set=[I.SW_SI_1985], sw_mass=[I.MASS_SI]) as srv:
+        q = queue.Queue()
+
+        def waiter():
+            while True:
+                jid = q.get()
+                if jid is None:
+                    return
+                results.append(srv.wait(jid)[0])
+
+        th = threading.Thread(target=waiter, daemon=True)
+        th.start()
+        t_next = time.perf_counter()
+        for k, gap in enumerate(gaps):
+            t_next += gap
+            while time.perf_counter() < t_next:
+                time.sleep(min(0.002, max(0.0, t_next - time.perf_counter())))
+            j = jobs[k]
+            q.put(srv.submit(j["kind"], j["pos"], j["vel"], j["box"], j["pbc"], j["steps"], j["pset"],
+                             j["types"], j["damp"], want_state=True))
+            jobs[k] = None   # the server holds its own copy
+        q.put(None)
+        th.join()
+        st = srv.stats()
+    lat = np.array([r.t_done - r.t_submit for r in results])
+    t0 = min(r.t_submit for r in results)
+    t1 = max(r.t_done for r in results)
+    work = sum(n * st_ for n, st_ in sizes)
+    return {"requests": len(sizes), "rate_per_s": args.serve_rate, "completed": int(st.completed),
+            "failed": int(st.failed), "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "mean_atoms": float(np.mean([n for n, _ in sizes])), "value": work / (t1 - t0), "unit": "atom-steps/s",
+            "offered": args.serve_rate * work / len(sizes), "precision": "mixed", "wall_s": t1 - t0}
+
+
+def mixed_force_error():
+    """Force error of the mixed path against the fp64 path on the serving job kinds."""
+    from paper_1610_03343_gb300 import md
+    worst = 0.0
+    for s in (I.si_diamond_tersoff(n=6), I.c_graphene_tersoff(nx=20, ny=30), I.si_diamond_sw(n=6, jitter_amp=0.05)):
+        f = []
+        for prec in (md.MD_FP64, md.MD_MIXED):
+            with md.from_inputs(s, precision=prec) as g:
+                f.append(g.compute(want=("f",))["F"])
+        worst = max(worst, float(np.abs(f[1] - f[0]).max() / np.abs(f[0]).max()))
+    return worst
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -202,6 +348,10 @@ def main():
     ap.add_argument("--precision", default="both", choices=["both", "fp64", "mixed"])
     ap.add_argument("--eager", action="store_true",
                     help="launch each kernel eagerly instead of replaying graphs (for profilers)")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -275,6 +425,11 @@ def main():
     if t_e2e is not None:
         out["e2e"] = {"value": world * n * args.steps / t_e2e, "unit": "atom-steps/s",
                       "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps}
+    if not args.no_batch:
+        out["batch"] = run_batch(args, max(8, args.steps // 2), args.warmup)
+    if not args.no_serve:
+        out["serve"] = run_serve(args)
+        out["serve"]["force_err_mixed_vs_fp64"] = mixed_force_error()
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args)
     print(json.dumps(out))

@@ -956,7 +956,7 @@ md_status md_batch_get_state(md_ctx *ctx, int id, double *x, double *v)
     const SysDev &sd = ctx->sys_host[id];
     const cudaMemcpyKind k = ctx->io == MD_IO_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (x) {
-        launch_wrap_copy(p, ctx->stream, p.stage);
+        launch_wrap_copy(p, ctx->stream, p.stage, sd.atom_start, sd.n_atoms);
         for (int c = 0; c < 3; ++c)
             CK(cudaMemcpyAsync(x + c * sd.n_atoms, p.stage + c * p.N + sd.atom_start, sizeof(double) * sd.n_atoms, k,
                                ctx->stream));
@@ -1100,7 +1100,7 @@ md_status md_get_state(md_ctx *ctx, double *x, double *v)
     md_status s;
     if (x && ctx->p.N > 0) {
         // positions move unwrapped between list builds; report them wrapped into the box
-        launch_wrap_copy(ctx->p, ctx->stream, ctx->p.stage);
+        launch_wrap_copy(ctx->p, ctx->stream, ctx->p.stage, 0, ctx->p.N);
         if ((s = download(ctx, x, ctx->p.stage, 3 * ctx->p.N)) != MD_OK) return s;
     }
     if ((s = download(ctx, v, ctx->p.vel, 3 * ctx->p.N)) != MD_OK) return s;

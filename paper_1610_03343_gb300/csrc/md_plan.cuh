@@ -73,8 +73,8 @@ float list_margin_for(double lmax, double rl);
 int launch_rebuild(const Plan &p, cudaStream_t s);
 // Request a rebuild where an atom moved more than skin/2 since the last build.
 void launch_displacement_check(const Plan &p, cudaStream_t s);
-// dst[3N] = positions wrapped into [0, L) on periodic axes.
-void launch_wrap_copy(const Plan &p, cudaStream_t s, double *dst);
+// dst[a N + i] = positions of atoms [a0, a0 + n) wrapped into [0, L) on periodic axes.
+void launch_wrap_copy(const Plan &p, cudaStream_t s, double *dst, int64_t a0, int64_t n);
 
 // force.cu
 size_t pair_smem_bytes(const Plan &p);

@@ -319,11 +319,11 @@ __global__ void k_displacement(int64_t N, const double *pos, const double *pos_b
 
 // Wrapped copy of the positions (for output): dst[3N] = pos wrapped into [0, L).
 template <bool BATCH>
-__global__ void k_wrap_copy(int64_t N, const double *pos, double *dst, Box box0, const int *sys_of,
-                            const SysDev *sys)
+__global__ void k_wrap_copy(int64_t N, int64_t a0, int64_t n, const double *pos, double *dst, Box box0,
+                            const int *sys_of, const SysDev *sys)
 {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
+    const int64_t i = a0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a0 + n) return;
     const Box &box = BATCH ? sys[sys_of[i]].box : box0;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -397,14 +397,14 @@ void launch_displacement_check(const Plan &p, cudaStream_t s)
                                                               p.sys_of, p.sys, p.flags);
 }
 
-void launch_wrap_copy(const Plan &p, cudaStream_t s, double *dst)
+void launch_wrap_copy(const Plan &p, cudaStream_t s, double *dst, int64_t a0, int64_t n)
 {
-    if (p.N == 0) return;
+    if (n <= 0) return;
     const int T = 256;
     if (p.batch)
-        k_wrap_copy<true><<<blocks_for(p.N, T), T, 0, s>>>(p.N, p.pos, dst, p.box, p.sys_of, p.sys);
+        k_wrap_copy<true><<<blocks_for(n, T), T, 0, s>>>(p.N, a0, n, p.pos, dst, p.box, p.sys_of, p.sys);
     else
-        k_wrap_copy<false><<<blocks_for(p.N, T), T, 0, s>>>(p.N, p.pos, dst, p.box, p.sys_of, p.sys);
+        k_wrap_copy<false><<<blocks_for(n, T), T, 0, s>>>(p.N, a0, n, p.pos, dst, p.box, p.sys_of, p.sys);
 }
 
 }  // namespace mdk
