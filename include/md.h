@@ -274,6 +274,37 @@ double md_server_clock(const md_server *srv);
 /* Finishes the jobs already submitted, stops the pool threads and frees the pools. */
 void md_server_destroy(md_server *srv);
 
+/* ------------------------------------------------------ allocation-free evaluation --
+ * The paper has no counterpart to this entry point; it exists for callers that cannot
+ * allocate device memory when they need forces (code running inside another runtime's
+ * allocator or memory-pool callback, plugins whose host forbids allocation after
+ * start-up, hosts that plan their whole device footprint in advance).
+ *
+ * md_compute_static is md_compute without a context: one force evaluation of one system
+ * (F, U, W, J per atom and the 13 totals, the same kernels and results), using as scratch
+ * a single file-scope device array of MD_STATIC_SCRATCH_BYTES that every GPU loading the
+ * library holds until the process exits.  It calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ *   - kind, params: as md_params (one element); mass in amu; precision MD_FP64/MD_MIXED.
+ *   - x, y, z: device arrays of n_atoms positions; vx, vy, vz: device velocities or NULL
+ *     (zero); f [3N], u [N], w [9N], j [3N]: device outputs, any may be NULL; totals: host
+ *     array of 13 (U, W, J) or NULL.  Runs on cuda_stream (NULL: the default stream) and
+ *     returns after synchronising it.
+ *   - Sizes: n_atoms <= MD_STATIC_MAX_ATOMS, else MD_ERR_OOM (no work done); MD_ERR_OOM
+ *     also when the cell grid would not fit (the grid is capped at 4 n + 64 cells).
+ *   - The first call on a device resolves the array's device address with that device
+ *     current; make that first call before any stream capture.
+ *   - Every call reuses the same array and it keeps the previous call's contents (each
+ *     call clears what must start at zero).  Calls that overlap on the GPU race on it:
+ *     serialise them. */
+#define MD_STATIC_SCRATCH_BYTES (16u << 20)
+#define MD_STATIC_MAX_ATOMS 12288
+md_status md_compute_static(int kind, const double *params, int precision, const double box[3],
+                            const int pbc[3], int64_t n_atoms, const double *x, const double *y,
+                            const double *z, const double *vx, const double *vy, const double *vz,
+                            double mass, double *f, double *u, double *w, double *j, double *totals,
+                            void *cuda_stream);
+
 /* Message of the last failing call (empty string if none).  Never NULL. */
 const char *md_last_error(const md_ctx *ctx);
 

@@ -98,7 +98,7 @@ EXPORTS = ["md_default_options", "md_create", "md_set_positions", "md_set_veloci
            "md_kernel_times", "md_batch_create", "md_batch_add", "md_batch_remove", "md_batch_status",
            "md_batch_get_state", "md_server_create", "md_server_submit", "md_server_poll", "md_server_wait",
            "md_server_drain", "md_server_stats_get", "md_server_clock", "md_server_destroy",
-           "md_last_error", "md_destroy"]
+           "md_compute_static", "md_last_error", "md_destroy"]
 
 
 def library_path() -> str:
@@ -150,6 +150,8 @@ def load(build_if_missing: bool = False):
         lib.md_server_clock.restype = ctypes.c_double
         lib.md_server_destroy.argtypes = [P]
         lib.md_server_destroy.restype = None
+        lib.md_compute_static.argtypes = [ctypes.c_int, P, ctypes.c_int, P, P, ctypes.c_int64, P, P, P, P, P, P,
+                                          ctypes.c_double, P, P, P, P, P, P]
         lib.md_last_error.argtypes = [P]
         lib.md_last_error.restype = ctypes.c_char_p
         lib.md_destroy.argtypes = [P]
@@ -371,6 +373,20 @@ def md_server_clock(srv) -> float:
 def md_server_destroy(srv):
     if srv:
         load().md_server_destroy(srv)
+
+
+def md_compute_static(kind, params, precision, box, pbc, n_atoms, x, y, z, vx, vy, vz, mass,
+                      f=None, u=None, w=None, j=None, totals=None, stream=None):
+    """Allocation-free force evaluation (device pointers / torch CUDA tensors in and out)."""
+    lib = load()
+    prm = np.ascontiguousarray(params, dtype=np.float64)
+    b = np.ascontiguousarray(box, dtype=np.float64)
+    pb = np.ascontiguousarray(pbc, dtype=np.int32)
+    st = lib.md_compute_static(int(kind), _ptr(prm), int(precision), _ptr(b), _ptr(pb), int(n_atoms),
+                               _ptr(x), _ptr(y), _ptr(z), _ptr(vx), _ptr(vy), _ptr(vz), float(mass),
+                               _ptr(f), _ptr(u), _ptr(w), _ptr(j), _ptr(totals), stream)
+    if st != MD_OK:
+        raise MDError(st, "md_compute_static failed")
 
 
 def md_last_error(ctx) -> str:
