@@ -227,7 +227,14 @@ def run_batch(args, steps, warmup):
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
-        out[tag] = {"value": n_tot * steps / (ms / 1e3), "unit": "atom-steps/s", "ms_per_step": ms / steps}
+        r0 = md.md_get_stats(pool.ctx).n_rebuilds
+        md.md_set_profiling(pool.ctx, True)
+        pool.run(min(steps, 40), 0.5)
+        kt = md.md_kernel_times(pool.ctx)
+        md.md_set_profiling(pool.ctx, False)
+        out[tag] = {"value": n_tot * steps / (ms / 1e3), "unit": "atom-steps/s", "ms_per_step": ms / steps,
+                    "kernel_ms_per_step": {k: (v[1] / v[0] if v[0] else None) for k, v in kt.items()},
+                    "rebuilds_per_step": (md.md_get_stats(pool.ctx).n_rebuilds - r0) / min(steps, 40)}
         pool.close()
     return out
 
@@ -320,7 +327,10 @@ def run_serve(args):
     return {"requests": len(sizes), "rate_per_s": args.serve_rate, "completed": int(st.completed),
             "failed": int(st.failed), "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
             "mean_atoms": float(np.mean([n for n, _ in sizes])), "value": work / (t1 - t0), "unit": "atom-steps/s",
-            "offered": args.serve_rate * work / len(sizes), "precision": "mixed", "wall_s": t1 - t0}
+            "offered": args.serve_rate * work / len(sizes), "precision": "mixed", "wall_s": t1 - t0,
+            "pool_seconds": {"busy": st.busy_seconds, "run": st.run_seconds, "admit": st.admit_seconds,
+                             "harvest": st.harvest_seconds, "chunks": int(st.chunks)},
+            "resident_atom_steps_per_run_s": st.resident_atom_steps / max(st.run_seconds, 1e-9)}
 
 
 def mixed_force_error():
@@ -352,6 +362,8 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--only", default="", choices=["", "batch", "serve"],
+                    help="run one leg alone and print its JSON (diagnostics)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -367,6 +379,16 @@ def main():
     if args.impl == "reference":
         if rank == 0:
             print(json.dumps(reference_arm(args)))
+        return
+    if args.only == "batch":
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps(run_batch(args, max(8, args.steps // 2), args.warmup)))
+        return
+    if args.only == "serve":
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps(run_serve(args)))
         return
 
     n, dt, res, t_e2e, h2d, d2h, mixed_err = run_ours(args, rank, world)

@@ -213,7 +213,9 @@ md_status md_batch_get_state(md_ctx *ctx, int id, double *x, double *v);
  * A request loop over pools (continuous batching).  Jobs are submitted from any
  * thread at any time; each potential kind has a pool driven by its own host thread,
  * which admits queued jobs (first fit into the pool's free atom and cell ranges: the
- * job's device footprint), steps all admitted jobs together in graph-replayed chunks,
+ * job's device footprint; a job that does not fit lets later jobs pass for up to half a
+ * second, then holds the queue until it fits), steps all admitted jobs together in
+ * graph-replayed chunks,
  * and harvests jobs whose step budget ran out on the device (final state copied into
  * the job's output buffers, slot freed).  Jobs arriving while others run are admitted
  * as slots free up; the pools of different kinds run on their own streams and overlap
@@ -254,7 +256,13 @@ typedef struct {
 typedef struct {
     int64_t submitted, admitted, completed, failed;
     double atom_steps;          /* atom-steps of completed jobs                            */
-    double busy_seconds;        /* wall time with at least one job admitted                */
+    double busy_seconds;        /* wall time with at least one job admitted (per pool, summed) */
+    double run_seconds;         /* time inside md_run chunks (per pool, summed)            */
+    double admit_seconds;       /* time admitting jobs                                     */
+    double harvest_seconds;     /* time reading back and removing finished jobs            */
+    int64_t chunks;             /* scheduling rounds                                       */
+    double resident_atom_steps; /* atoms resident in the pools x chunk steps (incl. jobs that
+                                   stopped inside a chunk)                                  */
 } md_server_stats;
 
 /* tersoff_sets: 2 parameter sets (Si, C) and masses (Si, C); sw_set: 1 set, its mass. */

@@ -22,6 +22,8 @@
 // Precision: T = double (fp64 path) or float (mixed path: per-pair arithmetic and
 // per-atom sums in fp32; bond vectors from fp64 positions; velocities, positions and
 // the block / system totals in fp64).
+#include <algorithm>
+
 #include "md_plan.cuh"
 
 namespace mdk {
@@ -29,6 +31,8 @@ namespace mdk {
 const char *kKernelClassNames[KC_COUNT] = {"kick_drift", "rebuild", "pair", "gather", "reduce"};
 
 namespace {
+
+constexpr int kPoolChunk = 128;   // pools place systems on 128-atom chunk boundaries
 
 // ---------------------------------------------------------------- precision
 template <typename T> struct M;
@@ -110,7 +114,7 @@ SWC<T> sw_const(const SWP &p)
 // pass: the atom is then appended to the deferred list and left to the full pass.
 // The cutoff decision is symmetric in i and j: the two fp64 differences are exact
 // negatives of each other, and so are their conversions.
-template <typename T, int CAP, int BLOCK, bool FULL_CAP>
+template <typename T, int CAP, int BLOCK, bool FULL_CAP, bool PREFILTER>
 __device__ __forceinline__ int collect_bonds(const PairArgs<T> &a, int64_t i, const Box &box, T rc2,
                                              uint32_t &mask, const Stage<T, CAP, BLOCK> &S, int fx, int fy,
                                              int fz, int fr2)
@@ -118,24 +122,59 @@ __device__ __forceinline__ int collect_bonds(const PairArgs<T> &a, int64_t i, co
     const int64_t N = a.N;
     const int S_ = a.stride;
     const double xi = a.pos[i], yi = a.pos[N + i], zi = a.pos[2 * N + i];
+    float fxi = 0.f, fyi = 0.f, fzi = 0.f, lim2 = 0.f;
+    if (PREFILTER) {
+        fxi = a.posf[i]; fyi = a.posf[N + i]; fzi = a.posf[2 * N + i];
+        // margin: the box-based bound plus the rounding of this atom's own coordinates,
+        // which on an open axis may lie far outside the box
+        const float mag = fmaxf(fabsf(fxi), fmaxf(fabsf(fyi), fabsf(fzi)));
+        const float lim = sqrtf((float)rc2) + a.margin + 32.f * mag * 1.1920929e-7f;
+        lim2 = lim * lim;
+    }
     const int nn = a.nn[i];
     int na = 0;
     mask = 0u;
     for (int m0 = 0; m0 < nn; m0 += 4) {
         int e[4];
+        bool keep[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) e[q] = (m0 + q < nn) ? a.nl[(int64_t)(m0 + q) * N + i] : 0;
+        for (int q = 0; q < 4; ++q) {
+            e[q] = (m0 + q < nn) ? a.nl[(int64_t)(m0 + q) * N + i] : 0;
+            keep[q] = m0 + q < nn;
+        }
+        if (PREFILTER) {
+            // fp32 distance from the step's fp32 positions: skips entries that are outside
+            // the cutoff by more than the fp32 rounding margin (exact: the fp64 test below
+            // would reject them too; symmetric: fp32 negation is exact)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (!keep[q]) continue;
+                const int j = list_atom(e[q]);
+                float dx = a.posf[j] - fxi, dy = a.posf[N + j] - fyi, dz = a.posf[2 * N + j] - fzi;
+                const int code = list_code(e[q]);
+                if (code != kNoShift) {
+                    const int sx = code % 3 - 1, sy = (code / 3) % 3 - 1, sz = code / 9 - 1;
+                    dx = fmaf((float)sx, (float)box.L[0], dx);
+                    dy = fmaf((float)sy, (float)box.L[1], dy);
+                    dz = fmaf((float)sz, (float)box.L[2], dz);
+                }
+                keep[q] = dx * dx + dy * dy + dz * dz < lim2;
+            }
+        }
         double px[4], py[4], pz[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int j = list_atom(e[q]);
-            px[q] = a.pos[j];
-            py[q] = a.pos[N + j];
-            pz[q] = a.pos[2 * N + j];
+            if (keep[q]) {
+                px[q] = a.pos[j];
+                py[q] = a.pos[N + j];
+                pz[q] = a.pos[2 * N + j];
+            }
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             if (m0 + q >= nn) break;
+            if (!keep[q]) continue;
             double dx = px[q] - xi, dy = py[q] - yi, dz = pz[q] - zi;
             const int code = list_code(e[q]);
             if (code != kNoShift) {
@@ -223,7 +262,7 @@ __device__ __forceinline__ void tersoff_atom(const PairArgs<T> &a, const Tersoff
     auto INV = [&](int q) -> T & { return sinv[q * BLOCK + threadIdx.x]; };
 
     uint32_t mask;
-    const int na = collect_bonds<T, CAP, BLOCK, FULL_CAP>(a, i, box, p.rc2, mask, S, TF_UX, TF_UY, TF_UZ, TF_IR);
+    const int na = collect_bonds<T, CAP, BLOCK, FULL_CAP, false>(a, i, box, p.rc2, mask, S, TF_UX, TF_UY, TF_UZ, TF_IR);
     if (na < 0) return;   // deferred to the full-capacity pass
 
     // per-bond radial functions (the staged vectors become unit vectors, r^2 -> 1/r)
@@ -322,7 +361,7 @@ __device__ __forceinline__ void sw_atom(const PairArgs<T> &a, const SWC<T> &p, c
     const int S_ = a.stride;
     Stage<T, CAP, BLOCK> S{base, (int)threadIdx.x};
     uint32_t mask;
-    const int na = collect_bonds<T, CAP, BLOCK, FULL_CAP>(a, i, box, p.rc2, mask, S, SW_UX, SW_UY, SW_UZ, SW_IR);
+    const int na = collect_bonds<T, CAP, BLOCK, FULL_CAP, true>(a, i, box, p.rc2, mask, S, SW_UX, SW_UY, SW_UZ, SW_IR);
     if (na < 0) return;
 
     T ui = T(0);
@@ -405,7 +444,12 @@ __device__ __forceinline__ void pair_dispatch(const PairArgs<T> &a, const Sets &
             fn(ps.s[0], a.box, i);
         }
     };
-    if (!FULL_CAP) {
+    if (!FULL_CAP && BATCH) {
+        // pools: loop over the live systems' 128-atom chunks
+        const int nch = *a.act_count;
+        for (int k = blockIdx.x; k < nch; k += gridDim.x)
+            for (int t = threadIdx.x; t < kPoolChunk; t += BLOCK) one((int64_t)a.act_chunks[k] + t);
+    } else if (!FULL_CAP) {
         const int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
         if (i < a.N) one(i);
     } else {
@@ -437,6 +481,46 @@ __global__ void __launch_bounds__(BLOCK) k_pair_sw(PairArgs<T> a, SWSets<T> ps)
 
 __global__ void k_pair_reset(int *ovf_count) { *ovf_count = 0; }
 
+// Pools: the 128-atom chunks of the systems that run now (stopped systems and free atom
+// ranges are skipped).  plan[0] = number of chunks.
+__global__ void __launch_bounds__(1024) k_active_plan(int n_sys, const SysDev *sys, const Flags *flags, int *plan,
+                                                      int *chunks)
+{
+    __shared__ int warp_b[32];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int s0 = 0; s0 < n_sys; s0 += blockDim.x) {
+        const int s = s0 + threadIdx.x;
+        const bool f = s < n_sys && system_live(sys[s], flags);
+        const int nch = f ? (int)((sys[s].n_atoms + kPoolChunk - 1) / kPoolChunk) : 0;
+        int b = nch;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, b, o);
+            if (lane >= o) b += y;
+        }
+        if (lane == 31) warp_b[wid] = b;
+        __syncthreads();
+        if (wid == 0) {
+            int w = lane < (int)(blockDim.x >> 5) ? warp_b[lane] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            warp_b[lane] = w;
+        }
+        __syncthreads();
+        const int pb = carry + (wid ? warp_b[wid - 1] : 0) + b - nch;
+        const long long a0 = f ? sys[s].atom_start : 0;
+        for (int k = 0; k < nch; ++k) chunks[pb + k] = (int)(a0 + (long long)k * kPoolChunk);
+        __syncthreads();
+        if (threadIdx.x == 0) carry += warp_b[(blockDim.x >> 5) - 1];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) plan[0] = carry;
+}
+
 // End of the force evaluation that follows admissions: the new systems are no longer
 // fresh, and later evaluations cover every running system again.
 __global__ void k_clear_fresh(int n_sys, SysDev *sys, Flags *flags)
@@ -453,7 +537,7 @@ __global__ void k_clear_fresh(int n_sys, SysDev *sys, Flags *flags)
 // system - system of the block's first atom); a single system has one segment.
 template <int BLOCK, int NC>
 __device__ __forceinline__ void block_partials(const double (&vals)[NC], int seg, int nseg, int seg_max,
-                                               double *out)
+                                               double *out, int64_t bidx)
 {
     static_assert(BLOCK == 128, "block_partials assumes 128 threads");
     __shared__ double red[NC][BLOCK];
@@ -476,18 +560,18 @@ __device__ __forceinline__ void block_partials(const double (&vals)[NC], int seg
             s += __shfl_xor_sync(grp, s, 4, 8);
             s += __shfl_xor_sync(grp, s, 2, 8);
             s += __shfl_xor_sync(grp, s, 1, 8);
-            if (sub == 0) out[((int64_t)blockIdx.x * seg_max + g) * NC + c] = s;
+            if (sub == 0) out[(bidx * seg_max + g) * NC + c] = s;
         }
     }
+    __syncthreads();   // the shared buffers are reused by the next chunk
 }
 
 // FULL: a force evaluation (per-atom F, W, J stored; U, K, J, W partials) or a
 // velocity-Verlet step (F and the kick only; U, K, J partials).
 template <typename T, int MAXA, int BLOCK, bool FULL, bool BATCH>
-__global__ void __launch_bounds__(BLOCK) k_gather(GatherArgs<T> a)
+__device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, int64_t bidx)
 {
     constexpr int NC = FULL ? kNumPartials : kStepPartials;
-    const int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
     const int64_t N = a.N;
     double vals[NC];
 #pragma unroll
@@ -582,14 +666,34 @@ __global__ void __launch_bounds__(BLOCK) k_gather(GatherArgs<T> a)
             }
         }
     }
-    block_partials<BLOCK, NC>(vals, seg, nseg, a.seg_max, a.partials);
+    block_partials<BLOCK, NC>(vals, seg, nseg, a.seg_max, a.partials, bidx);
 }
+
+// Single system: one thread per atom.  Pools: loop over the live systems' chunks (a
+// chunk is one gather block: every system starts on a chunk boundary).
+template <typename T, int MAXA, int BLOCK, bool FULL, bool BATCH>
+__global__ void __launch_bounds__(BLOCK) k_gather(GatherArgs<T> a)
+{
+    static_assert(BLOCK == kPoolChunk, "a gather block is one pool chunk");
+    if (BATCH) {
+        const int nch = *a.act_count;
+        for (int k = blockIdx.x; k < nch; k += gridDim.x) {
+            const int64_t c0 = a.act_chunks[k];
+            gather_atom<T, MAXA, BLOCK, FULL, BATCH>(a, c0 + threadIdx.x, c0 / BLOCK);
+        }
+    } else {
+        gather_atom<T, MAXA, BLOCK, FULL, BATCH>(a, (int64_t)blockIdx.x * BLOCK + threadIdx.x, blockIdx.x);
+    }
+}
+
+
 
 // One block per (system, component): that system's block partials of that component
 // added in a fixed order; totals[s NC_ALL + c] and, when recording,
 // series[(row n_sys + s) 5 + c].  Pools: a system that ran this step counts down its
 // step budget (component-0 block) and stops at zero.
-constexpr int kReduceThreads = 512;
+constexpr int kReduceThreads = 512;       // single system: thousands of blocks to add
+constexpr int kReduceThreadsPool = 128;   // pools: one reduction per system
 template <bool BATCH>
 __global__ void __launch_bounds__(kReduceThreads)
 k_reduce(const double *partials, int nc, int seg_max, int64_t N, int block, const int *sys_of, SysDev *sys,
@@ -607,7 +711,7 @@ k_reduce(const double *partials, int nc, int seg_max, int64_t N, int block, cons
     }
     const int64_t b0 = na > 0 ? a0 / block : 0, b1 = na > 0 ? (a0 + na - 1) / block : -1;
     double acc = 0.0;
-    for (int64_t b = b0 + threadIdx.x; b <= b1; b += kReduceThreads) {
+    for (int64_t b = b0 + threadIdx.x; b <= b1; b += blockDim.x) {
         const int seg = BATCH ? s - sys_of[b * block] : 0;
         acc += partials[(b * seg_max + seg) * nc + c];
     }
@@ -618,7 +722,7 @@ k_reduce(const double *partials, int nc, int seg_max, int64_t N, int block, cons
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
-        for (int w = 0; w < kReduceThreads / 32; ++w) t += red[w];
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
         totals[(int64_t)s * kNumPartials + c] = t;
         if (record && c < kStepPartials) series[(flags->row * n_sys + s) * kStepPartials + c] = t;
         if (BATCH && record && c == 0 && sys[s].steps_left > 0) {
@@ -631,6 +735,8 @@ k_reduce(const double *partials, int nc, int seg_max, int64_t N, int block, cons
 // ------------------------------------------------------------------ integrator
 struct KickDriftArgs {
     int64_t N;
+    float *posf;
+    const int *act_count, *act_chunks;
     const int *sys_of;
     SysDev *sys;
     double *pos, *vel;
@@ -645,9 +751,8 @@ struct KickDriftArgs {
 // v += F/m dt/2; x += v dt (no wrap: positions are wrapped when the list is rebuilt);
 // request a rebuild when an atom has moved more than skin/2 since the last build.
 template <bool BATCH>
-__global__ void k_kick_drift(KickDriftArgs a)
+__device__ __forceinline__ void kick_drift_atom(const KickDriftArgs &a, int64_t i)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.N) return;
     if (BATCH && !a.sys[a.sys_of[i]].active) return;
     const int64_t N = a.N;
@@ -659,6 +764,7 @@ __global__ void k_kick_drift(KickDriftArgs a)
         const double x = fma(a.dt, v, a.pos[c * N + i]);
         a.vel[c * N + i] = v;
         a.pos[c * N + i] = x;
+        a.posf[c * N + i] = (float)x;
         const float d = (float)(x - a.pos_build[c * N + i]);
         d2 = fmaf(d, d, d2);
     }
@@ -666,6 +772,18 @@ __global__ void k_kick_drift(KickDriftArgs a)
     if (!(d2 <= hs2)) {
         a.flags->rebuild = 1;
         if (BATCH) a.sys[a.sys_of[i]].rebuild = 1;
+    }
+}
+
+template <bool BATCH>
+__global__ void k_kick_drift(KickDriftArgs a)
+{
+    if (BATCH) {
+        const int nch = *a.act_count;
+        for (int k = blockIdx.x; k < nch; k += gridDim.x)
+            for (int t = threadIdx.x; t < kPoolChunk; t += blockDim.x) kick_drift_atom<true>(a, (int64_t)a.act_chunks[k] + t);
+    } else {
+        kick_drift_atom<false>(a, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
     }
 }
 
@@ -679,9 +797,14 @@ __global__ void k_step_begin(Flags *flags, int *ovf_count, cudaGraphConditionalH
 
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// Bounded grid of the pool kernels that loop over the chunk list.
+unsigned pool_grid(const Plan &p) { return (unsigned)std::min<int64_t>((p.N + kPoolChunk - 1) / kPoolChunk, 16 * 152); }
+
 constexpr int kPairBlockF64 = 64;
 constexpr int kPairBlockF32 = 128;
-constexpr int kPairCapSmall = 4;     // bonds staged per atom in the common-case pass
+constexpr int kPairCapSmall = 4;     // Tersoff: bonds staged per atom in the common-case pass
+constexpr int kPairCapSmallSW = 8;   // SW: its second shell sits just outside the cutoff, and at
+                                     // room temperature many atoms have 5-6 bonds inside it
 constexpr int kPairBlockFull = 32;   // full-capacity pass over the deferred atoms
 constexpr int kGatherBlock = 128;
 
@@ -709,6 +832,7 @@ template <typename T, bool BATCH>
 void configure_type()
 {
     set_smem<T, kPairCapSmall, pair_block<T>(), false, BATCH>();
+    set_smem<T, kPairCapSmallSW, pair_block<T>(), false, BATCH>();
     set_smem<T, 8, kPairBlockFull, true, BATCH>();
     set_smem<T, 16, kPairBlockFull, true, BATCH>();
 }
@@ -732,10 +856,14 @@ void pair_launch(const Plan &p, cudaStream_t s)
     a.sys = p.sys;
     a.ovf_count = p.ovf_count;
     a.ovf_list = p.ovf_list;
+    a.act_count = p.act_plan;
+    a.act_chunks = p.act_chunks;
+    a.posf = p.posf;
+    a.margin = p.list_margin;
     a.mask = p.mask;
     a.u = p.u;
     a.flags = p.flags;
-    const unsigned nb = blocks_for(p.N, B);
+    const unsigned nb = BATCH ? pool_grid(p) : blocks_for(p.N, B);
     int64_t nbf = (p.N + kPairBlockFull - 1) / kPairBlockFull;
     if (nbf > 4 * 152) nbf = 4 * 152;
     if (p.kind == 1) {
@@ -747,7 +875,7 @@ void pair_launch(const Plan &p, cudaStream_t s)
     } else {
         SWSets<T> c;
         for (int k = 0; k < kMaxSets; ++k) c.s[k] = sw_const<T>(p.sp[k < p.n_sets ? k : 0]);
-        k_pair_sw<T, kPairCapSmall, B, false, BATCH><<<nb, B, smem_for<T, kPairCapSmall, B>(2), s>>>(a, c);
+        k_pair_sw<T, kPairCapSmallSW, B, false, BATCH><<<nb, B, smem_for<T, kPairCapSmallSW, B>(2), s>>>(a, c);
         k_pair_sw<T, FULL, kPairBlockFull, true, BATCH>
             <<<(unsigned)nbf, kPairBlockFull, smem_for<T, FULL, kPairBlockFull>(2), s>>>(a, c);
     }
@@ -780,7 +908,9 @@ void gather_launch(const Plan &p, cudaStream_t s, const double *hk, double dt, b
     a.sys = p.sys;
     a.dt = dt;
     a.flags = p.flags;
-    const unsigned nb = blocks_for(p.N, kGatherBlock);
+    a.act_count = p.act_plan;
+    a.act_chunks = p.act_chunks;
+    const unsigned nb = BATCH ? pool_grid(p) : blocks_for(p.N, kGatherBlock);
     if (full)
         k_gather<T, MAXA, kGatherBlock, true, BATCH><<<nb, kGatherBlock, 0, s>>>(a);
     else
@@ -791,6 +921,9 @@ void gather_launch(const Plan &p, cudaStream_t s, const double *hk, double dt, b
 
 size_t pair_smem_bytes(const Plan &p)
 {
+    if (p.kind == 2)
+        return p.precision == 0 ? smem_for<double, kPairCapSmallSW, kPairBlockF64>(2)
+                                : smem_for<float, kPairCapSmallSW, kPairBlockF32>(2);
     if (p.precision == 0) return smem_for<double, kPairCapSmall, kPairBlockF64>(p.kind);
     return smem_for<float, kPairCapSmall, kPairBlockF32>(p.kind);
 }
@@ -817,13 +950,16 @@ void launch_kick_drift(const Plan &p, cudaStream_t s, const double *hk, double d
     a.vel = p.vel;
     a.force = p.force;
     a.pos_build = p.pos_build;
+    a.posf = p.posf;
     a.type = p.type;
     for (int t = 0; t < kMaxTypes; ++t) a.hk[t] = hk[t];
     a.dt = dt;
     const double hs = 0.5 * p.skin;
     a.half_skin2 = (float)(hs * hs);
     a.flags = p.flags;
-    if (p.batch) k_kick_drift<true><<<blocks_for(p.N, 256), 256, 0, s>>>(a);
+    a.act_count = p.act_plan;
+    a.act_chunks = p.act_chunks;
+    if (p.batch) k_kick_drift<true><<<pool_grid(p), kPoolChunk, 0, s>>>(a);
     else k_kick_drift<false><<<blocks_for(p.N, 256), 256, 0, s>>>(a);
 }
 
@@ -833,6 +969,12 @@ void launch_step_begin(const Plan &p, cudaStream_t s, const cudaGraphConditional
 }
 
 void launch_pair_reset(const Plan &p, cudaStream_t s) { k_pair_reset<<<1, 1, 0, s>>>(p.ovf_count); }
+
+void launch_active_plan(const Plan &p, cudaStream_t s)
+{
+    if (!p.batch) return;
+    k_active_plan<<<1, 1024, 0, s>>>(p.n_sys, p.sys, p.flags, p.act_plan, p.act_chunks);
+}
 
 void launch_clear_fresh(const Plan &p, cudaStream_t s)
 {
@@ -879,7 +1021,7 @@ void launch_reduce(const Plan &p, cudaStream_t s, bool full, bool record_series)
     const int nc = full ? kNumPartials : kStepPartials;
     const bool rec = record_series && p.series != nullptr;
     if (p.batch)
-        k_reduce<true><<<dim3(p.n_sys, nc), kReduceThreads, 0, s>>>(p.partials, nc, p.seg_max, p.N, kGatherBlock,
+        k_reduce<true><<<dim3(p.n_sys, nc), kReduceThreadsPool, 0, s>>>(p.partials, nc, p.seg_max, p.N, kGatherBlock,
                                                                     p.sys_of, p.sys, p.n_sys, p.totals, p.series,
                                                                     p.flags, rec);
     else

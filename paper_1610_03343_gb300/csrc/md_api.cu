@@ -334,6 +334,7 @@ md_status add_conditional_rebuild(md_ctx *ctx, cudaGraphConditionalHandle h)
 //   pair pass -> gather (+ half-kick) -> reduce (series row)
 md_status enqueue_step(md_ctx *ctx, const Recorder &rec, const double *hk, double dt, int *n_kernels)
 {
+    launch_active_plan(ctx->p, ctx->stream);
     rec.begin(KC_KICK_DRIFT);
     launch_kick_drift(ctx->p, ctx->stream, hk, dt);
     rec.end(KC_KICK_DRIFT);
@@ -361,7 +362,7 @@ md_status enqueue_step(md_ctx *ctx, const Recorder &rec, const double *hk, doubl
     launch_reduce(ctx->p, ctx->stream, false, true);
     rec.end(KC_REDUCE);
     // kernels launched every step; a taken rebuild adds the body's kernels
-    *n_kernels = ctx->p.N > 0 ? 6 : 2;
+    *n_kernels = (ctx->p.N > 0 ? 6 : 2) + (ctx->p.batch ? 1 : 0);
     return MD_OK;
 }
 
@@ -371,6 +372,7 @@ md_status enqueue_step(md_ctx *ctx, const Recorder &rec, const double *hk, doubl
 md_status eager_step(md_ctx *ctx, const double *hk, double dt)
 {
     Recorder rec{ctx, 0, false};
+    launch_active_plan(ctx->p, ctx->stream);
     rec.begin(KC_KICK_DRIFT);
     launch_kick_drift(ctx->p, ctx->stream, hk, dt);
     rec.end(KC_KICK_DRIFT);
@@ -471,6 +473,7 @@ md_status force_eval(md_ctx *ctx, bool full, bool fresh_only = false)
     CK(cudaStreamSynchronize(ctx->stream));
     if (rebuild) launch_rebuild(ctx->p, ctx->stream);
     launch_pair_reset(ctx->p, ctx->stream);
+    launch_active_plan(ctx->p, ctx->stream);
     launch_pair(ctx->p, ctx->stream);
     launch_gather(ctx->p, ctx->stream, nullptr, 0.0, full);
     launch_reduce(ctx->p, ctx->stream, full, false);
@@ -635,6 +638,11 @@ md_status ctx_alloc(md_ctx *ctx)
     AL(p.atom_rank, N1);
     p.nscanb = (p.ncell + scan_block_elems() - 1) / scan_block_elems();
     AL(p.scan_blocks, p.nscanb + 1);
+    AL(p.rb_plan, 2);
+    AL(p.rb_sys, (size_t)p.n_sys + 1);
+    AL(p.rb_chunks, N1 / 128 + 1);
+    AL(p.act_plan, 2);
+    AL(p.act_chunks, N1 / 128 + 1);
     p.nb_gather = gather_blocks(p.N);
     p.seg_max = 1;
     AL(p.partials, (size_t)p.nb_gather * kNumPartials);
@@ -652,6 +660,7 @@ md_status ctx_alloc(md_ctx *ctx)
     cudaMemsetAsync(p.mask, 0, sizeof(uint32_t) * N1, ctx->stream);
     cudaMemsetAsync(p.type, 0, sizeof(int) * N1, ctx->stream);
     cudaMemsetAsync(p.totals, 0, sizeof(double) * p.n_sys * kNumPartials, ctx->stream);
+    cudaMemsetAsync(p.act_plan, 0, sizeof(int) * 2, ctx->stream);
     return MD_OK;
 }
 

@@ -118,6 +118,10 @@ struct PairArgs {
     const SysDev *sys;      // system table (pools)
     int *ovf_count;         // atoms deferred by the small-capacity pass ...
     int *ovf_list;          // ... and their indices (capacity N)
+    const int *act_count;   // pools: number of live 128-atom chunks ...
+    const int *act_chunks;  // ... and their first atoms
+    const float *posf;      // fp32 positions of this step (prefilter of list entries)
+    float margin;           // fp32 rounding margin of that prefilter
     uint32_t *mask;         // N : bit m set <=> list slot m is inside the cutoff
     double *u;              // N : U_i
     Flags *flags;
@@ -146,6 +150,8 @@ struct GatherArgs {
     const int *sys_of;      // N: system of each atom (pools)
     const SysDev *sys;      // system table (pools)
     double dt;              // time step (damping)
+    const int *act_count;   // pools: live chunks (see PairArgs)
+    const int *act_chunks;
     Flags *flags;
 };
 

@@ -49,6 +49,8 @@ struct Plan {
     int *cell_count = nullptr, *cell_start = nullptr, *cell_atoms = nullptr;
     int *atom_cell = nullptr, *atom_rank = nullptr, *scan_blocks = nullptr;
     int64_t nscanb = 1;
+    int *rb_plan = nullptr, *rb_sys = nullptr, *rb_chunks = nullptr;   // pool rebuild work lists
+    int *act_plan = nullptr, *act_chunks = nullptr;   // pools: 128-atom chunks of the live systems
     // reductions
     double *partials = nullptr;
     int nb_gather = 1;
@@ -85,6 +87,9 @@ void launch_kick_drift(const Plan &p, cudaStream_t s, const double *half_kick, d
 // down per-system step budgets (pools) and set the rebuild conditional from
 // flags->rebuild (h may be null when the graph has no rebuild node).
 void launch_step_begin(const Plan &p, cudaStream_t s, const cudaGraphConditionalHandle *h);
+// Pools: list the 128-atom chunks of the systems that run now (kick, pair and gather loop
+// over this list, so a step costs in proportion to the atoms resident and running).
+void launch_active_plan(const Plan &p, cudaStream_t s);
 // Zero the pair pass's deferred-atom count (force evaluations outside a step).
 void launch_pair_reset(const Plan &p, cudaStream_t s);
 // Pools: mark every system as no longer fresh and end a fresh-only evaluation.

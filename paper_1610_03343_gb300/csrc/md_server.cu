@@ -30,6 +30,7 @@
 namespace {
 
 using Clock = std::chrono::steady_clock;
+constexpr double kHeadWait = 0.5;   // seconds a job that does not fit lets later ones pass
 
 struct Job {
     int64_t id = 0;
@@ -127,22 +128,28 @@ void runner(md_server *srv, int which)
     const int chunk = srv->opt.chunk_steps > 0 ? srv->opt.chunk_steps : 8;
     double busy_since = -1.0;
     for (;;) {
-        // admission (FIFO): admit while the queue's head fits
+        // admission: first fit over the queue in arrival order.  A job that does not fit
+        // yet (no free slot, or no contiguous range for its atoms in the fragmented pool)
+        // lets later jobs pass, unless it has waited longer than kHeadWait: then it
+        // blocks the queue until it fits, so large jobs are not starved.
         {
             std::unique_lock<std::mutex> lk(srv->mu);
             srv->cv_work.wait(lk, [&] { return srv->stop || !pr.queue.empty() || !pr.running.empty(); });
             if (srv->stop && pr.queue.empty() && pr.running.empty()) break;
-            while (!pr.queue.empty()) {
-                std::shared_ptr<Job> j = pr.queue.front();
+            for (size_t qi = 0; qi < pr.queue.size();) {
+                std::shared_ptr<Job> j = pr.queue[qi];
                 lk.unlock();
+                const double t_a = srv->now();
                 const md_status s = admit(srv, pr, j);
                 lk.lock();
+                srv->stats.admit_seconds += srv->now() - t_a;
                 if (s == MD_OK) {
-                    pr.queue.pop_front();
+                    pr.queue.erase(pr.queue.begin() + (long)qi);
                 } else if (s == MD_ERR_OOM && !pr.running.empty()) {
-                    break;   // wait for slots or memory to free up
+                    if (srv->now() - j->res.t_submit > kHeadWait) break;   // it waits; so do the rest
+                    ++qi;
                 } else {
-                    pr.queue.pop_front();   // can never fit, or invalid
+                    pr.queue.erase(pr.queue.begin() + (long)qi);   // can never fit, or invalid
                     lk.unlock();
                     finish(srv, j, s);
                     lk.lock();
@@ -151,8 +158,12 @@ void runner(md_server *srv, int which)
         }
         if (pr.running.empty()) continue;
         if (busy_since < 0) busy_since = srv->now();
+        const double t_run = srv->now();
+        double resident = 0;
+        for (auto &kv : pr.running) resident += (double)kv.second->n;
         md_status s = md_run(pr.ctx, chunk, pr.dt, nullptr);
         if (s == MD_OK) s = md_batch_status(pr.ctx, active.data(), left.data(), tot.data(), kin.data());
+        const double t_harvest = srv->now();
         if (s != MD_OK) {   // fail every running job of this pool
             for (auto &kv : pr.running) {
                 md_batch_remove(pr.ctx, kv.first);
@@ -173,10 +184,16 @@ void runner(md_server *srv, int which)
             pr.running.erase(slot);
             finish(srv, j, g);
         }
-        if (pr.running.empty() && busy_since >= 0) {
+        {
             std::lock_guard<std::mutex> lk(srv->mu);
-            srv->stats.busy_seconds += srv->now() - busy_since;
-            busy_since = -1.0;
+            srv->stats.run_seconds += t_harvest - t_run;
+            srv->stats.resident_atom_steps += resident * chunk;
+            srv->stats.harvest_seconds += srv->now() - t_harvest;
+            srv->stats.chunks += 1;
+            if (pr.running.empty() && busy_since >= 0) {
+                srv->stats.busy_seconds += srv->now() - busy_since;
+                busy_since = -1.0;
+            }
         }
     }
 }

@@ -16,6 +16,8 @@
 // apply the exact cutoff.  fp32 negation is exact, so the test is symmetric in i and j
 // and the lists stay symmetric.  Atom order inside a cell depends on atomic timing, but
 // each list is sorted by atom index, so the lists are deterministic.
+#include <algorithm>
+
 #include "md_plan.cuh"
 
 namespace mdk {
@@ -35,12 +37,10 @@ __device__ __forceinline__ int cell_coord(double x, int nc, double invL)
 // Wrap coordinates on periodic axes into [0, L), keep an fp32 copy, bin into cells.
 // Pools (BATCH): only atoms of systems with a rebuild request, each in its own grid.
 template <bool BATCH>
-__global__ void k_cell_count(int64_t N, double *pos, float *posf, Box box0, int nc0, int nc1, int nc2,
-                             const int *sys_of, const SysDev *sys, int *atom_cell, int *atom_rank,
-                             int *count)
+__device__ __forceinline__ void cell_count_atom(int64_t i, int64_t N, double *pos, float *posf, Box box0, int nc0,
+                                                int nc1, int nc2, const int *sys_of, const SysDev *sys,
+                                                int *atom_cell, int *atom_rank, int *count)
 {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
     const Box *bp = &box0;
     int nc[3] = {nc0, nc1, nc2};
     long long off = 0;
@@ -158,11 +158,10 @@ __global__ void k_scan_add(int64_t n, int *out, const int *block_sums)
 }
 
 template <bool BATCH>
-__global__ void k_cell_fill(int64_t N, const int *atom_cell, const int *atom_rank, const int *cell_start,
-                            int *cell_atoms, const int *sys_of, const SysDev *sys)
+__device__ __forceinline__ void cell_fill_atom(int64_t i, const int *atom_cell, const int *atom_rank,
+                                               const int *cell_start, int *cell_atoms, const int *sys_of,
+                                               const SysDev *sys)
 {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
     if (BATCH && !sys[sys_of[i]].rebuild) return;
     cell_atoms[cell_start[atom_cell[i]] + atom_rank[i]] = (int)i;
 }
@@ -190,13 +189,12 @@ __device__ __forceinline__ int stencil_axis(int c, int nc, int periodic, int *ou
 // with |r_ij| < rl + margin (fp32, minimum image), in ascending index order, each with
 // the image shift it was found at.  Snapshots the build positions for the skin test.
 template <bool BATCH>
-__global__ void k_build_list(int64_t N, const double *pos, const float *posf, Box box0, int nc0, int nc1,
-                             int nc2, const int *sys_of, const SysDev *sys, const int *atom_cell,
-                             const int *cell_start, const int *cell_count, const int *cell_atoms, float rlm2,
-                             int cap, int *nn, int *nl, double *pos_build, Flags *flags)
+__device__ __forceinline__ void build_list_atom(int64_t i, int64_t N, const double *pos, const float *posf,
+                                                Box box0, int nc0, int nc1, int nc2, const int *sys_of,
+                                                const SysDev *sys, const int *atom_cell, const int *cell_start,
+                                                const int *cell_count, const int *cell_atoms, float rlm2, int cap,
+                                                int *nn, int *nl, double *pos_build, Flags *flags)
 {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
     const Box *bp = &box0;
     int nc[3] = {nc0, nc1, nc2};
     long long off = 0;
@@ -213,6 +211,11 @@ __global__ void k_build_list(int64_t N, const double *pos, const float *posf, Bo
     pos_build[N + i] = pos[N + i];
     pos_build[2 * N + i] = pos[2 * N + i];
     const float xi = posf[i], yi = posf[N + i], zi = posf[2 * N + i];
+    // The box-based margin is widened, per pair, by the rounding of the larger of the two
+    // atoms' coordinates (on an open axis atoms may lie far outside the box); taking the
+    // larger of the two keeps the test symmetric in i and j.
+    const float rl0 = sqrtf(rlm2);
+    const float mag_i = fmaxf(fabsf(xi), fmaxf(fabsf(yi), fabsf(zi)));
     const float L0 = (float)box.L[0], L1 = (float)box.L[1], L2 = (float)box.L[2];
     const float iL0 = (float)box.invL[0], iL1 = (float)box.invL[1], iL2 = (float)box.invL[2];
     const int c = (int)(atom_cell[i] - off);
@@ -239,7 +242,9 @@ __global__ void k_build_list(int64_t N, const double *pos, const float *posf, Bo
                     dx = fmaf(sx, L0, dx);
                     dy = fmaf(sy, L1, dy);
                     dz = fmaf(sz, L2, dz);
-                    if (dx * dx + dy * dy + dz * dz < rlm2) {
+                    const float mag = fmaxf(mag_i, fmaxf(fabsf(posf[j]), fmaxf(fabsf(posf[N + j]), fabsf(posf[2 * N + j]))));
+                    const float lim = rl0 + 32.f * mag * 1.1920929e-7f;
+                    if (dx * dx + dy * dy + dz * dz < lim * lim) {
                         const int e_ = list_entry(j, (int)sx, (int)sy, (int)sz);
                         if (cnt < cap) {       // insertion into the index-sorted prefix
                             int m = cnt;
@@ -262,11 +267,9 @@ __global__ void k_build_list(int64_t N, const double *pos, const float *posf, Bo
 
 // rev[m N + i] = slot of i in the list of j = atom of nl[m N + i] (lists are symmetric).
 template <bool BATCH>
-__global__ void k_build_rev(int64_t N, const int *nn, const int *nl, uint8_t *rev, const int *sys_of,
-                            const SysDev *sys, Flags *flags)
+__device__ __forceinline__ void build_rev_atom(int64_t i, int64_t N, const int *nn, const int *nl, uint8_t *rev,
+                                               const int *sys_of, const SysDev *sys, Flags *flags)
 {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
     if (BATCH && !sys[sys_of[i]].rebuild) return;
     const int n = nn[i];
     for (int m = 0; m < n; ++m) {
@@ -278,6 +281,191 @@ __global__ void k_build_rev(int64_t N, const int *nn, const int *nl, uint8_t *re
         if (found < 0) { flags->asym = 1; found = 0; }
         rev[(int64_t)m * N + i] = (uint8_t)found;
     }
+}
+
+// Single system: one thread per atom.
+__global__ void k_cell_count(int64_t N, double *pos, float *posf, Box box, int nc0, int nc1, int nc2,
+                             int *atom_cell, int *atom_rank, int *count)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) cell_count_atom<false>(i, N, pos, posf, box, nc0, nc1, nc2, nullptr, nullptr, atom_cell, atom_rank, count);
+}
+__global__ void k_cell_fill(int64_t N, const int *atom_cell, const int *atom_rank, const int *cell_start,
+                            int *cell_atoms)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) cell_fill_atom<false>(i, atom_cell, atom_rank, cell_start, cell_atoms, nullptr, nullptr);
+}
+__global__ void k_build_list(int64_t N, const double *pos, const float *posf, Box box, int nc0, int nc1, int nc2,
+                             const int *atom_cell, const int *cell_start, const int *cell_count,
+                             const int *cell_atoms, float rlm2, int cap, int *nn, int *nl, double *pos_build,
+                             Flags *flags)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N)
+        build_list_atom<false>(i, N, pos, posf, box, nc0, nc1, nc2, nullptr, nullptr, atom_cell, cell_start,
+                               cell_count, cell_atoms, rlm2, cap, nn, nl, pos_build, flags);
+}
+__global__ void k_build_rev(int64_t N, const int *nn, const int *nl, uint8_t *rev, Flags *flags)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) build_rev_atom<false>(i, N, nn, nl, rev, nullptr, nullptr, flags);
+}
+
+// Pools: a rebuild touches only the systems that requested one.  The plan kernel lists
+// them and their 128-atom chunks (every system starts on a chunk boundary); the other
+// kernels loop over those lists with a bounded grid, so a rebuild costs in proportion
+// to the systems rebuilt, not to the pool's capacity.
+//   plan[0] = number of chunks, plan[1] = number of systems;
+//   chunks[k] = first atom of chunk k; rsys[k] = k-th system to rebuild.
+constexpr int kChunk = 128;
+__global__ void __launch_bounds__(1024) k_rebuild_plan(int n_sys, const SysDev *sys, int *plan, int *rsys,
+                                                       int *chunks)
+{
+    __shared__ int warp_a[32], warp_b[32];
+    __shared__ int carry_a, carry_b;
+    if (threadIdx.x == 0) { carry_a = 0; carry_b = 0; }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int s0 = 0; s0 < n_sys; s0 += blockDim.x) {
+        const int s = s0 + threadIdx.x;
+        const bool f = s < n_sys && sys[s].rebuild;
+        const int nch = f ? (int)((sys[s].n_atoms + kChunk - 1) / kChunk) : 0;
+        int a = f ? 1 : 0, b = nch;          // inclusive scans of flags and chunk counts
+        for (int o = 1; o < 32; o <<= 1) {
+            const int ya = __shfl_up_sync(0xffffffffu, a, o), yb = __shfl_up_sync(0xffffffffu, b, o);
+            if (lane >= o) { a += ya; b += yb; }
+        }
+        if (lane == 31) { warp_a[wid] = a; warp_b[wid] = b; }
+        __syncthreads();
+        if (wid == 0) {
+            int wa = lane < (int)(blockDim.x >> 5) ? warp_a[lane] : 0, wb = lane < (int)(blockDim.x >> 5) ? warp_b[lane] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int ya = __shfl_up_sync(0xffffffffu, wa, o), yb = __shfl_up_sync(0xffffffffu, wb, o);
+                if (lane >= o) { wa += ya; wb += yb; }
+            }
+            warp_a[lane] = wa;
+            warp_b[lane] = wb;
+        }
+        __syncthreads();
+        const int pa = carry_a + (wid ? warp_a[wid - 1] : 0) + a - (f ? 1 : 0);
+        const int pb = carry_b + (wid ? warp_b[wid - 1] : 0) + b - nch;
+        if (f) {
+            rsys[pa] = s;
+            const long long a0 = sys[s].atom_start;
+            for (int k = 0; k < nch; ++k) chunks[pb + k] = (int)(a0 + (long long)k * kChunk);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            carry_a += warp_a[(blockDim.x >> 5) - 1];
+            carry_b += warp_b[(blockDim.x >> 5) - 1];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        plan[0] = carry_b;
+        plan[1] = carry_a;
+    }
+}
+
+// Zero the cell counts of the systems being rebuilt (one system per block iteration).
+__global__ void k_cells_clear_pool(const int *plan, const int *rsys, const SysDev *sys, int *count)
+{
+    for (int k = blockIdx.x; k < plan[1]; k += gridDim.x) {
+        const SysDev &sd = sys[rsys[k]];
+        const long long nc = (long long)sd.nc[0] * sd.nc[1] * sd.nc[2];
+        for (long long c = threadIdx.x; c < nc; c += blockDim.x) count[sd.cell_off + c] = 0;
+    }
+}
+
+// Exclusive scan of each rebuilt system's cell counts, offset by its first atom (its
+// atoms fill cell_atoms[atom_start, atom_start + n_atoms) in cell order).  One block per
+// system: 1024 threads x 8 cells per pass.
+constexpr int kPoolScanThreads = 1024;
+constexpr int kPoolScanPer = 8;
+__global__ void __launch_bounds__(kPoolScanThreads) k_cells_scan_pool(const int *plan, const int *rsys,
+                                                                      const SysDev *sys, const int *count,
+                                                                      int *start)
+{
+    __shared__ int warp_tot[32];
+    __shared__ int carry;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int k = blockIdx.x; k < plan[1]; k += gridDim.x) {
+        const SysDev &sd = sys[rsys[k]];
+        const long long nc = (long long)sd.nc[0] * sd.nc[1] * sd.nc[2];
+        if (threadIdx.x == 0) carry = (int)sd.atom_start;
+        __syncthreads();
+        for (long long c0 = 0; c0 < nc; c0 += (long long)kPoolScanThreads * kPoolScanPer) {
+            const long long cb = c0 + (long long)threadIdx.x * kPoolScanPer;
+            int v[kPoolScanPer];
+            int t = 0;
+#pragma unroll
+            for (int q = 0; q < kPoolScanPer; ++q) {
+                v[q] = cb + q < nc ? count[sd.cell_off + cb + q] : 0;
+                t += v[q];
+            }
+            int incl = t;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            if (lane == 31) warp_tot[wid] = incl;
+            __syncthreads();
+            if (wid == 0) {
+                int w = warp_tot[lane];
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, w, o);
+                    if (lane >= o) w += y;
+                }
+                warp_tot[lane] = w;
+            }
+            __syncthreads();
+            int run = carry + (wid ? warp_tot[wid - 1] : 0) + incl - t;
+#pragma unroll
+            for (int q = 0; q < kPoolScanPer; ++q) {
+                if (cb + q < nc) start[sd.cell_off + cb + q] = run;
+                run += v[q];
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) carry += warp_tot[31];
+            __syncthreads();
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kChunk) k_cell_count_pool(const int *plan, const int *chunks, int64_t N,
+                                                            double *pos, float *posf, const int *sys_of,
+                                                            const SysDev *sys, int *atom_cell, int *atom_rank,
+                                                            int *count)
+{
+    for (int k = blockIdx.x; k < plan[0]; k += gridDim.x)
+        cell_count_atom<true>(chunks[k] + threadIdx.x, N, pos, posf, Box{}, 1, 1, 1, sys_of, sys, atom_cell,
+                              atom_rank, count);
+}
+__global__ void __launch_bounds__(kChunk) k_cell_fill_pool(const int *plan, const int *chunks, const int *atom_cell,
+                                                           const int *atom_rank, const int *cell_start,
+                                                           int *cell_atoms, const int *sys_of, const SysDev *sys)
+{
+    for (int k = blockIdx.x; k < plan[0]; k += gridDim.x)
+        cell_fill_atom<true>(chunks[k] + threadIdx.x, atom_cell, atom_rank, cell_start, cell_atoms, sys_of, sys);
+}
+__global__ void __launch_bounds__(kChunk) k_build_list_pool(const int *plan, const int *chunks, int64_t N,
+                                                            const double *pos, const float *posf,
+                                                            const int *sys_of, const SysDev *sys,
+                                                            const int *atom_cell, const int *cell_start,
+                                                            const int *cell_count, const int *cell_atoms, int cap,
+                                                            int *nn, int *nl, double *pos_build, Flags *flags)
+{
+    for (int k = blockIdx.x; k < plan[0]; k += gridDim.x)
+        build_list_atom<true>(chunks[k] + threadIdx.x, N, pos, posf, Box{}, 1, 1, 1, sys_of, sys, atom_cell,
+                              cell_start, cell_count, cell_atoms, 0.f, cap, nn, nl, pos_build, flags);
+}
+__global__ void __launch_bounds__(kChunk) k_build_rev_pool(const int *plan, const int *chunks, int64_t N,
+                                                           const int *nn, const int *nl, uint8_t *rev,
+                                                           const int *sys_of, const SysDev *sys, Flags *flags)
+{
+    for (int k = blockIdx.x; k < plan[0]; k += gridDim.x)
+        build_rev_atom<true>(chunks[k] + threadIdx.x, N, nn, nl, rev, sys_of, sys, flags);
 }
 
 // Clear the rebuild requests (pools: every system's, then the global one).
@@ -353,35 +541,54 @@ float list_margin_for(double lmax, double rl)
     return (float)(16.0 * ulp + 1e-6 * rl);
 }
 
-template <bool B>
-int rebuild_impl(const Plan &p, cudaStream_t s)
+int rebuild_single(const Plan &p, cudaStream_t s)
 {
     const int T = 256;
     cudaMemsetAsync(p.cell_count, 0, sizeof(int) * p.ncell, s);
     cudaMemsetAsync(&p.flags->max_nn, 0, sizeof(int), s);
-    k_cell_count<B><<<blocks_for(p.N, T), T, 0, s>>>(p.N, p.pos, p.posf, p.box, p.nc[0], p.nc[1], p.nc[2],
-                                                    p.sys_of, p.sys, p.atom_cell, p.atom_rank, p.cell_count);
+    k_cell_count<<<blocks_for(p.N, T), T, 0, s>>>(p.N, p.pos, p.posf, p.box, p.nc[0], p.nc[1], p.nc[2],
+                                                 p.atom_cell, p.atom_rank, p.cell_count);
     const int64_t nb = (p.ncell + kScanElems - 1) / kScanElems;
     k_scan_blocks<<<(unsigned)nb, kScanThreads, 0, s>>>(p.ncell, p.cell_count, p.cell_start, p.scan_blocks);
     k_scan_sums<<<1, kScanThreads, 0, s>>>(nb, p.scan_blocks);
     k_scan_add<<<blocks_for(p.ncell, T), T, 0, s>>>(p.ncell, p.cell_start, p.scan_blocks);
-    k_cell_fill<B><<<blocks_for(p.N, T), T, 0, s>>>(p.N, p.atom_cell, p.atom_rank, p.cell_start, p.cell_atoms,
-                                                   p.sys_of, p.sys);
+    k_cell_fill<<<blocks_for(p.N, T), T, 0, s>>>(p.N, p.atom_cell, p.atom_rank, p.cell_start, p.cell_atoms);
     const int TB = 128;
     const float rlm = (float)p.rl + p.list_margin;
-    k_build_list<B><<<blocks_for(p.N, TB), TB, 0, s>>>(p.N, p.pos, p.posf, p.box, p.nc[0], p.nc[1], p.nc[2],
-                                                      p.sys_of, p.sys, p.atom_cell, p.cell_start,
-                                                      p.cell_count, p.cell_atoms, rlm * rlm, p.cap, p.nn,
-                                                      p.nl, p.pos_build, p.flags);
-    k_build_rev<B><<<blocks_for(p.N, T), T, 0, s>>>(p.N, p.nn, p.nl, p.rev, p.sys_of, p.sys, p.flags);
-    k_build_done<B><<<blocks_for(p.n_sys, T), T, 0, s>>>(p.n_sys, p.sys, p.flags);
+    k_build_list<<<blocks_for(p.N, TB), TB, 0, s>>>(p.N, p.pos, p.posf, p.box, p.nc[0], p.nc[1], p.nc[2],
+                                                   p.atom_cell, p.cell_start, p.cell_count, p.cell_atoms,
+                                                   rlm * rlm, p.cap, p.nn, p.nl, p.pos_build, p.flags);
+    k_build_rev<<<blocks_for(p.N, T), T, 0, s>>>(p.N, p.nn, p.nl, p.rev, p.flags);
+    k_build_done<false><<<1, 1, 0, s>>>(p.n_sys, p.sys, p.flags);
+    return 8;
+}
+
+int rebuild_pool(const Plan &p, cudaStream_t s)
+{
+    // grids bounded by the work a rebuild can have: loop over the listed chunks/systems
+    const unsigned gc = (unsigned)std::min<int64_t>((p.N + kChunk - 1) / kChunk, 8 * 152);
+    const unsigned gs = (unsigned)std::min<int64_t>(p.n_sys, 4 * 152);
+    cudaMemsetAsync(&p.flags->max_nn, 0, sizeof(int), s);
+    k_rebuild_plan<<<1, 1024, 0, s>>>(p.n_sys, p.sys, p.rb_plan, p.rb_sys, p.rb_chunks);
+    k_cells_clear_pool<<<gs, 256, 0, s>>>(p.rb_plan, p.rb_sys, p.sys, p.cell_count);
+    k_cell_count_pool<<<gc, kChunk, 0, s>>>(p.rb_plan, p.rb_chunks, p.N, p.pos, p.posf, p.sys_of, p.sys,
+                                            p.atom_cell, p.atom_rank, p.cell_count);
+    k_cells_scan_pool<<<gs, kPoolScanThreads, 0, s>>>(p.rb_plan, p.rb_sys, p.sys, p.cell_count, p.cell_start);
+    k_cell_fill_pool<<<gc, kChunk, 0, s>>>(p.rb_plan, p.rb_chunks, p.atom_cell, p.atom_rank, p.cell_start,
+                                           p.cell_atoms, p.sys_of, p.sys);
+    k_build_list_pool<<<gc, kChunk, 0, s>>>(p.rb_plan, p.rb_chunks, p.N, p.pos, p.posf, p.sys_of, p.sys,
+                                            p.atom_cell, p.cell_start, p.cell_count, p.cell_atoms, p.cap, p.nn,
+                                            p.nl, p.pos_build, p.flags);
+    k_build_rev_pool<<<gc, kChunk, 0, s>>>(p.rb_plan, p.rb_chunks, p.N, p.nn, p.nl, p.rev, p.sys_of, p.sys,
+                                           p.flags);
+    k_build_done<true><<<blocks_for(p.n_sys, 256), 256, 0, s>>>(p.n_sys, p.sys, p.flags);
     return 8;
 }
 
 int launch_rebuild(const Plan &p, cudaStream_t s)
 {
     if (p.N == 0) return 0;
-    return p.batch ? rebuild_impl<true>(p, s) : rebuild_impl<false>(p, s);
+    return p.batch ? rebuild_pool(p, s) : rebuild_single(p, s);
 }
 
 void launch_displacement_check(const Plan &p, cudaStream_t s)

@@ -80,7 +80,10 @@ class md_job_result(ctypes.Structure):
 
 class md_server_stats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64), ("completed", ctypes.c_int64),
-                ("failed", ctypes.c_int64), ("atom_steps", ctypes.c_double), ("busy_seconds", ctypes.c_double)]
+                ("failed", ctypes.c_int64), ("atom_steps", ctypes.c_double), ("busy_seconds", ctypes.c_double),
+                ("run_seconds", ctypes.c_double), ("admit_seconds", ctypes.c_double),
+                ("harvest_seconds", ctypes.c_double), ("chunks", ctypes.c_int64),
+                ("resident_atom_steps", ctypes.c_double)]
 
 
 class md_stats(ctypes.Structure):
