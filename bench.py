@@ -57,6 +57,8 @@ def workload(name: str, scale: int = 1):
         return I.si_diamond_sw(n=40 // scale), 1.0
     if name == "tersoff_si_1728":
         return I.si_diamond_tersoff(n=6), 1.0
+    if name == "tersoff_si_216k":
+        return I.si_diamond_tersoff(n=30 // scale), 1.0
     raise ValueError(name)
 
 
@@ -132,6 +134,13 @@ def run_ours(args, rank, world):
         if args.eager:
             md.md_set_graph_mode(g.ctx, False)
         f0 = g.compute(want=("f",))["F"].copy()
+        tuning = None
+        if args.pair_block:
+            pb = dict(zip(("fp64", "mixed"), (int(v) for v in args.pair_block.split(","))))[tag]
+            md.md_set_tuning(g.ctx, pair_block=pb)
+            tuning = {"pair_block": pb, "imposed": True}
+        elif not args.no_tune:
+            tuning = md.tuning_dict(md.md_autotune(g.ctx, 10))
         g.run(args.warmup, dt, record=False)
         rebuilds0 = g.stats().n_rebuilds
         md.md_set_profiling(g.ctx, True)
@@ -143,7 +152,7 @@ def run_ours(args, rank, world):
         clocks = ClockSampler(torch.cuda.current_device())
         with clocks:
             e0.record(stream)
-            g.run(args.steps, dt, record=True)
+            ser = g.run(args.steps, dt, record=True)
             e1.record(stream)
             torch.cuda.synchronize()
         if world > 1:
@@ -152,7 +161,7 @@ def run_ours(args, rank, world):
         kt = md.md_kernel_times(g.ctx)
         md.md_set_profiling(g.ctx, False)
         st = g.stats()
-        res[tag] = dict(ms=ms, kt=kt, f0=f0, clocks=clocks.summary(), stats=st, sys=g,
+        res[tag] = dict(ms=ms, kt=kt, f0=f0, clocks=clocks.summary(), stats=st, sys=g, tuning=tuning, series=ser,
                         rebuilds=int(st.n_rebuilds - rebuilds0),
                         launches=int(st.kernel_launches_per_step) * args.steps
                         + int(st.kernel_launches_per_rebuild) * int(st.n_rebuilds - rebuilds0))
@@ -218,6 +227,16 @@ def run_batch(args, steps, warmup):
                        [I.MASS_SI, I.MASS_C], precision=prec, stream=stream.cuda_stream)
         for s, pset in systems:
             pool.add(s.pos, s.vel, s.box, s.pbc, pset, np.full(s.n, pset, np.int32))
+        if args.eager:
+            md.md_set_graph_mode(pool.ctx, False)
+        pool.run(1, 0.5)
+        tuning = None
+        if args.pool_tuning:
+            pb, g = dict(zip(("fp64", "mixed"), args.pool_tuning.split(",")))[tag].split("x")
+            md.md_set_tuning(pool.ctx, pair_block=int(pb), pool_blocks_per_sm=int(g))
+            tuning = {"pair_block": int(pb), "pool_blocks_per_sm": int(g), "imposed": True}
+        elif not args.no_tune:
+            tuning = md.tuning_dict(md.md_autotune(pool.ctx, 5))
         pool.run(warmup, 0.5)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -234,7 +253,8 @@ def run_batch(args, steps, warmup):
         md.md_set_profiling(pool.ctx, False)
         out[tag] = {"value": n_tot * steps / (ms / 1e3), "unit": "atom-steps/s", "ms_per_step": ms / steps,
                     "kernel_ms_per_step": {k: (v[1] / v[0] if v[0] else None) for k, v in kt.items()},
-                    "rebuilds_per_step": (md.md_get_stats(pool.ctx).n_rebuilds - r0) / min(steps, 40)}
+                    "rebuilds_per_step": (md.md_get_stats(pool.ctx).n_rebuilds - r0) / min(steps, 40),
+                    "tuning": tuning}
         pool.close()
     return out
 
@@ -333,6 +353,27 @@ def run_serve(args):
             "resident_atom_steps_per_run_s": st.resident_atom_steps / max(st.run_seconds, 1e-9)}
 
 
+def precision_report(res, n, dt, box):
+    """Energy drift of each path over the timed run and the heat-current autocorrelation
+    (md_hcacf on each path's J series) of the mixed path against the fp64 path."""
+    from paper_1610_03343_gb300 import md
+    out = {}
+    for tag in res:
+        e = res[tag]["series"][:, 0] + res[tag]["series"][:, 1]
+        out[f"energy_drift_ev_per_atom_{tag}"] = float((e[-1] - e[0]) / n)
+    if "fp64" in res and "mixed" in res:
+        rows = res["fp64"]["series"].shape[0]
+        lags = max(1, min(200, rows // 2))
+        c64, _ = md.green_kubo(res["fp64"]["series"], lags)
+        cmx, _ = md.green_kubo(res["mixed"]["series"], lags)
+        a64, amx = c64.sum(axis=1), cmx.sum(axis=1)
+        out["hcacf_lags"] = lags
+        out["hcacf_max_diff_rel_c0"] = float(np.abs(amx - a64).max() / abs(a64[0]))
+        out["j_series_max_diff_rel"] = float(np.abs(res["mixed"]["series"][:, 2:5] - res["fp64"]["series"][:, 2:5]).max()
+                                             / np.abs(res["fp64"]["series"][:, 2:5]).max())
+    return out
+
+
 def mixed_force_error():
     """Force error of the mixed path against the fp64 path on the serving job kinds."""
     from paper_1610_03343_gb300 import md
@@ -358,6 +399,11 @@ def main():
     ap.add_argument("--precision", default="both", choices=["both", "fp64", "mixed"])
     ap.add_argument("--eager", action="store_true",
                     help="launch each kernel eagerly instead of replaying graphs (for profilers)")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default launch shapes (no autotuner)")
+    ap.add_argument("--pair-block", default="",
+                    help="impose the pair block size instead of autotuning: 'FP64,MIXED', e.g. 64,128")
+    ap.add_argument("--pool-tuning", default="",
+                    help="impose the batch leg's tuning: 'PBxBPS,PBxBPS' for fp64 and mixed, e.g. 64x16,128x16")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=2000)
@@ -438,12 +484,15 @@ def main():
         "gpu_launches": res[primary]["launches"],
         "rebuilds": res[primary]["rebuilds"],
         "clocks": res[primary]["clocks"],
+        "tuning": res[primary]["tuning"],
     }
     if "mixed" in res and primary != "mixed":
         out["mixed"] = {"value": world * n * args.steps / (ms_mixed / 1e3), "ms_per_step": ms_mixed / args.steps,
                         "dtype": "f32+f64", "force_err_vs_fp64": mixed_err,
                         "kernel_ms_per_step": {k: (v[1] / v[0] if v[0] else None)
-                                               for k, v in res["mixed"]["kt"].items()}}
+                                               for k, v in res["mixed"]["kt"].items()},
+                        "tuning": res["mixed"]["tuning"]}
+    out["precision"] = precision_report(res, n, dt, sysm.box)
     if t_e2e is not None:
         out["e2e"] = {"value": world * n * args.steps / t_e2e, "unit": "atom-steps/s",
                       "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps}

@@ -152,6 +152,39 @@ md_status md_get_stats(md_ctx *ctx, md_stats *out);
  * look inside graphs with conditional nodes see every kernel this way. */
 md_status md_set_graph_mode(md_ctx *ctx, int use_graphs);
 
+/* Launch tuning.  Two launch parameters are free choices that do not change any result
+ * (every atom is computed by one thread the same way whatever they are; the gather's
+ * partial sums are per 128-atom chunk, not per CUDA block), only the speed:
+ *   pair_block          threads per block of the pair pass's common-case launch
+ *                       (32, 64, 128 or 256; each thread stages one atom's bonds in shared
+ *                       memory, so a block covers pair_block atoms);
+ *   pool_blocks_per_sm  pools: blocks per SM of the kick, pair and gather kernels that
+ *                       loop over the running systems' 128-atom chunks (1..64), i.e. how
+ *                       many chunks (atoms / 128) one block takes on per step.
+ * md_autotune times each candidate on the context's current state with CUDA events on
+ * its stream -- pair_block over {32, 64, 128, 256} with the pair pass alone, then (pools)
+ * pool_blocks_per_sm over {4, 8, 16, 32, 64} with the pair pass and a gather without the
+ * half-kick -- `repeats` launches each (0: 10), keeps the fastest and stores it in the
+ * context; the next md_run captures its graphs with it.  The timed launches recompute the
+ * current forces and change no state (positions, velocities, lists, step budgets).
+ * Positions must be set (MD_ERR_STATE otherwise).  `out` (may be NULL) receives the
+ * choice and every candidate's mean time.  md_set_tuning imposes a choice (MD_ERR_ARG for
+ * values outside the sets above; pair_block 0 = the precision's default: 64 for
+ * MD_FP64, 128 for MD_MIXED) and md_get_tuning reads the one in use.  The paper fixes
+ * its block size by hand (Sec. 3); this tuner has no counterpart there. */
+#define MD_TUNE_MAX 16
+typedef struct md_tuning {
+    int pair_block;
+    int pool_blocks_per_sm;
+    int n_tried;                      /* md_autotune: candidates timed                */
+    int tried_pair_block[MD_TUNE_MAX];
+    int tried_blocks_per_sm[MD_TUNE_MAX];
+    double tried_ms[MD_TUNE_MAX];     /* mean ms of one timed launch sequence          */
+} md_tuning;
+md_status md_autotune(md_ctx *ctx, int repeats, md_tuning *out);
+md_status md_set_tuning(md_ctx *ctx, const md_tuning *t);
+md_status md_get_tuning(md_ctx *ctx, md_tuning *out);
+
 /* Per-kernel timing.  While enabled, md_run records CUDA events around each kernel
  * class of every step and accumulates their elapsed times; md_kernel_times returns, for
  * up to max_k classes, the name, the number of timed launches and the total ms. */
@@ -312,6 +345,27 @@ md_status md_compute_static(int kind, const double *params, int precision, const
                             const double *z, const double *vx, const double *vy, const double *vz,
                             double mass, double *f, double *u, double *w, double *j, double *totals,
                             void *cuda_stream);
+
+/* Green-Kubo transport from the heat current.  The paper derives the potential part of
+ * the heat current for many-body potentials (Sec. 2.3, Eq. 30) for thermal-conductivity
+ * work but does not print the Green-Kubo relation; this uses the textbook one on the
+ * total J that md_run records every step:
+ *   acf[m*3 + a]   = C_a(m) = 1/(T-m) sum_{t=0}^{T-m-1} J_a(t) J_a(t+m),  m < n_lags,
+ *                    a = x, y, z (every time origin of the T = n_rows rows);
+ *   kappa[m*3 + a] = 1/(k_B T^2 V) * trapezoid integral of C_a over lags 0..m with step
+ *                    dt_fs, in W/(m K) (J in eV A/fs, V = volume in A^3, T = temperature
+ *                    in K; kappa[0] = 0).
+ * Layout: J_x of row t at j[t*row_stride], J_y at +1, J_z at +2.  For md_run's series
+ * pass j = series + 2 with row_stride 5 (one system) or series + 5 s + 2 with row_stride
+ * 5 n_systems (system s of a pool).  io: MD_IO_HOST (host arrays; copied through
+ * stream-ordered device scratch) or MD_IO_DEVICE (device arrays).  kappa may be NULL
+ * (then dt_fs, volume and temperature are not used).  Runs on cuda_stream and returns
+ * after synchronising it; fp64 throughout, fixed summation order (deterministic).
+ * Errors: MD_ERR_ARG for NULL j/acf, n_rows < 1, n_lags outside 1..n_rows, row_stride < 3,
+ * or non-positive dt/volume/temperature with kappa requested; MD_ERR_CUDA otherwise. */
+md_status md_hcacf(const double *j, int64_t n_rows, int64_t row_stride, int64_t n_lags, double dt_fs,
+                   double volume, double temperature, double *acf, double *kappa, int io,
+                   void *cuda_stream);
 
 /* Message of the last failing call (empty string if none).  Never NULL. */
 const char *md_last_error(const md_ctx *ctx);

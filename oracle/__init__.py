@@ -13,6 +13,8 @@ Functions follow the paper (arXiv:1610.03343) as documented in oracle.c:
   sw_conventional / sw_dUdr   the same two routes for Stillinger-Weber
   manybody_fwj         Eqs. 28-30 (F_i, W_i, J_i) from dU_i/dr_ij
   run                  velocity Verlet with per-step U, K, J
+  hcacf, running_kappa Green-Kubo HCACF and thermal conductivity from a J series
+                       (green_kubo.py, numpy)
 """
 from __future__ import annotations
 
@@ -22,6 +24,8 @@ import subprocess
 import threading
 
 import numpy as np
+
+from .green_kubo import hcacf, running_kappa  # noqa: F401
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")

@@ -797,20 +797,18 @@ __global__ void k_step_begin(Flags *flags, int *ovf_count, cudaGraphConditionalH
 
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-// Bounded grid of the pool kernels that loop over the chunk list.
-unsigned pool_grid(const Plan &p) { return (unsigned)std::min<int64_t>((p.N + kPoolChunk - 1) / kPoolChunk, 16 * 152); }
+// Bounded grid of the pool kernels that loop over the chunk list (tuned: blocks per SM).
+unsigned pool_grid(const Plan &p)
+{
+    const int64_t chunks = (p.N + kPoolChunk - 1) / kPoolChunk;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(chunks, (int64_t)p.pool_bps * p.n_sm));
+}
 
-constexpr int kPairBlockF64 = 64;
-constexpr int kPairBlockF32 = 128;
 constexpr int kPairCapSmall = 4;     // Tersoff: bonds staged per atom in the common-case pass
 constexpr int kPairCapSmallSW = 8;   // SW: its second shell sits just outside the cutoff, and at
                                      // room temperature many atoms have 5-6 bonds inside it
 constexpr int kPairBlockFull = 32;   // full-capacity pass over the deferred atoms
 constexpr int kGatherBlock = 128;
-
-template <typename T> constexpr int pair_block();
-template <> constexpr int pair_block<double>() { return kPairBlockF64; }
-template <> constexpr int pair_block<float>() { return kPairBlockF32; }
 
 template <typename T, int CAP, int BLOCK>
 size_t smem_for(int kind)
@@ -828,19 +826,27 @@ void set_smem()
                          (int)smem_for<T, CAP, BLOCK>(2));
 }
 
+template <typename T, int B, bool BATCH>
+void configure_block()
+{
+    set_smem<T, kPairCapSmall, B, false, BATCH>();
+    set_smem<T, kPairCapSmallSW, B, false, BATCH>();
+}
+
 template <typename T, bool BATCH>
 void configure_type()
 {
-    set_smem<T, kPairCapSmall, pair_block<T>(), false, BATCH>();
-    set_smem<T, kPairCapSmallSW, pair_block<T>(), false, BATCH>();
+    configure_block<T, 32, BATCH>();
+    configure_block<T, 64, BATCH>();
+    configure_block<T, 128, BATCH>();
+    configure_block<T, 256, BATCH>();
     set_smem<T, 8, kPairBlockFull, true, BATCH>();
     set_smem<T, 16, kPairBlockFull, true, BATCH>();
 }
 
-template <typename T, int FULL, bool BATCH>
-void pair_launch(const Plan &p, cudaStream_t s)
+template <typename T, int FULL, bool BATCH, int B>
+void pair_launch_b(const Plan &p, cudaStream_t s)
 {
-    constexpr int B = pair_block<T>();
     PairArgs<T> a;
     a.N = p.N;
     a.box = p.box;
@@ -865,7 +871,7 @@ void pair_launch(const Plan &p, cudaStream_t s)
     a.flags = p.flags;
     const unsigned nb = BATCH ? pool_grid(p) : blocks_for(p.N, B);
     int64_t nbf = (p.N + kPairBlockFull - 1) / kPairBlockFull;
-    if (nbf > 4 * 152) nbf = 4 * 152;
+    if (nbf > 4 * (int64_t)p.n_sm) nbf = 4 * (int64_t)p.n_sm;
     if (p.kind == 1) {
         TersoffSets<T> c;
         for (int k = 0; k < kMaxSets; ++k) c.s[k] = tersoff_const<T>(p.tp[k < p.n_sets ? k : 0]);
@@ -878,6 +884,19 @@ void pair_launch(const Plan &p, cudaStream_t s)
         k_pair_sw<T, kPairCapSmallSW, B, false, BATCH><<<nb, B, smem_for<T, kPairCapSmallSW, B>(2), s>>>(a, c);
         k_pair_sw<T, FULL, kPairBlockFull, true, BATCH>
             <<<(unsigned)nbf, kPairBlockFull, smem_for<T, FULL, kPairBlockFull>(2), s>>>(a, c);
+    }
+}
+
+// The common-case pass's block size is a run-time choice (the autotuner's); every
+// candidate computes each atom in one thread the same way, so results do not depend on it.
+template <typename T, int FULL, bool BATCH>
+void pair_launch(const Plan &p, cudaStream_t s)
+{
+    switch (effective_pair_block(p)) {
+    case 32: pair_launch_b<T, FULL, BATCH, 32>(p, s); break;
+    case 128: pair_launch_b<T, FULL, BATCH, 128>(p, s); break;
+    case 256: pair_launch_b<T, FULL, BATCH, 256>(p, s); break;
+    default: pair_launch_b<T, FULL, BATCH, 64>(p, s); break;
     }
 }
 
@@ -919,14 +938,13 @@ void gather_launch(const Plan &p, cudaStream_t s, const double *hk, double dt, b
 
 }  // namespace
 
-size_t pair_smem_bytes(const Plan &p)
+int effective_pair_block(const Plan &p)
 {
-    if (p.kind == 2)
-        return p.precision == 0 ? smem_for<double, kPairCapSmallSW, kPairBlockF64>(2)
-                                : smem_for<float, kPairCapSmallSW, kPairBlockF32>(2);
-    if (p.precision == 0) return smem_for<double, kPairCapSmall, kPairBlockF64>(p.kind);
-    return smem_for<float, kPairCapSmall, kPairBlockF32>(p.kind);
+    if (valid_pair_block(p.pair_block)) return p.pair_block;
+    return p.precision == 0 ? 64 : 128;   // measured defaults (fp64: 64, fp32: 128)
 }
+
+bool valid_pair_block(int b) { return b == 32 || b == 64 || b == 128 || b == 256; }
 
 void configure_kernels(const Plan &)
 {

@@ -569,6 +569,10 @@ md_status ctx_init(md_ctx *ctx, const md_options &opt)
         cudaGetLastError();
         return MD_ERR_CUDA;
     }
+    int n_sm = 0;
+    if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, ctx->device) == cudaSuccess && n_sm > 0)
+        ctx->p.n_sm = n_sm;
+    cudaGetLastError();
     configure_kernels(ctx->p);
     return MD_OK;
 }
@@ -1140,6 +1144,136 @@ md_status md_set_graph_mode(md_ctx *ctx, int use_graphs)
 {
     if (!ctx) return MD_ERR_ARG;
     ctx->use_graphs = use_graphs != 0;
+    return MD_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Mean time of `repeats` launch sequences (pair pass, and the gather without the
+// half-kick when `with_gather`) on the context's stream, after one untimed sequence.
+// The sequence recomputes the current forces from the current positions and list, so it
+// changes no state.
+md_status time_launches(md_ctx *ctx, int repeats, bool with_gather, double *ms)
+{
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    cudaError_t e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(ctx, e, "cudaEventCreate");
+    }
+    auto seq = [&]() {
+        launch_pair_reset(ctx->p, ctx->stream);
+        launch_active_plan(ctx->p, ctx->stream);
+        launch_pair(ctx->p, ctx->stream);
+        if (with_gather) launch_gather(ctx->p, ctx->stream, nullptr, 0.0, false);
+    };
+    seq();
+    cudaEventRecord(e0, ctx->stream);
+    for (int r = 0; r < repeats; ++r) seq();
+    cudaEventRecord(e1, ctx->stream);
+    e = cudaEventSynchronize(e1);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "autotune timing");
+    *ms = (double)t / repeats;
+    return MD_OK;
+}
+
+void fill_tuning(const md_ctx *ctx, md_tuning *out)
+{
+    out->pair_block = effective_pair_block(ctx->p);
+    out->pool_blocks_per_sm = ctx->p.pool_bps;
+}
+
+}  // namespace
+
+extern "C" {
+
+md_status md_autotune(md_ctx *ctx, int repeats, md_tuning *out)
+{
+    if (!ctx) return MD_ERR_ARG;
+    if (repeats < 0 || repeats > 10000) return fail(ctx, MD_ERR_ARG, "repeats out of range");
+    if (repeats == 0) repeats = 10;
+    if (!ctx->pos_set && ctx->p.N > 0) return fail(ctx, MD_ERR_STATE, "positions not set");
+    md_tuning res;
+    std::memset(&res, 0, sizeof(res));
+    if (ctx->p.N > 0) {
+        md_status s;
+        if (!ctx->forces_valid) {   // lists (and forces) for the current positions
+            s = force_eval(ctx, false, ctx->is_pool);
+            if (s != MD_OK) return s;
+        }
+        s = clear_error_flags(ctx);
+        if (s != MD_OK) return s;
+        static const int blocks[] = {32, 64, 128, 256};
+        double best = 0.0;
+        int best_b = effective_pair_block(ctx->p);
+        for (int b : blocks) {
+            ctx->p.pair_block = b;
+            double ms = 0.0;
+            s = time_launches(ctx, repeats, false, &ms);
+            if (s != MD_OK) return s;
+            res.tried_pair_block[res.n_tried] = b;
+            res.tried_blocks_per_sm[res.n_tried] = ctx->p.pool_bps;
+            res.tried_ms[res.n_tried++] = ms;
+            if (best == 0.0 || ms < best) {
+                best = ms;
+                best_b = b;
+            }
+        }
+        ctx->p.pair_block = best_b;
+        if (ctx->is_pool) {
+            static const int bps[] = {4, 8, 16, 32, 64};
+            best = 0.0;
+            int best_g = ctx->p.pool_bps;
+            for (int g : bps) {
+                ctx->p.pool_bps = g;
+                double ms = 0.0;
+                s = time_launches(ctx, repeats, true, &ms);
+                if (s != MD_OK) return s;
+                res.tried_pair_block[res.n_tried] = best_b;
+                res.tried_blocks_per_sm[res.n_tried] = g;
+                res.tried_ms[res.n_tried++] = ms;
+                if (best == 0.0 || ms < best) {
+                    best = ms;
+                    best_g = g;
+                }
+            }
+            ctx->p.pool_bps = best_g;
+        }
+        s = check_flags(ctx);
+        if (s != MD_OK) return s;
+        destroy_graph(ctx);   // the next md_run captures with the chosen launches
+    }
+    fill_tuning(ctx, &res);
+    if (out) *out = res;
+    return MD_OK;
+}
+
+md_status md_set_tuning(md_ctx *ctx, const md_tuning *t)
+{
+    if (!ctx || !t) return MD_ERR_ARG;
+    if (t->pair_block != 0 && !valid_pair_block(t->pair_block))
+        return fail(ctx, MD_ERR_ARG, "pair_block must be 0, 32, 64, 128 or 256");
+    if (t->pool_blocks_per_sm < 1 || t->pool_blocks_per_sm > 64)
+        return fail(ctx, MD_ERR_ARG, "pool_blocks_per_sm must be in 1..64");
+    ctx->p.pair_block = t->pair_block;
+    ctx->p.pool_bps = t->pool_blocks_per_sm;
+    destroy_graph(ctx);
+    return MD_OK;
+}
+
+md_status md_get_tuning(md_ctx *ctx, md_tuning *out)
+{
+    if (!ctx || !out) return MD_ERR_ARG;
+    std::memset(out, 0, sizeof(*out));
+    fill_tuning(ctx, out);
     return MD_OK;
 }
 

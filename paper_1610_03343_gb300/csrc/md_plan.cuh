@@ -15,6 +15,12 @@ struct Plan {
     int maxa = 8;          // in-cutoff capacity (compact pair rows)
     double rc = 0, rl = 0, skin = 0;
     float list_margin = 0.f;   // fp32 margin of the list build
+    // launch tuning (results do not depend on it): threads per block of the pair pass's
+    // common-case launch (0 = default for the precision) and, for pools, blocks per SM of
+    // the kernels that loop over the running systems' chunks
+    int pair_block = 0;
+    int pool_bps = 16;
+    int n_sm = 152;
     // parameter sets (a single system uses set 0)
     int n_sets = 1;
     TersoffP tp[kMaxSets]{};
@@ -79,7 +85,9 @@ void launch_displacement_check(const Plan &p, cudaStream_t s);
 void launch_wrap_copy(const Plan &p, cudaStream_t s, double *dst, int64_t a0, int64_t n);
 
 // force.cu
-size_t pair_smem_bytes(const Plan &p);
+// Pair-pass block size in use (the tuned one, else the precision's default).
+int effective_pair_block(const Plan &p);
+bool valid_pair_block(int b);
 void configure_kernels(const Plan &p);
 // Half-kick + drift + displacement check (first half of a velocity-Verlet step).
 void launch_kick_drift(const Plan &p, cudaStream_t s, const double *half_kick, double dt);

@@ -23,6 +23,8 @@ MD_FP64 = 0
 MD_MIXED = 1
 MD_IO_HOST = 0
 MD_IO_DEVICE = 1
+MD_ERR_ARG, MD_ERR_BOX, MD_ERR_NEIGH_OVERFLOW, MD_ERR_OOM = -1, -2, -3, -4
+MD_ERR_CUDA, MD_ERR_TIMEOUT, MD_ERR_NAN, MD_ERR_STATE = -5, -6, -7, -8
 
 STATUS = {0: "MD_OK", -1: "MD_ERR_ARG", -2: "MD_ERR_BOX", -3: "MD_ERR_NEIGH_OVERFLOW",
           -4: "MD_ERR_OOM", -5: "MD_ERR_CUDA", -6: "MD_ERR_TIMEOUT", -7: "MD_ERR_NAN",
@@ -93,15 +95,25 @@ class md_stats(ctypes.Structure):
                 ("device_bytes", ctypes.c_size_t)]
 
 
+MD_TUNE_MAX = 16
+
+
+class md_tuning(ctypes.Structure):
+    _fields_ = [("pair_block", ctypes.c_int), ("pool_blocks_per_sm", ctypes.c_int), ("n_tried", ctypes.c_int),
+                ("tried_pair_block", ctypes.c_int * MD_TUNE_MAX),
+                ("tried_blocks_per_sm", ctypes.c_int * MD_TUNE_MAX),
+                ("tried_ms", ctypes.c_double * MD_TUNE_MAX)]
+
+
 _lock = threading.Lock()
 _lib = None
 
 EXPORTS = ["md_default_options", "md_create", "md_set_positions", "md_set_velocities", "md_compute",
            "md_run", "md_get_state", "md_get_stats", "md_set_graph_mode", "md_set_profiling",
-           "md_kernel_times", "md_batch_create", "md_batch_add", "md_batch_remove", "md_batch_status",
+           "md_kernel_times", "md_autotune", "md_set_tuning", "md_get_tuning", "md_batch_create", "md_batch_add", "md_batch_remove", "md_batch_status",
            "md_batch_get_state", "md_server_create", "md_server_submit", "md_server_poll", "md_server_wait",
            "md_server_drain", "md_server_stats_get", "md_server_clock", "md_server_destroy",
-           "md_compute_static", "md_last_error", "md_destroy"]
+           "md_compute_static", "md_hcacf", "md_last_error", "md_destroy"]
 
 
 def library_path() -> str:
@@ -135,6 +147,9 @@ def load(build_if_missing: bool = False):
         lib.md_kernel_times.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
                                         ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_int)]
+        lib.md_autotune.argtypes = [P, ctypes.c_int, ctypes.POINTER(md_tuning)]
+        lib.md_set_tuning.argtypes = [P, ctypes.POINTER(md_tuning)]
+        lib.md_get_tuning.argtypes = [P, ctypes.POINTER(md_tuning)]
         lib.md_batch_create.argtypes = [ctypes.POINTER(P), ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                         ctypes.POINTER(md_params), ctypes.c_int, P,
                                         ctypes.POINTER(md_batch_options), ctypes.POINTER(md_options)]
@@ -155,6 +170,8 @@ def load(build_if_missing: bool = False):
         lib.md_server_destroy.restype = None
         lib.md_compute_static.argtypes = [ctypes.c_int, P, ctypes.c_int, P, P, ctypes.c_int64, P, P, P, P, P, P,
                                           ctypes.c_double, P, P, P, P, P, P]
+        lib.md_hcacf.argtypes = [P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
+                                 ctypes.c_double, ctypes.c_double, P, P, ctypes.c_int, P]
         lib.md_last_error.argtypes = [P]
         lib.md_last_error.restype = ctypes.c_char_p
         lib.md_destroy.argtypes = [P]
@@ -264,6 +281,34 @@ def md_kernel_times(ctx):
     nout = ctypes.c_int()
     _check(lib, ctx, lib.md_kernel_times(ctx, k, names, n, ms, ctypes.byref(nout)))
     return {names[i].decode(): (int(n[i]), float(ms[i])) for i in range(nout.value)}
+
+
+def md_autotune(ctx, repeats: int = 0) -> md_tuning:
+    lib = load()
+    t = md_tuning()
+    _check(lib, ctx, lib.md_autotune(ctx, int(repeats), ctypes.byref(t)))
+    return t
+
+
+def md_set_tuning(ctx, pair_block: int = 0, pool_blocks_per_sm: int = 16):
+    lib = load()
+    t = md_tuning()
+    t.pair_block, t.pool_blocks_per_sm = int(pair_block), int(pool_blocks_per_sm)
+    _check(lib, ctx, lib.md_set_tuning(ctx, ctypes.byref(t)))
+
+
+def md_get_tuning(ctx) -> md_tuning:
+    lib = load()
+    t = md_tuning()
+    _check(lib, ctx, lib.md_get_tuning(ctx, ctypes.byref(t)))
+    return t
+
+
+def tuning_dict(t: md_tuning) -> dict:
+    """The chosen launch parameters and every timed candidate, as plain data."""
+    return {"pair_block": t.pair_block, "pool_blocks_per_sm": t.pool_blocks_per_sm,
+            "tried": [{"pair_block": t.tried_pair_block[k], "pool_blocks_per_sm": t.tried_blocks_per_sm[k],
+                       "ms": t.tried_ms[k]} for k in range(t.n_tried)]}
 
 
 def md_batch_create(atom_capacity, max_systems, kind, param_sets, masses_by_type,
@@ -390,6 +435,31 @@ def md_compute_static(kind, params, precision, box, pbc, n_atoms, x, y, z, vx, v
                                _ptr(f), _ptr(u), _ptr(w), _ptr(j), _ptr(totals), stream)
     if st != MD_OK:
         raise MDError(st, "md_compute_static failed")
+
+
+def md_hcacf(j, n_rows, row_stride, n_lags, dt_fs=0.0, volume=0.0, temperature=0.0, acf=None, kappa=None,
+             io=MD_IO_HOST, stream=None):
+    """Raw call: j, acf, kappa are numpy arrays (io=MD_IO_HOST) or torch CUDA tensors
+    (io=MD_IO_DEVICE); j points at the first J_x of the layout md_hcacf documents."""
+    lib = load()
+    st = lib.md_hcacf(_ptr(j), int(n_rows), int(row_stride), int(n_lags), float(dt_fs), float(volume),
+                      float(temperature), _ptr(acf), _ptr(kappa), int(io), stream)
+    if st != MD_OK:
+        raise MDError(st, "md_hcacf")
+
+
+def green_kubo(series, n_lags, dt_fs=0.0, volume=0.0, temperature=0.0, system=0):
+    """HCACF (n_lags, 3) and running kappa (n_lags, 3) of one system from md_run's series:
+    a (steps, 5) array (one system) or (steps, n_systems, 5) (a pool)."""
+    s = np.ascontiguousarray(series, dtype=np.float64)
+    rows = s.shape[0]
+    flat = s.reshape(rows, -1)
+    stride = flat.shape[1]
+    j = flat.reshape(-1)[5 * int(system) + 2:]
+    acf = np.zeros((n_lags, 3))
+    kappa = np.zeros((n_lags, 3)) if temperature > 0 else None
+    md_hcacf(j, rows, stride, n_lags, dt_fs, volume, temperature, acf, kappa)
+    return acf, kappa
 
 
 def md_last_error(ctx) -> str:
