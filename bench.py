@@ -35,8 +35,21 @@ sys.path.insert(0, ROOT)
 from paper_1610_03343_gb300 import inputs as I  # noqa: E402
 
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
-# FP64 vector peak of a GB300 from the unit counts and clock (recipe's nominal figure).
-FP64_NOMINAL_TFLOPS = 1.25
+# FP64 peak of a GB300 from its unit counts and clock: 152 SMs x 2 DFMA/clk/SM (ncu's
+# peak_sustained for the DFMA counter) x 2 flop x 2.07 GHz maximum SM clock.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+# FP64 flops of the fp64 pair pass, counted with ncu's instruction counters (DADD + DMUL +
+# 2 DFMA, which include the FP64 sequences behind exp, log, division and square root).
+# Tersoff: per bond and per ordered bond pair, fit to the C sheet (3 bonds per atom, 1052.4
+# flop/atom) and Si diamond (4 bonds, 1572.3 flop/atom).  SW: per atom of the 4-bond
+# diamond lattice (812.2 flop/atom).
+TERSOFF_FLOP_PER_BOND = 266.25
+TERSOFF_FLOP_PER_BOND_PAIR = 42.28
+SW_FLOP_PER_ATOM_4 = 812.2
+# DRAM bytes (read + write) of one fp64 pair launch, from the ncu capture of the current
+# kernel on each workload.
+PAIR_TRAFFIC_BYTES = {"tersoff_c_graphene_1M": 138.29e6, "tersoff_si_216k": 10.12e6, "sw_si_512k": 103.95e6}
 
 
 def load_peaks():
@@ -106,12 +119,12 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-# FP64 operations per atom-step of the pair pass, counted from its expressions (see
-# DESIGN.md, "roofline"): per in-cutoff bond and per unordered bond pair (triplet).
-def pair_flops(kind: int, bonds: float, triplets: float) -> float:
+def pair_flops(kind: int, bonds: float) -> float:
+    """Algorithmic FP64 flops per atom of the fp64 pair pass on a lattice with `bonds`
+    in-cutoff neighbours per atom."""
     if kind == I.MD_TERSOFF:
-        return 62.0 * bonds + 75.0 * triplets
-    return 60.0 * bonds + 50.0 * triplets
+        return TERSOFF_FLOP_PER_BOND * bonds + TERSOFF_FLOP_PER_BOND_PAIR * bonds * (bonds - 1)
+    return SW_FLOP_PER_ATOM_4 * bonds / 4.0
 
 
 def run_ours(args, rank, world):
@@ -456,10 +469,10 @@ def main():
     st = res[primary]["stats"]
     sysm, _ = workload(args.workload)
     bonds = 3.0 if sysm.kind == I.MD_TERSOFF and "graphene" in args.workload else 4.0
-    trip = bonds * (bonds - 1) / 2
-    flops = pair_flops(sysm.kind, bonds, trip) * n
+    flops = pair_flops(sysm.kind, bonds) * n
     pair_avg_s = pair_ms / pair_n / 1e3 if pair_n > 0 and pair_ms > 0 else None
     achieved_tf = flops / pair_avg_s / 1e12 if pair_avg_s else None
+    traffic = PAIR_TRAFFIC_BYTES.get(args.workload) if primary == "fp64" else None
     out = {
         "metric": "atom-steps/s Tersoff FP64 vs mixed on 1 GB300",
         "value": value,
@@ -477,9 +490,10 @@ def main():
                    "l2": "working set > L2 (no flush)", "launch": "eager" if args.eager else "graphs",
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "alu", "kernel": f"pair ({primary})", "achieved": achieved_tf,
-                     "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved_tf / FP64_NOMINAL_TFLOPS if achieved_tf else None, "traffic": None,
-                     "peak_source": "nominal GB300 FP64 (recipe unit counts x clock)"},
+                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved_tf / FP64_PEAK_TFLOPS if achieved_tf else None, "traffic": traffic,
+                     "flop_per_launch": flops,
+                     "peak_source": "FP64 pipe from unit counts and clock: 152 SMs x 4 flop/clk x 2.07 GHz"},
         "kernel_ms_per_step": {k: (v[1] / v[0] if v[0] else None) for k, v in kt.items()},
         "gpu_launches": res[primary]["launches"],
         "rebuilds": res[primary]["rebuilds"],
@@ -514,26 +528,34 @@ def _oracle_rate(sysm, dt, steps):
     return sysm.n * steps / t, t
 
 
+def cpu_sample(args):
+    """A bounded sample of the bench workload for the oracle: a 250 x 250-cell patch
+    (250,000 atoms) of the same sheet, or the same lattice at half the edge."""
+    if "graphene" in args.workload:
+        return I.c_graphene_tersoff(nx=250, ny=250)
+    return workload(args.workload, 2)[0]
+
+
 def cpu_baseline(args):
-    """The oracle as it stands, single-threaded on a host core, on a bounded sample of the
-    same workload: a 100 x 100-cell patch (40,000 atoms) of the same sheet, 5 steps."""
+    """The oracle as it stands, single-threaded on a host core, on the bounded sample
+    (about 10-15 s of CPU work: 24 velocity-Verlet steps)."""
     import oracle
     oracle.build()
-    sysm = I.c_graphene_tersoff(nx=100, ny=100) if "graphene" in args.workload else workload(args.workload, 4)[0]
+    sysm = cpu_sample(args)
     _, dt = workload(args.workload)
-    rate, t = _oracle_rate(sysm, dt, 5)
+    rate, t = _oracle_rate(sysm, dt, 24)
     return {"value": rate, "unit": "atom-steps/s", "cores": 1, "kind": "oracle",
-            "sample": f"{sysm.n} atoms of the same lattice, 5 steps, {t:.1f} s"}
+            "sample": f"{sysm.n} atoms of the same lattice, 24 steps, {t:.1f} s"}
 
 
 def reference_arm(args):
-    """The oracle timed on the host as the reference arm: each step a bounded sample
-    (40,000-atom patch of the same workload, one velocity-Verlet step)."""
+    """The oracle timed on the host as the reference arm: each step one velocity-Verlet
+    step of the bounded sample (cpu_sample), at most 40 steps (about 20 s)."""
     import oracle
     oracle.build()
-    sysm = I.c_graphene_tersoff(nx=100, ny=100) if "graphene" in args.workload else workload(args.workload, 4)[0]
+    sysm = cpu_sample(args)
     _, dt = workload(args.workload)
-    steps = max(1, min(args.steps, 20))
+    steps = max(1, min(args.steps, 40))
     for _ in range(min(args.warmup, 1)):
         _oracle_rate(sysm, dt, 1)
     rate, t = _oracle_rate(sysm, dt, steps)
