@@ -142,6 +142,8 @@ typedef struct {
     int pair_deferred;       /* atoms with more than 4 in-cutoff bonds at the last pair pass
                                 (handled by the full-capacity pass)                      */
     size_t device_bytes;     /* bytes the context has allocated on the device         */
+    int64_t atoms_rebuilt;   /* atoms whose neighbour list was built, summed over builds
+                                (pools: only the systems that needed a rebuild)          */
 } md_stats;
 md_status md_get_stats(md_ctx *ctx, md_stats *out);
 

@@ -482,18 +482,25 @@ __global__ void __launch_bounds__(BLOCK) k_pair_sw(PairArgs<T> a, SWSets<T> ps)
 __global__ void k_pair_reset(int *ovf_count) { *ovf_count = 0; }
 
 // Pools: the 128-atom chunks of the systems that run now (stopped systems and free atom
-// ranges are skipped).  plan[0] = number of chunks.
+// ranges are skipped).  plan[0] = number of chunks.  With skip_rebuilding, systems whose
+// list is to be rebuilt this step are left out too, and the rebuild conditional (when
+// has_cond) is set if any running system is to be rebuilt or a rebuild was requested.
 __global__ void __launch_bounds__(1024) k_active_plan(int n_sys, const SysDev *sys, const Flags *flags, int *plan,
-                                                      int *chunks)
+                                                      int *chunks, int skip_rebuilding, cudaGraphConditionalHandle h,
+                                                      int has_cond)
 {
     __shared__ int warp_b[32];
     __shared__ int carry;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
+    int skipped_any = 0;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int s0 = 0; s0 < n_sys; s0 += blockDim.x) {
         const int s = s0 + threadIdx.x;
-        const bool f = s < n_sys && system_live(sys[s], flags);
+        const bool live = s < n_sys && system_live(sys[s], flags);
+        const bool skip = live && skip_rebuilding && sys[s].rebuild;
+        skipped_any |= __syncthreads_or(skip ? 1 : 0);
+        const bool f = live && !skip;
         const int nch = f ? (int)((sys[s].n_atoms + kPoolChunk - 1) / kPoolChunk) : 0;
         int b = nch;
         for (int o = 1; o < 32; o <<= 1) {
@@ -518,7 +525,10 @@ __global__ void __launch_bounds__(1024) k_active_plan(int n_sys, const SysDev *s
         if (threadIdx.x == 0) carry += warp_b[(blockDim.x >> 5) - 1];
         __syncthreads();
     }
-    if (threadIdx.x == 0) plan[0] = carry;
+    if (threadIdx.x == 0) {
+        plan[0] = carry;
+        if (has_cond) cudaGraphSetConditional(h, (skipped_any || flags->rebuild) ? 1u : 0u);
+    }
 }
 
 // End of the force evaluation that follows admissions: the new systems are no longer
@@ -735,7 +745,9 @@ k_reduce(const double *partials, int nc, int seg_max, int64_t N, int block, cons
 // ------------------------------------------------------------------ integrator
 struct KickDriftArgs {
     int64_t N;
-    float *posf;
+    float *posf;   // fp32 positions, refreshed every step only where the pair pass reads them
+                   // between list builds (the SW prefilter); null otherwise (the list build
+                   // writes its own copy)
     const int *act_count, *act_chunks;
     const int *sys_of;
     SysDev *sys;
@@ -764,7 +776,7 @@ __device__ __forceinline__ void kick_drift_atom(const KickDriftArgs &a, int64_t 
         const double x = fma(a.dt, v, a.pos[c * N + i]);
         a.vel[c * N + i] = v;
         a.pos[c * N + i] = x;
-        a.posf[c * N + i] = (float)x;
+        if (a.posf) a.posf[c * N + i] = (float)x;
         const float d = (float)(x - a.pos_build[c * N + i]);
         d2 = fmaf(d, d, d2);
     }
@@ -845,7 +857,7 @@ void configure_type()
 }
 
 template <typename T, int FULL, bool BATCH, int B>
-void pair_launch_b(const Plan &p, cudaStream_t s)
+void pair_launch_b(const Plan &p, cudaStream_t s, int list, int parts)
 {
     PairArgs<T> a;
     a.N = p.N;
@@ -862,8 +874,8 @@ void pair_launch_b(const Plan &p, cudaStream_t s)
     a.sys = p.sys;
     a.ovf_count = p.ovf_count;
     a.ovf_list = p.ovf_list;
-    a.act_count = p.act_plan;
-    a.act_chunks = p.act_chunks;
+    a.act_count = list == PAIR_STABLE ? p.stable_plan : (list == PAIR_REBUILT ? p.rb_plan : p.act_plan);
+    a.act_chunks = list == PAIR_STABLE ? p.stable_chunks : (list == PAIR_REBUILT ? p.rb_chunks : p.act_chunks);
     a.posf = p.posf;
     a.margin = p.list_margin;
     a.mask = p.mask;
@@ -875,28 +887,32 @@ void pair_launch_b(const Plan &p, cudaStream_t s)
     if (p.kind == 1) {
         TersoffSets<T> c;
         for (int k = 0; k < kMaxSets; ++k) c.s[k] = tersoff_const<T>(p.tp[k < p.n_sets ? k : 0]);
-        k_pair_tersoff<T, kPairCapSmall, B, false, BATCH><<<nb, B, smem_for<T, kPairCapSmall, B>(1), s>>>(a, c);
-        k_pair_tersoff<T, FULL, kPairBlockFull, true, BATCH>
-            <<<(unsigned)nbf, kPairBlockFull, smem_for<T, FULL, kPairBlockFull>(1), s>>>(a, c);
+        if (parts & PAIR_FAST)
+            k_pair_tersoff<T, kPairCapSmall, B, false, BATCH><<<nb, B, smem_for<T, kPairCapSmall, B>(1), s>>>(a, c);
+        if (parts & PAIR_DEFERRED)
+            k_pair_tersoff<T, FULL, kPairBlockFull, true, BATCH>
+                <<<(unsigned)nbf, kPairBlockFull, smem_for<T, FULL, kPairBlockFull>(1), s>>>(a, c);
     } else {
         SWSets<T> c;
         for (int k = 0; k < kMaxSets; ++k) c.s[k] = sw_const<T>(p.sp[k < p.n_sets ? k : 0]);
-        k_pair_sw<T, kPairCapSmallSW, B, false, BATCH><<<nb, B, smem_for<T, kPairCapSmallSW, B>(2), s>>>(a, c);
-        k_pair_sw<T, FULL, kPairBlockFull, true, BATCH>
-            <<<(unsigned)nbf, kPairBlockFull, smem_for<T, FULL, kPairBlockFull>(2), s>>>(a, c);
+        if (parts & PAIR_FAST)
+            k_pair_sw<T, kPairCapSmallSW, B, false, BATCH><<<nb, B, smem_for<T, kPairCapSmallSW, B>(2), s>>>(a, c);
+        if (parts & PAIR_DEFERRED)
+            k_pair_sw<T, FULL, kPairBlockFull, true, BATCH>
+                <<<(unsigned)nbf, kPairBlockFull, smem_for<T, FULL, kPairBlockFull>(2), s>>>(a, c);
     }
 }
 
 // The common-case pass's block size is a run-time choice (the autotuner's); every
 // candidate computes each atom in one thread the same way, so results do not depend on it.
 template <typename T, int FULL, bool BATCH>
-void pair_launch(const Plan &p, cudaStream_t s)
+void pair_launch(const Plan &p, cudaStream_t s, int list, int parts)
 {
     switch (effective_pair_block(p)) {
-    case 32: pair_launch_b<T, FULL, BATCH, 32>(p, s); break;
-    case 128: pair_launch_b<T, FULL, BATCH, 128>(p, s); break;
-    case 256: pair_launch_b<T, FULL, BATCH, 256>(p, s); break;
-    default: pair_launch_b<T, FULL, BATCH, 64>(p, s); break;
+    case 32: pair_launch_b<T, FULL, BATCH, 32>(p, s, list, parts); break;
+    case 128: pair_launch_b<T, FULL, BATCH, 128>(p, s, list, parts); break;
+    case 256: pair_launch_b<T, FULL, BATCH, 256>(p, s, list, parts); break;
+    default: pair_launch_b<T, FULL, BATCH, 64>(p, s, list, parts); break;
     }
 }
 
@@ -968,7 +984,7 @@ void launch_kick_drift(const Plan &p, cudaStream_t s, const double *hk, double d
     a.vel = p.vel;
     a.force = p.force;
     a.pos_build = p.pos_build;
-    a.posf = p.posf;
+    a.posf = p.kind == 2 ? p.posf : nullptr;
     a.type = p.type;
     for (int t = 0; t < kMaxTypes; ++t) a.hk[t] = hk[t];
     a.dt = dt;
@@ -991,7 +1007,15 @@ void launch_pair_reset(const Plan &p, cudaStream_t s) { k_pair_reset<<<1, 1, 0, 
 void launch_active_plan(const Plan &p, cudaStream_t s)
 {
     if (!p.batch) return;
-    k_active_plan<<<1, 1024, 0, s>>>(p.n_sys, p.sys, p.flags, p.act_plan, p.act_chunks);
+    k_active_plan<<<1, 1024, 0, s>>>(p.n_sys, p.sys, p.flags, p.act_plan, p.act_chunks, 0,
+                                     cudaGraphConditionalHandle(0), 0);
+}
+
+void launch_stable_plan(const Plan &p, cudaStream_t s, const cudaGraphConditionalHandle *h)
+{
+    if (!p.batch) return;
+    k_active_plan<<<1, 1024, 0, s>>>(p.n_sys, p.sys, p.flags, p.stable_plan, p.stable_chunks, 1,
+                                     h ? *h : cudaGraphConditionalHandle(0), h ? 1 : 0);
 }
 
 void launch_clear_fresh(const Plan &p, cudaStream_t s)
@@ -1000,20 +1024,23 @@ void launch_clear_fresh(const Plan &p, cudaStream_t s)
 }
 
 template <bool BATCH>
-void pair_dispatch_launch(const Plan &p, cudaStream_t s)
+void pair_dispatch_launch(const Plan &p, cudaStream_t s, int list, int parts)
 {
     if (p.precision == 0) {
-        if (p.maxa <= 8) pair_launch<double, 8, BATCH>(p, s); else pair_launch<double, 16, BATCH>(p, s);
+        if (p.maxa <= 8) pair_launch<double, 8, BATCH>(p, s, list, parts);
+        else pair_launch<double, 16, BATCH>(p, s, list, parts);
     } else {
-        if (p.maxa <= 8) pair_launch<float, 8, BATCH>(p, s); else pair_launch<float, 16, BATCH>(p, s);
+        if (p.maxa <= 8) pair_launch<float, 8, BATCH>(p, s, list, parts);
+        else pair_launch<float, 16, BATCH>(p, s, list, parts);
     }
 }
 
-int launch_pair(const Plan &p, cudaStream_t s)
+int launch_pair(const Plan &p, cudaStream_t s, int list, int parts)
 {
     if (p.N == 0) return 0;
-    if (p.batch) pair_dispatch_launch<true>(p, s); else pair_dispatch_launch<false>(p, s);
-    return 2;
+    if (p.batch) pair_dispatch_launch<true>(p, s, list, parts);
+    else pair_dispatch_launch<false>(p, s, PAIR_ALL, parts);
+    return (parts & PAIR_FAST ? 1 : 0) + (parts & PAIR_DEFERRED ? 1 : 0);
 }
 
 template <bool BATCH>

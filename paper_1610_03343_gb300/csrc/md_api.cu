@@ -81,6 +81,8 @@ struct md_ctx {
     double *g_series = nullptr;
     bool g_prof = false;
     cudaStream_t side = nullptr;   // stream used to capture conditional bodies
+    cudaStream_t side2 = nullptr;  // pools: second branch of the step graph (rebuild)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool use_graphs = true;        // false: eager launches, rebuild decided on the host
     // profiling
     bool profiling = false;
@@ -95,6 +97,7 @@ struct md_ctx {
     int64_t cell_capacity = 0;
     int64_t min_atoms = 1;
     double skin_option = 0.0;
+    int nc_full[3] = {1, 1, 1};    // single system: the cell grid from the box alone
     std::string err;
 };
 
@@ -269,6 +272,30 @@ md_status system_box(const Plan &p, double rl, const double box[3], const int pb
     return MD_OK;
 }
 
+// Merge into one cell every cell axis that the atoms barely occupy -- at most a quarter of
+// its cells hold an atom (a sheet with vacuum along a periodic axis, a slab).  Any grid
+// whose cells are at least the list radius wide yields the same (index-sorted) lists, so
+// this changes no result; it only removes empty cells from every rebuild's clear and scan.
+void coarsen_sparse_axes(const double *const xyz[3], int64_t n, const Box &box, int nc[3])
+{
+    for (int a = 0; a < 3; ++a) {
+        if (nc[a] < 4 || n <= 0) continue;
+        std::vector<char> occ((size_t)nc[a], 0);
+        int used = 0;
+        for (int64_t i = 0; i < n && 4 * used <= nc[a]; ++i) {
+            double x = xyz[a][i];
+            if (box.pbc[a]) x -= box.L[a] * std::floor(x * box.invL[a]);
+            int c = (int)std::floor(x * box.invL[a] * (double)nc[a]);
+            c = c < 0 ? 0 : (c >= nc[a] ? nc[a] - 1 : c);
+            if (!occ[(size_t)c]) {
+                occ[(size_t)c] = 1;
+                ++used;
+            }
+        }
+        if (4 * used <= nc[a]) nc[a] = 1;
+    }
+}
+
 // half-kick factors dt/2 * acc / m per type (same expression order as the oracle)
 void half_kick(const md_ctx *ctx, double dt, double *hk)
 {
@@ -283,32 +310,32 @@ struct Recorder {
     // Under capture the records must be "external" to become event-record nodes of the
     // graph (a plain record only marks a capture dependency); outside capture the flag
     // is not allowed, so a plain record is used there.
-    void rec(cudaEvent_t e) const
+    void rec(cudaEvent_t e, cudaStream_t st) const
     {
-        if (capturing) cudaEventRecordWithFlags(e, ctx->stream, cudaEventRecordExternal);
-        else cudaEventRecord(e, ctx->stream);
+        if (capturing) cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+        else cudaEventRecord(e, st);
     }
-    void begin(int kc) const
+    void begin(int kc, cudaStream_t st = nullptr) const
     {
-        if (ctx->profiling) rec(ctx->ev[step * KC_COUNT + kc].ev[0]);
+        if (ctx->profiling) rec(ctx->ev[step * KC_COUNT + kc].ev[0], st ? st : ctx->stream);
     }
-    void end(int kc) const
+    void end(int kc, cudaStream_t st = nullptr) const
     {
-        if (ctx->profiling) rec(ctx->ev[step * KC_COUNT + kc].ev[1]);
+        if (ctx->profiling) rec(ctx->ev[step * KC_COUNT + kc].ev[1], st ? st : ctx->stream);
     }
 };
 
-// Inside a capture on ctx->stream: a conditional IF node whose body is the list
-// rebuild, taken when the handle's value is non-zero.  The body is captured on the
-// side stream.  Returns the number of kernels in the body.
-md_status add_conditional_rebuild(md_ctx *ctx, cudaGraphConditionalHandle h)
+// Inside a capture on stream `on`: a conditional IF node whose body is the list rebuild
+// (pools, `with_pair`: followed by the pair pass of the rebuilt systems), taken when the
+// handle's value is non-zero.  The body is captured on the side stream.
+md_status add_conditional_rebuild(md_ctx *ctx, cudaGraphConditionalHandle h, cudaStream_t on, bool with_pair)
 {
     cudaStreamCaptureStatus cs;
     cudaGraph_t g = nullptr;
     const cudaGraphNode_t *deps = nullptr;
     const cudaGraphEdgeData *edges = nullptr;
     size_t nd = 0;
-    CK(cudaStreamGetCaptureInfo(ctx->stream, &cs, nullptr, &g, &deps, &edges, &nd));
+    CK(cudaStreamGetCaptureInfo(on, &cs, nullptr, &g, &deps, &edges, &nd));
     if (cs != cudaStreamCaptureStatusActive) return fail(ctx, MD_ERR_CUDA, "stream is not capturing");
     // the parameter union has no usable default constructor: zero a raw buffer instead
     alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
@@ -321,11 +348,49 @@ md_status add_conditional_rebuild(md_ctx *ctx, cudaGraphConditionalHandle h)
     cudaGraphNode_t node;
     CK(cudaGraphAddNode(&node, g, deps, edges, nd, &np));
     cudaGraph_t body = np.conditional.phGraph_out[0];
-    CK(cudaStreamUpdateCaptureDependencies(ctx->stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    CK(cudaStreamUpdateCaptureDependencies(on, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
     CK(cudaStreamBeginCaptureToGraph(ctx->side, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     ctx->kernels_per_rebuild = launch_rebuild(ctx->p, ctx->side);
+    if (with_pair) ctx->kernels_per_rebuild += launch_pair(ctx->p, ctx->side, PAIR_REBUILT, PAIR_FAST);
     cudaGraph_t out = nullptr;
     CK(cudaStreamEndCapture(ctx->side, &out));
+    return MD_OK;
+}
+
+// Pools, the rest of a step after the kick: the pair pass of the systems that keep their
+// lists runs while the others are rebuilt, on two branches of the graph:
+//   step begin -> stable plan (sets the rebuild conditional) -+-> pair(stable) -------------+
+//                                                             +-> IF: rebuild, pair(rebuilt) +
+//   -> deferred atoms' pair pass -> gather (+ half-kick) -> reduce (series row)
+// Each atom's work is the same as on a single branch, so results do not change.
+md_status enqueue_pool_tail(md_ctx *ctx, const Recorder &rec, const double *hk, double dt, int *n_kernels)
+{
+    cudaGraphConditionalHandle h;
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamGetCaptureInfo(ctx->stream, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+    CK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+    launch_step_begin(ctx->p, ctx->stream, nullptr);
+    launch_stable_plan(ctx->p, ctx->stream, &h);
+    CK(cudaEventRecord(ctx->ev_fork, ctx->stream));
+    CK(cudaStreamWaitEvent(ctx->side2, ctx->ev_fork, 0));
+    rec.begin(KC_REBUILD, ctx->side2);
+    md_status s = add_conditional_rebuild(ctx, h, ctx->side2, true);
+    if (s != MD_OK) return s;
+    rec.end(KC_REBUILD, ctx->side2);
+    rec.begin(KC_PAIR);
+    launch_pair(ctx->p, ctx->stream, PAIR_STABLE, PAIR_FAST);
+    CK(cudaEventRecord(ctx->ev_join, ctx->side2));
+    CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
+    launch_pair(ctx->p, ctx->stream, PAIR_ALL, PAIR_DEFERRED);
+    rec.end(KC_PAIR);
+    rec.begin(KC_GATHER);
+    launch_gather(ctx->p, ctx->stream, hk, dt, false);
+    rec.end(KC_GATHER);
+    rec.begin(KC_REDUCE);
+    launch_reduce(ctx->p, ctx->stream, false, true);
+    rec.end(KC_REDUCE);
+    *n_kernels = 8;   // active plan, kick, step begin, stable plan, 2 pair, gather, reduce
     return MD_OK;
 }
 
@@ -338,6 +403,7 @@ md_status enqueue_step(md_ctx *ctx, const Recorder &rec, const double *hk, doubl
     rec.begin(KC_KICK_DRIFT);
     launch_kick_drift(ctx->p, ctx->stream, hk, dt);
     rec.end(KC_KICK_DRIFT);
+    if (ctx->p.batch && ctx->p.N > 0) return enqueue_pool_tail(ctx, rec, hk, dt, n_kernels);
     rec.begin(KC_REBUILD);
     if (ctx->p.N > 0) {
         cudaGraphConditionalHandle h;
@@ -346,7 +412,7 @@ md_status enqueue_step(md_ctx *ctx, const Recorder &rec, const double *hk, doubl
         CK(cudaStreamGetCaptureInfo(ctx->stream, &cs, nullptr, &g, nullptr, nullptr, nullptr));
         CK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
         launch_step_begin(ctx->p, ctx->stream, &h);
-        md_status s = add_conditional_rebuild(ctx, h);
+        md_status s = add_conditional_rebuild(ctx, h, ctx->stream, false);
         if (s != MD_OK) return s;
     } else {
         launch_step_begin(ctx->p, ctx->stream, nullptr);   // no atoms: nothing to rebuild
@@ -564,7 +630,17 @@ md_status ctx_init(md_ctx *ctx, const md_options &opt)
         }
         ctx->own_stream = true;
     }
-    e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
+    // the rebuild branch of a pool step is a chain of short kernels beside a pair pass that
+    // fills the GPU: its streams get the highest priority so that its blocks go first
+    int prio_least = 0, prio_greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest) != cudaSuccess) {
+        cudaGetLastError();
+        prio_greatest = 0;
+    }
+    e = cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, prio_greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&ctx->side2, cudaStreamNonBlocking, prio_greatest);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return MD_ERR_CUDA;
@@ -647,6 +723,8 @@ md_status ctx_alloc(md_ctx *ctx)
     AL(p.rb_chunks, N1 / 128 + 1);
     AL(p.act_plan, 2);
     AL(p.act_chunks, N1 / 128 + 1);
+    AL(p.stable_plan, 2);
+    AL(p.stable_chunks, N1 / 128 + 1);
     p.nb_gather = gather_blocks(p.N);
     p.seg_max = 1;
     AL(p.partials, (size_t)p.nb_gather * kNumPartials);
@@ -665,6 +743,8 @@ md_status ctx_alloc(md_ctx *ctx)
     cudaMemsetAsync(p.type, 0, sizeof(int) * N1, ctx->stream);
     cudaMemsetAsync(p.totals, 0, sizeof(double) * p.n_sys * kNumPartials, ctx->stream);
     cudaMemsetAsync(p.act_plan, 0, sizeof(int) * 2, ctx->stream);
+    cudaMemsetAsync(p.stable_plan, 0, sizeof(int) * 2, ctx->stream);
+    cudaMemsetAsync(p.rb_plan, 0, sizeof(int) * 2, ctx->stream);
     return MD_OK;
 }
 
@@ -726,6 +806,7 @@ md_status md_create(md_ctx **out, const double box[3], const int pbc[3], int64_t
         return st;
     }
     p.ncell = (int64_t)p.nc[0] * p.nc[1] * p.nc[2];
+    for (int a = 0; a < 3; ++a) ctx->nc_full[a] = p.nc[a];
     p.batch = false;
     p.n_sys = 1;
     if ((st = ctx_init(ctx, opt)) != MD_OK || (st = ctx_alloc(ctx)) != MD_OK) {
@@ -860,6 +941,10 @@ md_status md_batch_add(md_ctx *ctx, const md_system *sysd, int *id_out)
     const int64_t max_cells = std::max<int64_t>(64, 4 * n);
     md_status st = system_box(p, rl, sysd->box, sysd->pbc, max_cells, &sd.box, sd.nc);
     if (st != MD_OK) return fail(ctx, st, "box too small for the cutoff");
+    if (ctx->io == MD_IO_HOST) {
+        const double *xyz[3] = {sysd->x, sysd->y, sysd->z};
+        coarsen_sparse_axes(xyz, n, sd.box, sd.nc);
+    }
     int id = -1;
     for (int k = 0; k < p.n_sys; ++k)
         if (!ctx->sys_used[k]) { id = k; break; }
@@ -990,6 +1075,16 @@ md_status md_set_positions(md_ctx *ctx, const double *x, const double *y, const 
     if (ctx->p.N > 0) {
         md_status s = upload3(ctx, ctx->p.pos, x, y, z);
         if (s != MD_OK) return s;
+        if (ctx->io == MD_IO_HOST) {   // cell grid for this configuration (within the allocated cells)
+            int nc[3] = {ctx->nc_full[0], ctx->nc_full[1], ctx->nc_full[2]};
+            const double *xyz[3] = {x, y, z};
+            coarsen_sparse_axes(xyz, ctx->p.N, ctx->p.box, nc);
+            if (nc[0] != ctx->p.nc[0] || nc[1] != ctx->p.nc[1] || nc[2] != ctx->p.nc[2]) {
+                for (int a = 0; a < 3; ++a) ctx->p.nc[a] = nc[a];
+                ctx->p.ncell = (int64_t)nc[0] * nc[1] * nc[2];
+                destroy_graph(ctx);   // the graphs carry the grid in their arguments
+            }
+        }
     }
     md_status s = set_flag_rebuild(ctx);
     if (s != MD_OK) return s;
@@ -1137,6 +1232,7 @@ md_status md_get_stats(md_ctx *ctx, md_stats *out)
     CK(cudaMemcpy(&deferred, ctx->p.ovf_count, sizeof(int), cudaMemcpyDeviceToHost));
     out->pair_deferred = deferred;
     out->device_bytes = ctx->allocated;
+    out->atoms_rebuilt = f.atoms_rebuilt;
     return MD_OK;
 }
 
@@ -1320,6 +1416,9 @@ void md_destroy(md_ctx *ctx)
         if (a) cudaFree(a);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     if (ctx->side) cudaStreamDestroy(ctx->side);
+    if (ctx->side2) cudaStreamDestroy(ctx->side2);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     delete ctx;
 }
 

@@ -71,6 +71,7 @@ struct Flags {
     long long row;        // series row of the step in flight
     int fresh_only;       // pools: the force evaluation in flight covers admitted systems only
     int pad2;
+    long long atoms_rebuilt;   // atoms whose list was built, summed over builds
 };
 
 // Pools: does atom work of system `sd` run now?  Stopped systems never; during the

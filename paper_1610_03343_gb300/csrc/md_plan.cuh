@@ -57,6 +57,7 @@ struct Plan {
     int64_t nscanb = 1;
     int *rb_plan = nullptr, *rb_sys = nullptr, *rb_chunks = nullptr;   // pool rebuild work lists
     int *act_plan = nullptr, *act_chunks = nullptr;   // pools: 128-atom chunks of the live systems
+    int *stable_plan = nullptr, *stable_chunks = nullptr;   // pools: the live systems not rebuilding
     // reductions
     double *partials = nullptr;
     int nb_gather = 1;
@@ -98,6 +99,11 @@ void launch_step_begin(const Plan &p, cudaStream_t s, const cudaGraphConditional
 // Pools: list the 128-atom chunks of the systems that run now (kick, pair and gather loop
 // over this list, so a step costs in proportion to the atoms resident and running).
 void launch_active_plan(const Plan &p, cudaStream_t s);
+// Pools: list the chunks of the running systems that do not rebuild their list this step
+// (taken after the kick's skin test), so that their pair pass need not wait for the
+// rebuild of the others; sets the rebuild conditional h (may be null) when any running
+// system is to be rebuilt or a rebuild was requested.
+void launch_stable_plan(const Plan &p, cudaStream_t s, const cudaGraphConditionalHandle *h);
 // Zero the pair pass's deferred-atom count (force evaluations outside a step).
 void launch_pair_reset(const Plan &p, cudaStream_t s);
 // Pools: mark every system as no longer fresh and end a fresh-only evaluation.
@@ -106,7 +112,13 @@ void launch_clear_fresh(const Plan &p, cudaStream_t s);
 // a pass whose shared-memory staging holds 4 bonds per atom (the crystals' common case),
 // which defers any atom with more to a list, and a pass over that list with the full
 // capacity.  Returns the number of kernels launched.
-int launch_pair(const Plan &p, cudaStream_t s);
+// Pools choose the atoms by chunk list: every running system (PAIR_ALL), those not
+// rebuilding (PAIR_STABLE) or those just rebuilt (PAIR_REBUILT, the rebuild plan's list);
+// `parts` selects the common-case launch (PAIR_FAST), the deferred atoms' launch
+// (PAIR_DEFERRED) or both.  Single systems ignore the list.
+enum { PAIR_ALL = 0, PAIR_STABLE = 1, PAIR_REBUILT = 2 };
+enum { PAIR_FAST = 1, PAIR_DEFERRED = 2, PAIR_BOTH = 3 };
+int launch_pair(const Plan &p, cudaStream_t s, int list = PAIR_ALL, int parts = PAIR_BOTH);
 // Per-atom gather: F_i (Eq. 28), J_i (Eq. 30) and, for a force evaluation, W_i (Eq. 29)
 // and per-atom outputs; optional half-kick (and per-system damping); block partials.
 void launch_gather(const Plan &p, cudaStream_t s, const double *half_kick, double dt, bool full_outputs);

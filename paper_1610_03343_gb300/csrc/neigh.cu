@@ -185,6 +185,45 @@ __device__ __forceinline__ int stencil_axis(int c, int nc, int periodic, int *ou
     return n;
 }
 
+// fp32 candidate test of the list build for atom i (coordinates xi, yi, zi, largest
+// magnitude mag_i) and atom j: minimum-image separation below rl0 widened by the rounding
+// of the larger coordinate of the two (the same test for (i, j) and (j, i)).  On success
+// *entry is j with the image shift it was found at.
+struct ListFrame {
+    float xi, yi, zi, mag_i, rl0, L0, L1, L2, iL0, iL1, iL2;
+    int p0, p1, p2;
+};
+__device__ __forceinline__ bool list_candidate(const ListFrame &f, float xj, float yj, float zj, int j, int *entry)
+{
+    float dx = xj - f.xi, dy = yj - f.yi, dz = zj - f.zi;
+    // image shift s in {-1, 0, 1}: r_ij = x_j - x_i + s L
+    const float sx = f.p0 ? -rintf(dx * f.iL0) : 0.f;
+    const float sy = f.p1 ? -rintf(dy * f.iL1) : 0.f;
+    const float sz = f.p2 ? -rintf(dz * f.iL2) : 0.f;
+    dx = fmaf(sx, f.L0, dx);
+    dy = fmaf(sy, f.L1, dy);
+    dz = fmaf(sz, f.L2, dz);
+    const float mag = fmaxf(f.mag_i, fmaxf(fabsf(xj), fmaxf(fabsf(yj), fabsf(zj))));
+    const float lim = f.rl0 + 32.f * mag * 1.1920929e-7f;
+    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    *entry = list_entry(j, (int)sx, (int)sy, (int)sz);
+    return r2 < lim * lim;
+}
+
+__device__ __forceinline__ ListFrame list_frame(const float *posf, int64_t N, int64_t i, const Box &box, float rlm2)
+{
+    ListFrame f;
+    f.xi = posf[i];
+    f.yi = posf[N + i];
+    f.zi = posf[2 * N + i];
+    f.mag_i = fmaxf(fabsf(f.xi), fmaxf(fabsf(f.yi), fabsf(f.zi)));
+    f.rl0 = sqrtf(rlm2);
+    f.L0 = (float)box.L[0]; f.L1 = (float)box.L[1]; f.L2 = (float)box.L[2];
+    f.iL0 = (float)box.invL[0]; f.iL1 = (float)box.invL[1]; f.iL2 = (float)box.invL[2];
+    f.p0 = box.pbc[0]; f.p1 = box.pbc[1]; f.p2 = box.pbc[2];
+    return f;
+}
+
 // One thread per atom: search the distinct neighbouring cells and keep every j != i
 // with |r_ij| < rl + margin (fp32, minimum image), in ascending index order, each with
 // the image shift it was found at.  Snapshots the build positions for the skin test.
@@ -210,54 +249,63 @@ __device__ __forceinline__ void build_list_atom(int64_t i, int64_t N, const doub
     pos_build[i] = pos[i];
     pos_build[N + i] = pos[N + i];
     pos_build[2 * N + i] = pos[2 * N + i];
-    const float xi = posf[i], yi = posf[N + i], zi = posf[2 * N + i];
-    // The box-based margin is widened, per pair, by the rounding of the larger of the two
-    // atoms' coordinates (on an open axis atoms may lie far outside the box); taking the
-    // larger of the two keeps the test symmetric in i and j.
-    const float rl0 = sqrtf(rlm2);
-    const float mag_i = fmaxf(fabsf(xi), fmaxf(fabsf(yi), fabsf(zi)));
-    const float L0 = (float)box.L[0], L1 = (float)box.L[1], L2 = (float)box.L[2];
-    const float iL0 = (float)box.invL[0], iL1 = (float)box.invL[1], iL2 = (float)box.invL[2];
+    const ListFrame fr = list_frame(posf, N, i, box, rlm2);
     const int c = (int)(atom_cell[i] - off);
     const int cz = c % nc[2], cy = (c / nc[2]) % nc[1], cx = c / (nc[1] * nc[2]);
     int ox[3], oy[3], oz[3];
     const int nx = stencil_axis(cx, nc[0], box.pbc[0], ox);
     const int ny = stencil_axis(cy, nc[1], box.pbc[1], oy);
     const int nz = stencil_axis(cz, nc[2], box.pbc[2], oz);
+    // the stencil cells' ranges first (independent loads), then their atoms as one
+    // sequence taken four at a time, so that four candidates' loads are in flight
+    const int ns = nx * ny * nz;
+    int cs[27], ce[27];
+    for (int l = 0; l < ns; ++l) {
+        const int a = l / (ny * nz), b = (l / nz) % ny, e = l % nz;
+        const long long cc = off + ((long long)ox[a] * nc[1] + oy[b]) * nc[2] + oz[e];
+        cs[l] = cell_start[cc];
+        ce[l] = cs[l] + cell_count[cc];
+    }
     int loc[kMaxListCap];
     int cnt = 0;
-    for (int a = 0; a < nx; ++a)
-        for (int b = 0; b < ny; ++b)
-            for (int e = 0; e < nz; ++e) {
-                const long long cc = off + (ox[a] * nc[1] + oy[b]) * nc[2] + oz[e];
-                const int s0 = cell_start[cc], s1 = s0 + cell_count[cc];
-                for (int q = s0; q < s1; ++q) {
-                    const int j = cell_atoms[q];
-                    if (j == (int)i) continue;
-                    float dx = posf[j] - xi, dy = posf[N + j] - yi, dz = posf[2 * N + j] - zi;
-                    // image shift s in {-1, 0, 1}: r_ij = x_j - x_i + s L
-                    const float sx = box.pbc[0] ? -rintf(dx * iL0) : 0.f;
-                    const float sy = box.pbc[1] ? -rintf(dy * iL1) : 0.f;
-                    const float sz = box.pbc[2] ? -rintf(dz * iL2) : 0.f;
-                    dx = fmaf(sx, L0, dx);
-                    dy = fmaf(sy, L1, dy);
-                    dz = fmaf(sz, L2, dz);
-                    const float mag = fmaxf(mag_i, fmaxf(fabsf(posf[j]), fmaxf(fabsf(posf[N + j]), fabsf(posf[2 * N + j]))));
-                    const float lim = rl0 + 32.f * mag * 1.1920929e-7f;
-                    if (dx * dx + dy * dy + dz * dz < lim * lim) {
-                        const int e_ = list_entry(j, (int)sx, (int)sy, (int)sz);
-                        if (cnt < cap) {       // insertion into the index-sorted prefix
-                            int m = cnt;
-                            while (m > 0 && list_atom(loc[m - 1]) > j) {
-                                loc[m] = loc[m - 1];
-                                --m;
-                            }
-                            loc[m] = e_;
-                        }
-                        ++cnt;
-                    }
-                }
+    int cell = 0, q = ns > 0 ? cs[0] : 0;
+    while (true) {
+        int jj[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            while (cell < ns && q >= ce[cell]) {
+                ++cell;
+                if (cell < ns) q = cs[cell];
             }
+            jj[u] = cell < ns ? cell_atoms[q++] : -1;
+        }
+        if (jj[0] < 0) break;
+        float xs[4], ys[4], zs[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int j = jj[u] < 0 ? (int)i : jj[u];
+            xs[u] = posf[j];
+            ys[u] = posf[N + j];
+            zs[u] = posf[2 * N + j];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int j = jj[u];
+            if (j < 0 || j == (int)i) continue;
+            int e_;
+            if (list_candidate(fr, xs[u], ys[u], zs[u], j, &e_)) {
+                if (cnt < cap) {       // insertion into the index-sorted prefix
+                    int m = cnt;
+                    while (m > 0 && list_atom(loc[m - 1]) > j) {
+                        loc[m] = loc[m - 1];
+                        --m;
+                    }
+                    loc[m] = e_;
+                }
+                ++cnt;
+            }
+        }
+    }
     const int keep = cnt < cap ? cnt : cap;
     for (int m = 0; m < keep; ++m) nl[(int64_t)m * N + i] = loc[m];
     nn[i] = keep;
@@ -470,14 +518,16 @@ __global__ void __launch_bounds__(kChunk) k_build_rev_pool(const int *plan, cons
 
 // Clear the rebuild requests (pools: every system's, then the global one).
 template <bool BATCH>
-__global__ void k_build_done(int n_sys, SysDev *sys, Flags *flags)
+__global__ void k_build_done(int n_sys, int64_t n_atoms, SysDev *sys, Flags *flags)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (BATCH && s < n_sys && sys[s].rebuild) {
         sys[s].rebuild = 0;
         sys[s].built = 1;
+        atomicAdd(reinterpret_cast<unsigned long long *>(&flags->atoms_rebuilt), (unsigned long long)sys[s].n_atoms);
     }
     if (s == 0) {
+        if (!BATCH) flags->atoms_rebuilt += n_atoms;
         flags->rebuild = 0;
         flags->n_rebuilds += 1;
     }
@@ -559,7 +609,7 @@ int rebuild_single(const Plan &p, cudaStream_t s)
                                                    p.atom_cell, p.cell_start, p.cell_count, p.cell_atoms,
                                                    rlm * rlm, p.cap, p.nn, p.nl, p.pos_build, p.flags);
     k_build_rev<<<blocks_for(p.N, T), T, 0, s>>>(p.N, p.nn, p.nl, p.rev, p.flags);
-    k_build_done<false><<<1, 1, 0, s>>>(p.n_sys, p.sys, p.flags);
+    k_build_done<false><<<1, 1, 0, s>>>(p.n_sys, p.N, p.sys, p.flags);
     return 8;
 }
 
@@ -581,7 +631,7 @@ int rebuild_pool(const Plan &p, cudaStream_t s)
                                             p.nl, p.pos_build, p.flags);
     k_build_rev_pool<<<gc, kChunk, 0, s>>>(p.rb_plan, p.rb_chunks, p.N, p.nn, p.nl, p.rev, p.sys_of, p.sys,
                                            p.flags);
-    k_build_done<true><<<blocks_for(p.n_sys, 256), 256, 0, s>>>(p.n_sys, p.sys, p.flags);
+    k_build_done<true><<<blocks_for(p.n_sys, 256), 256, 0, s>>>(p.n_sys, p.N, p.sys, p.flags);
     return 8;
 }
 
