@@ -316,16 +316,18 @@ class JobFactory:
                     types=np.full(pos.shape[0], elem, np.int32))
 
 
-def run_serve(args):
+def run_serve(args, rate=None, n_requests=None, seed=31):
     """Poisson arrivals into the serving loop; a waiter thread collects results in
     submission order (and releases each job's output buffers) while submission goes on."""
     import queue
     from paper_1610_03343_gb300 import md
-    rng = np.random.Generator(np.random.PCG64(31))
+    rate = args.serve_rate if rate is None else rate
+    n_requests = args.serve_requests if n_requests is None else n_requests
+    rng = np.random.Generator(np.random.PCG64(seed))
     fac = JobFactory()
-    jobs = [fac.make(k) for k in range(args.serve_requests)]
+    jobs = [fac.make(k) for k in range(n_requests)]
     sizes = [(j["pos"].shape[0], j["steps"]) for j in jobs]
-    gaps = rng.exponential(1.0 / args.serve_rate, size=len(jobs))
+    gaps = rng.exponential(1.0 / rate, size=len(jobs))
     results = []
     with md.Server(precision=md.MD_MIXED, tersoff_atoms=12_000_000, sw_atoms=6_000_000, max_jobs_per_pool=1024,
                    tersoff_dt=0.5, sw_dt=1.0, chunk_steps=8, tersoff_sets=[I.TERSOFF_SI_1989, I.TERSOFF_C_1989],
@@ -357,10 +359,14 @@ def run_serve(args):
     t0 = min(r.t_submit for r in results)
     t1 = max(r.t_done for r in results)
     work = sum(n * st_ for n, st_ in sizes)
-    return {"requests": len(sizes), "rate_per_s": args.serve_rate, "completed": int(st.completed),
+    # queue stable: the last tenth of the jobs waits no longer than twice the first tenth
+    tenth = max(1, len(lat) // 10)
+    stable = bool(np.mean(lat[-tenth:]) <= 2.0 * np.mean(lat[:tenth]))
+    return {"requests": len(sizes), "rate_per_s": rate, "completed": int(st.completed), "queue_stable": stable,
             "failed": int(st.failed), "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
             "mean_atoms": float(np.mean([n for n, _ in sizes])), "value": work / (t1 - t0), "unit": "atom-steps/s",
-            "offered": args.serve_rate * work / len(sizes), "precision": "mixed", "wall_s": t1 - t0,
+            "offered": rate * work / len(sizes), "precision": "mixed", "wall_s": t1 - t0,
+            "mean_job_atom_steps": work / len(sizes),
             "pool_seconds": {"busy": st.busy_seconds, "run": st.run_seconds, "admit": st.admit_seconds,
                              "harvest": st.harvest_seconds, "chunks": int(st.chunks)},
             "resident_atom_steps_per_run_s": st.resident_atom_steps / max(st.run_seconds, 1e-9)}
@@ -421,6 +427,8 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-requests-low", type=int, default=400,
+                    help="requests of each below-capacity serving run (50%% and 80%% of capacity)")
     ap.add_argument("--only", default="", choices=["", "batch", "serve"],
                     help="run one leg alone and print its JSON (diagnostics)")
     args = ap.parse_args()
@@ -515,6 +523,13 @@ def main():
     if not args.no_serve:
         out["serve"] = run_serve(args)
         out["serve"]["force_err_mixed_vs_fp64"] = mixed_force_error()
+        # below capacity: the same job mix at 50% and 80% of the capacity just measured
+        cap_jobs = out["serve"]["value"] / out["serve"]["mean_job_atom_steps"]
+        out["serve"]["capacity_jobs_per_s"] = cap_jobs
+        out["serve"]["below_capacity"] = [
+            {k: v for k, v in run_serve(args, rate=f * cap_jobs, n_requests=args.serve_requests_low, seed=41).items()
+             if k in ("rate_per_s", "requests", "p50_s", "p99_s", "value", "queue_stable", "completed")}
+            | {"fraction_of_capacity": f} for f in (0.5, 0.8)]
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args)
     print(json.dumps(out))

@@ -13,6 +13,7 @@ Functions follow the paper (arXiv:1610.03343) as documented in oracle.c:
   sw_conventional / sw_dUdr   the same two routes for Stillinger-Weber
   manybody_fwj         Eqs. 28-30 (F_i, W_i, J_i) from dU_i/dr_ij
   run                  velocity Verlet with per-step U, K, J
+  run_npt              the same with the Berendsen thermostat and barostat (NPT)
   hcacf, running_kappa Green-Kubo HCACF and thermal conductivity from a J series
                        (green_kubo.py, numpy)
 """
@@ -66,6 +67,7 @@ def _load():
         lib.oracle_sw_dUdr.argtypes = [I64, P, P, P, P, P, P, I, P, P, P, P]
         lib.oracle_manybody_fwj.argtypes = [I64, P, P, P, P, P, I, P, P, P, P, P, P, P, P, P]
         lib.oracle_run.argtypes = [I64, P, P, P, P, P, P, P, P, P, I, P, I, I64, D, D, P]
+        lib.oracle_run_ex.argtypes = [I64, P, P, P, P, P, P, P, P, P, I, P, I, I64, D, D, P, P]
         for f in ("oracle_neighbors_brute", "oracle_neighbors_cells", "oracle_tersoff_conventional",
                   "oracle_tersoff_dUdr", "oracle_sw_conventional", "oracle_sw_dUdr",
                   "oracle_manybody_fwj", "oracle_run"):
@@ -226,6 +228,29 @@ def run(pos, vel, masses, box, pbc, kind, params, n_steps, dt, cap=32, damp=0.0)
         raise RuntimeError(f"oracle_run failed: {rc}")
     return (np.stack([x, y, z], axis=1), np.stack([vx, vy, vz], axis=1),
             series[:5 * n_steps].reshape(n_steps, 5))
+
+
+def run_npt(pos, vel, masses, box, pbc, kind, params, n_steps, dt, T0=300.0, P0=0.0, tau_T=100.0, tau_P=1000.0,
+            beta=0.01, couple=(1, 1, 1), cap=32, damp=0.0):
+    """Velocity Verlet with the Berendsen thermostat and barostat (oracle.c,
+    oracle_run_ex): returns (pos, vel, series[n_steps, 5], box).  The scaling computed at
+    the last step is left pending, as the library leaves it for its next run."""
+    lib = _load()
+    x, y, z = _soa(pos)
+    vx, vy, vz = _soa(vel)
+    n = x.shape[0]
+    m = np.ascontiguousarray(np.broadcast_to(np.asarray(masses, dtype=np.float64), (n,)))
+    b, p = _box(box, pbc)
+    b = np.array(b, dtype=np.float64)
+    prm = np.ascontiguousarray(params, dtype=np.float64)
+    npt = np.array([T0, P0, tau_T, tau_P, beta, *[float(c) for c in couple]], dtype=np.float64)
+    series = np.zeros(5 * max(n_steps, 1))
+    rc = lib.oracle_run_ex(n, _p(x), _p(y), _p(z), _p(vx), _p(vy), _p(vz), _p(m), _p(b), _p(p), int(kind),
+                           _p(prm), int(cap), int(n_steps), float(dt), float(damp), _p(npt), _p(series))
+    if rc != 0:
+        raise RuntimeError(f"oracle_run_ex failed: {rc}")
+    return (np.stack([x, y, z], axis=1), np.stack([vx, vy, vz], axis=1),
+            series[:5 * n_steps].reshape(n_steps, 5), b)
 
 
 def kinetic_energy(vel, masses):

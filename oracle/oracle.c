@@ -21,7 +21,8 @@
  *   - the many-body per-atom force, virial and heat current of Eqs. 28-30 from it;
  *   - the same two routes for Stillinger-Weber (Stillinger & Weber 1985 energy; the
  *     three-body term is assigned to its vertex atom);
- *   - velocity-Verlet integration (Sec. 3), neighbour lists rebuilt every step.
+ *   - velocity-Verlet integration (Sec. 3), neighbour lists rebuilt every step, and
+ *     the Berendsen thermostat and barostat of the paper's NPT runs (Sec. 3).
  *
  * Conventions: r_ij = r_j - r_i (Sec. 2.1, below Eq. 6).  Per-atom arrays are SoA
  * (x[0..N), y, z; 3-vectors as F[0..N) = Fx, F[N..2N) = Fy, F[2N..3N) = Fz).  Per-atom
@@ -627,23 +628,52 @@ static void conventional_forces(int kind, int64_t N, const double *x, const doub
  * series (n_steps x 5, or NULL) receives U, K, Jx, Jy, Jz after every step.
  * masses: per-atom masses (amu).  x, y, z, vx, vy, vz are updated in place.
  * Returns 0, -1 on allocation failure, -3 on neighbour overflow. */
-int oracle_run(int64_t N, double *x, double *y, double *z, double *vx, double *vy, double *vz,
-               const double *masses, const double *box, const int *pbc, int kind,
-               const double *params, int cap, int64_t n_steps, double dt, double damp, double *series)
+/* Berendsen weak coupling (Berendsen et al., J. Chem. Phys. 81, 3684 (1984)), the NPT
+ * ensemble the paper's benchmarks run in (Sec. 3: 300 K, 0 Pa).  At the end of step s,
+ * with K = sum_i m_i v_i^2 / 2, K_aa = sum_i m_i v_ia^2 / 2, the total virial W (the sum of
+ * the Eq. 29 per-atom virials) and V = Lx Ly Lz:
+ *     T      = 2 K / (k_B (3N - 3)),
+ *     lambda = sqrt(1 + (dt / tau_T) (T0 / T - 1)),
+ *     P_aa   = (2 K_aa + W_aa) / V                      (converted to GPa),
+ *     mu_a   = cbrt(1 - (beta dt / tau_P) (P0 - P_aa))  on each coupled periodic axis, else 1.
+ * The velocities are multiplied by lambda and every coordinate and box edge along a by
+ * mu_a at the start of step s + 1, before its half-kick; the scaling computed at the last
+ * step of a run is not applied (it stays pending).  tau_T <= 0 or tau_P <= 0 switches that
+ * half off.  npt = {T0 (K), P0 (GPa), tau_T (fs), tau_P (fs), beta (1/GPa), couple_x,
+ * couple_y, couple_z}. */
+static const double K_BOLTZMANN = 8.617333262e-5;            /* eV / K */
+static const double EV_PER_A3_IN_GPA = 160.21766340;          /* 1.602176634e-19 J / 1e-30 m^3 */
+
+int oracle_run_ex(int64_t N, double *x, double *y, double *z, double *vx, double *vy, double *vz,
+                  const double *masses, double *box, const int *pbc, int kind, const double *params, int cap,
+                  int64_t n_steps, double dt, double damp, const double *npt, double *series)
 {
     double rc = pot_cutoff(kind, params);
-    int *NN = (int *)malloc(sizeof(int) * (size_t)(N > 0 ? N : 1));
-    int *NL = (int *)malloc(sizeof(int) * (size_t)(cap * (N > 0 ? N : 1)));
-    double *U = (double *)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
-    double *F = (double *)malloc(sizeof(double) * 3 * (size_t)(N > 0 ? N : 1));
-    double *D = (double *)malloc(sizeof(double) * 3 * (size_t)cap * (size_t)(N > 0 ? N : 1));
-    double *Jv = (double *)malloc(sizeof(double) * 3 * (size_t)(N > 0 ? N : 1));
-    double *Ud = (double *)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
+    size_t n1 = (size_t)(N > 0 ? N : 1);
+    int *NN = (int *)malloc(sizeof(int) * n1);
+    int *NL = (int *)malloc(sizeof(int) * (size_t)cap * n1);
+    double *U = (double *)malloc(sizeof(double) * n1);
+    double *F = (double *)malloc(sizeof(double) * 3 * n1);
+    double *D = (double *)malloc(sizeof(double) * 3 * (size_t)cap * n1);
+    double *Jv = (double *)malloc(sizeof(double) * 3 * n1);
+    double *Wv = (double *)malloc(sizeof(double) * 9 * n1);
+    double *Ud = (double *)malloc(sizeof(double) * n1);
+    double lam = 1.0, mu[3] = {1.0, 1.0, 1.0};
+    int pending = 0;
     int rc_status = 0;
-    if (!NN || !NL || !U || !F || !D || !Jv || !Ud) { rc_status = -1; goto done; }
+    if (!NN || !NL || !U || !F || !D || !Jv || !Wv || !Ud) { rc_status = -1; goto done; }
     if (build_list(N, x, y, z, box, pbc, rc, cap, NN, NL) > cap) { rc_status = -3; goto done; }
     conventional_forces(kind, N, x, y, z, box, pbc, params, NN, NL, U, F);
     for (int64_t s = 0; s < n_steps; ++s) {
+        if (pending) {   /* Berendsen scaling computed at the end of the previous step */
+            double *c[3] = {x, y, z};
+            for (int64_t i = 0; i < N; ++i) {
+                vx[i] *= lam; vy[i] *= lam; vz[i] *= lam;
+                for (int a = 0; a < 3; ++a) c[a][i] *= mu[a];
+            }
+            for (int a = 0; a < 3; ++a) box[a] *= mu[a];
+            pending = 0;
+        }
         for (int64_t i = 0; i < N; ++i) {
             double h = 0.5 * dt * ACC_UNIT / masses[i];
             vx[i] += h * F[i]; vy[i] += h * F[N + i]; vz[i] += h * F[2 * N + i];
@@ -657,7 +687,7 @@ int oracle_run(int64_t N, double *x, double *y, double *z, double *vx, double *v
         }
         if (build_list(N, x, y, z, box, pbc, rc, cap, NN, NL) > cap) { rc_status = -3; goto done; }
         conventional_forces(kind, N, x, y, z, box, pbc, params, NN, NL, U, F);
-        double Ut = 0.0, K = 0.0, Jt[3] = {0, 0, 0};
+        double Ut = 0.0, K = 0.0, Kaa[3] = {0, 0, 0}, Jt[3] = {0, 0, 0}, Waa[3] = {0, 0, 0};
         for (int64_t i = 0; i < N; ++i) {
             double h = 0.5 * dt * ACC_UNIT / masses[i];
             vx[i] += h * F[i]; vy[i] += h * F[N + i]; vz[i] += h * F[2 * N + i];
@@ -667,17 +697,49 @@ int oracle_run(int64_t N, double *x, double *y, double *z, double *vx, double *v
             }
             Ut += U[i];
             K += 0.5 * masses[i] * (vx[i] * vx[i] + vy[i] * vy[i] + vz[i] * vz[i]) / ACC_UNIT;
+            Kaa[0] += 0.5 * masses[i] * vx[i] * vx[i] / ACC_UNIT;
+            Kaa[1] += 0.5 * masses[i] * vy[i] * vy[i] / ACC_UNIT;
+            Kaa[2] += 0.5 * masses[i] * vz[i] * vz[i] / ACC_UNIT;
         }
         if (kind == ORACLE_TERSOFF) oracle_tersoff_dUdr(N, x, y, z, box, pbc, params, cap, NN, NL, Ud, D);
         else oracle_sw_dUdr(N, x, y, z, box, pbc, params, cap, NN, NL, Ud, D);
-        oracle_manybody_fwj(N, x, y, z, box, pbc, cap, NN, NL, D, vx, vy, vz, NULL, NULL, Jv);
+        oracle_manybody_fwj(N, x, y, z, box, pbc, cap, NN, NL, D, vx, vy, vz, NULL, npt ? Wv : NULL, Jv);
         for (int64_t i = 0; i < N; ++i) for (int a = 0; a < 3; ++a) Jt[a] += Jv[a * N + i];
         if (series) {
             series[5 * s + 0] = Ut; series[5 * s + 1] = K;
             series[5 * s + 2] = Jt[0]; series[5 * s + 3] = Jt[1]; series[5 * s + 4] = Jt[2];
         }
+        if (npt) {
+            for (int64_t i = 0; i < N; ++i) for (int a = 0; a < 3; ++a) Waa[a] += Wv[(4 * a) * N + i];
+            double T0 = npt[0], P0 = npt[1], tauT = npt[2], tauP = npt[3], beta = npt[4];
+            double ndof = 3.0 * (double)N - 3.0;
+            double T = ndof > 0 ? 2.0 * K / (K_BOLTZMANN * ndof) : 0.0;
+            lam = 1.0;
+            if (tauT > 0.0 && T > 0.0) {
+                double l2 = 1.0 + dt / tauT * (T0 / T - 1.0);
+                lam = l2 > 0.0 ? sqrt(l2) : 0.0;
+            }
+            double V = box[0] * box[1] * box[2];
+            for (int a = 0; a < 3; ++a) {
+                mu[a] = 1.0;
+                if (tauP > 0.0 && pbc[a] && npt[5 + a] != 0.0) {
+                    double P = (2.0 * Kaa[a] + Waa[a]) / V * EV_PER_A3_IN_GPA;
+                    mu[a] = cbrt(1.0 - beta * dt / tauP * (P0 - P));
+                }
+            }
+            pending = 1;
+        }
     }
 done:
-    free(NN); free(NL); free(U); free(F); free(D); free(Jv); free(Ud);
+    free(NN); free(NL); free(U); free(F); free(D); free(Jv); free(Wv); free(Ud);
     return rc_status;
+}
+
+int oracle_run(int64_t N, double *x, double *y, double *z, double *vx, double *vy, double *vz,
+               const double *masses, const double *box, const int *pbc, int kind,
+               const double *params, int cap, int64_t n_steps, double dt, double damp, double *series)
+{
+    double b[3] = {box[0], box[1], box[2]};
+    return oracle_run_ex(N, x, y, z, vx, vy, vz, masses, b, pbc, kind, params, cap, n_steps, dt, damp, NULL,
+                         series);
 }
