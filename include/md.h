@@ -131,6 +131,41 @@ md_status md_run(md_ctx *ctx, int64_t n_steps, double dt_fs, double *series);
 /* Current positions and velocities, each 3N SoA; either may be NULL. */
 md_status md_get_state(md_ctx *ctx, double *x, double *v);
 
+/* Berendsen weak coupling (NPT).  The paper's benchmarks run in the NPT ensemble at 300 K
+ * and 0 Pa (Sec. 3) without printing the coupling; this is Berendsen et al., J. Chem.
+ * Phys. 81, 3684 (1984).  At the end of every md_run step, from that step's totals,
+ *   T      = 2K / (k_B (3N - 3)),      lambda = sqrt(1 + dt/tau_T (T0/T - 1))  (0 if negative),
+ *   P_aa   = (2 K_aa + W_aa) / V,      mu_a   = cbrt(1 - beta dt/tau_P (P0 - P_aa)),
+ * with K_aa = sum_i m_i v_ia^2 / 2, W the total virial (the sum of the per-atom virials of
+ * Eq. 29), V = Lx Ly Lz, P in GPa (1 eV/A^3 = 160.2176634 GPa).  The next step starts by
+ * multiplying every velocity by lambda and every coordinate and box edge along a by mu_a
+ * (mu_a = 1 on open axes, uncoupled axes, or tau_P <= 0; lambda = 1 for tau_T <= 0), then
+ * takes its half-kick.  The scaling computed at the last step of a call stays pending and
+ * is applied at the first step of the next md_run (so consecutive calls continue one
+ * trajectory); md_set_positions drops it.  Everything runs on the device inside the
+ * graph-replayed steps (the host is not involved between steps).
+ *   system: 0 for md_create contexts; a pool's slot id.
+ *   npt:    the coupling, or NULL to return the system to NVE (its list is then rebuilt).
+ *           T0 >= 0, beta >= 0, all finite; couple[a] in {0, 1}.  Setting new constants on
+ *           a coupled system keeps its pending scaling.
+ * The box changes: md_get_box reads it.  The neighbour list stays exact: the skin test
+ * allows for the scaling since the last build, and a cell grid whose cells became
+ * narrower than the list radius is coarsened on the device.  A periodic edge that shrinks
+ * below 2 (cutoff + skin) + 0.01 A makes md_run return MD_ERR_BOX.  MD_ERR_ARG for a bad
+ * system or parameter. */
+typedef struct {
+    double T0;      /* bath temperature (K)                                  */
+    double P0;      /* bath pressure (GPa), the same on every coupled axis   */
+    double tau_T;   /* thermostat time constant (fs); <= 0: no thermostat    */
+    double tau_P;   /* barostat time constant (fs); <= 0: no barostat        */
+    double beta;    /* isothermal compressibility (1/GPa)                    */
+    int couple[3];  /* 1: the barostat scales this (periodic) axis           */
+} md_npt;
+md_status md_set_npt(md_ctx *ctx, int system, const md_npt *npt);
+
+/* Current box edges (A) of a system (0 for md_create contexts; a pool's slot id). */
+md_status md_get_box(md_ctx *ctx, int system, double box[3]);
+
 /* Counters for tests and benchmarks. */
 typedef struct {
     int64_t n_atoms;

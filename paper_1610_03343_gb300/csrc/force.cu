@@ -440,6 +440,9 @@ __device__ __forceinline__ void pair_dispatch(const PairArgs<T> &a, const Sets &
             const SysDev &sd = a.sys[a.sys_of[i]];
             if (!system_live(sd, a.flags)) return;
             fn(ps.s[sd.pset], sd.box, i);
+        } else if (a.dev_box) {
+            const Box bx = a.sys[0].box;
+            fn(ps.s[0], bx, i);
         } else {
             fn(ps.s[0], a.box, i);
         }
@@ -577,11 +580,13 @@ __device__ __forceinline__ void block_partials(const double (&vals)[NC], int seg
 }
 
 // FULL: a force evaluation (per-atom F, W, J stored; U, K, J, W partials) or a
-// velocity-Verlet step (F and the kick only; U, K, J partials).
-template <typename T, int MAXA, int BLOCK, bool FULL, bool BATCH>
+// velocity-Verlet step (F and the kick only; U, K, J partials).  NPT (steps): also the
+// diagonal kinetic and virial partials K_aa, W_aa that the barostat's pressure needs.
+template <typename T, int MAXA, int BLOCK, bool FULL, bool BATCH, bool NPT>
 __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, int64_t bidx)
 {
-    constexpr int NC = FULL ? kNumPartials : kStepPartials;
+    constexpr int NC = FULL ? kNumPartials : (NPT ? kNptPartials : kStepPartials);
+    constexpr bool WDIAG = NPT && !FULL;
     const int64_t N = a.N;
     double vals[NC];
 #pragma unroll
@@ -600,6 +605,7 @@ __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, i
         uint32_t mask = a.mask[i];
         T f0 = 0, f1 = 0, f2 = 0;
         T w[9], mj[9];
+        T wd0 = 0, wd1 = 0, wd2 = 0;
 #pragma unroll
         for (int c = 0; c < 9; ++c) { w[c] = 0; mj[c] = 0; }
         int k = 0;
@@ -624,6 +630,7 @@ __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, i
                     w[3] += ry * gx; w[4] += ry * gy; w[5] += ry * gz;
                     w[6] += rz * gx; w[7] += rz * gy; w[8] += rz * gz;
                 }
+                if (WDIAG) { wd0 += rx * gx; wd1 += ry * gy; wd2 += rz * gz; }
                 mj[0] += rx * ex; mj[1] += rx * ey; mj[2] += rx * ez;
                 mj[3] += ry * ex; mj[4] += ry * ey; mj[5] += ry * ez;
                 mj[6] += rz * ex; mj[7] += rz * ey; mj[8] += rz * ez;
@@ -662,6 +669,15 @@ __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, i
         vals[2] = double(J0);
         vals[3] = double(J1);
         vals[4] = double(J2);
+        if (WDIAG) {
+            const T hm = T(0.5 / kAccUnit) * T(a.mass[t]);
+            vals[5] = double(hm * vx * vx);
+            vals[6] = double(hm * vy * vy);
+            vals[7] = double(hm * vz * vz);
+            vals[8] = -0.5 * double(wd0);
+            vals[9] = -0.5 * double(wd1);
+            vals[10] = -0.5 * double(wd2);
+        }
         if (FULL) {
 #pragma unroll
             for (int c = 0; c < 9; ++c) vals[5 + c] = -0.5 * double(w[c]);
@@ -681,7 +697,7 @@ __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, i
 
 // Single system: one thread per atom.  Pools: loop over the live systems' chunks (a
 // chunk is one gather block: every system starts on a chunk boundary).
-template <typename T, int MAXA, int BLOCK, bool FULL, bool BATCH>
+template <typename T, int MAXA, int BLOCK, bool FULL, bool BATCH, bool NPT>
 __global__ void __launch_bounds__(BLOCK) k_gather(GatherArgs<T> a)
 {
     static_assert(BLOCK == kPoolChunk, "a gather block is one pool chunk");
@@ -689,25 +705,25 @@ __global__ void __launch_bounds__(BLOCK) k_gather(GatherArgs<T> a)
         const int nch = *a.act_count;
         for (int k = blockIdx.x; k < nch; k += gridDim.x) {
             const int64_t c0 = a.act_chunks[k];
-            gather_atom<T, MAXA, BLOCK, FULL, BATCH>(a, c0 + threadIdx.x, c0 / BLOCK);
+            gather_atom<T, MAXA, BLOCK, FULL, BATCH, NPT>(a, c0 + threadIdx.x, c0 / BLOCK);
         }
     } else {
-        gather_atom<T, MAXA, BLOCK, FULL, BATCH>(a, (int64_t)blockIdx.x * BLOCK + threadIdx.x, blockIdx.x);
+        gather_atom<T, MAXA, BLOCK, FULL, BATCH, NPT>(a, (int64_t)blockIdx.x * BLOCK + threadIdx.x, blockIdx.x);
     }
 }
 
 
 
 // One block per (system, component): that system's block partials of that component
-// added in a fixed order; totals[s NC_ALL + c] and, when recording,
-// series[(row n_sys + s) 5 + c].  Pools: a system that ran this step counts down its
+// added in a fixed order; totals[s NC_ALL + c] (an NPT step's K_aa, W_aa components:
+// npt_totals[s kNptExtra + c - 5]) and, when recording, series[(row n_sys + s) 5 + c].  Pools: a system that ran this step counts down its
 // step budget (component-0 block) and stops at zero.
 constexpr int kReduceThreads = 512;       // single system: thousands of blocks to add
 constexpr int kReduceThreadsPool = 128;   // pools: one reduction per system
 template <bool BATCH>
 __global__ void __launch_bounds__(kReduceThreads)
 k_reduce(const double *partials, int nc, int seg_max, int64_t N, int block, const int *sys_of, SysDev *sys,
-         int n_sys, double *totals, double *series, Flags *flags, bool record)
+         int n_sys, double *totals, double *npt_totals, double *series, Flags *flags, bool record)
 {
     __shared__ double red[kReduceThreads / 32];
     const int s = blockIdx.x, c = blockIdx.y;
@@ -733,7 +749,8 @@ k_reduce(const double *partials, int nc, int seg_max, int64_t N, int block, cons
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-        totals[(int64_t)s * kNumPartials + c] = t;
+        if (nc == kNptPartials && c >= kStepPartials) npt_totals[(int64_t)s * kNptExtra + c - kStepPartials] = t;
+        else totals[(int64_t)s * kNumPartials + c] = t;
         if (record && c < kStepPartials) series[(flags->row * n_sys + s) * kStepPartials + c] = t;
         if (BATCH && record && c == 0 && sys[s].steps_left > 0) {
             sys[s].steps_left -= 1;
@@ -752,7 +769,8 @@ struct KickDriftArgs {
     const int *sys_of;
     SysDev *sys;
     double *pos, *vel;
-    const double *force, *pos_build;
+    const double *force;
+    double *pos_build;      // scaled with the positions under NPT
     const int *type;
     double hk[kMaxTypes];   // dt/2 * acc / m per type
     double dt;
@@ -762,41 +780,114 @@ struct KickDriftArgs {
 
 // v += F/m dt/2; x += v dt (no wrap: positions are wrapped when the list is rebuilt);
 // request a rebuild when an atom has moved more than skin/2 since the last build.
-template <bool BATCH>
+// NPT: a pending Berendsen scaling is applied first (v *= lambda; x, x_build *= mu), and
+// the skin test takes the box scaling since the build into account (npt_half_skin2).
+template <bool BATCH, bool NPT>
 __device__ __forceinline__ void kick_drift_atom(const KickDriftArgs &a, int64_t i)
 {
     if (i >= a.N) return;
     if (BATCH && !a.sys[a.sys_of[i]].active) return;
     const int64_t N = a.N;
     const double h = a.hk[a.type[i]];
+    const SysDev *sdp = NPT ? (BATCH ? &a.sys[a.sys_of[i]] : a.sys) : nullptr;
+    const bool scale = NPT && sdp->npt.on && sdp->npt.pending;
     float d2 = 0.f;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const double v = fma(h, a.force[c * N + i], a.vel[c * N + i]);
-        const double x = fma(a.dt, v, a.pos[c * N + i]);
+        double v0 = a.vel[c * N + i], x0 = a.pos[c * N + i], xb = a.pos_build[c * N + i];
+        if (scale) {
+            v0 *= sdp->npt.lam;
+            x0 *= sdp->npt.mu[c];
+            xb *= sdp->npt.mu[c];
+            a.pos_build[c * N + i] = xb;
+        }
+        const double v = fma(h, a.force[c * N + i], v0);
+        const double x = fma(a.dt, v, x0);
         a.vel[c * N + i] = v;
         a.pos[c * N + i] = x;
         if (a.posf) a.posf[c * N + i] = (float)x;
-        const float d = (float)(x - a.pos_build[c * N + i]);
+        const float d = (float)(x - xb);
         d2 = fmaf(d, d, d2);
     }
-    const float hs2 = BATCH ? a.sys[a.sys_of[i]].half_skin2 : a.half_skin2;
+    const float hs2 = (NPT && sdp->npt.on) ? npt_half_skin2(*sdp, true)
+                                           : (BATCH ? a.sys[a.sys_of[i]].half_skin2 : a.half_skin2);
     if (!(d2 <= hs2)) {
         a.flags->rebuild = 1;
         if (BATCH) a.sys[a.sys_of[i]].rebuild = 1;
     }
 }
 
-template <bool BATCH>
+template <bool BATCH, bool NPT>
 __global__ void k_kick_drift(KickDriftArgs a)
 {
     if (BATCH) {
         const int nch = *a.act_count;
         for (int k = blockIdx.x; k < nch; k += gridDim.x)
-            for (int t = threadIdx.x; t < kPoolChunk; t += blockDim.x) kick_drift_atom<true>(a, (int64_t)a.act_chunks[k] + t);
+            for (int t = threadIdx.x; t < kPoolChunk; t += blockDim.x)
+                kick_drift_atom<true, NPT>(a, (int64_t)a.act_chunks[k] + t);
     } else {
-        kick_drift_atom<false>(a, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+        kick_drift_atom<false, NPT>(a, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
     }
+}
+
+// ------------------------------------------------------------------ Berendsen (NPT)
+constexpr double kBoltzmann = 8.617333262e-5;        // eV / K (CODATA 2018, exact)
+constexpr double kEvPerA3InGPa = 160.21766340;       // 1 eV / A^3 = 1.602176634e-19 J / 1e-30 m^3
+
+// After the kick of a step: the kick scaled the velocities and coordinates of every
+// running coupled system with a pending scaling; scale its box edges the same way,
+// shrink its cell grid where a cell became narrower than the stencil needs, and clear the
+// pending flag.  A periodic edge below 2 cell edges + 0.01 A sets flags->box_error (the
+// minimum image would no longer be unique).  One thread per system.
+__global__ void k_npt_apply(int n_sys, SysDev *sys, int batch, Flags *flags)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_sys) return;
+    SysDev &sd = sys[s];
+    if (!sd.npt.on || !sd.npt.pending) return;
+    if (batch && !sd.active) return;   // the kick skipped it too
+    for (int a = 0; a < 3; ++a) {
+        const double m = sd.npt.mu[a];
+        sd.box.L[a] *= m;
+        sd.box.invL[a] = 1.0 / sd.box.L[a];
+        sd.npt.mu_cum[a] *= m;
+        if (sd.box.pbc[a]) {
+            if (!(sd.box.L[a] >= 2.0 * sd.cell_edge + 0.01)) flags->box_error = 1;
+            const int fit = (int)floor(sd.box.L[a] / sd.cell_edge);
+            if (fit < sd.nc[a]) sd.nc[a] = fit < 1 ? 1 : fit;
+        }
+    }
+    sd.npt.pending = 0;
+}
+
+// At the end of a step: lambda and mu of every coupled system from this step's totals
+// (K, U in totals; K_aa, W_aa in npt_totals), left pending for the next step's kick.
+__global__ void k_npt_couple(int n_sys, SysDev *sys, const double *totals, const double *npt_totals, double dt)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_sys) return;
+    SysDev &sd = sys[s];
+    if (!sd.npt.on || sd.n_atoms < 1) return;
+    const double K = totals[(int64_t)s * kNumPartials + 1];
+    const double *e = npt_totals + (int64_t)s * kNptExtra;
+    const double ndof = 3.0 * (double)sd.n_atoms - 3.0;
+    const double T = ndof > 0.0 ? 2.0 * K / (kBoltzmann * ndof) : 0.0;
+    double lam = 1.0;
+    if (sd.npt.tau_T > 0.0 && T > 0.0) {
+        const double l2 = 1.0 + dt / sd.npt.tau_T * (sd.npt.T0 / T - 1.0);
+        lam = l2 > 0.0 ? sqrt(l2) : 0.0;
+    }
+    const double V = sd.box.L[0] * sd.box.L[1] * sd.box.L[2];
+    for (int a = 0; a < 3; ++a) {
+        double m = 1.0;
+        if (sd.npt.tau_P > 0.0 && sd.box.pbc[a] && sd.npt.couple[a]) {
+            const double P = (2.0 * e[a] + e[3 + a]) / V * kEvPerA3InGPa;
+            m = cbrt(1.0 - sd.npt.beta * dt / sd.npt.tau_P * (sd.npt.P0 - P));
+        }
+        sd.npt.mu[a] = m;
+    }
+    sd.npt.lam = lam;
+    sd.npt.pending = 1;
 }
 
 __global__ void k_step_begin(Flags *flags, int *ovf_count, cudaGraphConditionalHandle h, int has_cond)
@@ -863,6 +954,7 @@ void pair_launch_b(const Plan &p, cudaStream_t s, int list, int parts)
     a.N = p.N;
     a.box = p.box;
     a.pos = p.pos;
+    a.dev_box = (!BATCH && p.npt) ? 1 : 0;
     a.nn = p.nn;
     a.nl = p.nl;
     a.cap = p.cap;
@@ -947,9 +1039,11 @@ void gather_launch(const Plan &p, cudaStream_t s, const double *hk, double dt, b
     a.act_chunks = p.act_chunks;
     const unsigned nb = BATCH ? pool_grid(p) : blocks_for(p.N, kGatherBlock);
     if (full)
-        k_gather<T, MAXA, kGatherBlock, true, BATCH><<<nb, kGatherBlock, 0, s>>>(a);
+        k_gather<T, MAXA, kGatherBlock, true, BATCH, false><<<nb, kGatherBlock, 0, s>>>(a);
+    else if (p.npt)
+        k_gather<T, MAXA, kGatherBlock, false, BATCH, true><<<nb, kGatherBlock, 0, s>>>(a);
     else
-        k_gather<T, MAXA, kGatherBlock, false, BATCH><<<nb, kGatherBlock, 0, s>>>(a);
+        k_gather<T, MAXA, kGatherBlock, false, BATCH, false><<<nb, kGatherBlock, 0, s>>>(a);
 }
 
 }  // namespace
@@ -993,8 +1087,13 @@ void launch_kick_drift(const Plan &p, cudaStream_t s, const double *hk, double d
     a.flags = p.flags;
     a.act_count = p.act_plan;
     a.act_chunks = p.act_chunks;
-    if (p.batch) k_kick_drift<true><<<pool_grid(p), kPoolChunk, 0, s>>>(a);
-    else k_kick_drift<false><<<blocks_for(p.N, 256), 256, 0, s>>>(a);
+    if (p.batch) {
+        if (p.npt) k_kick_drift<true, true><<<pool_grid(p), kPoolChunk, 0, s>>>(a);
+        else k_kick_drift<true, false><<<pool_grid(p), kPoolChunk, 0, s>>>(a);
+    } else {
+        if (p.npt) k_kick_drift<false, true><<<blocks_for(p.N, 256), 256, 0, s>>>(a);
+        else k_kick_drift<false, false><<<blocks_for(p.N, 256), 256, 0, s>>>(a);
+    }
 }
 
 void launch_step_begin(const Plan &p, cudaStream_t s, const cudaGraphConditionalHandle *h)
@@ -1063,16 +1162,28 @@ void launch_gather(const Plan &p, cudaStream_t s, const double *hk, double dt, b
 
 void launch_reduce(const Plan &p, cudaStream_t s, bool full, bool record_series)
 {
-    const int nc = full ? kNumPartials : kStepPartials;
+    const int nc = full ? kNumPartials : (p.npt ? kNptPartials : kStepPartials);
     const bool rec = record_series && p.series != nullptr;
     if (p.batch)
         k_reduce<true><<<dim3(p.n_sys, nc), kReduceThreadsPool, 0, s>>>(p.partials, nc, p.seg_max, p.N, kGatherBlock,
-                                                                    p.sys_of, p.sys, p.n_sys, p.totals, p.series,
-                                                                    p.flags, rec);
+                                                                    p.sys_of, p.sys, p.n_sys, p.totals,
+                                                                    p.npt_totals, p.series, p.flags, rec);
     else
         k_reduce<false><<<dim3(1, nc), kReduceThreads, 0, s>>>(p.partials, nc, p.seg_max, p.N, kGatherBlock,
-                                                               p.sys_of, p.sys, 1, p.totals, p.series, p.flags,
-                                                               rec);
+                                                               p.sys_of, p.sys, 1, p.totals, p.npt_totals,
+                                                               p.series, p.flags, rec);
+}
+
+void launch_npt_apply(const Plan &p, cudaStream_t s)
+{
+    if (!p.npt || p.N == 0) return;
+    k_npt_apply<<<(unsigned)((p.n_sys + 127) / 128), 128, 0, s>>>(p.n_sys, p.sys, p.batch ? 1 : 0, p.flags);
+}
+
+void launch_npt_couple(const Plan &p, cudaStream_t s, double dt)
+{
+    if (!p.npt || p.N == 0) return;
+    k_npt_couple<<<(unsigned)((p.n_sys + 127) / 128), 128, 0, s>>>(p.n_sys, p.sys, p.totals, p.npt_totals, dt);
 }
 
 int gather_block() { return kGatherBlock; }

@@ -182,9 +182,10 @@ md_status set_flag_rebuild(md_ctx *ctx)
 // Reset the per-call error words (the rebuild request and counters persist).
 md_status clear_error_flags(md_ctx *ctx)
 {
-    const int zeros[4] = {0, 0, 0, 0};
+    static const int zeros[4] = {0, 0, 0, 0};
     CK(cudaMemcpyAsync(&ctx->p.flags->list_overflow, zeros, 4 * sizeof(int), cudaMemcpyHostToDevice,
                        ctx->stream));
+    CK(cudaMemcpyAsync(&ctx->p.flags->box_error, zeros, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
     return MD_OK;
 }
 
@@ -207,6 +208,10 @@ md_status check_flags(md_ctx *ctx)
         return fail(ctx, MD_ERR_NEIGH_OVERFLOW, "more in-cutoff neighbours than max_active");
     if (f.asym) return fail(ctx, MD_ERR_CUDA, "internal: asymmetric neighbour list");
     if (f.nonfinite) return fail(ctx, MD_ERR_NAN, "non-finite force");
+    if (f.box_error) {
+        ctx->forces_valid = false;
+        return fail(ctx, MD_ERR_BOX, "NPT: a periodic box edge shrank below 2 (cutoff + skin)");
+    }
     return MD_OK;
 }
 
@@ -389,8 +394,10 @@ md_status enqueue_pool_tail(md_ctx *ctx, const Recorder &rec, const double *hk, 
     rec.end(KC_GATHER);
     rec.begin(KC_REDUCE);
     launch_reduce(ctx->p, ctx->stream, false, true);
+    launch_npt_couple(ctx->p, ctx->stream, dt);
     rec.end(KC_REDUCE);
-    *n_kernels = 8;   // active plan, kick, step begin, stable plan, 2 pair, gather, reduce
+    // active plan, kick, step begin, stable plan, 2 pair, gather, reduce (+ NPT apply, couple)
+    *n_kernels = 8 + (ctx->p.npt ? 2 : 0);
     return MD_OK;
 }
 
@@ -402,6 +409,7 @@ md_status enqueue_step(md_ctx *ctx, const Recorder &rec, const double *hk, doubl
     launch_active_plan(ctx->p, ctx->stream);
     rec.begin(KC_KICK_DRIFT);
     launch_kick_drift(ctx->p, ctx->stream, hk, dt);
+    launch_npt_apply(ctx->p, ctx->stream);
     rec.end(KC_KICK_DRIFT);
     if (ctx->p.batch && ctx->p.N > 0) return enqueue_pool_tail(ctx, rec, hk, dt, n_kernels);
     rec.begin(KC_REBUILD);
@@ -426,9 +434,10 @@ md_status enqueue_step(md_ctx *ctx, const Recorder &rec, const double *hk, doubl
     rec.end(KC_GATHER);
     rec.begin(KC_REDUCE);
     launch_reduce(ctx->p, ctx->stream, false, true);
+    launch_npt_couple(ctx->p, ctx->stream, dt);
     rec.end(KC_REDUCE);
     // kernels launched every step; a taken rebuild adds the body's kernels
-    *n_kernels = (ctx->p.N > 0 ? 6 : 2) + (ctx->p.batch ? 1 : 0);
+    *n_kernels = (ctx->p.N > 0 ? 6 : 2) + (ctx->p.batch ? 1 : 0) + (ctx->p.npt && ctx->p.N > 0 ? 2 : 0);
     return MD_OK;
 }
 
@@ -441,6 +450,7 @@ md_status eager_step(md_ctx *ctx, const double *hk, double dt)
     launch_active_plan(ctx->p, ctx->stream);
     rec.begin(KC_KICK_DRIFT);
     launch_kick_drift(ctx->p, ctx->stream, hk, dt);
+    launch_npt_apply(ctx->p, ctx->stream);
     rec.end(KC_KICK_DRIFT);
     launch_step_begin(ctx->p, ctx->stream, nullptr);
     int rebuild = 0;
@@ -457,6 +467,7 @@ md_status eager_step(md_ctx *ctx, const double *hk, double dt)
     rec.end(KC_GATHER);
     rec.begin(KC_REDUCE);
     launch_reduce(ctx->p, ctx->stream, false, true);
+    launch_npt_couple(ctx->p, ctx->stream, dt);
     rec.end(KC_REDUCE);
     CK(cudaGetLastError());
     return MD_OK;
@@ -729,6 +740,7 @@ md_status ctx_alloc(md_ctx *ctx)
     p.seg_max = 1;
     AL(p.partials, (size_t)p.nb_gather * kNumPartials);
     AL(p.totals, (size_t)p.n_sys * kNumPartials);
+    AL(p.npt_totals, (size_t)p.n_sys * kNptExtra);
     AL(p.flags, 1);
 #undef AL
     st = ensure_series(ctx, 1024);
@@ -742,6 +754,7 @@ md_status ctx_alloc(md_ctx *ctx)
     cudaMemsetAsync(p.mask, 0, sizeof(uint32_t) * N1, ctx->stream);
     cudaMemsetAsync(p.type, 0, sizeof(int) * N1, ctx->stream);
     cudaMemsetAsync(p.totals, 0, sizeof(double) * p.n_sys * kNumPartials, ctx->stream);
+    cudaMemsetAsync(p.npt_totals, 0, sizeof(double) * p.n_sys * kNptExtra, ctx->stream);
     cudaMemsetAsync(p.act_plan, 0, sizeof(int) * 2, ctx->stream);
     cudaMemsetAsync(p.stable_plan, 0, sizeof(int) * 2, ctx->stream);
     cudaMemsetAsync(p.rb_plan, 0, sizeof(int) * 2, ctx->stream);
@@ -821,6 +834,11 @@ md_status md_create(md_ctx **out, const double box[3], const int pbc[3], int64_t
     sd.n_atoms = p.N;
     sd.steps_left = -1;
     sd.active = 1;
+    sd.rc = p.rc;
+    sd.rl = p.rl;
+    sd.cell_edge = p.rl + p.list_margin;
+    sd.half_skin2 = (float)(0.25 * p.skin * p.skin);
+    sd.npt.mu_cum[0] = sd.npt.mu_cum[1] = sd.npt.mu_cum[2] = 1.0;
     ctx->sys_host.assign(2, SysDev{});
     ctx->sys_host[0] = sd;
     if ((st = upload_sys_table(ctx)) != MD_OK) {
@@ -938,6 +956,10 @@ md_status md_batch_add(md_ctx *ctx, const md_system *sysd, int *id_out)
     const double rl = rc + skin;
     sd.rlm2 = (float)((rl + p.list_margin) * (rl + p.list_margin));
     sd.half_skin2 = (float)(0.25 * skin * skin);
+    sd.rc = rc;
+    sd.rl = rl;
+    sd.cell_edge = rl + p.list_margin;
+    sd.npt.mu_cum[0] = sd.npt.mu_cum[1] = sd.npt.mu_cum[2] = 1.0;
     const int64_t max_cells = std::max<int64_t>(64, 4 * n);
     md_status st = system_box(p, rl, sysd->box, sysd->pbc, max_cells, &sd.box, sd.nc);
     if (st != MD_OK) return fail(ctx, st, "box too small for the cutoff");
@@ -1075,16 +1097,30 @@ md_status md_set_positions(md_ctx *ctx, const double *x, const double *y, const 
     if (ctx->p.N > 0) {
         md_status s = upload3(ctx, ctx->p.pos, x, y, z);
         if (s != MD_OK) return s;
-        if (ctx->io == MD_IO_HOST) {   // cell grid for this configuration (within the allocated cells)
-            int nc[3] = {ctx->nc_full[0], ctx->nc_full[1], ctx->nc_full[2]};
+        if (ctx->p.npt) {   // the barostat may have scaled the box: take the device's
+            if ((s = download_sys_table(ctx)) != MD_OK) return s;
+            ctx->p.box = ctx->sys_host[0].box;
+        }
+        // cell grid for this box and configuration (within the allocated cells)
+        int nc[3] = {ctx->nc_full[0], ctx->nc_full[1], ctx->nc_full[2]};
+        if (ctx->p.npt)
+            for (int a = 0; a < 3; ++a) {
+                const int fit = (int)std::floor(ctx->p.box.L[a] / ctx->sys_host[0].cell_edge);
+                nc[a] = std::max(1, std::min(nc[a], fit));
+            }
+        if (ctx->io == MD_IO_HOST) {
             const double *xyz[3] = {x, y, z};
             coarsen_sparse_axes(xyz, ctx->p.N, ctx->p.box, nc);
-            if (nc[0] != ctx->p.nc[0] || nc[1] != ctx->p.nc[1] || nc[2] != ctx->p.nc[2]) {
-                for (int a = 0; a < 3; ++a) ctx->p.nc[a] = nc[a];
-                ctx->p.ncell = (int64_t)nc[0] * nc[1] * nc[2];
-                destroy_graph(ctx);   // the graphs carry the grid in their arguments
-            }
         }
+        if (nc[0] != ctx->p.nc[0] || nc[1] != ctx->p.nc[1] || nc[2] != ctx->p.nc[2]) {
+            for (int a = 0; a < 3; ++a) ctx->p.nc[a] = nc[a];
+            ctx->p.ncell = (int64_t)nc[0] * nc[1] * nc[2];
+            destroy_graph(ctx);   // the graphs carry the grid in their arguments
+        }
+        // the system entry: same grid; new positions drop a pending Berendsen scaling
+        for (int a = 0; a < 3; ++a) ctx->sys_host[0].nc[a] = nc[a];
+        ctx->sys_host[0].npt.pending = 0;
+        CK(cudaMemcpyAsync(&ctx->p.sys[0], &ctx->sys_host[0], sizeof(SysDev), cudaMemcpyHostToDevice, ctx->stream));
     }
     md_status s = set_flag_rebuild(ctx);
     if (s != MD_OK) return s;
@@ -1199,6 +1235,80 @@ md_status md_run(md_ctx *ctx, int64_t n_steps, double dt_fs, double *series)
         ctx->forces_valid = false;
         return s;
     }
+    return MD_OK;
+}
+
+md_status md_set_npt(md_ctx *ctx, int system, const md_npt *npt)
+{
+    if (!ctx) return MD_ERR_ARG;
+    const bool pool = ctx->is_pool;
+    if (system < 0 || system >= ctx->p.n_sys || (pool && !ctx->sys_used[system]))
+        return fail(ctx, MD_ERR_ARG, "no such system");
+    if (npt) {
+        const bool ok = std::isfinite(npt->T0) && npt->T0 >= 0 && std::isfinite(npt->P0) &&
+                        std::isfinite(npt->tau_T) && std::isfinite(npt->tau_P) && std::isfinite(npt->beta) &&
+                        npt->beta >= 0;
+        if (!ok) return fail(ctx, MD_ERR_ARG, "bad NPT coupling parameters");
+        for (int a = 0; a < 3; ++a)
+            if (npt->couple[a] != 0 && npt->couple[a] != 1) return fail(ctx, MD_ERR_ARG, "couple[] must be 0 or 1");
+    }
+    md_status s = download_sys_table(ctx);   // current device state: box, budgets, scaling
+    if (s != MD_OK) return s;
+    SysDev &sd = ctx->sys_host[system];
+    const bool was_on = sd.npt.on != 0;
+    if (npt) {
+        sd.npt.on = 1;
+        sd.npt.T0 = npt->T0;
+        sd.npt.P0 = npt->P0;
+        sd.npt.tau_T = npt->tau_T;
+        sd.npt.tau_P = npt->tau_P;
+        sd.npt.beta = npt->beta;
+        for (int a = 0; a < 3; ++a) sd.npt.couple[a] = npt->couple[a];
+        if (!was_on) {
+            sd.npt.pending = 0;
+            sd.npt.lam = 1.0;
+            sd.npt.mu[0] = sd.npt.mu[1] = sd.npt.mu[2] = 1.0;
+        }
+    } else {
+        // back to NVE: drop a pending scaling; the plain skin test is exact only for a
+        // list built in the current box, so rebuild
+        sd.npt.on = 0;
+        sd.npt.pending = 0;
+        if (was_on) sd.rebuild = 1;
+    }
+    CK(cudaMemcpyAsync(&ctx->p.sys[system], &sd, sizeof(SysDev), cudaMemcpyHostToDevice, ctx->stream));
+    if (!npt && was_on) {
+        s = set_flag_rebuild(ctx);
+        if (s != MD_OK) return s;
+    }
+    bool any = false;
+    for (int k = 0; k < ctx->p.n_sys; ++k)
+        if ((!pool || ctx->sys_used[k]) && ctx->sys_host[k].npt.on) any = true;
+    // pools keep the NPT step once a system was coupled (uncoupled systems are unaffected);
+    // a single system returns to the by-value box and grid of the NVE step
+    const bool want = pool ? (ctx->p.npt || any) : any;
+    if (want != ctx->p.npt) {
+        if (!pool && !want) {
+            ctx->p.box = ctx->sys_host[0].box;
+            for (int a = 0; a < 3; ++a) ctx->p.nc[a] = ctx->sys_host[0].nc[a];
+            ctx->p.ncell = (int64_t)ctx->p.nc[0] * ctx->p.nc[1] * ctx->p.nc[2];
+        }
+        ctx->p.npt = want;
+        destroy_graph(ctx);
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return MD_OK;
+}
+
+md_status md_get_box(md_ctx *ctx, int system, double box[3])
+{
+    if (!ctx || !box) return MD_ERR_ARG;
+    if (system < 0 || system >= ctx->p.n_sys || (ctx->is_pool && !ctx->sys_used[system]))
+        return fail(ctx, MD_ERR_ARG, "no such system");
+    SysDev sd;
+    CK(cudaMemcpyAsync(&sd, &ctx->p.sys[system], sizeof(SysDev), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int a = 0; a < 3; ++a) box[a] = sd.box.L[a];
     return MD_OK;
 }
 

@@ -40,6 +40,27 @@ struct Box {
 // n_atoms), its own box, cell grid (cells [cell_off, cell_off + nc0 nc1 nc2)) and
 // parameter set.  The table lives in device memory; the host edits it between calls.
 constexpr int kMaxSets = 4;
+
+// Berendsen weak coupling of one system to a heat bath and a pressure bath (NPT;
+// Berendsen et al., J. Chem. Phys. 81, 3684 (1984)), the ensemble of the paper's
+// benchmarks (Sec. 3: 300 K, 0 Pa).  At the end of a step, from that step's totals,
+//   lambda = sqrt(1 + dt/tau_T (T0/T - 1)),              T = 2K / (k_B (3N - 3)),
+//   mu_a   = cbrt(1 - beta dt/tau_P (P0 - P_aa)),        P_aa = (2 K_aa + W_aa) / V,
+// with W the total virial (the sum of Eq. 29); the next step starts by multiplying the
+// velocities by lambda and every coordinate and box edge along a by mu_a.
+struct NptDev {
+    int on;               // 1: couple this system; 0: NVE (or damped)
+    int couple[3];        // the barostat scales this axis (periodic axes only)
+    double T0, P0;        // K, GPa
+    double tau_T, tau_P;  // fs (<= 0: that half is off)
+    double beta;          // isothermal compressibility, 1/GPa
+    double lam;           // pending velocity scale ...
+    double mu[3];         // ... and coordinate / edge scales
+    int pending;          // 1: lam, mu computed at the end of the last step, not yet applied
+    int pad;
+    double mu_cum[3];     // product of the edge scales applied since the last list build
+};
+
 struct SysDev {
     Box box;
     int nc[3];
@@ -55,6 +76,10 @@ struct SysDev {
     int rebuild;              // 1: rebuild this system's lists at the next rebuild
     int built;                // 1 once its lists exist
     int fresh;                // 1 until its first force evaluation (just admitted)
+    double rc;                // potential cutoff of this system's parameter set
+    double rl;                // list radius rc + skin
+    double cell_edge;         // smallest cell edge the 27-cell stencil allows (rl + fp32 margin)
+    NptDev npt;
 };
 
 // Device status words written by kernels and read by the host after a call.
@@ -66,7 +91,7 @@ struct Flags {
     int asym;             // a pair was missing from the partner's list
     int max_nn;           // longest list at the last build
     int n_rebuilds;       // builds since creation
-    int pad;
+    int box_error;        // NPT: a periodic edge shrank below 2 (list radius + margin)
     long long step;       // index of the next series row
     long long row;        // series row of the step in flight
     int fresh_only;       // pools: the force evaluation in flight covers admitted systems only
@@ -116,7 +141,8 @@ struct PairArgs {
     T *d;                   // 3 x S x N : d[(c S + k) N + i] = dU_i/dr_ij (component c)
     T *r;                   // 3 x S x N : r_ij
     const int *sys_of;      // N: system of each atom (pools)
-    const SysDev *sys;      // system table (pools)
+    const SysDev *sys;      // system table (pools; a single system: its one entry)
+    int dev_box;            // single system: read the box from sys[0] (it changes under NPT)
     int *ovf_count;         // atoms deferred by the small-capacity pass ...
     int *ovf_list;          // ... and their indices (capacity N)
     const int *act_count;   // pools: number of live 128-atom chunks ...
@@ -156,9 +182,30 @@ struct GatherArgs {
     Flags *flags;
 };
 
-// per-block partial sums: U, K, J(3), W(9); a velocity-Verlet step needs the first 5
+// per-block partial sums: U, K, J(3), W(9); a velocity-Verlet step needs the first 5,
+// a step under Berendsen coupling (NPT) those 5 and K_aa(3), W_aa(3) (totals of the last
+// 6 go to a separate n_sys x 6 array)
 constexpr int kNumPartials = 14;
 constexpr int kStepPartials = 5;
+constexpr int kNptPartials = 11;
+constexpr int kNptExtra = kNptPartials - kStepPartials;
+
+// Skin test of a system under box scaling.  Positions and build positions are scaled
+// together, so x - x_build is the displacement that scaling does not explain.  A pair
+// left out of the list at the build (|r| > rl) now has |r| >= mu_min rl - 2 max|x - x_build|,
+// mu_min the smallest per-axis scale since the build; it stays outside the cutoff rc
+// while every displacement is below (mu_min rl - rc) / 2.  Returns that bound squared,
+// or -1 (rebuild now) when it is not positive.
+__host__ __device__ __forceinline__ float npt_half_skin2(const SysDev &sd, bool with_pending)
+{
+    double mmin = 1e300;
+    for (int a = 0; a < 3; ++a) {
+        const double m = sd.npt.mu_cum[a] * (with_pending && sd.npt.pending ? sd.npt.mu[a] : 1.0);
+        mmin = m < mmin ? m : mmin;
+    }
+    const double h = 0.5 * (mmin * sd.rl - sd.rc);
+    return h > 0.0 ? (float)(h * h) : -1.0f;
+}
 
 // r_ij from positions and a list entry's image code (three fp64 subtractions, plus
 // one addition per shifted axis).

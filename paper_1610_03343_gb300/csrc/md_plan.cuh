@@ -58,6 +58,11 @@ struct Plan {
     int *rb_plan = nullptr, *rb_sys = nullptr, *rb_chunks = nullptr;   // pool rebuild work lists
     int *act_plan = nullptr, *act_chunks = nullptr;   // pools: 128-atom chunks of the live systems
     int *stable_plan = nullptr, *stable_chunks = nullptr;   // pools: the live systems not rebuilding
+    // Berendsen coupling (NPT): some system of the context is coupled; steps then scale
+    // velocities, coordinates and boxes on the device, and kernels of a single system read
+    // its box and cell grid from sys[0]
+    bool npt = false;
+    double *npt_totals = nullptr;   // n_sys x kNptExtra: K_aa (3), W_aa (3) of the last step
     // reductions
     double *partials = nullptr;
     int nb_gather = 1;
@@ -127,5 +132,12 @@ int gather_blocks(int64_t N);
 // Fixed-order reduction of the gather's block partials into per-system totals (and a
 // series row).
 void launch_reduce(const Plan &p, cudaStream_t s, bool full_outputs, bool record_series);
+// NPT, right after the kick of a step: scale the box edges of the coupled systems by the
+// pending mu (the kick scaled velocities and coordinates), shrink cell grids that became
+// too fine for the stencil, and clear the pending scaling.
+void launch_npt_apply(const Plan &p, cudaStream_t s);
+// NPT, at the end of a step: lambda and mu of each coupled system from the step's
+// totals, left pending for the next step.
+void launch_npt_couple(const Plan &p, cudaStream_t s, double dt);
 
 }  // namespace mdk

@@ -50,6 +50,9 @@ __device__ __forceinline__ void cell_count_atom(int64_t i, int64_t N, double *po
         bp = &sd.box;
         nc[0] = sd.nc[0]; nc[1] = sd.nc[1]; nc[2] = sd.nc[2];
         off = sd.cell_off;
+    } else if (sys) {   // single system under NPT: the box and grid of sys[0]
+        bp = &sys[0].box;
+        nc[0] = sys[0].nc[0]; nc[1] = sys[0].nc[1]; nc[2] = sys[0].nc[2];
     }
     const Box &box = *bp;
     int cc[3];
@@ -244,6 +247,9 @@ __device__ __forceinline__ void build_list_atom(int64_t i, int64_t N, const doub
         nc[0] = sd.nc[0]; nc[1] = sd.nc[1]; nc[2] = sd.nc[2];
         off = sd.cell_off;
         rlm2 = sd.rlm2;
+    } else if (sys) {   // single system under NPT: the box and grid of sys[0]
+        bp = &sys[0].box;
+        nc[0] = sys[0].nc[0]; nc[1] = sys[0].nc[1]; nc[2] = sys[0].nc[2];
     }
     const Box &box = *bp;
     pos_build[i] = pos[i];
@@ -332,11 +338,12 @@ __device__ __forceinline__ void build_rev_atom(int64_t i, int64_t N, const int *
 }
 
 // Single system: one thread per atom.
+// sys1: null, or (NPT) the system whose device box and grid replace box and nc.
 __global__ void k_cell_count(int64_t N, double *pos, float *posf, Box box, int nc0, int nc1, int nc2,
-                             int *atom_cell, int *atom_rank, int *count)
+                             const SysDev *sys1, int *atom_cell, int *atom_rank, int *count)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < N) cell_count_atom<false>(i, N, pos, posf, box, nc0, nc1, nc2, nullptr, nullptr, atom_cell, atom_rank, count);
+    if (i < N) cell_count_atom<false>(i, N, pos, posf, box, nc0, nc1, nc2, nullptr, sys1, atom_cell, atom_rank, count);
 }
 __global__ void k_cell_fill(int64_t N, const int *atom_cell, const int *atom_rank, const int *cell_start,
                             int *cell_atoms)
@@ -345,13 +352,13 @@ __global__ void k_cell_fill(int64_t N, const int *atom_cell, const int *atom_ran
     if (i < N) cell_fill_atom<false>(i, atom_cell, atom_rank, cell_start, cell_atoms, nullptr, nullptr);
 }
 __global__ void k_build_list(int64_t N, const double *pos, const float *posf, Box box, int nc0, int nc1, int nc2,
-                             const int *atom_cell, const int *cell_start, const int *cell_count,
-                             const int *cell_atoms, float rlm2, int cap, int *nn, int *nl, double *pos_build,
-                             Flags *flags)
+                             const SysDev *sys1, const int *atom_cell, const int *cell_start,
+                             const int *cell_count, const int *cell_atoms, float rlm2, int cap, int *nn, int *nl,
+                             double *pos_build, Flags *flags)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < N)
-        build_list_atom<false>(i, N, pos, posf, box, nc0, nc1, nc2, nullptr, nullptr, atom_cell, cell_start,
+        build_list_atom<false>(i, N, pos, posf, box, nc0, nc1, nc2, nullptr, sys1, atom_cell, cell_start,
                                cell_count, cell_atoms, rlm2, cap, nn, nl, pos_build, flags);
 }
 __global__ void k_build_rev(int64_t N, const int *nn, const int *nl, uint8_t *rev, Flags *flags)
@@ -516,7 +523,8 @@ __global__ void __launch_bounds__(kChunk) k_build_rev_pool(const int *plan, cons
         build_rev_atom<true>(chunks[k] + threadIdx.x, N, nn, nl, rev, sys_of, sys, flags);
 }
 
-// Clear the rebuild requests (pools: every system's, then the global one).
+// Clear the rebuild requests (pools: every system's, then the global one).  The build
+// positions are now the wrapped positions: no box scaling since the build (NPT).
 template <bool BATCH>
 __global__ void k_build_done(int n_sys, int64_t n_atoms, SysDev *sys, Flags *flags)
 {
@@ -524,25 +532,34 @@ __global__ void k_build_done(int n_sys, int64_t n_atoms, SysDev *sys, Flags *fla
     if (BATCH && s < n_sys && sys[s].rebuild) {
         sys[s].rebuild = 0;
         sys[s].built = 1;
+        sys[s].npt.mu_cum[0] = sys[s].npt.mu_cum[1] = sys[s].npt.mu_cum[2] = 1.0;
         atomicAdd(reinterpret_cast<unsigned long long *>(&flags->atoms_rebuilt), (unsigned long long)sys[s].n_atoms);
     }
     if (s == 0) {
-        if (!BATCH) flags->atoms_rebuilt += n_atoms;
+        if (!BATCH) {
+            flags->atoms_rebuilt += n_atoms;
+            sys[0].npt.mu_cum[0] = sys[0].npt.mu_cum[1] = sys[0].npt.mu_cum[2] = 1.0;
+        }
         flags->rebuild = 0;
         flags->n_rebuilds += 1;
     }
 }
 
 // skin/2 test.  Positions are not wrapped between builds, so x - x_build is the true
-// displacement; the difference is taken in fp64 and squared in fp32.
+// displacement; the difference is taken in fp64 and squared in fp32.  NPT systems use the
+// bound that accounts for the box scaling since the build.
 template <bool BATCH>
 __global__ void k_displacement(int64_t N, const double *pos, const double *pos_build, float half_skin2,
-                               const int *sys_of, SysDev *sys, Flags *flags)
+                               const int *sys_of, SysDev *sys, int npt, Flags *flags)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     if (BATCH && !sys[sys_of[i]].active) return;
     if (BATCH) half_skin2 = sys[sys_of[i]].half_skin2;
+    if (npt) {
+        const SysDev &sd = BATCH ? sys[sys_of[i]] : sys[0];
+        if (sd.npt.on) half_skin2 = npt_half_skin2(sd, false);
+    }
     float d2 = 0.f;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -558,11 +575,11 @@ __global__ void k_displacement(int64_t N, const double *pos, const double *pos_b
 // Wrapped copy of the positions (for output): dst[3N] = pos wrapped into [0, L).
 template <bool BATCH>
 __global__ void k_wrap_copy(int64_t N, int64_t a0, int64_t n, const double *pos, double *dst, Box box0,
-                            const int *sys_of, const SysDev *sys)
+                            const int *sys_of, const SysDev *sys, int dev_box)
 {
     const int64_t i = a0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a0 + n) return;
-    const Box &box = BATCH ? sys[sys_of[i]].box : box0;
+    const Box &box = BATCH ? sys[sys_of[i]].box : (dev_box ? sys[0].box : box0);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         double x = pos[a * N + i];
@@ -596,7 +613,8 @@ int rebuild_single(const Plan &p, cudaStream_t s)
     const int T = 256;
     cudaMemsetAsync(p.cell_count, 0, sizeof(int) * p.ncell, s);
     cudaMemsetAsync(&p.flags->max_nn, 0, sizeof(int), s);
-    k_cell_count<<<blocks_for(p.N, T), T, 0, s>>>(p.N, p.pos, p.posf, p.box, p.nc[0], p.nc[1], p.nc[2],
+    const SysDev *sys1 = p.npt ? p.sys : nullptr;
+    k_cell_count<<<blocks_for(p.N, T), T, 0, s>>>(p.N, p.pos, p.posf, p.box, p.nc[0], p.nc[1], p.nc[2], sys1,
                                                  p.atom_cell, p.atom_rank, p.cell_count);
     const int64_t nb = (p.ncell + kScanElems - 1) / kScanElems;
     k_scan_blocks<<<(unsigned)nb, kScanThreads, 0, s>>>(p.ncell, p.cell_count, p.cell_start, p.scan_blocks);
@@ -605,7 +623,7 @@ int rebuild_single(const Plan &p, cudaStream_t s)
     k_cell_fill<<<blocks_for(p.N, T), T, 0, s>>>(p.N, p.atom_cell, p.atom_rank, p.cell_start, p.cell_atoms);
     const int TB = 128;
     const float rlm = (float)p.rl + p.list_margin;
-    k_build_list<<<blocks_for(p.N, TB), TB, 0, s>>>(p.N, p.pos, p.posf, p.box, p.nc[0], p.nc[1], p.nc[2],
+    k_build_list<<<blocks_for(p.N, TB), TB, 0, s>>>(p.N, p.pos, p.posf, p.box, p.nc[0], p.nc[1], p.nc[2], sys1,
                                                    p.atom_cell, p.cell_start, p.cell_count, p.cell_atoms,
                                                    rlm * rlm, p.cap, p.nn, p.nl, p.pos_build, p.flags);
     k_build_rev<<<blocks_for(p.N, T), T, 0, s>>>(p.N, p.nn, p.nl, p.rev, p.flags);
@@ -648,10 +666,10 @@ void launch_displacement_check(const Plan &p, cudaStream_t s)
     const double hs = 0.5 * p.skin;
     if (p.batch)
         k_displacement<true><<<blocks_for(p.N, T), T, 0, s>>>(p.N, p.pos, p.pos_build, (float)(hs * hs),
-                                                             p.sys_of, p.sys, p.flags);
+                                                             p.sys_of, p.sys, p.npt ? 1 : 0, p.flags);
     else
         k_displacement<false><<<blocks_for(p.N, T), T, 0, s>>>(p.N, p.pos, p.pos_build, (float)(hs * hs),
-                                                              p.sys_of, p.sys, p.flags);
+                                                              p.sys_of, p.sys, p.npt ? 1 : 0, p.flags);
 }
 
 void launch_wrap_copy(const Plan &p, cudaStream_t s, double *dst, int64_t a0, int64_t n)
@@ -659,9 +677,10 @@ void launch_wrap_copy(const Plan &p, cudaStream_t s, double *dst, int64_t a0, in
     if (n <= 0) return;
     const int T = 256;
     if (p.batch)
-        k_wrap_copy<true><<<blocks_for(n, T), T, 0, s>>>(p.N, a0, n, p.pos, dst, p.box, p.sys_of, p.sys);
+        k_wrap_copy<true><<<blocks_for(n, T), T, 0, s>>>(p.N, a0, n, p.pos, dst, p.box, p.sys_of, p.sys, 0);
     else
-        k_wrap_copy<false><<<blocks_for(n, T), T, 0, s>>>(p.N, a0, n, p.pos, dst, p.box, p.sys_of, p.sys);
+        k_wrap_copy<false><<<blocks_for(n, T), T, 0, s>>>(p.N, a0, n, p.pos, dst, p.box, p.sys_of, p.sys,
+                                                           p.npt ? 1 : 0);
 }
 
 }  // namespace mdk

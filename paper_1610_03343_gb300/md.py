@@ -95,6 +95,11 @@ class md_stats(ctypes.Structure):
                 ("device_bytes", ctypes.c_size_t), ("atoms_rebuilt", ctypes.c_int64)]
 
 
+class md_npt(ctypes.Structure):
+    _fields_ = [("T0", ctypes.c_double), ("P0", ctypes.c_double), ("tau_T", ctypes.c_double),
+                ("tau_P", ctypes.c_double), ("beta", ctypes.c_double), ("couple", ctypes.c_int * 3)]
+
+
 MD_TUNE_MAX = 16
 
 
@@ -109,7 +114,7 @@ _lock = threading.Lock()
 _lib = None
 
 EXPORTS = ["md_default_options", "md_create", "md_set_positions", "md_set_velocities", "md_compute",
-           "md_run", "md_get_state", "md_get_stats", "md_set_graph_mode", "md_set_profiling",
+           "md_run", "md_get_state", "md_set_npt", "md_get_box", "md_get_stats", "md_set_graph_mode", "md_set_profiling",
            "md_kernel_times", "md_autotune", "md_set_tuning", "md_get_tuning", "md_batch_create", "md_batch_add", "md_batch_remove", "md_batch_status",
            "md_batch_get_state", "md_server_create", "md_server_submit", "md_server_poll", "md_server_wait",
            "md_server_drain", "md_server_stats_get", "md_server_clock", "md_server_destroy",
@@ -141,6 +146,8 @@ def load(build_if_missing: bool = False):
         lib.md_compute.argtypes = [P, P, P, P, P, P]
         lib.md_run.argtypes = [P, ctypes.c_int64, ctypes.c_double, P]
         lib.md_get_state.argtypes = [P, P, P]
+        lib.md_set_npt.argtypes = [P, ctypes.c_int, ctypes.POINTER(md_npt)]
+        lib.md_get_box.argtypes = [P, ctypes.c_int, P]
         lib.md_get_stats.argtypes = [P, ctypes.POINTER(md_stats)]
         lib.md_set_graph_mode.argtypes = [P, ctypes.c_int]
         lib.md_set_profiling.argtypes = [P, ctypes.c_int]
@@ -253,6 +260,26 @@ def md_run(ctx, n_steps, dt_fs, series=None):
 def md_get_state(ctx, x=None, v=None):
     lib = load()
     _check(lib, ctx, lib.md_get_state(ctx, _ptr(x), _ptr(v)))
+
+
+def md_set_npt(ctx, system=0, T0=300.0, P0=0.0, tau_T=100.0, tau_P=1000.0, beta=0.01, couple=(1, 1, 1),
+               off=False):
+    """Berendsen coupling of one system (off=True: back to NVE)."""
+    lib = load()
+    if off:
+        _check(lib, ctx, lib.md_set_npt(ctx, int(system), None))
+        return
+    c = md_npt()
+    c.T0, c.P0, c.tau_T, c.tau_P, c.beta = float(T0), float(P0), float(tau_T), float(tau_P), float(beta)
+    c.couple = (ctypes.c_int * 3)(*[int(a) for a in couple])
+    _check(lib, ctx, lib.md_set_npt(ctx, int(system), ctypes.byref(c)))
+
+
+def md_get_box(ctx, system=0) -> np.ndarray:
+    lib = load()
+    b = np.zeros(3)
+    _check(lib, ctx, lib.md_get_box(ctx, int(system), _ptr(b)))
+    return b
 
 
 def md_get_stats(ctx) -> md_stats:
@@ -577,6 +604,12 @@ class System:
     def stats(self):
         return md_get_stats(self.ctx)
 
+    def set_npt(self, off=False, **kw):
+        md_set_npt(self.ctx, 0, off=off, **kw)
+
+    def box(self):
+        return md_get_box(self.ctx, 0)
+
 
 def from_inputs(sysm, precision=MD_FP64, **kw) -> System:
     """Context for an inputs.System, with its positions and velocities uploaded."""
@@ -626,6 +659,12 @@ class Pool:
     def remove(self, sid):
         md_batch_remove(self.ctx, sid)
         self.n_atoms.pop(sid, None)
+
+    def set_npt(self, sid, off=False, **kw):
+        md_set_npt(self.ctx, sid, off=off, **kw)
+
+    def box(self, sid):
+        return md_get_box(self.ctx, sid)
 
     def run(self, n_steps, dt, record=False):
         series = np.zeros((max(n_steps, 1), self.max_systems, 5)) if record else None
