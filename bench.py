@@ -212,6 +212,47 @@ def run_ours(args, rank, world):
     return n, dt, res, t_e2e, h2d, d2h, mixed_err
 
 
+# ---------------------------------------------------------------- NPT leg
+def run_npt_leg(args, steps, warmup):
+    """The same workload in the paper's benchmark ensemble (Sec. 3: NPT, 300 K, 0 Pa):
+    Berendsen thermostat and barostat on the device inside the graph-replayed steps
+    (periodic in-plane axes coupled for the sheet, every periodic axis for a crystal).
+    Reports atom-steps/s for fp64 and mixed, and where the box and temperature went."""
+    import torch
+    from paper_1610_03343_gb300 import md
+
+    sysm, dt = workload(args.workload)
+    n = sysm.n
+    couple = (1, 1, 0) if "graphene" in args.workload else (1, 1, 1)
+    cpl = dict(T0=300.0, P0=0.0, tau_T=100.0, tau_P=1000.0, beta=0.01, couple=couple)
+    stream = torch.cuda.Stream()
+    out = {"coupling": {k: (list(v) if isinstance(v, tuple) else v) for k, v in cpl.items()},
+           "steps": steps, "dt_fs": dt}
+    for prec, tag in ((md.MD_FP64, "fp64"), (md.MD_MIXED, "mixed")):
+        g = md.System(sysm.box, sysm.pbc, n, sysm.kind, sysm.params, sysm.mass, precision=prec,
+                      stream=stream.cuda_stream)
+        g.set_positions(sysm.pos)
+        g.set_velocities(sysm.vel)
+        g.set_npt(**cpl)
+        g.run(warmup, dt, record=False)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ser = g.run(steps, dt, record=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        box = g.box()
+        T = 2.0 * ser[-1, 1] / (I.KB_EV_PER_K * (3 * n - 3))
+        out[tag] = {"value": n * steps / (ms / 1e3), "ms_per_step": ms / steps,
+                    "box_rel_change": [float(b / b0 - 1.0) for b, b0 in zip(box, sysm.box)],
+                    "temperature_K_last": float(T),
+                    "kernel_launches_per_step": int(g.stats().kernel_launches_per_step)}
+        g.close()
+    return out
+
+
 # ---------------------------------------------------------------- batched pool
 def batch_systems(n_sys=512, lo=64, hi=20000, seed=11):
     """512 Si diamond / C graphene cells, atom counts log-uniform in [64, 20000] snapped to
@@ -425,6 +466,7 @@ def main():
                     help="impose the batch leg's tuning: 'PBxBPS,PBxBPS' for fp64 and mixed, e.g. 64x16,128x16")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-npt", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-requests-low", type=int, default=400,
@@ -518,6 +560,8 @@ def main():
     if t_e2e is not None:
         out["e2e"] = {"value": world * n * args.steps / t_e2e, "unit": "atom-steps/s",
                       "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps}
+    if not args.no_npt:
+        out["npt"] = run_npt_leg(args, max(8, args.steps // 2), args.warmup)
     if not args.no_batch:
         out["batch"] = run_batch(args, max(8, args.steps // 2), args.warmup)
     if not args.no_serve:

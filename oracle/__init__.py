@@ -14,6 +14,8 @@ Functions follow the paper (arXiv:1610.03343) as documented in oracle.c:
   manybody_fwj         Eqs. 28-30 (F_i, W_i, J_i) from dU_i/dr_ij
   run                  velocity Verlet with per-step U, K, J
   run_npt              the same with the Berendsen thermostat and barostat (NPT)
+  tersoff_multi_conventional / tersoff_multi_dUdr / compute_multi / run_multi
+                       multi-element Tersoff (Tersoff 1989 mixing rules and chi)
   hcacf, running_kappa Green-Kubo HCACF and thermal conductivity from a J series
                        (green_kubo.py, numpy)
 """
@@ -68,9 +70,13 @@ def _load():
         lib.oracle_manybody_fwj.argtypes = [I64, P, P, P, P, P, I, P, P, P, P, P, P, P, P, P]
         lib.oracle_run.argtypes = [I64, P, P, P, P, P, P, P, P, P, I, P, I, I64, D, D, P]
         lib.oracle_run_ex.argtypes = [I64, P, P, P, P, P, P, P, P, P, I, P, I, I64, D, D, P, P]
+        lib.oracle_tersoff_multi_conventional.argtypes = [I64, P, P, P, P, P, P, I, P, P, P, P, P, P, P]
+        lib.oracle_tersoff_multi_dUdr.argtypes = [I64, P, P, P, P, P, P, I, P, P, I, P, P, P, P]
+        lib.oracle_run_multi.argtypes = [I64, P, P, P, P, P, P, P, P, P, P, I, P, P, I, I64, D, D, P, P]
         for f in ("oracle_neighbors_brute", "oracle_neighbors_cells", "oracle_tersoff_conventional",
                   "oracle_tersoff_dUdr", "oracle_sw_conventional", "oracle_sw_dUdr",
-                  "oracle_manybody_fwj", "oracle_run"):
+                  "oracle_manybody_fwj", "oracle_run", "oracle_run_ex", "oracle_tersoff_multi_conventional",
+                  "oracle_tersoff_multi_dUdr", "oracle_run_multi"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -258,3 +264,89 @@ def kinetic_energy(vel, masses):
     v = np.asarray(vel)
     m = np.broadcast_to(np.asarray(masses, dtype=np.float64), (v.shape[0],))
     return float(0.5 * np.sum(m[:, None] * v * v) / 9.648533215665328e-3)
+
+
+# ---------------------------------------------------------------- multi-element Tersoff
+def _multi_args(types, params, chi):
+    params = np.ascontiguousarray(np.asarray(params, dtype=np.float64).reshape(-1, 11))
+    nt = params.shape[0]
+    chi = np.ascontiguousarray(np.asarray(chi, dtype=np.float64).reshape(nt, nt))
+    types = np.ascontiguousarray(types, dtype=np.int32)
+    return types, nt, params.reshape(-1).copy(), chi.reshape(-1).copy()
+
+
+def multi_cutoff(params):
+    """Largest mixed cutoff sqrt(S_a S_b) of a multi-element parameter table."""
+    S = np.asarray(params, dtype=np.float64).reshape(-1, 11)[:, 10]
+    return float(np.sqrt(np.outer(S, S)).max())
+
+
+def tersoff_multi_conventional(pos, box, pbc, types, params, chi, NN, NL):
+    """Algorithm 1 for multi-element Tersoff: U (N,), F (N,3), W_total (9,)."""
+    lib = _load()
+    x, y, z = _soa(pos)
+    b, p = _box(box, pbc)
+    n = x.shape[0]
+    t, nt, prm, ch = _multi_args(types, params, chi)
+    U = np.zeros(n)
+    F = np.zeros(3 * n)
+    Wt = np.zeros(9)
+    NN = np.ascontiguousarray(NN, dtype=np.int32)
+    NL = np.ascontiguousarray(NL, dtype=np.int32)
+    rc = lib.oracle_tersoff_multi_conventional(n, _p(x), _p(y), _p(z), _p(b), _p(p), _p(t), nt, _p(prm), _p(ch),
+                                               _p(NN), _p(NL), _p(U), _p(F), _p(Wt))
+    if rc != 0:
+        raise ValueError("bad multi-element parameters")
+    return U, F.reshape(3, n).T.copy(), Wt
+
+
+def tersoff_multi_dUdr(pos, box, pbc, types, params, chi, NN, NL):
+    """Per-slot dU_i/dr_ij for multi-element Tersoff: U (N,), D (3, cap, N)."""
+    lib = _load()
+    x, y, z = _soa(pos)
+    b, p = _box(box, pbc)
+    n = x.shape[0]
+    t, nt, prm, ch = _multi_args(types, params, chi)
+    NL = np.ascontiguousarray(NL, dtype=np.int32)
+    cap = NL.shape[0]
+    NN = np.ascontiguousarray(NN, dtype=np.int32)
+    U = np.zeros(n)
+    D = np.zeros(3 * cap * n)
+    rc = lib.oracle_tersoff_multi_dUdr(n, _p(x), _p(y), _p(z), _p(b), _p(p), _p(t), nt, _p(prm), _p(ch), cap,
+                                       _p(NN), _p(NL), _p(U), _p(D))
+    if rc != 0:
+        raise ValueError("bad multi-element parameters")
+    return U, D.reshape(3, cap, n)
+
+
+def compute_multi(pos, box, pbc, types, params, chi, vel=None, cap=32):
+    """compute() for multi-element Tersoff: U_i, F_i by Algorithm 1, W_i and J_i (Eqs.
+    29-30) from dU_i/dr_ij, totals."""
+    rc = multi_cutoff(params)
+    NN, NL = neighbors(pos, box, pbc, rc, cap)
+    U, F, Wtot_conv = tersoff_multi_conventional(pos, box, pbc, types, params, chi, NN, NL)
+    Ud, D = tersoff_multi_dUdr(pos, box, pbc, types, params, chi, NN, NL)
+    Fp, W, J = manybody_fwj(pos, box, pbc, NN, NL, D, vel)
+    out = dict(U=U, F=F, W=W, J=J, F_pair=Fp, U_d=Ud, W_total_conv=Wtot_conv, NN=NN, NL=NL, D=D)
+    out["totals"] = np.concatenate([[U.sum()], W.sum(axis=0),
+                                    J.sum(axis=0) if J is not None else np.zeros(3)])
+    return out
+
+
+def run_multi(pos, vel, masses, box, pbc, types, params, chi, n_steps, dt, cap=32, damp=0.0):
+    """Velocity Verlet with multi-element Tersoff (masses per atom): (pos, vel, series)."""
+    lib = _load()
+    x, y, z = _soa(pos)
+    vx, vy, vz = _soa(vel)
+    n = x.shape[0]
+    m = np.ascontiguousarray(np.broadcast_to(np.asarray(masses, dtype=np.float64), (n,)))
+    b, p = _box(box, pbc)
+    b = np.array(b, dtype=np.float64)
+    t, nt, prm, ch = _multi_args(types, params, chi)
+    series = np.zeros(5 * max(n_steps, 1))
+    rc = lib.oracle_run_multi(n, _p(x), _p(y), _p(z), _p(vx), _p(vy), _p(vz), _p(m), _p(b), _p(p), _p(t), nt,
+                              _p(prm), _p(ch), int(cap), int(n_steps), float(dt), float(damp), None, _p(series))
+    if rc != 0:
+        raise RuntimeError(f"oracle_run_multi failed: {rc}")
+    return (np.stack([x, y, z], axis=1), np.stack([vx, vy, vz], axis=1),
+            series[:5 * n_steps].reshape(n_steps, 5))

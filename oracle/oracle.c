@@ -415,6 +415,211 @@ int oracle_tersoff_dUdr(int64_t N, const double *x, const double *y, const doubl
     return 0;
 }
 
+/* ------------------------------------------------ multi-element Tersoff */
+/* Tersoff's multicomponent form (J. Tersoff, Phys. Rev. B 39, 5566 (1989)); the paper
+ * states that its formulation holds for any many-body potential of this kind (Sec. 2.1,
+ * Sec. 2.4).  For atoms i, j of elements a = t_i, b = t_j:
+ *   U_ij   = f_C^{ab}(r_ij) [ f_R^{ab}(r_ij) - b_ij f_A^{ab}(r_ij) ],   U_i = 1/2 sum_j U_ij,
+ *   f_R^{ab} = A_ab e^{-lambda_ab r},  f_A^{ab} = B_ab e^{-mu_ab r},  f_C^{ab}: R_ab, S_ab,
+ *   A_ab = sqrt(A_a A_b), B_ab = sqrt(B_a B_b), R_ab = sqrt(R_a R_b), S_ab = sqrt(S_a S_b),
+ *   lambda_ab = (lambda_a + lambda_b)/2, mu_ab = (mu_a + mu_b)/2,
+ *   b_ij   = chi_ab (1 + beta_a^{n_a} zeta_ij^{n_a})^{-1/(2 n_a)},
+ *   zeta_ij = sum_{k != j} f_C^{a t_k}(r_ik) g_a(theta_ijk)        (omega = 1),
+ *   g_a(theta) = 1 + c_a^2/d_a^2 - c_a^2 / (d_a^2 + (h_a - cos theta)^2).
+ * One element with chi = 1 gives Eqs. 2-6.  Arguments: types[N] element of each atom
+ * (0 .. n_types-1, n_types <= 4); params[n_types x 11] per element in the packing of the
+ * single-element routines; chi[n_types x n_types].
+ * Implementation: a table of tersoff_t per ordered element pair (a, b), whose radial
+ * fields (A, B, lambda, mu, R, S) are the mixed ones and whose angular and bond-order
+ * fields (beta, n, c, d, h) are element a's, so the single-element helpers apply. */
+#define ORACLE_MAXT 4
+typedef struct {
+    int nt;
+    tersoff_t P[ORACLE_MAXT][ORACLE_MAXT];
+    double chi[ORACLE_MAXT][ORACLE_MAXT];
+} tersoff_multi_t;
+
+static int tersoff_multi_unpack(int n_types, const double *params, const double *chi, tersoff_multi_t *T)
+{
+    if (n_types < 1 || n_types > ORACLE_MAXT) return -1;
+    T->nt = n_types;
+    for (int a = 0; a < n_types; ++a)
+        for (int b = 0; b < n_types; ++b) {
+            tersoff_t ea = tersoff_unpack(params + 11 * a), eb = tersoff_unpack(params + 11 * b);
+            tersoff_t m = ea;
+            m.A = sqrt(ea.A * eb.A);
+            m.B = sqrt(ea.B * eb.B);
+            m.lam = 0.5 * (ea.lam + eb.lam);
+            m.mu = 0.5 * (ea.mu + eb.mu);
+            m.R = sqrt(ea.R * eb.R);
+            m.S = sqrt(ea.S * eb.S);
+            T->P[a][b] = m;
+            T->chi[a][b] = chi[a * n_types + b];
+        }
+    return 0;
+}
+
+/* zeta_ij for the pair (i, j = NL[mj N + i]) of atom i (element a) */
+static double tm_zeta(const tersoff_multi_t *T, const int *types, int64_t N, const double *x, const double *y,
+                      const double *z, const double *box, const int *pbc, const int *NN, const int *NL,
+                      int64_t i, int mj, const double *rij)
+{
+    int a = types[i];
+    double r1 = vnorm(rij), zeta = 0.0;
+    for (int mk = 0; mk < NN[i]; ++mk) {
+        if (mk == mj) continue;
+        int64_t k = NL[(int64_t)mk * N + i];
+        double rik[3];
+        bond(N, x, y, z, box, pbc, i, k, rik);
+        double r2 = vnorm(rik);
+        double cs = vdot(rij, rik) / (r1 * r2);
+        zeta += t_fc(&T->P[a][types[k]], r2) * t_g(&T->P[a][a], cs);
+    }
+    return zeta;
+}
+
+/* Algorithm 1 (Eqs. 7-11) for the multicomponent form: U_i, F_i and the total virial
+ * (Wtot may be NULL).  Same loop structure as oracle_tersoff_conventional, each radial
+ * function taken with the pair's mixed parameters, g and the bond order with atom i's
+ * element, b_ij and its derivative scaled by chi_ij.  Returns 0, -1 on bad n_types. */
+int oracle_tersoff_multi_conventional(int64_t N, const double *x, const double *y, const double *z,
+                                      const double *box, const int *pbc, const int *types, int n_types,
+                                      const double *params, const double *chi, const int *NN, const int *NL,
+                                      double *U, double *F, double *Wtot)
+{
+    tersoff_multi_t T;
+    if (tersoff_multi_unpack(n_types, params, chi, &T) != 0) return -1;
+    for (int64_t i = 0; i < N; ++i) {
+        U[i] = 0.0;
+        F[i] = F[N + i] = F[2 * N + i] = 0.0;
+    }
+    if (Wtot) for (int c = 0; c < 9; ++c) Wtot[c] = 0.0;
+
+    for (int64_t i = 0; i < N; ++i) {
+        int a = types[i];
+        const tersoff_t *Pa = &T.P[a][a];
+        for (int mj = 0; mj < NN[i]; ++mj) {
+            int64_t j = NL[(int64_t)mj * N + i];
+            const tersoff_t *Pij = &T.P[a][types[j]];
+            double chi_ij = T.chi[a][types[j]];
+            double rij[3];
+            bond(N, x, y, z, box, pbc, i, j, rij);
+            double r = vnorm(rij);
+            if (r >= Pij->S) continue;
+            double zeta = tm_zeta(&T, types, N, x, y, z, box, pbc, NN, NL, i, mj, rij);
+            double b = chi_ij * t_b(Pa, zeta), db = chi_ij * t_db(Pa, zeta);
+            double fc = t_fc(Pij, r), dfc = t_dfc(Pij, r);
+            double fR = t_fR(Pij, r), dfR = t_dfR(Pij, r);
+            double fA = t_fA(Pij, r), dfA = t_dfA(Pij, r);
+            U[i] += 0.5 * fc * (fR - b * fA);
+
+            double dR = dfc * fR + fc * dfR, dA = dfc * fA + fc * dfA;
+            double Fi[3];
+            for (int q = 0; q < 3; ++q) Fi[q] = (0.5 * dR - 0.5 * b * dA) * rij[q] / r;     /* Eq. 7 */
+            for (int q = 0; q < 3; ++q) { F[q * N + i] += Fi[q]; F[q * N + j] -= Fi[q]; } /* Eq. 8 */
+            if (Wtot)
+                for (int q = 0; q < 3; ++q)
+                    for (int c = 0; c < 3; ++c) Wtot[3 * q + c] += -rij[q] * Fi[c];
+
+            double pref = 0.5 * fc * fA * db;
+            for (int mk = 0; mk < NN[i]; ++mk) {
+                if (mk == mj) continue;
+                int64_t k = NL[(int64_t)mk * N + i];
+                const tersoff_t *Pik = &T.P[a][types[k]];
+                double rik[3];
+                bond(N, x, y, z, box, pbc, i, k, rik);
+                double r2 = vnorm(rik);
+                double cs = vdot(rij, rik) / (r * r2);
+                double fck = t_fc(Pik, r2), dfck = t_dfc(Pik, r2);
+                double gk = t_g(Pa, cs), dgk = t_dg(Pa, cs);
+                double Fj[3], Fk[3];
+                for (int q = 0; q < 3; ++q) {
+                    double dcos_drj = (rik[q] / r2 - cs * rij[q] / r) / r;
+                    double dcos_drk = (rij[q] / r - cs * rik[q] / r2) / r2;
+                    double dj = fck * dgk * dcos_drj;
+                    double dk = dfck * gk * rik[q] / r2 + fck * dgk * dcos_drk;
+                    Fj[q] = pref * dj;                                          /* Eq. 10 */
+                    Fk[q] = pref * dk;                                          /* Eq. 11 */
+                    F[q * N + i] += -pref * (dj + dk);                          /* Eq. 9  */
+                }
+                for (int q = 0; q < 3; ++q) { F[q * N + j] += Fj[q]; F[q * N + k] += Fk[q]; }
+                if (Wtot)
+                    for (int q = 0; q < 3; ++q)
+                        for (int c = 0; c < 3; ++c) Wtot[3 * q + c] += rij[q] * Fj[c] + rik[q] * Fk[c];
+            }
+        }
+    }
+    return 0;
+}
+
+/* dU_i/dr_ij for the multicomponent form, per list slot (layout of oracle_tersoff_dUdr):
+ *   dU_i/dr_ij = 1/2 [ (f_C f_R)'_ij - b_ij (f_C f_A)'_ij ] r_ij/r_ij
+ *              - 1/2 f_C^{ij} f_A^{ij} b'_ij dzeta_ij/dr_ij
+ *              - 1/2 sum_{k != j} f_C^{ik} f_A^{ik} b'_ik dzeta_ik/dr_ij,
+ *   dzeta_ik/dr_ij = f_C^{ij}'(r_ij) g_a(cos) r_ij/r_ij + f_C^{ij}(r_ij) g_a'(cos) dcos/dr_ij,
+ * b' = chi db/dzeta.  Also U_i.  Slots with r_ij >= S_ij get D = 0.  Returns 0, -1 on
+ * allocation failure or bad n_types. */
+int oracle_tersoff_multi_dUdr(int64_t N, const double *x, const double *y, const double *z,
+                              const double *box, const int *pbc, const int *types, int n_types,
+                              const double *params, const double *chi, int cap, const int *NN, const int *NL,
+                              double *U, double *D)
+{
+    tersoff_multi_t T;
+    if (tersoff_multi_unpack(n_types, params, chi, &T) != 0) return -1;
+    int64_t CN = (int64_t)cap * N;
+    double *zeta = (double *)malloc(sizeof(double) * (size_t)(cap > 0 ? cap : 1));
+    if (!zeta) return -1;
+    for (int64_t i = 0; i < N; ++i) {
+        int a = types[i], nn = NN[i];
+        const tersoff_t *Pa = &T.P[a][a];
+        for (int mj = 0; mj < nn; ++mj) {
+            double rij[3];
+            bond(N, x, y, z, box, pbc, i, NL[(int64_t)mj * N + i], rij);
+            zeta[mj] = tm_zeta(&T, types, N, x, y, z, box, pbc, NN, NL, i, mj, rij);
+        }
+        U[i] = 0.0;
+        for (int mj = 0; mj < nn; ++mj) {
+            int64_t j = NL[(int64_t)mj * N + i];
+            const tersoff_t *Pij = &T.P[a][types[j]];
+            double chi_ij = T.chi[a][types[j]];
+            double rij[3];
+            bond(N, x, y, z, box, pbc, i, j, rij);
+            double r = vnorm(rij);
+            double fc = t_fc(Pij, r), dfc = t_dfc(Pij, r);
+            double fR = t_fR(Pij, r), dfR = t_dfR(Pij, r);
+            double fA = t_fA(Pij, r), dfA = t_dfA(Pij, r);
+            double b = chi_ij * t_b(Pa, zeta[mj]), db = chi_ij * t_db(Pa, zeta[mj]);
+            U[i] += 0.5 * fc * (fR - b * fA);
+            double d[3];
+            double radial = 0.5 * ((dfc * fR + fc * dfR) - b * (dfc * fA + fc * dfA));
+            for (int q = 0; q < 3; ++q) d[q] = radial * rij[q] / r;
+            for (int mk = 0; mk < nn; ++mk) {
+                if (mk == mj) continue;
+                int64_t k = NL[(int64_t)mk * N + i];
+                const tersoff_t *Pik = &T.P[a][types[k]];
+                double chi_ik = T.chi[a][types[k]];
+                double rik[3];
+                bond(N, x, y, z, box, pbc, i, k, rik);
+                double r2 = vnorm(rik);
+                double cs = vdot(rij, rik) / (r * r2);
+                double fck = t_fc(Pik, r2), fAk = t_fA(Pik, r2);
+                double g = t_g(Pa, cs), dg = t_dg(Pa, cs);
+                double bk = chi_ik * t_db(Pa, zeta[mk]);
+                for (int q = 0; q < 3; ++q) {
+                    double dcos = (rik[q] / r2 - cs * rij[q] / r) / r;
+                    d[q] += -0.5 * fc * fA * db * fck * dg * dcos;
+                    d[q] += -0.5 * fck * fAk * bk * (dfc * g * rij[q] / r + fc * dg * dcos);
+                }
+            }
+            for (int q = 0; q < 3; ++q) D[q * CN + (int64_t)mj * N + i] = (r < Pij->S) ? d[q] : 0.0;
+        }
+        for (int mj = nn; mj < cap; ++mj)
+            for (int q = 0; q < 3; ++q) D[q * CN + (int64_t)mj * N + i] = 0.0;
+    }
+    free(zeta);
+    return 0;
+}
+
 /* ------------------------------------------------------- Stillinger-Weber */
 /* Packed parameters: epsilon, sigma, a, lambda, gamma, A, B, p, q (SW 1985). */
 typedef struct { double eps, sig, a, lam, gam, A, B, p, q; } sw_t;
@@ -597,12 +802,28 @@ int oracle_manybody_fwj(int64_t N, const double *x, const double *y, const doubl
 }
 
 /* ------------------------------------------------------------ time stepping */
-enum { ORACLE_TERSOFF = 1, ORACLE_SW = 2 };
+enum { ORACLE_TERSOFF = 1, ORACLE_SW = 2, ORACLE_TERSOFF_MULTI = 3 };
 
-static double pot_cutoff(int kind, const double *params)
+/* the potential of a run: one element (Tersoff or SW), or multi-element Tersoff */
+typedef struct {
+    int kind;
+    const double *params;
+    const int *types;     /* multi-element only */
+    int n_types;
+    const double *chi;
+} pot_t;
+
+static double pot_cutoff(const pot_t *pot)
 {
-    if (kind == ORACLE_TERSOFF) return params[10];
-    return params[1] * params[2];
+    if (pot->kind == ORACLE_TERSOFF) return pot->params[10];
+    if (pot->kind == ORACLE_SW) return pot->params[1] * pot->params[2];
+    double rc = 0.0;   /* largest mixed S_ab */
+    for (int a = 0; a < pot->n_types; ++a)
+        for (int b = 0; b < pot->n_types; ++b) {
+            double s = sqrt(pot->params[11 * a + 10] * pot->params[11 * b + 10]);
+            if (s > rc) rc = s;
+        }
+    return rc;
 }
 
 static int build_list(int64_t N, const double *x, const double *y, const double *z,
@@ -612,12 +833,28 @@ static int build_list(int64_t N, const double *x, const double *y, const double 
     return oracle_neighbors_cells(N, x, y, z, box, pbc, rc, cap, NN, NL);
 }
 
-static void conventional_forces(int kind, int64_t N, const double *x, const double *y, const double *z,
-                                const double *box, const int *pbc, const double *params,
-                                const int *NN, const int *NL, double *U, double *F)
+static void conventional_forces(const pot_t *pot, int64_t N, const double *x, const double *y, const double *z,
+                                const double *box, const int *pbc, const int *NN, const int *NL, double *U,
+                                double *F)
 {
-    if (kind == ORACLE_TERSOFF) oracle_tersoff_conventional(N, x, y, z, box, pbc, params, NN, NL, U, F, NULL, NULL);
-    else oracle_sw_conventional(N, x, y, z, box, pbc, params, NN, NL, U, F, NULL);
+    if (pot->kind == ORACLE_TERSOFF)
+        oracle_tersoff_conventional(N, x, y, z, box, pbc, pot->params, NN, NL, U, F, NULL, NULL);
+    else if (pot->kind == ORACLE_SW)
+        oracle_sw_conventional(N, x, y, z, box, pbc, pot->params, NN, NL, U, F, NULL);
+    else
+        oracle_tersoff_multi_conventional(N, x, y, z, box, pbc, pot->types, pot->n_types, pot->params, pot->chi,
+                                          NN, NL, U, F, NULL);
+}
+
+static void pair_derivatives(const pot_t *pot, int64_t N, const double *x, const double *y, const double *z,
+                             const double *box, const int *pbc, int cap, const int *NN, const int *NL, double *U,
+                             double *D)
+{
+    if (pot->kind == ORACLE_TERSOFF) oracle_tersoff_dUdr(N, x, y, z, box, pbc, pot->params, cap, NN, NL, U, D);
+    else if (pot->kind == ORACLE_SW) oracle_sw_dUdr(N, x, y, z, box, pbc, pot->params, cap, NN, NL, U, D);
+    else
+        oracle_tersoff_multi_dUdr(N, x, y, z, box, pbc, pot->types, pot->n_types, pot->params, pot->chi, cap, NN,
+                                  NL, U, D);
 }
 
 /* Velocity Verlet (Sec. 3): per step
@@ -644,11 +881,11 @@ static void conventional_forces(int kind, int64_t N, const double *x, const doub
 static const double K_BOLTZMANN = 8.617333262e-5;            /* eV / K */
 static const double EV_PER_A3_IN_GPA = 160.21766340;          /* 1.602176634e-19 J / 1e-30 m^3 */
 
-int oracle_run_ex(int64_t N, double *x, double *y, double *z, double *vx, double *vy, double *vz,
-                  const double *masses, double *box, const int *pbc, int kind, const double *params, int cap,
-                  int64_t n_steps, double dt, double damp, const double *npt, double *series)
+static int run_core(int64_t N, double *x, double *y, double *z, double *vx, double *vy, double *vz,
+                    const double *masses, double *box, const int *pbc, const pot_t *pot, int cap,
+                    int64_t n_steps, double dt, double damp, const double *npt, double *series)
 {
-    double rc = pot_cutoff(kind, params);
+    double rc = pot_cutoff(pot);
     size_t n1 = (size_t)(N > 0 ? N : 1);
     int *NN = (int *)malloc(sizeof(int) * n1);
     int *NL = (int *)malloc(sizeof(int) * (size_t)cap * n1);
@@ -663,7 +900,7 @@ int oracle_run_ex(int64_t N, double *x, double *y, double *z, double *vx, double
     int rc_status = 0;
     if (!NN || !NL || !U || !F || !D || !Jv || !Wv || !Ud) { rc_status = -1; goto done; }
     if (build_list(N, x, y, z, box, pbc, rc, cap, NN, NL) > cap) { rc_status = -3; goto done; }
-    conventional_forces(kind, N, x, y, z, box, pbc, params, NN, NL, U, F);
+    conventional_forces(pot, N, x, y, z, box, pbc, NN, NL, U, F);
     for (int64_t s = 0; s < n_steps; ++s) {
         if (pending) {   /* Berendsen scaling computed at the end of the previous step */
             double *c[3] = {x, y, z};
@@ -686,7 +923,7 @@ int oracle_run_ex(int64_t N, double *x, double *y, double *z, double *vx, double
             }
         }
         if (build_list(N, x, y, z, box, pbc, rc, cap, NN, NL) > cap) { rc_status = -3; goto done; }
-        conventional_forces(kind, N, x, y, z, box, pbc, params, NN, NL, U, F);
+        conventional_forces(pot, N, x, y, z, box, pbc, NN, NL, U, F);
         double Ut = 0.0, K = 0.0, Kaa[3] = {0, 0, 0}, Jt[3] = {0, 0, 0}, Waa[3] = {0, 0, 0};
         for (int64_t i = 0; i < N; ++i) {
             double h = 0.5 * dt * ACC_UNIT / masses[i];
@@ -701,8 +938,7 @@ int oracle_run_ex(int64_t N, double *x, double *y, double *z, double *vx, double
             Kaa[1] += 0.5 * masses[i] * vy[i] * vy[i] / ACC_UNIT;
             Kaa[2] += 0.5 * masses[i] * vz[i] * vz[i] / ACC_UNIT;
         }
-        if (kind == ORACLE_TERSOFF) oracle_tersoff_dUdr(N, x, y, z, box, pbc, params, cap, NN, NL, Ud, D);
-        else oracle_sw_dUdr(N, x, y, z, box, pbc, params, cap, NN, NL, Ud, D);
+        pair_derivatives(pot, N, x, y, z, box, pbc, cap, NN, NL, Ud, D);
         oracle_manybody_fwj(N, x, y, z, box, pbc, cap, NN, NL, D, vx, vy, vz, NULL, npt ? Wv : NULL, Jv);
         for (int64_t i = 0; i < N; ++i) for (int a = 0; a < 3; ++a) Jt[a] += Jv[a * N + i];
         if (series) {
@@ -733,6 +969,26 @@ int oracle_run_ex(int64_t N, double *x, double *y, double *z, double *vx, double
 done:
     free(NN); free(NL); free(U); free(F); free(D); free(Jv); free(Wv); free(Ud);
     return rc_status;
+}
+
+int oracle_run_ex(int64_t N, double *x, double *y, double *z, double *vx, double *vy, double *vz,
+                  const double *masses, double *box, const int *pbc, int kind, const double *params, int cap,
+                  int64_t n_steps, double dt, double damp, const double *npt, double *series)
+{
+    pot_t pot = {kind, params, NULL, 1, NULL};
+    return run_core(N, x, y, z, vx, vy, vz, masses, box, pbc, &pot, cap, n_steps, dt, damp, npt, series);
+}
+
+/* The same integrator for multi-element Tersoff (types, n_types, params, chi as in
+ * oracle_tersoff_multi_conventional). */
+int oracle_run_multi(int64_t N, double *x, double *y, double *z, double *vx, double *vy, double *vz,
+                     const double *masses, double *box, const int *pbc, const int *types, int n_types,
+                     const double *params, const double *chi, int cap, int64_t n_steps, double dt, double damp,
+                     const double *npt, double *series)
+{
+    if (n_types < 1 || n_types > ORACLE_MAXT) return -1;
+    pot_t pot = {ORACLE_TERSOFF_MULTI, params, types, n_types, chi};
+    return run_core(N, x, y, z, vx, vy, vz, masses, box, pbc, &pot, cap, n_steps, dt, damp, npt, series);
 }
 
 int oracle_run(int64_t N, double *x, double *y, double *z, double *vx, double *vy, double *vz,

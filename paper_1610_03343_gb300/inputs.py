@@ -44,6 +44,10 @@ TERSOFF_SI_1989 = (1830.8, 471.18, 2.4799, 1.7322, 1.1e-6, 0.78734,
 # Tersoff, Phys. Rev. B 39, 5566 (1989), carbon.
 TERSOFF_C_1989 = (1393.6, 346.74, 3.4879, 2.2119, 1.5724e-7, 0.72751,
                   38049.0, 4.3484, -0.57058, 1.8, 2.1)
+# Tersoff, Phys. Rev. B 39, 5566 (1989): the Si-C system, element 0 = Si, element 1 = C
+# (per-element parameters as above) and the Si-C bond-order factor chi.
+TERSOFF_SIC_1989 = (TERSOFF_SI_1989, TERSOFF_C_1989)
+CHI_SIC_1989 = ((1.0, 0.9776), (0.9776, 1.0))
 # Stillinger & Weber, Phys. Rev. B 31, 5262 (1985), silicon:
 #   epsilon, sigma, a, lambda, gamma, A, B, p, q
 SW_SI_1985 = (2.1683, 2.0951, 1.80, 21.0, 1.20, 7.049556277, 0.6022245584, 4.0, 0.0)
@@ -260,3 +264,80 @@ def batch_sizes(n_sys: int, lo: int, hi: int, seed: int):
             ny = max(3, int(round(1.732 * nx)))
             out.append(("c_graphene", nx, ny, 4 * nx * ny))
     return out
+
+
+# ---------------------------------------------------------------------------
+# Several elements (multi-element Tersoff)
+# ---------------------------------------------------------------------------
+@dataclass
+class MultiSystem:
+    """A synthetic system of several elements: per-atom element index `types`, a
+    parameter row per element (`params`, n_types x 11), the bond-order factors `chi`
+    (n_types x n_types) and a mass per element."""
+    name: str
+    pos: np.ndarray
+    box: np.ndarray
+    pbc: np.ndarray
+    types: np.ndarray          # (N,) int32
+    params: tuple              # n_types rows of 11
+    chi: tuple                 # n_types x n_types
+    masses: tuple              # amu per element
+    vel: np.ndarray = field(default=None)
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n(self) -> int:
+        return int(self.pos.shape[0])
+
+    @property
+    def atom_masses(self) -> np.ndarray:
+        return np.asarray(self.masses, dtype=np.float64)[self.types]
+
+
+def maxwell_boltzmann_per_atom(masses: np.ndarray, temperature: float, seed: int) -> np.ndarray:
+    """Gaussian velocities for per-atom masses, zero total momentum, rescaled so that the
+    kinetic temperature with 3N-3 degrees of freedom equals `temperature` exactly."""
+    m = np.asarray(masses, dtype=np.float64)
+    n = m.shape[0]
+    if n == 0 or temperature == 0.0:
+        return np.zeros((n, 3))
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sigma = np.sqrt(KB_EV_PER_K * temperature / m * EV_PER_A_AMU_TO_A_PER_FS2)
+    v = rng.normal(0.0, 1.0, size=(n, 3)) * sigma[:, None]
+    if n > 1:
+        v -= (m[:, None] * v).sum(axis=0, keepdims=True) / m.sum()
+        ke = 0.5 * np.sum(m[:, None] * v * v) / EV_PER_A_AMU_TO_A_PER_FS2
+        t_now = 2.0 * ke / ((3 * n - 3) * KB_EV_PER_K)
+        v *= math.sqrt(temperature / t_now)
+    return v
+
+
+def sic_zincblende(n: int = 4, a: float = 4.32, jitter_amp: float = 0.03, temperature: float = 300.0,
+                   seed_pos: int = 1, seed_vel: int = 2) -> MultiSystem:
+    """3C-SiC (zincblende): Si on the fcc sites, C on the fcc sites shifted by a(1,1,1)/4;
+    n^3 conventional cells of 8 atoms, Tersoff 1989 Si-C parameters."""
+    pos, box = diamond_positions(n, a)
+    pbc = np.array([1, 1, 1], dtype=np.int32)
+    types = np.tile(np.array([0, 0, 0, 0, 1, 1, 1, 1], dtype=np.int32), n ** 3)
+    pos = wrap(jitter(pos, jitter_amp, seed_pos), box, pbc)
+    masses = (MASS_SI, MASS_C)
+    vel = maxwell_boltzmann_per_atom(np.asarray(masses)[types], temperature, seed_vel)
+    return MultiSystem(f"tersoff_sic_zincblende_{n}", pos, box, pbc, types, TERSOFF_SIC_1989, CHI_SIC_1989,
+                       masses, vel, dict(n_cells=n, a=a, jitter=jitter_amp, T=temperature))
+
+
+def sic_substituted_diamond(n: int = 4, a: float = 5.2, c_fraction: float = 0.3, jitter_amp: float = 0.08,
+                            temperature: float = 300.0, seed_types: int = 5, seed_pos: int = 6,
+                            seed_vel: int = 7) -> MultiSystem:
+    """Diamond lattice with a random fraction of the sites carbon, the rest silicon: every
+    element pair meets (Si-Si, Si-C, C-C), and at a = 5.2 A the 2.25 A bonds fall inside
+    the Si-Si core, the Si-C switching shell and beyond the C-C cutoff."""
+    pos, box = diamond_positions(n, a)
+    pbc = np.array([1, 1, 1], dtype=np.int32)
+    rng = np.random.Generator(np.random.PCG64(seed_types))
+    types = (rng.uniform(0.0, 1.0, size=pos.shape[0]) < c_fraction).astype(np.int32)
+    pos = wrap(jitter(pos, jitter_amp, seed_pos), box, pbc)
+    masses = (MASS_SI, MASS_C)
+    vel = maxwell_boltzmann_per_atom(np.asarray(masses)[types], temperature, seed_vel)
+    return MultiSystem(f"tersoff_sic_substituted_{n}", pos, box, pbc, types, TERSOFF_SIC_1989, CHI_SIC_1989,
+                       masses, vel, dict(n_cells=n, a=a, c_fraction=c_fraction, jitter=jitter_amp, T=temperature))
