@@ -59,11 +59,20 @@ enum { MD_TERSOFF = 1, MD_SW = 2 };      /* md_params.kind */
 enum { MD_FP64 = 0, MD_MIXED = 1 };      /* md_options.precision */
 enum { MD_IO_HOST = 0, MD_IO_DEVICE = 1 }; /* md_options.io */
 
-/* Potential parameters (single element; n_types must be 1).
- *   MD_TERSOFF: p[11] = A (eV), B (eV), lambda (1/A), mu (1/A), beta, n, c, d, h, R (A), S (A)
- *               Eqs. 2-6 with f_R = A exp(-lambda r), f_A = B exp(-mu r), and
+/* Potential parameters.
+ *   MD_TERSOFF, n_types = 1: p[11] = A (eV), B (eV), lambda (1/A), mu (1/A), beta, n, c, d, h,
+ *               R (A), S (A): Eqs. 2-6 with f_R = A exp(-lambda r), f_A = B exp(-mu r), and
  *               f_C = 1 (r < R), 1/2 + 1/2 cos(pi (r-R)/(S-R)) (R <= r < S), 0 (r >= S).
- *   MD_SW:      p[9]  = epsilon (eV), sigma (A), a, lambda, gamma, A, B, p, q
+ *   MD_TERSOFF, n_types = T in 2..4 (md_create only; Sec. 2.1 closes by noting that the
+ *               method covers systems of several elements): the multicomponent form of Tersoff, Phys.
+ *               Rev. B 39, 5566 (1989).  p[11 T + T T] = T element rows of the 11 values
+ *               above, then chi[a][b] row-major (each > 0).  A bond from an atom of element
+ *               a to one of element b uses A_ab = sqrt(A_a A_b), B_ab = sqrt(B_a B_b),
+ *               R_ab = sqrt(R_a R_b), S_ab = sqrt(S_a S_b), lambda_ab = (lambda_a +
+ *               lambda_b)/2, mu_ab likewise; g and the bond order use element a's c, d, h,
+ *               beta, n, and b_ij = chi_ab (1 + (beta_a zeta_ij)^n_a)^(-1/(2 n_a)), with
+ *               zeta_ij = sum_k f_C^{a t_k}(r_ik) g_a(theta_ijk).  types[] are element rows.
+ *   MD_SW:      p[9]  = epsilon (eV), sigma (A), a, lambda, gamma, A, B, p, q (n_types = 1)
  *               U_i = 1/2 sum_j phi2(r_ij) + sum_{j<k} phi3(r_ij, r_ik, theta_jik),
  *               the three-body term belonging to its vertex atom i.
  * The array is copied at md_create. */
@@ -82,8 +91,9 @@ typedef struct {
                           than skin/2 since the last build (0 = default, 0.15 x cutoff). */
     int max_neigh;     /* list capacity per atom, <= 32 (default 32)                    */
     int max_active;    /* capacity of in-cutoff neighbours per atom, <= 16 (0 = default:
-                          8 for Tersoff, 16 for SW, whose second shell in diamond Si sits
-                          only 0.07 A outside the cutoff)                                 */
+                          8 for one-element Tersoff; 16 for SW, whose second shell in
+                          diamond Si sits only 0.07 A outside the cutoff, and for several
+                          Tersoff elements, SiC's second Si-Si shell being as close)     */
     int io;            /* MD_IO_HOST (default) or MD_IO_DEVICE                           */
     void *cuda_stream; /* cudaStream_t to run on, or NULL: the context creates its own  */
     size_t hbm_budget; /* bytes the context may allocate; 0 = unlimited                 */
@@ -97,8 +107,10 @@ md_status md_default_options(md_options *opt);
 /* Create a context for n_atoms atoms (n_atoms >= 0).
  *   box[3]  orthorhombic edge lengths (A), each > 0
  *   pbc[3]  1 = periodic along that axis, 0 = open
- *   types   n_atoms element indices (all 0 for a single element) -- host pointer always
- *   masses_by_type  n_types masses (amu), host pointer
+ *   types   n_atoms element indices < params->n_types (all 0 for a single element) -- host
+ *           pointer always
+ *   masses_by_type  params->n_types masses (amu), host pointer
+ * MD_ERR_ARG for an index out of range, several elements with SW, or a bad parameter.
  * Positions and velocities start at zero; set them before computing. */
 md_status md_create(md_ctx **out, const double box[3], const int pbc[3], int64_t n_atoms,
                     const int32_t *types, const double *masses_by_type,

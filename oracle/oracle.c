@@ -417,8 +417,8 @@ int oracle_tersoff_dUdr(int64_t N, const double *x, const double *y, const doubl
 
 /* ------------------------------------------------ multi-element Tersoff */
 /* Tersoff's multicomponent form (J. Tersoff, Phys. Rev. B 39, 5566 (1989)); the paper
- * states that its formulation holds for any many-body potential of this kind (Sec. 2.1,
- * Sec. 2.4).  For atoms i, j of elements a = t_i, b = t_j:
+ * presents the single-element form and notes that its method covers systems with several
+ * kinds of atoms (end of Sec. 2.1).  For atoms i, j of elements a = t_i, b = t_j:
  *   U_ij   = f_C^{ab}(r_ij) [ f_R^{ab}(r_ij) - b_ij f_A^{ab}(r_ij) ],   U_i = 1/2 sum_j U_ij,
  *   f_R^{ab} = A_ab e^{-lambda_ab r},  f_A^{ab} = B_ab e^{-mu_ab r},  f_C^{ab}: R_ab, S_ab,
  *   A_ab = sqrt(A_a A_b), B_ab = sqrt(B_a B_b), R_ab = sqrt(R_a R_b), S_ab = sqrt(S_a S_b),

@@ -114,10 +114,13 @@ SWC<T> sw_const(const SWP &p)
 // pass: the atom is then appended to the deferred list and left to the full pass.
 // The cutoff decision is symmetric in i and j: the two fp64 differences are exact
 // negatives of each other, and so are their conversions.
-template <typename T, int CAP, int BLOCK, bool FULL_CAP, bool PREFILTER>
+// MULTI (multi-element Tersoff): the cutoff is that of the element pair, row[t_j].rc2
+// (row: atom i's row of the pair table, rc2 its largest entry), and the neighbour's element
+// is staged in field ftype.
+template <typename T, int CAP, int BLOCK, bool FULL_CAP, bool PREFILTER, bool MULTI = false>
 __device__ __forceinline__ int collect_bonds(const PairArgs<T> &a, int64_t i, const Box &box, T rc2,
                                              uint32_t &mask, const Stage<T, CAP, BLOCK> &S, int fx, int fy,
-                                             int fz, int fr2)
+                                             int fz, int fr2, const TersoffC<T> *row = nullptr, int ftype = 0)
 {
     const int64_t N = a.N;
     const int S_ = a.stride;
@@ -185,9 +188,16 @@ __device__ __forceinline__ int collect_bonds(const PairArgs<T> &a, int64_t i, co
             }
             const T tx = T(dx), ty = T(dy), tz = T(dz);
             const T r2 = tx * tx + ty * ty + tz * tz;
-            if (r2 < rc2) {
+            int tj = 0;
+            T cut2 = rc2;
+            if (MULTI) {
+                tj = a.type[list_atom(e[q])];
+                cut2 = row[tj].rc2;
+            }
+            if (r2 < cut2) {
                 if (na < CAP) {
                     S(fx, na) = tx; S(fy, na) = ty; S(fz, na) = tz; S(fr2, na) = r2;
+                    if (MULTI) S(ftype, na) = T(tj);
                     a.r[(int64_t)(0 * S_ + na) * N + i] = tx;
                     a.r[(int64_t)(1 * S_ + na) * N + i] = ty;
                     a.r[(int64_t)(2 * S_ + na) * N + i] = tz;
@@ -250,10 +260,21 @@ __device__ __forceinline__ int tri(int j, int k) { return k * (k - 1) / 2 + j; }
 template <int CAP>
 constexpr int tersoff_smem_fields() { return TF_NF * CAP + CAP * (CAP - 1) / 2; }
 
-// Pair pass for one atom (Tersoff).
-template <typename T, int CAP, int BLOCK, bool FULL_CAP>
+// Constants of bond k of the atom: its element pair's (MULTI: the row entry of the element
+// staged in field TF_DX), else the single set's.
+template <bool MULTI, typename T>
+__device__ __forceinline__ const TersoffC<T> &bond_const(const TersoffC<T> &p, const TersoffC<T> *row, T tcode)
+{
+    if constexpr (MULTI) return row[(int)tcode];
+    else return p;
+}
+
+// Pair pass for one atom (Tersoff).  MULTI: p holds atom i's element constants (angular
+// and bond-order; rc2 = its row's largest cutoff) and row its pair-constant row; each
+// bond's radial functions take the pair's constants (chi folded into B).
+template <typename T, int CAP, int BLOCK, bool FULL_CAP, bool MULTI = false>
 __device__ __forceinline__ void tersoff_atom(const PairArgs<T> &a, const TersoffC<T> &p, const Box &box, T *base,
-                                             int64_t i)
+                                             int64_t i, const TersoffC<T> *row = nullptr)
 {
     const int64_t N = a.N;
     const int S_ = a.stride;
@@ -262,11 +283,13 @@ __device__ __forceinline__ void tersoff_atom(const PairArgs<T> &a, const Tersoff
     auto INV = [&](int q) -> T & { return sinv[q * BLOCK + threadIdx.x]; };
 
     uint32_t mask;
-    const int na = collect_bonds<T, CAP, BLOCK, FULL_CAP, false>(a, i, box, p.rc2, mask, S, TF_UX, TF_UY, TF_UZ, TF_IR);
+    const int na = collect_bonds<T, CAP, BLOCK, FULL_CAP, false, MULTI>(a, i, box, p.rc2, mask, S, TF_UX, TF_UY,
+                                                                        TF_UZ, TF_IR, row, TF_DX);
     if (na < 0) return;   // deferred to the full-capacity pass
 
     // per-bond radial functions (the staged vectors become unit vectors, r^2 -> 1/r)
     for (int k = 0; k < na; ++k) {
+        const TersoffC<T> &pk = bond_const<MULTI>(p, row, MULTI ? S(TF_DX, k) : T(0));
         const T r2 = S(TF_IR, k);
         const T ir = M<T>::rsqrt_(r2);
         const T r = r2 * ir;
@@ -274,17 +297,19 @@ __device__ __forceinline__ void tersoff_atom(const PairArgs<T> &a, const Tersoff
         S(TF_UY, k) *= ir;
         S(TF_UZ, k) *= ir;
         S(TF_IR, k) = ir;
+        // f_C = 1/2 + 1/2 cos(x) = cos^2(x/2), f_C' = -(pi/(S-R)) sin(x/2) cos(x/2),
+        // x = pi (r-R)/(S-R): the half-angle form has no cancellation as f_C -> 0 near S
         T fc = T(1), dfc = T(0);
-        if (r >= p.R) {
+        if (r >= pk.R) {
             T sn, cn;
-            M<T>::sincos_(p.pi_SR * (r - p.R), &sn, &cn);
-            fc = T(0.5) + T(0.5) * cn;
-            dfc = T(-0.5) * p.pi_SR * sn;
+            M<T>::sincos_(T(0.5) * pk.pi_SR * (r - pk.R), &sn, &cn);
+            fc = cn * cn;
+            dfc = -pk.pi_SR * sn * cn;
         }
         S(TF_FC, k) = fc;
         S(TF_DFC, k) = dfc;
-        S(TF_FR, k) = p.A * M<T>::exp_(-p.lam * r);
-        S(TF_FA, k) = p.B * M<T>::exp_(-p.mu * r);
+        S(TF_FR, k) = pk.A * M<T>::exp_(-pk.lam * r);
+        S(TF_FA, k) = pk.B * M<T>::exp_(-pk.mu * r);
         S(TF_Z, k) = T(0);
     }
     // zeta_ij = sum_{k != j} f_C(r_ik) g(theta_ijk), each unordered pair once
@@ -305,12 +330,13 @@ __device__ __forceinline__ void tersoff_atom(const PairArgs<T> &a, const Tersoff
     // bond orders, U_i, radial part of dU_i/dr_ij; P_k = -1/2 f_C f_A b'_k kept in TF_Z
     T ui = T(0);
     for (int k = 0; k < na; ++k) {
+        const TersoffC<T> &pk = bond_const<MULTI>(p, row, MULTI ? S(TF_DX, k) : T(0));
         T b, db;
         tersoff_b(p, S(TF_Z, k), b, db);
         const T fc = S(TF_FC, k), dfc = S(TF_DFC, k), fr = S(TF_FR, k), fa = S(TF_FA, k);
         ui += T(0.5) * fc * (fr - b * fa);
-        const T dR = dfc * fr - p.lam * fc * fr;   // (f_C f_R)'
-        const T dA = dfc * fa - p.mu * fc * fa;    // (f_C f_A)'
+        const T dR = dfc * fr - pk.lam * fc * fr;   // (f_C f_R)'
+        const T dA = dfc * fa - pk.mu * fc * fa;    // (f_C f_A)'
         const T radial = T(0.5) * (dR - b * dA);
         S(TF_DX, k) = radial * S(TF_UX, k);
         S(TF_DY, k) = radial * S(TF_UY, k);
@@ -462,13 +488,22 @@ __device__ __forceinline__ void pair_dispatch(const PairArgs<T> &a, const Sets &
     }
 }
 
-template <typename T, int CAP, int BLOCK, bool FULL_CAP, bool BATCH>
+template <typename T, int CAP, int BLOCK, bool FULL_CAP, bool BATCH, bool MULTI = false>
 __global__ void __launch_bounds__(BLOCK) k_pair_tersoff(PairArgs<T> a, TersoffSets<T> ps)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     T *base = reinterpret_cast<T *>(smem);
     pair_dispatch<T, CAP, BLOCK, FULL_CAP, BATCH>(a, ps, base, [&](const TersoffC<T> &p, const Box &box, int64_t i) {
-        tersoff_atom<T, CAP, BLOCK, FULL_CAP>(a, p, box, base, i);
+        if constexpr (MULTI) {
+            // atom i's row of the pair table; its own element's entry carries the angular
+            // and bond-order constants (each bond's cutoff is its row entry's)
+            const int ti = a.type[i];
+            const TersoffC<T> *row = static_cast<const TersoffC<T> *>(a.ttab) + ti * kMaxTypes;
+            const TersoffC<T> own = row[ti];
+            tersoff_atom<T, CAP, BLOCK, FULL_CAP, true>(a, own, box, base, i, row);
+        } else {
+            tersoff_atom<T, CAP, BLOCK, FULL_CAP>(a, p, box, base, i);
+        }
     });
 }
 
@@ -927,6 +962,9 @@ void set_smem()
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_for<T, CAP, BLOCK>(1));
     cudaFuncSetAttribute(k_pair_sw<T, CAP, BLOCK, FULL_CAP, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem_for<T, CAP, BLOCK>(2));
+    if constexpr (!BATCH)
+        cudaFuncSetAttribute(k_pair_tersoff<T, CAP, BLOCK, FULL_CAP, false, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_for<T, CAP, BLOCK>(1));
 }
 
 template <typename T, int B, bool BATCH>
@@ -955,6 +993,8 @@ void pair_launch_b(const Plan &p, cudaStream_t s, int list, int parts)
     a.box = p.box;
     a.pos = p.pos;
     a.dev_box = (!BATCH && p.npt) ? 1 : 0;
+    a.type = p.type;
+    a.ttab = p.ttab;
     a.nn = p.nn;
     a.nl = p.nl;
     a.cap = p.cap;
@@ -979,6 +1019,17 @@ void pair_launch_b(const Plan &p, cudaStream_t s, int list, int parts)
     if (p.kind == 1) {
         TersoffSets<T> c;
         for (int k = 0; k < kMaxSets; ++k) c.s[k] = tersoff_const<T>(p.tp[k < p.n_sets ? k : 0]);
+        if constexpr (!BATCH) {
+            if (p.multi) {   // several elements: per-pair constants from the device table
+                if (parts & PAIR_FAST)
+                    k_pair_tersoff<T, kPairCapSmall, B, false, false, true>
+                        <<<nb, B, smem_for<T, kPairCapSmall, B>(1), s>>>(a, c);
+                if (parts & PAIR_DEFERRED)
+                    k_pair_tersoff<T, FULL, kPairBlockFull, true, false, true>
+                        <<<(unsigned)nbf, kPairBlockFull, smem_for<T, FULL, kPairBlockFull>(1), s>>>(a, c);
+                return;
+            }
+        }
         if (parts & PAIR_FAST)
             k_pair_tersoff<T, kPairCapSmall, B, false, BATCH><<<nb, B, smem_for<T, kPairCapSmall, B>(1), s>>>(a, c);
         if (parts & PAIR_DEFERRED)
@@ -1046,7 +1097,27 @@ void gather_launch(const Plan &p, cudaStream_t s, const double *hk, double dt, b
         k_gather<T, MAXA, kGatherBlock, false, BATCH, false><<<nb, kGatherBlock, 0, s>>>(a);
 }
 
+template <typename T>
+void fill_table(const Plan &p, void *host)
+{
+    TersoffC<T> *t = static_cast<TersoffC<T> *>(host);
+    for (int a = 0; a < kMaxTypes; ++a)
+        for (int b = 0; b < kMaxTypes; ++b)
+            t[a * kMaxTypes + b] = tersoff_const<T>(p.tpair[a < p.n_elem ? a : 0][b < p.n_elem ? b : 0]);
+}
+
 }  // namespace
+
+size_t tersoff_table_bytes(const Plan &p)
+{
+    return (size_t)kMaxTypes * kMaxTypes * (p.precision == 0 ? sizeof(TersoffC<double>) : sizeof(TersoffC<float>));
+}
+
+void fill_tersoff_table(const Plan &p, void *host)
+{
+    if (p.precision == 0) fill_table<double>(p, host);
+    else fill_table<float>(p, host);
+}
 
 int effective_pair_block(const Plan &p)
 {

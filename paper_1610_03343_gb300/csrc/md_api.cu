@@ -251,6 +251,43 @@ md_status parse_params(const md_params *params, Plan &p, int idx, double *rc)
     return MD_OK;
 }
 
+// Multi-element Tersoff (Tersoff 1989 multicomponent form): n_types element rows of 11
+// parameters followed by the n_types x n_types factors chi.  Element a goes to p.tp[a];
+// every ordered pair (a, b) gets the constants of a bond from an atom of element a to one
+// of element b: A, B, R, S mixed geometrically and lambda, mu arithmetically, B scaled by
+// chi_ab (b_ij = chi_ab b~_ij enters U_i only as b~_ij (chi_ab f_A)), and element a's
+// beta, n, c, d, h.  rc receives the largest mixed cutoff.
+md_status parse_multi(const md_params *params, Plan &p, double *rc)
+{
+    const int nt = params->n_types;
+    for (int a = 0; a < nt; ++a) {
+        md_params e{MD_TERSOFF, 1, params->p + 11 * a};
+        double rca = 0;
+        if (parse_params(&e, p, a, &rca) != MD_OK) return MD_ERR_ARG;
+    }
+    const double *chi = params->p + 11 * nt;
+    *rc = 0.0;
+    for (int a = 0; a < nt; ++a)
+        for (int b = 0; b < nt; ++b) {
+            const double x = chi[a * nt + b];
+            if (!(x > 0) || !std::isfinite(x)) return MD_ERR_ARG;
+            const TersoffP &ea = p.tp[a], &eb = p.tp[b];
+            TersoffP m = ea;
+            m.A = std::sqrt(ea.A * eb.A);
+            m.B = std::sqrt(ea.B * eb.B) * x;
+            m.lam = 0.5 * (ea.lam + eb.lam);
+            m.mu = 0.5 * (ea.mu + eb.mu);
+            m.R = std::sqrt(ea.R * eb.R);
+            m.S = std::sqrt(ea.S * eb.S);
+            m.pi_SR = M_PI / (m.S - m.R);
+            p.tpair[a][b] = m;
+            *rc = std::max(*rc, m.S);
+        }
+    p.multi = true;
+    p.n_elem = nt;
+    return MD_OK;
+}
+
 // Box and cell grid of one system: periodic edges must exceed 2 (rl + margin); cells
 // have edge >= rl + margin; a grid larger than `max_cells` is coarsened (coarser cells
 // are still correct, only slower).
@@ -678,7 +715,9 @@ void apply_options(Plan &p, const md_options &opt, int kind, double rc)
     p.kind = kind;
     p.precision = opt.precision;
     p.cap = opt.max_neigh;
-    const int want_active = opt.max_active > 0 ? opt.max_active : (kind == MD_SW ? 16 : 8);
+    // SW: diamond Si's second shell sits 0.07 A outside the cutoff; several Tersoff elements:
+    // zincblende SiC's second Si-Si shell (3.06 A) sits 0.06 A outside the Si-Si cutoff
+    const int want_active = opt.max_active > 0 ? opt.max_active : ((kind == MD_SW || p.multi) ? 16 : 8);
     p.maxa = want_active <= 8 ? 8 : 16;
     p.rc = rc;
     p.skin = opt.skin > 0 ? opt.skin : 0.15 * rc;
@@ -793,24 +832,28 @@ md_status md_create(md_ctx **out, const double box[3], const int pbc[3], int64_t
     md_options opt;
     if (opt_in) opt = *opt_in; else md_default_options(&opt);
     if (check_options(opt) != MD_OK) return MD_ERR_ARG;
-    if (params->n_types != 1) return MD_ERR_ARG;
-    if (!(masses_by_type[0] > 0)) return MD_ERR_ARG;
+    const int nt = params->n_types;   // several elements: Tersoff only
+    if (nt < 1 || nt > kMaxTypes || (nt > 1 && params->kind != MD_TERSOFF)) return MD_ERR_ARG;
+    for (int t = 0; t < nt; ++t)
+        if (!(masses_by_type[t] > 0)) return MD_ERR_ARG;
     for (int64_t i = 0; i < n_atoms; ++i)
-        if (types[i] != 0) return MD_ERR_ARG;   // single element
+        if (types[i] < 0 || types[i] >= nt) return MD_ERR_ARG;
 
     md_ctx *ctx = new md_ctx();
     Plan &p = ctx->p;
     double rc = 0;
-    if (parse_params(params, p, 0, &rc) != MD_OK) {
+    if ((nt == 1 ? parse_params(params, p, 0, &rc) : parse_multi(params, p, &rc)) != MD_OK) {
         delete ctx;
         return MD_ERR_ARG;
     }
     apply_options(p, opt, params->kind, rc);
     p.N = n_atoms;
-    p.ntypes = 1;
+    p.ntypes = nt;
     p.n_sets = 1;
-    p.mass[0] = masses_by_type[0];
-    p.inv_mass[0] = 1.0 / masses_by_type[0];
+    for (int t = 0; t < nt; ++t) {
+        p.mass[t] = masses_by_type[t];
+        p.inv_mass[t] = 1.0 / masses_by_type[t];
+    }
     double lmax = std::max(box[0], std::max(box[1], box[2]));
     p.list_margin = list_margin_for(lmax, p.rl);
     md_status st = system_box(p, p.rl, box, pbc, INT64_MAX, &p.box, p.nc);
@@ -846,6 +889,15 @@ md_status md_create(md_ctx **out, const double box[3], const int pbc[3], int64_t
         return st;
     }
     if (p.N > 0) cudaMemcpyAsync(p.type, types, sizeof(int32_t) * p.N, cudaMemcpyHostToDevice, ctx->stream);
+    if (p.multi) {   // pair constants of every element pair, in the pair pass's precision
+        std::vector<unsigned char> tab(tersoff_table_bytes(p));
+        fill_tersoff_table(p, tab.data());
+        if ((st = dalloc(ctx, &p.ttab, tab.size())) != MD_OK) {
+            md_destroy(ctx);
+            return st;
+        }
+        cudaMemcpyAsync(p.ttab, tab.data(), tab.size(), cudaMemcpyHostToDevice, ctx->stream);
+    }
     if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
         cudaGetLastError();
         md_destroy(ctx);
@@ -878,7 +930,8 @@ md_status md_batch_create(md_ctx **out, int64_t atom_capacity, int max_systems, 
     double rcmax = 0;
     for (int k = 0; k < n_sets; ++k) {
         double rc = 0;
-        if (param_sets[k].kind != param_sets[0].kind || parse_params(&param_sets[k], p, k, &rc) != MD_OK) {
+        if (param_sets[k].kind != param_sets[0].kind || param_sets[k].n_types != 1 ||
+            parse_params(&param_sets[k], p, k, &rc) != MD_OK) {
             delete ctx;
             return MD_ERR_ARG;
         }

@@ -143,6 +143,9 @@ struct PairArgs {
     const int *sys_of;      // N: system of each atom (pools)
     const SysDev *sys;      // system table (pools; a single system: its one entry)
     int dev_box;            // single system: read the box from sys[0] (it changes under NPT)
+    const int *type;        // N: element of each atom (multi-element Tersoff)
+    const void *ttab;       // multi-element Tersoff: kMaxTypes x kMaxTypes constants per
+                            // ordered element pair, in T (see force.cu, TersoffC)
     int *ovf_count;         // atoms deferred by the small-capacity pass ...
     int *ovf_list;          // ... and their indices (capacity N)
     const int *act_count;   // pools: number of live 128-atom chunks ...

@@ -26,6 +26,13 @@ struct Plan {
     TersoffP tp[kMaxSets]{};
     SWP sp[kMaxSets]{};
     int ntypes = 1;
+    // multi-element Tersoff (one system, n_elem > 1 elements): constants of every ordered
+    // element pair (a, b): radial parameters mixed, B scaled by chi_ab, angular and
+    // bond-order parameters of element a; and their device copy in the pair pass's type
+    bool multi = false;
+    int n_elem = 1;
+    TersoffP tpair[kMaxTypes][kMaxTypes]{};
+    void *ttab = nullptr;
     double mass[kMaxTypes] = {0, 0, 0, 0};
     double inv_mass[kMaxTypes] = {0, 0, 0, 0};
 
@@ -91,6 +98,10 @@ void launch_displacement_check(const Plan &p, cudaStream_t s);
 void launch_wrap_copy(const Plan &p, cudaStream_t s, double *dst, int64_t a0, int64_t n);
 
 // force.cu
+// Multi-element Tersoff: bytes of the device table of pair constants, and the table
+// itself (host buffer of that size) from p.tpair in the precision of p.
+size_t tersoff_table_bytes(const Plan &p);
+void fill_tersoff_table(const Plan &p, void *host);
 // Pair-pass block size in use (the tuned one, else the precision's default).
 int effective_pair_block(const Plan &p);
 bool valid_pair_block(int b);

@@ -221,14 +221,16 @@ def md_default_options() -> md_options:
     return o
 
 
-def md_create(box, pbc, n_atoms, types, masses_by_type, kind, params, opt: md_options | None = None):
+def md_create(box, pbc, n_atoms, types, masses_by_type, kind, params, opt: md_options | None = None, n_types=1):
+    """params: one element's packed parameters, or (n_types > 1, Tersoff) n_types rows of 11
+    followed by the n_types x n_types chi factors."""
     lib = load()
     box = np.ascontiguousarray(box, dtype=np.float64)
     pbc = np.ascontiguousarray(pbc, dtype=np.int32)
     types = np.ascontiguousarray(types, dtype=np.int32)
     masses = np.ascontiguousarray(masses_by_type, dtype=np.float64)
     prm_arr = np.ascontiguousarray(params, dtype=np.float64)
-    prm = md_params(int(kind), 1, prm_arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    prm = md_params(int(kind), int(n_types), prm_arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
     ctx = ctypes.c_void_p()
     st = lib.md_create(ctypes.byref(ctx), _ptr(box), _ptr(pbc), int(n_atoms), _ptr(types), _ptr(masses),
                        ctypes.byref(prm), ctypes.byref(opt) if opt is not None else None)
@@ -505,7 +507,7 @@ class System:
     library; the transposes below are the marshalling."""
 
     def __init__(self, box, pbc, n_atoms, kind, params, mass, precision=MD_FP64, skin=0.0,
-                 max_neigh=32, max_active=0, io=MD_IO_HOST, stream=None, hbm_budget=0):
+                 max_neigh=32, max_active=0, io=MD_IO_HOST, stream=None, hbm_budget=0, types=None, n_types=1):
         self.n = int(n_atoms)
         self.io = io
         opt = md_default_options()
@@ -516,7 +518,9 @@ class System:
         opt.io = io
         opt.cuda_stream = stream
         opt.hbm_budget = hbm_budget
-        self.ctx = md_create(box, pbc, self.n, np.zeros(self.n, np.int32), [mass], kind, params, opt)
+        t = np.zeros(self.n, np.int32) if types is None else np.asarray(types, dtype=np.int32)
+        masses = [float(m) for m in mass] if np.ndim(mass) else [float(mass)]
+        self.ctx = md_create(box, pbc, self.n, t, masses, kind, params, opt, n_types=n_types)
 
     def close(self):
         if self.ctx:
@@ -609,6 +613,24 @@ class System:
 
     def box(self):
         return md_get_box(self.ctx, 0)
+
+
+def multi_params(element_rows, chi):
+    """Packed multi-element Tersoff parameters: the element rows, then chi row-major."""
+    rows = np.asarray(element_rows, dtype=np.float64).reshape(-1, 11)
+    return np.concatenate([rows.reshape(-1), np.asarray(chi, dtype=np.float64).reshape(-1)])
+
+
+def from_multi(msys, precision=MD_FP64, **kw) -> System:
+    """Context for an inputs.MultiSystem (multi-element Tersoff), positions and velocities
+    uploaded."""
+    nt = len(msys.params)
+    s = System(msys.box, msys.pbc, msys.n, MD_TERSOFF, multi_params(msys.params, msys.chi), list(msys.masses),
+               precision=precision, types=msys.types, n_types=nt, **kw)
+    s.set_positions(msys.pos)
+    if msys.vel is not None:
+        s.set_velocities(msys.vel)
+    return s
 
 
 def from_inputs(sysm, precision=MD_FP64, **kw) -> System:
