@@ -24,6 +24,7 @@
 // the block / system totals in fp64).
 #include <algorithm>
 
+#include "fastmath.cuh"
 #include "md_plan.cuh"
 
 namespace mdk {
@@ -36,11 +37,17 @@ constexpr int kPoolChunk = 128;   // pools place systems on 128-atom chunk bound
 
 // ---------------------------------------------------------------- precision
 template <typename T> struct M;
+// texp_, tlog_, tlog1p_: the Tersoff pair pass's exponentials and logarithms, whose
+// arguments stay inside the table-driven routines' domain (fastmath.cuh); tlog1p_ needs
+// only absolute accuracy (it enters b = exp(-log(1 + x)/(2n))).
 template <> struct M<double> {
     static __device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
     static __device__ __forceinline__ double exp_(double x) { return exp(x); }
     static __device__ __forceinline__ double log_(double x) { return log(x); }
     static __device__ __forceinline__ double log1p_(double x) { return log1p(x); }
+    static __device__ __forceinline__ double texp_(double x) { return exp_tab(x); }
+    static __device__ __forceinline__ double tlog_(double x) { return log_tab(x); }
+    static __device__ __forceinline__ double tlog1p_(double x) { return log_tab(1.0 + x); }
     static __device__ __forceinline__ void sincos_(double x, double *s, double *c) { sincos(x, s, c); }
     static __device__ __forceinline__ double pow_(double x, double y) { return pow(x, y); }
 };
@@ -49,6 +56,9 @@ template <> struct M<float> {
     static __device__ __forceinline__ float exp_(float x) { return expf(x); }
     static __device__ __forceinline__ float log_(float x) { return logf(x); }
     static __device__ __forceinline__ float log1p_(float x) { return log1pf(x); }
+    static __device__ __forceinline__ float texp_(float x) { return expf(x); }
+    static __device__ __forceinline__ float tlog_(float x) { return logf(x); }
+    static __device__ __forceinline__ float tlog1p_(float x) { return log1pf(x); }
     static __device__ __forceinline__ void sincos_(float x, float *s, float *c) { sincosf(x, s, c); }
     static __device__ __forceinline__ float pow_(float x, float y) { return powf(x, y); }
 };
@@ -249,8 +259,8 @@ __device__ __forceinline__ void tersoff_b(const TersoffC<T> &p, T zeta, T &b, T 
         db = T(0);
         return;
     }
-    const T x = M<T>::exp_(p.n * (M<T>::log_(zeta) + p.ln_beta));
-    b = M<T>::exp_(-p.inv2n * M<T>::log1p_(x));
+    const T x = M<T>::texp_(p.n * (M<T>::tlog_(zeta) + p.ln_beta));
+    b = M<T>::texp_(-p.inv2n * M<T>::tlog1p_(x));
     db = T(-0.5) * b * x / (zeta * (T(1) + x));
 }
 
@@ -308,8 +318,8 @@ __device__ __forceinline__ void tersoff_atom(const PairArgs<T> &a, const Tersoff
         }
         S(TF_FC, k) = fc;
         S(TF_DFC, k) = dfc;
-        S(TF_FR, k) = pk.A * M<T>::exp_(-pk.lam * r);
-        S(TF_FA, k) = pk.B * M<T>::exp_(-pk.mu * r);
+        S(TF_FR, k) = pk.A * M<T>::texp_(-pk.lam * r);
+        S(TF_FA, k) = pk.B * M<T>::texp_(-pk.mu * r);
         S(TF_Z, k) = T(0);
     }
     // zeta_ij = sum_{k != j} f_C(r_ik) g(theta_ijk), each unordered pair once
@@ -1108,6 +1118,14 @@ void fill_table(const Plan &p, void *host)
 
 }  // namespace
 
+namespace {
+__global__ void k_fastmath_eval(int fn, int64_t n, const double *x, double *y)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = fn == 0 ? exp_tab(x[i]) : log_tab(x[i]);
+}
+}  // namespace
+
 size_t tersoff_table_bytes(const Plan &p)
 {
     return (size_t)kMaxTypes * kMaxTypes * (p.precision == 0 ? sizeof(TersoffC<double>) : sizeof(TersoffC<float>));
@@ -1261,3 +1279,29 @@ int gather_block() { return kGatherBlock; }
 int gather_blocks(int64_t N) { return N == 0 ? 1 : (int)blocks_for(N, kGatherBlock); }
 
 }  // namespace mdk
+
+// Diagnostics: the pair pass's table-driven fp64 exp (fn 0) or log (fn 1) of n host values
+// on the current device (accuracy tests).  Returns 0, -1 for bad arguments, -5 on a CUDA
+// error.
+extern "C" int md_fastmath_eval(int fn, int64_t n, const double *x, double *y)
+{
+    if ((fn != 0 && fn != 1) || n < 0 || (n > 0 && (!x || !y))) return -1;
+    if (n == 0) return 0;
+    double *d = nullptr;
+    if (cudaMalloc(&d, sizeof(double) * 2 * (size_t)n) != cudaSuccess) {
+        cudaGetLastError();
+        return -5;
+    }
+    cudaError_t e = cudaMemcpy(d, x, sizeof(double) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        mdk::k_fastmath_eval<<<(unsigned)((n + 255) / 256), 256>>>(fn, n, d, d + n);
+        e = cudaMemcpy(y, d + n, sizeof(double) * n, cudaMemcpyDeviceToHost);
+    }
+    cudaFree(d);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return -5;
+    }
+    return 0;
+}
+

@@ -118,7 +118,7 @@ EXPORTS = ["md_default_options", "md_create", "md_set_positions", "md_set_veloci
            "md_kernel_times", "md_autotune", "md_set_tuning", "md_get_tuning", "md_batch_create", "md_batch_add", "md_batch_remove", "md_batch_status",
            "md_batch_get_state", "md_server_create", "md_server_submit", "md_server_poll", "md_server_wait",
            "md_server_drain", "md_server_stats_get", "md_server_clock", "md_server_destroy",
-           "md_compute_static", "md_hcacf", "md_last_error", "md_destroy"]
+           "md_compute_static", "md_hcacf", "md_fastmath_eval", "md_last_error", "md_destroy"]
 
 
 def library_path() -> str:
@@ -179,6 +179,8 @@ def load(build_if_missing: bool = False):
                                           ctypes.c_double, P, P, P, P, P, P]
         lib.md_hcacf.argtypes = [P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
                                  ctypes.c_double, ctypes.c_double, P, P, ctypes.c_int, P]
+        lib.md_fastmath_eval.argtypes = [ctypes.c_int, ctypes.c_int64, P, P]
+        lib.md_fastmath_eval.restype = ctypes.c_int
         lib.md_last_error.argtypes = [P]
         lib.md_last_error.restype = ctypes.c_char_p
         lib.md_destroy.argtypes = [P]
@@ -282,6 +284,17 @@ def md_get_box(ctx, system=0) -> np.ndarray:
     b = np.zeros(3)
     _check(lib, ctx, lib.md_get_box(ctx, int(system), _ptr(b)))
     return b
+
+
+def md_fastmath_eval(fn: int, x) -> np.ndarray:
+    """The pair pass's table-driven fp64 exp (fn 0) or log (fn 1), evaluated on the GPU."""
+    lib = load()
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.empty_like(x)
+    st = lib.md_fastmath_eval(int(fn), x.size, _ptr(x), _ptr(y))
+    if st != 0:
+        raise MDError(st, "md_fastmath_eval failed")
+    return y
 
 
 def md_get_stats(ctx) -> md_stats:

@@ -1,0 +1,62 @@
+"""The table-driven fp64 exp and log of the Tersoff pair pass (fastmath.cuh, Tang's
+method) against numpy's libm on the host: exp within 2 ulp over the pair pass's domain and
+beyond, log within an absolute 2e-16 (1 + |binary exponent|), including the table and
+interval boundaries, powers of two, values next to 1 and subnormal-free extremes."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def md():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1610_03343_gb300 import _build, md as M
+    _build.build()
+    M.load()
+    return M
+
+
+def ulp_err(y, ref):
+    return np.abs(y - ref) / np.spacing(np.abs(ref))
+
+
+def test_exp_within_two_ulp(md):
+    rng = np.random.Generator(np.random.PCG64(1))
+    ln2_64 = np.log(2.0) / 64
+    x = np.concatenate([
+        rng.uniform(-12.0, 0.0, 400000),              # -lambda r, -mu r
+        rng.uniform(-80.0, 10.0, 400000),             # n log(beta zeta), -log(1+x)/(2n)
+        rng.uniform(-700.0, 700.0, 100000),
+        np.arange(-2000, 2000) * ln2_64,              # table boundaries
+        np.arange(-2000, 2000) * ln2_64 + ln2_64 / 2,  # reduction interval edges
+        np.nextafter(np.arange(-2000, 2000) * ln2_64 + ln2_64 / 2, 0.0),
+        [0.0, -0.0, 1e-300, -1e-300, 1e-10, -1e-10, 1.0, -1.0, 700.0, -700.0],
+    ])
+    y = md.md_fastmath_eval(0, x)
+    e = ulp_err(y, np.exp(x))
+    assert e.max() <= 2.0, (x[np.argmax(e)], e.max())
+    assert np.median(e) <= 0.5
+
+
+def test_log_absolute_error(md):
+    rng = np.random.Generator(np.random.PCG64(2))
+    x = np.concatenate([
+        np.exp(rng.uniform(-75.0, 25.0, 400000)),      # zeta, 1 + x of the bond order
+        1.0 + rng.uniform(0.0, 300.0, 200000),
+        1.0 + np.exp(rng.uniform(-40.0, 0.0, 100000)),
+        2.0 ** np.arange(-1000, 1000, dtype=np.float64),
+        np.nextafter(2.0 ** np.arange(-1000, 1000, dtype=np.float64), 0.0),
+        1.0 + np.arange(129) / 128.0,                  # table interval boundaries
+        np.nextafter(1.0 + np.arange(1, 129) / 128.0, 0.0),
+        [1.0, np.nextafter(1.0, 2.0), np.nextafter(1.0, 0.0), 1e-300, 1e300, 2.2250738585072014e-308],
+    ])
+    y = md.md_fastmath_eval(1, x)
+    ref = np.log(x)
+    expo = np.abs(np.frexp(x)[1] - 1).astype(np.float64)
+    bound = 2e-16 * (1.0 + expo)
+    err = np.abs(y - ref)
+    assert np.all(err <= bound), (x[np.argmax(err / bound)], (err / bound).max())
+    assert y[-6] == 0.0 or abs(y[-6]) < 1e-17            # log(1) ~ 0
