@@ -48,6 +48,9 @@ template <> struct M<double> {
     static __device__ __forceinline__ double texp_(double x) { return exp_tab(x); }
     static __device__ __forceinline__ double tlog_(double x) { return log_tab(x); }
     static __device__ __forceinline__ double tlog1p_(double x) { return log_tab(1.0 + x); }
+    // SW: exp(sigma/(r - a sigma)) and exp(gamma sigma/(r - a sigma)) go to -infinity at the
+    // cutoff; below -700 the factor is < 1e-304 and is taken as e^-700
+    static __device__ __forceinline__ double sexp_(double x) { return exp_tab(fmax(x, -700.0)); }
     static __device__ __forceinline__ void sincos_(double x, double *s, double *c) { sincos(x, s, c); }
     static __device__ __forceinline__ double pow_(double x, double y) { return pow(x, y); }
 };
@@ -59,6 +62,7 @@ template <> struct M<float> {
     static __device__ __forceinline__ float texp_(float x) { return expf(x); }
     static __device__ __forceinline__ float tlog_(float x) { return logf(x); }
     static __device__ __forceinline__ float tlog1p_(float x) { return log1pf(x); }
+    static __device__ __forceinline__ float sexp_(float x) { return expf(x); }
     static __device__ __forceinline__ void sincos_(float x, float *s, float *c) { sincosf(x, s, c); }
     static __device__ __forceinline__ float pow_(float x, float y) { return powf(x, y); }
 };
@@ -78,6 +82,7 @@ struct Stage {
     T *s;
     int t;
     __device__ __forceinline__ T &operator()(int f, int k) const { return s[(f * CAP + k) * BLOCK + t]; }
+    __device__ __forceinline__ void set(int f, int k, T v) const { s[(f * CAP + k) * BLOCK + t] = v; }
 };
 
 // Potential constants in the pair pass's arithmetic type (no conversions in the loops).
@@ -127,10 +132,10 @@ SWC<T> sw_const(const SWP &p)
 // MULTI (multi-element Tersoff): the cutoff is that of the element pair, row[t_j].rc2
 // (row: atom i's row of the pair table, rc2 its largest entry), and the neighbour's element
 // is staged in field ftype.
-template <typename T, int CAP, int BLOCK, bool FULL_CAP, bool PREFILTER, bool MULTI = false>
+template <typename T, int CAP, int BLOCK, bool FULL_CAP, bool PREFILTER, bool MULTI = false, typename ST>
 __device__ __forceinline__ int collect_bonds(const PairArgs<T> &a, int64_t i, const Box &box, T rc2,
-                                             uint32_t &mask, const Stage<T, CAP, BLOCK> &S, int fx, int fy,
-                                             int fz, int fr2, const TersoffC<T> *row = nullptr, int ftype = 0)
+                                             uint32_t &mask, ST &S, int fx, int fy, int fz, int fr2,
+                                             const TersoffC<T> *row = nullptr, int ftype = 0)
 {
     const int64_t N = a.N;
     const int S_ = a.stride;
@@ -196,7 +201,7 @@ __device__ __forceinline__ int collect_bonds(const PairArgs<T> &a, int64_t i, co
                 if (sy) dy += sy > 0 ? box.L[1] : -box.L[1];
                 if (sz) dz += sz > 0 ? box.L[2] : -box.L[2];
             }
-            const T tx = T(dx), ty = T(dy), tz = T(dz);
+            const T tx = to_t<T>(dx), ty = to_t<T>(dy), tz = to_t<T>(dz);
             const T r2 = tx * tx + ty * ty + tz * tz;
             int tj = 0;
             T cut2 = rc2;
@@ -206,8 +211,8 @@ __device__ __forceinline__ int collect_bonds(const PairArgs<T> &a, int64_t i, co
             }
             if (r2 < cut2) {
                 if (na < CAP) {
-                    S(fx, na) = tx; S(fy, na) = ty; S(fz, na) = tz; S(fr2, na) = r2;
-                    if (MULTI) S(ftype, na) = T(tj);
+                    S.set(fx, na, tx); S.set(fy, na, ty); S.set(fz, na, tz); S.set(fr2, na, r2);
+                    if (MULTI) S.set(ftype, na, T(tj));
                     a.r[(int64_t)(0 * S_ + na) * N + i] = tx;
                     a.r[(int64_t)(1 * S_ + na) * N + i] = ty;
                     a.r[(int64_t)(2 * S_ + na) * N + i] = tz;
@@ -380,7 +385,7 @@ __device__ __forceinline__ void tersoff_atom(const PairArgs<T> &a, const Tersoff
         a.d[(int64_t)(2 * S_ + j) * N + i] = djz;
     }
     a.mask[i] = mask;
-    a.u[i] = double(ui);
+    a.u[i] = to_d(ui);
 }
 
 // ---------------------------------------------------------- Stillinger-Weber
@@ -408,8 +413,8 @@ __device__ __forceinline__ void sw_atom(const PairArgs<T> &a, const SWC<T> &p, c
         const T ux = S(SW_UX, k) * ir, uy = S(SW_UY, k) * ir, uz = S(SW_UZ, k) * ir;
         S(SW_UX, k) = ux; S(SW_UY, k) = uy; S(SW_UZ, k) = uz; S(SW_IR, k) = ir;
         const T irc = T(1) / (r - p.rc);                 // 1/(r - a sigma) < 0
-        const T e2 = M<T>::exp_(p.sig * irc);
-        const T E = M<T>::exp_(p.gamsig * irc);
+        const T e2 = M<T>::sexp_(p.sig * irc);
+        const T E = M<T>::sexp_(p.gamsig * irc);
         S(SW_E, k) = E;
         S(SW_DE, k) = -p.gamsig * irc * irc * E;
         // phi2 = A eps [B (sigma/r)^p - (sigma/r)^q] exp(sigma/(r - a sigma))
@@ -452,7 +457,7 @@ __device__ __forceinline__ void sw_atom(const PairArgs<T> &a, const SWC<T> &p, c
         a.d[(int64_t)(2 * S_ + j) * N + i] = djz;
     }
     a.mask[i] = mask;
-    a.u[i] = double(ui);
+    a.u[i] = to_d(ui);
 }
 
 template <typename T>
@@ -683,7 +688,7 @@ __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, i
             ++k;
         }
         if (!(isfinite(f0) && isfinite(f1) && isfinite(f2))) a.flags->nonfinite = 1;
-        const double F[3] = {double(f0), double(f1), double(f2)};
+        const double F[3] = {to_d(f0), to_d(f1), to_d(f2)};
         a.force[i] = F[0];
         a.force[N + i] = F[1];
         a.force[2 * N + i] = F[2];
@@ -704,28 +709,28 @@ __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, i
         }
         // J_i = M_i . v_i and K_i = m v^2 / 2 in T (the fp32 per-atom value of the mixed
         // path feeds an fp64 total)
-        const T vx = T(v[0]), vy = T(v[1]), vz = T(v[2]);
+        const T vx = to_t<T>(v[0]), vy = to_t<T>(v[1]), vz = to_t<T>(v[2]);
         const T J0 = mj[0] * vx + mj[1] * vy + mj[2] * vz;
         const T J1 = mj[3] * vx + mj[4] * vy + mj[5] * vz;
         const T J2 = mj[6] * vx + mj[7] * vy + mj[8] * vz;
-        const T ke = T(0.5 / kAccUnit) * T(a.mass[t]) * (vx * vx + vy * vy + vz * vz);
+        const T hm = a.hm[t];
+        const T ke = hm * (vx * vx + vy * vy + vz * vz);
         vals[0] = a.u[i];
-        vals[1] = double(ke);
-        vals[2] = double(J0);
-        vals[3] = double(J1);
-        vals[4] = double(J2);
+        vals[1] = to_d(ke);
+        vals[2] = to_d(J0);
+        vals[3] = to_d(J1);
+        vals[4] = to_d(J2);
         if (WDIAG) {
-            const T hm = T(0.5 / kAccUnit) * T(a.mass[t]);
-            vals[5] = double(hm * vx * vx);
-            vals[6] = double(hm * vy * vy);
-            vals[7] = double(hm * vz * vz);
-            vals[8] = -0.5 * double(wd0);
-            vals[9] = -0.5 * double(wd1);
-            vals[10] = -0.5 * double(wd2);
+            vals[5] = to_d(hm * vx * vx);
+            vals[6] = to_d(hm * vy * vy);
+            vals[7] = to_d(hm * vz * vz);
+            vals[8] = -0.5 * to_d(wd0);
+            vals[9] = -0.5 * to_d(wd1);
+            vals[10] = -0.5 * to_d(wd2);
         }
         if (FULL) {
 #pragma unroll
-            for (int c = 0; c < 9; ++c) vals[5 + c] = -0.5 * double(w[c]);
+            for (int c = 0; c < 9; ++c) vals[5 + c] = -0.5 * to_d(w[c]);
             if (a.w_out) {
 #pragma unroll
                 for (int c = 0; c < 9; ++c) a.w_out[c * N + i] = vals[5 + c];
@@ -781,10 +786,24 @@ k_reduce(const double *partials, int nc, int seg_max, int64_t N, int block, cons
         if (!ran) return;
     }
     const int64_t b0 = na > 0 ? a0 / block : 0, b1 = na > 0 ? (a0 + na - 1) / block : -1;
+    // each thread adds its blocks b0 + t, b0 + t + T, ... in that order; eight loads are
+    // issued before their additions so that they are in flight together
+    // (a missing block contributes +0.0, which leaves the sum unchanged)
     double acc = 0.0;
-    for (int64_t b = b0 + threadIdx.x; b <= b1; b += blockDim.x) {
-        const int seg = BATCH ? s - sys_of[b * block] : 0;
-        acc += partials[(b * seg_max + seg) * nc + c];
+    const int64_t stride = blockDim.x;
+    for (int64_t b = b0 + threadIdx.x; b <= b1; b += 8 * stride) {
+        double v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int64_t bq = b + q * stride;
+            v[q] = 0.0;
+            if (bq <= b1) {
+                const int seg = BATCH ? s - sys_of[bq * block] : 0;
+                v[q] = partials[(bq * seg_max + seg) * nc + c];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc += v[q];
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
@@ -851,7 +870,7 @@ __device__ __forceinline__ void kick_drift_atom(const KickDriftArgs &a, int64_t 
         a.vel[c * N + i] = v;
         a.pos[c * N + i] = x;
         if (a.posf) a.posf[c * N + i] = (float)x;
-        const float d = (float)(x - xb);
+        const float d = d2f_trunc(x - xb);
         d2 = fmaf(d, d, d2);
     }
     const float hs2 = (NPT && sdp->npt.on) ? npt_half_skin2(*sdp, true)
@@ -1083,6 +1102,7 @@ void gather_launch(const Plan &p, cudaStream_t s, const double *hk, double dt, b
     a.type = p.type;
     for (int t = 0; t < kMaxTypes; ++t) {
         a.mass[t] = p.mass[t];
+        a.hm[t] = T(0.5 / kAccUnit) * T(p.mass[t]);
         a.hk[t] = hk ? hk[t] : 0.0;
     }
     a.kick = hk != nullptr;

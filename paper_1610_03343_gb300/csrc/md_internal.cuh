@@ -169,6 +169,7 @@ struct GatherArgs {
     const double *u;
     const int *type;
     double mass[kMaxTypes];
+    T hm[kMaxTypes];        // m / (2 acc) per type in T (kinetic energy m v^2 / 2)
     double hk[kMaxTypes];   // half-kick factor dt/2 * acc / m per type
     int kick;               // apply the half-kick v += hk F
     double *vel;            // 3N, updated in place when kicking
@@ -209,6 +210,38 @@ __host__ __device__ __forceinline__ float npt_half_skin2(const SysDev &sd, bool 
     const double h = 0.5 * (mmin * sd.rl - sd.rc);
     return h > 0.0 ? (float)(h * h) : -1.0f;
 }
+
+// Conversions between fp32 and fp64 with integer instructions.  GB300 executes
+// F2F conversions on its fp64 pipe (1/64 of the fp32 rate); the mixed path needs a few per
+// atom, and integer shifts and adds cost nothing next to that.
+//   f2d_int: exact for zero and normal floats; subnormal floats become a signed zero (the
+//            values converted -- forces, per-atom sums, bond vectors -- are never subnormal
+//            in magnitude that matters); inf/NaN become large finite doubles (non-finite
+//            forces are flagged before conversion).
+//   d2f_trunc: rounds toward zero (at most 1 float ulp); magnitudes below the float normal
+//            range become a signed zero; the argument must stay below 3.4e38.
+__device__ __forceinline__ double f2d_int(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    const unsigned a = u & 0x7fffffffu, s = u & 0x80000000u;
+    const bool nrm = a >= 0x00800000u;
+    const unsigned hi = nrm ? (s | ((a >> 3) + 0x38000000u)) : s;   // exponent bias 127 -> 1023
+    const unsigned lo = nrm ? (a << 29) : 0u;
+    return __hiloint2double((int)hi, (int)lo);
+}
+__device__ __forceinline__ float d2f_trunc(double d)
+{
+    const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+    const unsigned a = hi & 0x7fffffffu, s = hi & 0x80000000u;
+    const unsigned f = a >= 0x38100000u ? (((a - 0x38000000u) << 3) | (lo >> 29)) : 0u;
+    return __uint_as_float(s | f);
+}
+// x in the pair pass's type T, and back to fp64 (identities for T = double)
+template <typename T> __device__ __forceinline__ T to_t(double x);
+template <> __device__ __forceinline__ double to_t<double>(double x) { return x; }
+template <> __device__ __forceinline__ float to_t<float>(double x) { return d2f_trunc(x); }
+__device__ __forceinline__ double to_d(double x) { return x; }
+__device__ __forceinline__ double to_d(float x) { return f2d_int(x); }
 
 // r_ij from positions and a list entry's image code (three fp64 subtractions, plus
 // one addition per shifted axis).
