@@ -155,7 +155,8 @@ def run_ours(args, rank, world):
         elif not args.no_tune:
             tuning = md.tuning_dict(md.md_autotune(g.ctx, 10))
         g.run(args.warmup, dt, record=False)
-        rebuilds0 = g.stats().n_rebuilds
+        st0 = g.stats()
+        rebuilds0, kernels0 = st0.n_rebuilds, st0.kernels_launched
         md.md_set_profiling(g.ctx, True)
         if world > 1:
             torch.distributed.barrier()
@@ -176,7 +177,7 @@ def run_ours(args, rank, world):
         st = g.stats()
         res[tag] = dict(ms=ms, kt=kt, f0=f0, clocks=clocks.summary(), stats=st, sys=g, tuning=tuning, series=ser,
                         rebuilds=int(st.n_rebuilds - rebuilds0),
-                        launches=int(st.kernel_launches_per_step) * args.steps
+                        launches=int(st.kernels_launched - kernels0)
                         + int(st.kernel_launches_per_rebuild) * int(st.n_rebuilds - rebuilds0))
     # end-to-end through the public API with host buffers (pinned), copies inside the
     # timed region: upload x, v; run K steps; read back the series and the final state

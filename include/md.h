@@ -184,13 +184,18 @@ typedef struct {
     int64_t steps_done;      /* MD steps since creation                               */
     int64_t n_rebuilds;      /* neighbour-list builds since creation                  */
     int max_neigh_seen;      /* largest list length at the last build                 */
-    int kernel_launches_per_step; /* kernels every md_run step launches               */
+    int kernel_launches_per_step; /* kernels of one md_run step launched on its own (inside
+                                 a graph of steps, each step after the first has its first
+                                 half-kick fused into the previous step's gather)         */
     int kernel_launches_per_rebuild; /* extra kernels of a step that rebuilds the list */
     int pair_deferred;       /* atoms with more than 4 in-cutoff bonds at the last pair pass
                                 (handled by the full-capacity pass)                      */
     size_t device_bytes;     /* bytes the context has allocated on the device         */
     int64_t atoms_rebuilt;   /* atoms whose neighbour list was built, summed over builds
                                 (pools: only the systems that needed a rebuild)          */
+    int64_t kernels_launched; /* kernels md_run has launched (graph replays included; the
+                                 kernels of taken list rebuilds are not counted: add
+                                 kernel_launches_per_rebuild per rebuild)               */
 } md_stats;
 md_status md_get_stats(md_ctx *ctx, md_stats *out);
 

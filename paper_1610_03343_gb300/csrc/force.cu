@@ -646,10 +646,16 @@ __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, i
     const int seg = 0, nseg = 1;
     bool live = i < N;
     double damp = 0.0;
+    bool fuse = a.fuse_kick != 0;
+    float hs2 = a.half_skin2;
+    int sid = 0;
     if (BATCH && live) {
-        const SysDev &sd = a.sys[a.sys_of[i]];
+        sid = a.sys_of[i];
+        const SysDev &sd = a.sys[sid];
         live = system_live(sd, a.flags);
         damp = sd.damp;
+        fuse = fuse && sd.steps_left != 1;   // a system's last budgeted step ends here
+        hs2 = sd.half_skin2;
     }
     if (live) {
         uint32_t mask = a.mask[i];
@@ -703,9 +709,26 @@ __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, i
                 const double f = 1.0 - damp * a.dt;
                 v[0] *= f; v[1] *= f; v[2] *= f;
             }
-            a.vel[i] = v[0];
-            a.vel[N + i] = v[1];
-            a.vel[2 * N + i] = v[2];
+            double vn[3] = {v[0], v[1], v[2]};
+            if (fuse) {   // the next step's half-kick and drift (k_kick_drift's arithmetic)
+                float d2 = 0.f;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    vn[c] = fma(h, F[c], v[c]);
+                    const double x = fma(a.dt, vn[c], a.pos[c * N + i]);
+                    a.pos[c * N + i] = x;
+                    if (a.posf) a.posf[c * N + i] = (float)x;
+                    const float d = d2f_trunc(x - a.pos_build[c * N + i]);
+                    d2 = fmaf(d, d, d2);
+                }
+                if (!(d2 <= hs2)) {
+                    a.flags->rebuild = 1;
+                    if (BATCH) a.sys[sid].rebuild = 1;
+                }
+            }
+            a.vel[i] = vn[0];
+            a.vel[N + i] = vn[1];
+            a.vel[2 * N + i] = vn[2];
         }
         // J_i = M_i . v_i and K_i = m v^2 / 2 in T (the fp32 per-atom value of the mixed
         // path feeds an fp64 total)
@@ -1089,7 +1112,7 @@ void pair_launch(const Plan &p, cudaStream_t s, int list, int parts)
 }
 
 template <typename T, int MAXA, bool BATCH>
-void gather_launch(const Plan &p, cudaStream_t s, const double *hk, double dt, bool full)
+void gather_launch(const Plan &p, cudaStream_t s, const double *hk, double dt, bool full, bool fuse_next)
 {
     GatherArgs<T> a;
     a.N = p.N;
@@ -1118,6 +1141,11 @@ void gather_launch(const Plan &p, cudaStream_t s, const double *hk, double dt, b
     a.flags = p.flags;
     a.act_count = p.act_plan;
     a.act_chunks = p.act_chunks;
+    a.fuse_kick = (fuse_next && hk && !full && !p.npt) ? 1 : 0;
+    a.pos = p.pos;
+    a.pos_build = p.pos_build;
+    a.posf = p.kind == 2 ? p.posf : nullptr;
+    a.half_skin2 = (float)(0.25 * p.skin * p.skin);
     const unsigned nb = BATCH ? pool_grid(p) : blocks_for(p.N, kGatherBlock);
     if (full)
         k_gather<T, MAXA, kGatherBlock, true, BATCH, false><<<nb, kGatherBlock, 0, s>>>(a);
@@ -1252,21 +1280,22 @@ int launch_pair(const Plan &p, cudaStream_t s, int list, int parts)
 }
 
 template <bool BATCH>
-void gather_dispatch(const Plan &p, cudaStream_t s, const double *hk, double dt, bool full)
+void gather_dispatch(const Plan &p, cudaStream_t s, const double *hk, double dt, bool full, bool fuse)
 {
     if (p.precision == 0) {
-        if (p.maxa <= 8) gather_launch<double, 8, BATCH>(p, s, hk, dt, full);
-        else gather_launch<double, 16, BATCH>(p, s, hk, dt, full);
+        if (p.maxa <= 8) gather_launch<double, 8, BATCH>(p, s, hk, dt, full, fuse);
+        else gather_launch<double, 16, BATCH>(p, s, hk, dt, full, fuse);
     } else {
-        if (p.maxa <= 8) gather_launch<float, 8, BATCH>(p, s, hk, dt, full);
-        else gather_launch<float, 16, BATCH>(p, s, hk, dt, full);
+        if (p.maxa <= 8) gather_launch<float, 8, BATCH>(p, s, hk, dt, full, fuse);
+        else gather_launch<float, 16, BATCH>(p, s, hk, dt, full, fuse);
     }
 }
 
-void launch_gather(const Plan &p, cudaStream_t s, const double *hk, double dt, bool full)
+void launch_gather(const Plan &p, cudaStream_t s, const double *hk, double dt, bool full, bool fuse_next)
 {
     if (p.N == 0) return;
-    if (p.batch) gather_dispatch<true>(p, s, hk, dt, full); else gather_dispatch<false>(p, s, hk, dt, full);
+    if (p.batch) gather_dispatch<true>(p, s, hk, dt, full, fuse_next);
+    else gather_dispatch<false>(p, s, hk, dt, full, fuse_next);
 }
 
 void launch_reduce(const Plan &p, cudaStream_t s, bool full, bool record_series)

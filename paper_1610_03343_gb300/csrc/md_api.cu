@@ -75,6 +75,8 @@ struct md_ctx {
     int64_t steps_done = 0;
     int kernels_per_step = 0;
     int kernels_per_rebuild = 0;
+    int kernels_g8 = 0, kernels_g1 = 0;   // kernels of one replay of each step graph
+    int64_t kernels_launched = 0;         // by md_run steps (rebuild bodies not counted)
     // graph cache: an 8-step and a 1-step graph of the velocity-Verlet step
     cudaGraphExec_t gexec = nullptr, gexec1 = nullptr;
     double g_dt = 0.0;
@@ -405,7 +407,8 @@ md_status add_conditional_rebuild(md_ctx *ctx, cudaGraphConditionalHandle h, cud
 //                                                             +-> IF: rebuild, pair(rebuilt) +
 //   -> deferred atoms' pair pass -> gather (+ half-kick) -> reduce (series row)
 // Each atom's work is the same as on a single branch, so results do not change.
-md_status enqueue_pool_tail(md_ctx *ctx, const Recorder &rec, const double *hk, double dt, int *n_kernels)
+md_status enqueue_pool_tail(md_ctx *ctx, const Recorder &rec, const double *hk, double dt, int *n_kernels,
+                            bool fuse_prev, bool fuse_next)
 {
     cudaGraphConditionalHandle h;
     cudaStreamCaptureStatus cs;
@@ -427,28 +430,32 @@ md_status enqueue_pool_tail(md_ctx *ctx, const Recorder &rec, const double *hk, 
     launch_pair(ctx->p, ctx->stream, PAIR_ALL, PAIR_DEFERRED);
     rec.end(KC_PAIR);
     rec.begin(KC_GATHER);
-    launch_gather(ctx->p, ctx->stream, hk, dt, false);
+    launch_gather(ctx->p, ctx->stream, hk, dt, false, fuse_next);
     rec.end(KC_GATHER);
     rec.begin(KC_REDUCE);
     launch_reduce(ctx->p, ctx->stream, false, true);
     launch_npt_couple(ctx->p, ctx->stream, dt);
     rec.end(KC_REDUCE);
-    // active plan, kick, step begin, stable plan, 2 pair, gather, reduce (+ NPT apply, couple)
-    *n_kernels = 8 + (ctx->p.npt ? 2 : 0);
+    // active plan, kick (unless fused into the previous gather), step begin, stable plan,
+    // 2 pair, gather, reduce (+ NPT apply, couple)
+    *n_kernels = 8 + (ctx->p.npt ? 2 : 0) - (fuse_prev ? 1 : 0);
     return MD_OK;
 }
 
 // One velocity-Verlet step inside a capture:
 //   kick/drift -> [step begin: series row, rebuild condition] -> IF(rebuild) ->
 //   pair pass -> gather (+ half-kick) -> reduce (series row)
-md_status enqueue_step(md_ctx *ctx, const Recorder &rec, const double *hk, double dt, int *n_kernels)
+// fuse_prev: the previous step's gather already took this step's kick and drift;
+// fuse_next: this step's gather takes the next step's (see launch_gather).
+md_status enqueue_step(md_ctx *ctx, const Recorder &rec, const double *hk, double dt, int *n_kernels,
+                       bool fuse_prev = false, bool fuse_next = false)
 {
     launch_active_plan(ctx->p, ctx->stream);
     rec.begin(KC_KICK_DRIFT);
-    launch_kick_drift(ctx->p, ctx->stream, hk, dt);
+    if (!fuse_prev) launch_kick_drift(ctx->p, ctx->stream, hk, dt);
     launch_npt_apply(ctx->p, ctx->stream);
     rec.end(KC_KICK_DRIFT);
-    if (ctx->p.batch && ctx->p.N > 0) return enqueue_pool_tail(ctx, rec, hk, dt, n_kernels);
+    if (ctx->p.batch && ctx->p.N > 0) return enqueue_pool_tail(ctx, rec, hk, dt, n_kernels, fuse_prev, fuse_next);
     rec.begin(KC_REBUILD);
     if (ctx->p.N > 0) {
         cudaGraphConditionalHandle h;
@@ -467,14 +474,15 @@ md_status enqueue_step(md_ctx *ctx, const Recorder &rec, const double *hk, doubl
     launch_pair(ctx->p, ctx->stream);
     rec.end(KC_PAIR);
     rec.begin(KC_GATHER);
-    launch_gather(ctx->p, ctx->stream, hk, dt, false);
+    launch_gather(ctx->p, ctx->stream, hk, dt, false, fuse_next);
     rec.end(KC_GATHER);
     rec.begin(KC_REDUCE);
     launch_reduce(ctx->p, ctx->stream, false, true);
     launch_npt_couple(ctx->p, ctx->stream, dt);
     rec.end(KC_REDUCE);
     // kernels launched every step; a taken rebuild adds the body's kernels
-    *n_kernels = (ctx->p.N > 0 ? 6 : 2) + (ctx->p.batch ? 1 : 0) + (ctx->p.npt && ctx->p.N > 0 ? 2 : 0);
+    *n_kernels = (ctx->p.N > 0 ? 6 : 2) + (ctx->p.batch ? 1 : 0) + (ctx->p.npt && ctx->p.N > 0 ? 2 : 0) -
+                 (fuse_prev && ctx->p.N > 0 ? 1 : 0);
     return MD_OK;
 }
 
@@ -599,13 +607,21 @@ md_status force_eval(md_ctx *ctx, bool full, bool fresh_only = false)
     return MD_OK;
 }
 
-md_status capture_one(md_ctx *ctx, const double *hk, double dt, int steps, cudaGraphExec_t *out)
+// A graph of `steps` consecutive steps.  Inside it each step's first half-kick and drift
+// run in the previous step's gather (not under NPT, whose scaling comes between them); the
+// graph's first step launches its own kick, so every replay starts and ends on a state with
+// x, v at the same time.  *kernels: kernels of one replay (rebuild bodies not counted).
+md_status capture_one(md_ctx *ctx, const double *hk, double dt, int steps, cudaGraphExec_t *out, int *kernels)
 {
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
     int per_step = 0;
+    *kernels = 0;
+    const bool fusable = !ctx->p.npt && ctx->p.N > 0;
     for (int st = 0; st < steps; ++st) {
-        md_status s = enqueue_step(ctx, Recorder{ctx, st, true}, hk, dt, &per_step);
+        md_status s = enqueue_step(ctx, Recorder{ctx, st, true}, hk, dt, &per_step, fusable && st > 0,
+                                   fusable && st + 1 < steps);
+        *kernels += per_step;
         if (s != MD_OK) {
             cudaStreamEndCapture(ctx->stream, &g);
             if (g) cudaGraphDestroy(g);
@@ -624,9 +640,9 @@ md_status capture_one(md_ctx *ctx, const double *hk, double dt, int steps, cudaG
 md_status capture_graph(md_ctx *ctx, const double *hk, double dt)
 {
     destroy_graph(ctx);
-    md_status s = capture_one(ctx, hk, dt, kStepsPerGraph, &ctx->gexec);
+    md_status s = capture_one(ctx, hk, dt, kStepsPerGraph, &ctx->gexec, &ctx->kernels_g8);
     if (s != MD_OK) return s;
-    s = capture_one(ctx, hk, dt, 1, &ctx->gexec1);
+    s = capture_one(ctx, hk, dt, 1, &ctx->gexec1, &ctx->kernels_g1);
     if (s != MD_OK) return s;
     ctx->g_dt = dt;
     ctx->g_series = ctx->p.series;
@@ -1250,6 +1266,8 @@ md_status md_run(md_ctx *ctx, int64_t n_steps, double dt_fs, double *series)
         for (int64_t done = 0; done < n_steps; ++done) {
             s = eager_step(ctx, hk, dt_fs);
             if (s != MD_OK) return s;
+            ctx->kernels_launched += (ctx->p.N > 0 ? 6 : 2) + (ctx->p.batch ? 1 : 0) +
+                                     (ctx->p.npt && ctx->p.N > 0 ? 2 : 0);
             if (ctx->profiling) {
                 s = accumulate_times(ctx, 1);
                 if (s != MD_OK) return s;
@@ -1264,6 +1282,7 @@ md_status md_run(md_ctx *ctx, int64_t n_steps, double dt_fs, double *series)
         int64_t done = 0;
         while (n_steps - done >= kStepsPerGraph) {
             CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
+            ctx->kernels_launched += ctx->kernels_g8;
             if (ctx->profiling) {
                 s = accumulate_times(ctx, kStepsPerGraph);
                 if (s != MD_OK) return s;
@@ -1272,6 +1291,7 @@ md_status md_run(md_ctx *ctx, int64_t n_steps, double dt_fs, double *series)
         }
         for (; done < n_steps; ++done) {
             CK(cudaGraphLaunch(ctx->gexec1, ctx->stream));
+            ctx->kernels_launched += ctx->kernels_g1;
             if (ctx->profiling) {
                 s = accumulate_times(ctx, 1);
                 if (s != MD_OK) return s;
@@ -1396,6 +1416,7 @@ md_status md_get_stats(md_ctx *ctx, md_stats *out)
     out->pair_deferred = deferred;
     out->device_bytes = ctx->allocated;
     out->atoms_rebuilt = f.atoms_rebuilt;
+    out->kernels_launched = ctx->kernels_launched;
     return MD_OK;
 }
 

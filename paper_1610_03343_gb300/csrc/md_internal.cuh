@@ -179,11 +179,19 @@ struct GatherArgs {
     double *partials;       // per (block, system segment): partials[(b seg_max + seg) NC + c]
     int seg_max;            // system segments a block may hold
     const int *sys_of;      // N: system of each atom (pools)
-    const SysDev *sys;      // system table (pools)
-    double dt;              // time step (damping)
+    SysDev *sys;            // system table (pools)
+    double dt;              // time step (damping, fused kick)
     const int *act_count;   // pools: live chunks (see PairArgs)
     const int *act_chunks;
     Flags *flags;
+    // fused first half of the next step (graph-replayed steps that are followed by another
+    // in the same graph): after the second half-kick, v += hk F, x += v dt and the skin test,
+    // exactly as k_kick_drift would do at the start of the next step
+    int fuse_kick;
+    double *pos;
+    const double *pos_build;
+    float *posf;            // fp32 positions to refresh (SW prefilter), or null
+    float half_skin2;       // single system: (skin/2)^2
 };
 
 // per-block partial sums: U, K, J(3), W(9); a velocity-Verlet step needs the first 5,

@@ -137,7 +137,10 @@ enum { PAIR_FAST = 1, PAIR_DEFERRED = 2, PAIR_BOTH = 3 };
 int launch_pair(const Plan &p, cudaStream_t s, int list = PAIR_ALL, int parts = PAIR_BOTH);
 // Per-atom gather: F_i (Eq. 28), J_i (Eq. 30) and, for a force evaluation, W_i (Eq. 29)
 // and per-atom outputs; optional half-kick (and per-system damping); block partials.
-void launch_gather(const Plan &p, cudaStream_t s, const double *half_kick, double dt, bool full_outputs);
+// fuse_next (a step followed by another in the same graph; not under NPT): also the next
+// step's first half-kick, drift and skin test, so that step launches no k_kick_drift.
+void launch_gather(const Plan &p, cudaStream_t s, const double *half_kick, double dt, bool full_outputs,
+                   bool fuse_next = false);
 int gather_block();
 int gather_blocks(int64_t N);
 // Fixed-order reduction of the gather's block partials into per-system totals (and a

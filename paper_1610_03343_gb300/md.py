@@ -92,7 +92,8 @@ class md_stats(ctypes.Structure):
     _fields_ = [("n_atoms", ctypes.c_int64), ("steps_done", ctypes.c_int64), ("n_rebuilds", ctypes.c_int64),
                 ("max_neigh_seen", ctypes.c_int), ("kernel_launches_per_step", ctypes.c_int),
                 ("kernel_launches_per_rebuild", ctypes.c_int), ("pair_deferred", ctypes.c_int),
-                ("device_bytes", ctypes.c_size_t), ("atoms_rebuilt", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_size_t), ("atoms_rebuilt", ctypes.c_int64),
+                ("kernels_launched", ctypes.c_int64)]
 
 
 class md_npt(ctypes.Structure):
