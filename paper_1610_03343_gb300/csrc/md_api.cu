@@ -403,25 +403,23 @@ md_status add_conditional_rebuild(md_ctx *ctx, cudaGraphConditionalHandle h, cud
 
 // Pools, the rest of a step after the kick: the pair pass of the systems that keep their
 // lists runs while the others are rebuilt, on two branches of the graph:
-//   step begin -> stable plan (sets the rebuild conditional) -+-> pair(stable) -------------+
-//                                                             +-> IF: rebuild, pair(rebuilt) +
+//   step begin -> stable plan -+-> pair(stable) -------------------------------+
+//                              +-> rebuild chain (flagged systems), pair(rebuilt) +
 //   -> deferred atoms' pair pass -> gather (+ half-kick) -> reduce (series row)
-// Each atom's work is the same as on a single branch, so results do not change.
+// Each atom's work is the same as on a single branch, so results do not change.  Some
+// system of a pool rebuilds on most steps, so the chain is launched every step (each of
+// its kernels works on the flagged systems only, and on none when none is flagged) rather
+// than behind a conditional node, whose body's launch cost exceeded the chain's work.
 md_status enqueue_pool_tail(md_ctx *ctx, const Recorder &rec, const double *hk, double dt, int *n_kernels,
                             bool fuse_prev, bool fuse_next)
 {
-    cudaGraphConditionalHandle h;
-    cudaStreamCaptureStatus cs;
-    cudaGraph_t g = nullptr;
-    CK(cudaStreamGetCaptureInfo(ctx->stream, &cs, nullptr, &g, nullptr, nullptr, nullptr));
-    CK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
     launch_step_begin(ctx->p, ctx->stream, nullptr);
-    launch_stable_plan(ctx->p, ctx->stream, &h);
+    launch_stable_plan(ctx->p, ctx->stream, nullptr);
     CK(cudaEventRecord(ctx->ev_fork, ctx->stream));
     CK(cudaStreamWaitEvent(ctx->side2, ctx->ev_fork, 0));
     rec.begin(KC_REBUILD, ctx->side2);
-    md_status s = add_conditional_rebuild(ctx, h, ctx->side2, true);
-    if (s != MD_OK) return s;
+    const int n_rebuild = launch_rebuild(ctx->p, ctx->side2) + launch_pair(ctx->p, ctx->side2, PAIR_REBUILT, PAIR_FAST);
+    ctx->kernels_per_rebuild = 0;   // launched every step, counted below
     rec.end(KC_REBUILD, ctx->side2);
     rec.begin(KC_PAIR);
     launch_pair(ctx->p, ctx->stream, PAIR_STABLE, PAIR_FAST);
@@ -437,8 +435,8 @@ md_status enqueue_pool_tail(md_ctx *ctx, const Recorder &rec, const double *hk, 
     launch_npt_couple(ctx->p, ctx->stream, dt);
     rec.end(KC_REDUCE);
     // active plan, kick (unless fused into the previous gather), step begin, stable plan,
-    // 2 pair, gather, reduce (+ NPT apply, couple)
-    *n_kernels = 8 + (ctx->p.npt ? 2 : 0) - (fuse_prev ? 1 : 0);
+    // 2 pair, gather, reduce (+ NPT apply, couple), the rebuild chain
+    *n_kernels = 8 + (ctx->p.npt ? 2 : 0) - (fuse_prev ? 1 : 0) + n_rebuild;
     return MD_OK;
 }
 
@@ -630,7 +628,9 @@ md_status capture_one(md_ctx *ctx, const double *hk, double dt, int steps, cudaG
     }
     cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(out, g, 0);
+    // honour the node priorities captured from the streams (the rebuild branch of a pool step
+    // runs on a high-priority stream so that its short kernels go ahead of the pair pass)
+    e = cudaGraphInstantiateWithFlags(out, g, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
     ctx->kernels_per_step = per_step;

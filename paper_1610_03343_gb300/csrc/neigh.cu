@@ -375,7 +375,7 @@ __global__ void k_build_rev(int64_t N, const int *nn, const int *nl, uint8_t *re
 //   chunks[k] = first atom of chunk k; rsys[k] = k-th system to rebuild.
 constexpr int kChunk = 128;
 __global__ void __launch_bounds__(1024) k_rebuild_plan(int n_sys, const SysDev *sys, int *plan, int *rsys,
-                                                       int *chunks)
+                                                       int *chunks, Flags *flags)
 {
     __shared__ int warp_a[32], warp_b[32];
     __shared__ int carry_a, carry_b;
@@ -420,6 +420,7 @@ __global__ void __launch_bounds__(1024) k_rebuild_plan(int n_sys, const SysDev *
     if (threadIdx.x == 0) {
         plan[0] = carry_b;
         plan[1] = carry_a;
+        if (carry_a > 0) flags->max_nn = 0;   // the longest list of this build
     }
 }
 
@@ -524,9 +525,10 @@ __global__ void __launch_bounds__(kChunk) k_build_rev_pool(const int *plan, cons
 }
 
 // Clear the rebuild requests (pools: every system's, then the global one).  The build
-// positions are now the wrapped positions: no box scaling since the build (NPT).
+// positions are now the wrapped positions: no box scaling since the build (NPT).  Pools
+// count a build only when the plan held a system (their chain runs every step).
 template <bool BATCH>
-__global__ void k_build_done(int n_sys, int64_t n_atoms, SysDev *sys, Flags *flags)
+__global__ void k_build_done(int n_sys, int64_t n_atoms, SysDev *sys, Flags *flags, const int *plan)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (BATCH && s < n_sys && sys[s].rebuild) {
@@ -541,7 +543,7 @@ __global__ void k_build_done(int n_sys, int64_t n_atoms, SysDev *sys, Flags *fla
             sys[0].npt.mu_cum[0] = sys[0].npt.mu_cum[1] = sys[0].npt.mu_cum[2] = 1.0;
         }
         flags->rebuild = 0;
-        flags->n_rebuilds += 1;
+        if (!BATCH || plan[1] > 0) flags->n_rebuilds += 1;
     }
 }
 
@@ -627,7 +629,7 @@ int rebuild_single(const Plan &p, cudaStream_t s)
                                                    p.atom_cell, p.cell_start, p.cell_count, p.cell_atoms,
                                                    rlm * rlm, p.cap, p.nn, p.nl, p.pos_build, p.flags);
     k_build_rev<<<blocks_for(p.N, T), T, 0, s>>>(p.N, p.nn, p.nl, p.rev, p.flags);
-    k_build_done<false><<<1, 1, 0, s>>>(p.n_sys, p.N, p.sys, p.flags);
+    k_build_done<false><<<1, 1, 0, s>>>(p.n_sys, p.N, p.sys, p.flags, nullptr);
     return 8;
 }
 
@@ -636,8 +638,7 @@ int rebuild_pool(const Plan &p, cudaStream_t s)
     // grids bounded by the work a rebuild can have: loop over the listed chunks/systems
     const unsigned gc = (unsigned)std::min<int64_t>((p.N + kChunk - 1) / kChunk, 8 * 152);
     const unsigned gs = (unsigned)std::min<int64_t>(p.n_sys, 4 * 152);
-    cudaMemsetAsync(&p.flags->max_nn, 0, sizeof(int), s);
-    k_rebuild_plan<<<1, 1024, 0, s>>>(p.n_sys, p.sys, p.rb_plan, p.rb_sys, p.rb_chunks);
+    k_rebuild_plan<<<1, 1024, 0, s>>>(p.n_sys, p.sys, p.rb_plan, p.rb_sys, p.rb_chunks, p.flags);
     k_cells_clear_pool<<<gs, 256, 0, s>>>(p.rb_plan, p.rb_sys, p.sys, p.cell_count);
     k_cell_count_pool<<<gc, kChunk, 0, s>>>(p.rb_plan, p.rb_chunks, p.N, p.pos, p.posf, p.sys_of, p.sys,
                                             p.atom_cell, p.atom_rank, p.cell_count);
@@ -649,7 +650,7 @@ int rebuild_pool(const Plan &p, cudaStream_t s)
                                             p.nl, p.pos_build, p.flags);
     k_build_rev_pool<<<gc, kChunk, 0, s>>>(p.rb_plan, p.rb_chunks, p.N, p.nn, p.nl, p.rev, p.sys_of, p.sys,
                                            p.flags);
-    k_build_done<true><<<blocks_for(p.n_sys, 256), 256, 0, s>>>(p.n_sys, p.N, p.sys, p.flags);
+    k_build_done<true><<<blocks_for(p.n_sys, 256), 256, 0, s>>>(p.n_sys, p.N, p.sys, p.flags, p.rb_plan);
     return 8;
 }
 
