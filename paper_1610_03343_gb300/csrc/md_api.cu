@@ -986,6 +986,8 @@ md_status md_batch_create(md_ctx **out, int64_t atom_capacity, int max_systems, 
         }
     }
     ctx->sys_used.assign((size_t)max_systems, 0);
+    // cell counts start at zero; every rebuild zeroes the counts it used
+    cudaMemsetAsync(p.cell_count, 0, sizeof(int) * (size_t)p.ncell, ctx->stream);
     ctx->atoms_free.init(cap_atoms);
     ctx->cells_free.init(ctx->cell_capacity);
     // every atom starts free: it belongs to the inactive sentinel system max_systems

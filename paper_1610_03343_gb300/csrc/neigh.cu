@@ -420,17 +420,11 @@ __global__ void __launch_bounds__(1024) k_rebuild_plan(int n_sys, const SysDev *
     if (threadIdx.x == 0) {
         plan[0] = carry_b;
         plan[1] = carry_a;
-        if (carry_a > 0) flags->max_nn = 0;   // the longest list of this build
-    }
-}
-
-// Zero the cell counts of the systems being rebuilt (one system per block iteration).
-__global__ void k_cells_clear_pool(const int *plan, const int *rsys, const SysDev *sys, int *count)
-{
-    for (int k = blockIdx.x; k < plan[1]; k += gridDim.x) {
-        const SysDev &sd = sys[rsys[k]];
-        const long long nc = (long long)sd.nc[0] * sd.nc[1] * sd.nc[2];
-        for (long long c = threadIdx.x; c < nc; c += blockDim.x) count[sd.cell_off + c] = 0;
+        flags->rebuild = 0;                   // the requests are taken by this plan
+        if (carry_a > 0) {
+            flags->max_nn = 0;                // the longest list of this build
+            flags->n_rebuilds += 1;
+        }
     }
 }
 
@@ -516,34 +510,27 @@ __global__ void __launch_bounds__(kChunk) k_build_list_pool(const int *plan, con
         build_list_atom<true>(chunks[k] + threadIdx.x, N, pos, posf, Box{}, 1, 1, 1, sys_of, sys, atom_cell,
                               cell_start, cell_count, cell_atoms, 0.f, cap, nn, nl, pos_build, flags);
 }
+// Reverse slots of the rebuilt systems' atoms (their chunks only; padding atoms belong to the
+// inactive sentinel, which has no atoms), then the rest of the build: every atom zeroes its
+// cell's count (so the next build needs no clearing pass; every other cell is already zero)
+// and the first atom of each system clears its request and marks it built.
 __global__ void __launch_bounds__(kChunk) k_build_rev_pool(const int *plan, const int *chunks, int64_t N,
                                                            const int *nn, const int *nl, uint8_t *rev,
-                                                           const int *sys_of, const SysDev *sys, Flags *flags)
+                                                           const int *sys_of, SysDev *sys, const int *atom_cell,
+                                                           int *count, Flags *flags)
 {
-    for (int k = blockIdx.x; k < plan[0]; k += gridDim.x)
-        build_rev_atom<true>(chunks[k] + threadIdx.x, N, nn, nl, rev, sys_of, sys, flags);
-}
-
-// Clear the rebuild requests (pools: every system's, then the global one).  The build
-// positions are now the wrapped positions: no box scaling since the build (NPT).  Pools
-// count a build only when the plan held a system (their chain runs every step).
-template <bool BATCH>
-__global__ void k_build_done(int n_sys, int64_t n_atoms, SysDev *sys, Flags *flags, const int *plan)
-{
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (BATCH && s < n_sys && sys[s].rebuild) {
-        sys[s].rebuild = 0;
-        sys[s].built = 1;
-        sys[s].npt.mu_cum[0] = sys[s].npt.mu_cum[1] = sys[s].npt.mu_cum[2] = 1.0;
-        atomicAdd(reinterpret_cast<unsigned long long *>(&flags->atoms_rebuilt), (unsigned long long)sys[s].n_atoms);
-    }
-    if (s == 0) {
-        if (!BATCH) {
-            flags->atoms_rebuilt += n_atoms;
-            sys[0].npt.mu_cum[0] = sys[0].npt.mu_cum[1] = sys[0].npt.mu_cum[2] = 1.0;
+    for (int k = blockIdx.x; k < plan[0]; k += gridDim.x) {
+        const int64_t i = chunks[k] + threadIdx.x;
+        SysDev &sd = sys[sys_of[i]];
+        if (i - sd.atom_start >= sd.n_atoms) continue;
+        build_rev_atom<false>(i, N, nn, nl, rev, nullptr, nullptr, flags);
+        count[atom_cell[i]] = 0;
+        if (i == sd.atom_start) {
+            sd.rebuild = 0;
+            sd.built = 1;
+            sd.npt.mu_cum[0] = sd.npt.mu_cum[1] = sd.npt.mu_cum[2] = 1.0;
+            atomicAdd(reinterpret_cast<unsigned long long *>(&flags->atoms_rebuilt), (unsigned long long)sd.n_atoms);
         }
-        flags->rebuild = 0;
-        if (!BATCH || plan[1] > 0) flags->n_rebuilds += 1;
     }
 }
 
@@ -594,6 +581,16 @@ __global__ void k_wrap_copy(int64_t N, int64_t a0, int64_t n, const double *pos,
     }
 }
 
+// Single system: clear the rebuild request and count the build.  The build positions are
+// now the wrapped positions: no box scaling since the build (NPT).
+__global__ void k_build_done(int64_t n_atoms, SysDev *sys, Flags *flags)
+{
+    flags->atoms_rebuilt += n_atoms;
+    sys[0].npt.mu_cum[0] = sys[0].npt.mu_cum[1] = sys[0].npt.mu_cum[2] = 1.0;
+    flags->rebuild = 0;
+    flags->n_rebuilds += 1;
+}
+
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
@@ -629,7 +626,7 @@ int rebuild_single(const Plan &p, cudaStream_t s)
                                                    p.atom_cell, p.cell_start, p.cell_count, p.cell_atoms,
                                                    rlm * rlm, p.cap, p.nn, p.nl, p.pos_build, p.flags);
     k_build_rev<<<blocks_for(p.N, T), T, 0, s>>>(p.N, p.nn, p.nl, p.rev, p.flags);
-    k_build_done<false><<<1, 1, 0, s>>>(p.n_sys, p.N, p.sys, p.flags, nullptr);
+    k_build_done<<<1, 1, 0, s>>>(p.N, p.sys, p.flags);
     return 8;
 }
 
@@ -639,7 +636,6 @@ int rebuild_pool(const Plan &p, cudaStream_t s)
     const unsigned gc = (unsigned)std::min<int64_t>((p.N + kChunk - 1) / kChunk, 8 * 152);
     const unsigned gs = (unsigned)std::min<int64_t>(p.n_sys, 4 * 152);
     k_rebuild_plan<<<1, 1024, 0, s>>>(p.n_sys, p.sys, p.rb_plan, p.rb_sys, p.rb_chunks, p.flags);
-    k_cells_clear_pool<<<gs, 256, 0, s>>>(p.rb_plan, p.rb_sys, p.sys, p.cell_count);
     k_cell_count_pool<<<gc, kChunk, 0, s>>>(p.rb_plan, p.rb_chunks, p.N, p.pos, p.posf, p.sys_of, p.sys,
                                             p.atom_cell, p.atom_rank, p.cell_count);
     k_cells_scan_pool<<<gs, kPoolScanThreads, 0, s>>>(p.rb_plan, p.rb_sys, p.sys, p.cell_count, p.cell_start);
@@ -649,9 +645,8 @@ int rebuild_pool(const Plan &p, cudaStream_t s)
                                             p.atom_cell, p.cell_start, p.cell_count, p.cell_atoms, p.cap, p.nn,
                                             p.nl, p.pos_build, p.flags);
     k_build_rev_pool<<<gc, kChunk, 0, s>>>(p.rb_plan, p.rb_chunks, p.N, p.nn, p.nl, p.rev, p.sys_of, p.sys,
-                                           p.flags);
-    k_build_done<true><<<blocks_for(p.n_sys, 256), 256, 0, s>>>(p.n_sys, p.N, p.sys, p.flags, p.rb_plan);
-    return 8;
+                                           p.atom_cell, p.cell_count, p.flags);
+    return 6;
 }
 
 int launch_rebuild(const Plan &p, cudaStream_t s)
