@@ -774,6 +774,7 @@ template <typename T, int MAXA, int BLOCK, bool FULL, bool BATCH, bool NPT>
 __global__ void __launch_bounds__(BLOCK) k_gather(GatherArgs<T> a)
 {
     static_assert(BLOCK == kPoolChunk, "a gather block is one pool chunk");
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.flags->row_reduce = a.flags->row;
     if (BATCH) {
         const int nch = *a.act_count;
         for (int k = blockIdx.x; k < nch; k += gridDim.x) {
@@ -838,7 +839,7 @@ k_reduce(const double *partials, int nc, int seg_max, int64_t N, int block, cons
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
         if (nc == kNptPartials && c >= kStepPartials) npt_totals[(int64_t)s * kNptExtra + c - kStepPartials] = t;
         else totals[(int64_t)s * kNumPartials + c] = t;
-        if (record && c < kStepPartials) series[(flags->row * n_sys + s) * kStepPartials + c] = t;
+        if (record && c < kStepPartials) series[(flags->row_reduce * n_sys + s) * kStepPartials + c] = t;
         if (BATCH && record && c == 0 && sys[s].steps_left > 0) {
             sys[s].steps_left -= 1;
             if (sys[s].steps_left == 0) sys[s].active = 0;

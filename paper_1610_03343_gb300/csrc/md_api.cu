@@ -85,6 +85,7 @@ struct md_ctx {
     cudaStream_t side = nullptr;   // stream used to capture conditional bodies
     cudaStream_t side2 = nullptr;  // pools: second branch of the step graph (rebuild)
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_red = nullptr;  // single systems: a step's reduction, on the side branch
     bool use_graphs = true;        // false: eager launches, rebuild decided on the host
     // profiling
     bool profiling = false;
@@ -445,8 +446,13 @@ md_status enqueue_pool_tail(md_ctx *ctx, const Recorder &rec, const double *hk, 
 //   pair pass -> gather (+ half-kick) -> reduce (series row)
 // fuse_prev: the previous step's gather already took this step's kick and drift;
 // fuse_next: this step's gather takes the next step's (see launch_gather).
+// Single systems: when another step follows in the graph (and not under NPT, whose coupling
+// needs the totals before the next kick), the step's reduction runs on a side branch beside
+// the next step's step-begin, rebuild and pair pass; *reduce_pending tells the next step to
+// join it before its gather, which overwrites the block partials.  The reduction takes its
+// series row from flags->row_reduce, which the gather sets, so the next step-begin may move on.
 md_status enqueue_step(md_ctx *ctx, const Recorder &rec, const double *hk, double dt, int *n_kernels,
-                       bool fuse_prev = false, bool fuse_next = false)
+                       bool fuse_prev = false, bool fuse_next = false, bool *reduce_pending = nullptr)
 {
     launch_active_plan(ctx->p, ctx->stream);
     rec.begin(KC_KICK_DRIFT);
@@ -471,13 +477,27 @@ md_status enqueue_step(md_ctx *ctx, const Recorder &rec, const double *hk, doubl
     rec.begin(KC_PAIR);
     launch_pair(ctx->p, ctx->stream);
     rec.end(KC_PAIR);
+    if (reduce_pending && *reduce_pending) {
+        CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_red, 0));
+        *reduce_pending = false;
+    }
     rec.begin(KC_GATHER);
     launch_gather(ctx->p, ctx->stream, hk, dt, false, fuse_next);
     rec.end(KC_GATHER);
-    rec.begin(KC_REDUCE);
-    launch_reduce(ctx->p, ctx->stream, false, true);
-    launch_npt_couple(ctx->p, ctx->stream, dt);
-    rec.end(KC_REDUCE);
+    if (reduce_pending && fuse_next && !ctx->p.npt && ctx->p.N > 0) {
+        CK(cudaEventRecord(ctx->ev_fork, ctx->stream));
+        CK(cudaStreamWaitEvent(ctx->side2, ctx->ev_fork, 0));
+        rec.begin(KC_REDUCE, ctx->side2);
+        launch_reduce(ctx->p, ctx->side2, false, true);
+        rec.end(KC_REDUCE, ctx->side2);
+        CK(cudaEventRecord(ctx->ev_red, ctx->side2));
+        *reduce_pending = true;
+    } else {
+        rec.begin(KC_REDUCE);
+        launch_reduce(ctx->p, ctx->stream, false, true);
+        launch_npt_couple(ctx->p, ctx->stream, dt);
+        rec.end(KC_REDUCE);
+    }
     // kernels launched every step; a taken rebuild adds the body's kernels
     *n_kernels = (ctx->p.N > 0 ? 6 : 2) + (ctx->p.batch ? 1 : 0) + (ctx->p.npt && ctx->p.N > 0 ? 2 : 0) -
                  (fuse_prev && ctx->p.N > 0 ? 1 : 0);
@@ -616,9 +636,10 @@ md_status capture_one(md_ctx *ctx, const double *hk, double dt, int steps, cudaG
     int per_step = 0;
     *kernels = 0;
     const bool fusable = !ctx->p.npt && ctx->p.N > 0;
+    bool reduce_pending = false;
     for (int st = 0; st < steps; ++st) {
         md_status s = enqueue_step(ctx, Recorder{ctx, st, true}, hk, dt, &per_step, fusable && st > 0,
-                                   fusable && st + 1 < steps);
+                                   fusable && st + 1 < steps, ctx->p.batch ? nullptr : &reduce_pending);
         *kernels += per_step;
         if (s != MD_OK) {
             cudaStreamEndCapture(ctx->stream, &g);
@@ -705,6 +726,7 @@ md_status ctx_init(md_ctx *ctx, const md_options &opt)
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&ctx->side2, cudaStreamNonBlocking, prio_greatest);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_red, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return MD_ERR_CUDA;
@@ -1605,6 +1627,7 @@ void md_destroy(md_ctx *ctx)
     if (ctx->side2) cudaStreamDestroy(ctx->side2);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+    if (ctx->ev_red) cudaEventDestroy(ctx->ev_red);
     delete ctx;
 }
 

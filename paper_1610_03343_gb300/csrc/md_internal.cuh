@@ -97,6 +97,8 @@ struct Flags {
     int fresh_only;       // pools: the force evaluation in flight covers admitted systems only
     int pad2;
     long long atoms_rebuilt;   // atoms whose list was built, summed over builds
+    long long row_reduce;      // series row of the last gather's partials (the reduction of a
+                               // step may run beside the next step's first kernels)
 };
 
 // Pools: does atom work of system `sd` run now?  Stopped systems never; during the
