@@ -421,11 +421,13 @@ md_status md_hcacf(const double *j, int64_t n_rows, int64_t row_stride, int64_t 
                    double volume, double temperature, double *acf, double *kappa, int io,
                    void *cuda_stream);
 
-/* Diagnostics for accuracy tests: evaluates, on the current CUDA device, the table-driven
- * fp64 exponential (fn = 0) or logarithm (fn = 1) that the Tersoff pair pass uses in place
- * of the CUDA math library (P. T. P. Tang's table-driven method; exp within 2 ulp for
+/* Diagnostics for accuracy tests: evaluates, on the current CUDA device, the fp64 routines
+ * that the pair passes use in place of the CUDA math library: the table-driven exponential
+ * (fn = 0) or logarithm (fn = 1) (P. T. P. Tang's table-driven method; exp within 2 ulp for
  * |x| <= 708, log to about 1e-16 (1 + |binary exponent of x|) absolute for positive normal
- * x).  x, y: n host doubles.  Returns 0, -1 for bad arguments, -5 on a CUDA error.
+ * x), or the reciprocal (fn = 2: fp32 seed and two Newton steps, within 1 ulp for
+ * 1.2e-38 < |x| < 8.5e37).  x, y: n host doubles.  Returns 0, -1 for bad arguments, -5 on
+ * a CUDA error.
  * Allocates and frees its own device scratch. */
 int md_fastmath_eval(int fn, int64_t n, const double *x, double *y);
 

@@ -22,6 +22,7 @@
 #pragma once
 
 #include "fastmath_tables.cuh"
+#include "md_internal.cuh"
 
 namespace mdk {
 
@@ -56,6 +57,24 @@ __device__ __forceinline__ double log_tab(double x)
     const double p = fma(q, r * r, r);                   // log(1 + r)
     const double ed = (double)e;
     return fma(ed, kLn2Hi, __ldg(&kLogTab[j]) + fma(ed, kLn2Lo, p));
+}
+
+// 1/x for 1.2e-38 < |x| < 8.5e37 (x and 1/x normal in fp32): an fp32 seed
+// (rcp.approx on the value truncated to fp32 with integer instructions, relative error
+// below 2^-21), then two Newton steps y <- y + y (1 - x y), each squaring the relative error
+// (below 2^-84 before rounding): four fp64 FMAs, within 1 ulp.  Used for the Tersoff
+// angular denominator d^2 + (h - cos)^2, zeta (1 + (beta zeta)^n) and the SW 1/(r - a sigma)
+// (whose magnitude is at least 1/(a sigma) and at most 1/(fp64 rounding of r - a sigma)).
+__device__ __forceinline__ double rcp_nr(double x)
+{
+    const float xf = d2f_trunc(x);
+    float yf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(xf));
+    double y = f2d_int(yf);
+    double e = fma(-x, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-x, y, 1.0);
+    return fma(y, e, y);
 }
 
 }  // namespace mdk

@@ -51,6 +51,7 @@ template <> struct M<double> {
     // SW: exp(sigma/(r - a sigma)) and exp(gamma sigma/(r - a sigma)) go to -infinity at the
     // cutoff; below -700 the factor is < 1e-304 and is taken as e^-700
     static __device__ __forceinline__ double sexp_(double x) { return exp_tab(fmax(x, -700.0)); }
+    static __device__ __forceinline__ double rcp_(double x) { return rcp_nr(x); }
     static __device__ __forceinline__ void sincos_(double x, double *s, double *c) { sincos(x, s, c); }
     static __device__ __forceinline__ double pow_(double x, double y) { return pow(x, y); }
 };
@@ -63,6 +64,7 @@ template <> struct M<float> {
     static __device__ __forceinline__ float tlog_(float x) { return logf(x); }
     static __device__ __forceinline__ float tlog1p_(float x) { return log1pf(x); }
     static __device__ __forceinline__ float sexp_(float x) { return expf(x); }
+    static __device__ __forceinline__ float rcp_(float x) { return 1.0f / x; }
     static __device__ __forceinline__ void sincos_(float x, float *s, float *c) { sincosf(x, s, c); }
     static __device__ __forceinline__ float pow_(float x, float y) { return powf(x, y); }
 };
@@ -244,7 +246,7 @@ template <typename T>
 __device__ __forceinline__ T tersoff_inv_den(const TersoffC<T> &p, T cs)
 {
     const T hc = p.h - cs;
-    return T(1) / (p.d2 + hc * hc);
+    return M<T>::rcp_(p.d2 + hc * hc);
 }
 template <typename T>
 __device__ __forceinline__ void tersoff_g(const TersoffC<T> &p, T cs, T inv, T &g, T &dg)
@@ -266,7 +268,7 @@ __device__ __forceinline__ void tersoff_b(const TersoffC<T> &p, T zeta, T &b, T 
     }
     const T x = M<T>::texp_(p.n * (M<T>::tlog_(zeta) + p.ln_beta));
     b = M<T>::texp_(-p.inv2n * M<T>::tlog1p_(x));
-    db = T(-0.5) * b * x / (zeta * (T(1) + x));
+    db = T(-0.5) * b * x * M<T>::rcp_(zeta * (T(1) + x));
 }
 
 // index of the unordered bond pair (j, k), j < k
@@ -412,7 +414,7 @@ __device__ __forceinline__ void sw_atom(const PairArgs<T> &a, const SWC<T> &p, c
         const T r = r2 * ir;
         const T ux = S(SW_UX, k) * ir, uy = S(SW_UY, k) * ir, uz = S(SW_UZ, k) * ir;
         S(SW_UX, k) = ux; S(SW_UY, k) = uy; S(SW_UZ, k) = uz; S(SW_IR, k) = ir;
-        const T irc = T(1) / (r - p.rc);                 // 1/(r - a sigma) < 0
+        const T irc = M<T>::rcp_(r - p.rc);              // 1/(r - a sigma) < 0
         const T e2 = M<T>::sexp_(p.sig * irc);
         const T E = M<T>::sexp_(p.gamsig * irc);
         S(SW_E, k) = E;
@@ -1171,7 +1173,7 @@ namespace {
 __global__ void k_fastmath_eval(int fn, int64_t n, const double *x, double *y)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) y[i] = fn == 0 ? exp_tab(x[i]) : log_tab(x[i]);
+    if (i < n) y[i] = fn == 0 ? exp_tab(x[i]) : (fn == 1 ? log_tab(x[i]) : rcp_nr(x[i]));
 }
 }  // namespace
 
@@ -1330,12 +1332,13 @@ int gather_blocks(int64_t N) { return N == 0 ? 1 : (int)blocks_for(N, kGatherBlo
 
 }  // namespace mdk
 
-// Diagnostics: the pair pass's table-driven fp64 exp (fn 0) or log (fn 1) of n host values
+// Diagnostics: the pair pass's table-driven fp64 exp (fn 0), log (fn 1) or Newton reciprocal
+// (fn 2) of n host values
 // on the current device (accuracy tests).  Returns 0, -1 for bad arguments, -5 on a CUDA
 // error.
 extern "C" int md_fastmath_eval(int fn, int64_t n, const double *x, double *y)
 {
-    if ((fn != 0 && fn != 1) || n < 0 || (n > 0 && (!x || !y))) return -1;
+    if (fn < 0 || fn > 2 || n < 0 || (n > 0 && (!x || !y))) return -1;
     if (n == 0) return 0;
     double *d = nullptr;
     if (cudaMalloc(&d, sizeof(double) * 2 * (size_t)n) != cudaSuccess) {

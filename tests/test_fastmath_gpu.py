@@ -1,7 +1,8 @@
-"""The table-driven fp64 exp and log of the Tersoff pair pass (fastmath.cuh, Tang's
-method) against numpy's libm on the host: exp within 2 ulp over the pair pass's domain and
-beyond, log within an absolute 2e-16 (1 + |binary exponent|), including the table and
-interval boundaries, powers of two, values next to 1 and subnormal-free extremes."""
+"""The fp64 routines of the pair passes (fastmath.cuh) against numpy on the host: the
+table-driven exp (Tang's method) within 2 ulp over the pair pass's domain and beyond, the
+table-driven log within an absolute 2e-16 (1 + |binary exponent|), the Newton reciprocal
+within 1 ulp (of the correctly rounded 1/x) for 1.2e-38 < |x| < 8.5e37, including table and interval
+boundaries, powers of two, values next to 1 and the range ends."""
 import numpy as np
 import pytest
 
@@ -60,3 +61,18 @@ def test_log_absolute_error(md):
     err = np.abs(y - ref)
     assert np.all(err <= bound), (x[np.argmax(err / bound)], (err / bound).max())
     assert y[-6] == 0.0 or abs(y[-6]) < 1e-17            # log(1) ~ 0
+
+
+def test_reciprocal_within_one_ulp(md):
+    rng = np.random.Generator(np.random.PCG64(3))
+    x = np.concatenate([
+        rng.uniform(18.0, 300.0, 200000),                  # d^2 + (h - cos)^2
+        np.exp(rng.uniform(-70.0, 30.0, 400000)),          # zeta (1 + (beta zeta)^n)
+        -np.exp(rng.uniform(-36.0, 1.4, 200000)),          # SW r - a sigma < 0
+        2.0 ** np.arange(-125, 127, dtype=np.float64),
+        np.nextafter(2.0 ** np.arange(-125, 127, dtype=np.float64), 0.0),
+        [1.0, 3.0, 1.2e-38, 8.0e37, -1.0, 7.0],
+    ])
+    y = md.md_fastmath_eval(2, x)
+    e = ulp_err(y, 1.0 / x)
+    assert e.max() <= 1.0, (x[np.argmax(e)], e.max())
