@@ -639,6 +639,7 @@ __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, i
 {
     constexpr int NC = FULL ? kNumPartials : (NPT ? kNptPartials : kStepPartials);
     constexpr bool WDIAG = NPT && !FULL;
+    constexpr bool JPASS = sizeof(T) == 8;   // heat current by a second walk over the bonds
     const int64_t N = a.N;
     double vals[NC];
 #pragma unroll
@@ -689,9 +690,11 @@ __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, i
                     w[6] += rz * gx; w[7] += rz * gy; w[8] += rz * gz;
                 }
                 if (WDIAG) { wd0 += rx * gx; wd1 += ry * gy; wd2 += rz * gz; }
-                mj[0] += rx * ex; mj[1] += rx * ey; mj[2] += rx * ez;
-                mj[3] += ry * ex; mj[4] += ry * ey; mj[5] += ry * ez;
-                mj[6] += rz * ex; mj[7] += rz * ey; mj[8] += rz * ez;
+                if (!JPASS) {
+                    mj[0] += rx * ex; mj[1] += rx * ey; mj[2] += rx * ez;
+                    mj[3] += ry * ex; mj[4] += ry * ey; mj[5] += ry * ez;
+                    mj[6] += rz * ex; mj[7] += rz * ey; mj[8] += rz * ez;
+                }
             }
             ++k;
         }
@@ -732,12 +735,37 @@ __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, i
             a.vel[N + i] = vn[1];
             a.vel[2 * N + i] = vn[2];
         }
-        // J_i = M_i . v_i and K_i = m v^2 / 2 in T (the fp32 per-atom value of the mixed
-        // path feeds an fp64 total)
+        // J_i (Eq. 30) with v_i after the half-kick, and K_i = m v^2 / 2, in T (the fp32
+        // per-atom value of the mixed path feeds an fp64 total).  fp64: a second walk over
+        // the bonds, J_i = sum_j r_ij (d_ji . v_i), 6 FMAs per bond (the loads hit the cache;
+        // the fp64 pipe is the bound); fp32: J_i = M_i . v_i from the first walk.
         const T vx = to_t<T>(v[0]), vy = to_t<T>(v[1]), vz = to_t<T>(v[2]);
-        const T J0 = mj[0] * vx + mj[1] * vy + mj[2] * vz;
-        const T J1 = mj[3] * vx + mj[4] * vy + mj[5] * vz;
-        const T J2 = mj[6] * vx + mj[7] * vy + mj[8] * vz;
+        T J0, J1, J2;
+        if (JPASS) {
+            J0 = J1 = J2 = T(0);
+            uint32_t m2 = a.mask[i];
+            int k2 = 0;
+            while (m2 != 0u && k2 < MAXA) {
+                const int m = __ffs(m2) - 1;
+                m2 &= m2 - 1u;
+                const int j = list_atom(a.nl[(int64_t)m * N + i]);
+                const int mr = a.rev[(int64_t)m * N + i];
+                const int kr = __popc(a.mask[j] & ((1u << mr) - 1u));
+                if (kr < MAXA) {
+                    const T ex = a.d[(int64_t)(0 * MAXA + kr) * N + j], ey = a.d[(int64_t)(1 * MAXA + kr) * N + j],
+                            ez = a.d[(int64_t)(2 * MAXA + kr) * N + j];
+                    const T rx = a.r[(int64_t)(0 * MAXA + k2) * N + i], ry = a.r[(int64_t)(1 * MAXA + k2) * N + i],
+                            rz = a.r[(int64_t)(2 * MAXA + k2) * N + i];
+                    const T dv = ex * vx + ey * vy + ez * vz;
+                    J0 += rx * dv; J1 += ry * dv; J2 += rz * dv;
+                }
+                ++k2;
+            }
+        } else {
+            J0 = mj[0] * vx + mj[1] * vy + mj[2] * vz;
+            J1 = mj[3] * vx + mj[4] * vy + mj[5] * vz;
+            J2 = mj[6] * vx + mj[7] * vy + mj[8] * vz;
+        }
         const T hm = a.hm[t];
         const T ke = hm * (vx * vx + vy * vy + vz * vz);
         vals[0] = a.u[i];
