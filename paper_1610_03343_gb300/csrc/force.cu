@@ -639,7 +639,6 @@ __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, i
 {
     constexpr int NC = FULL ? kNumPartials : (NPT ? kNptPartials : kStepPartials);
     constexpr bool WDIAG = NPT && !FULL;
-    constexpr bool JPASS = sizeof(T) == 8;   // heat current by a second walk over the bonds
     const int64_t N = a.N;
     double vals[NC];
 #pragma unroll
@@ -663,10 +662,10 @@ __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, i
     if (live) {
         uint32_t mask = a.mask[i];
         T f0 = 0, f1 = 0, f2 = 0;
-        T w[9], mj[9];
+        T w[9];
         T wd0 = 0, wd1 = 0, wd2 = 0;
 #pragma unroll
-        for (int c = 0; c < 9; ++c) { w[c] = 0; mj[c] = 0; }
+        for (int c = 0; c < 9; ++c) w[c] = 0;
         int k = 0;
         while (mask != 0u && k < MAXA) {
             const int m = __ffs(mask) - 1;
@@ -690,11 +689,6 @@ __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, i
                     w[6] += rz * gx; w[7] += rz * gy; w[8] += rz * gz;
                 }
                 if (WDIAG) { wd0 += rx * gx; wd1 += ry * gy; wd2 += rz * gz; }
-                if (!JPASS) {
-                    mj[0] += rx * ex; mj[1] += rx * ey; mj[2] += rx * ez;
-                    mj[3] += ry * ex; mj[4] += ry * ey; mj[5] += ry * ez;
-                    mj[6] += rz * ex; mj[7] += rz * ey; mj[8] += rz * ez;
-                }
             }
             ++k;
         }
@@ -736,13 +730,13 @@ __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, i
             a.vel[2 * N + i] = vn[2];
         }
         // J_i (Eq. 30) with v_i after the half-kick, and K_i = m v^2 / 2, in T (the fp32
-        // per-atom value of the mixed path feeds an fp64 total).  fp64: a second walk over
-        // the bonds, J_i = sum_j r_ij (d_ji . v_i), 6 FMAs per bond (the loads hit the cache;
-        // the fp64 pipe is the bound); fp32: J_i = M_i . v_i from the first walk.
+        // per-atom value of the mixed path feeds an fp64 total): a second walk over the bonds,
+        // J_i = sum_j r_ij (d_ji . v_i), 6 FMAs per bond (its loads hit the cache), instead
+        // of accumulating the 3x3 tensor sum_j r_ij (x) d_ji in the first walk (9 per bond,
+        // 9 more registers).
         const T vx = to_t<T>(v[0]), vy = to_t<T>(v[1]), vz = to_t<T>(v[2]);
-        T J0, J1, J2;
-        if (JPASS) {
-            J0 = J1 = J2 = T(0);
+        T J0 = T(0), J1 = T(0), J2 = T(0);
+        {
             uint32_t m2 = a.mask[i];
             int k2 = 0;
             while (m2 != 0u && k2 < MAXA) {
@@ -761,10 +755,6 @@ __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, i
                 }
                 ++k2;
             }
-        } else {
-            J0 = mj[0] * vx + mj[1] * vy + mj[2] * vz;
-            J1 = mj[3] * vx + mj[4] * vy + mj[5] * vz;
-            J2 = mj[6] * vx + mj[7] * vy + mj[8] * vz;
         }
         const T hm = a.hm[t];
         const T ke = hm * (vx * vx + vy * vy + vz * vz);
