@@ -274,8 +274,14 @@ __device__ __forceinline__ void tersoff_b(const TersoffC<T> &p, T zeta, T &b, T 
 // index of the unordered bond pair (j, k), j < k
 __device__ __forceinline__ int tri(int j, int k) { return k * (k - 1) / 2 + j; }
 
-template <int CAP>
-constexpr int tersoff_smem_fields() { return TF_NF * CAP + CAP * (CAP - 1) / 2; }
+// Per unordered bond pair the fp64 pass keeps cos theta, g and g' from the zeta loop for the
+// angular loop (it is bound by its fp64 pipe); the fp32 pass keeps only 1/(d^2 + (h - cos)^2)
+// and recomputes the rest (it is bound by instruction issue and occupancy, and three words
+// per pair would cost it resident blocks).
+template <typename T>
+constexpr bool kCachePairs = sizeof(T) == 8;
+template <typename T, int CAP>
+constexpr int tersoff_smem_fields() { return TF_NF * CAP + (kCachePairs<T> ? 3 : 1) * (CAP * (CAP - 1) / 2); }
 
 // Constants of bond k of the atom: its element pair's (MULTI: the row entry of the element
 // staged in field TF_DX), else the single set's.
@@ -296,8 +302,13 @@ __device__ __forceinline__ void tersoff_atom(const PairArgs<T> &a, const Tersoff
     const int64_t N = a.N;
     const int S_ = a.stride;
     Stage<T, CAP, BLOCK> S{base, (int)threadIdx.x};
-    T *sinv = base + TF_NF * CAP * BLOCK;   // per bond pair: 1/(d^2 + (h - cos)^2)
-    auto INV = [&](int q) -> T & { return sinv[q * BLOCK + threadIdx.x]; };
+    // per unordered bond pair q: fp64, cos theta, g and dg/dcos from the zeta loop; fp32,
+    // 1/(d^2 + (h - cos)^2) (slot PCS)
+    constexpr int NP = CAP * (CAP - 1) / 2;
+    T *spair = base + TF_NF * CAP * BLOCK;
+    auto PCS = [&](int q) -> T & { return spair[q * BLOCK + threadIdx.x]; };
+    auto PG = [&](int q) -> T & { return spair[(NP + q) * BLOCK + threadIdx.x]; };
+    auto PDG = [&](int q) -> T & { return spair[(2 * NP + q) * BLOCK + threadIdx.x]; };
 
     uint32_t mask;
     const int na = collect_bonds<T, CAP, BLOCK, FULL_CAP, false, MULTI>(a, i, box, p.rc2, mask, S, TF_UX, TF_UY,
@@ -336,9 +347,16 @@ __device__ __forceinline__ void tersoff_atom(const PairArgs<T> &a, const Tersoff
         for (int k = j + 1; k < na; ++k) {
             const T cs = ujx * S(TF_UX, k) + ujy * S(TF_UY, k) + ujz * S(TF_UZ, k);
             const T inv = tersoff_inv_den(p, cs);
-            INV(tri(j, k)) = inv;
             T g, dg;
             tersoff_g(p, cs, inv, g, dg);
+            const int q = tri(j, k);
+            if constexpr (kCachePairs<T>) {
+                PCS(q) = cs;
+                PG(q) = g;
+                PDG(q) = dg;
+            } else {
+                PCS(q) = inv;
+            }
             zj += S(TF_FC, k) * g;
             S(TF_Z, k) += fcj * g;
         }
@@ -369,9 +387,16 @@ __device__ __forceinline__ void tersoff_atom(const PairArgs<T> &a, const Tersoff
         for (int k = j + 1; k < na; ++k) {
             const T ukx = S(TF_UX, k), uky = S(TF_UY, k), ukz = S(TF_UZ, k);
             const T irk = S(TF_IR, k), fck = S(TF_FC, k), dfck = S(TF_DFC, k), Pk = S(TF_Z, k);
-            const T cs = ujx * ukx + ujy * uky + ujz * ukz;
-            T g, dg;
-            tersoff_g(p, cs, INV(tri(j, k)), g, dg);
+            const int q = tri(j, k);
+            T cs, g, dg;
+            if constexpr (kCachePairs<T>) {
+                cs = PCS(q);
+                g = PG(q);
+                dg = PDG(q);
+            } else {
+                cs = ujx * ukx + ujy * uky + ujz * ukz;
+                tersoff_g(p, cs, PCS(q), g, dg);
+            }
             const T Q = (Pj * fck + Pk * fcj) * dg;
             const T cj = Pk * dfcj * g, ck = Pj * dfck * g;
             const T qj = Q * irj, qk = Q * irk;
@@ -639,6 +664,9 @@ __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, i
 {
     constexpr int NC = FULL ? kNumPartials : (NPT ? kNptPartials : kStepPartials);
     constexpr bool WDIAG = NPT && !FULL;
+    // heat current: fp64 by a second walk over the bonds (fewer fp64 instructions, fewer
+    // registers); fp32 from the 3x3 tensor of the first walk (one walk over memory)
+    constexpr bool JPASS = sizeof(T) == 8;
     const int64_t N = a.N;
     double vals[NC];
 #pragma unroll
@@ -662,10 +690,10 @@ __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, i
     if (live) {
         uint32_t mask = a.mask[i];
         T f0 = 0, f1 = 0, f2 = 0;
-        T w[9];
+        T w[9], mj[9];
         T wd0 = 0, wd1 = 0, wd2 = 0;
 #pragma unroll
-        for (int c = 0; c < 9; ++c) w[c] = 0;
+        for (int c = 0; c < 9; ++c) { w[c] = 0; mj[c] = 0; }
         int k = 0;
         while (mask != 0u && k < MAXA) {
             const int m = __ffs(mask) - 1;
@@ -689,6 +717,11 @@ __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, i
                     w[6] += rz * gx; w[7] += rz * gy; w[8] += rz * gz;
                 }
                 if (WDIAG) { wd0 += rx * gx; wd1 += ry * gy; wd2 += rz * gz; }
+                if (!JPASS) {   // M_i = sum_j r_ij (x) d_ji
+                    mj[0] += rx * ex; mj[1] += rx * ey; mj[2] += rx * ez;
+                    mj[3] += ry * ex; mj[4] += ry * ey; mj[5] += ry * ez;
+                    mj[6] += rz * ex; mj[7] += rz * ey; mj[8] += rz * ez;
+                }
             }
             ++k;
         }
@@ -730,13 +763,16 @@ __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, i
             a.vel[2 * N + i] = vn[2];
         }
         // J_i (Eq. 30) with v_i after the half-kick, and K_i = m v^2 / 2, in T (the fp32
-        // per-atom value of the mixed path feeds an fp64 total): a second walk over the bonds,
-        // J_i = sum_j r_ij (d_ji . v_i), 6 FMAs per bond (its loads hit the cache), instead
-        // of accumulating the 3x3 tensor sum_j r_ij (x) d_ji in the first walk (9 per bond,
-        // 9 more registers).
+        // per-atom value of the mixed path feeds an fp64 total).  fp64: a second walk over
+        // the bonds, J_i = sum_j r_ij (d_ji . v_i), 6 FMAs per bond (its loads hit the cache;
+        // the fp64 pipe is the bound); fp32: J_i = M_i . v_i.
         const T vx = to_t<T>(v[0]), vy = to_t<T>(v[1]), vz = to_t<T>(v[2]);
         T J0 = T(0), J1 = T(0), J2 = T(0);
-        {
+        if (!JPASS) {
+            J0 = mj[0] * vx + mj[1] * vy + mj[2] * vz;
+            J1 = mj[3] * vx + mj[4] * vy + mj[5] * vz;
+            J2 = mj[6] * vx + mj[7] * vy + mj[8] * vz;
+        } else {
             uint32_t m2 = a.mask[i];
             int k2 = 0;
             while (m2 != 0u && k2 < MAXA) {
@@ -1024,7 +1060,7 @@ constexpr int kGatherBlock = 128;
 template <typename T, int CAP, int BLOCK>
 size_t smem_for(int kind)
 {
-    const int nf = kind == 1 ? tersoff_smem_fields<CAP>() : sw_smem_fields<CAP>();
+    const int nf = kind == 1 ? tersoff_smem_fields<T, CAP>() : sw_smem_fields<CAP>();
     return (size_t)nf * BLOCK * sizeof(T);
 }
 
