@@ -28,10 +28,26 @@ constexpr int kScanThreads = 256;
 constexpr int kScanPerThread = 4;
 constexpr int kScanElems = kScanThreads * kScanPerThread;  // per block
 
-__device__ __forceinline__ int cell_coord(double x, int nc, double invL)
+// Cell index along one axis from the fp32 coordinate (FMA pipe instead of GB300's 1/64-rate
+// fp64 pipe).  A coordinate within rounding distance of a cell boundary may land in the
+// neighbouring cell; the cells are at least the list radius plus the fp32 margin wide, which
+// exceeds that distance, so the 27-cell search still covers every neighbour within rl.
+__device__ __forceinline__ int cell_coord_f(float x, int nc, float nc_over_L)
 {
-    int c = (int)floor(x * invL * (double)nc);
-    return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
+    const float t = fminf(fmaxf(x * nc_over_L, 0.f), (float)(nc - 1));
+    return (int)t;
+}
+
+// x wrapped into [0, L) (periodic axis), in fp64 only for the atoms outside it: for
+// non-negative doubles the bit patterns order like the values, so the test is integer.
+__device__ __forceinline__ double wrap_coord(double x, double L, double invL)
+{
+    const long long xb = __double_as_longlong(x);
+    if (xb >= 0 && xb < __double_as_longlong(L)) return x;
+    x -= L * floor(x * invL);
+    if (x >= L) x -= L;
+    if (x < 0.0) x += L;
+    return x;
 }
 
 // Wrap coordinates on periodic axes into [0, L), keep an fp32 copy, bin into cells.
@@ -60,13 +76,13 @@ __device__ __forceinline__ void cell_count_atom(int64_t i, int64_t N, double *po
     for (int a = 0; a < 3; ++a) {
         double x = pos[a * N + i];
         if (box.pbc[a]) {
-            x -= box.L[a] * floor(x * box.invL[a]);
-            if (x >= box.L[a]) x -= box.L[a];
-            if (x < 0.0) x += box.L[a];
-            pos[a * N + i] = x;
+            const double xw = wrap_coord(x, box.L[a], box.invL[a]);
+            if (__double_as_longlong(xw) != __double_as_longlong(x)) pos[a * N + i] = xw;
+            x = xw;
         }
-        posf[a * N + i] = (float)x;
-        cc[a] = cell_coord(x, nc[a], box.invL[a]);
+        const float xf = d2f_trunc(x);
+        posf[a * N + i] = xf;
+        cc[a] = cell_coord_f(xf, nc[a], (float)nc[a] * d2f_trunc(box.invL[a]));
     }
     const long long c = off + (cc[0] * nc[1] + cc[1]) * nc[2] + cc[2];
     atom_cell[i] = (int)c;
@@ -552,7 +568,7 @@ __global__ void k_displacement(int64_t N, const double *pos, const double *pos_b
     float d2 = 0.f;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const float d = (float)(pos[a * N + i] - pos_build[a * N + i]);
+        const float d = d2f_trunc(pos[a * N + i] - pos_build[a * N + i]);
         d2 = fmaf(d, d, d2);
     }
     if (!(d2 <= half_skin2)) {
