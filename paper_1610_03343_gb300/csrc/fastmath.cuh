@@ -6,15 +6,15 @@
 // P. T. P. Tang (exp: ACM TOMS 15 (1989) 144-157; log: ACM TOMS 16 (1990) 378-400), written
 // here from the mathematics with short Taylor polynomials:
 //
-//   exp: x = (64 m + j) ln2/64 + r, |r| <= ln2/128;  e^x = 2^m 2^(j/64) (1 + p(r)),
-//        p(r) = r + r^2/2 + r^3/6 + r^4/24 + r^5/120  (truncation below 0.2 ulp).
-//        Ten fp64 instructions; error within 2 ulp.  Domain |x| <= 708 (no clamping: the
+//   exp: x = (256 m + j) ln2/256 + r, |r| <= ln2/512;  e^x = 2^m 2^(j/256) (1 + p(r)),
+//        p(r) = r + r^2/2 + r^3/6 + r^4/24  (truncation below 0.2 ulp).
+//        Nine fp64 instructions; error within 2 ulp.  Domain |x| <= 708 (no clamping: the
 //        pair pass's arguments are -lambda r with r < S, and n log(beta zeta) and
 //        -log(1 + x)/(2n) with zeta >= f_C > 1e-32, all far inside).
-//   log: x = 2^e m, m in [1, 2), c_j = 1 + (j + 1/2)/128 for the top seven bits j of m,
+//   log: x = 2^e m, m in [1, 2), c_j = 1 + (j + 1/2)/256 for the top eight bits j of m,
 //        log x = e ln2 - log(RN(1/c_j)) + log(1 + r), r = m RN(1/c_j) - 1 (one fma),
-//        |r| < 1/256, log(1 + r) by its Taylor series to r^6 (truncation 2e-18).
-//        Eleven fp64 instructions; absolute error about 1e-16 (1 + |e|), which is what the
+//        |r| < 1/512, log(1 + r) by its Taylor series to r^5 (truncation 1e-17).
+//        Ten fp64 instructions; absolute error about 1e-16 (1 + |e|), which is what the
 //        bond order needs (an absolute error d in log(1 + x) is a relative error d/(2n) in
 //        b, and an absolute error in log zeta a relative error n d in (beta zeta)^n).
 //        Domain: positive normal x.
@@ -29,29 +29,27 @@ namespace mdk {
 __device__ __forceinline__ double exp_tab(double x)
 {
     const double kShift = 0x1.8p52;                      // 1.5 * 2^52: rounds to an integer
-    const double t = fma(x, kInvLn2o64, kShift);
-    const int k = __double2loint(t);                     // round(x 64/ln2), two's complement
+    const double t = fma(x, kInvLn2o256, kShift);
+    const int k = __double2loint(t);                     // round(x 256/ln2), two's complement
     const double kd = t - kShift;
-    double r = fma(kd, -kLn2o64Hi, x);
-    r = fma(kd, -kLn2o64Lo, r);
-    double q = fma(r, 1.0 / 120.0, 1.0 / 24.0);
-    q = fma(q, r, 1.0 / 6.0);
+    double r = fma(kd, -kLn2o256Hi, x);
+    r = fma(kd, -kLn2o256Lo, r);
+    double q = fma(r, 1.0 / 24.0, 1.0 / 6.0);
     q = fma(q, r, 0.5);
     const double p = fma(q, r * r, r);                   // e^r - 1
-    const double tj = __ldg(&kExp2Tab[k & 63]);
-    const double y = fma(tj, p, tj);                     // 2^(j/64) e^r, in [0.99, 2)
-    return __hiloint2double(__double2hiint(y) + ((k >> 6) << 20), __double2loint(y));
+    const double tj = __ldg(&kExp2Tab[k & 255]);
+    const double y = fma(tj, p, tj);                     // 2^(j/256) e^r, in [0.997, 2)
+    return __hiloint2double(__double2hiint(y) + ((k >> 8) << 20), __double2loint(y));
 }
 
 __device__ __forceinline__ double log_tab(double x)
 {
     const int hi = __double2hiint(x), lo = __double2loint(x);
     const int e = (hi >> 20) - 1023;
-    const int j = (hi >> 13) & 127;
+    const int j = (hi >> 12) & 255;
     const double m = __hiloint2double((hi & 0x000fffff) | 0x3ff00000, lo);
     const double r = fma(m, __ldg(&kLogInvTab[j]), -1.0);
-    double q = fma(r, -1.0 / 6.0, 0.2);
-    q = fma(q, r, -0.25);
+    double q = fma(r, 0.2, -0.25);
     q = fma(q, r, 1.0 / 3.0);
     q = fma(q, r, -0.5);
     const double p = fma(q, r * r, r);                   // log(1 + r)

@@ -17,24 +17,24 @@ def d(x: Decimal) -> str:
 def main():
     lines = ["// fastmath_tables.cuh -- written by gen_fastmath_tables.py; do not edit.", "#pragma once", "",
              "namespace mdk {", ""]
-    # exp: 2^(j/64), j = 0..63
-    lines.append("// 2^(j/64), j = 0..63, rounded to double")
-    vals = [d((LN2 * j / 64).exp()) for j in range(64)]
-    lines.append("__device__ const double kExp2Tab[64] = {")
+    # exp: 2^(j/256), j = 0..255
+    lines.append("// 2^(j/256), j = 0..255, rounded to double")
+    vals = [d((LN2 * j / 256).exp()) for j in range(256)]
+    lines.append("__device__ const double kExp2Tab[256] = {")
     lines += [f"    {v}," for v in vals]
     lines.append("};")
-    # ln2/64 split into a head and a tail (head rounded to 32 significant bits so that
-    # k * head is exact for |k| < 2^20)
-    l64 = LN2 / 64
+    # ln2/256 split into a head and a tail (head rounded to 32 significant bits so that
+    # k * head is exact for |k| < 2^21)
+    l64 = LN2 / 256
     head = float(l64)
     # keep 32 significant bits of the head
     import math
     m, e = math.frexp(head)
     head = math.ldexp(math.floor(m * 2 ** 32) / 2 ** 32, e)
     tail = float(l64 - Decimal(head))
-    lines.append(f"constexpr double kLn2o64Hi = {head.hex()};   // ln2/64, 32 leading bits")
-    lines.append(f"constexpr double kLn2o64Lo = {tail.hex()};   // ln2/64 - kLn2o64Hi")
-    lines.append(f"constexpr double kInvLn2o64 = {d(64 / LN2)};   // 64/ln2")
+    lines.append(f"constexpr double kLn2o256Hi = {head.hex()};   // ln2/256, 32 leading bits")
+    lines.append(f"constexpr double kLn2o256Lo = {tail.hex()};   // ln2/256 - kLn2o256Hi")
+    lines.append(f"constexpr double kInvLn2o256 = {d(256 / LN2)};   // 256/ln2")
     # ln2 split for the log
     h2 = float(LN2)
     m, e = math.frexp(h2)
@@ -43,20 +43,20 @@ def main():
     lines.append(f"constexpr double kLn2Hi = {h2.hex()};   // ln2, 32 leading bits")
     lines.append(f"constexpr double kLn2Lo = {t2.hex()};   // ln2 - kLn2Hi")
     lines.append("")
-    # log: for the mantissa interval j (m in [1 + j/128, 1 + (j+1)/128)), c_j = 1 + (j + 1/2)/128,
+    # log: for the mantissa interval j (m in [1 + j/256, 1 + (j+1)/256)), c_j = 1 + (j + 1/2)/256,
     # inv_j = RN(1/c_j) and minus the logarithm of inv_j (exactly the inv used)
     inv, lg = [], []
-    for j in range(128):
-        c = 1 + (Decimal(j) + Decimal("0.5")) / 128
+    for j in range(256):
+        c = 1 + (Decimal(j) + Decimal("0.5")) / 256
         iv = float(Decimal(1) / c)
         inv.append(iv.hex())
         lg.append(d(-Decimal(iv).ln()))
-    lines.append("// 1/c_j rounded to double, c_j = 1 + (j + 1/2)/128, j = 0..127")
-    lines.append("__device__ const double kLogInvTab[128] = {")
+    lines.append("// 1/c_j rounded to double, c_j = 1 + (j + 1/2)/256, j = 0..255")
+    lines.append("__device__ const double kLogInvTab[256] = {")
     lines += [f"    {v}," for v in inv]
     lines.append("};")
     lines.append("// -log(kLogInvTab[j]) rounded to double")
-    lines.append("__device__ const double kLogTab[128] = {")
+    lines.append("__device__ const double kLogTab[256] = {")
     lines += [f"    {v}," for v in lg]
     lines.append("};")
     lines += ["", "}  // namespace mdk", ""]
