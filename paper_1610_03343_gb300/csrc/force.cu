@@ -400,12 +400,14 @@ __device__ __forceinline__ void tersoff_atom(const PairArgs<T> &a, const Tersoff
             const T Q = (Pj * fck + Pk * fcj) * dg;
             const T cj = Pk * dfcj * g, ck = Pj * dfck * g;
             const T qj = Q * irj, qk = Q * irk;
-            djx += qj * (ukx - cs * ujx) + cj * ujx;
-            djy += qj * (uky - cs * ujy) + cj * ujy;
-            djz += qj * (ukz - cs * ujz) + cj * ujz;
-            S(TF_DX, k) += qk * (ujx - cs * ukx) + ck * ukx;
-            S(TF_DY, k) += qk * (ujy - cs * uky) + ck * uky;
-            S(TF_DZ, k) += qk * (ujz - cs * ukz) + ck * ukz;
+            // d_j += qj (u_k - cos u_j) + cj u_j, written as qj u_k + (cj - qj cos) u_j
+            const T aj = cj - qj * cs, ak = ck - qk * cs;
+            djx += qj * ukx + aj * ujx;
+            djy += qj * uky + aj * ujy;
+            djz += qj * ukz + aj * ujz;
+            S(TF_DX, k) += qk * ujx + ak * ukx;
+            S(TF_DY, k) += qk * ujy + ak * uky;
+            S(TF_DZ, k) += qk * ujz + ak * ukz;
         }
         a.d[(int64_t)(0 * S_ + j) * N + i] = djx;
         a.d[(int64_t)(1 * S_ + j) * N + i] = djy;
