@@ -45,12 +45,12 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # to the C sheet (3 bonds per atom, 731.45 flop/atom) and Si diamond (4 bonds, 1120.27
 # flop/atom).  SW: per atom of the 4-bond diamond lattice (812.2 flop/atom, counted before
 # its table-driven exp and reciprocal).
-TERSOFF_FLOP_PER_BOND = 171.315
-TERSOFF_FLOP_PER_BOND_PAIR = 36.251
+TERSOFF_FLOP_PER_BOND = 159.316
+TERSOFF_FLOP_PER_BOND_PAIR = 32.250
 SW_FLOP_PER_ATOM_4 = 812.2
 # DRAM bytes (read + write) of one fp64 pair launch, from the ncu capture of the current
 # kernel on each workload.
-PAIR_TRAFFIC_BYTES = {"tersoff_c_graphene_1M": 139.66e6, "tersoff_si_216k": 9.72e6, "sw_si_512k": None}
+PAIR_TRAFFIC_BYTES = {"tersoff_c_graphene_1M": 140.43e6, "tersoff_si_216k": 9.71e6, "sw_si_512k": None}
 
 
 def load_peaks():
