@@ -120,6 +120,25 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+def reduce_max_over_ranks(values, world, device):
+    """Each value's maximum over the ranks (the slowest rank sets a replica run's time);
+    the values themselves for one rank.  device: where the collective's tensor lives (cuda
+    for NCCL, cpu for gloo)."""
+    if world == 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def job_value(world, n_atoms, steps, ms):
+    """Whole-job atom-steps/s of `world` replicas of n_atoms atoms run for `steps` steps,
+    timed by the slowest rank (ms)."""
+    return world * n_atoms * steps / (ms / 1e3)
+
+
 def pair_flops(kind: int, bonds: float) -> float:
     """Algorithmic FP64 flops per atom of the fp64 pair pass on a lattice with `bonds`
     in-cutoff neighbours per atom."""
@@ -506,14 +525,9 @@ def main():
     primary = "fp64" if "fp64" in res else "mixed"
     ms = res[primary]["ms"]
     ms_mixed = res["mixed"]["ms"] if "mixed" in res else 0.0
-    if world > 1:
-        import torch
-        import torch.distributed as dist
-        t = torch.tensor([ms, ms_mixed, t_e2e or 0.0], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, ms_mixed, t_e2e_max = (float(v) for v in t.tolist())
-        t_e2e = t_e2e_max if t_e2e is not None else None
-    value = world * n * args.steps / (ms / 1e3)
+    ms, ms_mixed, t_e2e_max = reduce_max_over_ranks([ms, ms_mixed, t_e2e or 0.0], world, "cuda")
+    t_e2e = t_e2e_max if t_e2e is not None else None
+    value = job_value(world, n, args.steps, ms)
     if rank != 0:
         return
     kt = res[primary]["kt"]
@@ -553,7 +567,7 @@ def main():
         "tuning": res[primary]["tuning"],
     }
     if "mixed" in res and primary != "mixed":
-        out["mixed"] = {"value": world * n * args.steps / (ms_mixed / 1e3), "ms_per_step": ms_mixed / args.steps,
+        out["mixed"] = {"value": job_value(world, n, args.steps, ms_mixed), "ms_per_step": ms_mixed / args.steps,
                         "dtype": "f32+f64", "force_err_vs_fp64": mixed_err,
                         "kernel_ms_per_step": {k: (v[1] / v[0] if v[0] else None)
                                                for k, v in res["mixed"]["kt"].items()},
