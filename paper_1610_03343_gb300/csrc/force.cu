@@ -1054,8 +1054,11 @@ unsigned pool_grid(const Plan &p)
 }
 
 constexpr int kPairCapSmall = 4;     // Tersoff: bonds staged per atom in the common-case pass
-constexpr int kPairCapSmallSW = 8;   // SW: its second shell sits just outside the cutoff, and at
-                                     // room temperature many atoms have 5-6 bonds inside it
+// SW: its second shell sits just outside the cutoff, and at room temperature many atoms have
+// 5-6 bonds inside it (a 12-bond fp32 staging moved the rarer heavier atoms into the common
+// pass but cost the pools' occupancy more than it saved: serving 2.94e9 -> 2.7e9 atom-steps/s)
+template <typename T>
+constexpr int kPairCapSmallSW = 8;
 constexpr int kPairBlockFull = 32;   // full-capacity pass over the deferred atoms
 constexpr int kGatherBlock = 128;
 
@@ -1082,7 +1085,7 @@ template <typename T, int B, bool BATCH>
 void configure_block()
 {
     set_smem<T, kPairCapSmall, B, false, BATCH>();
-    set_smem<T, kPairCapSmallSW, B, false, BATCH>();
+    set_smem<T, kPairCapSmallSW<T>, B, false, BATCH>();
 }
 
 template <typename T, bool BATCH>
@@ -1150,7 +1153,7 @@ void pair_launch_b(const Plan &p, cudaStream_t s, int list, int parts)
         SWSets<T> c;
         for (int k = 0; k < kMaxSets; ++k) c.s[k] = sw_const<T>(p.sp[k < p.n_sets ? k : 0]);
         if (parts & PAIR_FAST)
-            k_pair_sw<T, kPairCapSmallSW, B, false, BATCH><<<nb, B, smem_for<T, kPairCapSmallSW, B>(2), s>>>(a, c);
+            k_pair_sw<T, kPairCapSmallSW<T>, B, false, BATCH><<<nb, B, smem_for<T, kPairCapSmallSW<T>, B>(2), s>>>(a, c);
         if (parts & PAIR_DEFERRED)
             k_pair_sw<T, FULL, kPairBlockFull, true, BATCH>
                 <<<(unsigned)nbf, kPairBlockFull, smem_for<T, FULL, kPairBlockFull>(2), s>>>(a, c);

@@ -73,9 +73,15 @@ def test_compute_fp64_matches_oracle(md, name, make):
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_atoms_with_many_bonds_take_the_full_capacity_pass(md, precision):
-    """Jittered SW silicon puts up to 10 neighbours inside the cutoff: those atoms are
-    deferred by the 4-bond pass and computed by the full-capacity pass."""
-    s = I.si_diamond_sw(n=5, jitter_amp=0.1)
+    """Atoms with more in-cutoff bonds than the common-case pass stages (SW: 8) are deferred
+    to the full-capacity pass.  fp64: jittered SW silicon puts up to 10 neighbours inside
+    the cutoff (some atoms deferred); fp32: SW silicon compressed to a = 5.1 A brings the
+    12-atom second shell (3.61 A) inside the 3.77 A cutoff, 16 bonds per atom (all atoms
+    deferred)."""
+    if precision == 0:
+        s = I.si_diamond_sw(n=5, jitter_amp=0.1)
+    else:
+        s = I.si_diamond_sw(n=5, a=5.1, jitter_amp=0.05)
     ref = O.compute(s.pos, s.box, s.pbc, s.kind, s.params, s.vel)
     with md.from_inputs(s, precision=precision) as g:
         out = g.compute()
