@@ -142,9 +142,11 @@ __device__ __forceinline__ int collect_bonds(const PairArgs<T> &a, int64_t i, co
     const int64_t N = a.N;
     const int S_ = a.stride;
     const double xi = a.pos[i], yi = a.pos[N + i], zi = a.pos[2 * N + i];
-    float fxi = 0.f, fyi = 0.f, fzi = 0.f, lim2 = 0.f;
+    float fxi = 0.f, fyi = 0.f, fzi = 0.f, lim2 = 0.f, fL0 = 0.f, fL1 = 0.f, fL2 = 0.f;
     if (PREFILTER) {
         fxi = a.posf[i]; fyi = a.posf[N + i]; fzi = a.posf[2 * N + i];
+        // box edges in fp32 once per atom, with integer instructions (within the margin)
+        fL0 = d2f_trunc(box.L[0]); fL1 = d2f_trunc(box.L[1]); fL2 = d2f_trunc(box.L[2]);
         // margin: the box-based bound plus the rounding of this atom's own coordinates,
         // which on an open axis may lie far outside the box
         const float mag = fmaxf(fabsf(fxi), fmaxf(fabsf(fyi), fabsf(fzi)));
@@ -174,9 +176,9 @@ __device__ __forceinline__ int collect_bonds(const PairArgs<T> &a, int64_t i, co
                 const int code = list_code(e[q]);
                 if (code != kNoShift) {
                     const int sx = code % 3 - 1, sy = (code / 3) % 3 - 1, sz = code / 9 - 1;
-                    dx = fmaf((float)sx, (float)box.L[0], dx);
-                    dy = fmaf((float)sy, (float)box.L[1], dy);
-                    dz = fmaf((float)sz, (float)box.L[2], dz);
+                    dx = fmaf((float)sx, fL0, dx);
+                    dy = fmaf((float)sy, fL1, dy);
+                    dz = fmaf((float)sz, fL2, dz);
                 }
                 keep[q] = dx * dx + dy * dy + dz * dz < lim2;
             }
