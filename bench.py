@@ -41,13 +41,16 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 # FP64 flops of the fp64 pair pass, counted with ncu's instruction counters (DADD + DMUL +
 # 2 DFMA, which include the fp64 instruction sequences of the table-driven exp and log, the
-# Newton reciprocal and the square root).  Tersoff: per bond and per ordered bond pair, fit
-# to the C sheet (3 bonds per atom, 731.45 flop/atom) and Si diamond (4 bonds, 1120.27
-# flop/atom).  SW: per atom of the 4-bond diamond lattice (812.2 flop/atom, counted before
-# its table-driven exp and reciprocal).
+# Newton reciprocal and the square root), per in-cutoff bond and per ordered pair of bonds
+# (j, k != j) of one atom.  Tersoff: fit to the C sheet (3 bonds per atom, 671.45 flop/atom)
+# and Si diamond (4 bonds, 1024.27 flop/atom).  SW: fit to the Si diamond lattice (4 bonds,
+# 12 ordered pairs: 700.21 flop/atom) and the same crystal after 150 fs at 300 K (5.065
+# bonds, 21.461 ordered pairs: 1058.31 flop/atom; second-shell atoms at 3.84 A move inside
+# the 3.77 A cutoff).
 TERSOFF_FLOP_PER_BOND = 159.316
 TERSOFF_FLOP_PER_BOND_PAIR = 32.250
-SW_FLOP_PER_ATOM_4 = 812.2
+SW_FLOP_PER_BOND = 92.859
+SW_FLOP_PER_BOND_PAIR = 27.398
 # DRAM bytes (read + write) of one fp64 pair launch, from the ncu capture of the current
 # kernel on each workload.
 PAIR_TRAFFIC_BYTES = {"tersoff_c_graphene_1M": 140.43e6, "tersoff_si_216k": 9.71e6, "sw_si_512k": None}
@@ -139,12 +142,32 @@ def job_value(world, n_atoms, steps, ms):
     return world * n_atoms * steps / (ms / 1e3)
 
 
-def pair_flops(kind: int, bonds: float) -> float:
-    """Algorithmic FP64 flops per atom of the fp64 pair pass on a lattice with `bonds`
-    in-cutoff neighbours per atom."""
+def pair_flops(kind: int, bonds: float, bond_pairs: float) -> float:
+    """Algorithmic FP64 flops per atom of the fp64 pair pass for a mean of `bonds` in-cutoff
+    neighbours and `bond_pairs` ordered bond pairs (the mean of M (M - 1)) per atom."""
     if kind == I.MD_TERSOFF:
-        return TERSOFF_FLOP_PER_BOND * bonds + TERSOFF_FLOP_PER_BOND_PAIR * bonds * (bonds - 1)
-    return SW_FLOP_PER_ATOM_4 * bonds / 4.0
+        return TERSOFF_FLOP_PER_BOND * bonds + TERSOFF_FLOP_PER_BOND_PAIR * bond_pairs
+    return SW_FLOP_PER_BOND * bonds + SW_FLOP_PER_BOND_PAIR * bond_pairs
+
+
+def bond_statistics(pos, box, pbc, rc):
+    """Mean number M of neighbours within the cutoff rc per atom and the mean of M (M - 1),
+    by minimum image along the periodic axes (a k-d tree over the wrapped positions)."""
+    from scipy.spatial import cKDTree
+    pos = np.asarray(pos, dtype=np.float64)
+    box = np.asarray(box, dtype=np.float64)
+    per = np.asarray(pbc) != 0
+    x = pos.copy()
+    x[:, per] = np.mod(x[:, per], box[per])
+    x[:, per] = np.where(x[:, per] >= box[per], 0.0, x[:, per])   # mod can round up to L
+    lo = x.min(axis=0)
+    size = box.copy()
+    # an open axis gets a period long enough that no pair wraps across it
+    size[~per] = (x.max(axis=0) - lo)[~per] + 4.0 * rc + 1.0
+    x[:, ~per] -= lo[~per]
+    pairs = cKDTree(x, boxsize=size).query_pairs(rc, output_type="ndarray")
+    m = np.bincount(pairs.ravel(), minlength=x.shape[0]).astype(np.float64)
+    return float(m.mean()), float((m * (m - 1.0)).mean())
 
 
 def run_ours(args, rank, world):
@@ -167,6 +190,11 @@ def run_ours(args, rank, world):
         if args.eager:
             md.md_set_graph_mode(g.ctx, False)
         f0 = g.compute(want=("f",))["F"].copy()
+        # untimed equilibration from the lattice start, so that the tuner and the timed
+        # window see the thermal state that dominates a long run (SW silicon gains about
+        # one bond per atom in the first ~100 fs)
+        if args.equilibrate:
+            g.run(args.equilibrate, dt, record=False)
         tuning = None
         if args.pair_block:
             pb = dict(zip(("fp64", "mixed"), (int(v) for v in args.pair_block.split(","))))[tag]
@@ -175,6 +203,7 @@ def run_ours(args, rank, world):
         elif not args.no_tune:
             tuning = md.tuning_dict(md.md_autotune(g.ctx, 10))
         g.run(args.warmup, dt, record=False)
+        pos_first = g.state()[0] if tag == precs[0][1] else None
         st0 = g.stats()
         rebuilds0, kernels0 = st0.n_rebuilds, st0.kernels_launched
         md.md_set_profiling(g.ctx, True)
@@ -195,7 +224,9 @@ def run_ours(args, rank, world):
         kt = md.md_kernel_times(g.ctx)
         md.md_set_profiling(g.ctx, False)
         st = g.stats()
+        pos_last = g.state()[0] if tag == precs[0][1] else None
         res[tag] = dict(ms=ms, kt=kt, f0=f0, clocks=clocks.summary(), stats=st, sys=g, tuning=tuning, series=ser,
+                        pos_window=(pos_first, pos_last),
                         rebuilds=int(st.n_rebuilds - rebuilds0),
                         launches=int(st.kernels_launched - kernels0)
                         + int(st.kernel_launches_per_rebuild) * int(st.n_rebuilds - rebuilds0))
@@ -473,6 +504,8 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--equilibrate", type=int, default=100,
+                    help="untimed steps from the initial state before tuning and warm-up")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="tersoff_c_graphene_1M")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -534,8 +567,13 @@ def main():
     pair_n, pair_ms = kt.get("pair", (0, 0.0))
     st = res[primary]["stats"]
     sysm, _ = workload(args.workload)
-    bonds = 3.0 if sysm.kind == I.MD_TERSOFF and "graphene" in args.workload else 4.0
-    flops = pair_flops(sysm.kind, bonds) * n
+    # bonds at the first and the last step of the timed region (SW's count grows as the
+    # crystal warms up); the pair pass's flops per launch use their mean
+    rc = I.cutoff(sysm.kind, sysm.params)
+    bstats = [bond_statistics(p, sysm.box, sysm.pbc, rc) for p in res[primary]["pos_window"]]
+    bonds = 0.5 * (bstats[0][0] + bstats[1][0])
+    bond_pairs = 0.5 * (bstats[0][1] + bstats[1][1])
+    flops = pair_flops(sysm.kind, bonds, bond_pairs) * n
     pair_avg_s = pair_ms / pair_n / 1e3 if pair_n > 0 and pair_ms > 0 else None
     achieved_tf = flops / pair_avg_s / 1e12 if pair_avg_s else None
     traffic = PAIR_TRAFFIC_BYTES.get(args.workload) if primary == "fp64" else None
@@ -553,12 +591,15 @@ def main():
         "dtype": "f64" if primary == "fp64" else "f32+f64",
         "data": "synthetic",
         "config": {"workload": args.workload, "n_atoms": n, "dt_fs": dt, "ensemble": "NVE",
+                   "equilibration_steps": args.equilibrate,
                    "l2": "working set > L2 (no flush)", "launch": "eager" if args.eager else "graphs",
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "alu", "kernel": f"pair ({primary})", "achieved": achieved_tf,
                      "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved_tf / FP64_PEAK_TFLOPS if achieved_tf else None, "traffic": traffic,
                      "flop_per_launch": flops,
+                     "bonds_per_atom": [round(b[0], 4) for b in bstats],
+                     "bond_pairs_per_atom": [round(b[1], 4) for b in bstats],
                      "peak_source": "FP64 pipe from unit counts and clock: 152 SMs x 4 flop/clk x 2.07 GHz"},
         "kernel_ms_per_step": {k: (v[1] / v[0] if v[0] else None) for k, v in kt.items()},
         "gpu_launches": res[primary]["launches"],

@@ -425,17 +425,15 @@ enum { SW_UX, SW_UY, SW_UZ, SW_IR, SW_E, SW_DE, SW_DX, SW_DY, SW_DZ, SW_NF };
 template <int CAP>
 constexpr int sw_smem_fields() { return SW_NF * CAP; }
 
-// Pair pass for one atom (SW): two-body and vertex three-body terms.
-template <typename T, int CAP, int BLOCK, bool FULL_CAP>
-__device__ __forceinline__ void sw_atom(const PairArgs<T> &a, const SWC<T> &p, const Box &box, T *base, int64_t i)
+// SW terms of atom i from its na bonds staged in shared-memory slot `slot` (by
+// collect_bonds): two-body and vertex three-body terms, dU_i/dr_ij per bond, U_i.
+template <typename T, int CAP, int BLOCK>
+__device__ __forceinline__ void sw_terms(const PairArgs<T> &a, const SWC<T> &p, T *base, int64_t i, int slot, int na,
+                                         uint32_t mask)
 {
     const int64_t N = a.N;
     const int S_ = a.stride;
-    Stage<T, CAP, BLOCK> S{base, (int)threadIdx.x};
-    uint32_t mask;
-    const int na = collect_bonds<T, CAP, BLOCK, FULL_CAP, true>(a, i, box, p.rc2, mask, S, SW_UX, SW_UY, SW_UZ, SW_IR);
-    if (na < 0) return;
-
+    Stage<T, CAP, BLOCK> S{base, slot};
     T ui = T(0);
     for (int k = 0; k < na; ++k) {
         const T r2 = S(SW_IR, k);
@@ -489,6 +487,75 @@ __device__ __forceinline__ void sw_atom(const PairArgs<T> &a, const SWC<T> &p, c
     }
     a.mask[i] = mask;
     a.u[i] = to_d(ui);
+}
+
+// Pair pass for one atom (SW) in its own thread's slot.
+template <typename T, int CAP, int BLOCK, bool FULL_CAP>
+__device__ __forceinline__ void sw_atom(const PairArgs<T> &a, const SWC<T> &p, const Box &box, T *base, int64_t i)
+{
+    Stage<T, CAP, BLOCK> S{base, (int)threadIdx.x};
+    uint32_t mask;
+    const int na = collect_bonds<T, CAP, BLOCK, FULL_CAP, true>(a, i, box, p.rc2, mask, S, SW_UX, SW_UY, SW_UZ, SW_IR);
+    if (na < 0) return;   // deferred to the full-capacity pass
+    sw_terms<T, CAP, BLOCK>(a, p, base, i, (int)threadIdx.x, na, mask);
+}
+
+// Position of this thread's key among the block's keys (0 <= key < NK) in the stable
+// order by key: the number of threads with a smaller key plus those with the same key
+// and a lower thread index.  Deterministic; every thread of the block must call it.
+template <int BLOCK, int NK>
+__device__ __forceinline__ int block_rank(int key)
+{
+    constexpr int NW = BLOCK / 32;
+    __shared__ int cnt[NW][NK];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int below = 0;
+#pragma unroll
+    for (int v = 0; v < NK; ++v) {
+        const unsigned b = __ballot_sync(0xffffffffu, key == v);
+        if (lane == 0) cnt[w][v] = __popc(b);
+        if (key == v) below = __popc(b & ((1u << lane) - 1u));
+    }
+    __syncthreads();
+    // the bucket's start, then the same key in lower warps
+    int r = below;
+    for (int v = 0; v < key; ++v)
+#pragma unroll
+        for (int q = 0; q < NW; ++q) r += cnt[q][v];
+    for (int q = 0; q < w; ++q) r += cnt[q][key];
+    return r;
+}
+
+// Single systems, common case (SW): the block's atoms are processed in the order of their
+// bond count.  Each thread stages its own atom's bonds; the block then ranks the atoms by
+// that count and thread t takes the atom of rank t, so the atoms of one warp have (nearly)
+// the same number of bonds and bond pairs and the warp's loops do not wait for its
+// heaviest atom (at room temperature SW silicon's atoms have 4 to 8 bonds, since its second
+// shell lies just outside the cutoff).  Each atom's arithmetic is the same whichever
+// thread runs it: results do not depend on the order.
+template <typename T, int CAP, int BLOCK>
+__device__ __forceinline__ void sw_block_sorted(const PairArgs<T> &a, const SWC<T> &p, const Box &box, T *base)
+{
+    __shared__ short perm[BLOCK];
+    __shared__ signed char nas[BLOCK];
+    __shared__ uint32_t masks[BLOCK];
+    const int t = threadIdx.x;
+    const int64_t i0 = (int64_t)blockIdx.x * BLOCK;
+    int na = -1;
+    uint32_t mask = 0u;
+    if (i0 + t < a.N) {
+        Stage<T, CAP, BLOCK> S{base, t};
+        na = collect_bonds<T, CAP, BLOCK, false, true>(a, i0 + t, box, p.rc2, mask, S, SW_UX, SW_UY, SW_UZ, SW_IR);
+    }
+    // deferred atoms and the tail past N go last and do nothing here
+    const int r = block_rank<BLOCK, CAP + 2>(na < 0 ? CAP + 1 : na);
+    perm[r] = (short)t;
+    nas[t] = (signed char)na;
+    masks[t] = mask;
+    __syncthreads();
+    const int slot = perm[t];
+    const int n_s = nas[slot];
+    if (n_s >= 0) sw_terms<T, CAP, BLOCK>(a, p, base, i0 + slot, slot, n_s, masks[slot]);
 }
 
 template <typename T>
@@ -558,9 +625,18 @@ __global__ void __launch_bounds__(BLOCK) k_pair_sw(PairArgs<T> a, SWSets<T> ps)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     T *base = reinterpret_cast<T *>(smem);
-    pair_dispatch<T, CAP, BLOCK, FULL_CAP, BATCH>(a, ps, base, [&](const SWC<T> &p, const Box &box, int64_t i) {
-        sw_atom<T, CAP, BLOCK, FULL_CAP>(a, p, box, base, i);
-    });
+    if constexpr (!FULL_CAP && !BATCH) {
+        if (a.dev_box) {
+            const Box bx = a.sys[0].box;
+            sw_block_sorted<T, CAP, BLOCK>(a, ps.s[0], bx, base);
+        } else {
+            sw_block_sorted<T, CAP, BLOCK>(a, ps.s[0], a.box, base);
+        }
+    } else {
+        pair_dispatch<T, CAP, BLOCK, FULL_CAP, BATCH>(a, ps, base, [&](const SWC<T> &p, const Box &box, int64_t i) {
+            sw_atom<T, CAP, BLOCK, FULL_CAP>(a, p, box, base, i);
+        });
+    }
 }
 
 __global__ void k_pair_reset(int *ovf_count) { *ovf_count = 0; }
