@@ -188,8 +188,9 @@ typedef struct {
                                  a graph of steps, each step after the first has its first
                                  half-kick fused into the previous step's gather)         */
     int kernel_launches_per_rebuild; /* extra kernels of a step that rebuilds the list */
-    int pair_deferred;       /* atoms with more than 4 in-cutoff bonds at the last pair pass
-                                (handled by the full-capacity pass)                      */
+    int pair_deferred;       /* atoms with more in-cutoff bonds than the common-case pass
+                                stages (Tersoff 4, SW 8) at the last pair pass, handled
+                                by the full-capacity pass (SW: one warp per atom)        */
     size_t device_bytes;     /* bytes the context has allocated on the device         */
     int64_t atoms_rebuilt;   /* atoms whose neighbour list was built, summed over builds
                                 (pools: only the systems that needed a rebuild)          */

@@ -122,6 +122,32 @@ SWC<T> sw_const(const SWP &p)
     return c;
 }
 
+// |r|^2 of a bond vector in the pass's type.  Every pass that decides whether a bond is
+// inside the cutoff uses this one expression, so that atom i's pass and atom j's pass
+// (which may be different kernels) reach the same decision from negated vectors.
+template <typename T>
+__device__ __forceinline__ T bond_r2(T x, T y, T z)
+{
+    return fma(z, z, fma(y, y, x * x));
+}
+
+// fp64 bond vector r_j - r_i of list entry e (image shift from the entry), in type T
+template <typename T>
+__device__ __forceinline__ void bond_vector(const double *pos, int64_t N, int e, double xi, double yi, double zi,
+                                            const Box &box, T &tx, T &ty, T &tz)
+{
+    const int j = list_atom(e);
+    double dx = pos[j] - xi, dy = pos[N + j] - yi, dz = pos[2 * N + j] - zi;
+    const int code = list_code(e);
+    if (code != kNoShift) {
+        const int sx = code % 3 - 1, sy = (code / 3) % 3 - 1, sz = code / 9 - 1;
+        if (sx) dx += sx > 0 ? box.L[0] : -box.L[0];
+        if (sy) dy += sy > 0 ? box.L[1] : -box.L[1];
+        if (sz) dz += sz > 0 ? box.L[2] : -box.L[2];
+    }
+    tx = to_t<T>(dx); ty = to_t<T>(dy); tz = to_t<T>(dz);
+}
+
 // ------------------------------------------------------- neighbour staging
 // For each list slot, the fp64 bond r_ij (image shift from the entry); keeps the slots
 // with |r_ij|^2 < rc^2, writes their bond vectors (compact row k) to global memory and
@@ -206,7 +232,7 @@ __device__ __forceinline__ int collect_bonds(const PairArgs<T> &a, int64_t i, co
                 if (sz) dz += sz > 0 ? box.L[2] : -box.L[2];
             }
             const T tx = to_t<T>(dx), ty = to_t<T>(dy), tz = to_t<T>(dz);
-            const T r2 = tx * tx + ty * ty + tz * tz;
+            const T r2 = bond_r2(tx, ty, tz);
             int tj = 0;
             T cut2 = rc2;
             if (MULTI) {
@@ -425,6 +451,39 @@ enum { SW_UX, SW_UY, SW_UZ, SW_IR, SW_E, SW_DE, SW_DX, SW_DY, SW_DZ, SW_NF };
 template <int CAP>
 constexpr int sw_smem_fields() { return SW_NF * CAP; }
 
+// Per-bond SW terms from r^2 and the bond vector: the unit vector u, 1/r, E = exp(gamma
+// sigma/(r - a sigma)) and dE/dr of the three-body factor, this bond's two-body share of U_i
+// (half of phi2) and of dU_i/dr_ij (half of dphi2/dr along u).
+template <typename T>
+struct SWBond {
+    T ux, uy, uz, ir, E, dE, u2, dx, dy, dz;
+};
+template <typename T>
+__device__ __forceinline__ SWBond<T> sw_bond(const SWC<T> &p, T r2, T tx, T ty, T tz)
+{
+    SWBond<T> b;
+    const T ir = M<T>::rsqrt_(r2);
+    const T r = r2 * ir;
+    b.ux = tx * ir; b.uy = ty * ir; b.uz = tz * ir; b.ir = ir;
+    const T irc = M<T>::rcp_(r - p.rc);              // 1/(r - a sigma) < 0
+    const T e2 = M<T>::sexp_(p.sig * irc);
+    b.E = M<T>::sexp_(p.gamsig * irc);
+    b.dE = -p.gamsig * irc * irc * b.E;
+    // phi2 = A eps [B (sigma/r)^p - (sigma/r)^q] exp(sigma/(r - a sigma))
+    const T sr = p.sig * ir;
+    T sp, sq;
+    if (p.p_int >= 0) sp = ipow(sr, p.p_int); else sp = M<T>::pow_(sr, p.p);
+    if (p.q_int >= 0) sq = ipow(sr, p.q_int); else sq = M<T>::pow_(sr, p.q);
+    const T poly = p.B * sp - sq;
+    const T dpoly = (-p.p * p.B * sp + p.q * sq) * ir;
+    b.u2 = T(0.5) * p.Aeps * poly * e2;
+    const T dphi = p.Aeps * (dpoly * e2 - poly * p.sig * irc * irc * e2);
+    b.dx = T(0.5) * dphi * b.ux;
+    b.dy = T(0.5) * dphi * b.uy;
+    b.dz = T(0.5) * dphi * b.uz;
+    return b;
+}
+
 // SW terms of atom i from its na bonds staged in shared-memory slot `slot` (by
 // collect_bonds): two-body and vertex three-body terms, dU_i/dr_ij per bond, U_i.
 template <typename T, int CAP, int BLOCK>
@@ -436,28 +495,14 @@ __device__ __forceinline__ void sw_terms(const PairArgs<T> &a, const SWC<T> &p, 
     Stage<T, CAP, BLOCK> S{base, slot};
     T ui = T(0);
     for (int k = 0; k < na; ++k) {
-        const T r2 = S(SW_IR, k);
-        const T ir = M<T>::rsqrt_(r2);
-        const T r = r2 * ir;
-        const T ux = S(SW_UX, k) * ir, uy = S(SW_UY, k) * ir, uz = S(SW_UZ, k) * ir;
-        S(SW_UX, k) = ux; S(SW_UY, k) = uy; S(SW_UZ, k) = uz; S(SW_IR, k) = ir;
-        const T irc = M<T>::rcp_(r - p.rc);              // 1/(r - a sigma) < 0
-        const T e2 = M<T>::sexp_(p.sig * irc);
-        const T E = M<T>::sexp_(p.gamsig * irc);
-        S(SW_E, k) = E;
-        S(SW_DE, k) = -p.gamsig * irc * irc * E;
-        // phi2 = A eps [B (sigma/r)^p - (sigma/r)^q] exp(sigma/(r - a sigma))
-        const T sr = p.sig * ir;
-        T sp, sq;
-        if (p.p_int >= 0) sp = ipow(sr, p.p_int); else sp = M<T>::pow_(sr, p.p);
-        if (p.q_int >= 0) sq = ipow(sr, p.q_int); else sq = M<T>::pow_(sr, p.q);
-        const T poly = p.B * sp - sq;
-        const T dpoly = (-p.p * p.B * sp + p.q * sq) * ir;
-        ui += T(0.5) * p.Aeps * poly * e2;
-        const T dphi = p.Aeps * (dpoly * e2 - poly * p.sig * irc * irc * e2);
-        S(SW_DX, k) = T(0.5) * dphi * ux;
-        S(SW_DY, k) = T(0.5) * dphi * uy;
-        S(SW_DZ, k) = T(0.5) * dphi * uz;
+        const SWBond<T> b = sw_bond(p, S(SW_IR, k), S(SW_UX, k), S(SW_UY, k), S(SW_UZ, k));
+        S(SW_UX, k) = b.ux; S(SW_UY, k) = b.uy; S(SW_UZ, k) = b.uz; S(SW_IR, k) = b.ir;
+        S(SW_E, k) = b.E;
+        S(SW_DE, k) = b.dE;
+        ui += b.u2;
+        S(SW_DX, k) = b.dx;
+        S(SW_DY, k) = b.dy;
+        S(SW_DZ, k) = b.dz;
     }
     // phi3 = lambda eps (cos + 1/3)^2 E(r_ij) E(r_ik), vertex i, each unordered pair once
     for (int j = 0; j < na; ++j) {
@@ -558,6 +603,75 @@ __device__ __forceinline__ void sw_block_sorted(const PairArgs<T> &a, const SWC<
     if (n_s >= 0) sw_terms<T, CAP, BLOCK>(a, p, base, i0 + slot, slot, n_s, masks[slot]);
 }
 
+// Full-capacity pass for one deferred atom (SW), one warp per atom: lane m tests list slot m
+// (lists hold at most 32), the in-cutoff slots are numbered in list order by a ballot, and
+// lane k then owns bond k: its per-bond terms, and dU_i/dr_ik from the ordered pairs (k, m),
+// m != k (the k side of each vertex three-body term; the m side is lane m's).  U_i is the
+// warp's sum in a fixed order.  sh: this warp's staging of u and E, 4 x FULL values.
+template <typename T, int FULL>
+__device__ __forceinline__ void sw_atom_warp(const PairArgs<T> &a, const SWC<T> &p, const Box &box, T (*sh)[FULL],
+                                             int64_t i, int lane)
+{
+    const int64_t N = a.N;
+    const int S_ = a.stride;
+    const int nn = a.nn[i];
+    T tx = T(0), ty = T(0), tz = T(0), r2 = T(0);
+    bool in = false;
+    if (lane < nn) {
+        bond_vector<T>(a.pos, N, a.nl[(int64_t)lane * N + i], a.pos[i], a.pos[N + i], a.pos[2 * N + i], box, tx,
+                       ty, tz);
+        r2 = bond_r2(tx, ty, tz);
+        in = r2 < p.rc2;
+    }
+    const uint32_t mask = __ballot_sync(0xffffffffu, in);
+    const int k = __popc(mask & ((1u << lane) - 1u));
+    int na = __popc(mask);
+    if (na > FULL) {
+        if (lane == 0) a.flags->active_overflow = 1;
+        na = FULL;
+    }
+    const bool mine = in && k < FULL;
+    T ui = T(0), dx = T(0), dy = T(0), dz = T(0);
+    SWBond<T> b{};
+    if (mine) {
+        a.r[(int64_t)(0 * S_ + k) * N + i] = tx;
+        a.r[(int64_t)(1 * S_ + k) * N + i] = ty;
+        a.r[(int64_t)(2 * S_ + k) * N + i] = tz;
+        b = sw_bond(p, r2, tx, ty, tz);
+        sh[0][k] = b.ux; sh[1][k] = b.uy; sh[2][k] = b.uz; sh[3][k] = b.E;
+        ui = b.u2;
+        dx = b.dx; dy = b.dy; dz = b.dz;
+    }
+    __syncwarp();
+    if (mine) {
+        // phi3 = lambda eps (cos + 1/3)^2 E(r_ik) E(r_im); its energy is counted by the
+        // lower of the two bonds
+        for (int m = 0; m < na; ++m) {
+            if (m == k) continue;
+            const T umx = sh[0][m], umy = sh[1][m], umz = sh[2][m], Em = sh[3][m];
+            const T cs = b.ux * umx + b.uy * umy + b.uz * umz;
+            const T t = cs + T(1.0 / 3.0);
+            const T EE = b.E * Em;
+            if (m > k) ui += p.lameps * t * t * EE;
+            const T q = T(2) * p.lameps * t * EE * b.ir;
+            const T c = p.lameps * t * t * b.dE * Em;
+            dx += q * (umx - cs * b.ux) + c * b.ux;
+            dy += q * (umy - cs * b.uy) + c * b.uy;
+            dz += q * (umz - cs * b.uz) + c * b.uz;
+        }
+        a.d[(int64_t)(0 * S_ + k) * N + i] = dx;
+        a.d[(int64_t)(1 * S_ + k) * N + i] = dy;
+        a.d[(int64_t)(2 * S_ + k) * N + i] = dz;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ui += __shfl_xor_sync(0xffffffffu, ui, o);
+    if (lane == 0) {
+        a.mask[i] = mask;
+        a.u[i] = to_d(ui);
+    }
+    __syncwarp();   // the staging is reused by the warp's next atom
+}
+
 template <typename T>
 struct TersoffSets {
     TersoffC<T> s[kMaxSets];
@@ -638,6 +752,31 @@ __global__ void __launch_bounds__(BLOCK) k_pair_sw(PairArgs<T> a, SWSets<T> ps)
         });
     }
 }
+
+// Full-capacity pass (SW): WARPS warps per block, each taking deferred atoms in turn.
+// Deferred atoms are few (a fraction of a percent at room temperature) and heavy: one
+// thread per atom would leave them to a handful of warps on a few SMs.
+template <typename T, int FULL, int WARPS, bool BATCH>
+__global__ void __launch_bounds__(32 * WARPS) k_pair_sw_warp(PairArgs<T> a, SWSets<T> ps)
+{
+    __shared__ T sh[WARPS][4][FULL];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int cnt = *a.ovf_count;
+    for (int q = blockIdx.x * WARPS + w; q < cnt; q += gridDim.x * WARPS) {
+        const int64_t i = a.ovf_list[q];
+        if (BATCH) {
+            const SysDev &sd = a.sys[a.sys_of[i]];
+            if (!system_live(sd, a.flags)) continue;
+            sw_atom_warp<T, FULL>(a, ps.s[sd.pset], sd.box, sh[w], i, lane);
+        } else if (a.dev_box) {
+            const Box bx = a.sys[0].box;
+            sw_atom_warp<T, FULL>(a, ps.s[0], bx, sh[w], i, lane);
+        } else {
+            sw_atom_warp<T, FULL>(a, ps.s[0], a.box, sh[w], i, lane);
+        }
+    }
+}
+constexpr int kSwFullWarps = 4;
 
 __global__ void k_pair_reset(int *ovf_count) { *ovf_count = 0; }
 
@@ -1152,8 +1291,9 @@ void set_smem()
 {
     cudaFuncSetAttribute(k_pair_tersoff<T, CAP, BLOCK, FULL_CAP, BATCH>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_for<T, CAP, BLOCK>(1));
-    cudaFuncSetAttribute(k_pair_sw<T, CAP, BLOCK, FULL_CAP, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem_for<T, CAP, BLOCK>(2));
+    if constexpr (!FULL_CAP)
+        cudaFuncSetAttribute(k_pair_sw<T, CAP, BLOCK, FULL_CAP, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_for<T, CAP, BLOCK>(2));
     if constexpr (!BATCH)
         cudaFuncSetAttribute(k_pair_tersoff<T, CAP, BLOCK, FULL_CAP, false, true>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_for<T, CAP, BLOCK>(1));
@@ -1233,8 +1373,7 @@ void pair_launch_b(const Plan &p, cudaStream_t s, int list, int parts)
         if (parts & PAIR_FAST)
             k_pair_sw<T, kPairCapSmallSW<T>, B, false, BATCH><<<nb, B, smem_for<T, kPairCapSmallSW<T>, B>(2), s>>>(a, c);
         if (parts & PAIR_DEFERRED)
-            k_pair_sw<T, FULL, kPairBlockFull, true, BATCH>
-                <<<(unsigned)nbf, kPairBlockFull, smem_for<T, FULL, kPairBlockFull>(2), s>>>(a, c);
+            k_pair_sw_warp<T, FULL, kSwFullWarps, BATCH><<<(unsigned)nbf, 32 * kSwFullWarps, 0, s>>>(a, c);
     }
 }
 

@@ -72,13 +72,15 @@ def test_compute_fp64_matches_oracle(md, name, make):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-def test_atoms_with_many_bonds_take_the_full_capacity_pass(md, precision):
+@pytest.mark.parametrize("lattice", ["jittered", "compressed"])
+def test_atoms_with_many_bonds_take_the_full_capacity_pass(md, precision, lattice):
     """Atoms with more in-cutoff bonds than the common-case pass stages (SW: 8) are deferred
-    to the full-capacity pass.  fp64: jittered SW silicon puts up to 10 neighbours inside
-    the cutoff (some atoms deferred); fp32: SW silicon compressed to a = 5.1 A brings the
-    12-atom second shell (3.61 A) inside the 3.77 A cutoff, 16 bonds per atom (all atoms
-    deferred)."""
-    if precision == 0:
+    to the full-capacity pass (one warp per atom).  Jittered SW silicon puts up to 10
+    neighbours inside the cutoff (some atoms deferred, the rest in the common pass: every
+    bond between the two passes must be seen from both ends); silicon compressed to
+    a = 5.1 A brings the 12-atom second shell (3.61 A) inside the 3.77 A cutoff, 16 bonds
+    per atom (all atoms deferred)."""
+    if lattice == "jittered":
         s = I.si_diamond_sw(n=5, jitter_amp=0.1)
     else:
         s = I.si_diamond_sw(n=5, a=5.1, jitter_amp=0.05)
@@ -86,9 +88,36 @@ def test_atoms_with_many_bonds_take_the_full_capacity_pass(md, precision):
     with md.from_inputs(s, precision=precision) as g:
         out = g.compute()
         st = g.stats()
-    assert st.pair_deferred > 10
+    if lattice == "jittered":
+        assert 10 < st.pair_deferred < s.n // 2
+    else:
+        assert st.pair_deferred == s.n
     tol = FP64_TOL if precision == 0 else MIXED_TOL
-    assert rel(out["F"], ref["F"]) < tol and rel(out["U"], ref["U"]) < tol
+    for k in ("F", "U", "W", "J"):
+        assert rel(out[k], ref[k]) < tol, k
+    # Newton's third law across the two passes: a bond seen from one end only would leave a
+    # residue of the order of one bond's force; fp32 per-atom sums leave ~1e-7 of it
+    newton = 1e-11 if precision == 0 else MIXED_TOL
+    assert np.abs(out["F"].sum(axis=0)).max() < newton * np.abs(out["F"]).max()
+
+
+def test_trajectory_with_deferred_atoms_matches_oracle(md):
+    """NVE steps of hot SW silicon in which a few atoms per step go to the full-capacity
+    pass: positions, velocities and the U, K, J series against the oracle."""
+    s = I.si_diamond_sw(n=5, jitter_amp=0.1, temperature=900.0, seed_pos=7, seed_vel=8)
+    steps, dt = 30, 1.0
+    with md.from_inputs(s) as g:
+        g.compute()
+        assert g.stats().pair_deferred > 0
+        ser = g.run(steps, dt)
+        pos, vel = g.state()
+    p2, v2, ser2 = O.run(s.pos, s.vel, s.mass, s.box, s.pbc, s.kind, s.params, steps, dt)
+    d = pos - p2
+    d -= np.round(d / s.box) * s.box * s.pbc
+    assert np.abs(d).max() < TRAJ_TOL
+    assert rel(vel, v2) < TRAJ_TOL
+    for c in range(5):
+        assert rel(ser[:, c], ser2[:, c]) < TRAJ_TOL, c
 
 
 @pytest.mark.parametrize("name,make", CASES[:6], ids=[c[0] for c in CASES[:6]])

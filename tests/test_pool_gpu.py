@@ -144,6 +144,25 @@ def test_damped_relaxation_matches_oracle(md):
     assert np.abs(d).max() < TRAJ_TOL and rel(v, v_ref) < TRAJ_TOL
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_sw_pool_with_deferred_atoms_matches_standalone(md, precision):
+    """Hot, jittered SW cells whose heaviest atoms go to the full-capacity pass (one warp per
+    atom, in a pool over the flattened index): bit for bit what each system gives alone."""
+    systems = [I.si_diamond_sw(n=4, jitter_amp=0.12, temperature=900.0, seed_pos=k, seed_vel=k + 1)
+               for k in (11, 13)]
+    systems.append(I.si_diamond_sw(n=3, jitter_amp=0.12, temperature=900.0, seed_pos=15, seed_vel=16))
+    with md.from_inputs(systems[0], precision=precision) as g:
+        g.compute()
+        assert g.stats().pair_deferred > 0
+    with md.Pool(4000, 4, I.MD_SW, [I.SW_SI_1985], [I.MASS_SI], precision=precision) as pool:
+        ids = [pool.add(s.pos, s.vel, s.box, s.pbc) for s in systems]
+        pool.run(12, 1.0)
+        for s, sid in zip(systems, ids):
+            (p1, v1), _ = standalone(md, s, 12, 1.0, precision=precision)
+            p2, v2 = pool.state(sid)
+            assert np.array_equal(p1, p2) and np.array_equal(v1, v2)
+
+
 def test_sw_pool_matches_standalone(md):
     systems = [I.si_diamond_sw(n=3, jitter_amp=0.05, seed_pos=k, seed_vel=k + 1) for k in (1, 3)]
     systems.append(I.si_diamond_sw(n=4, jitter_amp=0.05, seed_pos=5, seed_vel=6))
