@@ -51,9 +51,9 @@ TERSOFF_FLOP_PER_BOND = 159.316
 TERSOFF_FLOP_PER_BOND_PAIR = 32.250
 SW_FLOP_PER_BOND = 92.859
 SW_FLOP_PER_BOND_PAIR = 27.398
-# DRAM bytes (read + write) of one fp64 pair launch, from the ncu capture of the current
-# kernel on each workload.
-PAIR_TRAFFIC_BYTES = {"tersoff_c_graphene_1M": 140.43e6, "tersoff_si_216k": 9.71e6, "sw_si_512k": None}
+# DRAM bytes (read + write) of one fp64 pair pass (SW: the common-case and full-capacity
+# launches of one step at 300 K), from the ncu capture of the current kernels.
+PAIR_TRAFFIC_BYTES = {"tersoff_c_graphene_1M": 140.43e6, "tersoff_si_216k": 9.71e6, "sw_si_512k": 202.65e6}
 
 
 def load_peaks():
