@@ -426,8 +426,9 @@ md_status md_hcacf(const double *j, int64_t n_rows, int64_t row_stride, int64_t 
  * that the pair passes use in place of the CUDA math library: the table-driven exponential
  * (fn = 0) or logarithm (fn = 1) (P. T. P. Tang's table-driven method; exp within 2 ulp for
  * |x| <= 708, log to about 1e-16 (1 + |binary exponent of x|) absolute for positive normal
- * x), or the reciprocal (fn = 2: fp32 seed and two Newton steps, within 1 ulp for
- * 1.2e-38 < |x| < 8.5e37).  x, y: n host doubles.  Returns 0, -1 for bad arguments, -5 on
+ * x), the reciprocal (fn = 2: fp32 seed and one third-order step, within 1 ulp for
+ * 1.2e-38 < |x| < 8.5e37) or the reciprocal square root (fn = 3: fp32 seed and one
+ * third-order step, within 1 ulp for 1.2e-38 < x < 3.4e38).  x, y: n host doubles.  Returns 0, -1 for bad arguments, -5 on
  * a CUDA error.
  * Allocates and frees its own device scratch. */
 int md_fastmath_eval(int fn, int64_t n, const double *x, double *y);

@@ -41,7 +41,7 @@ template <typename T> struct M;
 // arguments stay inside the table-driven routines' domain (fastmath.cuh); tlog1p_ needs
 // only absolute accuracy (it enters b = exp(-log(1 + x)/(2n))).
 template <> struct M<double> {
-    static __device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
+    static __device__ __forceinline__ double rsqrt_(double x) { return rsqrt_nr(x); }
     static __device__ __forceinline__ double exp_(double x) { return exp(x); }
     static __device__ __forceinline__ double log_(double x) { return log(x); }
     static __device__ __forceinline__ double log1p_(double x) { return log1p(x); }
@@ -50,7 +50,7 @@ template <> struct M<double> {
     static __device__ __forceinline__ double tlog1p_(double x) { return log_tab(1.0 + x); }
     // SW: exp(sigma/(r - a sigma)) and exp(gamma sigma/(r - a sigma)) go to -infinity at the
     // cutoff; below -700 the factor is < 1e-304 and is taken as e^-700
-    static __device__ __forceinline__ double sexp_(double x) { return exp_tab(fmax(x, -700.0)); }
+    static __device__ __forceinline__ double sexp_(double x) { return exp_tab(clamp_neg700(x)); }
     static __device__ __forceinline__ double rcp_(double x) { return rcp_nr(x); }
     static __device__ __forceinline__ void sincos_(double x, double *s, double *c) { sincos(x, s, c); }
     static __device__ __forceinline__ double pow_(double x, double y) { return pow(x, y); }
@@ -133,18 +133,11 @@ __device__ __forceinline__ T bond_r2(T x, T y, T z)
 
 // fp64 bond vector r_j - r_i of list entry e (image shift from the entry), in type T
 template <typename T>
-__device__ __forceinline__ void bond_vector(const double *pos, int64_t N, int e, double xi, double yi, double zi,
-                                            const Box &box, T &tx, T &ty, T &tz)
+__device__ __forceinline__ void bond_vector_t(const double *pos, int64_t N, int64_t i, int e, double xi, double yi,
+                                              double zi, const Box &box, T &tx, T &ty, T &tz)
 {
-    const int j = list_atom(e);
-    double dx = pos[j] - xi, dy = pos[N + j] - yi, dz = pos[2 * N + j] - zi;
-    const int code = list_code(e);
-    if (code != kNoShift) {
-        const int sx = code % 3 - 1, sy = (code / 3) % 3 - 1, sz = code / 9 - 1;
-        if (sx) dx += sx > 0 ? box.L[0] : -box.L[0];
-        if (sy) dy += sy > 0 ? box.L[1] : -box.L[1];
-        if (sz) dz += sz > 0 ? box.L[2] : -box.L[2];
-    }
+    double dx, dy, dz;
+    bond_vector(pos, N, i, e, box, xi, yi, zi, dx, dy, dz);
     tx = to_t<T>(dx); ty = to_t<T>(dy); tz = to_t<T>(dz);
 }
 
@@ -239,7 +232,7 @@ __device__ __forceinline__ int collect_bonds(const PairArgs<T> &a, int64_t i, co
                 tj = a.type[list_atom(e[q])];
                 cut2 = row[tj].rc2;
             }
-            if (r2 < cut2) {
+            if (lt_nonneg(r2, cut2)) {
                 if (na < CAP) {
                     S.set(fx, na, tx); S.set(fy, na, ty); S.set(fz, na, tz); S.set(fr2, na, r2);
                     if (MULTI) S.set(ftype, na, T(tj));
@@ -289,7 +282,7 @@ __device__ __forceinline__ void tersoff_g(const TersoffC<T> &p, T cs, T inv, T &
 template <typename T>
 __device__ __forceinline__ void tersoff_b(const TersoffC<T> &p, T zeta, T &b, T &db)
 {
-    if (!(zeta > T(0)) || p.beta_zero) {
+    if (!positive_nonneg(zeta) || p.beta_zero) {
         b = T(1);
         db = T(0);
         return;
@@ -356,7 +349,7 @@ __device__ __forceinline__ void tersoff_atom(const PairArgs<T> &a, const Tersoff
         // f_C = 1/2 + 1/2 cos(x) = cos^2(x/2), f_C' = -(pi/(S-R)) sin(x/2) cos(x/2),
         // x = pi (r-R)/(S-R): the half-angle form has no cancellation as f_C -> 0 near S
         T fc = T(1), dfc = T(0);
-        if (r >= pk.R) {
+        if (!lt_nonneg(r, pk.R)) {
             T sn, cn;
             M<T>::sincos_(T(0.5) * pk.pi_SR * (r - pk.R), &sn, &cn);
             fc = cn * cn;
@@ -618,10 +611,10 @@ __device__ __forceinline__ void sw_atom_warp(const PairArgs<T> &a, const SWC<T> 
     T tx = T(0), ty = T(0), tz = T(0), r2 = T(0);
     bool in = false;
     if (lane < nn) {
-        bond_vector<T>(a.pos, N, a.nl[(int64_t)lane * N + i], a.pos[i], a.pos[N + i], a.pos[2 * N + i], box, tx,
-                       ty, tz);
+        bond_vector_t<T>(a.pos, N, i, a.nl[(int64_t)lane * N + i], a.pos[i], a.pos[N + i], a.pos[2 * N + i], box,
+                         tx, ty, tz);
         r2 = bond_r2(tx, ty, tz);
-        in = r2 < p.rc2;
+        in = lt_nonneg(r2, p.rc2);
     }
     const uint32_t mask = __ballot_sync(0xffffffffu, in);
     const int k = __popc(mask & ((1u << lane) - 1u));
@@ -1449,7 +1442,7 @@ namespace {
 __global__ void k_fastmath_eval(int fn, int64_t n, const double *x, double *y)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) y[i] = fn == 0 ? exp_tab(x[i]) : (fn == 1 ? log_tab(x[i]) : rcp_nr(x[i]));
+    if (i < n) y[i] = fn == 0 ? exp_tab(x[i]) : (fn == 1 ? log_tab(x[i]) : (fn == 2 ? rcp_nr(x[i]) : rsqrt_nr(x[i])));
 }
 }  // namespace
 
@@ -1614,7 +1607,7 @@ int gather_blocks(int64_t N) { return N == 0 ? 1 : (int)blocks_for(N, kGatherBlo
 // error.
 extern "C" int md_fastmath_eval(int fn, int64_t n, const double *x, double *y)
 {
-    if (fn < 0 || fn > 2 || n < 0 || (n > 0 && (!x || !y))) return -1;
+    if (fn < 0 || fn > 3 || n < 0 || (n > 0 && (!x || !y))) return -1;
     if (n == 0) return 0;
     double *d = nullptr;
     if (cudaMalloc(&d, sizeof(double) * 2 * (size_t)n) != cudaSuccess) {

@@ -288,7 +288,8 @@ def md_get_box(ctx, system=0) -> np.ndarray:
 
 
 def md_fastmath_eval(fn: int, x) -> np.ndarray:
-    """The pair pass's fp64 exp (fn 0), log (fn 1) or reciprocal (fn 2), evaluated on the GPU."""
+    """The pair pass's fp64 exp (fn 0), log (fn 1), reciprocal (fn 2) or reciprocal square
+    root (fn 3), evaluated on the GPU."""
     lib = load()
     x = np.ascontiguousarray(x, dtype=np.float64)
     y = np.empty_like(x)

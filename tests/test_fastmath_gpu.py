@@ -1,8 +1,9 @@
 """The fp64 routines of the pair passes (fastmath.cuh) against numpy on the host: the
 table-driven exp (Tang's method) within 2 ulp over the pair pass's domain and beyond, the
-table-driven log within an absolute 2e-16 (1 + |binary exponent|), the Newton reciprocal
-within 1 ulp (of the correctly rounded 1/x) for 1.2e-38 < |x| < 8.5e37, including table and interval
-boundaries, powers of two, values next to 1 and the range ends."""
+table-driven log within an absolute 2e-16 (1 + |binary exponent|), the reciprocal within 1 ulp
+(of the correctly rounded 1/x) for 1.2e-38 < |x| < 8.5e37 and the reciprocal square root
+within 1 ulp for 1.2e-38 < x < 3.4e38 (each an fp32 seed and one third-order step), including
+table and interval boundaries, powers of two, values next to 1 and the range ends."""
 import numpy as np
 import pytest
 
@@ -76,3 +77,23 @@ def test_reciprocal_within_one_ulp(md):
     y = md.md_fastmath_eval(2, x)
     e = ulp_err(y, 1.0 / x)
     assert e.max() <= 1.0, (x[np.argmax(e)], e.max())
+
+
+def test_reciprocal_sqrt_within_one_ulp(md):
+    """1/sqrt(x) against the value computed in extended precision (np.longdouble), over the
+    bonds' r^2, decades of the fp32-normal range, powers of two and their neighbours."""
+    rng = np.random.Generator(np.random.PCG64(4))
+    x = np.concatenate([
+        rng.uniform(0.5, 16.0, 400000),                     # r^2 of bonds (A^2)
+        np.exp(rng.uniform(-85.0, 85.0, 200000)),
+        2.0 ** np.arange(-125, 127, dtype=np.float64),
+        np.nextafter(2.0 ** np.arange(-125, 127, dtype=np.float64), 0.0),
+        np.nextafter(2.0 ** np.arange(-125, 127, dtype=np.float64), np.inf),
+        [1.0, 2.0, 3.0, 4.0, 1.2e-38, 3.0e38, 2.25, 5.29],
+    ])
+    y = md.md_fastmath_eval(3, x)
+    ref = (1.0 / np.sqrt(x.astype(np.longdouble)))
+    e = np.abs(y.astype(np.longdouble) - ref) / np.spacing(ref.astype(np.float64)).astype(np.longdouble)
+    e = e.astype(np.float64)
+    assert e.max() <= 1.0, (x[np.argmax(e)], e.max())
+    assert np.median(e) <= 0.5
