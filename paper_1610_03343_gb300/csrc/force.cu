@@ -273,8 +273,18 @@ template <typename T>
 __device__ __forceinline__ void tersoff_g(const TersoffC<T> &p, T cs, T inv, T &g, T &dg)
 {
     const T hc = p.h - cs;
-    g = T(1) + p.c2d2 * hc * hc * inv;
-    dg = T(-2) * p.c2 * hc * inv * inv;
+    const T t = hc * inv;                                // (h - cos)/den
+    g = fma(p.c2d2 * hc, t, T(1));
+    dg = T(-2) * p.c2 * t * inv;
+}
+
+// f_C' is +0 exactly for a bond below R (f_C = 1 there) and <= -0 inside the switching
+// region: the bit pattern tells them apart on the integer pipe
+template <typename T>
+__device__ __forceinline__ bool no_switch(T dfc)
+{
+    if constexpr (sizeof(T) == 8) return __double_as_longlong(dfc) == 0;
+    else return __float_as_int(dfc) == 0;
 }
 
 // b = (1 + (beta zeta)^n)^(-1/(2n)) (Eq. 3) and db/dzeta = -1/2 b x / (zeta (1 + x)),
@@ -390,14 +400,22 @@ __device__ __forceinline__ void tersoff_atom(const PairArgs<T> &a, const Tersoff
         T b, db;
         tersoff_b(p, S(TF_Z, k), b, db);
         const T fc = S(TF_FC, k), dfc = S(TF_DFC, k), fr = S(TF_FR, k), fa = S(TF_FA, k);
-        ui += T(0.5) * fc * (fr - b * fa);
-        const T dR = dfc * fr - pk.lam * fc * fr;   // (f_C f_R)'
-        const T dA = dfc * fa - pk.mu * fc * fa;    // (f_C f_A)'
-        const T radial = T(0.5) * (dR - b * dA);
+        T radial;
+        if (no_switch(dfc)) {
+            // f_C = 1, f_C' = 0: the same arithmetic without the unit factors and zero terms
+            ui += T(0.5) * (fr - b * fa);
+            radial = T(0.5) * (-pk.lam * fr + b * (pk.mu * fa));
+            S(TF_Z, k) = T(-0.5) * fa * db;
+        } else {
+            ui += T(0.5) * fc * (fr - b * fa);
+            const T dR = dfc * fr - pk.lam * fc * fr;   // (f_C f_R)'
+            const T dA = dfc * fa - pk.mu * fc * fa;    // (f_C f_A)'
+            radial = T(0.5) * (dR - b * dA);
+            S(TF_Z, k) = T(-0.5) * fc * fa * db;
+        }
         S(TF_DX, k) = radial * S(TF_UX, k);
         S(TF_DY, k) = radial * S(TF_UY, k);
         S(TF_DZ, k) = radial * S(TF_UZ, k);
-        S(TF_Z, k) = T(-0.5) * fc * fa * db;
     }
     // angular part: for each unordered pair (j,k), with dcos_j = (u_k - cos u_j)/r_ij,
     //   d_j += (P_j fc_k + P_k fc_j) g' dcos_j + P_k fc'_j g u_j   (and j <-> k)
@@ -418,11 +436,19 @@ __device__ __forceinline__ void tersoff_atom(const PairArgs<T> &a, const Tersoff
                 cs = ujx * ukx + ujy * uky + ujz * ukz;
                 tersoff_g(p, cs, PCS(q), g, dg);
             }
-            const T Q = (Pj * fck + Pk * fcj) * dg;
-            const T cj = Pk * dfcj * g, ck = Pj * dfck * g;
-            const T qj = Q * irj, qk = Q * irk;
             // d_j += qj (u_k - cos u_j) + cj u_j, written as qj u_k + (cj - qj cos) u_j
-            const T aj = cj - qj * cs, ak = ck - qk * cs;
+            T qj, qk, aj, ak;
+            if (no_switch(dfcj) && no_switch(dfck)) {
+                // both below R: f_C = 1, f_C' = 0
+                const T Q = (Pj + Pk) * dg;
+                qj = Q * irj; qk = Q * irk;
+                aj = -qj * cs; ak = -qk * cs;
+            } else {
+                const T Q = (Pj * fck + Pk * fcj) * dg;
+                const T cj = Pk * dfcj * g, ck = Pj * dfck * g;
+                qj = Q * irj; qk = Q * irk;
+                aj = cj - qj * cs; ak = ck - qk * cs;
+            }
             djx += qj * ukx + aj * ujx;
             djy += qj * uky + aj * ujy;
             djz += qj * ukz + aj * ujz;
