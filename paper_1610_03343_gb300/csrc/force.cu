@@ -90,7 +90,7 @@ struct Stage {
 // Potential constants in the pair pass's arithmetic type (no conversions in the loops).
 template <typename T>
 struct TersoffC {
-    T A, B, lam, mu, n, c2, d2, c2d2, h, R, pi_SR, ln_beta, inv2n;
+    T A, B, lam, mu, n, c2, d2, c2d2, h, R, pi_SR, n_ln_beta, inv2n;   // n_ln_beta = n log(beta)
     T rc2;   // S^2
     int beta_zero;
 };
@@ -100,7 +100,7 @@ TersoffC<T> tersoff_const(const TersoffP &p)
     TersoffC<T> c;
     c.A = T(p.A); c.B = T(p.B); c.lam = T(p.lam); c.mu = T(p.mu); c.n = T(p.n);
     c.c2 = T(p.c2); c.d2 = T(p.d2); c.c2d2 = T(p.c2d2); c.h = T(p.h); c.R = T(p.R);
-    c.pi_SR = T(p.pi_SR); c.ln_beta = T(p.ln_beta); c.inv2n = T(p.inv2n);
+    c.pi_SR = T(p.pi_SR); c.n_ln_beta = T(p.n * p.ln_beta); c.inv2n = T(p.inv2n);
     c.rc2 = T(p.S * p.S);
     c.beta_zero = p.beta_zero;
     return c;
@@ -297,7 +297,7 @@ __device__ __forceinline__ void tersoff_b(const TersoffC<T> &p, T zeta, T &b, T 
         db = T(0);
         return;
     }
-    const T x = M<T>::texp_(p.n * (M<T>::tlog_(zeta) + p.ln_beta));
+    const T x = M<T>::texp_(fma(p.n, M<T>::tlog_(zeta), p.n_ln_beta));   // (beta zeta)^n
     b = M<T>::texp_(-p.inv2n * M<T>::tlog1p_(x));
     db = T(-0.5) * b * x * M<T>::rcp_(zeta * (T(1) + x));
 }
@@ -963,7 +963,7 @@ __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, i
             }
             ++k;
         }
-        if (!(isfinite(f0) && isfinite(f1) && isfinite(f2))) a.flags->nonfinite = 1;
+        if (!(finite_bits(f0) && finite_bits(f1) && finite_bits(f2))) a.flags->nonfinite = 1;
         const double F[3] = {to_d(f0), to_d(f1), to_d(f2)};
         a.force[i] = F[0];
         a.force[N + i] = F[1];
@@ -987,7 +987,7 @@ __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, i
                     vn[c] = fma(h, F[c], v[c]);
                     const double x = fma(a.dt, vn[c], a.pos[c * N + i]);
                     a.pos[c * N + i] = x;
-                    if (a.posf) a.posf[c * N + i] = (float)x;
+                    if (a.posf) a.posf[c * N + i] = d2f_trunc(x);
                     const float d = d2f_trunc(x - a.pos_build[c * N + i]);
                     d2 = fmaf(d, d, d2);
                 }
@@ -1187,7 +1187,7 @@ __device__ __forceinline__ void kick_drift_atom(const KickDriftArgs &a, int64_t 
         const double x = fma(a.dt, v, x0);
         a.vel[c * N + i] = v;
         a.pos[c * N + i] = x;
-        if (a.posf) a.posf[c * N + i] = (float)x;
+        if (a.posf) a.posf[c * N + i] = d2f_trunc(x);
         const float d = d2f_trunc(x - xb);
         d2 = fmaf(d, d, d2);
     }

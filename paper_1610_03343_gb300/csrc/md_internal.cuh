@@ -246,6 +246,15 @@ __device__ __forceinline__ float d2f_trunc(double d)
     const unsigned f = a >= 0x38100000u ? (((a - 0x38000000u) << 3) | (lo >> 29)) : 0u;
     return __uint_as_float(s | f);
 }
+// x is finite (exponent field not all ones), tested on the integer pipe
+__device__ __forceinline__ bool finite_bits(double x)
+{
+    return ((unsigned)__double2hiint(x) & 0x7ff00000u) != 0x7ff00000u;
+}
+__device__ __forceinline__ bool finite_bits(float x)
+{
+    return (__float_as_uint(x) & 0x7f800000u) != 0x7f800000u;
+}
 // x in the pair pass's type T, and back to fp64 (identities for T = double)
 template <typename T> __device__ __forceinline__ T to_t(double x);
 template <> __device__ __forceinline__ double to_t<double>(double x) { return x; }
