@@ -393,7 +393,10 @@ __device__ __forceinline__ void tersoff_atom(const PairArgs<T> &a, const Tersoff
         }
         S(TF_Z, j) = zj;
     }
-    // bond orders, U_i, radial part of dU_i/dr_ij; P_k = -1/2 f_C f_A b'_k kept in TF_Z
+    // bond orders, U_i, radial part of dU_i/dr_ij; P_k = -1/2 f_C f_A b'_k kept in TF_Z.
+    // dU_i/dr_ij is assembled as A_j u_j + V_j: the scalar A_j (radial part plus the
+    // angular terms along u_j) in TF_FR, the vector V_j (angular terms along the other
+    // bonds) in TF_DX..TF_DZ.
     T ui = T(0);
     for (int k = 0; k < na; ++k) {
         const TersoffC<T> &pk = bond_const<MULTI>(p, row, MULTI ? S(TF_DX, k) : T(0));
@@ -413,16 +416,19 @@ __device__ __forceinline__ void tersoff_atom(const PairArgs<T> &a, const Tersoff
             radial = T(0.5) * (dR - b * dA);
             S(TF_Z, k) = T(-0.5) * fc * fa * db;
         }
-        S(TF_DX, k) = radial * S(TF_UX, k);
-        S(TF_DY, k) = radial * S(TF_UY, k);
-        S(TF_DZ, k) = radial * S(TF_UZ, k);
+        S(TF_FR, k) = radial;
+        S(TF_DX, k) = T(0);
+        S(TF_DY, k) = T(0);
+        S(TF_DZ, k) = T(0);
     }
     // angular part: for each unordered pair (j,k), with dcos_j = (u_k - cos u_j)/r_ij,
-    //   d_j += (P_j fc_k + P_k fc_j) g' dcos_j + P_k fc'_j g u_j   (and j <-> k)
+    //   d_j += (P_j fc_k + P_k fc_j) g' dcos_j + P_k fc'_j g u_j   (and j <-> k),
+    // i.e. V_j += q_j u_k and A_j += c_j - q_j cos, q_j = (P_j fc_k + P_k fc_j) g'/r_ij
     for (int j = 0; j < na; ++j) {
         const T ujx = S(TF_UX, j), ujy = S(TF_UY, j), ujz = S(TF_UZ, j);
         const T irj = S(TF_IR, j), fcj = S(TF_FC, j), dfcj = S(TF_DFC, j), Pj = S(TF_Z, j);
-        T djx = S(TF_DX, j), djy = S(TF_DY, j), djz = S(TF_DZ, j);
+        T Aj = S(TF_FR, j);
+        T vjx = S(TF_DX, j), vjy = S(TF_DY, j), vjz = S(TF_DZ, j);
         for (int k = j + 1; k < na; ++k) {
             const T ukx = S(TF_UX, k), uky = S(TF_UY, k), ukz = S(TF_UZ, k);
             const T irk = S(TF_IR, k), fck = S(TF_FC, k), dfck = S(TF_DFC, k), Pk = S(TF_Z, k);
@@ -436,29 +442,30 @@ __device__ __forceinline__ void tersoff_atom(const PairArgs<T> &a, const Tersoff
                 cs = ujx * ukx + ujy * uky + ujz * ukz;
                 tersoff_g(p, cs, PCS(q), g, dg);
             }
-            // d_j += qj (u_k - cos u_j) + cj u_j, written as qj u_k + (cj - qj cos) u_j
-            T qj, qk, aj, ak;
+            T qj, qk;
             if (no_switch(dfcj) && no_switch(dfck)) {
                 // both below R: f_C = 1, f_C' = 0
                 const T Q = (Pj + Pk) * dg;
                 qj = Q * irj; qk = Q * irk;
-                aj = -qj * cs; ak = -qk * cs;
+                Aj = fma(-qj, cs, Aj);
+                S(TF_FR, k) = fma(-qk, cs, S(TF_FR, k));
             } else {
                 const T Q = (Pj * fck + Pk * fcj) * dg;
                 const T cj = Pk * dfcj * g, ck = Pj * dfck * g;
                 qj = Q * irj; qk = Q * irk;
-                aj = cj - qj * cs; ak = ck - qk * cs;
+                Aj += cj - qj * cs;
+                S(TF_FR, k) += ck - qk * cs;
             }
-            djx += qj * ukx + aj * ujx;
-            djy += qj * uky + aj * ujy;
-            djz += qj * ukz + aj * ujz;
-            S(TF_DX, k) += qk * ujx + ak * ukx;
-            S(TF_DY, k) += qk * ujy + ak * uky;
-            S(TF_DZ, k) += qk * ujz + ak * ukz;
+            vjx = fma(qj, ukx, vjx);
+            vjy = fma(qj, uky, vjy);
+            vjz = fma(qj, ukz, vjz);
+            S(TF_DX, k) = fma(qk, ujx, S(TF_DX, k));
+            S(TF_DY, k) = fma(qk, ujy, S(TF_DY, k));
+            S(TF_DZ, k) = fma(qk, ujz, S(TF_DZ, k));
         }
-        a.d[(int64_t)(0 * S_ + j) * N + i] = djx;
-        a.d[(int64_t)(1 * S_ + j) * N + i] = djy;
-        a.d[(int64_t)(2 * S_ + j) * N + i] = djz;
+        a.d[(int64_t)(0 * S_ + j) * N + i] = fma(Aj, ujx, vjx);
+        a.d[(int64_t)(1 * S_ + j) * N + i] = fma(Aj, ujy, vjy);
+        a.d[(int64_t)(2 * S_ + j) * N + i] = fma(Aj, ujz, vjz);
     }
     a.mask[i] = mask;
     a.u[i] = to_d(ui);
