@@ -545,12 +545,14 @@ __device__ __forceinline__ void sw_terms(const PairArgs<T> &a, const SWC<T> &p, 
             const T c1 = T(2) * p.lameps * t * EE;
             const T cj = p.lameps * t * t * dEj * Ek, ck = p.lameps * t * t * Ej * dEk;
             const T qj = c1 * irj, qk = c1 * irk;
-            djx += qj * (ukx - cs * ujx) + cj * ujx;
-            djy += qj * (uky - cs * ujy) + cj * ujy;
-            djz += qj * (ukz - cs * ujz) + cj * ujz;
-            S(SW_DX, k) += qk * (ujx - cs * ukx) + ck * ukx;
-            S(SW_DY, k) += qk * (ujy - cs * uky) + ck * uky;
-            S(SW_DZ, k) += qk * (ujz - cs * ukz) + ck * ukz;
+            // d_j += qj (u_k - cos u_j) + cj u_j, written as qj u_k + (cj - qj cos) u_j
+            const T aj = fma(-qj, cs, cj), ak = fma(-qk, cs, ck);
+            djx = fma(qj, ukx, fma(aj, ujx, djx));
+            djy = fma(qj, uky, fma(aj, ujy, djy));
+            djz = fma(qj, ukz, fma(aj, ujz, djz));
+            S(SW_DX, k) = fma(qk, ujx, fma(ak, ukx, S(SW_DX, k)));
+            S(SW_DY, k) = fma(qk, ujy, fma(ak, uky, S(SW_DY, k)));
+            S(SW_DZ, k) = fma(qk, ujz, fma(ak, ukz, S(SW_DZ, k)));
         }
         a.d[(int64_t)(0 * S_ + j) * N + i] = djx;
         a.d[(int64_t)(1 * S_ + j) * N + i] = djy;
@@ -681,9 +683,10 @@ __device__ __forceinline__ void sw_atom_warp(const PairArgs<T> &a, const SWC<T> 
             if (m > k) ui += p.lameps * t * t * EE;
             const T q = T(2) * p.lameps * t * EE * b.ir;
             const T c = p.lameps * t * t * b.dE * Em;
-            dx += q * (umx - cs * b.ux) + c * b.ux;
-            dy += q * (umy - cs * b.uy) + c * b.uy;
-            dz += q * (umz - cs * b.uz) + c * b.uz;
+            const T ac = fma(-q, cs, c);   // q (u_m - cos u_k) + c u_k = q u_m + (c - q cos) u_k
+            dx = fma(q, umx, fma(ac, b.ux, dx));
+            dy = fma(q, umy, fma(ac, b.uy, dy));
+            dz = fma(q, umz, fma(ac, b.uz, dz));
         }
         a.d[(int64_t)(0 * S_ + k) * N + i] = dx;
         a.d[(int64_t)(1 * S_ + k) * N + i] = dy;
