@@ -42,18 +42,18 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # FP64 flops of the fp64 pair pass, counted with ncu's instruction counters (DADD + DMUL +
 # 2 DFMA, which include the fp64 instruction sequences of the table-driven exp and log, the
 # Newton reciprocal and the square root), per in-cutoff bond and per ordered pair of bonds
-# (j, k != j) of one atom.  Tersoff: fit to the C sheet (3 bonds per atom, 572.449 flop/atom)
-# and Si diamond (4 bonds, 870.266 flop/atom).  SW: fit to the Si diamond lattice (4 bonds,
-# 12 ordered pairs: 668.215 flop/atom) and the same crystal after 100 fs at 300 K (5.0726
-# bonds, 21.5767 ordered pairs: 1034.775 flop/atom; second-shell atoms at 3.84 A move
+# (j, k != j) of one atom.  Tersoff: fit to the C sheet (3 bonds per atom, 551.449 flop/atom)
+# and Si diamond (4 bonds, 822.266 flop/atom).  SW: fit to the Si diamond lattice (4 bonds,
+# 12 ordered pairs: 620.215 flop/atom) and the same crystal after 100 fs at 300 K (5.0726
+# bonds, 21.5767 ordered pairs: 947.165 flop/atom; second-shell atoms at 3.84 A move
 # inside the 3.77 A cutoff).
-TERSOFF_FLOP_PER_BOND = 137.316
-TERSOFF_FLOP_PER_BOND_PAIR = 26.750
-SW_FLOP_PER_BOND = 78.653
-SW_FLOP_PER_BOND_PAIR = 29.467
+TERSOFF_FLOP_PER_BOND = 140.316
+TERSOFF_FLOP_PER_BOND_PAIR = 21.750
+SW_FLOP_PER_BOND = 79.267
+SW_FLOP_PER_BOND_PAIR = 25.262
 # DRAM bytes (read + write) of one fp64 pair pass (SW: the common-case and full-capacity
 # launches of one step at 300 K), from the ncu capture of the current kernels.
-PAIR_TRAFFIC_BYTES = {"tersoff_c_graphene_1M": 140.45e6, "tersoff_si_216k": 10.20e6, "sw_si_512k": 203.57e6}
+PAIR_TRAFFIC_BYTES = {"tersoff_c_graphene_1M": 140.24e6, "tersoff_si_216k": 10.20e6, "sw_si_512k": 204.87e6}
 
 
 def load_peaks():
