@@ -943,11 +943,23 @@ __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, i
 #pragma unroll
         for (int c = 0; c < 9; ++c) { w[c] = 0; mj[c] = 0; }
         int k = 0;
+        // each bond's list entry and reverse slot are loaded one bond ahead, while the
+        // previous bond's loads through atom j are in flight
+        int e_nx = 0, mr_nx = 0;
+        if (mask != 0u) {
+            const int m0 = __ffs(mask) - 1;
+            e_nx = a.nl[(int64_t)m0 * N + i];
+            mr_nx = a.rev[(int64_t)m0 * N + i];
+        }
         while (mask != 0u && k < MAXA) {
-            const int m = __ffs(mask) - 1;
             mask &= mask - 1u;
-            const int j = list_atom(a.nl[(int64_t)m * N + i]);
-            const int mr = a.rev[(int64_t)m * N + i];
+            const int j = list_atom(e_nx);
+            const int mr = mr_nx;
+            if (mask != 0u) {
+                const int m1 = __ffs(mask) - 1;
+                e_nx = a.nl[(int64_t)m1 * N + i];
+                mr_nx = a.rev[(int64_t)m1 * N + i];
+            }
             const uint32_t maskj = a.mask[j];
             const int kr = __popc(maskj & ((1u << mr) - 1u));
             if (kr < MAXA) {
