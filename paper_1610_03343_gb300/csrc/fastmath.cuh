@@ -103,7 +103,11 @@ __device__ __forceinline__ double rsqrt_nr(double x)
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(xf));
     const double y = f2d_int(yf);
     const double e = fma(-x, y * y, 1.0);
-    return fma(y, e * fma(e, 0.375, 0.5), y);
+    const double r = fma(y, e * fma(e, 0.375, 0.5), y);
+    // below the fp32 normal range (only a zero bond, i.e. coincident atoms, gets there) the
+    // seed is not finite: return +inf, as 1/sqrt(+0) is, so that the forces turn non-finite
+    // and the step reports it (integer compare: x's bit pattern below that of 2^-126)
+    return __double_as_longlong(x) < 0x3810000000000000ll ? __longlong_as_double(0x7ff0000000000000ll) : r;
 }
 
 // a < b for a, b >= +0 (not NaN): non-negative doubles order like their bit patterns read
