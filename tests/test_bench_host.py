@@ -60,3 +60,16 @@ def test_matches_brute_force_over_images():
     m, mm = bench.bond_statistics(pos, box, np.array([1, 1, 1]), rc)
     assert m == pytest.approx(cnt.mean(), abs=0)
     assert mm == pytest.approx((cnt * (cnt - 1)).mean(), abs=0)
+
+
+def test_flop_model_reproduces_the_counted_launches():
+    """The roofline's per-bond and per-bond-pair FP64 flops are solved from ncu instruction
+    counts of two states each (profiles/pair_*_fp64_*.md); they must give those counts back."""
+    I_T, I_S = bench.I.MD_TERSOFF, bench.I.MD_SW
+    for kind, bonds, pairs, counted in [
+        (I_T, 3.0, 6.0, 551.449),        # C sheet
+        (I_T, 4.0, 12.0, 822.266),       # Si diamond
+        (I_S, 4.0, 12.0, 620.215),       # SW lattice
+        (I_S, 5.0726, 21.5767, 947.165),  # SW after 100 fs at 300 K
+    ]:
+        assert bench.pair_flops(kind, bonds, pairs) == pytest.approx(counted, abs=0.02)
