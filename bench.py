@@ -35,9 +35,69 @@ sys.path.insert(0, ROOT)
 from paper_1610_03343_gb300 import inputs as I  # noqa: E402
 
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
-# FP64 peak of a GB300 from its unit counts and clock: 152 SMs x 2 DFMA/clk/SM (ncu's
-# peak_sustained for the DFMA counter) x 2 flop x 2.07 GHz maximum SM clock.
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# FP64 peak of a GB300 from its unit counts and clock (152 SMs x 2 DFMA/clk/SM x 2 flop x
+# 2.07 GHz): context for the measured peak (md_peak_flops), which the roofline uses.
+FP64_PEAK_NOMINAL_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# iterations per FMA chain of the peak kernels: about 40 ms (fp64) and 30 ms (fp32) a launch
+PEAK_ITERS = {"fp64": 20_000, "fp32": 1_000_000}
+
+# Algorithmic flops of the pair pass, counted from the final expressions of the method
+# (Eqs. 2-6 and dU_i/dr_ij = 1/2 [(f_C f_R)' - b (f_C f_A)'] u_j - 1/2 f_C f_A b'_j dzeta_ij/dr_ij
+#  - 1/2 sum_k f_C f_A b'_k dzeta_ik/dr_ij), not from the kernel: an addition, subtraction or
+# multiplication is 1 flop; a division, reciprocal or reciprocal square root 8 (a seed and
+# Newton steps); exp, log and a sine-cosine pair 16 each (reduction and a polynomial).  Bonds
+# below R (f_C = 1, f_C' = 0: every bond of the crystal and sheet workloads at 300 K).
+# Each entry: (what, flops).
+EL, DIV = 16, 8
+TERSOFF_ALG_PER_BOND = [
+    ("r_ij = r_j - r_i", 3), ("|r|^2", 5), ("1/r", DIV), ("r = r^2 (1/r)", 1), ("u_j = r_ij / r", 3),
+    ("f_R = A exp(-lambda r)", 2 + EL), ("f_A = B exp(-mu r)", 2 + EL),
+    ("(beta zeta)^n = exp(n log(beta zeta))", 2 + 2 * EL), ("b = exp(-log(1 + x) / 2n)", 2 + 2 * EL),
+    ("b' = -b x / (2 zeta (1 + x))", 4 + DIV), ("U_i += (f_R - b f_A) / 2", 4),
+    ("radial (f_R' - b f_A') / 2", 5), ("P_j = -f_A b'_j / 2", 2), ("dU_i/dr_ij = A_j u_j + V_j", 6),
+]
+TERSOFF_ALG_PER_UNORDERED_PAIR = [
+    ("cos theta = u_j . u_k", 5), ("g = 1 + c^2/d^2 - c^2/(d^2 + (h - cos)^2)", 5 + DIV),
+    ("g' = -2 c^2 (h - cos) / (d^2 + (h - cos)^2)^2", 3 + DIV), ("Q = (P_j + P_k) g'", 2),
+]
+TERSOFF_ALG_PER_ORDERED_PAIR = [
+    ("zeta_ij += f_C(r_ik) g", 1), ("dcos/dr_ij = (u_k - cos u_j) / r_ij", 9), ("d_ij += Q dcos/dr_ij", 6),
+]
+SW_ALG_PER_BOND = [
+    ("r_ij, |r|^2, 1/r, r, u_j", 3 + 5 + DIV + 1 + 3), ("1/(r - a sigma)", 1 + DIV),
+    ("exp(sigma/(r - a sigma))", 1 + EL), ("E = exp(gamma sigma/(r - a sigma))", 1 + EL), ("dE/dr", 3),
+    ("(sigma/r)^p, (sigma/r)^q", 3), ("B (sigma/r)^p - (sigma/r)^q and its r-derivative", 2 + 5),
+    ("phi2 / 2", 3), ("dphi2/dr", 6), ("two-body part of dU_i/dr_ij", 4), ("U_i += phi2 / 2", 1),
+]
+SW_ALG_PER_UNORDERED_PAIR = [
+    ("cos, t = cos + 1/3, E_j E_k, U_i += lambda eps t^2 E_j E_k", 10),
+    ("2 lambda eps t E_j E_k, lambda eps t^2 (E_j' E_k, E_j E_k')", 7), ("q_j, q_k", 2),
+    ("d_j += q_j (u_k - cos u_j) + c_j u_j, and d_k", 36),
+]
+
+
+def pair_flops_algorithmic(kind: int, bonds: float, bond_pairs: float) -> float:
+    """Algorithmic flops per atom of the pair pass (the tables above) for a mean of `bonds`
+    in-cutoff neighbours and `bond_pairs` ordered bond pairs per atom."""
+    if kind == I.MD_TERSOFF:
+        per_bond = sum(f for _, f in TERSOFF_ALG_PER_BOND)
+        per_pair = sum(f for _, f in TERSOFF_ALG_PER_ORDERED_PAIR) + \
+            0.5 * sum(f for _, f in TERSOFF_ALG_PER_UNORDERED_PAIR)
+    else:
+        per_bond = sum(f for _, f in SW_ALG_PER_BOND)
+        per_pair = 0.5 * sum(f for _, f in SW_ALG_PER_UNORDERED_PAIR)
+    return per_bond * bonds + per_pair * bond_pairs
+
+
+def gather_bytes_algorithmic(bonds: float, fused: bool = True, elem: int = 4) -> float:
+    """Algorithmic DRAM bytes per atom of one step's gather (the mixed path's largest kernel):
+    what it must read and write once each -- its list mask (4), the in-cutoff list entries (4 M)
+    and reverse slots (M), the bonds' derivatives dU_i/dr_ij (3 M elem; the partner's dU_j/dr_ji
+    is another atom's own row, read once overall), the bond vectors (3 M elem), U_i (8), the
+    element (4), the velocity (24 read, 24 written), the force (24 written), and with the next
+    step's drift fused in: the position (24 read, 24 written) and the build position (24 read)."""
+    b = 4 + 5 * bonds + 6 * elem * bonds + 8 + 4 + 48 + 24
+    return b + (72 if fused else 0)
 
 # FP64 flops of the fp64 pair pass, counted with ncu's instruction counters (DADD + DMUL +
 # 2 DFMA, which include the fp64 instruction sequences of the table-driven exp and log, the
@@ -54,6 +114,9 @@ SW_FLOP_PER_BOND_PAIR = 25.262
 # DRAM bytes (read + write) of one fp64 pair pass (SW: the common-case and full-capacity
 # launches of one step at 300 K), from the ncu capture of the current kernels.
 PAIR_TRAFFIC_BYTES = {"tersoff_c_graphene_1M": 140.24e6, "tersoff_si_216k": 10.20e6, "sw_si_512k": 204.87e6}
+# DRAM bytes (read + write) of one mixed gather launch of the current kernel (ncu), by
+# workload; absent until captured
+GATHER_TRAFFIC_BYTES = {}
 
 
 def load_peaks():
@@ -499,6 +562,116 @@ def mixed_force_error():
     return worst
 
 
+def measure_peaks():
+    """FP64 and FP32 FMA peaks of this GPU (md_peak_flops: independent FMA chains on every SM,
+    best of 8 launches timed with CUDA events), with the SM clock sampled meanwhile."""
+    import torch
+    from paper_1610_03343_gb300 import md
+    out = {}
+    clocks = ClockSampler(torch.cuda.current_device())
+    with clocks:
+        for tag, prec in (("fp64", md.MD_FP64), ("fp32", md.MD_MIXED)):
+            tf, ms = md.md_peak_flops(prec, PEAK_ITERS[tag], 8)
+            out[f"{tag}_tflops"] = tf
+            out[f"{tag}_ms_per_launch"] = ms
+    out["clocks"] = clocks.summary()
+    out["how"] = ("md_peak_flops: 8 independent FMA chains per thread, 1024 threads per SM on every SM, "
+                  "best of 8 launches timed with CUDA events, 2 flop per FMA")
+    return out
+
+
+def precision_vs_oracle():
+    """Errors of the mixed path against the FP64 oracle: forces, per-atom energy, virial
+    and heat current of one evaluation on the serving job kinds; and over a 200-step NVE run
+    of a 2400-atom sheet (dt 0.5 fs) from the same state, the energy drift of each and the
+    difference of their heat-current autocorrelations (both formed by the oracle's
+    Green-Kubo routine, normalised by the oracle's C(0))."""
+    import oracle
+    from oracle import green_kubo as gk
+    from paper_1610_03343_gb300 import md
+    oracle.build()
+
+    def rel(a, b):
+        return float(np.abs(np.asarray(a) - np.asarray(b)).max() / np.abs(np.asarray(b)).max())
+
+    out = {"evaluation": {}}
+    for s in (I.si_diamond_tersoff(n=6), I.c_graphene_tersoff(nx=20, ny=30), I.si_diamond_sw(n=6, jitter_amp=0.05)):
+        ref = oracle.compute(s.pos, s.box, s.pbc, s.kind, s.params, s.vel)
+        with md.from_inputs(s, precision=md.MD_MIXED) as g:
+            got = g.compute()
+        out["evaluation"][s.name] = {k: rel(got[k], ref[k]) for k in ("F", "U", "W", "J")}
+    out["force_err_max"] = max(e["F"] for e in out["evaluation"].values())
+    s = I.c_graphene_tersoff(nx=20, ny=30)
+    steps, dt = 200, 0.5
+    _, _, ser_o = oracle.run(s.pos, s.vel, s.mass, s.box, s.pbc, s.kind, s.params, steps, dt)
+    sers = {}
+    for tag, prec in (("fp64", md.MD_FP64), ("mixed", md.MD_MIXED)):
+        with md.from_inputs(s, precision=prec) as g:
+            sers[tag] = g.run(steps, dt)
+    e_o = ser_o[:, 0] + ser_o[:, 1]
+    traj = {"system": s.name, "n_atoms": s.n, "steps": steps, "dt_fs": dt,
+            "energy_drift_ev_per_atom_oracle": float((e_o[-1] - e_o[0]) / s.n)}
+    lags = 100
+    c_o = gk.hcacf(ser_o[:, 2:5], lags).sum(axis=1)
+    for tag, ser in sers.items():
+        e = ser[:, 0] + ser[:, 1]
+        traj[f"energy_drift_ev_per_atom_{tag}"] = float((e[-1] - e[0]) / s.n)
+        traj[f"energy_series_max_diff_ev_per_atom_{tag}"] = float(np.abs(e - e_o).max() / s.n)
+        traj[f"j_series_max_diff_rel_{tag}"] = rel(ser[:, 2:5], ser_o[:, 2:5])
+        traj[f"hcacf_max_diff_rel_c0_{tag}"] = float(np.abs(gk.hcacf(ser[:, 2:5], lags).sum(axis=1) - c_o).max()
+                                                     / abs(c_o[0]))
+    out["trajectory"] = traj
+    return out
+
+
+def run_sw_leg(args, steps, warmup):
+    """Stillinger-Weber silicon, 40^3 cells (512,000 atoms), 300 K, dt 1 fs: fp64 and mixed
+    atom-steps/s after 100 untimed steps (the crystal gains about one bond per atom as its
+    second shell moves inside the cutoff), with the fp64 pair pass's roofline."""
+    import torch
+    from paper_1610_03343_gb300 import md
+    sysm, dt = workload("sw_si_512k")
+    n = sysm.n
+    stream = torch.cuda.Stream()
+    out = {"workload": "sw_si_512k", "n_atoms": n, "dt_fs": dt, "steps": steps, "equilibration_steps": 100}
+    for prec, tag in ((md.MD_FP64, "fp64"), (md.MD_MIXED, "mixed")):
+        g = md.System(sysm.box, sysm.pbc, n, sysm.kind, sysm.params, sysm.mass, precision=prec,
+                      stream=stream.cuda_stream)
+        g.set_positions(sysm.pos)
+        g.set_velocities(sysm.vel)
+        g.run(100, dt, record=False)
+        md.md_autotune(g.ctx, 5)
+        g.run(warmup, dt, record=False)
+        pos0 = g.state()[0]
+        md.md_set_profiling(g.ctx, True)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.run(steps, dt, record=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        kt = md.md_kernel_times(g.ctx)
+        md.md_set_profiling(g.ctx, False)
+        pos1 = g.state()[0]
+        g.close()
+        rc = I.cutoff(sysm.kind, sysm.params)
+        bst = [bond_statistics(p_, sysm.box, sysm.pbc, rc) for p_ in (pos0, pos1)]
+        bonds, pairs = 0.5 * (bst[0][0] + bst[1][0]), 0.5 * (bst[0][1] + bst[1][1])
+        pn, pms = kt.get("pair", (0, 0.0))
+        leg = {"value": n * steps / (ms / 1e3), "unit": "atom-steps/s", "ms_per_step": ms / steps,
+               "kernel_ms_per_step": {k: (v[1] / v[0] if v[0] else None) for k, v in kt.items()},
+               "bonds_per_atom": round(bonds, 4), "bond_pairs_per_atom": round(pairs, 4)}
+        if pn:
+            t_pair = pms / pn / 1e3
+            leg["pair_tflops_algorithmic"] = pair_flops_algorithmic(sysm.kind, bonds, pairs) * n / t_pair / 1e12
+            if tag == "fp64":
+                leg["pair_tflops_counted"] = pair_flops(sysm.kind, bonds, pairs) * n / t_pair / 1e12
+        out[tag] = leg
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -521,6 +694,9 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-npt", action="store_true")
+    ap.add_argument("--no-sw", action="store_true", help="skip the Stillinger-Weber 512k-atom leg")
+    ap.add_argument("--no-oracle-precision", action="store_true",
+                    help="skip the mixed-path errors against the oracle (about 5 s of CPU work)")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-requests-low", type=int, default=400,
@@ -565,18 +741,37 @@ def main():
         return
     kt = res[primary]["kt"]
     pair_n, pair_ms = kt.get("pair", (0, 0.0))
-    st = res[primary]["stats"]
     sysm, _ = workload(args.workload)
+    peaks_hw = load_peaks()
+    peaks = measure_peaks()
+    fp64_peak = peaks["fp64_tflops"]
     # bonds at the first and the last step of the timed region (SW's count grows as the
     # crystal warms up); the pair pass's flops per launch use their mean
     rc = I.cutoff(sysm.kind, sysm.params)
     bstats = [bond_statistics(p, sysm.box, sysm.pbc, rc) for p in res[primary]["pos_window"]]
     bonds = 0.5 * (bstats[0][0] + bstats[1][0])
     bond_pairs = 0.5 * (bstats[0][1] + bstats[1][1])
-    flops = pair_flops(sysm.kind, bonds, bond_pairs) * n
+    flops_alg = pair_flops_algorithmic(sysm.kind, bonds, bond_pairs) * n
+    flops_cnt = pair_flops(sysm.kind, bonds, bond_pairs) * n
     pair_avg_s = pair_ms / pair_n / 1e3 if pair_n > 0 and pair_ms > 0 else None
-    achieved_tf = flops / pair_avg_s / 1e12 if pair_avg_s else None
+    ach_alg = flops_alg / pair_avg_s / 1e12 if pair_avg_s else None
+    ach_cnt = flops_cnt / pair_avg_s / 1e12 if pair_avg_s else None
     traffic = PAIR_TRAFFIC_BYTES.get(args.workload) if primary == "fp64" else None
+    roofline = {"bound": "alu", "kernel": f"pair ({primary})", "achieved": ach_alg, "peak": fp64_peak,
+                "unit": "TFLOP/s", "frac": ach_alg / fp64_peak if ach_alg else None, "traffic": traffic,
+                "flop_per_launch": flops_alg,
+                "flop_model": "expression count of Eqs. 2-6 and dU_i/dr_ij: +,-,* 1 flop; division, "
+                              "reciprocal, 1/sqrt 8; exp, log 16",
+                "peak_source": "measured on this GPU: md_peak_flops FP64 FMA chains "
+                               f"(SM clock median {peaks['clocks'].get('sm_mhz')} MHz)",
+                "peak_nominal": FP64_PEAK_NOMINAL_TFLOPS,
+                "frac_of_nominal": ach_alg / FP64_PEAK_NOMINAL_TFLOPS if ach_alg else None,
+                "counted": {"achieved": ach_cnt, "frac": ach_cnt / fp64_peak if ach_cnt else None,
+                            "flop_per_launch": flops_cnt,
+                            "flop_model": "DADD + DMUL + 2 DFMA thread instructions of the kernel (ncu), "
+                                          "per bond and per ordered bond pair"},
+                "bonds_per_atom": [round(b[0], 4) for b in bstats],
+                "bond_pairs_per_atom": [round(b[1], 4) for b in bstats]}
     out = {
         "metric": "atom-steps/s Tersoff FP64 vs mixed on 1 GB300",
         "value": value,
@@ -594,13 +789,8 @@ def main():
                    "equilibration_steps": args.equilibrate,
                    "l2": "working set > L2 (no flush)", "launch": "eager" if args.eager else "graphs",
                    "parallelism": "replicas" if world > 1 else "single"},
-        "roofline": {"bound": "alu", "kernel": f"pair ({primary})", "achieved": achieved_tf,
-                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved_tf / FP64_PEAK_TFLOPS if achieved_tf else None, "traffic": traffic,
-                     "flop_per_launch": flops,
-                     "bonds_per_atom": [round(b[0], 4) for b in bstats],
-                     "bond_pairs_per_atom": [round(b[1], 4) for b in bstats],
-                     "peak_source": "FP64 pipe from unit counts and clock: 152 SMs x 4 flop/clk x 2.07 GHz"},
+        "roofline": roofline,
+        "peaks": peaks,
         "kernel_ms_per_step": {k: (v[1] / v[0] if v[0] else None) for k, v in kt.items()},
         "gpu_launches": res[primary]["launches"],
         "rebuilds": res[primary]["rebuilds"],
@@ -608,22 +798,52 @@ def main():
         "tuning": res[primary]["tuning"],
     }
     if "mixed" in res and primary != "mixed":
+        kmx = res["mixed"]["kt"]
         out["mixed"] = {"value": job_value(world, n, args.steps, ms_mixed), "ms_per_step": ms_mixed / args.steps,
                         "dtype": "f32+f64", "force_err_vs_fp64": mixed_err,
-                        "kernel_ms_per_step": {k: (v[1] / v[0] if v[0] else None)
-                                               for k, v in res["mixed"]["kt"].items()},
+                        "kernel_ms_per_step": {k: (v[1] / v[0] if v[0] else None) for k, v in kmx.items()},
                         "tuning": res["mixed"]["tuning"]}
+        # the mixed step's largest kernel is the gather (memory-latency bound): its roofline
+        # is HBM, on the algorithmic bytes one launch must move; the pair pass's is the FP32
+        # pipe, on the expression-count flops
+        gn, gms = kmx.get("gather", (0, 0.0))
+        pn, pms = kmx.get("pair", (0, 0.0))
+        hbm = peaks_hw["hbm_gbs"]
+        rm = {"bound": "hbm", "kernel": "gather (mixed)", "unit": "GB/s", "peak": hbm,
+              "peak_source": f"{peaks_hw['_source']} HBM copy bandwidth (MEASURED_PEAKS.json)",
+              "traffic": GATHER_TRAFFIC_BYTES.get(args.workload),
+              "bytes_per_launch": gather_bytes_algorithmic(bonds) * n,
+              "bytes_model": "per atom: mask 4 + list 5M + dU/dr 12M + r 12M + U 8 + type 4 + v 48 + F 24 "
+                             "+ fused drift 72 (M in-cutoff bonds)"}
+        if gn:
+            t = gms / gn / 1e3
+            rm["achieved"] = rm["bytes_per_launch"] / t / 1e9
+            rm["frac"] = rm["achieved"] / hbm
+            rm["launch_ms"] = t * 1e3
+        if pn:
+            t = pms / pn / 1e3
+            a32 = pair_flops_algorithmic(sysm.kind, bonds, bond_pairs) * n / t / 1e12
+            rm["pair"] = {"bound": "alu", "kernel": "pair (mixed, fp32)", "unit": "TFLOP/s", "achieved": a32,
+                          "peak": peaks["fp32_tflops"], "frac": a32 / peaks["fp32_tflops"], "launch_ms": t * 1e3,
+                          "peak_source": "measured on this GPU: md_peak_flops FP32 FMA chains"}
+        out["roofline_mixed"] = rm
     out["precision"] = precision_report(res, n, dt, sysm.box)
+    if not args.no_oracle_precision:
+        out["precision"]["vs_oracle"] = precision_vs_oracle()
     if t_e2e is not None:
         out["e2e"] = {"value": world * n * args.steps / t_e2e, "unit": "atom-steps/s",
                       "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps}
     if not args.no_npt:
         out["npt"] = run_npt_leg(args, max(8, args.steps // 2), args.warmup)
+    if not args.no_sw:
+        out["sw"] = run_sw_leg(args, max(20, args.steps // 2), args.warmup)
     if not args.no_batch:
         out["batch"] = run_batch(args, max(8, args.steps // 2), args.warmup)
     if not args.no_serve:
         out["serve"] = run_serve(args)
         out["serve"]["force_err_mixed_vs_fp64"] = mixed_force_error()
+        if "vs_oracle" in out["precision"]:
+            out["serve"]["force_err_mixed_vs_oracle"] = out["precision"]["vs_oracle"]["force_err_max"]
         # below capacity: the same job mix at 50% and 80% of the capacity just measured
         cap_jobs = out["serve"]["value"] / out["serve"]["mean_job_atom_steps"]
         out["serve"]["capacity_jobs_per_s"] = cap_jobs

@@ -50,8 +50,8 @@ typedef enum {
     MD_ERR_NEIGH_OVERFLOW = -3, /* an atom had more neighbours than max_neigh / max_active */
     MD_ERR_OOM = -4,            /* device allocation failed or exceeded hbm_budget        */
     MD_ERR_CUDA = -5,           /* a CUDA runtime call failed                             */
-    MD_ERR_TIMEOUT = -6,        /* a bounded device-side wait gave up                    */
-    MD_ERR_NAN = -7,            /* a non-finite force appeared                            */
+    MD_ERR_TIMEOUT = -6,        /* a bounded wait gave up (md_server_wait_timeout)        */
+    MD_ERR_NAN = -7,            /* a non-finite force, position or velocity appeared      */
     MD_ERR_STATE = -8           /* call out of order (e.g. run before positions are set)  */
 } md_status;
 
@@ -142,6 +142,23 @@ md_status md_run(md_ctx *ctx, int64_t n_steps, double dt_fs, double *series);
 
 /* Current positions and velocities, each 3N SoA; either may be NULL. */
 md_status md_get_state(md_ctx *ctx, double *x, double *v);
+
+/* Checkpoint and resume (single-system contexts; pools: MD_ERR_STATE).  The paper has no
+ * counterpart: it runs one uninterrupted simulation per benchmark (Sec. 3).  A checkpoint is
+ * the whole state the next md_run step reads -- positions as stored (unwrapped since the
+ * last list build), velocities, forces, build positions, the neighbour list and its reverse
+ * slots, the box, cell grid and Berendsen state, and the pending rebuild request -- so a run
+ * resumed from it in another context is bitwise identical to the uninterrupted run (no
+ * atomics anywhere: every result depends only on that state).  md_get_state's wrapped
+ * positions are not enough for that: a list built from them rounds differently.
+ *   md_checkpoint_size: bytes of the image (header + about 96 + 13 cap bytes per atom).
+ *   md_checkpoint_save: writes the image into a host buffer of at least that size.
+ *   md_checkpoint_load: restores an image into a context created with the same atom count,
+ *     types, masses, potential and options (precision, skin, list capacities); MD_ERR_ARG if
+ *     the image is not a checkpoint, is truncated, or came from a different context. */
+md_status md_checkpoint_size(md_ctx *ctx, size_t *bytes);
+md_status md_checkpoint_save(md_ctx *ctx, void *buf, size_t bytes);
+md_status md_checkpoint_load(md_ctx *ctx, const void *buf, size_t bytes);
 
 /* Berendsen weak coupling (NPT).  The paper's benchmarks run in the NPT ensemble at 300 K
  * and 0 Pa (Sec. 3) without printing the coupling; this is Berendsen et al., J. Chem.
@@ -294,6 +311,15 @@ md_status md_batch_remove(md_ctx *ctx, int id);
  * step or force evaluation) and kinetic energy K of the last step. */
 md_status md_batch_status(md_ctx *ctx, int *active, int64_t *steps_left, double *totals, double *kinetic);
 
+/* Per slot (max_systems entries): MD_OK, or the md_status of the failure that stopped
+ * that system on the device -- MD_ERR_NAN (a non-finite force, position or velocity),
+ * MD_ERR_NEIGH_OVERFLOW (an atom with more than max_neigh listed or max_active in-cutoff
+ * neighbours), MD_ERR_BOX (NPT: an edge shrank below 2 (cutoff + skin)).  Such a failure
+ * concerns one system: it stops (md_batch_status reports it inactive) while md_run goes on
+ * with the others and returns MD_OK; the caller removes it.  Empty slots read MD_OK.
+ * md_batch_add with host I/O rejects non-finite positions or velocities itself (MD_ERR_NAN). */
+md_status md_batch_errors(md_ctx *ctx, int *status);
+
 /* Positions (wrapped) and velocities of one system, each 3 n_atoms SoA. */
 md_status md_batch_get_state(md_ctx *ctx, int id, double *x, double *v);
 
@@ -362,6 +388,10 @@ md_status md_server_submit(md_server *srv, const md_job *job, int64_t *job_id);
 md_status md_server_poll(md_server *srv, int64_t job_id, md_job_result *out);
 /* Block until the job is done. */
 md_status md_server_wait(md_server *srv, int64_t job_id, md_job_result *out);
+/* Block until the job is done or timeout_s seconds have passed: MD_OK (done; *out holds
+ * the result) or MD_ERR_TIMEOUT (not done yet; *out holds its state so far, done = 0).  For
+ * callers with a deadline; the job keeps running either way. */
+md_status md_server_wait_timeout(md_server *srv, int64_t job_id, double timeout_s, md_job_result *out);
 /* Block until every submitted job is done. */
 md_status md_server_drain(md_server *srv);
 md_status md_server_stats_get(md_server *srv, md_server_stats *out);
@@ -433,6 +463,16 @@ md_status md_hcacf(const double *j, int64_t n_rows, int64_t row_stride, int64_t 
  * x, y: n host doubles.  Returns 0, -1 for bad arguments, -5 on a CUDA error.
  * Allocates and frees its own device scratch. */
 int md_fastmath_eval(int fn, int64_t n, const double *x, double *y);
+
+/* Diagnostics for rooflines: the fused multiply-add peak of the current device in fp64
+ * (precision = MD_FP64) or fp32 (MD_MIXED), measured -- the paper's hardware figures
+ * (Sec. 3) are a vendor's, this is what the GPU at hand delivers.  A kernel of independent
+ * FMA chains (8 per thread, 1024 threads per SM on every SM, `iters` FMAs per chain) runs
+ * `repeats` times after a warm-up launch, each timed with CUDA events; *tflops receives the
+ * best rate (2 flop per FMA, TFLOP/s) and *ms (may be NULL) that launch's time.  Allocates
+ * and frees a small output buffer.  MD_ERR_ARG for iters < 1, repeats < 1 or another
+ * precision. */
+int md_peak_flops(int precision, int64_t iters, int repeats, double *tflops, double *ms);
 
 /* Message of the last failing call (empty string if none).  Never NULL. */
 const char *md_last_error(const md_ctx *ctx);

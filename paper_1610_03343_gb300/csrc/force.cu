@@ -23,6 +23,7 @@
 // per-atom sums in fp32; bond vectors from fp64 positions; velocities, positions and
 // the block / system totals in fp64).
 #include <algorithm>
+#include <mutex>
 
 #include "fastmath.cuh"
 #include "md_plan.cuh"
@@ -141,6 +142,16 @@ __device__ __forceinline__ void bond_vector_t(const double *pos, int64_t N, int6
     tx = to_t<T>(dx); ty = to_t<T>(dy); tz = to_t<T>(dz);
 }
 
+// A failure found by the pair pass for atom i: its system's entry in a pool (the rest of
+// the pool carries on), the context's status words otherwise.
+template <typename T>
+__device__ __noinline__ void pair_fail(const PairArgs<T> &a, int64_t i, int status)
+{
+    if (a.batch) fail_system(a.sys[a.sys_of[i]], status);
+    else if (status == MD_ERR_NAN) a.flags->nonfinite = 1;
+    else a.flags->active_overflow = 1;
+}
+
 // ------------------------------------------------------- neighbour staging
 // For each list slot, the fp64 bond r_ij (image shift from the entry); keeps the slots
 // with |r_ij|^2 < rc^2, writes their bond vectors (compact row k) to global memory and
@@ -161,6 +172,9 @@ __device__ __forceinline__ int collect_bonds(const PairArgs<T> &a, int64_t i, co
     const int64_t N = a.N;
     const int S_ = a.stride;
     const double xi = a.pos[i], yi = a.pos[N + i], zi = a.pos[2 * N + i];
+    // a non-finite position has no bond inside the cutoff (its distances are NaN): report
+    // it, as its force would otherwise be a silent zero
+    if (!(finite_bits(xi) && finite_bits(yi) && finite_bits(zi))) pair_fail(a, i, MD_ERR_NAN);
     float fxi = 0.f, fyi = 0.f, fzi = 0.f, lim2 = 0.f, fL0 = 0.f, fL1 = 0.f, fL2 = 0.f;
     if (PREFILTER) {
         fxi = a.posf[i]; fyi = a.posf[N + i]; fzi = a.posf[2 * N + i];
@@ -250,7 +264,7 @@ __device__ __forceinline__ int collect_bonds(const PairArgs<T> &a, int64_t i, co
             a.ovf_list[atomicAdd(a.ovf_count, 1)] = (int)i;
             return -1;
         }
-        a.flags->active_overflow = 1;
+        pair_fail(a, i, MD_ERR_NEIGH_OVERFLOW);
         na = CAP;
     }
     return na;
@@ -655,7 +669,7 @@ __device__ __forceinline__ void sw_atom_warp(const PairArgs<T> &a, const SWC<T> 
     const int k = __popc(mask & ((1u << lane) - 1u));
     int na = __popc(mask);
     if (na > FULL) {
-        if (lane == 0) a.flags->active_overflow = 1;
+        if (lane == 0) pair_fail(a, i, MD_ERR_NEIGH_OVERFLOW);
         na = FULL;
     }
     const bool mine = in && k < FULL;
@@ -985,7 +999,6 @@ __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, i
             }
             ++k;
         }
-        if (!(finite_bits(f0) && finite_bits(f1) && finite_bits(f2))) a.flags->nonfinite = 1;
         const double F[3] = {to_d(f0), to_d(f1), to_d(f2)};
         a.force[i] = F[0];
         a.force[N + i] = F[1];
@@ -1021,6 +1034,13 @@ __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, i
             a.vel[i] = vn[0];
             a.vel[N + i] = vn[1];
             a.vel[2 * N + i] = vn[2];
+        }
+        // a non-finite force or velocity (after the kick; without one, as given) stops the
+        // system in a pool and fails the call for a single system
+        if (!(finite_bits(f0) && finite_bits(f1) && finite_bits(f2) && finite_bits(v[0]) && finite_bits(v[1]) &&
+              finite_bits(v[2]))) {
+            if (BATCH) fail_system(a.sys[sid], MD_ERR_NAN);
+            else a.flags->nonfinite = 1;
         }
         // J_i (Eq. 30) with v_i after the half-kick, and K_i = m v^2 / 2, in T (the fp32
         // per-atom value of the mixed path feeds an fp64 total).  fp64: a second walk over
@@ -1256,7 +1276,10 @@ __global__ void k_npt_apply(int n_sys, SysDev *sys, int batch, Flags *flags)
         sd.box.invL[a] = 1.0 / sd.box.L[a];
         sd.npt.mu_cum[a] *= m;
         if (sd.box.pbc[a]) {
-            if (!(sd.box.L[a] >= 2.0 * sd.cell_edge + 0.01)) flags->box_error = 1;
+            if (!(sd.box.L[a] >= 2.0 * sd.cell_edge + 0.01)) {
+                if (batch) fail_system(sd, MD_ERR_BOX);
+                else flags->box_error = 1;
+            }
             const int fit = (int)floor(sd.box.L[a] / sd.cell_edge);
             if (fit < sd.nc[a]) sd.nc[a] = fit < 1 ? 1 : fit;
         }
@@ -1386,6 +1409,7 @@ void pair_launch_b(const Plan &p, cudaStream_t s, int list, int parts)
     a.mask = p.mask;
     a.u = p.u;
     a.flags = p.flags;
+    a.batch = BATCH ? 1 : 0;
     const unsigned nb = BATCH ? pool_grid(p) : blocks_for(p.N, B);
     int64_t nbf = (p.N + kPairBlockFull - 1) / kPairBlockFull;
     if (nbf > 4 * (int64_t)p.n_sm) nbf = 4 * (int64_t)p.n_sm;
@@ -1513,15 +1537,29 @@ int effective_pair_block(const Plan &p)
 
 bool valid_pair_block(int b) { return b == 32 || b == 64 || b == 128 || b == 256; }
 
-void configure_kernels(const Plan &)
+// The shared-memory opt-in of the pair kernels is an attribute of the kernel in the
+// current device's context: it is set once per device, under a lock (contexts, servers and
+// the allocation-free entry point may be created from several threads and on several
+// devices).  Returns false when the current device cannot be read or the opt-in failed.
+bool configure_kernels(const Plan &)
 {
-    static bool done = false;
-    if (done) return;
+    static std::mutex mu;
+    static bool done[kMaxConfigDevices] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxConfigDevices) {
+        cudaGetLastError();
+        return false;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    if (done[dev]) return true;
+    cudaGetLastError();   // a stale error of an earlier call must not count as this one's
     configure_type<double, false>();
     configure_type<float, false>();
     configure_type<double, true>();
     configure_type<float, true>();
-    done = true;
+    if (cudaGetLastError() != cudaSuccess) return false;
+    done[dev] = true;
+    return true;
 }
 
 void launch_kick_drift(const Plan &p, cudaStream_t s, const double *hk, double dt)

@@ -210,7 +210,7 @@ md_status check_flags(md_ctx *ctx)
     if (f.active_overflow)
         return fail(ctx, MD_ERR_NEIGH_OVERFLOW, "more in-cutoff neighbours than max_active");
     if (f.asym) return fail(ctx, MD_ERR_CUDA, "internal: asymmetric neighbour list");
-    if (f.nonfinite) return fail(ctx, MD_ERR_NAN, "non-finite force");
+    if (f.nonfinite) return fail(ctx, MD_ERR_NAN, "non-finite force, position or velocity");
     if (f.box_error) {
         ctx->forces_valid = false;
         return fail(ctx, MD_ERR_BOX, "NPT: a periodic box edge shrank below 2 (cutoff + skin)");
@@ -735,7 +735,7 @@ md_status ctx_init(md_ctx *ctx, const md_options &opt)
     if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, ctx->device) == cudaSuccess && n_sm > 0)
         ctx->p.n_sm = n_sm;
     cudaGetLastError();
-    configure_kernels(ctx->p);
+    if (!configure_kernels(ctx->p)) return MD_ERR_CUDA;
     return MD_OK;
 }
 
@@ -1041,6 +1041,13 @@ md_status md_batch_add(md_ctx *ctx, const md_system *sysd, int *id_out)
     if (!(sysd->damp >= 0)) return fail(ctx, MD_ERR_ARG, "bad damping");
     for (int64_t i = 0; i < n; ++i)
         if (sysd->types[i] < 0 || sysd->types[i] >= p.ntypes) return fail(ctx, MD_ERR_ARG, "bad type");
+    if (ctx->io == MD_IO_HOST) {   // device inputs are checked by the first force evaluation
+        const double *in[6] = {sysd->x, sysd->y, sysd->z, sysd->vx, sysd->vy, sysd->vz};
+        for (int c = 0; c < 6; ++c)
+            if (in[c])
+                for (int64_t i = 0; i < n; ++i)
+                    if (!std::isfinite(in[c][i])) return fail(ctx, MD_ERR_NAN, "non-finite position or velocity");
+    }
     SysDev sd;
     std::memset(&sd, 0, sizeof(sd));
     // cutoff, skin and list radius of this system's parameter set
@@ -1157,6 +1164,16 @@ md_status md_batch_status(md_ctx *ctx, int *active, int64_t *steps_left, double 
             for (int c = 0; c < 3; ++c) o[10 + c] = q[2 + c];
         }
     }
+    return MD_OK;
+}
+
+md_status md_batch_errors(md_ctx *ctx, int *status)
+{
+    if (!ctx || !status) return MD_ERR_ARG;
+    if (!ctx->is_pool) return fail(ctx, MD_ERR_STATE, "not a pool");
+    md_status s = download_sys_table(ctx);
+    if (s != MD_OK) return s;
+    for (int k = 0; k < ctx->p.n_sys; ++k) status[k] = ctx->sys_used[k] ? ctx->sys_host[k].error : 0;
     return MD_OK;
 }
 
@@ -1420,6 +1437,137 @@ md_status md_get_state(md_ctx *ctx, double *x, double *v)
     }
     if ((s = download(ctx, v, ctx->p.vel, 3 * ctx->p.N)) != MD_OK) return s;
     CK(cudaStreamSynchronize(ctx->stream));
+    return MD_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Checkpoint image of a single-system context: a header, then the device state that the
+// next step reads, in this order: positions (as stored: unwrapped since the last list
+// build), velocities, forces, build positions (3N doubles each), fp32 positions (3N
+// floats), list lengths (N ints), list entries (cap N ints), reverse slots (cap N bytes).
+constexpr uint64_t kCheckpointMagic = 0x3130315444504b43ull;   // "CKPDT101"
+struct CheckpointHeader {
+    uint64_t magic;
+    int64_t n_atoms;
+    int32_t kind, precision, cap, maxa, ntypes, n_elem;
+    int32_t pos_set, forces_valid, npt, pad;
+    int64_t steps_done;
+    double mass[kMaxTypes];
+    double skin;
+    TersoffP tp;       // parameter set 0 (a restored context must use the same potential)
+    SWP sp;
+    SysDev sys;        // box, cell grid, Berendsen state
+    Flags flags;       // pending rebuild request, counters
+};
+
+size_t checkpoint_bytes(const Plan &p)
+{
+    const size_t N = (size_t)p.N;
+    return sizeof(CheckpointHeader) + 4 * 3 * N * sizeof(double) + 3 * N * sizeof(float) + N * sizeof(int) +
+           (size_t)p.cap * N * (sizeof(int) + sizeof(uint8_t));
+}
+
+struct Section {
+    void *dev;
+    size_t bytes;
+};
+
+std::vector<Section> checkpoint_sections(const Plan &p)
+{
+    const size_t N = (size_t)p.N;
+    return {{p.pos, 3 * N * sizeof(double)},       {p.vel, 3 * N * sizeof(double)},
+            {p.force, 3 * N * sizeof(double)},     {p.pos_build, 3 * N * sizeof(double)},
+            {p.posf, 3 * N * sizeof(float)},       {p.nn, N * sizeof(int)},
+            {p.nl, (size_t)p.cap * N * sizeof(int)}, {p.rev, (size_t)p.cap * N * sizeof(uint8_t)}};
+}
+
+}  // namespace
+
+extern "C" {
+
+md_status md_checkpoint_size(md_ctx *ctx, size_t *bytes)
+{
+    if (!ctx || !bytes) return MD_ERR_ARG;
+    if (ctx->is_pool) return fail(ctx, MD_ERR_STATE, "checkpoints cover single-system contexts");
+    *bytes = checkpoint_bytes(ctx->p);
+    return MD_OK;
+}
+
+md_status md_checkpoint_save(md_ctx *ctx, void *buf, size_t bytes)
+{
+    if (!ctx || !buf) return MD_ERR_ARG;
+    if (ctx->is_pool) return fail(ctx, MD_ERR_STATE, "checkpoints cover single-system contexts");
+    const Plan &p = ctx->p;
+    if (bytes < checkpoint_bytes(p)) return fail(ctx, MD_ERR_ARG, "checkpoint buffer too small");
+    CheckpointHeader h;
+    std::memset(&h, 0, sizeof(h));
+    h.magic = kCheckpointMagic;
+    h.n_atoms = p.N;
+    h.kind = p.kind;
+    h.precision = p.precision;
+    h.cap = p.cap;
+    h.maxa = p.maxa;
+    h.ntypes = p.ntypes;
+    h.n_elem = p.n_elem;
+    h.pos_set = ctx->pos_set ? 1 : 0;
+    h.forces_valid = ctx->forces_valid ? 1 : 0;
+    h.npt = p.npt ? 1 : 0;
+    h.steps_done = ctx->steps_done;
+    for (int t = 0; t < kMaxTypes; ++t) h.mass[t] = p.mass[t];
+    h.skin = p.skin;
+    h.tp = p.tp[0];
+    h.sp = p.sp[0];
+    CK(cudaMemcpyAsync(&h.sys, p.sys, sizeof(SysDev), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(&h.flags, p.flags, sizeof(Flags), cudaMemcpyDeviceToHost, ctx->stream));
+    unsigned char *o = static_cast<unsigned char *>(buf) + sizeof(CheckpointHeader);
+    for (const Section &sec : checkpoint_sections(p)) {
+        if (sec.bytes) CK(cudaMemcpyAsync(o, sec.dev, sec.bytes, cudaMemcpyDeviceToHost, ctx->stream));
+        o += sec.bytes;
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    std::memcpy(buf, &h, sizeof(h));
+    return MD_OK;
+}
+
+md_status md_checkpoint_load(md_ctx *ctx, const void *buf, size_t bytes)
+{
+    if (!ctx || !buf) return MD_ERR_ARG;
+    if (ctx->is_pool) return fail(ctx, MD_ERR_STATE, "checkpoints cover single-system contexts");
+    Plan &p = ctx->p;
+    if (bytes < sizeof(CheckpointHeader)) return fail(ctx, MD_ERR_ARG, "not a checkpoint");
+    CheckpointHeader h;
+    std::memcpy(&h, buf, sizeof(h));
+    if (h.magic != kCheckpointMagic) return fail(ctx, MD_ERR_ARG, "not a checkpoint");
+    const bool same = h.n_atoms == p.N && h.kind == p.kind && h.precision == p.precision && h.cap == p.cap &&
+                      h.maxa == p.maxa && h.ntypes == p.ntypes && h.n_elem == p.n_elem && h.skin == p.skin &&
+                      std::memcmp(h.mass, p.mass, sizeof(h.mass)) == 0 &&
+                      std::memcmp(&h.tp, &p.tp[0], sizeof(TersoffP)) == 0 &&
+                      std::memcmp(&h.sp, &p.sp[0], sizeof(SWP)) == 0;
+    if (!same) return fail(ctx, MD_ERR_ARG, "checkpoint of a context with other atoms, potential or options");
+    if (bytes < checkpoint_bytes(p)) return fail(ctx, MD_ERR_ARG, "checkpoint truncated");
+    for (int a = 0; a < 3; ++a)
+        if (h.sys.nc[a] < 1 || h.sys.nc[a] > ctx->nc_full[a] || h.sys.box.pbc[a] != p.box.pbc[a])
+            return fail(ctx, MD_ERR_ARG, "checkpoint cell grid or periodicity does not fit this context");
+    const unsigned char *o = static_cast<const unsigned char *>(buf) + sizeof(CheckpointHeader);
+    for (const Section &sec : checkpoint_sections(p)) {
+        if (sec.bytes) CK(cudaMemcpyAsync(sec.dev, o, sec.bytes, cudaMemcpyHostToDevice, ctx->stream));
+        o += sec.bytes;
+    }
+    CK(cudaMemcpyAsync(p.sys, &h.sys, sizeof(SysDev), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(p.flags, &h.flags, sizeof(Flags), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->sys_host[0] = h.sys;
+    p.box = h.sys.box;
+    for (int a = 0; a < 3; ++a) p.nc[a] = h.sys.nc[a];
+    p.ncell = (int64_t)p.nc[0] * p.nc[1] * p.nc[2];
+    p.npt = h.npt != 0;
+    ctx->pos_set = h.pos_set != 0;
+    ctx->forces_valid = h.forces_valid != 0;
+    ctx->steps_done = h.steps_done;
+    destroy_graph(ctx);   // the graphs carry the box and grid in their arguments
     return MD_OK;
 }
 

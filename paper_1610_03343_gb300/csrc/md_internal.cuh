@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "md.h"
+
 namespace mdk {
 
 // eV/(A amu) -> A/fs^2 (exact elementary charge, CODATA-2018 atomic mass constant)
@@ -76,6 +78,8 @@ struct SysDev {
     int rebuild;              // 1: rebuild this system's lists at the next rebuild
     int built;                // 1 once its lists exist
     int fresh;                // 1 until its first force evaluation (just admitted)
+    int error;                // pools: md_status of the failure that stopped this system
+                              // (0 = none); the rest of the pool keeps running
     double rc;                // potential cutoff of this system's parameter set
     double rl;                // list radius rc + skin
     double cell_edge;         // smallest cell edge the 27-cell stencil allows (rl + fp32 margin)
@@ -100,6 +104,16 @@ struct Flags {
     long long row_reduce;      // series row of the last gather's partials (the reduction of a
                                // step may run beside the next step's first kernels)
 };
+
+// Pools: a failure that concerns one system only (a non-finite force, position or
+// velocity, an overlong neighbour list, a box shrunk below the cutoff) is recorded in that
+// system's entry -- the first status stays -- and stops it; the other systems of the pool
+// are not affected (their atoms never list its atoms).
+__device__ __forceinline__ void fail_system(SysDev &sd, int status)
+{
+    atomicCAS(&sd.error, 0, status);
+    sd.active = 0;
+}
 
 // Pools: does atom work of system `sd` run now?  Stopped systems never; during the
 // force evaluation that follows admissions, only the newly admitted systems.
@@ -143,7 +157,7 @@ struct PairArgs {
     T *d;                   // 3 x S x N : d[(c S + k) N + i] = dU_i/dr_ij (component c)
     T *r;                   // 3 x S x N : r_ij
     const int *sys_of;      // N: system of each atom (pools)
-    const SysDev *sys;      // system table (pools; a single system: its one entry)
+    SysDev *sys;            // system table (pools; a single system: its one entry)
     int dev_box;            // single system: read the box from sys[0] (it changes under NPT)
     const int *type;        // N: element of each atom (multi-element Tersoff)
     const void *ttab;       // multi-element Tersoff: kMaxTypes x kMaxTypes constants per
@@ -157,6 +171,7 @@ struct PairArgs {
     uint32_t *mask;         // N : bit m set <=> list slot m is inside the cutoff
     double *u;              // N : U_i
     Flags *flags;
+    int batch;              // pools: failures go to the atom's system entry (fail_system)
 };
 
 // Arguments of the per-atom gather (one thread per atom i; Eqs. 28-30 + half-kick).

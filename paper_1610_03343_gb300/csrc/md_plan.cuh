@@ -105,7 +105,10 @@ void fill_tersoff_table(const Plan &p, void *host);
 // Pair-pass block size in use (the tuned one, else the precision's default).
 int effective_pair_block(const Plan &p);
 bool valid_pair_block(int b);
-void configure_kernels(const Plan &p);
+// Opt the pair kernels into their dynamic shared memory on the current device (once per
+// device); false if that failed.
+constexpr int kMaxConfigDevices = 64;
+bool configure_kernels(const Plan &p);
 // Half-kick + drift + displacement check (first half of a velocity-Verlet step).
 void launch_kick_drift(const Plan &p, cudaStream_t s, const double *half_kick, double dt);
 // Start of a step: claim the series row, reset the pair pass's deferred count, count

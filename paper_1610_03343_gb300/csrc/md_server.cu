@@ -125,6 +125,7 @@ void runner(md_server *srv, int which)
     std::vector<int> active(pr.max_jobs);
     std::vector<int64_t> left(pr.max_jobs);
     std::vector<double> tot((size_t)pr.max_jobs * 13), kin(pr.max_jobs);
+    std::vector<int> err(pr.max_jobs);
     const int chunk = srv->opt.chunk_steps > 0 ? srv->opt.chunk_steps : 8;
     double busy_since = -1.0;
     for (;;) {
@@ -163,8 +164,9 @@ void runner(md_server *srv, int which)
         for (auto &kv : pr.running) resident += (double)kv.second->n;
         md_status s = md_run(pr.ctx, chunk, pr.dt, nullptr);
         if (s == MD_OK) s = md_batch_status(pr.ctx, active.data(), left.data(), tot.data(), kin.data());
+        if (s == MD_OK) s = md_batch_errors(pr.ctx, err.data());
         const double t_harvest = srv->now();
-        if (s != MD_OK) {   // fail every running job of this pool
+        if (s != MD_OK) {   // the pool itself failed (a CUDA error): fail every running job
             for (auto &kv : pr.running) {
                 md_batch_remove(pr.ctx, kv.first);
                 finish(srv, kv.second, s);
@@ -172,11 +174,19 @@ void runner(md_server *srv, int which)
             pr.running.clear();
             continue;
         }
+        // a job that failed on the device (non-finite values, an overlong list, ...) was
+        // stopped there alone: it fails with that status, the others go on
         std::vector<int> done;
         for (auto &kv : pr.running)
             if (active[kv.first] == 0) done.push_back(kv.first);
         for (int slot : done) {
             std::shared_ptr<Job> j = pr.running[slot];
+            if (err[slot] != MD_OK) {
+                md_batch_remove(pr.ctx, slot);
+                pr.running.erase(slot);
+                finish(srv, j, err[slot]);
+                continue;
+            }
             const md_status g = md_batch_get_state(pr.ctx, slot, j->x_out, j->v_out);
             j->res.U = tot[(size_t)slot * 13];
             j->res.K = kin[slot];
@@ -297,6 +307,19 @@ md_status md_server_wait(md_server *srv, int64_t job_id, md_job_result *out)
     srv->cv_done.wait(lk, [&] { return j->res.done != 0; });
     if (out) *out = j->res;
     return MD_OK;
+}
+
+md_status md_server_wait_timeout(md_server *srv, int64_t job_id, double timeout_s, md_job_result *out)
+{
+    if (!srv || !(timeout_s >= 0)) return MD_ERR_ARG;
+    std::unique_lock<std::mutex> lk(srv->mu);
+    auto it = srv->jobs.find(job_id);
+    if (it == srv->jobs.end()) return MD_ERR_ARG;
+    std::shared_ptr<Job> j = it->second;
+    const auto limit = std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double>(timeout_s));
+    const bool done = srv->cv_done.wait_for(lk, limit, [&] { return j->res.done != 0; });
+    if (out) *out = j->res;
+    return done ? MD_OK : MD_ERR_TIMEOUT;
 }
 
 md_status md_server_drain(md_server *srv)

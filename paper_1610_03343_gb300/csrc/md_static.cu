@@ -81,6 +81,7 @@ extern "C" md_status md_compute_static(int kind, const double *params, int preci
     if (kind != MD_TERSOFF && kind != MD_SW) return MD_ERR_ARG;
     const int64_t n = n_atoms;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    cudaGetLastError();   // an earlier call's error must not be reported as this call's
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MD_ERR_CUDA;
@@ -179,28 +180,35 @@ extern "C" md_status md_compute_static(int kind, const double *params, int preci
     p.flags = c.take<Flags>(1);
     if (c.used > c.cap) return MD_ERR_OOM;   // the cell grid pushed the layout past the array
 
-    configure_kernels(p);
-    // inputs in, zero-initialised state (the array keeps the previous call's contents)
+    if (!configure_kernels(p)) return MD_ERR_CUDA;
+    // inputs in, zero-initialised state (the array keeps the previous call's contents);
+    // every copy is checked before any kernel is launched
     const double *src[3] = {x, y, z};
+    const double *vsrc[3] = {vx, vy, vz};
     for (int a = 0; a < 3; ++a) {
-        cudaMemcpyAsync(p.pos + a * n, src[a], sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
-        const double *vs = a == 0 ? vx : (a == 1 ? vy : vz);
-        if (vs) cudaMemcpyAsync(p.vel + a * n, vs, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
-        else cudaMemsetAsync(p.vel + a * n, 0, sizeof(double) * n, s);
+        if (cudaMemcpyAsync(p.pos + a * n, src[a], sizeof(double) * n, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return MD_ERR_CUDA;
+        const cudaError_t e = vsrc[a] ? cudaMemcpyAsync(p.vel + a * n, vsrc[a], sizeof(double) * n,
+                                                        cudaMemcpyDeviceToDevice, s)
+                                      : cudaMemsetAsync(p.vel + a * n, 0, sizeof(double) * n, s);
+        if (e != cudaSuccess) return MD_ERR_CUDA;
     }
-    cudaMemsetAsync(p.type, 0, sizeof(int) * n, s);
-    cudaMemsetAsync(p.flags, 0, sizeof(Flags), s);
-    cudaMemsetAsync(p.sys, 0, sizeof(SysDev) * 2, s);
+    if (cudaMemsetAsync(p.type, 0, sizeof(int) * n, s) != cudaSuccess ||
+        cudaMemsetAsync(p.flags, 0, sizeof(Flags), s) != cudaSuccess ||
+        cudaMemsetAsync(p.sys, 0, sizeof(SysDev) * 2, s) != cudaSuccess)
+        return MD_ERR_CUDA;
     launch_rebuild(p, s);
     launch_pair_reset(p, s);
     launch_pair(p, s);
     launch_gather(p, s, nullptr, 0.0, true);
     launch_reduce(p, s, true, false);
+    if (cudaGetLastError() != cudaSuccess) return MD_ERR_CUDA;   // a launch failed
     Flags fl;
     double t[kNumPartials];
-    cudaMemcpyAsync(&fl, p.flags, sizeof(Flags), cudaMemcpyDeviceToHost, s);
-    cudaMemcpyAsync(t, p.totals, sizeof(t), cudaMemcpyDeviceToHost, s);
-    if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return MD_ERR_CUDA;
+    if (cudaMemcpyAsync(&fl, p.flags, sizeof(Flags), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(t, p.totals, sizeof(t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return MD_ERR_CUDA;
     if (fl.list_overflow || fl.active_overflow) return MD_ERR_NEIGH_OVERFLOW;
     if (fl.asym) return MD_ERR_CUDA;
     if (fl.nonfinite) return MD_ERR_NAN;

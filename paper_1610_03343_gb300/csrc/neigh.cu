@@ -249,7 +249,7 @@ __device__ __forceinline__ ListFrame list_frame(const float *posf, int64_t N, in
 template <bool BATCH>
 __device__ __forceinline__ void build_list_atom(int64_t i, int64_t N, const double *pos, const float *posf,
                                                 Box box0, int nc0, int nc1, int nc2, const int *sys_of,
-                                                const SysDev *sys, const int *atom_cell, const int *cell_start,
+                                                SysDev *sys, const int *atom_cell, const int *cell_start,
                                                 const int *cell_count, const int *cell_atoms, float rlm2, int cap,
                                                 int *nn, int *nl, double *pos_build, Flags *flags)
 {
@@ -331,7 +331,10 @@ __device__ __forceinline__ void build_list_atom(int64_t i, int64_t N, const doub
     const int keep = cnt < cap ? cnt : cap;
     for (int m = 0; m < keep; ++m) nl[(int64_t)m * N + i] = loc[m];
     nn[i] = keep;
-    if (cnt > cap) flags->list_overflow = 1;
+    if (cnt > cap) {
+        if (BATCH) fail_system(sys[sys_of[i]], MD_ERR_NEIGH_OVERFLOW);   // this system only
+        else flags->list_overflow = 1;
+    }
     atomicMax(&flags->max_nn, cnt);
 }
 
@@ -368,7 +371,7 @@ __global__ void k_cell_fill(int64_t N, const int *atom_cell, const int *atom_ran
     if (i < N) cell_fill_atom<false>(i, atom_cell, atom_rank, cell_start, cell_atoms, nullptr, nullptr);
 }
 __global__ void k_build_list(int64_t N, const double *pos, const float *posf, Box box, int nc0, int nc1, int nc2,
-                             const SysDev *sys1, const int *atom_cell, const int *cell_start,
+                             SysDev *sys1, const int *atom_cell, const int *cell_start,
                              const int *cell_count, const int *cell_atoms, float rlm2, int cap, int *nn, int *nl,
                              double *pos_build, Flags *flags)
 {
@@ -517,7 +520,7 @@ __global__ void __launch_bounds__(kChunk) k_cell_fill_pool(const int *plan, cons
 }
 __global__ void __launch_bounds__(kChunk) k_build_list_pool(const int *plan, const int *chunks, int64_t N,
                                                             const double *pos, const float *posf,
-                                                            const int *sys_of, const SysDev *sys,
+                                                            const int *sys_of, SysDev *sys,
                                                             const int *atom_cell, const int *cell_start,
                                                             const int *cell_count, const int *cell_atoms, int cap,
                                                             int *nn, int *nl, double *pos_build, Flags *flags)
@@ -539,7 +542,9 @@ __global__ void __launch_bounds__(kChunk) k_build_rev_pool(const int *plan, cons
         const int64_t i = chunks[k] + threadIdx.x;
         SysDev &sd = sys[sys_of[i]];
         if (i - sd.atom_start >= sd.n_atoms) continue;
-        build_rev_atom<false>(i, N, nn, nl, rev, nullptr, nullptr, flags);
+        // a system whose list overflowed has truncated, asymmetric lists: it has failed
+        // and stopped, and its reverse slots are not needed
+        if (sd.error == 0) build_rev_atom<false>(i, N, nn, nl, rev, nullptr, nullptr, flags);
         count[atom_cell[i]] = 0;
         if (i == sd.atom_start) {
             sd.rebuild = 0;
@@ -628,7 +633,7 @@ int rebuild_single(const Plan &p, cudaStream_t s)
     const int T = 256;
     cudaMemsetAsync(p.cell_count, 0, sizeof(int) * p.ncell, s);
     cudaMemsetAsync(&p.flags->max_nn, 0, sizeof(int), s);
-    const SysDev *sys1 = p.npt ? p.sys : nullptr;
+    SysDev *sys1 = p.npt ? p.sys : nullptr;
     k_cell_count<<<blocks_for(p.N, T), T, 0, s>>>(p.N, p.pos, p.posf, p.box, p.nc[0], p.nc[1], p.nc[2], sys1,
                                                  p.atom_cell, p.atom_rank, p.cell_count);
     const int64_t nb = (p.ncell + kScanElems - 1) / kScanElems;

@@ -115,11 +115,13 @@ _lock = threading.Lock()
 _lib = None
 
 EXPORTS = ["md_default_options", "md_create", "md_set_positions", "md_set_velocities", "md_compute",
-           "md_run", "md_get_state", "md_set_npt", "md_get_box", "md_get_stats", "md_set_graph_mode", "md_set_profiling",
-           "md_kernel_times", "md_autotune", "md_set_tuning", "md_get_tuning", "md_batch_create", "md_batch_add", "md_batch_remove", "md_batch_status",
+           "md_run", "md_get_state", "md_checkpoint_size", "md_checkpoint_save", "md_checkpoint_load",
+           "md_set_npt", "md_get_box", "md_get_stats", "md_set_graph_mode", "md_set_profiling",
+           "md_kernel_times", "md_autotune", "md_set_tuning", "md_get_tuning", "md_batch_create", "md_batch_add", "md_batch_remove", "md_batch_status", "md_batch_errors",
            "md_batch_get_state", "md_server_create", "md_server_submit", "md_server_poll", "md_server_wait",
+           "md_server_wait_timeout",
            "md_server_drain", "md_server_stats_get", "md_server_clock", "md_server_destroy",
-           "md_compute_static", "md_hcacf", "md_fastmath_eval", "md_last_error", "md_destroy"]
+           "md_compute_static", "md_hcacf", "md_fastmath_eval", "md_peak_flops", "md_last_error", "md_destroy"]
 
 
 def library_path() -> str:
@@ -147,6 +149,9 @@ def load(build_if_missing: bool = False):
         lib.md_compute.argtypes = [P, P, P, P, P, P]
         lib.md_run.argtypes = [P, ctypes.c_int64, ctypes.c_double, P]
         lib.md_get_state.argtypes = [P, P, P]
+        lib.md_checkpoint_size.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
+        lib.md_checkpoint_save.argtypes = [P, P, ctypes.c_size_t]
+        lib.md_checkpoint_load.argtypes = [P, P, ctypes.c_size_t]
         lib.md_set_npt.argtypes = [P, ctypes.c_int, ctypes.POINTER(md_npt)]
         lib.md_get_box.argtypes = [P, ctypes.c_int, P]
         lib.md_get_stats.argtypes = [P, ctypes.POINTER(md_stats)]
@@ -164,12 +169,14 @@ def load(build_if_missing: bool = False):
         lib.md_batch_add.argtypes = [P, ctypes.POINTER(md_system), ctypes.POINTER(ctypes.c_int)]
         lib.md_batch_remove.argtypes = [P, ctypes.c_int]
         lib.md_batch_status.argtypes = [P, P, P, P, P]
+        lib.md_batch_errors.argtypes = [P, P]
         lib.md_batch_get_state.argtypes = [P, ctypes.c_int, P, P]
         lib.md_server_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(md_server_options),
                                          ctypes.POINTER(md_params), P, ctypes.POINTER(md_params), P]
         lib.md_server_submit.argtypes = [P, ctypes.POINTER(md_job), ctypes.POINTER(ctypes.c_int64)]
         lib.md_server_poll.argtypes = [P, ctypes.c_int64, ctypes.POINTER(md_job_result)]
         lib.md_server_wait.argtypes = [P, ctypes.c_int64, ctypes.POINTER(md_job_result)]
+        lib.md_server_wait_timeout.argtypes = [P, ctypes.c_int64, ctypes.c_double, ctypes.POINTER(md_job_result)]
         lib.md_server_drain.argtypes = [P]
         lib.md_server_stats_get.argtypes = [P, ctypes.POINTER(md_server_stats)]
         lib.md_server_clock.argtypes = [P]
@@ -182,6 +189,8 @@ def load(build_if_missing: bool = False):
                                  ctypes.c_double, ctypes.c_double, P, P, ctypes.c_int, P]
         lib.md_fastmath_eval.argtypes = [ctypes.c_int, ctypes.c_int64, P, P]
         lib.md_fastmath_eval.restype = ctypes.c_int
+        lib.md_peak_flops.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int, P, P]
+        lib.md_peak_flops.restype = ctypes.c_int
         lib.md_last_error.argtypes = [P]
         lib.md_last_error.restype = ctypes.c_char_p
         lib.md_destroy.argtypes = [P]
@@ -267,6 +276,27 @@ def md_get_state(ctx, x=None, v=None):
     _check(lib, ctx, lib.md_get_state(ctx, _ptr(x), _ptr(v)))
 
 
+def md_checkpoint_size(ctx) -> int:
+    lib = load()
+    n = ctypes.c_size_t()
+    _check(lib, ctx, lib.md_checkpoint_size(ctx, ctypes.byref(n)))
+    return n.value
+
+
+def md_checkpoint_save(ctx) -> np.ndarray:
+    """The context's full state as a host byte array (md_checkpoint_save)."""
+    lib = load()
+    buf = np.zeros(md_checkpoint_size(ctx), dtype=np.uint8)
+    _check(lib, ctx, lib.md_checkpoint_save(ctx, _ptr(buf), buf.size))
+    return buf
+
+
+def md_checkpoint_load(ctx, buf):
+    lib = load()
+    buf = np.ascontiguousarray(buf, dtype=np.uint8)
+    _check(lib, ctx, lib.md_checkpoint_load(ctx, _ptr(buf), buf.size))
+
+
 def md_set_npt(ctx, system=0, T0=300.0, P0=0.0, tau_T=100.0, tau_P=1000.0, beta=0.01, couple=(1, 1, 1),
                off=False):
     """Berendsen coupling of one system (off=True: back to NVE)."""
@@ -297,6 +327,17 @@ def md_fastmath_eval(fn: int, x) -> np.ndarray:
     if st != 0:
         raise MDError(st, "md_fastmath_eval failed")
     return y
+
+
+def md_peak_flops(precision: int, iters: int, repeats: int = 3):
+    """(TFLOP/s, ms) of the FMA-chain peak kernel in fp64 (MD_FP64) or fp32 (MD_MIXED)."""
+    lib = load()
+    tf = ctypes.c_double()
+    ms = ctypes.c_double()
+    st = lib.md_peak_flops(int(precision), int(iters), int(repeats), ctypes.byref(tf), ctypes.byref(ms))
+    if st != 0:
+        raise MDError(st, "md_peak_flops failed")
+    return tf.value, ms.value
 
 
 def md_get_stats(ctx) -> md_stats:
@@ -394,6 +435,14 @@ def md_batch_status(ctx, max_systems):
     return active, left, tot, kin
 
 
+def md_batch_errors(ctx, max_systems) -> np.ndarray:
+    """Per-slot md_status of systems that failed on the device (0: none)."""
+    lib = load()
+    st = np.zeros(max_systems, dtype=np.int32)
+    _check(lib, ctx, lib.md_batch_errors(ctx, _ptr(st)))
+    return st
+
+
 def md_batch_get_state(ctx, sys_id, x=None, v=None):
     lib = load()
     _check(lib, ctx, lib.md_batch_get_state(ctx, int(sys_id), _ptr(x), _ptr(v)))
@@ -446,6 +495,16 @@ def md_server_wait(srv, job_id) -> md_job_result:
     return r
 
 
+def md_server_wait_timeout(srv, job_id, timeout_s):
+    """(status, result): status MD_OK when the job finished within timeout_s seconds,
+    MD_ERR_TIMEOUT when it had not (the job keeps running)."""
+    r = md_job_result()
+    st = load().md_server_wait_timeout(srv, int(job_id), float(timeout_s), ctypes.byref(r))
+    if st not in (MD_OK, MD_ERR_TIMEOUT):
+        raise MDError(st, "md_server_wait_timeout failed")
+    return st, r
+
+
 def md_server_drain(srv):
     st = load().md_server_drain(srv)
     if st != MD_OK:
@@ -467,10 +526,34 @@ def md_server_destroy(srv):
         load().md_server_destroy(srv)
 
 
+def _check_device_f64(name, t, count):
+    """t must be None or a contiguous float64 CUDA tensor of at least `count` elements:
+    the library reads and writes it as raw device memory."""
+    if t is None:
+        return
+    if not hasattr(t, "data_ptr") or not getattr(t, "is_cuda", False):
+        raise ValueError(f"{name}: a CUDA tensor is required")
+    import torch
+    if t.dtype != torch.float64 or not t.is_contiguous():
+        raise ValueError(f"{name}: a contiguous float64 tensor is required")
+    if t.numel() < count:
+        raise ValueError(f"{name}: {t.numel()} elements, at least {count} required")
+
+
 def md_compute_static(kind, params, precision, box, pbc, n_atoms, x, y, z, vx, vy, vz, mass,
                       f=None, u=None, w=None, j=None, totals=None, stream=None):
-    """Allocation-free force evaluation (device pointers / torch CUDA tensors in and out)."""
+    """Allocation-free force evaluation (torch CUDA tensors in and out; totals a host
+    float64 array of 13, or None)."""
     lib = load()
+    if totals is not None and not (isinstance(totals, np.ndarray) and totals.dtype == np.float64
+                                   and totals.flags["C_CONTIGUOUS"] and totals.size >= 13):
+        raise ValueError("totals: a contiguous host float64 array of at least 13 elements is required")
+    n = int(n_atoms)
+    for name, t, c in (("x", x, n), ("y", y, n), ("z", z, n), ("vx", vx, n), ("vy", vy, n), ("vz", vz, n),
+                       ("f", f, 3 * n), ("u", u, n), ("w", w, 9 * n), ("j", j, 3 * n)):
+        if name in ("x", "y", "z") and t is None:
+            raise ValueError(f"{name}: positions are required")
+        _check_device_f64(name, t, c)
     prm = np.ascontiguousarray(params, dtype=np.float64)
     b = np.ascontiguousarray(box, dtype=np.float64)
     pb = np.ascontiguousarray(pbc, dtype=np.int32)
@@ -623,6 +706,12 @@ class System:
     def stats(self):
         return md_get_stats(self.ctx)
 
+    def checkpoint(self) -> np.ndarray:
+        return md_checkpoint_save(self.ctx)
+
+    def restore(self, image):
+        md_checkpoint_load(self.ctx, image)
+
     def set_npt(self, off=False, **kw):
         md_set_npt(self.ctx, 0, off=off, **kw)
 
@@ -710,6 +799,9 @@ class Pool:
 
     def status(self):
         return md_batch_status(self.ctx, self.max_systems)
+
+    def errors(self):
+        return md_batch_errors(self.ctx, self.max_systems)
 
     def state(self, sid):
         n = self.n_atoms[sid]

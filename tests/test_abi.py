@@ -77,3 +77,22 @@ def test_null_context_calls_return_arg_error(lib):
     assert lib.md_compute(None, None, None, None, None, None) == -1
     assert lib.md_last_error(None) == b""
     lib.md_destroy(None)
+
+
+def test_static_binding_rejects_host_arrays_and_short_outputs(lib):
+    """md_compute_static writes through raw device pointers: the binding refuses host
+    arrays, wrong dtypes and short outputs before calling the library."""
+    from paper_1610_03343_gb300 import inputs, md
+    s = inputs.si_diamond_tersoff(n=2)
+    x = np.ascontiguousarray(s.pos[:, 0])
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        md.md_compute_static(s.kind, s.params, md.MD_FP64, s.box, s.pbc, s.n, x, x, x, None, None, None,
+                             s.mass)
+    torch = pytest.importorskip("torch")
+    t32 = torch.zeros(s.n, dtype=torch.float32)
+    with pytest.raises(ValueError):
+        md.md_compute_static(s.kind, s.params, md.MD_FP64, s.box, s.pbc, s.n, t32, t32, t32, None, None, None,
+                             s.mass)
+    with pytest.raises(ValueError, match="totals"):
+        md.md_compute_static(s.kind, s.params, md.MD_FP64, s.box, s.pbc, s.n, None, None, None, None, None,
+                             None, s.mass, totals=np.zeros(5))

@@ -189,6 +189,36 @@ def test_trajectory_matches_oracle(md, make, steps, dt):
     assert st.steps_done == steps
 
 
+MIXED_TRAJ = [
+    ("tersoff_si_1728", lambda: I.si_diamond_tersoff(n=6), 1.0),
+    ("tersoff_c_graphene_960", lambda: I.c_graphene_tersoff(nx=10, ny=24), 0.5),
+    ("sw_si_1000", lambda: I.si_diamond_sw(n=5, jitter_amp=0.05), 1.0),
+]
+
+
+@pytest.mark.parametrize("name,make,dt", MIXED_TRAJ, ids=[c[0] for c in MIXED_TRAJ])
+def test_mixed_trajectory_matches_oracle(md, name, make, dt):
+    """Mixed path over 50 NVE steps against the fp64 oracle.  Bounds, from the force bound:
+    a relative force error e < 1e-5 on forces of ~1 eV/A moves an atom of mass m by at most
+    about (e/m) t^2/2 (acceleration unit 9.65e-3 A/fs^2 per eV/(A amu)), below 1e-5 A after
+    50 fs for m >= 12 amu, so positions within 1e-4 A; the per-step energies carry fp32 sums
+    of per-atom terms (relative 1e-7 each), so U and K within 1e-5 eV per atom; the heat
+    current J = sum_i M_i v_i within 1e-3 of the series' largest |J| (fp32 per-atom products,
+    and velocities that follow the slightly different forces)."""
+    s = make()
+    steps = 50
+    with md.from_inputs(s, precision=1) as g:
+        ser = g.run(steps, dt)
+        pos, vel = g.state()
+    p2, v2, ser2 = O.run(s.pos, s.vel, s.mass, s.box, s.pbc, s.kind, s.params, steps, dt)
+    d = pos - p2
+    d -= np.round(d / s.box) * s.box * s.pbc
+    assert np.abs(d).max() < 1e-4
+    for c in (0, 1):
+        assert np.abs(ser[:, c] - ser2[:, c]).max() / s.n < 1e-5, c
+    assert rel(ser[:, 2:5], ser2[:, 2:5]) < 1e-3
+
+
 def test_rebuilds_happen_and_stay_exact(md):
     """A hot, small-skin run forces several list rebuilds; results still match."""
     s = I.si_diamond_tersoff(n=3, jitter_amp=0.05, temperature=1500.0)
