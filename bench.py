@@ -575,7 +575,7 @@ def measure_peaks():
             out[f"{tag}_tflops"] = tf
             out[f"{tag}_ms_per_launch"] = ms
     out["clocks"] = clocks.summary()
-    out["how"] = ("md_peak_flops: 8 independent FMA chains per thread, 1024 threads per SM on every SM, "
+    out["how"] = ("md_peak_flops: independent FMA chains (8 per thread fp64, 16 fp32), 1024 threads per SM on every SM, "
                   "best of 8 launches timed with CUDA events, 2 flop per FMA")
     return out
 

@@ -467,9 +467,10 @@ int md_fastmath_eval(int fn, int64_t n, const double *x, double *y);
 /* Diagnostics for rooflines: the fused multiply-add peak of the current device in fp64
  * (precision = MD_FP64) or fp32 (MD_MIXED), measured -- the paper's hardware figures
  * (Sec. 3) are a vendor's, this is what the GPU at hand delivers.  A kernel of independent
- * FMA chains (8 per thread, 1024 threads per SM on every SM, `iters` FMAs per chain) runs
- * `repeats` times after a warm-up launch, each timed with CUDA events; *tflops receives the
- * best rate (2 flop per FMA, TFLOP/s) and *ms (may be NULL) that launch's time.  Allocates
+ * FMA chains (8 per thread in fp64, 16 in fp32; 1024 threads per SM on every SM; `iters`
+ * FMAs per chain) runs `repeats` times after a warm-up launch, each timed with CUDA events;
+ * *tflops receives the best rate (2 flop per FMA, TFLOP/s) and *ms (may be NULL) that
+ * launch's time.  Allocates
  * and frees a small output buffer.  MD_ERR_ARG for iters < 1, repeats < 1 or another
  * precision. */
 int md_peak_flops(int precision, int64_t iters, int repeats, double *tflops, double *ms);

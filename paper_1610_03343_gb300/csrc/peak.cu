@@ -3,10 +3,10 @@
 // The pair passes are bound by the FP64 pipe (fp64 path) or by instruction issue and the
 // FP32 pipe (mixed path), so their rooflines need the rate at which this GPU retires FMAs
 // in each precision.  A kernel of independent FMA chains measures it: every thread keeps
-// kChains accumulators a_k <- a_k * b + c (no chain depends on another, so a warp always
-// has an FMA ready to issue), 8 warps per scheduler partition on every SM, timed with CUDA
-// events around one launch after a warm-up launch.  2 flop per FMA.  The result goes to
-// out[] only so that the chains are not removed as dead code.
+// accumulators a_k <- a_k * b + c that do not depend on one another, so a warp always has an
+// FMA ready to issue (8 chains in fp64, 16 in fp32), with 8 warps per scheduler partition on
+// every SM, timed with CUDA events around one launch after a warm-up launch.  2 flop per
+// FMA.  The result goes to out[] only so that the chains are not removed as dead code.
 #include <cstdint>
 
 #include <cuda_runtime.h>
@@ -15,11 +15,12 @@
 
 namespace {
 
-constexpr int kChains = 8;
+constexpr int kChains64 = 8;    // any count from 4 to 16 gave the same fp64 rate
+constexpr int kChains32 = 16;   // fp32: 16 chains keep every scheduler's FMA pipe fed
 constexpr int kThreads = 256;
 constexpr int kBlocksPerSm = 4;   // 1024 threads = 32 warps per SM
 
-template <typename T>
+template <typename T, int kChains>
 __global__ void __launch_bounds__(kThreads) k_fma_chains(int64_t iters, T b, T c, T *out)
 {
     T a[kChains];
@@ -40,6 +41,7 @@ __global__ void __launch_bounds__(kThreads) k_fma_chains(int64_t iters, T b, T c
 template <typename T>
 int run_peak(int64_t iters, int repeats, double *tflops, double *ms_out)
 {
+    constexpr int kChains = sizeof(T) == 8 ? kChains64 : kChains32;
     int dev = 0, n_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm < 1) {
@@ -59,10 +61,10 @@ int run_peak(int64_t iters, int repeats, double *tflops, double *ms_out)
     // b slightly below 1 and c small keep every chain finite and normal for any length
     const T b = T(0.999999), c = T(1e-3);
     if (e == cudaSuccess) {
-        k_fma_chains<T><<<blocks, kThreads>>>(iters / 8 + 1, b, c, out);   // warm-up
+        k_fma_chains<T, kChains><<<blocks, kThreads>>>(iters / 8 + 1, b, c, out);   // warm-up
         for (int r = 0; r < repeats && e == cudaSuccess; ++r) {
             cudaEventRecord(e0);
-            k_fma_chains<T><<<blocks, kThreads>>>(iters, b, c, out);
+            k_fma_chains<T, kChains><<<blocks, kThreads>>>(iters, b, c, out);
             cudaEventRecord(e1);
             e = cudaEventSynchronize(e1);
             float ms = 0.f;
