@@ -345,7 +345,6 @@ __device__ __forceinline__ void tersoff_atom(const PairArgs<T> &a, const Tersoff
                                              int64_t i, const TersoffC<T> *row = nullptr)
 {
     const int64_t N = a.N;
-    const int S_ = a.stride;
     Stage<T, CAP, BLOCK> S{base, (int)threadIdx.x};
     // per unordered bond pair q: fp64, cos theta, g and dg/dcos from the zeta loop; fp32,
     // 1/(d^2 + (h - cos)^2) (slot PCS)
@@ -477,9 +476,7 @@ __device__ __forceinline__ void tersoff_atom(const PairArgs<T> &a, const Tersoff
             S(TF_DY, k) = fma(qk, ujy, S(TF_DY, k));
             S(TF_DZ, k) = fma(qk, ujz, S(TF_DZ, k));
         }
-        a.d[(int64_t)(0 * S_ + j) * N + i] = fma(Aj, ujx, vjx);
-        a.d[(int64_t)(1 * S_ + j) * N + i] = fma(Aj, ujy, vjy);
-        a.d[(int64_t)(2 * S_ + j) * N + i] = fma(Aj, ujz, vjz);
+        a.d[(int64_t)j * N + i] = Vec4<T>{fma(Aj, ujx, vjx), fma(Aj, ujy, vjy), fma(Aj, ujz, vjz), T(0)};
     }
     a.mask[i] = mask;
     a.u[i] = to_d(ui);
@@ -531,7 +528,6 @@ __device__ __forceinline__ void sw_terms(const PairArgs<T> &a, const SWC<T> &p, 
                                          uint32_t mask)
 {
     const int64_t N = a.N;
-    const int S_ = a.stride;
     Stage<T, CAP, BLOCK> S{base, slot};
     T ui = T(0);
     for (int k = 0; k < na; ++k) {
@@ -568,9 +564,7 @@ __device__ __forceinline__ void sw_terms(const PairArgs<T> &a, const SWC<T> &p, 
             S(SW_DY, k) = fma(qk, ujy, fma(ak, uky, S(SW_DY, k)));
             S(SW_DZ, k) = fma(qk, ujz, fma(ak, ukz, S(SW_DZ, k)));
         }
-        a.d[(int64_t)(0 * S_ + j) * N + i] = djx;
-        a.d[(int64_t)(1 * S_ + j) * N + i] = djy;
-        a.d[(int64_t)(2 * S_ + j) * N + i] = djz;
+        a.d[(int64_t)j * N + i] = Vec4<T>{djx, djy, djz, T(0)};
     }
     a.mask[i] = mask;
     a.u[i] = to_d(ui);
@@ -702,9 +696,7 @@ __device__ __forceinline__ void sw_atom_warp(const PairArgs<T> &a, const SWC<T> 
             dy = fma(q, umy, fma(ac, b.uy, dy));
             dz = fma(q, umz, fma(ac, b.uz, dz));
         }
-        a.d[(int64_t)(0 * S_ + k) * N + i] = dx;
-        a.d[(int64_t)(1 * S_ + k) * N + i] = dy;
-        a.d[(int64_t)(2 * S_ + k) * N + i] = dz;
+        a.d[(int64_t)k * N + i] = Vec4<T>{dx, dy, dz, T(0)};
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) ui += __shfl_xor_sync(0xffffffffu, ui, o);
@@ -977,10 +969,8 @@ __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, i
             const uint32_t maskj = a.mask[j];
             const int kr = __popc(maskj & ((1u << mr) - 1u));
             if (kr < MAXA) {
-                const T dx = a.d[(int64_t)(0 * MAXA + k) * N + i], dy = a.d[(int64_t)(1 * MAXA + k) * N + i],
-                        dz = a.d[(int64_t)(2 * MAXA + k) * N + i];
-                const T ex = a.d[(int64_t)(0 * MAXA + kr) * N + j], ey = a.d[(int64_t)(1 * MAXA + kr) * N + j],
-                        ez = a.d[(int64_t)(2 * MAXA + kr) * N + j];
+                const Vec4<T> dv = a.d[(int64_t)k * N + i], ev = a.d[(int64_t)kr * N + j];
+                const T dx = dv.x, dy = dv.y, dz = dv.z, ex = ev.x, ey = ev.y, ez = ev.z;
                 const T rx = a.r[(int64_t)(0 * MAXA + k) * N + i], ry = a.r[(int64_t)(1 * MAXA + k) * N + i],
                         rz = a.r[(int64_t)(2 * MAXA + k) * N + i];
                 const T gx = dx - ex, gy = dy - ey, gz = dz - ez;   // F_ij = d_ij - d_ji
@@ -1062,8 +1052,8 @@ __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, i
                 const int mr = a.rev[(int64_t)m * N + i];
                 const int kr = __popc(a.mask[j] & ((1u << mr) - 1u));
                 if (kr < MAXA) {
-                    const T ex = a.d[(int64_t)(0 * MAXA + kr) * N + j], ey = a.d[(int64_t)(1 * MAXA + kr) * N + j],
-                            ez = a.d[(int64_t)(2 * MAXA + kr) * N + j];
+                    const Vec4<T> ev = a.d[(int64_t)kr * N + j];
+                    const T ex = ev.x, ey = ev.y, ez = ev.z;
                     const T rx = a.r[(int64_t)(0 * MAXA + k2) * N + i], ry = a.r[(int64_t)(1 * MAXA + k2) * N + i],
                             rz = a.r[(int64_t)(2 * MAXA + k2) * N + i];
                     const T dv = ex * vx + ey * vy + ez * vz;
@@ -1396,7 +1386,7 @@ void pair_launch_b(const Plan &p, cudaStream_t s, int list, int parts)
     a.cap = p.cap;
     a.rc2 = T(p.rc * p.rc);
     a.stride = p.maxa;
-    a.d = static_cast<T *>(p.pd);
+    a.d = static_cast<Vec4<T> *>(p.pd);
     a.r = static_cast<T *>(p.pr);
     a.sys_of = p.sys_of;
     a.sys = p.sys;
@@ -1463,7 +1453,7 @@ void gather_launch(const Plan &p, cudaStream_t s, const double *hk, double dt, b
     a.nl = p.nl;
     a.rev = p.rev;
     a.mask = p.mask;
-    a.d = static_cast<const T *>(p.pd);
+    a.d = static_cast<const Vec4<T> *>(p.pd);
     a.r = static_cast<const T *>(p.pr);
     a.u = p.u;
     a.type = p.type;

@@ -791,8 +791,8 @@ md_status ctx_alloc(md_ctx *ctx)
     AL(p.sys_of, p.batch ? N1 : 1);
     AL(p.sys, (size_t)p.n_sys + 1);
     {
-        void *v = nullptr;
-        st = dalloc(ctx, &v, 3 * (size_t)p.maxa * N1 * esz);
+        void *v = nullptr;   // dU_i/dr_ij: one 4-word vector per compact row
+        st = dalloc(ctx, &v, 4 * (size_t)p.maxa * N1 * esz);
         if (st != MD_OK) return st;
         p.pd = v;
         st = dalloc(ctx, &v, 3 * (size_t)p.maxa * N1 * esz);

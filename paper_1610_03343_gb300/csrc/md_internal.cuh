@@ -140,6 +140,14 @@ struct SWP {
     int p_int, q_int;           // exponents as integers when they are (4 and 0 in SW 1985)
 };
 
+// dU_i/dr_ij of one bond as a 16- (fp32) or 32-byte (fp64) vector: x, y, z and an unused
+// fourth word, so that the gather reads a partner's value with one vector load (one memory
+// sector) instead of three loads from three component planes.
+template <typename T>
+struct alignas(4 * sizeof(T)) Vec4 {
+    T x, y, z, w;
+};
+
 // Arguments of the per-atom pair pass (one thread per atom i; computes U_i and
 // dU_i/dr_ij for every in-cutoff neighbour j of i, Eqs. 14 / 28-30's building block).
 template <typename T>
@@ -154,8 +162,8 @@ struct PairArgs {
     // outputs, "compact active" layout: row k = k-th in-cutoff neighbour of i, with a row
     // stride of S = allocated rows (the staging capacity of a kernel may be smaller)
     int stride;             // S
-    T *d;                   // 3 x S x N : d[(c S + k) N + i] = dU_i/dr_ij (component c)
-    T *r;                   // 3 x S x N : r_ij
+    Vec4<T> *d;             // S x N : d[k N + i] = dU_i/dr_ij
+    T *r;                   // 3 x S x N : r[(c S + k) N + i] = r_ij (component c)
     const int *sys_of;      // N: system of each atom (pools)
     SysDev *sys;            // system table (pools; a single system: its one entry)
     int dev_box;            // single system: read the box from sys[0] (it changes under NPT)
@@ -181,7 +189,7 @@ struct GatherArgs {
     const int *nl;
     const uint8_t *rev;     // cap x N: slot of i in j's list
     const uint32_t *mask;
-    const T *d;
+    const Vec4<T> *d;       // MAXA x N (see PairArgs)
     const T *r;
     const double *u;
     const int *type;

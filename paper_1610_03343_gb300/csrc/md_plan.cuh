@@ -54,7 +54,8 @@ struct Plan {
     uint8_t *rev = nullptr;
     uint32_t *mask = nullptr;
     int *ovf_count = nullptr, *ovf_list = nullptr;   // deferred atoms of the pair pass
-    // pair arrays, element type double (fp64) or float (mixed)
+    // pair arrays, element type double (fp64) or float (mixed): dU_i/dr_ij as maxa x N
+    // vectors (Vec4), bond vectors as 3 x maxa x N components
     void *pd = nullptr, *pr = nullptr;
     // cells (single system: nc; pools: per-system grids in `sys`)
     int nc[3] = {1, 1, 1};

@@ -164,7 +164,7 @@ extern "C" md_status md_compute_static(int kind, const double *params, int preci
     p.ovf_list = c.take<int>(n);
     p.sys_of = c.take<int>(1);
     p.sys = c.take<SysDev>(2);
-    p.pd = c.take<unsigned char>(3 * (size_t)p.maxa * n * esz);
+    p.pd = c.take<unsigned char>(4 * (size_t)p.maxa * n * esz);
     p.pr = c.take<unsigned char>(3 * (size_t)p.maxa * n * esz);
     p.cell_count = c.take<int>(p.ncell);
     p.cell_start = c.take<int>(p.ncell);
