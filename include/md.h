@@ -400,6 +400,69 @@ double md_server_clock(const md_server *srv);
 /* Finishes the jobs already submitted, stops the pool threads and frees the pools. */
 void md_server_destroy(md_server *srv);
 
+/* ------------------------------------------------------ spatial decomposition --------
+ * One system split over ranks (processes, typically one GPU each) in slabs along one
+ * periodic axis.  The paper runs a system on one GPU and compares with LAMMPS's MPI runs
+ * (Sec. 3); splitting needs a halo because dU_j/dr_ji of an owned atom's neighbour j depends
+ * on j's own neighbours (Eqs. 14, 28).  Rank r owns the atoms whose coordinate along `axis`
+ * (wrapped into [0, L)) lies in [r L/n, (r+1) L/n) and keeps as ghosts every atom within
+ * G = 2 (cutoff + skin + fp32 list margin) + 0.01 A of its slab, so it computes the
+ * derivatives of its first-shell ghosts itself; ghosts are neither integrated nor summed.
+ * Slabs must be at least 2G wide (MD_ERR_BOX).  Results equal the undivided system's up to
+ * summation order (bonds are taken in another order).
+ *
+ * The library packs and unpacks messages; the caller moves them between ranks (any
+ * transport: host-staged sockets, MPI, NCCL).  Each rank sends one message to its left
+ * neighbour (rank - 1 mod n) and one to its right (rank + 1 mod n) and passes md_domain_unpack
+ * the message its left neighbour sent right and the one its right neighbour sent left.
+ * Message kinds (mode):
+ *   MD_DOMAIN_POSITIONS  the current positions of the atoms the neighbour keeps as ghosts
+ *                        (every step without a rebuild);
+ *   MD_DOMAIN_MIGRATE    atoms whose slab changed (id, element, position, velocity);
+ *   MD_DOMAIN_GHOSTS     the new ghost sets (id, element, position), after a migration.
+ * A step of velocity Verlet (every rank, in this order):
+ *   md_domain_kick_drift(dt, &r)   first half-kick and drift of the owned atoms; r = 1 when
+ *                                  an owned atom moved more than skin/2 since the last build
+ *   r = OR of r over the ranks (the caller's reduction)
+ *   r == 0: exchange MD_DOMAIN_POSITIONS
+ *   r == 1: exchange MD_DOMAIN_MIGRATE, then MD_DOMAIN_GHOSTS (the list is then rebuilt)
+ *   md_domain_force(dt, totals)    forces, second half-kick; totals of the owned atoms (U, K,
+ *                                  Jx, Jy, Jz), which the caller sums over the ranks
+ * Start: md_domain_set_atoms (every rank may pass all atoms: each keeps its slab's), exchange
+ * MD_DOMAIN_GHOSTS, then md_domain_force(0) for the first forces.  Single element only. */
+typedef struct md_domain md_domain;
+enum { MD_DOMAIN_POSITIONS = 0, MD_DOMAIN_MIGRATE = 1, MD_DOMAIN_GHOSTS = 2 };
+
+/* Rank `rank` of `n_ranks` (>= 2); pbc[axis] must be 1; `capacity` bounds owned + ghost
+ * atoms on this rank (device memory is sized for it; MD_ERR_OOM when exceeded). */
+md_status md_domain_create(md_domain **out, const double box[3], const int pbc[3], int axis, int n_ranks, int rank,
+                           int64_t capacity, const md_params *params, const double *masses_by_type,
+                           const md_options *opt);
+/* Atoms (host arrays; ids unique over the system, types all 0; velocities may be NULL). */
+md_status md_domain_set_atoms(md_domain *dom, int64_t n, const int64_t *ids, const int32_t *types,
+                              const double *x, const double *y, const double *z, const double *vx,
+                              const double *vy, const double *vz);
+/* Largest message this rank may send next in each direction, in bytes. */
+md_status md_domain_message_bound(md_domain *dom, int mode, size_t *bytes);
+/* Writes the two messages of kind `mode` (each buffer at least the bound) and their sizes. */
+md_status md_domain_pack(md_domain *dom, int mode, void *to_left, void *to_right, size_t capacity,
+                         size_t *n_left, size_t *n_right);
+/* Takes the left neighbour's right-going and the right neighbour's left-going message;
+ * MD_ERR_ARG for a message of another kind or one that does not match the ghost sets. */
+md_status md_domain_unpack(md_domain *dom, int mode, const void *from_left, size_t n_left,
+                           const void *from_right, size_t n_right);
+md_status md_domain_kick_drift(md_domain *dom, double dt_fs, int *rebuild);
+/* Forces on the owned atoms; dt_fs != 0 also applies the second half-kick. */
+md_status md_domain_force(md_domain *dom, double dt_fs, double totals[5]);
+/* One force evaluation with per-atom outputs of the owned atoms, in md_domain_owned's order
+ * (host arrays: f 3n, u n, w 9n, j 3n SoA; any may be NULL) and the rank's totals[13]. */
+md_status md_domain_compute(md_domain *dom, double *f, double *u, double *w, double *j, double totals[13]);
+/* Owned atoms: count, ids (ascending), positions (wrapped, 3n SoA), velocities (3n SoA);
+ * any array may be NULL. */
+md_status md_domain_owned(md_domain *dom, int64_t *n, int64_t *ids, double *x, double *v);
+const char *md_domain_last_error(const md_domain *dom);
+void md_domain_destroy(md_domain *dom);
+
 /* ------------------------------------------------------ allocation-free evaluation --
  * The paper has no counterpart to this entry point; it exists for callers that cannot
  * allocate device memory when they need forces (code running inside another runtime's

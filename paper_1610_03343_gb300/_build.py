@@ -18,7 +18,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libmd.so")
-SOURCES = ["force.cu", "neigh.cu", "md_api.cu", "md_server.cu", "md_static.cu", "hcacf.cu", "peak.cu"]
+SOURCES = ["force.cu", "neigh.cu", "md_api.cu", "md_server.cu", "md_static.cu", "hcacf.cu", "peak.cu",
+           "md_domain.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -928,7 +928,7 @@ __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, i
     // Pools place every system on a block boundary, so a block holds one system plus
     // inactive padding atoms (which contribute zeros): one segment per block.
     const int seg = 0, nseg = 1;
-    bool live = i < N;
+    bool live = i < a.n_live;
     double damp = 0.0;
     bool fuse = a.fuse_kick != 0;
     float hs2 = a.half_skin2;
@@ -1176,6 +1176,7 @@ k_reduce(const double *partials, int nc, int seg_max, int64_t N, int block, cons
 // ------------------------------------------------------------------ integrator
 struct KickDriftArgs {
     int64_t N;
+    int64_t n_live;         // atoms integrated: [0, n_live) (ghosts beyond)
     float *posf;   // fp32 positions, refreshed every step only where the pair pass reads them
                    // between list builds (the SW prefilter); null otherwise (the list build
                    // writes its own copy)
@@ -1199,7 +1200,7 @@ struct KickDriftArgs {
 template <bool BATCH, bool NPT>
 __device__ __forceinline__ void kick_drift_atom(const KickDriftArgs &a, int64_t i)
 {
-    if (i >= a.N) return;
+    if (i >= a.n_live) return;
     if (BATCH && !a.sys[a.sys_of[i]].active) return;
     const int64_t N = a.N;
     const double h = a.hk[a.type[i]];
@@ -1450,6 +1451,7 @@ void gather_launch(const Plan &p, cudaStream_t s, const double *hk, double dt, b
 {
     GatherArgs<T> a;
     a.N = p.N;
+    a.n_live = p.n_owned >= 0 ? p.n_owned : p.N;
     a.nl = p.nl;
     a.rev = p.rev;
     a.mask = p.mask;
@@ -1557,6 +1559,7 @@ void launch_kick_drift(const Plan &p, cudaStream_t s, const double *hk, double d
     if (p.N == 0) return;
     KickDriftArgs a;
     a.N = p.N;
+    a.n_live = p.n_owned >= 0 ? p.n_owned : p.N;
     a.sys_of = p.sys_of;
     a.sys = p.sys;
     a.pos = p.pos;

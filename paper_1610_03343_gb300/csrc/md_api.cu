@@ -1780,3 +1780,19 @@ void md_destroy(md_ctx *ctx)
 }
 
 }  // extern "C"
+
+namespace mdk {
+
+// Parameter and option parsing shared with the spatial decomposition (md_domain.cu).
+md_status plan_params(const md_params *params, Plan &p, int idx, double *rc)
+{
+    return parse_params(params, p, idx, rc);
+}
+md_status plan_options(Plan &p, const md_options &opt, int kind, double rc)
+{
+    if (check_options(opt) != MD_OK) return MD_ERR_ARG;
+    apply_options(p, opt, kind, rc);
+    return MD_OK;
+}
+
+}  // namespace mdk

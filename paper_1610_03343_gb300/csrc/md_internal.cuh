@@ -186,6 +186,7 @@ struct PairArgs {
 template <typename T>
 struct GatherArgs {
     int64_t N;
+    int64_t n_live;         // atoms gathered, kicked and summed: [0, n_live) (ghosts beyond)
     const int *nl;
     const uint8_t *rev;     // cap x N: slot of i in j's list
     const uint32_t *mask;

@@ -8,6 +8,11 @@ namespace mdk {
 
 struct Plan {
     int64_t N = 0;         // atoms (a pool: its atom capacity)
+    // spatial decomposition: atoms [0, n_owned) are this rank's, the rest ghosts whose
+    // positions another rank supplies -- ghosts take part in the list and the pair pass
+    // (their neighbourhoods complete the owned atoms' forces) but are not integrated,
+    // gathered or summed.  -1: every atom is owned.
+    int64_t n_owned = -1;
     Box box{};             // box of the single system (pools: per-system boxes in `sys`)
     int kind = 0;          // 1 Tersoff, 2 SW
     int precision = 0;     // 0 fp64, 1 mixed
@@ -78,6 +83,11 @@ struct Plan {
     double *series = nullptr;   // rows x n_sys x 5
     Flags *flags = nullptr;
 };
+
+// md_api.cu: one parameter set of md_params into set idx of p (its cutoff in *rc), and the
+// options that fix a plan's precision, list capacities, cutoff and skin (MD_ERR_ARG if bad).
+md_status plan_params(const md_params *params, Plan &p, int idx, double *rc);
+md_status plan_options(Plan &p, const md_options &opt, int kind, double rc);
 
 // Kernel classes, for per-kernel timing.
 enum KernelClass { KC_KICK_DRIFT = 0, KC_REBUILD, KC_PAIR, KC_GATHER, KC_REDUCE, KC_COUNT };

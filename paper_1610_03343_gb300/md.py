@@ -25,6 +25,7 @@ MD_IO_HOST = 0
 MD_IO_DEVICE = 1
 MD_ERR_ARG, MD_ERR_BOX, MD_ERR_NEIGH_OVERFLOW, MD_ERR_OOM = -1, -2, -3, -4
 MD_ERR_CUDA, MD_ERR_TIMEOUT, MD_ERR_NAN, MD_ERR_STATE = -5, -6, -7, -8
+MD_DOMAIN_POSITIONS, MD_DOMAIN_MIGRATE, MD_DOMAIN_GHOSTS = 0, 1, 2
 
 STATUS = {0: "MD_OK", -1: "MD_ERR_ARG", -2: "MD_ERR_BOX", -3: "MD_ERR_NEIGH_OVERFLOW",
           -4: "MD_ERR_OOM", -5: "MD_ERR_CUDA", -6: "MD_ERR_TIMEOUT", -7: "MD_ERR_NAN",
@@ -121,7 +122,10 @@ EXPORTS = ["md_default_options", "md_create", "md_set_positions", "md_set_veloci
            "md_batch_get_state", "md_server_create", "md_server_submit", "md_server_poll", "md_server_wait",
            "md_server_wait_timeout",
            "md_server_drain", "md_server_stats_get", "md_server_clock", "md_server_destroy",
-           "md_compute_static", "md_hcacf", "md_fastmath_eval", "md_peak_flops", "md_last_error", "md_destroy"]
+           "md_compute_static", "md_hcacf", "md_fastmath_eval", "md_peak_flops",
+           "md_domain_create", "md_domain_set_atoms", "md_domain_message_bound", "md_domain_pack",
+           "md_domain_unpack", "md_domain_kick_drift", "md_domain_force", "md_domain_compute", "md_domain_owned",
+           "md_domain_last_error", "md_domain_destroy", "md_last_error", "md_destroy"]
 
 
 def library_path() -> str:
@@ -191,12 +195,28 @@ def load(build_if_missing: bool = False):
         lib.md_fastmath_eval.restype = ctypes.c_int
         lib.md_peak_flops.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int, P, P]
         lib.md_peak_flops.restype = ctypes.c_int
+        lib.md_domain_create.argtypes = [ctypes.POINTER(P), P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int64, ctypes.POINTER(md_params), P, ctypes.POINTER(md_options)]
+        lib.md_domain_set_atoms.argtypes = [P, ctypes.c_int64, P, P, P, P, P, P, P, P]
+        lib.md_domain_message_bound.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
+        lib.md_domain_pack.argtypes = [P, ctypes.c_int, P, P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t),
+                                       ctypes.POINTER(ctypes.c_size_t)]
+        lib.md_domain_unpack.argtypes = [P, ctypes.c_int, P, ctypes.c_size_t, P, ctypes.c_size_t]
+        lib.md_domain_kick_drift.argtypes = [P, ctypes.c_double, ctypes.POINTER(ctypes.c_int)]
+        lib.md_domain_force.argtypes = [P, ctypes.c_double, P]
+        lib.md_domain_compute.argtypes = [P, P, P, P, P, P]
+        lib.md_domain_owned.argtypes = [P, ctypes.POINTER(ctypes.c_int64), P, P, P]
+        lib.md_domain_last_error.argtypes = [P]
+        lib.md_domain_last_error.restype = ctypes.c_char_p
+        lib.md_domain_destroy.argtypes = [P]
+        lib.md_domain_destroy.restype = None
         lib.md_last_error.argtypes = [P]
         lib.md_last_error.restype = ctypes.c_char_p
         lib.md_destroy.argtypes = [P]
         lib.md_destroy.restype = None
         for f in EXPORTS:
-            if f not in ("md_last_error", "md_destroy", "md_server_clock", "md_server_destroy"):
+            if f not in ("md_last_error", "md_destroy", "md_server_clock", "md_server_destroy",
+                         "md_domain_last_error", "md_domain_destroy"):
                 getattr(lib, f).restype = S
         _lib = lib
         return lib
@@ -892,3 +912,305 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+# ----------------------------------------------------------------- spatial decomposition
+def _dcheck(lib, dom, status):
+    if status != MD_OK:
+        raise MDError(status, lib.md_domain_last_error(dom).decode() if dom else "")
+
+
+def md_domain_create(box, pbc, axis, n_ranks, rank, capacity, kind, params, mass, opt: md_options | None = None):
+    lib = load()
+    box = np.ascontiguousarray(box, dtype=np.float64)
+    pbc = np.ascontiguousarray(pbc, dtype=np.int32)
+    prm_arr = np.ascontiguousarray(params, dtype=np.float64)
+    prm = md_params(int(kind), 1, prm_arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    masses = np.ascontiguousarray([float(mass)], dtype=np.float64)
+    dom = ctypes.c_void_p()
+    st = lib.md_domain_create(ctypes.byref(dom), _ptr(box), _ptr(pbc), int(axis), int(n_ranks), int(rank),
+                              int(capacity), ctypes.byref(prm), _ptr(masses),
+                              ctypes.byref(opt) if opt is not None else None)
+    if st != MD_OK:
+        raise MDError(st, "md_domain_create failed")
+    return dom
+
+
+def md_domain_set_atoms(dom, ids, types, x, y, z, vx=None, vy=None, vz=None):
+    lib = load()
+    _dcheck(lib, dom, lib.md_domain_set_atoms(dom, len(ids), _ptr(ids), _ptr(types), _ptr(x), _ptr(y), _ptr(z),
+                                              _ptr(vx), _ptr(vy), _ptr(vz)))
+
+
+def md_domain_message_bound(dom, mode) -> int:
+    lib = load()
+    n = ctypes.c_size_t()
+    _dcheck(lib, dom, lib.md_domain_message_bound(dom, int(mode), ctypes.byref(n)))
+    return n.value
+
+
+def md_domain_pack(dom, mode):
+    """(to_left, to_right) byte arrays of kind `mode`."""
+    lib = load()
+    cap = md_domain_message_bound(dom, mode)
+    bl = np.empty(cap, dtype=np.uint8)
+    br = np.empty(cap, dtype=np.uint8)
+    nl, nr = ctypes.c_size_t(), ctypes.c_size_t()
+    _dcheck(lib, dom, lib.md_domain_pack(dom, int(mode), _ptr(bl), _ptr(br), cap, ctypes.byref(nl), ctypes.byref(nr)))
+    return bl[: nl.value], br[: nr.value]
+
+
+def md_domain_unpack(dom, mode, from_left, from_right):
+    lib = load()
+    fl = np.ascontiguousarray(from_left, dtype=np.uint8)
+    fr = np.ascontiguousarray(from_right, dtype=np.uint8)
+    _dcheck(lib, dom, lib.md_domain_unpack(dom, int(mode), _ptr(fl), fl.size, _ptr(fr), fr.size))
+
+
+def md_domain_kick_drift(dom, dt) -> bool:
+    lib = load()
+    r = ctypes.c_int()
+    _dcheck(lib, dom, lib.md_domain_kick_drift(dom, float(dt), ctypes.byref(r)))
+    return bool(r.value)
+
+
+def md_domain_force(dom, dt) -> np.ndarray:
+    lib = load()
+    t = np.zeros(5)
+    _dcheck(lib, dom, lib.md_domain_force(dom, float(dt), _ptr(t)))
+    return t
+
+
+def md_domain_owned(dom):
+    """(ids, x (n,3), v (n,3)) of the owned atoms."""
+    lib = load()
+    n = ctypes.c_int64()
+    _dcheck(lib, dom, lib.md_domain_owned(dom, ctypes.byref(n), None, None, None))
+    k = n.value
+    ids = np.empty(max(k, 1), dtype=np.int64)
+    x = np.empty(3 * max(k, 1))
+    v = np.empty(3 * max(k, 1))
+    _dcheck(lib, dom, lib.md_domain_owned(dom, ctypes.byref(n), _ptr(ids), _ptr(x), _ptr(v)))
+    return ids[:k].copy(), x[: 3 * k].reshape(3, k).T.copy(), v[: 3 * k].reshape(3, k).T.copy()
+
+
+def md_domain_compute(dom):
+    """Per-atom F, U, W, J of the owned atoms (md_domain_owned's order) and the rank's totals."""
+    lib = load()
+    n = ctypes.c_int64()
+    _dcheck(lib, dom, lib.md_domain_owned(dom, ctypes.byref(n), None, None, None))
+    k = n.value
+    mk = lambda c: np.empty(c * max(k, 1))
+    f, u, w, j, tot = mk(3), mk(1), mk(9), mk(3), np.zeros(13)
+    _dcheck(lib, dom, lib.md_domain_compute(dom, _ptr(f), _ptr(u), _ptr(w), _ptr(j), _ptr(tot)))
+    return {"F": f[: 3 * k].reshape(3, k).T.copy(), "U": u[:k].copy(), "W": w[: 9 * k].reshape(9, k).T.copy(),
+            "J": j[: 3 * k].reshape(3, k).T.copy(), "totals": tot}
+
+
+def md_domain_last_error(dom) -> str:
+    return load().md_domain_last_error(dom).decode()
+
+
+def md_domain_destroy(dom):
+    if dom:
+        load().md_domain_destroy(dom)
+
+
+def domain_route(outboxes):
+    """Messages between slab ranks: outboxes[r] = (to_left, to_right) of rank r; returns
+    inboxes[r] = (from_left, from_right), where from_left is what rank r - 1 sent right and
+    from_right what rank r + 1 sent left (indices mod the rank count)."""
+    n = len(outboxes)
+    return [(outboxes[(r - 1) % n][1], outboxes[(r + 1) % n][0]) for r in range(n)]
+
+
+class DomainGroup:
+    """Every rank of a slab decomposition held in one process (one GPU), the messages routed
+    in memory: each phase runs for all ranks before the next, so no rank waits for another
+    inside a kernel.  For tests and single-GPU use of the decomposed path."""
+
+    def __init__(self, box, pbc, axis, n_ranks, capacity, kind, params, mass, precision=MD_FP64, skin=0.0):
+        opt = md_default_options()
+        opt.precision = precision
+        opt.skin = skin
+        self.n = int(n_ranks)
+        self.doms = [md_domain_create(box, pbc, axis, n_ranks, r, capacity, kind, params, mass, opt)
+                     for r in range(self.n)]
+        self.rebuilds = 0
+
+    def close(self):
+        for d in self.doms:
+            md_domain_destroy(d)
+        self.doms = []
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def exchange(self, mode):
+        inbox = domain_route([md_domain_pack(d, mode) for d in self.doms])
+        for d, (fl, fr) in zip(self.doms, inbox):
+            md_domain_unpack(d, mode, fl, fr)
+
+    def start(self, pos, vel, ids=None):
+        """All atoms of the system (every rank keeps its slab's), ghosts, first forces."""
+        pos = np.asarray(pos, dtype=np.float64)
+        n = pos.shape[0]
+        ids = np.arange(n, dtype=np.int64) if ids is None else np.ascontiguousarray(ids, dtype=np.int64)
+        soa = np.ascontiguousarray(pos.T)
+        v = np.ascontiguousarray(np.asarray(vel, dtype=np.float64).T)
+        ty = np.zeros(n, dtype=np.int32)
+        for d in self.doms:
+            md_domain_set_atoms(d, ids, ty, soa[0], soa[1], soa[2], v[0], v[1], v[2])
+        self.exchange(MD_DOMAIN_GHOSTS)
+        return sum(md_domain_force(d, 0.0) for d in self.doms)
+
+    def step(self, dt):
+        """One velocity-Verlet step on every rank; the system's U, K, Jx, Jy, Jz."""
+        if any([md_domain_kick_drift(d, dt) for d in self.doms]):
+            self.exchange(MD_DOMAIN_MIGRATE)
+            self.exchange(MD_DOMAIN_GHOSTS)
+            self.rebuilds += 1
+        else:
+            self.exchange(MD_DOMAIN_POSITIONS)
+        tot = np.zeros(5)
+        for d in self.doms:     # rank order: a fixed summation order
+            tot += md_domain_force(d, dt)
+        return tot
+
+    def run(self, n_steps, dt):
+        return np.array([self.step(dt) for _ in range(n_steps)])
+
+    def state(self, n_atoms):
+        """Positions and velocities (n_atoms, 3) by atom id, gathered from the ranks."""
+        x = np.full((n_atoms, 3), np.nan)
+        v = np.full((n_atoms, 3), np.nan)
+        for d in self.doms:
+            ids, xo, vo = md_domain_owned(d)
+            x[ids] = xo
+            v[ids] = vo
+        return x, v
+
+    def compute(self, n_atoms):
+        out = {k: np.full((n_atoms, c), np.nan) for k, c in (("F", 3), ("U", 1), ("W", 9), ("J", 3))}
+        tot = np.zeros(13)
+        for d in self.doms:
+            ids, _, _ = md_domain_owned(d)
+            r = md_domain_compute(d)
+            for k in ("F", "W", "J"):
+                out[k][ids] = r[k]
+            out["U"][ids, 0] = r["U"]
+            tot += r["totals"]
+        out["U"] = out["U"][:, 0]
+        out["totals"] = tot
+        return out
+
+
+class DistTransport:
+    """Messages between the ranks of a torch.distributed process group (gloo: host memory;
+    the library's messages are host buffers), one rank per process."""
+
+    def __init__(self, group=None):
+        import torch.distributed as dist
+        self.dist = dist
+        self.group = group
+        self.rank = dist.get_rank(group)
+        self.n = dist.get_world_size(group)
+
+    def exchange(self, mode, to_left, to_right):
+        """(from_left, from_right): the left neighbour's right-going message and the right
+        neighbour's left-going one; sizes first, then the bytes (tags keep the two directions
+        apart when both neighbours are the same rank)."""
+        import torch
+        dist = self.dist
+        left, right = (self.rank - 1) % self.n, (self.rank + 1) % self.n
+        tl, tr = 100 + 4 * mode, 101 + 4 * mode       # sent left / sent right
+        sizes = [torch.tensor([len(to_left)], dtype=torch.int64), torch.tensor([len(to_right)], dtype=torch.int64)]
+        got = [torch.zeros(1, dtype=torch.int64), torch.zeros(1, dtype=torch.int64)]
+        reqs = [dist.isend(sizes[0], left, group=self.group, tag=tl),
+                dist.isend(sizes[1], right, group=self.group, tag=tr),
+                dist.irecv(got[0], left, group=self.group, tag=tr),
+                dist.irecv(got[1], right, group=self.group, tag=tl)]
+        for q in reqs:
+            q.wait()
+        out = [torch.from_numpy(np.ascontiguousarray(to_left)), torch.from_numpy(np.ascontiguousarray(to_right))]
+        inb = [torch.empty(int(got[0].item()), dtype=torch.uint8), torch.empty(int(got[1].item()), dtype=torch.uint8)]
+        reqs = [dist.isend(out[0], left, group=self.group, tag=tl + 2),
+                dist.isend(out[1], right, group=self.group, tag=tr + 2),
+                dist.irecv(inb[0], left, group=self.group, tag=tr + 2),
+                dist.irecv(inb[1], right, group=self.group, tag=tl + 2)]
+        for q in reqs:
+            q.wait()
+        return inb[0].numpy(), inb[1].numpy()
+
+    def any(self, flag):
+        import torch
+        t = torch.tensor([1 if flag else 0], dtype=torch.int64)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX, group=self.group)
+        return bool(t.item())
+
+    def sum(self, values):
+        """Sum over the ranks in rank order (gathered, then added on every rank)."""
+        import torch
+        t = torch.from_numpy(np.ascontiguousarray(values, dtype=np.float64))
+        parts = [torch.zeros_like(t) for _ in range(self.n)]
+        self.dist.all_gather(parts, t, group=self.group)
+        acc = np.zeros_like(np.asarray(values, dtype=np.float64))
+        for q in parts:
+            acc = acc + q.numpy()
+        return acc
+
+
+class Domain:
+    """This process's rank of a slab decomposition, its messages carried by `transport`
+    (DistTransport, or any object with the same exchange / any / sum methods)."""
+
+    def __init__(self, transport, box, pbc, axis, capacity, kind, params, mass, precision=MD_FP64, skin=0.0):
+        opt = md_default_options()
+        opt.precision = precision
+        opt.skin = skin
+        self.t = transport
+        self.dom = md_domain_create(box, pbc, axis, transport.n, transport.rank, capacity, kind, params, mass, opt)
+        self.rebuilds = 0
+
+    def close(self):
+        md_domain_destroy(self.dom)
+        self.dom = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def exchange(self, mode):
+        to_l, to_r = md_domain_pack(self.dom, mode)
+        fl, fr = self.t.exchange(mode, to_l, to_r)
+        md_domain_unpack(self.dom, mode, fl, fr)
+
+    def start(self, pos, vel, ids=None):
+        pos = np.asarray(pos, dtype=np.float64)
+        n = pos.shape[0]
+        ids = np.arange(n, dtype=np.int64) if ids is None else np.ascontiguousarray(ids, dtype=np.int64)
+        soa = np.ascontiguousarray(pos.T)
+        v = np.ascontiguousarray(np.asarray(vel, dtype=np.float64).T)
+        md_domain_set_atoms(self.dom, ids, np.zeros(n, dtype=np.int32), soa[0], soa[1], soa[2], v[0], v[1], v[2])
+        self.exchange(MD_DOMAIN_GHOSTS)
+        return self.t.sum(md_domain_force(self.dom, 0.0))
+
+    def step(self, dt):
+        if self.t.any(md_domain_kick_drift(self.dom, dt)):
+            self.exchange(MD_DOMAIN_MIGRATE)
+            self.exchange(MD_DOMAIN_GHOSTS)
+            self.rebuilds += 1
+        else:
+            self.exchange(MD_DOMAIN_POSITIONS)
+        return self.t.sum(md_domain_force(self.dom, dt))
+
+    def run(self, n_steps, dt):
+        return np.array([self.step(dt) for _ in range(n_steps)])
+
+    def owned(self):
+        return md_domain_owned(self.dom)
