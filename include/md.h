@@ -522,7 +522,10 @@ md_status md_hcacf(const double *j, int64_t n_rows, int64_t row_stride, int64_t 
  * x), the reciprocal (fn = 2: fp32 seed and one third-order step, within 1 ulp for
  * 1.2e-38 < |x| < 8.5e37) or the reciprocal square root (fn = 3: fp32 seed and one
  * third-order step, within 1 ulp for 1.2e-38 < x < 3.4e38; +inf for x < 2^-126, so that a
- * zero-length bond between coincident atoms makes the forces non-finite, MD_ERR_NAN).
+ * zero-length bond between coincident atoms makes the forces non-finite, MD_ERR_NAN), and the
+ * exponential (fn = 4) and logarithm (fn = 5) that the pair passes call: the same tables and
+ * bounds, the range reduction and final multiply-add in fp64 and the correction polynomial
+ * as pairs of floats on the fp32 pipe (three fp64 instructions each).
  * x, y: n host doubles.  Returns 0, -1 for bad arguments, -5 on a CUDA error.
  * Allocates and frees its own device scratch. */
 int md_fastmath_eval(int fn, int64_t n, const double *x, double *y);

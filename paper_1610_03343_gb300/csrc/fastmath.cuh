@@ -72,6 +72,137 @@ __device__ __forceinline__ double log_tab(double x)
     return fma(ed, kLn2Hi, __ldg(&kLogTab[j]) + fma(ed, kLn2Lo, p));
 }
 
+// ---------------------------------------------------------------- float pairs
+// GB300 issues fp64 at 1/64 of its fp32 rate.  The exponential and logarithm below keep in
+// fp64 only what must be exact -- the range reduction and the final multiply-add with the
+// table value -- and evaluate the small correction polynomial, whose result needs far fewer
+// than 53 bits relative to itself, as a pair of floats (hi + lo, about 48 bits) on the fp32
+// pipe, with the error-free transformations of Knuth (two-sum) and Dekker (two-product, via
+// the fused multiply-add).  The _rn intrinsics keep the compiler from contracting them.
+struct F2 {
+    float h, l;
+};
+// s + e = a + b exactly, for |a| >= |b| (Dekker's fast two-sum)
+__device__ __forceinline__ F2 fast_two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+// s + e = a + b exactly, any a, b (Knuth's two-sum)
+__device__ __forceinline__ F2 two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+// p + e = a b exactly (Dekker's two-product with a fused multiply-add)
+__device__ __forceinline__ F2 two_prod(float a, float b)
+{
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+// the integer n (0 <= n < 2^23) as a float, exactly, on the fp32 pipe
+__device__ __forceinline__ float int23_to_f(unsigned n) { return __fsub_rn(__uint_as_float(0x4b000000u | n), 8388608.0f); }
+
+// x = h + l + t: h = x truncated to a float (d2f_trunc), l = the next 23 bits of x as a
+// float (exact), t = the last 6 bits, |t| < 2^-46 |x| (dropped).  Zero for |x| < 2^-79.
+__device__ __forceinline__ F2 split_d(double x)
+{
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const int se = (int)((hi >> 20) & 0x7ffu) - 1023 - 46 + 127;   // float exponent of the lo part's unit
+    float l = 0.f;
+    if (se >= 1 && se <= 254) l = __fmul_rn(int23_to_f((lo & 0x1fffffffu) >> 6), __int_as_float(se << 23));
+    if (hi & 0x80000000u) l = -l;
+    return {d2f_trunc(x), l};
+}
+
+// e^x for |x| <= 700, within about 1 ulp: x = k ln2/256 + r (k = round(x 256/ln2), computed
+// as in exp_tab), e^x = 2^(k >> 8) T_j (1 + p), p = e^r - 1, j = k & 255.  fp64: the exact
+// first reduction step r1 = x - k ln2hi (ln2hi has 32 bits, so k ln2hi is exact for |k| <
+// 2^21), p rounded once to a double, and T_j + T_j p.  On the fp32 pipe: r = r1 - k ln2lo
+// (ln2lo as a float pair, k ln2lo by two-product) and p = r + r^2/2 + r^3/6 + r^4/24 + r^5/120
+// as a float pair (|r| <= 0.55 ln2/256 < 2^-8.4: r^6/720 < 2^-63).  Three fp64 instructions.
+__device__ __forceinline__ double exp_ff(double x)
+{
+    const float tf = fmaf(d2f_trunc(x), kInvLn2o256F, kShiftF);
+    const int k = __float_as_int(tf) - kShiftBits;
+    const float kf = __fsub_rn(tf, kShiftF);                 // k exactly
+    const double r1 = fma(f2d_int(kf), -kLn2o256Hi, x);      // exact
+    const F2 rs = split_d(r1);
+    const F2 d = two_prod(kf, kLn2o256LoF[0]);               // k ln2lo, head exactly
+    const float dl = __fmaf_rn(kf, kLn2o256LoF[1], d.l);
+    // r = rs.h + m + ml, m = rs.l - k ln2lo (|m| < 2^-22 for |k| < 2^19: its square counts)
+    const F2 mm = two_sum(rs.l, -d.h);
+    const float m = mm.h, ml = __fsub_rn(mm.l, dl);
+    const float rh = rs.h;
+    // r^2 = rh^2 + 2 rh m + m^2, rh^2 = s.h + s.l exactly
+    const F2 s = two_prod(rh, rh);
+    const float sq_l = __fmaf_rn(m, m, __fmaf_rn(2.f * rh, m, s.l));
+    // r^3 = rh^3 + 3 rh^2 m + 3 rh m^2: rh^3 = c.h + c.l + s.l rh;  r^3/6 = (c6.h, c6.l)
+    const F2 c = two_prod(s.h, rh);
+    const float c_l = __fmaf_rn(s.l, rh, __fmaf_rn(3.f * s.h, m, __fmaf_rn(3.f * rh * m, m, c.l)));
+    const F2 c6 = two_prod(c.h, kSixthF[0]);
+    const float c6l = __fmaf_rn(c.h, kSixthF[1], __fmaf_rn(c_l, kSixthF[0], c6.l));
+    // r^4/24 + r^5/120 (below 2^-41: one float suffices)
+    const float s2 = __fmul_rn(s.h, s.h);
+    const float q45 = __fmul_rn(s2, __fmaf_rn(rh, 1.f / 120.f, 1.f / 24.f));
+    // p = rh + s.h/2 + m + c6.h + (small terms)
+    F2 P = fast_two_sum(rh, __fmul_rn(0.5f, s.h));
+    const F2 P2 = two_sum(P.h, m);
+    const F2 P3 = two_sum(P2.h, c6.h);
+    const float pl = ((((P.l + P2.l) + P3.l) + ml) + __fmaf_rn(0.5f, sq_l, c6l)) + q45;
+    const double p = f2d_int(P3.h) + f2d_int(pl);
+    const double tj = __ldg(&kExp2Tab[k & 255]);
+    const double y = fma(tj, p, tj);                          // 2^(j/256) e^r, in [0.997, 2)
+    return __hiloint2double(__double2hiint(y) + ((k >> 8) << 20), __double2loint(y));
+}
+
+// log x for positive normal x, absolute error about 1e-16 (1 + |e|), e the binary exponent:
+// x = 2^e m, m in [1, 2) split exactly into three floats (m1 + m2 + m3, integer
+// instructions), i_j = RN_float(1/c_j), c_j = 1 + (j + 1/2)/256 for the top eight bits j of m;
+// log x = e ln2 + (-log i_j) + log(1 + r), r = m i_j - 1 (|r| < 2^-8.9) formed exactly-enough
+// as a float pair by two-products (m1 i_j is within 2^-9 of 1, so its difference from 1 is
+// exact), log(1 + r) = r - r^2/2 + r^3/3 - r^4/4 + r^5/5 as a float pair together with e ln2lo,
+// rounded once to a double and added to e ln2hi - log i_j (an exact product and one rounding).
+// Three fp64 instructions.
+__device__ __forceinline__ double log_ff(double x)
+{
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const int e = (int)(hi >> 20) - 1023;
+    const int j = (hi >> 12) & 255;
+    const float m1 = __uint_as_float(0x3f800000u | ((hi & 0xfffffu) << 3) | (lo >> 29));
+    const float m2 = __fmul_rn(int23_to_f((lo >> 6) & 0x7fffffu), 0x1p-46f);
+    const float m3 = __fmul_rn(int23_to_f(lo & 63u), 0x1p-52f);
+    const float inv = __ldg(&kLogInvTabF[j]);
+    const F2 p1 = two_prod(m1, inv);
+    const float r0 = __fsub_rn(p1.h, 1.f);                    // exact: p1.h is within 2^-8 of 1
+    const F2 p2 = two_prod(m2, inv);
+    const F2 t = two_sum(p1.l, p2.h);
+    const F2 R = two_sum(r0, t.h);
+    const float rl = __fmaf_rn(m3, inv, (R.l + t.l) + p2.l);
+    const F2 rr = fast_two_sum(R.h, rl);                      // r = rr.h + rr.l
+    const float rh = rr.h, m = rr.l;
+    const F2 s = two_prod(rh, rh);
+    const float sq_l = __fmaf_rn(2.f * rh, m, s.l);           // r^2 = s.h + sq_l
+    const F2 c = two_prod(s.h, rh);
+    const float c_l = __fmaf_rn(s.l, rh, __fmaf_rn(3.f * s.h, m, c.l));   // r^3 = c.h + c_l
+    const F2 c3 = two_prod(c.h, kThirdF[0]);
+    const float c3l = __fmaf_rn(c.h, kThirdF[1], __fmaf_rn(c_l, kThirdF[0], c3.l));
+    const float s2 = __fmul_rn(s.h, s.h);
+    const float q45 = __fmul_rn(s2, __fmaf_rn(rh, 0.2f, -0.25f));            // -r^4/4 + r^5/5
+    // e ln2lo (|e| <= 1023: the head product exact by two-product)
+    const float ef = __fsub_rn(__int_as_float(kShiftBits + e), kShiftF);   // e exactly
+    const F2 el = two_prod(ef, kLn2LoF[0]);
+    const float ell = __fmaf_rn(ef, kLn2LoF[1], el.l);
+    // q = rh - s.h/2 + c3.h + e ln2lo + (small terms)
+    const F2 Q = fast_two_sum(rh, __fmul_rn(-0.5f, s.h));
+    const F2 Q2 = two_sum(Q.h, c3.h);
+    const F2 Q3 = two_sum(Q2.h, el.h);
+    const float ql = (((((Q.l + Q2.l) + Q3.l) + m) + ell) + __fmaf_rn(-0.5f, sq_l, c3l)) + q45;
+    const double q = f2d_int(Q3.h) + f2d_int(ql);
+    return fma(int_to_d(e), kLn2Hi, __ldg(&kLogTabF[j])) + q;
+}
+
 // 1/x for 1.2e-38 < |x| < 8.5e37 (x and 1/x normal in fp32): an fp32 seed y
 // (rcp.approx on the value truncated to fp32 with integer instructions, relative error
 // e = 1 - x y below 2^-21), then one third-order step y (1 + e + e^2), for which

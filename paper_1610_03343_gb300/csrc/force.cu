@@ -46,12 +46,12 @@ template <> struct M<double> {
     static __device__ __forceinline__ double exp_(double x) { return exp(x); }
     static __device__ __forceinline__ double log_(double x) { return log(x); }
     static __device__ __forceinline__ double log1p_(double x) { return log1p(x); }
-    static __device__ __forceinline__ double texp_(double x) { return exp_tab(x); }
-    static __device__ __forceinline__ double tlog_(double x) { return log_tab(x); }
-    static __device__ __forceinline__ double tlog1p_(double x) { return log_tab(1.0 + x); }
+    static __device__ __forceinline__ double texp_(double x) { return exp_ff(x); }
+    static __device__ __forceinline__ double tlog_(double x) { return log_ff(x); }
+    static __device__ __forceinline__ double tlog1p_(double x) { return log_ff(1.0 + x); }
     // SW: exp(sigma/(r - a sigma)) and exp(gamma sigma/(r - a sigma)) go to -infinity at the
     // cutoff; below -700 the factor is < 1e-304 and is taken as e^-700
-    static __device__ __forceinline__ double sexp_(double x) { return exp_tab(clamp_neg700(x)); }
+    static __device__ __forceinline__ double sexp_(double x) { return exp_ff(clamp_neg700(x)); }
     static __device__ __forceinline__ double rcp_(double x) { return rcp_nr(x); }
     static __device__ __forceinline__ void sincos_(double x, double *s, double *c) { sincos(x, s, c); }
     static __device__ __forceinline__ double pow_(double x, double y) { return pow(x, y); }
@@ -1506,7 +1506,15 @@ namespace {
 __global__ void k_fastmath_eval(int fn, int64_t n, const double *x, double *y)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) y[i] = fn == 0 ? exp_tab(x[i]) : (fn == 1 ? log_tab(x[i]) : (fn == 2 ? rcp_nr(x[i]) : rsqrt_nr(x[i])));
+    if (i >= n) return;
+    switch (fn) {
+    case 0: y[i] = exp_tab(x[i]); break;
+    case 1: y[i] = log_tab(x[i]); break;
+    case 2: y[i] = rcp_nr(x[i]); break;
+    case 3: y[i] = rsqrt_nr(x[i]); break;
+    case 4: y[i] = exp_ff(x[i]); break;
+    default: y[i] = log_ff(x[i]); break;
+    }
 }
 }  // namespace
 
@@ -1686,7 +1694,7 @@ int gather_blocks(int64_t N) { return N == 0 ? 1 : (int)blocks_for(N, kGatherBlo
 // error.
 extern "C" int md_fastmath_eval(int fn, int64_t n, const double *x, double *y)
 {
-    if (fn < 0 || fn > 3 || n < 0 || (n > 0 && (!x || !y))) return -1;
+    if (fn < 0 || fn > 5 || n < 0 || (n > 0 && (!x || !y))) return -1;
     if (n == 0) return 0;
     double *d = nullptr;
     if (cudaMalloc(&d, sizeof(double) * 2 * (size_t)n) != cudaSuccess) {

@@ -59,6 +59,38 @@ def main():
     lines.append("__device__ const double kLogTab[256] = {")
     lines += [f"    {v}," for v in lg]
     lines.append("};")
+    # float-float routines: the reduction constants and polynomial coefficients as pairs of
+    # floats (head rounded to float, tail = the rest rounded to float)
+    def fpair(x: Decimal):
+        import struct
+        h = struct.unpack("f", struct.pack("f", float(x)))[0]
+        t = struct.unpack("f", struct.pack("f", float(x - Decimal(h))))[0]
+        return h, t
+    lines.append("")
+    lines.append("// ln2/256 - kLn2o256Hi as a float pair (head, tail)")
+    ch, ct = fpair(l64 - Decimal(head))
+    lines.append(f"constexpr float kLn2o256LoF[2] = {{{ch.hex()}f, {ct.hex()}f}};".replace("0x", "0x"))
+    for name, val in (("kThirdF", Decimal(1) / 3), ("kSixthF", Decimal(1) / 6)):
+        h, t = fpair(val)
+        lines.append(f"constexpr float {name}[2] = {{{h.hex()}f, {t.hex()}f}};   // {name[1:-1].lower()} as a float pair")
+    lines.append(f"constexpr float kLn2LoF[2] = {{{fpair(LN2 - Decimal(h2))[0].hex()}f, {fpair(LN2 - Decimal(h2))[1].hex()}f}};"
+                 "   // ln2 - kLn2Hi as a float pair")
+    # log with a float reciprocal: i_j = RN_float(1/c_j) and -log(i_j) (of that float) in double
+    import struct
+    invf, lgf = [], []
+    for j in range(256):
+        c = 1 + (Decimal(j) + Decimal("0.5")) / 256
+        iv = struct.unpack("f", struct.pack("f", float(Decimal(1) / c)))[0]
+        invf.append(iv.hex())
+        lgf.append(d(-Decimal(iv).ln()))
+    lines.append("// 1/c_j rounded to float, c_j = 1 + (j + 1/2)/256, j = 0..255")
+    lines.append("__device__ const float kLogInvTabF[256] = {")
+    lines += [f"    {v}f," for v in invf]
+    lines.append("};")
+    lines.append("// -log(kLogInvTabF[j]) rounded to double")
+    lines.append("__device__ const double kLogTabF[256] = {")
+    lines += [f"    {v}," for v in lgf]
+    lines.append("};")
     lines += ["", "}  // namespace mdk", ""]
     with open(os.path.join(HERE, "fastmath_tables.cuh"), "w") as f:
         f.write("\n".join(lines))

@@ -338,8 +338,9 @@ def md_get_box(ctx, system=0) -> np.ndarray:
 
 
 def md_fastmath_eval(fn: int, x) -> np.ndarray:
-    """The pair pass's fp64 exp (fn 0), log (fn 1), reciprocal (fn 2) or reciprocal square
-    root (fn 3), evaluated on the GPU."""
+    """The pair passes' fp64 routines evaluated on the GPU: all-fp64 exp (fn 0) and log
+    (fn 1), reciprocal (fn 2), reciprocal square root (fn 3), and the exp (fn 4) and log (fn 5)
+    whose correction polynomial runs as float pairs."""
     lib = load()
     x = np.ascontiguousarray(x, dtype=np.float64)
     y = np.empty_like(x)
