@@ -238,7 +238,7 @@ def run_ours(args, rank, world):
     from paper_1610_03343_gb300 import md
 
     torch.cuda.set_device(0 if world == 1 else int(os.environ.get("LOCAL_RANK", rank)))
-    sysm, dt = workload(args.workload)
+    sysm, dt = workload(args.workload, args.scale)
     n = sysm.n
     stream = torch.cuda.Stream()
     res = {}
@@ -681,6 +681,8 @@ def main():
                     help="untimed steps from the initial state before tuning and warm-up")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="tersoff_c_graphene_1M")
+    ap.add_argument("--scale", type=int, default=1,
+                    help="divide the workload's cell counts per axis by this (profiling captures of smaller systems)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--precision", default="both", choices=["both", "fp64", "mixed"])
@@ -741,7 +743,7 @@ def main():
         return
     kt = res[primary]["kt"]
     pair_n, pair_ms = kt.get("pair", (0, 0.0))
-    sysm, _ = workload(args.workload)
+    sysm, _ = workload(args.workload, args.scale)
     peaks_hw = load_peaks()
     peaks = measure_peaks()
     fp64_peak = peaks["fp64_tflops"]

@@ -203,6 +203,89 @@ __device__ __forceinline__ double log_ff(double x)
     return fma(int_to_d(e), kLn2Hi, __ldg(&kLogTabF[j])) + q;
 }
 
+// x = x1 + x2 + x3 exactly, three floats (x1: 24 leading bits, x2: the next 23, x3: the last
+// 6), for 2^-74 <= |x| < 2^128 (every part then a normal float or zero); the callers pass
+// mantissas in [1, 4).
+struct F3 {
+    float a, b, c;
+};
+__device__ __forceinline__ F3 split3_d(double x)
+{
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const int e = (int)((hi >> 20) & 0x7ffu) - 1023;
+    float b = __fmul_rn(int23_to_f((lo >> 6) & 0x7fffffu), __int_as_float((e - 46 + 127) << 23));
+    float c = __fmul_rn(int23_to_f(lo & 63u), __int_as_float((e - 52 + 127) << 23));
+    if (hi & 0x80000000u) {
+        b = -b;
+        c = -c;
+    }
+    return {d2f_trunc(x), b, c};
+}
+
+// 1/sqrt(x) for positive normal x within 1 ulp, two fp64 instructions.  x = m 2^(2h), m in
+// [1, 4) (integer instructions), 1/sqrt(x) = 2^-h / sqrt(m).  For m: the fp32 seed y of
+// rsqrt_nr (relative error below 2^-22), e = 1 - m y^2 formed exactly enough as a float pair
+// (m split into three floats, y^2 and the products by two-product; m1 y^2 lies within 2^-21
+// of 1, so its difference from 1 is exact), then m^(-1/2) = y (1 + e/2 + 3e^2/8) (the next
+// term, 5e^3/16, is below 2^-64): y + y c, with y c by two-product, added in fp64 (the first
+// addition exact, the second rounding once); 2^-h by integer instructions.  +inf below
+// 2^-126, as rsqrt_nr.
+__device__ __forceinline__ double rsqrt_ff(double x)
+{
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const int e = (int)((hi >> 20) & 0x7ffu) - 1023;
+    const int odd = e & 1;
+    const int h = (e - odd) / 2;
+    const double md = __hiloint2double((int)((hi & 0x000fffffu) | ((unsigned)(0x3ff + odd) << 20)), (int)lo);
+    const float mf = d2f_trunc(md);
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(mf));
+    const F3 ms = split3_d(md);
+    const F2 s = two_prod(y, y);                           // y^2 = s.h + s.l exactly
+    const F2 p = two_prod(ms.a, s.h);                      // m1 y^2 head
+    const F2 q1 = two_prod(ms.a, s.l);
+    const F2 q2 = two_prod(ms.b, s.h);
+    const F2 m1 = two_sum(q1.h, q2.h);
+    const F2 m2 = two_sum(m1.h, p.l);
+    const F2 E = two_sum(__fsub_rn(p.h, 1.f), m2.h);      // m y^2 - 1 = -e, head
+    const float el = (((E.l + m1.l) + m2.l) + (q1.l + q2.l)) + __fmaf_rn(ms.b, s.l, __fmul_rn(ms.c, s.h));
+    // c = e/2 + 3e^2/8 with e = -(E.h + el)
+    const float ch = __fmul_rn(-0.5f, E.h);
+    const float cl = __fmaf_rn(0.375f * E.h, E.h, __fmul_rn(-0.5f, el));
+    const F2 t = two_prod(y, ch);
+    // y + t.h is exact in fp64 (two floats 2^-21 apart in scale); the rest is rounded once
+    const double v = (f2d_int(y) + f2d_int(t.h)) + f2d_int(__fmaf_rn(y, cl, t.l));
+    const double r = __hiloint2double(__double2hiint(v) - (h << 20), __double2loint(v));
+    return __double_as_longlong(x) < 0x3810000000000000ll ? __longlong_as_double(0x7ff0000000000000ll) : r;
+}
+
+// 1/x for normal x (|x| < 2^1022) within 1 ulp, two fp64 instructions: x = m 2^e, m in
+// [1, 2) with x's sign, 1/x = 2^-e / m; for m the fp32 seed y of rcp_nr, e = 1 - m y as a
+// float pair (m split into three floats; m1 y lies within 2^-21 of 1), then 1/m = y (1 + e +
+// e^2) (the next term, e^3, is below 2^-63): y + y c added in fp64 as in rsqrt_ff; 2^-e by
+// integer instructions.
+__device__ __forceinline__ double rcp_ff(double x)
+{
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const int e = (int)((hi >> 20) & 0x7ffu) - 1023;
+    const double md = __hiloint2double((int)((hi & 0x800fffffu) | 0x3ff00000u), (int)lo);
+    const float mf = d2f_trunc(md);
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(mf));
+    const F3 ms = split3_d(md);
+    const F2 p = two_prod(ms.a, y);
+    const F2 q = two_prod(ms.b, y);
+    const F2 m = two_sum(q.h, p.l);
+    const F2 E = two_sum(__fsub_rn(p.h, 1.f), m.h);       // m y - 1 = -e, head
+    const float el = ((E.l + m.l) + q.l) + __fmul_rn(ms.c, y);
+    // c = e + e^2 with e = -(E.h + el)
+    const float ch = -E.h;
+    const float cl = __fmaf_rn(E.h, E.h, -el);
+    const F2 t = two_prod(y, ch);
+    const double v = (f2d_int(y) + f2d_int(t.h)) + f2d_int(__fmaf_rn(y, cl, t.l));
+    return __hiloint2double(__double2hiint(v) - (e << 20), __double2loint(v));
+}
+
 // 1/x for 1.2e-38 < |x| < 8.5e37 (x and 1/x normal in fp32): an fp32 seed y
 // (rcp.approx on the value truncated to fp32 with integer instructions, relative error
 // e = 1 - x y below 2^-21), then one third-order step y (1 + e + e^2), for which

@@ -42,7 +42,7 @@ template <typename T> struct M;
 // arguments stay inside the table-driven routines' domain (fastmath.cuh); tlog1p_ needs
 // only absolute accuracy (it enters b = exp(-log(1 + x)/(2n))).
 template <> struct M<double> {
-    static __device__ __forceinline__ double rsqrt_(double x) { return rsqrt_nr(x); }
+    static __device__ __forceinline__ double rsqrt_(double x) { return rsqrt_ff(x); }
     static __device__ __forceinline__ double exp_(double x) { return exp(x); }
     static __device__ __forceinline__ double log_(double x) { return log(x); }
     static __device__ __forceinline__ double log1p_(double x) { return log1p(x); }
@@ -52,7 +52,7 @@ template <> struct M<double> {
     // SW: exp(sigma/(r - a sigma)) and exp(gamma sigma/(r - a sigma)) go to -infinity at the
     // cutoff; below -700 the factor is < 1e-304 and is taken as e^-700
     static __device__ __forceinline__ double sexp_(double x) { return exp_ff(clamp_neg700(x)); }
-    static __device__ __forceinline__ double rcp_(double x) { return rcp_nr(x); }
+    static __device__ __forceinline__ double rcp_(double x) { return rcp_ff(x); }
     static __device__ __forceinline__ void sincos_(double x, double *s, double *c) { sincos(x, s, c); }
     static __device__ __forceinline__ double pow_(double x, double y) { return pow(x, y); }
 };
@@ -1513,7 +1513,9 @@ __global__ void k_fastmath_eval(int fn, int64_t n, const double *x, double *y)
     case 2: y[i] = rcp_nr(x[i]); break;
     case 3: y[i] = rsqrt_nr(x[i]); break;
     case 4: y[i] = exp_ff(x[i]); break;
-    default: y[i] = log_ff(x[i]); break;
+    case 5: y[i] = log_ff(x[i]); break;
+    case 6: y[i] = rcp_ff(x[i]); break;
+    default: y[i] = rsqrt_ff(x[i]); break;
     }
 }
 }  // namespace
@@ -1694,7 +1696,7 @@ int gather_blocks(int64_t N) { return N == 0 ? 1 : (int)blocks_for(N, kGatherBlo
 // error.
 extern "C" int md_fastmath_eval(int fn, int64_t n, const double *x, double *y)
 {
-    if (fn < 0 || fn > 5 || n < 0 || (n > 0 && (!x || !y))) return -1;
+    if (fn < 0 || fn > 7 || n < 0 || (n > 0 && (!x || !y))) return -1;
     if (n == 0) return 0;
     double *d = nullptr;
     if (cudaMalloc(&d, sizeof(double) * 2 * (size_t)n) != cudaSuccess) {

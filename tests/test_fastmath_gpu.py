@@ -100,3 +100,30 @@ def test_reciprocal_sqrt_within_one_ulp(md):
     e = e.astype(np.float64)
     assert e.max() <= 1.0, (x[np.argmax(e)], e.max())
     assert np.median(e) <= 0.5
+
+
+def test_float_pair_reciprocal_and_rsqrt_within_one_ulp(md):
+    """The reciprocal (fn 6) and reciprocal square root (fn 7) that finish their correction in
+    float pairs, within 1 ulp for normal arguments (a bond order's zeta (1 + x) reaches 1e-30
+    near the cutoff switch; the reciprocal square root from 2^-126 up, +inf below), including
+    powers of two, their neighbours and both signs."""
+    rng = np.random.Generator(np.random.PCG64(5))
+    core = np.concatenate([
+        rng.uniform(0.5, 16.0, 300000), rng.uniform(18.0, 300.0, 200000),
+        np.exp(rng.uniform(-700.0, 700.0, 300000)),
+        2.0 ** np.arange(-1021, 1021, dtype=np.float64),
+        np.nextafter(2.0 ** np.arange(-1021, 1021, dtype=np.float64), 0.0),
+        np.nextafter(2.0 ** np.arange(-1021, 1021, dtype=np.float64), np.inf),
+        [1.0, 2.0, 3.0, 4.0, 2.25, 5.29, 7.0, 1e-30, 1e-300],
+    ])
+    x = np.concatenate([core, -core])
+    y = md.md_fastmath_eval(6, x)
+    e = ulp_err(y, 1.0 / x)
+    assert e.max() <= 1.0, (x[np.argmax(e)], e.max())
+    pos = core[core >= 2.0 ** -126]          # below, +inf by design (a zero-length bond)
+    y = md.md_fastmath_eval(7, pos)
+    ref = 1.0 / np.sqrt(pos.astype(np.longdouble))
+    e = (np.abs(y.astype(np.longdouble) - ref) / np.spacing(ref.astype(np.float64)).astype(np.longdouble)).astype(np.float64)
+    assert e.max() <= 1.0, (pos[np.argmax(e)], e.max())
+    assert np.median(e) <= 0.5
+    assert np.isinf(md.md_fastmath_eval(7, np.array([0.0, 1e-300, 2.0 ** -127]))).all()
