@@ -155,8 +155,10 @@ __device__ __noinline__ void pair_fail(const PairArgs<T> &a, int64_t i, int stat
 // ------------------------------------------------------- neighbour staging
 // For each list slot, the fp64 bond r_ij (image shift from the entry); keeps the slots
 // with |r_ij|^2 < rc^2, writes their bond vectors (compact row k) to global memory and
-// stages (x, y, z, r^2) in the shared fields fx, fy, fz, fr2.  Slots are fetched four at a
-// time so that their index and position loads are in flight together.  Returns the
+// stages (x, y, z, r^2) in the shared fields fx, fy, fz, fr2.  Without a prefilter, slots
+// are fetched four at a time so that their index and position loads are in flight together;
+// with one (SW), an fp32 pass first marks the slots that may be bonds and the fp64 work
+// then runs over those only.  Returns the
 // in-cutoff count (and mask), or -1 when the count exceeds CAP in the small-capacity
 // pass: the atom is then appended to the deferred list and left to the full pass.
 // The cutoff decision is symmetric in i and j: the two fp64 differences are exact
@@ -189,21 +191,49 @@ __device__ __forceinline__ int collect_bonds(const PairArgs<T> &a, int64_t i, co
     const int nn = a.nn[i];
     int na = 0;
     mask = 0u;
-    for (int m0 = 0; m0 < nn; m0 += 4) {
-        int e[4];
-        bool keep[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            e[q] = (m0 + q < nn) ? a.nl[(int64_t)(m0 + q) * N + i] : 0;
-            keep[q] = m0 + q < nn;
+    // one bond: the fp64 vector r_ij of list slot m (entry e, neighbour position p), the exact
+    // cutoff test and the staging
+    auto bond = [&](int m, int e, double px, double py, double pz) {
+        double dx = px - xi, dy = py - yi, dz = pz - zi;
+        const int code = list_code(e);
+        if (code != kNoShift) {
+            const int sx = code % 3 - 1, sy = (code / 3) % 3 - 1, sz = code / 9 - 1;
+            if (sx) dx += sx > 0 ? box.L[0] : -box.L[0];
+            if (sy) dy += sy > 0 ? box.L[1] : -box.L[1];
+            if (sz) dz += sz > 0 ? box.L[2] : -box.L[2];
         }
-        if (PREFILTER) {
-            // fp32 distance from the step's fp32 positions: skips entries that are outside
-            // the cutoff by more than the fp32 rounding margin (exact: the fp64 test below
-            // would reject them too; symmetric: fp32 negation is exact)
+        const T tx = to_t<T>(dx), ty = to_t<T>(dy), tz = to_t<T>(dz);
+        const T r2 = bond_r2(tx, ty, tz);
+        int tj = 0;
+        T cut2 = rc2;
+        if (MULTI) {
+            tj = a.type[list_atom(e)];
+            cut2 = row[tj].rc2;
+        }
+        if (lt_nonneg(r2, cut2)) {
+            if (na < CAP) {
+                S.set(fx, na, tx); S.set(fy, na, ty); S.set(fz, na, tz); S.set(fr2, na, r2);
+                if (MULTI) S.set(ftype, na, T(tj));
+                a.r[(int64_t)(0 * S_ + na) * N + i] = tx;
+                a.r[(int64_t)(1 * S_ + na) * N + i] = ty;
+                a.r[(int64_t)(2 * S_ + na) * N + i] = tz;
+            }
+            mask |= 1u << m;
+            ++na;
+        }
+    };
+    if (PREFILTER) {
+        // pass 1, fp32 and integer pipes: the list slots whose fp32 distance (from the step's
+        // fp32 positions) is within the cutoff plus the fp32 rounding margin (exact: the fp64
+        // test would reject every other slot; symmetric: fp32 negation is exact)
+        uint32_t cand = 0u;
+        for (int m0 = 0; m0 < nn; m0 += 4) {
+            int e[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) e[q] = (m0 + q < nn) ? a.nl[(int64_t)(m0 + q) * N + i] : 0;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                if (!keep[q]) continue;
+                if (m0 + q >= nn) break;
                 const int j = list_atom(e[q]);
                 float dx = a.posf[j] - fxi, dy = a.posf[N + j] - fyi, dz = a.posf[2 * N + j] - fzi;
                 const int code = list_code(e[q]);
@@ -213,49 +243,39 @@ __device__ __forceinline__ int collect_bonds(const PairArgs<T> &a, int64_t i, co
                     dy = fmaf((float)sy, fL1, dy);
                     dz = fmaf((float)sz, fL2, dz);
                 }
-                keep[q] = dx * dx + dy * dy + dz * dz < lim2;
+                if (dx * dx + dy * dy + dz * dz < lim2) cand |= 1u << (m0 + q);
             }
         }
-        double px[4], py[4], pz[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int j = list_atom(e[q]);
-            if (keep[q]) {
-                px[q] = a.pos[j];
-                py[q] = a.pos[N + j];
-                pz[q] = a.pos[2 * N + j];
-            }
+        // pass 2, fp64: only the candidates, in list order, so that every lane of a warp does
+        // fp64 work for each iteration it takes (the list holds about three times as many
+        // slots as bonds: SW silicon's second shell lies inside the list radius)
+        while (cand != 0u) {
+            const int m = __ffs(cand) - 1;
+            cand &= cand - 1u;
+            const int e = a.nl[(int64_t)m * N + i];
+            const int j = list_atom(e);
+            bond(m, e, a.pos[j], a.pos[N + j], a.pos[2 * N + j]);
         }
+    } else {
+        // slots fetched four at a time, so that their index and position loads are in flight
+        // together
+        for (int m0 = 0; m0 < nn; m0 += 4) {
+            int e[4];
+            double px[4], py[4], pz[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            if (m0 + q >= nn) break;
-            if (!keep[q]) continue;
-            double dx = px[q] - xi, dy = py[q] - yi, dz = pz[q] - zi;
-            const int code = list_code(e[q]);
-            if (code != kNoShift) {
-                const int sx = code % 3 - 1, sy = (code / 3) % 3 - 1, sz = code / 9 - 1;
-                if (sx) dx += sx > 0 ? box.L[0] : -box.L[0];
-                if (sy) dy += sy > 0 ? box.L[1] : -box.L[1];
-                if (sz) dz += sz > 0 ? box.L[2] : -box.L[2];
-            }
-            const T tx = to_t<T>(dx), ty = to_t<T>(dy), tz = to_t<T>(dz);
-            const T r2 = bond_r2(tx, ty, tz);
-            int tj = 0;
-            T cut2 = rc2;
-            if (MULTI) {
-                tj = a.type[list_atom(e[q])];
-                cut2 = row[tj].rc2;
-            }
-            if (lt_nonneg(r2, cut2)) {
-                if (na < CAP) {
-                    S.set(fx, na, tx); S.set(fy, na, ty); S.set(fz, na, tz); S.set(fr2, na, r2);
-                    if (MULTI) S.set(ftype, na, T(tj));
-                    a.r[(int64_t)(0 * S_ + na) * N + i] = tx;
-                    a.r[(int64_t)(1 * S_ + na) * N + i] = ty;
-                    a.r[(int64_t)(2 * S_ + na) * N + i] = tz;
+            for (int q = 0; q < 4; ++q) {
+                e[q] = (m0 + q < nn) ? a.nl[(int64_t)(m0 + q) * N + i] : 0;
+                const int j = list_atom(e[q]);
+                if (m0 + q < nn) {
+                    px[q] = a.pos[j];
+                    py[q] = a.pos[N + j];
+                    pz[q] = a.pos[2 * N + j];
                 }
-                mask |= 1u << (m0 + q);
-                ++na;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (m0 + q >= nn) break;
+                bond(m0 + q, e[q], px[q], py[q], pz[q]);
             }
         }
     }
