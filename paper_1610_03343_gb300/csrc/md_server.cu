@@ -164,7 +164,9 @@ void runner(md_server *srv, int which)
         for (auto &kv : pr.running) resident += (double)kv.second->n;
         md_status s = md_run(pr.ctx, chunk, pr.dt, nullptr);
         if (s == MD_OK) s = md_batch_status(pr.ctx, active.data(), left.data(), tot.data(), kin.data());
-        if (s == MD_OK) s = md_batch_errors(pr.ctx, err.data());
+        bool any_stopped = false;
+        for (auto &kv : pr.running) any_stopped |= active[kv.first] == 0;
+        if (s == MD_OK && any_stopped) s = md_batch_errors(pr.ctx, err.data());   // why they stopped
         const double t_harvest = srv->now();
         if (s != MD_OK) {   // the pool itself failed (a CUDA error): fail every running job
             for (auto &kv : pr.running) {
