@@ -101,17 +101,18 @@ __device__ __forceinline__ F2 two_prod(float a, float b)
     const float p = __fmul_rn(a, b);
     return {p, __fmaf_rn(a, b, -p)};
 }
-// the integer n (0 <= n < 2^23) as a float, exactly, on the fp32 pipe
+// the integer n (0 <= n <= 2^23) as a float, exactly, on the fp32 pipe
 __device__ __forceinline__ float int23_to_f(unsigned n) { return __fsub_rn(__uint_as_float(0x4b000000u | n), 8388608.0f); }
 
-// x = h + l + t: h = x truncated to a float (d2f_trunc), l = the next 23 bits of x as a
-// float (exact), t = the last 6 bits, |t| < 2^-46 |x| (dropped).  Zero for |x| < 2^-79.
+// x = h + l + t: h = x truncated to a float (d2f_trunc), l = the next 23 bits of x rounded
+// to nearest on the last 6 (l is at most 2^23 units of 2^(e-46), exact as a float),
+// |t| <= 2^-47 |x|.  l is zero for |x| < 2^-79.
 __device__ __forceinline__ F2 split_d(double x)
 {
     const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
     const int se = (int)((hi >> 20) & 0x7ffu) - 1023 - 46 + 127;   // float exponent of the lo part's unit
     float l = 0.f;
-    if (se >= 1 && se <= 254) l = __fmul_rn(int23_to_f((lo & 0x1fffffffu) >> 6), __int_as_float(se << 23));
+    if (se >= 1 && se <= 254) l = __fmul_rn(int23_to_f(((lo & 0x1fffffffu) + 32u) >> 6), __int_as_float(se << 23));
     if (hi & 0x80000000u) l = -l;
     return {d2f_trunc(x), l};
 }
@@ -201,6 +202,47 @@ __device__ __forceinline__ double log_ff(double x)
     const float ql = (((((Q.l + Q2.l) + Q3.l) + m) + ell) + __fmaf_rn(-0.5f, sq_l, c3l)) + q45;
     const double q = f2d_int(Q3.h) + f2d_int(ql);
     return fma(int_to_d(e), kLn2Hi, __ldg(&kLogTabF[j])) + q;
+}
+
+// ---- float-pair arithmetic (about 48 bits; absolute error about 2^-48 of the operands'
+// magnitudes, which is what sums of force terms need).  A pair travels through an fp64
+// shared-memory slot as the two floats' bit patterns (ff_pack / ff_unpack: integer moves).
+__device__ __forceinline__ double ff_pack(F2 a) { return __hiloint2double(__float_as_int(a.h), __float_as_int(a.l)); }
+__device__ __forceinline__ F2 ff_unpack(double d)
+{
+    return {__int_as_float(__double2hiint(d)), __int_as_float(__double2loint(d))};
+}
+// a pair as a double (one fp64 addition, exact: the two floats span at most 48 bits);
+// split_d goes the other way
+__device__ __forceinline__ double ff_to_d(F2 a) { return f2d_int(a.h) + f2d_int(a.l); }
+__device__ __forceinline__ F2 ff_neg(F2 a) { return {-a.h, -a.l}; }
+__device__ __forceinline__ F2 ff_add(F2 a, F2 b)
+{
+    const F2 s = two_sum(a.h, b.h);
+    return fast_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
+}
+__device__ __forceinline__ F2 ff_mul(F2 a, F2 b)
+{
+    const F2 p = two_prod(a.h, b.h);
+    return fast_two_sum(p.h, __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, p.l)));
+}
+// a b + c
+__device__ __forceinline__ F2 ff_fma(F2 a, F2 b, F2 c)
+{
+    const F2 p = two_prod(a.h, b.h);
+    const F2 s = two_sum(p.h, c.h);
+    const float l = __fadd_rn(__fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, p.l)), __fadd_rn(c.l, s.l));
+    return fast_two_sum(s.h, l);
+}
+// 1/a: the correctly rounded float reciprocal y of a.h, then y + y e, e = 1 - a y (y a.h is
+// within 2^-23 of 1, so 1 minus its head is exact)
+__device__ __forceinline__ F2 ff_rcp(F2 a)
+{
+    const float y = __frcp_rn(a.h);
+    const F2 p = two_prod(a.h, y);
+    const float e = __fsub_rn(__fsub_rn(__fsub_rn(1.f, p.h), p.l), __fmul_rn(a.l, y));
+    const F2 t = two_prod(y, e);
+    return fast_two_sum(y, __fadd_rn(t.h, t.l));
 }
 
 // x = x1 + x2 + x3 exactly, three floats (x1: 24 leading bits, x2: the next 23, x3: the last

@@ -339,10 +339,10 @@ __device__ __forceinline__ void tersoff_b(const TersoffC<T> &p, T zeta, T &b, T 
 // index of the unordered bond pair (j, k), j < k
 __device__ __forceinline__ int tri(int j, int k) { return k * (k - 1) / 2 + j; }
 
-// Per unordered bond pair the fp64 pass keeps cos theta, g and g' from the zeta loop for the
-// angular loop (it is bound by its fp64 pipe); the fp32 pass keeps only 1/(d^2 + (h - cos)^2)
-// and recomputes the rest (it is bound by instruction issue and occupancy, and three words
-// per pair would cost it resident blocks).
+// Per unordered bond pair the fp64 pass keeps cos theta, g and g' (float pairs) from the zeta
+// loop for the angular loop, which saves it about a hundred fp32 instructions per pair; the
+// fp32 pass keeps only 1/(d^2 + (h - cos)^2) and recomputes the rest (it is bound by
+// instruction issue and occupancy, and three words per pair would cost it resident blocks).
 template <typename T>
 constexpr bool kCachePairs = sizeof(T) == 8;
 template <typename T, int CAP>
@@ -357,6 +357,93 @@ __device__ __forceinline__ const TersoffC<T> &bond_const(const TersoffC<T> &p, c
     else return p;
 }
 
+// The two bond-pair loops of the fp64 pass in float-pair arithmetic (fastmath.cuh): every
+// result carries an absolute error of about 2^-47 of the magnitudes it is formed from -- the
+// same order as rounding dU_i/dr_ij to a 47-bit mantissa.  The one exception is cos theta:
+// g' is proportional to h - cos theta, which is small (0.07 in graphene, where cos = -1/2
+// and h = -0.5706), so an absolute error e in cos is a relative error e/|h - cos| in g';
+// cos theta and h - cos theta are therefore formed in fp64 from the fp64 unit vectors (four
+// fp64 instructions per pair) and only then split.  The pair cache holds, per unordered
+// bond pair q = tri(j, k), cos theta, g and dg/dcos in slots q, NP + q, 2 NP + q.
+template <int CAP, int BLOCK>
+__device__ __forceinline__ void tersoff_zeta_ff(const TersoffC<double> &p, const Stage<double, CAP, BLOCK> &S,
+                                                double *spair, int na)
+{
+    constexpr int NP = CAP * (CAP - 1) / 2;
+    double *pc = spair + threadIdx.x;
+    const F2 d2 = split_d(p.d2), c2d2 = split_d(p.c2d2), m2c2 = split_d(-2.0 * p.c2);
+    const F2 one{1.f, 0.f};
+    for (int j = 0; j < na; ++j) {
+        const double ujx = S(TF_UX, j), ujy = S(TF_UY, j), ujz = S(TF_UZ, j);
+        const F2 fcj = ff_unpack(S(TF_FC, j));
+        F2 zj = ff_unpack(S(TF_Z, j));
+        for (int k = j + 1; k < na; ++k) {
+            const double csd = ujx * S(TF_UX, k) + ujy * S(TF_UY, k) + ujz * S(TF_UZ, k);
+            // g = 1 + (c^2/d^2) (h - cos)^2 / (d^2 + (h - cos)^2), g' = -2 c^2 (h - cos) / den^2
+            const F2 hc = split_d(p.h - csd);
+            const F2 inv = ff_rcp(ff_fma(hc, hc, d2));
+            const F2 t = ff_mul(hc, inv);
+            const F2 g = ff_fma(ff_mul(c2d2, hc), t, one);
+            const F2 dg = ff_mul(ff_mul(m2c2, t), inv);
+            const int q = tri(j, k);
+            pc[q * BLOCK] = ff_pack(split_d(csd));
+            pc[(NP + q) * BLOCK] = ff_pack(g);
+            pc[(2 * NP + q) * BLOCK] = ff_pack(dg);
+            zj = ff_fma(ff_unpack(S(TF_FC, k)), g, zj);
+            S(TF_Z, k) = ff_pack(ff_fma(fcj, g, ff_unpack(S(TF_Z, k))));
+        }
+        S(TF_Z, j) = ff_pack(zj);
+    }
+}
+
+template <int CAP, int BLOCK>
+__device__ __forceinline__ void tersoff_angular_ff(const PairArgs<double> &a, const Stage<double, CAP, BLOCK> &S,
+                                                   const double *spair, int na, int64_t i)
+{
+    constexpr int NP = CAP * (CAP - 1) / 2;
+    const double *pc = spair + threadIdx.x;
+    for (int j = 0; j < na; ++j) {
+        const F2 ujx = ff_unpack(S(TF_UX, j)), ujy = ff_unpack(S(TF_UY, j)), ujz = ff_unpack(S(TF_UZ, j));
+        const F2 irj = ff_unpack(S(TF_IR, j)), Pj = ff_unpack(S(TF_Z, j));
+        const bool swj = no_switch(S(TF_DFC, j));
+        F2 Aj = ff_unpack(S(TF_FR, j));
+        F2 vjx = ff_unpack(S(TF_DX, j)), vjy = ff_unpack(S(TF_DY, j)), vjz = ff_unpack(S(TF_DZ, j));
+        for (int k = j + 1; k < na; ++k) {
+            const int q = tri(j, k);
+            const F2 cs = ff_unpack(pc[q * BLOCK]), dg = ff_unpack(pc[(2 * NP + q) * BLOCK]);
+            const F2 irk = ff_unpack(S(TF_IR, k)), Pk = ff_unpack(S(TF_Z, k));
+            F2 qj, qk;
+            if (swj && no_switch(S(TF_DFC, k))) {
+                // both below R: f_C = 1, f_C' = 0
+                const F2 Q = ff_mul(ff_add(Pj, Pk), dg);
+                qj = ff_mul(Q, irj);
+                qk = ff_mul(Q, irk);
+                Aj = ff_fma(ff_neg(qj), cs, Aj);
+                S(TF_FR, k) = ff_pack(ff_fma(ff_neg(qk), cs, ff_unpack(S(TF_FR, k))));
+            } else {
+                const F2 g = ff_unpack(pc[(NP + q) * BLOCK]);
+                const F2 fcj = ff_unpack(S(TF_FC, j)), dfcj = ff_unpack(S(TF_DFC, j));
+                const F2 fck = ff_unpack(S(TF_FC, k)), dfck = ff_unpack(S(TF_DFC, k));
+                const F2 Q = ff_mul(ff_fma(Pj, fck, ff_mul(Pk, fcj)), dg);
+                const F2 cj = ff_mul(ff_mul(Pk, dfcj), g), ck = ff_mul(ff_mul(Pj, dfck), g);
+                qj = ff_mul(Q, irj);
+                qk = ff_mul(Q, irk);
+                Aj = ff_add(Aj, ff_fma(ff_neg(qj), cs, cj));
+                S(TF_FR, k) = ff_pack(ff_add(ff_unpack(S(TF_FR, k)), ff_fma(ff_neg(qk), cs, ck)));
+            }
+            const F2 ukx = ff_unpack(S(TF_UX, k)), uky = ff_unpack(S(TF_UY, k)), ukz = ff_unpack(S(TF_UZ, k));
+            vjx = ff_fma(qj, ukx, vjx);
+            vjy = ff_fma(qj, uky, vjy);
+            vjz = ff_fma(qj, ukz, vjz);
+            S(TF_DX, k) = ff_pack(ff_fma(qk, ujx, ff_unpack(S(TF_DX, k))));
+            S(TF_DY, k) = ff_pack(ff_fma(qk, ujy, ff_unpack(S(TF_DY, k))));
+            S(TF_DZ, k) = ff_pack(ff_fma(qk, ujz, ff_unpack(S(TF_DZ, k))));
+        }
+        a.d[(int64_t)j * a.N + i] = Vec4<double>{ff_to_d(ff_fma(Aj, ujx, vjx)), ff_to_d(ff_fma(Aj, ujy, vjy)),
+                                                 ff_to_d(ff_fma(Aj, ujz, vjz)), 0.0};
+    }
+}
+
 // Pair pass for one atom (Tersoff).  MULTI: p holds atom i's element constants (angular
 // and bond-order; rc2 = its row's largest cutoff) and row its pair-constant row; each
 // bond's radial functions take the pair's constants (chi folded into B).
@@ -366,23 +453,38 @@ __device__ __forceinline__ void tersoff_atom(const PairArgs<T> &a, const Tersoff
 {
     const int64_t N = a.N;
     Stage<T, CAP, BLOCK> S{base, (int)threadIdx.x};
-    // per unordered bond pair q: fp64, cos theta, g and dg/dcos from the zeta loop; fp32,
-    // 1/(d^2 + (h - cos)^2) (slot PCS)
-    constexpr int NP = CAP * (CAP - 1) / 2;
+    // per unordered bond pair q: fp64, cos theta, g and dg/dcos from the zeta loop (float
+    // pairs, three slots); fp32, 1/(d^2 + (h - cos)^2) (one slot)
     T *spair = base + TF_NF * CAP * BLOCK;
     auto PCS = [&](int q) -> T & { return spair[q * BLOCK + threadIdx.x]; };
-    auto PG = [&](int q) -> T & { return spair[(NP + q) * BLOCK + threadIdx.x]; };
-    auto PDG = [&](int q) -> T & { return spair[(2 * NP + q) * BLOCK + threadIdx.x]; };
 
     uint32_t mask;
     const int na = collect_bonds<T, CAP, BLOCK, FULL_CAP, false, MULTI>(a, i, box, p.rc2, mask, S, TF_UX, TF_UY,
                                                                         TF_UZ, TF_IR, row, TF_DX);
     if (na < 0) return;   // deferred to the full-capacity pass
 
+    // fp64: after the radial loop f_C, and after the bond-order loop every value the angular
+    // loop reads, are staged as float pairs (ff_pack); the two bond-pair loops then run on
+    // the fp32 pipe but for cos theta (see tersoff_zeta_ff, tersoff_angular_ff)
+    constexpr bool FF = sizeof(T) == 8;
+    auto put = [&](int f, int k, T v) {
+        if constexpr (FF) S(f, k) = ff_pack(split_d(v));
+        else S(f, k) = v;
+    };
+    auto get = [&](int f, int k) -> T {
+        if constexpr (FF) return ff_to_d(ff_unpack(S(f, k)));
+        else return S(f, k);
+    };
+
     // per-bond radial functions (the staged vectors become unit vectors, r^2 -> 1/r)
     for (int k = 0; k < na; ++k) {
         const TersoffC<T> &pk = bond_const<MULTI>(p, row, MULTI ? S(TF_DX, k) : T(0));
         const T r2 = S(TF_IR, k);
+        // the float-pair staging turns inf and NaN into finite values: a bond shorter than
+        // 1e-15 A (coincident atoms, 1/r = +inf) is reported here instead of through F
+        if constexpr (FF) {
+            if (!(r2 >= T(1e-30))) pair_fail(a, i, MD_ERR_NAN);
+        }
         const T ir = M<T>::rsqrt_(r2);
         const T r = r2 * ir;
         S(TF_UX, k) *= ir;
@@ -398,33 +500,30 @@ __device__ __forceinline__ void tersoff_atom(const PairArgs<T> &a, const Tersoff
             fc = cn * cn;
             dfc = -pk.pi_SR * sn * cn;
         }
-        S(TF_FC, k) = fc;
+        put(TF_FC, k, fc);
         S(TF_DFC, k) = dfc;
         S(TF_FR, k) = pk.A * M<T>::texp_(-pk.lam * r);
         S(TF_FA, k) = pk.B * M<T>::texp_(-pk.mu * r);
-        S(TF_Z, k) = T(0);
+        S(TF_Z, k) = T(0);   // also the float pair (0, 0)
     }
     // zeta_ij = sum_{k != j} f_C(r_ik) g(theta_ijk), each unordered pair once
-    for (int j = 0; j < na; ++j) {
-        const T ujx = S(TF_UX, j), ujy = S(TF_UY, j), ujz = S(TF_UZ, j), fcj = S(TF_FC, j);
-        T zj = S(TF_Z, j);
-        for (int k = j + 1; k < na; ++k) {
-            const T cs = ujx * S(TF_UX, k) + ujy * S(TF_UY, k) + ujz * S(TF_UZ, k);
-            const T inv = tersoff_inv_den(p, cs);
-            T g, dg;
-            tersoff_g(p, cs, inv, g, dg);
-            const int q = tri(j, k);
-            if constexpr (kCachePairs<T>) {
-                PCS(q) = cs;
-                PG(q) = g;
-                PDG(q) = dg;
-            } else {
-                PCS(q) = inv;
+    if constexpr (FF) {
+        tersoff_zeta_ff<CAP, BLOCK>(p, S, spair, na);
+    } else {
+        for (int j = 0; j < na; ++j) {
+            const T ujx = S(TF_UX, j), ujy = S(TF_UY, j), ujz = S(TF_UZ, j), fcj = S(TF_FC, j);
+            T zj = S(TF_Z, j);
+            for (int k = j + 1; k < na; ++k) {
+                const T cs = ujx * S(TF_UX, k) + ujy * S(TF_UY, k) + ujz * S(TF_UZ, k);
+                const T inv = tersoff_inv_den(p, cs);
+                T g, dg;
+                tersoff_g(p, cs, inv, g, dg);
+                PCS(tri(j, k)) = inv;
+                zj += S(TF_FC, k) * g;
+                S(TF_Z, k) += fcj * g;
             }
-            zj += S(TF_FC, k) * g;
-            S(TF_Z, k) += fcj * g;
+            S(TF_Z, j) = zj;
         }
-        S(TF_Z, j) = zj;
     }
     // bond orders, U_i, radial part of dU_i/dr_ij; P_k = -1/2 f_C f_A b'_k kept in TF_Z.
     // dU_i/dr_ij is assembled as A_j u_j + V_j: the scalar A_j (radial part plus the
@@ -434,22 +533,30 @@ __device__ __forceinline__ void tersoff_atom(const PairArgs<T> &a, const Tersoff
     for (int k = 0; k < na; ++k) {
         const TersoffC<T> &pk = bond_const<MULTI>(p, row, MULTI ? S(TF_DX, k) : T(0));
         T b, db;
-        tersoff_b(p, S(TF_Z, k), b, db);
-        const T fc = S(TF_FC, k), dfc = S(TF_DFC, k), fr = S(TF_FR, k), fa = S(TF_FA, k);
+        tersoff_b(p, get(TF_Z, k), b, db);
+        const T dfc = S(TF_DFC, k), fr = S(TF_FR, k), fa = S(TF_FA, k);
         T radial;
         if (no_switch(dfc)) {
             // f_C = 1, f_C' = 0: the same arithmetic without the unit factors and zero terms
             ui += T(0.5) * (fr - b * fa);
             radial = T(0.5) * (-pk.lam * fr + b * (pk.mu * fa));
-            S(TF_Z, k) = T(-0.5) * fa * db;
+            put(TF_Z, k, T(-0.5) * fa * db);
         } else {
+            const T fc = get(TF_FC, k);
             ui += T(0.5) * fc * (fr - b * fa);
             const T dR = dfc * fr - pk.lam * fc * fr;   // (f_C f_R)'
             const T dA = dfc * fa - pk.mu * fc * fa;    // (f_C f_A)'
             radial = T(0.5) * (dR - b * dA);
-            S(TF_Z, k) = T(-0.5) * fc * fa * db;
+            put(TF_Z, k, T(-0.5) * fc * fa * db);
         }
-        S(TF_FR, k) = radial;
+        put(TF_FR, k, radial);
+        if constexpr (FF) {
+            S(TF_UX, k) = ff_pack(split_d(S(TF_UX, k)));
+            S(TF_UY, k) = ff_pack(split_d(S(TF_UY, k)));
+            S(TF_UZ, k) = ff_pack(split_d(S(TF_UZ, k)));
+            S(TF_IR, k) = ff_pack(split_d(S(TF_IR, k)));
+            S(TF_DFC, k) = ff_pack(split_d(dfc));   // +0 stays the all-zero pattern
+        }
         S(TF_DX, k) = T(0);
         S(TF_DY, k) = T(0);
         S(TF_DZ, k) = T(0);
@@ -457,46 +564,43 @@ __device__ __forceinline__ void tersoff_atom(const PairArgs<T> &a, const Tersoff
     // angular part: for each unordered pair (j,k), with dcos_j = (u_k - cos u_j)/r_ij,
     //   d_j += (P_j fc_k + P_k fc_j) g' dcos_j + P_k fc'_j g u_j   (and j <-> k),
     // i.e. V_j += q_j u_k and A_j += c_j - q_j cos, q_j = (P_j fc_k + P_k fc_j) g'/r_ij
-    for (int j = 0; j < na; ++j) {
-        const T ujx = S(TF_UX, j), ujy = S(TF_UY, j), ujz = S(TF_UZ, j);
-        const T irj = S(TF_IR, j), fcj = S(TF_FC, j), dfcj = S(TF_DFC, j), Pj = S(TF_Z, j);
-        T Aj = S(TF_FR, j);
-        T vjx = S(TF_DX, j), vjy = S(TF_DY, j), vjz = S(TF_DZ, j);
-        for (int k = j + 1; k < na; ++k) {
-            const T ukx = S(TF_UX, k), uky = S(TF_UY, k), ukz = S(TF_UZ, k);
-            const T irk = S(TF_IR, k), fck = S(TF_FC, k), dfck = S(TF_DFC, k), Pk = S(TF_Z, k);
-            const int q = tri(j, k);
-            T cs, g, dg;
-            if constexpr (kCachePairs<T>) {
-                cs = PCS(q);
-                g = PG(q);
-                dg = PDG(q);
-            } else {
-                cs = ujx * ukx + ujy * uky + ujz * ukz;
-                tersoff_g(p, cs, PCS(q), g, dg);
+    if constexpr (FF) {
+        tersoff_angular_ff<CAP, BLOCK>(a, S, spair, na, i);
+    } else {
+        for (int j = 0; j < na; ++j) {
+            const T ujx = S(TF_UX, j), ujy = S(TF_UY, j), ujz = S(TF_UZ, j);
+            const T irj = S(TF_IR, j), fcj = S(TF_FC, j), dfcj = S(TF_DFC, j), Pj = S(TF_Z, j);
+            T Aj = S(TF_FR, j);
+            T vjx = S(TF_DX, j), vjy = S(TF_DY, j), vjz = S(TF_DZ, j);
+            for (int k = j + 1; k < na; ++k) {
+                const T ukx = S(TF_UX, k), uky = S(TF_UY, k), ukz = S(TF_UZ, k);
+                const T irk = S(TF_IR, k), fck = S(TF_FC, k), dfck = S(TF_DFC, k), Pk = S(TF_Z, k);
+                const T cs = ujx * ukx + ujy * uky + ujz * ukz;
+                T g, dg;
+                tersoff_g(p, cs, PCS(tri(j, k)), g, dg);
+                T qj, qk;
+                if (no_switch(dfcj) && no_switch(dfck)) {
+                    // both below R: f_C = 1, f_C' = 0
+                    const T Q = (Pj + Pk) * dg;
+                    qj = Q * irj; qk = Q * irk;
+                    Aj = fma(-qj, cs, Aj);
+                    S(TF_FR, k) = fma(-qk, cs, S(TF_FR, k));
+                } else {
+                    const T Q = (Pj * fck + Pk * fcj) * dg;
+                    const T cj = Pk * dfcj * g, ck = Pj * dfck * g;
+                    qj = Q * irj; qk = Q * irk;
+                    Aj += cj - qj * cs;
+                    S(TF_FR, k) += ck - qk * cs;
+                }
+                vjx = fma(qj, ukx, vjx);
+                vjy = fma(qj, uky, vjy);
+                vjz = fma(qj, ukz, vjz);
+                S(TF_DX, k) = fma(qk, ujx, S(TF_DX, k));
+                S(TF_DY, k) = fma(qk, ujy, S(TF_DY, k));
+                S(TF_DZ, k) = fma(qk, ujz, S(TF_DZ, k));
             }
-            T qj, qk;
-            if (no_switch(dfcj) && no_switch(dfck)) {
-                // both below R: f_C = 1, f_C' = 0
-                const T Q = (Pj + Pk) * dg;
-                qj = Q * irj; qk = Q * irk;
-                Aj = fma(-qj, cs, Aj);
-                S(TF_FR, k) = fma(-qk, cs, S(TF_FR, k));
-            } else {
-                const T Q = (Pj * fck + Pk * fcj) * dg;
-                const T cj = Pk * dfcj * g, ck = Pj * dfck * g;
-                qj = Q * irj; qk = Q * irk;
-                Aj += cj - qj * cs;
-                S(TF_FR, k) += ck - qk * cs;
-            }
-            vjx = fma(qj, ukx, vjx);
-            vjy = fma(qj, uky, vjy);
-            vjz = fma(qj, ukz, vjz);
-            S(TF_DX, k) = fma(qk, ujx, S(TF_DX, k));
-            S(TF_DY, k) = fma(qk, ujy, S(TF_DY, k));
-            S(TF_DZ, k) = fma(qk, ujz, S(TF_DZ, k));
+            a.d[(int64_t)j * N + i] = Vec4<T>{fma(Aj, ujx, vjx), fma(Aj, ujy, vjy), fma(Aj, ujz, vjz), T(0)};
         }
-        a.d[(int64_t)j * N + i] = Vec4<T>{fma(Aj, ujx, vjx), fma(Aj, ujy, vjy), fma(Aj, ujz, vjz), T(0)};
     }
     a.mask[i] = mask;
     a.u[i] = to_d(ui);
