@@ -336,6 +336,26 @@ __device__ __forceinline__ void tersoff_b(const TersoffC<T> &p, T zeta, T &b, T 
     db = T(-0.5) * b * x * M<T>::rcp_(zeta * (T(1) + x));
 }
 
+// fp64 pass: b as above (fp64-assisted exp and log: b multiplies f_A in the radial term
+// 1/2 ((f_C f_R)' - b (f_C f_A)'), whose two parts nearly cancel at equilibrium), and
+// P = -1/2 f_C f_A db/dzeta = cfa b x / (zeta (1 + x)) (cfa = f_C f_A / 4) as a float pair:
+// P only scales the angular terms, which the float-pair angular loop forms to 2^-47 anyway.
+// zeta (a float pair) counts as zero below the float normal range.
+__device__ __forceinline__ double tersoff_b_ff(const TersoffC<double> &p, F2 zf, F2 cfa, F2 &P)
+{
+    const double zeta = ff_to_d(zf);
+    if (!positive_nonneg(zeta) || p.beta_zero) {
+        P = F2{0.f, 0.f};
+        return 1.0;
+    }
+    const double x = exp_ff(fma(p.n, log_ff(zeta), p.n_ln_beta));   // (beta zeta)^n
+    const double b = exp_ff(-p.inv2n * log_ff(1.0 + x));
+    const F2 xf = split_d(x);
+    const F2 den = ff_mul(zf, ff_add(F2{1.f, 0.f}, xf));
+    P = ff_mul(ff_mul(ff_mul(cfa, split_d(b)), xf), ff_rcp(den));
+    return b;
+}
+
 // index of the unordered bond pair (j, k), j < k
 __device__ __forceinline__ int tri(int j, int k) { return k * (k - 1) / 2 + j; }
 
@@ -532,22 +552,32 @@ __device__ __forceinline__ void tersoff_atom(const PairArgs<T> &a, const Tersoff
     T ui = T(0);
     for (int k = 0; k < na; ++k) {
         const TersoffC<T> &pk = bond_const<MULTI>(p, row, MULTI ? S(TF_DX, k) : T(0));
-        T b, db;
-        tersoff_b(p, get(TF_Z, k), b, db);
         const T dfc = S(TF_DFC, k), fr = S(TF_FR, k), fa = S(TF_FA, k);
+        // f_C = 1, f_C' = 0 below R: the same arithmetic without the unit factors and zero terms
+        const bool sw = !no_switch(dfc);
+        T b;
+        if constexpr (FF) {
+            F2 cfa = split_d(fa);
+            cfa = F2{0.25f * cfa.h, 0.25f * cfa.l};
+            if (sw) cfa = ff_mul(cfa, ff_unpack(S(TF_FC, k)));
+            F2 P;
+            b = tersoff_b_ff(p, ff_unpack(S(TF_Z, k)), cfa, P);
+            S(TF_Z, k) = ff_pack(P);
+        } else {
+            T db;
+            tersoff_b(p, S(TF_Z, k), b, db);
+            S(TF_Z, k) = sw ? T(-0.5) * S(TF_FC, k) * fa * db : T(-0.5) * fa * db;
+        }
         T radial;
-        if (no_switch(dfc)) {
-            // f_C = 1, f_C' = 0: the same arithmetic without the unit factors and zero terms
+        if (!sw) {
             ui += T(0.5) * (fr - b * fa);
             radial = T(0.5) * (-pk.lam * fr + b * (pk.mu * fa));
-            put(TF_Z, k, T(-0.5) * fa * db);
         } else {
             const T fc = get(TF_FC, k);
             ui += T(0.5) * fc * (fr - b * fa);
             const T dR = dfc * fr - pk.lam * fc * fr;   // (f_C f_R)'
             const T dA = dfc * fa - pk.mu * fc * fa;    // (f_C f_A)'
             radial = T(0.5) * (dR - b * dA);
-            put(TF_Z, k, T(-0.5) * fc * fa * db);
         }
         put(TF_FR, k, radial);
         if constexpr (FF) {
