@@ -359,14 +359,19 @@ __device__ __forceinline__ double tersoff_b_ff(const TersoffC<double> &p, F2 zf,
 // index of the unordered bond pair (j, k), j < k
 __device__ __forceinline__ int tri(int j, int k) { return k * (k - 1) / 2 + j; }
 
-// Per unordered bond pair the fp64 pass keeps cos theta, g and g' (float pairs) from the zeta
-// loop for the angular loop, which saves it about a hundred fp32 instructions per pair; the
-// fp32 pass keeps only 1/(d^2 + (h - cos)^2) and recomputes the rest (it is bound by
-// instruction issue and occupancy, and three words per pair would cost it resident blocks).
-template <typename T>
-constexpr bool kCachePairs = sizeof(T) == 8;
-template <typename T, int CAP>
-constexpr int tersoff_smem_fields() { return TF_NF * CAP + (kCachePairs<T> ? 3 : 1) * (CAP * (CAP - 1) / 2); }
+// Shared-memory words per bond and per unordered bond pair.  fp32 pass: the twelve bond
+// fields, and per pair 1/(d^2 + (h - cos)^2) (it recomputes cos, g and g' in the angular loop:
+// it is bound by instruction issue and occupancy).  fp64 pass: nine bond fields (its angular
+// loop sums each bond's terms itself and scatters nothing, so it needs no TF_DX..TF_DZ) plus
+// the element code of MULTI in TF_DX, and per pair h - cos and g' as float pairs from the zeta
+// loop (g is recomputed for the rare bonds in the switching region).
+template <typename T, bool MULTI>
+constexpr int kTersoffBondFields = sizeof(T) == 8 ? TF_DX + (MULTI ? 1 : 0) : TF_NF;
+template <typename T, int CAP, bool MULTI = false>
+constexpr int tersoff_smem_fields()
+{
+    return kTersoffBondFields<T, MULTI> * CAP + (sizeof(T) == 8 ? 2 : 1) * (CAP * (CAP - 1) / 2);
+}
 
 // Constants of bond k of the atom: its element pair's (MULTI: the row entry of the element
 // staged in field TF_DX), else the single set's.
@@ -384,7 +389,7 @@ __device__ __forceinline__ const TersoffC<T> &bond_const(const TersoffC<T> &p, c
 // and h = -0.5706), so an absolute error e in cos is a relative error e/|h - cos| in g';
 // cos theta and h - cos theta are therefore formed in fp64 from the fp64 unit vectors (four
 // fp64 instructions per pair) and only then split.  The pair cache holds, per unordered
-// bond pair q = tri(j, k), cos theta, g and dg/dcos in slots q, NP + q, 2 NP + q.
+// bond pair q = tri(j, k), h - cos theta and dg/dcos in slots q and NP + q.
 template <int CAP, int BLOCK>
 __device__ __forceinline__ void tersoff_zeta_ff(const TersoffC<double> &p, const Stage<double, CAP, BLOCK> &S,
                                                 double *spair, int na)
@@ -406,9 +411,8 @@ __device__ __forceinline__ void tersoff_zeta_ff(const TersoffC<double> &p, const
             const F2 g = ff_fma(ff_mul(c2d2, hc), t, one);
             const F2 dg = ff_mul(ff_mul(m2c2, t), inv);
             const int q = tri(j, k);
-            pc[q * BLOCK] = ff_pack(split_d(csd));
-            pc[(NP + q) * BLOCK] = ff_pack(g);
-            pc[(2 * NP + q) * BLOCK] = ff_pack(dg);
+            pc[q * BLOCK] = ff_pack(hc);
+            pc[(NP + q) * BLOCK] = ff_pack(dg);
             zj = ff_fma(ff_unpack(S(TF_FC, k)), g, zj);
             S(TF_Z, k) = ff_pack(ff_fma(fcj, g, ff_unpack(S(TF_Z, k))));
         }
@@ -416,51 +420,48 @@ __device__ __forceinline__ void tersoff_zeta_ff(const TersoffC<double> &p, const
     }
 }
 
+// The angular loop, each bond j on its own: A_j and V_j take the terms of every pair (j, k),
+// k != j, so nothing is scattered into bond k's fields; the factor (P_j + P_k) g' of a pair
+// is formed once from each side, from the same values, so both sides see the same number.
 template <int CAP, int BLOCK>
-__device__ __forceinline__ void tersoff_angular_ff(const PairArgs<double> &a, const Stage<double, CAP, BLOCK> &S,
-                                                   const double *spair, int na, int64_t i)
+__device__ __forceinline__ void tersoff_angular_ff(const PairArgs<double> &a, const TersoffC<double> &p,
+                                                   const Stage<double, CAP, BLOCK> &S, const double *spair,
+                                                   int na, int64_t i)
 {
     constexpr int NP = CAP * (CAP - 1) / 2;
     const double *pc = spair + threadIdx.x;
+    const F2 h = split_d(p.h);
     for (int j = 0; j < na; ++j) {
-        const F2 ujx = ff_unpack(S(TF_UX, j)), ujy = ff_unpack(S(TF_UY, j)), ujz = ff_unpack(S(TF_UZ, j));
         const F2 irj = ff_unpack(S(TF_IR, j)), Pj = ff_unpack(S(TF_Z, j));
         const bool swj = no_switch(S(TF_DFC, j));
         F2 Aj = ff_unpack(S(TF_FR, j));
-        F2 vjx = ff_unpack(S(TF_DX, j)), vjy = ff_unpack(S(TF_DY, j)), vjz = ff_unpack(S(TF_DZ, j));
-        for (int k = j + 1; k < na; ++k) {
-            const int q = tri(j, k);
-            const F2 cs = ff_unpack(pc[q * BLOCK]), dg = ff_unpack(pc[(2 * NP + q) * BLOCK]);
-            const F2 irk = ff_unpack(S(TF_IR, k)), Pk = ff_unpack(S(TF_Z, k));
-            F2 qj, qk;
+        F2 vx{0.f, 0.f}, vy{0.f, 0.f}, vz{0.f, 0.f};
+        for (int k = 0; k < na; ++k) {
+            if (k == j) continue;
+            const int q = k > j ? tri(j, k) : tri(k, j);
+            const F2 hc = ff_unpack(pc[q * BLOCK]), dg = ff_unpack(pc[(NP + q) * BLOCK]);
+            const F2 cs = ff_add(h, ff_neg(hc));
+            const F2 Pk = ff_unpack(S(TF_Z, k));
+            F2 qj;
             if (swj && no_switch(S(TF_DFC, k))) {
                 // both below R: f_C = 1, f_C' = 0
-                const F2 Q = ff_mul(ff_add(Pj, Pk), dg);
-                qj = ff_mul(Q, irj);
-                qk = ff_mul(Q, irk);
+                qj = ff_mul(ff_mul(ff_add(Pj, Pk), dg), irj);
                 Aj = ff_fma(ff_neg(qj), cs, Aj);
-                S(TF_FR, k) = ff_pack(ff_fma(ff_neg(qk), cs, ff_unpack(S(TF_FR, k))));
             } else {
-                const F2 g = ff_unpack(pc[(NP + q) * BLOCK]);
+                const F2 inv = ff_rcp(ff_fma(hc, hc, split_d(p.d2)));
+                const F2 g = ff_fma(ff_mul(split_d(p.c2d2), hc), ff_mul(hc, inv), F2{1.f, 0.f});
                 const F2 fcj = ff_unpack(S(TF_FC, j)), dfcj = ff_unpack(S(TF_DFC, j));
-                const F2 fck = ff_unpack(S(TF_FC, k)), dfck = ff_unpack(S(TF_DFC, k));
-                const F2 Q = ff_mul(ff_fma(Pj, fck, ff_mul(Pk, fcj)), dg);
-                const F2 cj = ff_mul(ff_mul(Pk, dfcj), g), ck = ff_mul(ff_mul(Pj, dfck), g);
-                qj = ff_mul(Q, irj);
-                qk = ff_mul(Q, irk);
-                Aj = ff_add(Aj, ff_fma(ff_neg(qj), cs, cj));
-                S(TF_FR, k) = ff_pack(ff_add(ff_unpack(S(TF_FR, k)), ff_fma(ff_neg(qk), cs, ck)));
+                const F2 fck = ff_unpack(S(TF_FC, k));
+                qj = ff_mul(ff_mul(ff_fma(Pj, fck, ff_mul(Pk, fcj)), dg), irj);
+                Aj = ff_add(Aj, ff_fma(ff_neg(qj), cs, ff_mul(ff_mul(Pk, dfcj), g)));
             }
-            const F2 ukx = ff_unpack(S(TF_UX, k)), uky = ff_unpack(S(TF_UY, k)), ukz = ff_unpack(S(TF_UZ, k));
-            vjx = ff_fma(qj, ukx, vjx);
-            vjy = ff_fma(qj, uky, vjy);
-            vjz = ff_fma(qj, ukz, vjz);
-            S(TF_DX, k) = ff_pack(ff_fma(qk, ujx, ff_unpack(S(TF_DX, k))));
-            S(TF_DY, k) = ff_pack(ff_fma(qk, ujy, ff_unpack(S(TF_DY, k))));
-            S(TF_DZ, k) = ff_pack(ff_fma(qk, ujz, ff_unpack(S(TF_DZ, k))));
+            vx = ff_fma(qj, ff_unpack(S(TF_UX, k)), vx);
+            vy = ff_fma(qj, ff_unpack(S(TF_UY, k)), vy);
+            vz = ff_fma(qj, ff_unpack(S(TF_UZ, k)), vz);
         }
-        a.d[(int64_t)j * a.N + i] = Vec4<double>{ff_to_d(ff_fma(Aj, ujx, vjx)), ff_to_d(ff_fma(Aj, ujy, vjy)),
-                                                 ff_to_d(ff_fma(Aj, ujz, vjz)), 0.0};
+        const F2 ujx = ff_unpack(S(TF_UX, j)), ujy = ff_unpack(S(TF_UY, j)), ujz = ff_unpack(S(TF_UZ, j));
+        a.d[(int64_t)j * a.N + i] = Vec4<double>{ff_to_d(ff_fma(Aj, ujx, vx)), ff_to_d(ff_fma(Aj, ujy, vy)),
+                                                 ff_to_d(ff_fma(Aj, ujz, vz)), 0.0};
     }
 }
 
@@ -473,9 +474,9 @@ __device__ __forceinline__ void tersoff_atom(const PairArgs<T> &a, const Tersoff
 {
     const int64_t N = a.N;
     Stage<T, CAP, BLOCK> S{base, (int)threadIdx.x};
-    // per unordered bond pair q: fp64, cos theta, g and dg/dcos from the zeta loop (float
-    // pairs, three slots); fp32, 1/(d^2 + (h - cos)^2) (one slot)
-    T *spair = base + TF_NF * CAP * BLOCK;
+    // per unordered bond pair q: fp64, h - cos theta and dg/dcos from the zeta loop (float
+    // pairs, two slots); fp32, 1/(d^2 + (h - cos)^2) (one slot)
+    T *spair = base + kTersoffBondFields<T, MULTI> * CAP * BLOCK;
     auto PCS = [&](int q) -> T & { return spair[q * BLOCK + threadIdx.x]; };
 
     uint32_t mask;
@@ -586,16 +587,17 @@ __device__ __forceinline__ void tersoff_atom(const PairArgs<T> &a, const Tersoff
             S(TF_UZ, k) = ff_pack(split_d(S(TF_UZ, k)));
             S(TF_IR, k) = ff_pack(split_d(S(TF_IR, k)));
             S(TF_DFC, k) = ff_pack(split_d(dfc));   // +0 stays the all-zero pattern
+        } else {
+            S(TF_DX, k) = T(0);
+            S(TF_DY, k) = T(0);
+            S(TF_DZ, k) = T(0);
         }
-        S(TF_DX, k) = T(0);
-        S(TF_DY, k) = T(0);
-        S(TF_DZ, k) = T(0);
     }
     // angular part: for each unordered pair (j,k), with dcos_j = (u_k - cos u_j)/r_ij,
     //   d_j += (P_j fc_k + P_k fc_j) g' dcos_j + P_k fc'_j g u_j   (and j <-> k),
     // i.e. V_j += q_j u_k and A_j += c_j - q_j cos, q_j = (P_j fc_k + P_k fc_j) g'/r_ij
     if constexpr (FF) {
-        tersoff_angular_ff<CAP, BLOCK>(a, S, spair, na, i);
+        tersoff_angular_ff<CAP, BLOCK>(a, p, S, spair, na, i);
     } else {
         for (int j = 0; j < na; ++j) {
             const T ujx = S(TF_UX, j), ujy = S(TF_UY, j), ujz = S(TF_UZ, j);
@@ -1488,10 +1490,10 @@ constexpr int kPairCapSmallSW = 8;
 constexpr int kPairBlockFull = 32;   // full-capacity pass over the deferred atoms
 constexpr int kGatherBlock = 128;
 
-template <typename T, int CAP, int BLOCK>
+template <typename T, int CAP, int BLOCK, bool MULTI = false>
 size_t smem_for(int kind)
 {
-    const int nf = kind == 1 ? tersoff_smem_fields<T, CAP>() : sw_smem_fields<CAP>();
+    const int nf = kind == 1 ? tersoff_smem_fields<T, CAP, MULTI>() : sw_smem_fields<CAP>();
     return (size_t)nf * BLOCK * sizeof(T);
 }
 
@@ -1505,7 +1507,7 @@ void set_smem()
                              (int)smem_for<T, CAP, BLOCK>(2));
     if constexpr (!BATCH)
         cudaFuncSetAttribute(k_pair_tersoff<T, CAP, BLOCK, FULL_CAP, false, true>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_for<T, CAP, BLOCK>(1));
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_for<T, CAP, BLOCK, true>(1));
 }
 
 template <typename T, int B, bool BATCH>
@@ -1565,10 +1567,10 @@ void pair_launch_b(const Plan &p, cudaStream_t s, int list, int parts)
             if (p.multi) {   // several elements: per-pair constants from the device table
                 if (parts & PAIR_FAST)
                     k_pair_tersoff<T, kPairCapSmall, B, false, false, true>
-                        <<<nb, B, smem_for<T, kPairCapSmall, B>(1), s>>>(a, c);
+                        <<<nb, B, smem_for<T, kPairCapSmall, B, true>(1), s>>>(a, c);
                 if (parts & PAIR_DEFERRED)
                     k_pair_tersoff<T, FULL, kPairBlockFull, true, false, true>
-                        <<<(unsigned)nbf, kPairBlockFull, smem_for<T, FULL, kPairBlockFull>(1), s>>>(a, c);
+                        <<<(unsigned)nbf, kPairBlockFull, smem_for<T, FULL, kPairBlockFull, true>(1), s>>>(a, c);
                 return;
             }
         }
