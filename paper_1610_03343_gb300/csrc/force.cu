@@ -291,7 +291,7 @@ __device__ __forceinline__ int collect_bonds(const PairArgs<T> &a, int64_t i, co
 }
 
 // ------------------------------------------------------------------ Tersoff
-enum { TF_UX, TF_UY, TF_UZ, TF_IR, TF_FC, TF_DFC, TF_FR, TF_FA, TF_Z, TF_DX, TF_DY, TF_DZ, TF_NF };
+enum { TF_UX, TF_UY, TF_UZ, TF_IR, TF_FC, TF_DFC, TF_FR, TF_Z, TF_FA, TF_DX, TF_DY, TF_DZ, TF_NF };
 
 // g(cos) of Eq. 5 written as 1 + (c^2/d^2) (h-cos)^2 / (d^2 + (h-cos)^2): the same
 // function as printed, without the cancellation of c^2/d^2 - c^2/(d^2+(h-cos)^2)
@@ -360,13 +360,17 @@ __device__ __forceinline__ double tersoff_b_ff(const TersoffC<double> &p, F2 zf,
 __device__ __forceinline__ int tri(int j, int k) { return k * (k - 1) / 2 + j; }
 
 // Shared-memory words per bond and per unordered bond pair.  fp32 pass: the twelve bond
-// fields, and per pair 1/(d^2 + (h - cos)^2) (it recomputes cos, g and g' in the angular loop:
-// it is bound by instruction issue and occupancy).  fp64 pass: nine bond fields (its angular
-// loop sums each bond's terms itself and scatters nothing, so it needs no TF_DX..TF_DZ) plus
-// the element code of MULTI in TF_DX, and per pair h - cos and g' as float pairs from the zeta
+// fields (the element code of MULTI in TF_DX until the angular loop), and per pair
+// 1/(d^2 + (h - cos)^2) (it recomputes cos, g and g' in the angular loop: it is bound by
+// instruction issue and occupancy).  fp64 pass: eight bond fields -- TF_FR holds r until the
+// bond-order loop, which forms f_R and f_A itself, and its angular loop sums each bond's
+// terms itself and scatters nothing, so it needs neither TF_FA nor TF_DX..TF_DZ -- plus the
+// element code of MULTI in TF_FA, and per pair h - cos and g' as float pairs from the zeta
 // loop (g is recomputed for the rare bonds in the switching region).
 template <typename T, bool MULTI>
-constexpr int kTersoffBondFields = sizeof(T) == 8 ? TF_DX + (MULTI ? 1 : 0) : TF_NF;
+constexpr int kTersoffBondFields = sizeof(T) == 8 ? TF_FA + (MULTI ? 1 : 0) : TF_NF;
+template <typename T>
+constexpr int kTersoffTypeField = sizeof(T) == 8 ? TF_FA : TF_DX;
 template <typename T, int CAP, bool MULTI = false>
 constexpr int tersoff_smem_fields()
 {
@@ -374,7 +378,7 @@ constexpr int tersoff_smem_fields()
 }
 
 // Constants of bond k of the atom: its element pair's (MULTI: the row entry of the element
-// staged in field TF_DX), else the single set's.
+// staged in field kTersoffTypeField), else the single set's.
 template <bool MULTI, typename T>
 __device__ __forceinline__ const TersoffC<T> &bond_const(const TersoffC<T> &p, const TersoffC<T> *row, T tcode)
 {
@@ -481,7 +485,7 @@ __device__ __forceinline__ void tersoff_atom(const PairArgs<T> &a, const Tersoff
 
     uint32_t mask;
     const int na = collect_bonds<T, CAP, BLOCK, FULL_CAP, false, MULTI>(a, i, box, p.rc2, mask, S, TF_UX, TF_UY,
-                                                                        TF_UZ, TF_IR, row, TF_DX);
+                                                                        TF_UZ, TF_IR, row, kTersoffTypeField<T>);
     if (na < 0) return;   // deferred to the full-capacity pass
 
     // fp64: after the radial loop f_C, and after the bond-order loop every value the angular
@@ -499,7 +503,7 @@ __device__ __forceinline__ void tersoff_atom(const PairArgs<T> &a, const Tersoff
 
     // per-bond radial functions (the staged vectors become unit vectors, r^2 -> 1/r)
     for (int k = 0; k < na; ++k) {
-        const TersoffC<T> &pk = bond_const<MULTI>(p, row, MULTI ? S(TF_DX, k) : T(0));
+        const TersoffC<T> &pk = bond_const<MULTI>(p, row, MULTI ? S(kTersoffTypeField<T>, k) : T(0));
         const T r2 = S(TF_IR, k);
         // the float-pair staging turns inf and NaN into finite values: a bond shorter than
         // 1e-15 A (coincident atoms, 1/r = +inf) is reported here instead of through F
@@ -523,8 +527,12 @@ __device__ __forceinline__ void tersoff_atom(const PairArgs<T> &a, const Tersoff
         }
         put(TF_FC, k, fc);
         S(TF_DFC, k) = dfc;
-        S(TF_FR, k) = pk.A * M<T>::texp_(-pk.lam * r);
-        S(TF_FA, k) = pk.B * M<T>::texp_(-pk.mu * r);
+        if constexpr (FF) {
+            S(TF_FR, k) = r;
+        } else {
+            S(TF_FR, k) = pk.A * M<T>::texp_(-pk.lam * r);
+            S(TF_FA, k) = pk.B * M<T>::texp_(-pk.mu * r);
+        }
         S(TF_Z, k) = T(0);   // also the float pair (0, 0)
     }
     // zeta_ij = sum_{k != j} f_C(r_ik) g(theta_ijk), each unordered pair once
@@ -552,8 +560,17 @@ __device__ __forceinline__ void tersoff_atom(const PairArgs<T> &a, const Tersoff
     // bonds) in TF_DX..TF_DZ.
     T ui = T(0);
     for (int k = 0; k < na; ++k) {
-        const TersoffC<T> &pk = bond_const<MULTI>(p, row, MULTI ? S(TF_DX, k) : T(0));
-        const T dfc = S(TF_DFC, k), fr = S(TF_FR, k), fa = S(TF_FA, k);
+        const TersoffC<T> &pk = bond_const<MULTI>(p, row, MULTI ? S(kTersoffTypeField<T>, k) : T(0));
+        const T dfc = S(TF_DFC, k);
+        T fr, fa;
+        if constexpr (FF) {
+            const T r = S(TF_FR, k);
+            fr = pk.A * M<T>::texp_(-pk.lam * r);
+            fa = pk.B * M<T>::texp_(-pk.mu * r);
+        } else {
+            fr = S(TF_FR, k);
+            fa = S(TF_FA, k);
+        }
         // f_C = 1, f_C' = 0 below R: the same arithmetic without the unit factors and zero terms
         const bool sw = !no_switch(dfc);
         T b;
