@@ -245,6 +245,13 @@ __device__ __forceinline__ F2 ff_rcp(F2 a)
     return fast_two_sum(y, __fadd_rn(t.h, t.l));
 }
 
+// The per-bond outputs of the pair passes that the gather reads (dU_i/dr_ij and r_ij): the
+// fp64 path stores them as float pairs (ff_pack of split_d, integer instructions) and its
+// gather sums them in float-pair arithmetic; the fp32 path stores floats.  split_d turns inf
+// and NaN into finite values, so an fp64 writer checks finiteness itself before storing.
+__device__ __forceinline__ double bond_out(double x) { return ff_pack(split_d(x)); }
+__device__ __forceinline__ float bond_out(float x) { return x; }
+
 // x = x1 + x2 + x3 exactly, three floats (x1: 24 leading bits, x2: the next 23, x3: the last
 // 6), for 2^-74 <= |x| < 2^128 (every part then a normal float or zero); the callers pass
 // mantissas in [1, 4).

@@ -214,9 +214,9 @@ __device__ __forceinline__ int collect_bonds(const PairArgs<T> &a, int64_t i, co
             if (na < CAP) {
                 S.set(fx, na, tx); S.set(fy, na, ty); S.set(fz, na, tz); S.set(fr2, na, r2);
                 if (MULTI) S.set(ftype, na, T(tj));
-                a.r[(int64_t)(0 * S_ + na) * N + i] = tx;
-                a.r[(int64_t)(1 * S_ + na) * N + i] = ty;
-                a.r[(int64_t)(2 * S_ + na) * N + i] = tz;
+                a.r[(int64_t)(0 * S_ + na) * N + i] = bond_out(tx);
+                a.r[(int64_t)(1 * S_ + na) * N + i] = bond_out(ty);
+                a.r[(int64_t)(2 * S_ + na) * N + i] = bond_out(tz);
             }
             mask |= 1u << m;
             ++na;
@@ -464,8 +464,8 @@ __device__ __forceinline__ void tersoff_angular_ff(const PairArgs<double> &a, co
             vz = ff_fma(qj, ff_unpack(S(TF_UZ, k)), vz);
         }
         const F2 ujx = ff_unpack(S(TF_UX, j)), ujy = ff_unpack(S(TF_UY, j)), ujz = ff_unpack(S(TF_UZ, j));
-        a.d[(int64_t)j * a.N + i] = Vec4<double>{ff_to_d(ff_fma(Aj, ujx, vx)), ff_to_d(ff_fma(Aj, ujy, vy)),
-                                                 ff_to_d(ff_fma(Aj, ujz, vz)), 0.0};
+        a.d[(int64_t)j * a.N + i] = Vec4<double>{ff_pack(ff_fma(Aj, ujx, vx)), ff_pack(ff_fma(Aj, ujy, vy)),
+                                                 ff_pack(ff_fma(Aj, ujz, vz)), 0.0};   // float pairs, as bond_out
     }
 }
 
@@ -737,7 +737,8 @@ __device__ __forceinline__ void sw_terms(const PairArgs<T> &a, const SWC<T> &p, 
             S(SW_DY, k) = fma(qk, ujy, fma(ak, uky, S(SW_DY, k)));
             S(SW_DZ, k) = fma(qk, ujz, fma(ak, ukz, S(SW_DZ, k)));
         }
-        a.d[(int64_t)j * N + i] = Vec4<T>{djx, djy, djz, T(0)};
+        if (sizeof(T) == 8 && !(finite_bits(djx) && finite_bits(djy) && finite_bits(djz))) pair_fail(a, i, MD_ERR_NAN);
+        a.d[(int64_t)j * N + i] = Vec4<T>{bond_out(djx), bond_out(djy), bond_out(djz), T(0)};
     }
     a.mask[i] = mask;
     a.u[i] = to_d(ui);
@@ -843,9 +844,9 @@ __device__ __forceinline__ void sw_atom_warp(const PairArgs<T> &a, const SWC<T> 
     T ui = T(0), dx = T(0), dy = T(0), dz = T(0);
     SWBond<T> b{};
     if (mine) {
-        a.r[(int64_t)(0 * S_ + k) * N + i] = tx;
-        a.r[(int64_t)(1 * S_ + k) * N + i] = ty;
-        a.r[(int64_t)(2 * S_ + k) * N + i] = tz;
+        a.r[(int64_t)(0 * S_ + k) * N + i] = bond_out(tx);
+        a.r[(int64_t)(1 * S_ + k) * N + i] = bond_out(ty);
+        a.r[(int64_t)(2 * S_ + k) * N + i] = bond_out(tz);
         b = sw_bond(p, r2, tx, ty, tz);
         sh[0][k] = b.ux; sh[1][k] = b.uy; sh[2][k] = b.uz; sh[3][k] = b.E;
         ui = b.u2;
@@ -869,7 +870,8 @@ __device__ __forceinline__ void sw_atom_warp(const PairArgs<T> &a, const SWC<T> 
             dy = fma(q, umy, fma(ac, b.uy, dy));
             dz = fma(q, umz, fma(ac, b.uz, dz));
         }
-        a.d[(int64_t)k * N + i] = Vec4<T>{dx, dy, dz, T(0)};
+        if (sizeof(T) == 8 && !(finite_bits(dx) && finite_bits(dy) && finite_bits(dz))) pair_fail(a, i, MD_ERR_NAN);
+        a.d[(int64_t)k * N + i] = Vec4<T>{bond_out(dx), bond_out(dy), bond_out(dz), T(0)};
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) ui += __shfl_xor_sync(0xffffffffu, ui, o);
@@ -1121,6 +1123,9 @@ __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, i
         T wd0 = 0, wd1 = 0, wd2 = 0;
 #pragma unroll
         for (int c = 0; c < 9; ++c) { w[c] = 0; mj[c] = 0; }
+        // fp64: the stored d and r are float pairs (bond_out), summed as float pairs
+        constexpr bool FFG = sizeof(T) == 8;
+        F2 ff[3] = {}, fw[9] = {}, fwd[3] = {};
         int k = 0;
         // each bond's list entry and reverse slot are loaded one bond ahead, while the
         // previous bond's loads through atom j are in flight
@@ -1141,7 +1146,25 @@ __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, i
             }
             const uint32_t maskj = a.mask[j];
             const int kr = __popc(maskj & ((1u << mr) - 1u));
-            if (kr < MAXA) {
+            if (FFG && kr < MAXA) {
+                const Vec4<T> dv = a.d[(int64_t)k * N + i], ev = a.d[(int64_t)kr * N + j];
+                const F2 r[3] = {ff_unpack(a.r[(int64_t)(0 * MAXA + k) * N + i]),
+                                 ff_unpack(a.r[(int64_t)(1 * MAXA + k) * N + i]),
+                                 ff_unpack(a.r[(int64_t)(2 * MAXA + k) * N + i])};
+                const F2 g[3] = {ff_add(ff_unpack(dv.x), ff_neg(ff_unpack(ev.x))),
+                                 ff_add(ff_unpack(dv.y), ff_neg(ff_unpack(ev.y))),
+                                 ff_add(ff_unpack(dv.z), ff_neg(ff_unpack(ev.z)))};   // F_ij = d_ij - d_ji
+#pragma unroll
+                for (int c = 0; c < 3; ++c) ff[c] = ff_add(ff[c], g[c]);
+                if (FULL) {
+#pragma unroll
+                    for (int c = 0; c < 9; ++c) fw[c] = ff_fma(r[c / 3], g[c % 3], fw[c]);
+                }
+                if (WDIAG) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) fwd[c] = ff_fma(r[c], g[c], fwd[c]);
+                }
+            } else if (kr < MAXA) {
                 const Vec4<T> dv = a.d[(int64_t)k * N + i], ev = a.d[(int64_t)kr * N + j];
                 const T dx = dv.x, dy = dv.y, dz = dv.z, ex = ev.x, ey = ev.y, ez = ev.z;
                 const T rx = a.r[(int64_t)(0 * MAXA + k) * N + i], ry = a.r[(int64_t)(1 * MAXA + k) * N + i],
@@ -1162,7 +1185,12 @@ __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, i
             }
             ++k;
         }
-        const double F[3] = {to_d(f0), to_d(f1), to_d(f2)};
+        const double F[3] = {FFG ? ff_to_d(ff[0]) : to_d(f0), FFG ? ff_to_d(ff[1]) : to_d(f1),
+                             FFG ? ff_to_d(ff[2]) : to_d(f2)};
+        // finiteness of the sums, tested before a conversion to double (f2d_int gives inf and
+        // NaN finite values)
+        const bool f_fin = FFG ? finite_bits(ff[0].h) && finite_bits(ff[1].h) && finite_bits(ff[2].h)
+                               : finite_bits(f0) && finite_bits(f1) && finite_bits(f2);
         a.force[i] = F[0];
         a.force[N + i] = F[1];
         a.force[2 * N + i] = F[2];
@@ -1200,22 +1228,24 @@ __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, i
         }
         // a non-finite force or velocity (after the kick; without one, as given) stops the
         // system in a pool and fails the call for a single system
-        if (!(finite_bits(f0) && finite_bits(f1) && finite_bits(f2) && finite_bits(v[0]) && finite_bits(v[1]) &&
-              finite_bits(v[2]))) {
+        if (!(f_fin && finite_bits(v[0]) && finite_bits(v[1]) && finite_bits(v[2]))) {
             if (BATCH) fail_system(a.sys[sid], MD_ERR_NAN);
             else a.flags->nonfinite = 1;
         }
         // J_i (Eq. 30) with v_i after the half-kick, and K_i = m v^2 / 2, in T (the fp32
         // per-atom value of the mixed path feeds an fp64 total).  fp64: a second walk over
-        // the bonds, J_i = sum_j r_ij (d_ji . v_i), 6 FMAs per bond (its loads hit the cache;
-        // the fp64 pipe is the bound); fp32: J_i = M_i . v_i.
+        // the bonds, J_i = sum_j r_ij (d_ji . v_i), six float-pair FMAs per bond (its loads
+        // hit the cache); fp32: J_i = M_i . v_i.
         const T vx = to_t<T>(v[0]), vy = to_t<T>(v[1]), vz = to_t<T>(v[2]);
         T J0 = T(0), J1 = T(0), J2 = T(0);
+        F2 fj[3] = {};
         if (!JPASS) {
             J0 = mj[0] * vx + mj[1] * vy + mj[2] * vz;
             J1 = mj[3] * vx + mj[4] * vy + mj[5] * vz;
             J2 = mj[6] * vx + mj[7] * vy + mj[8] * vz;
         } else {
+            // JPASS is the fp64 path: d and r are float pairs
+            const F2 vf[3] = {split_d(v[0]), split_d(v[1]), split_d(v[2])};
             uint32_t m2 = a.mask[i];
             int k2 = 0;
             while (m2 != 0u && k2 < MAXA) {
@@ -1226,33 +1256,35 @@ __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, i
                 const int kr = __popc(a.mask[j] & ((1u << mr) - 1u));
                 if (kr < MAXA) {
                     const Vec4<T> ev = a.d[(int64_t)kr * N + j];
-                    const T ex = ev.x, ey = ev.y, ez = ev.z;
-                    const T rx = a.r[(int64_t)(0 * MAXA + k2) * N + i], ry = a.r[(int64_t)(1 * MAXA + k2) * N + i],
-                            rz = a.r[(int64_t)(2 * MAXA + k2) * N + i];
-                    const T dv = ex * vx + ey * vy + ez * vz;
-                    J0 += rx * dv; J1 += ry * dv; J2 += rz * dv;
+                    F2 dv = ff_mul(ff_unpack(ev.x), vf[0]);
+                    dv = ff_fma(ff_unpack(ev.y), vf[1], dv);
+                    dv = ff_fma(ff_unpack(ev.z), vf[2], dv);
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) fj[c] = ff_fma(ff_unpack(a.r[(int64_t)(c * MAXA + k2) * N + i]), dv, fj[c]);
                 }
                 ++k2;
             }
         }
         const T hm = a.hm[t];
         const T ke = hm * (vx * vx + vy * vy + vz * vz);
+        // -1/2 of a float pair: both parts scaled exactly, one conversion
+        auto half_neg = [](F2 x) { return ff_to_d(F2{-0.5f * x.h, -0.5f * x.l}); };
         vals[0] = a.u[i];
         vals[1] = to_d(ke);
-        vals[2] = to_d(J0);
-        vals[3] = to_d(J1);
-        vals[4] = to_d(J2);
+        vals[2] = JPASS ? ff_to_d(fj[0]) : to_d(J0);
+        vals[3] = JPASS ? ff_to_d(fj[1]) : to_d(J1);
+        vals[4] = JPASS ? ff_to_d(fj[2]) : to_d(J2);
         if (WDIAG) {
             vals[5] = to_d(hm * vx * vx);
             vals[6] = to_d(hm * vy * vy);
             vals[7] = to_d(hm * vz * vz);
-            vals[8] = -0.5 * to_d(wd0);
-            vals[9] = -0.5 * to_d(wd1);
-            vals[10] = -0.5 * to_d(wd2);
+            vals[8] = FFG ? half_neg(fwd[0]) : -0.5 * to_d(wd0);
+            vals[9] = FFG ? half_neg(fwd[1]) : -0.5 * to_d(wd1);
+            vals[10] = FFG ? half_neg(fwd[2]) : -0.5 * to_d(wd2);
         }
         if (FULL) {
 #pragma unroll
-            for (int c = 0; c < 9; ++c) vals[5 + c] = -0.5 * to_d(w[c]);
+            for (int c = 0; c < 9; ++c) vals[5 + c] = FFG ? half_neg(fw[c]) : -0.5 * to_d(w[c]);
             if (a.w_out) {
 #pragma unroll
                 for (int c = 0; c < 9; ++c) a.w_out[c * N + i] = vals[5 + c];
