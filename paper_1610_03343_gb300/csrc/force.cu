@@ -694,6 +694,51 @@ __device__ __forceinline__ SWBond<T> sw_bond(const SWC<T> &p, T r2, T tx, T ty, 
     return b;
 }
 
+// fp64 pass, three-body part in float-pair arithmetic: every term of phi3 and of its
+// derivative carries the factor t = cos + 1/3 (which vanishes at the tetrahedral angle) or
+// t^2, so an absolute error e in cos is an absolute error of about 2 lambda eps E E' e /r in
+// dU_i/dr_ij -- no cancellation amplifies it -- while the two-body part, whose two terms
+// cancel at the equilibrium bond length, stays fp64.  Staged fields and the scattered
+// dU/dr accumulators are float pairs; dU_i/dr_ij is stored as float pairs (bond_out).
+template <int CAP, int BLOCK>
+__device__ __forceinline__ void sw_three_body_ff(const PairArgs<double> &a, const SWC<double> &p,
+                                                 const Stage<double, CAP, BLOCK> &S, int na, int64_t i,
+                                                 double &ui)
+{
+    const F2 third = split_d(1.0 / 3.0), lameps = split_d(p.lameps);
+    F2 u3{0.f, 0.f};
+    for (int j = 0; j < na; ++j) {
+        const F2 ujx = ff_unpack(S(SW_UX, j)), ujy = ff_unpack(S(SW_UY, j)), ujz = ff_unpack(S(SW_UZ, j));
+        const F2 irj = ff_unpack(S(SW_IR, j)), Ej = ff_unpack(S(SW_E, j)), dEj = ff_unpack(S(SW_DE, j));
+        F2 djx = ff_unpack(S(SW_DX, j)), djy = ff_unpack(S(SW_DY, j)), djz = ff_unpack(S(SW_DZ, j));
+        for (int k = j + 1; k < na; ++k) {
+            const F2 ukx = ff_unpack(S(SW_UX, k)), uky = ff_unpack(S(SW_UY, k)), ukz = ff_unpack(S(SW_UZ, k));
+            const F2 irk = ff_unpack(S(SW_IR, k)), Ek = ff_unpack(S(SW_E, k)), dEk = ff_unpack(S(SW_DE, k));
+            F2 cs = ff_mul(ujx, ukx);
+            cs = ff_fma(ujy, uky, cs);
+            cs = ff_fma(ujz, ukz, cs);
+            const F2 t = ff_add(cs, third);
+            const F2 EE = ff_mul(Ej, Ek);
+            const F2 lt = ff_mul(lameps, t), lt2 = ff_mul(lt, t);
+            u3 = ff_fma(lt2, EE, u3);
+            F2 c1 = ff_mul(lt, EE);
+            c1 = F2{2.f * c1.h, 2.f * c1.l};
+            const F2 cj = ff_mul(ff_mul(lt2, dEj), Ek), ck = ff_mul(ff_mul(lt2, Ej), dEk);
+            const F2 qj = ff_mul(c1, irj), qk = ff_mul(c1, irk);
+            // d_j += qj (u_k - cos u_j) + cj u_j, written as qj u_k + (cj - qj cos) u_j
+            const F2 aj = ff_fma(ff_neg(qj), cs, cj), ak = ff_fma(ff_neg(qk), cs, ck);
+            djx = ff_fma(qj, ukx, ff_fma(aj, ujx, djx));
+            djy = ff_fma(qj, uky, ff_fma(aj, ujy, djy));
+            djz = ff_fma(qj, ukz, ff_fma(aj, ujz, djz));
+            S(SW_DX, k) = ff_pack(ff_fma(qk, ujx, ff_fma(ak, ukx, ff_unpack(S(SW_DX, k)))));
+            S(SW_DY, k) = ff_pack(ff_fma(qk, ujy, ff_fma(ak, uky, ff_unpack(S(SW_DY, k)))));
+            S(SW_DZ, k) = ff_pack(ff_fma(qk, ujz, ff_fma(ak, ukz, ff_unpack(S(SW_DZ, k)))));
+        }
+        a.d[(int64_t)j * a.N + i] = Vec4<double>{ff_pack(djx), ff_pack(djy), ff_pack(djz), 0.0};
+    }
+    ui += ff_to_d(u3);
+}
+
 // SW terms of atom i from its na bonds staged in shared-memory slot `slot` (by
 // collect_bonds): two-body and vertex three-body terms, dU_i/dr_ij per bond, U_i.
 template <typename T, int CAP, int BLOCK>
@@ -704,47 +749,55 @@ __device__ __forceinline__ void sw_terms(const PairArgs<T> &a, const SWC<T> &p, 
     Stage<T, CAP, BLOCK> S{base, slot};
     T ui = T(0);
     for (int k = 0; k < na; ++k) {
-        const SWBond<T> b = sw_bond(p, S(SW_IR, k), S(SW_UX, k), S(SW_UY, k), S(SW_UZ, k));
-        S(SW_UX, k) = b.ux; S(SW_UY, k) = b.uy; S(SW_UZ, k) = b.uz; S(SW_IR, k) = b.ir;
-        S(SW_E, k) = b.E;
-        S(SW_DE, k) = b.dE;
-        ui += b.u2;
-        S(SW_DX, k) = b.dx;
-        S(SW_DY, k) = b.dy;
-        S(SW_DZ, k) = b.dz;
-    }
-    // phi3 = lambda eps (cos + 1/3)^2 E(r_ij) E(r_ik), vertex i, each unordered pair once
-    for (int j = 0; j < na; ++j) {
-        const T ujx = S(SW_UX, j), ujy = S(SW_UY, j), ujz = S(SW_UZ, j);
-        const T irj = S(SW_IR, j), Ej = S(SW_E, j), dEj = S(SW_DE, j);
-        T djx = S(SW_DX, j), djy = S(SW_DY, j), djz = S(SW_DZ, j);
-        for (int k = j + 1; k < na; ++k) {
-            const T ukx = S(SW_UX, k), uky = S(SW_UY, k), ukz = S(SW_UZ, k);
-            const T irk = S(SW_IR, k), Ek = S(SW_E, k), dEk = S(SW_DE, k);
-            const T cs = ujx * ukx + ujy * uky + ujz * ukz;
-            const T t = cs + T(1.0 / 3.0);
-            const T EE = Ej * Ek;
-            ui += p.lameps * t * t * EE;
-            const T c1 = T(2) * p.lameps * t * EE;
-            const T cj = p.lameps * t * t * dEj * Ek, ck = p.lameps * t * t * Ej * dEk;
-            const T qj = c1 * irj, qk = c1 * irk;
-            // d_j += qj (u_k - cos u_j) + cj u_j, written as qj u_k + (cj - qj cos) u_j
-            const T aj = fma(-qj, cs, cj), ak = fma(-qk, cs, ck);
-            djx = fma(qj, ukx, fma(aj, ujx, djx));
-            djy = fma(qj, uky, fma(aj, ujy, djy));
-            djz = fma(qj, ukz, fma(aj, ujz, djz));
-            S(SW_DX, k) = fma(qk, ujx, fma(ak, ukx, S(SW_DX, k)));
-            S(SW_DY, k) = fma(qk, ujy, fma(ak, uky, S(SW_DY, k)));
-            S(SW_DZ, k) = fma(qk, ujz, fma(ak, ukz, S(SW_DZ, k)));
+        if constexpr (sizeof(T) == 8) {
+            // the float-pair staging turns inf and NaN into finite values: a bond shorter
+            // than 1e-15 A (coincident atoms, 1/r = +inf) is reported here instead of through F
+            if (!(S(SW_IR, k) >= T(1e-30))) pair_fail(a, i, MD_ERR_NAN);
         }
-        if (sizeof(T) == 8 && !(finite_bits(djx) && finite_bits(djy) && finite_bits(djz))) pair_fail(a, i, MD_ERR_NAN);
-        a.d[(int64_t)j * N + i] = Vec4<T>{bond_out(djx), bond_out(djy), bond_out(djz), T(0)};
+        const SWBond<T> b = sw_bond(p, S(SW_IR, k), S(SW_UX, k), S(SW_UY, k), S(SW_UZ, k));
+        S(SW_UX, k) = bond_out(b.ux); S(SW_UY, k) = bond_out(b.uy); S(SW_UZ, k) = bond_out(b.uz);
+        S(SW_IR, k) = bond_out(b.ir);
+        S(SW_E, k) = bond_out(b.E);
+        S(SW_DE, k) = bond_out(b.dE);
+        ui += b.u2;
+        S(SW_DX, k) = bond_out(b.dx);
+        S(SW_DY, k) = bond_out(b.dy);
+        S(SW_DZ, k) = bond_out(b.dz);
+    }
+    if constexpr (sizeof(T) == 8) {
+        sw_three_body_ff<CAP, BLOCK>(a, p, S, na, i, ui);
+    } else {
+        // phi3 = lambda eps (cos + 1/3)^2 E(r_ij) E(r_ik), vertex i, each unordered pair once
+        for (int j = 0; j < na; ++j) {
+            const T ujx = S(SW_UX, j), ujy = S(SW_UY, j), ujz = S(SW_UZ, j);
+            const T irj = S(SW_IR, j), Ej = S(SW_E, j), dEj = S(SW_DE, j);
+            T djx = S(SW_DX, j), djy = S(SW_DY, j), djz = S(SW_DZ, j);
+            for (int k = j + 1; k < na; ++k) {
+                const T ukx = S(SW_UX, k), uky = S(SW_UY, k), ukz = S(SW_UZ, k);
+                const T irk = S(SW_IR, k), Ek = S(SW_E, k), dEk = S(SW_DE, k);
+                const T cs = ujx * ukx + ujy * uky + ujz * ukz;
+                const T t = cs + T(1.0 / 3.0);
+                const T EE = Ej * Ek;
+                ui += p.lameps * t * t * EE;
+                const T c1 = T(2) * p.lameps * t * EE;
+                const T cj = p.lameps * t * t * dEj * Ek, ck = p.lameps * t * t * Ej * dEk;
+                const T qj = c1 * irj, qk = c1 * irk;
+                // d_j += qj (u_k - cos u_j) + cj u_j, written as qj u_k + (cj - qj cos) u_j
+                const T aj = fma(-qj, cs, cj), ak = fma(-qk, cs, ck);
+                djx = fma(qj, ukx, fma(aj, ujx, djx));
+                djy = fma(qj, uky, fma(aj, ujy, djy));
+                djz = fma(qj, ukz, fma(aj, ujz, djz));
+                S(SW_DX, k) = fma(qk, ujx, fma(ak, ukx, S(SW_DX, k)));
+                S(SW_DY, k) = fma(qk, ujy, fma(ak, uky, S(SW_DY, k)));
+                S(SW_DZ, k) = fma(qk, ujz, fma(ak, ukz, S(SW_DZ, k)));
+            }
+            a.d[(int64_t)j * N + i] = Vec4<T>{djx, djy, djz, T(0)};
+        }
     }
     a.mask[i] = mask;
     a.u[i] = to_d(ui);
 }
 
-// Pair pass for one atom (SW) in its own thread's slot.
 template <typename T, int CAP, int BLOCK, bool FULL_CAP>
 __device__ __forceinline__ void sw_atom(const PairArgs<T> &a, const SWC<T> &p, const Box &box, T *base, int64_t i)
 {
