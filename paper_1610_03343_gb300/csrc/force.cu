@@ -694,6 +694,44 @@ __device__ __forceinline__ SWBond<T> sw_bond(const SWC<T> &p, T r2, T tx, T ty, 
     return b;
 }
 
+// fp64 pass, per-bond SW terms: phi2 and its derivative in fp64 (their two terms cancel at
+// the equilibrium bond length), everything the float-pair three-body loop reads -- u, E and
+// dE/dr -- and the two-body dU/dr = 1/2 phi2' u as float pairs.
+struct SWBondFF {
+    F2 ux, uy, uz, ir, E, dE, dx, dy, dz;
+    double u2;
+};
+__device__ __forceinline__ SWBondFF sw_bond_ff(const SWC<double> &p, double r2, double tx, double ty, double tz)
+{
+    SWBondFF b;
+    const double ir = M<double>::rsqrt_(r2);
+    const double r = r2 * ir;
+    b.ir = split_d(ir);
+    b.ux = ff_mul(split_d(tx), b.ir);
+    b.uy = ff_mul(split_d(ty), b.ir);
+    b.uz = ff_mul(split_d(tz), b.ir);
+    const double irc = M<double>::rcp_(r - p.rc);   // 1/(r - a sigma) < 0
+    const double e2 = M<double>::sexp_(p.sig * irc);
+    b.E = split_d(M<double>::sexp_(p.gamsig * irc));
+    const F2 ircf = split_d(irc);
+    b.dE = ff_mul(ff_mul(split_d(-p.gamsig), ff_mul(ircf, ircf)), b.E);
+    // phi2 = A eps [B (sigma/r)^p - (sigma/r)^q] exp(sigma/(r - a sigma))
+    const double sr = p.sig * ir;
+    double sp, sq;
+    if (p.p_int >= 0) sp = ipow(sr, p.p_int); else sp = M<double>::pow_(sr, p.p);
+    if (p.q_int >= 0) sq = ipow(sr, p.q_int); else sq = M<double>::pow_(sr, p.q);
+    const double poly = p.B * sp - sq;
+    const double dpoly = (-p.p * p.B * sp + p.q * sq) * ir;
+    b.u2 = 0.5 * p.Aeps * poly * e2;
+    const double dphi = p.Aeps * (dpoly * e2 - poly * p.sig * irc * irc * e2);
+    F2 h = split_d(dphi);
+    h = F2{0.5f * h.h, 0.5f * h.l};
+    b.dx = ff_mul(h, b.ux);
+    b.dy = ff_mul(h, b.uy);
+    b.dz = ff_mul(h, b.uz);
+    return b;
+}
+
 // fp64 pass, three-body part in float-pair arithmetic: every term of phi3 and of its
 // derivative carries the factor t = cos + 1/3 (which vanishes at the tetrahedral angle) or
 // t^2, so an absolute error e in cos is an absolute error of about 2 lambda eps E E' e /r in
@@ -754,15 +792,26 @@ __device__ __forceinline__ void sw_terms(const PairArgs<T> &a, const SWC<T> &p, 
             // than 1e-15 A (coincident atoms, 1/r = +inf) is reported here instead of through F
             if (!(S(SW_IR, k) >= T(1e-30))) pair_fail(a, i, MD_ERR_NAN);
         }
-        const SWBond<T> b = sw_bond(p, S(SW_IR, k), S(SW_UX, k), S(SW_UY, k), S(SW_UZ, k));
-        S(SW_UX, k) = bond_out(b.ux); S(SW_UY, k) = bond_out(b.uy); S(SW_UZ, k) = bond_out(b.uz);
-        S(SW_IR, k) = bond_out(b.ir);
-        S(SW_E, k) = bond_out(b.E);
-        S(SW_DE, k) = bond_out(b.dE);
-        ui += b.u2;
-        S(SW_DX, k) = bond_out(b.dx);
-        S(SW_DY, k) = bond_out(b.dy);
-        S(SW_DZ, k) = bond_out(b.dz);
+        if constexpr (sizeof(T) == 8) {
+            const SWBondFF b = sw_bond_ff(p, S(SW_IR, k), S(SW_UX, k), S(SW_UY, k), S(SW_UZ, k));
+            S(SW_UX, k) = ff_pack(b.ux); S(SW_UY, k) = ff_pack(b.uy); S(SW_UZ, k) = ff_pack(b.uz);
+            S(SW_IR, k) = ff_pack(b.ir);
+            S(SW_E, k) = ff_pack(b.E);
+            S(SW_DE, k) = ff_pack(b.dE);
+            ui += b.u2;
+            S(SW_DX, k) = ff_pack(b.dx);
+            S(SW_DY, k) = ff_pack(b.dy);
+            S(SW_DZ, k) = ff_pack(b.dz);
+        } else {
+            const SWBond<T> b = sw_bond(p, S(SW_IR, k), S(SW_UX, k), S(SW_UY, k), S(SW_UZ, k));
+            S(SW_UX, k) = b.ux; S(SW_UY, k) = b.uy; S(SW_UZ, k) = b.uz; S(SW_IR, k) = b.ir;
+            S(SW_E, k) = b.E;
+            S(SW_DE, k) = b.dE;
+            ui += b.u2;
+            S(SW_DX, k) = b.dx;
+            S(SW_DY, k) = b.dy;
+            S(SW_DZ, k) = b.dz;
+        }
     }
     if constexpr (sizeof(T) == 8) {
         sw_three_body_ff<CAP, BLOCK>(a, p, S, na, i, ui);
