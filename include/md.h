@@ -525,7 +525,12 @@ md_status md_hcacf(const double *j, int64_t n_rows, int64_t row_stride, int64_t 
  * zero-length bond between coincident atoms makes the forces non-finite, MD_ERR_NAN), and the
  * exponential (fn = 4) and logarithm (fn = 5) that the pair passes call: the same tables and
  * bounds, the range reduction and final multiply-add in fp64 and the correction polynomial
- * as pairs of floats on the fp32 pipe (three fp64 instructions each).
+ * as pairs of floats on the fp32 pipe (three fp64 instructions each); the reciprocal (fn = 6)
+ * and reciprocal square root (fn = 7) whose last step runs as float pairs (two fp64
+ * instructions each); and the exponential (fn = 8; error about 2^-47 e^x + 2^-126 for
+ * -80 <= x <= 80, x clamped to that range) and logarithm (fn = 9; absolute error about
+ * 2^-47 (1 + |log x|) for 2^-78 <= x < 2^127) of the bond-order chain, which run on the
+ * fp32 pipe alone: x is split into a float pair and the float-pair result summed back.
  * x, y: n host doubles.  Returns 0, -1 for bad arguments, -5 on a CUDA error.
  * Allocates and frees its own device scratch. */
 int md_fastmath_eval(int fn, int64_t n, const double *x, double *y);

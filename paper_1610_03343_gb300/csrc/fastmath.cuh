@@ -245,6 +245,71 @@ __device__ __forceinline__ F2 ff_rcp(F2 a)
     return fast_two_sum(y, __fadd_rn(t.h, t.l));
 }
 
+// e^y of a float pair on the fp32 pipe alone, error about 2^-47 e^y plus, where the result's
+// low float is subnormal, an absolute error below 2^-126 (y.h clamped to [-80, 80]): y = k ln2/256 + r with k = round(y.h 256/ln2)
+// (as in exp_tab), r = y - k C1 - k C2 - k C3 (ln2/256 = C1 + C2 + C3: C1 has 9 bits, so
+// k C1 is exact for |k| < 2^15; k C2 by two-product), |r| <= 0.55 ln2/256;
+// e^r - 1 = r + r^2/2 (float pair) + r^3/6 + r^4/24 + r^5/120 (one float: below 2^-31);
+// e^y = 2^(k >> 8) T_j (1 + p), T_j = 2^(j/256) from the fp64 table, split.
+__device__ __forceinline__ F2 exp_f2(F2 y)
+{
+    const bool lo = y.h < -80.f, hi = y.h > 80.f;
+    const float yh = lo ? -80.f : (hi ? 80.f : y.h), yl = (lo || hi) ? 0.f : y.l;
+    const float tf = __fmaf_rn(yh, kInvLn2o256F, kShiftF);
+    const int k = __float_as_int(tf) - kShiftBits;
+    const float kf = __fsub_rn(tf, kShiftF);                          // k exactly
+    const float a = __fsub_rn(yh, __fmul_rn(kf, kLn2o256F3[0]));     // exact (Sterbenz)
+    const F2 p2 = two_prod(kf, kLn2o256F3[1]);
+    // r = a + yl - k C2 - k C3: the two larger additions exact, the small rest in one float
+    const F2 s1 = two_sum(a, yl);
+    const F2 t = two_sum(s1.h, -p2.h);
+    const float rl = __fsub_rn(__fsub_rn(__fadd_rn(t.l, s1.l), p2.l), __fmul_rn(kf, kLn2o256F3[2]));
+    const F2 r = fast_two_sum(t.h, rl);
+    F2 s = two_prod(r.h, r.h);                                         // r^2
+    s.l = __fmaf_rn(2.f * r.h, r.l, s.l);
+    const float c3 = __fmul_rn(__fmul_rn(s.h, r.h),
+                               __fmaf_rn(r.h, __fmaf_rn(r.h, 1.f / 120.f, 1.f / 24.f), kSixthF[0]));
+    F2 P = fast_two_sum(r.h, 0.5f * s.h);
+    P = fast_two_sum(P.h, __fadd_rn(__fadd_rn(P.l, r.l), __fmaf_rn(0.5f, s.l, c3)));
+    const F2 T = split_d(__ldg(&kExp2Tab[k & 255]));
+    const F2 e = ff_fma(T, P, T);
+    const float sc = __int_as_float((127 + (k >> 8)) << 23);          // 2^(k >> 8), |k >> 8| <= 116
+    return F2{__fmul_rn(e.h, sc), __fmul_rn(e.l, sc)};
+}
+
+// log z of a positive float pair on the fp32 pipe alone, absolute error about
+// 2^-47 (1 + |log z|), for z.h a normal float below 2^127 (with z.l normal or zero; below
+// z ~ 2^-102 the low float is subnormal and z itself holds fewer bits): z = 2^e m, m in [1, 2) (both parts scaled
+// exactly), j = the top eight bits of m's fraction, r = m i_j - 1 with i_j = RN_float(1/c_j)
+// (|r| < 2^-8.9), log z = e ln2 - log(i_j) + log(1 + r),
+// log(1 + r) = r - r^2/2 (float pair) + r^3/3 - r^4/4 + r^5/5 (one float: below 2^-27);
+// e ln2 with ln2 = H1 + H2 + H3 (H1 has 16 bits: e H1 exact; e H2 by two-product).
+__device__ __forceinline__ F2 log_f2(F2 z)
+{
+    const unsigned bits = __float_as_uint(z.h);
+    const int e = (int)(bits >> 23) - 127;
+    const int j = (int)((bits >> 15) & 255u);
+    const float mh = __uint_as_float((bits & 0x007fffffu) | 0x3f800000u);
+    const float ml = __fmul_rn(z.l, __uint_as_float((unsigned)(127 - e) << 23));
+    const float ic = __ldg(&kLogInvTabF[j]);
+    const F2 pr = two_prod(mh, ic);
+    // r = (pr.h - 1) + pr.l + ml ic, pr.h - 1 exact: the larger additions exact
+    const F2 q = two_prod(ml, ic);
+    const F2 u = two_sum(pr.l, q.h);
+    F2 r = two_sum(__fsub_rn(pr.h, 1.f), u.h);
+    r = fast_two_sum(r.h, __fadd_rn(r.l, __fadd_rn(u.l, q.l)));
+    F2 s = two_prod(r.h, r.h);
+    s.l = __fmaf_rn(2.f * r.h, r.l, s.l);
+    const float c3 = __fmul_rn(__fmul_rn(s.h, r.h), __fmaf_rn(r.h, __fmaf_rn(r.h, 0.2f, -0.25f), kThirdF[0]));
+    F2 L = fast_two_sum(r.h, -0.5f * s.h);
+    L = fast_two_sum(L.h, __fadd_rn(__fadd_rn(L.l, r.l), __fmaf_rn(-0.5f, s.l, c3)));
+    const float ef = (float)e;
+    const F2 e2 = two_prod(ef, kLn2F3[1]);
+    const F2 b = two_sum(__fmul_rn(ef, kLn2F3[0]), e2.h);
+    const F2 eln2 = fast_two_sum(b.h, __fadd_rn(b.l, __fmaf_rn(ef, kLn2F3[2], e2.l)));
+    return ff_add(ff_add(eln2, split_d(__ldg(&kLogTabF[j]))), L);
+}
+
 // The per-bond outputs of the pair passes that the gather reads (dU_i/dr_ij and r_ij): the
 // fp64 path stores them as float pairs (ff_pack of split_d, integer instructions) and its
 // gather sums them in float-pair arithmetic; the fp32 path stores floats.  split_d turns inf

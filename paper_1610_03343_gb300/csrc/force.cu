@@ -92,6 +92,7 @@ struct Stage {
 template <typename T>
 struct TersoffC {
     T A, B, lam, mu, n, c2, d2, c2d2, h, R, pi_SR, n_ln_beta, inv2n;   // n_ln_beta = n log(beta)
+    T beta;
     T rc2;   // S^2
     int beta_zero;
 };
@@ -101,7 +102,7 @@ TersoffC<T> tersoff_const(const TersoffP &p)
     TersoffC<T> c;
     c.A = T(p.A); c.B = T(p.B); c.lam = T(p.lam); c.mu = T(p.mu); c.n = T(p.n);
     c.c2 = T(p.c2); c.d2 = T(p.d2); c.c2d2 = T(p.c2d2); c.h = T(p.h); c.R = T(p.R);
-    c.pi_SR = T(p.pi_SR); c.n_ln_beta = T(p.n * p.ln_beta); c.inv2n = T(p.inv2n);
+    c.pi_SR = T(p.pi_SR); c.n_ln_beta = T(p.n * p.ln_beta); c.inv2n = T(p.inv2n); c.beta = T(p.beta);
     c.rc2 = T(p.S * p.S);
     c.beta_zero = p.beta_zero;
     return c;
@@ -336,23 +337,27 @@ __device__ __forceinline__ void tersoff_b(const TersoffC<T> &p, T zeta, T &b, T 
     db = T(-0.5) * b * x * M<T>::rcp_(zeta * (T(1) + x));
 }
 
-// fp64 pass: b as above (fp64-assisted exp and log: b multiplies f_A in the radial term
-// 1/2 ((f_C f_R)' - b (f_C f_A)'), whose two parts nearly cancel at equilibrium), and
-// P = -1/2 f_C f_A db/dzeta = cfa b x / (zeta (1 + x)) (cfa = f_C f_A / 4) as a float pair:
+// fp64 pass: b as above and P = -1/2 f_C f_A db/dzeta = cfa b x / (zeta (1 + x))
+// (cfa = f_C f_A / 4).  zeta arrives as a float pair from the float-pair zeta loop (relative
+// error about 2^-47, which alone puts a relative error of x/(2(1 + x)) 2^-47 < 2^-50 on b),
+// so x = (beta zeta)^n = exp(n log(beta zeta)) and log(1 + x) are formed as float pairs on
+// the fp32 pipe (exp_f2, log_f2: each adds an error of the same order to b); the last step,
+// b = exp(-log(1 + x)/(2n)), takes the fp64-assisted exp, since b multiplies f_A in the
+// radial term 1/2 ((f_C f_R)' - b (f_C f_A)'), whose two parts nearly cancel at equilibrium.
 // P only scales the angular terms, which the float-pair angular loop forms to 2^-47 anyway.
-// zeta (a float pair) counts as zero below the float normal range.
+// beta zeta below the float normal range (zeta < 1e-31: a bond within about 1e-18 A of the
+// cutoff) counts as zeta = 0.
 __device__ __forceinline__ double tersoff_b_ff(const TersoffC<double> &p, F2 zf, F2 cfa, F2 &P)
 {
-    const double zeta = ff_to_d(zf);
-    if (!positive_nonneg(zeta) || p.beta_zero) {
+    const F2 bz = ff_mul(split_d(p.beta), zf);
+    if (p.beta_zero || !(bz.h >= 1.17549435e-38f)) {
         P = F2{0.f, 0.f};
         return 1.0;
     }
-    const double x = exp_ff(fma(p.n, log_ff(zeta), p.n_ln_beta));   // (beta zeta)^n
-    const double b = exp_ff(-p.inv2n * log_ff(1.0 + x));
-    const F2 xf = split_d(x);
-    const F2 den = ff_mul(zf, ff_add(F2{1.f, 0.f}, xf));
-    P = ff_mul(ff_mul(ff_mul(cfa, split_d(b)), xf), ff_rcp(den));
+    const F2 x = exp_f2(ff_mul(split_d(p.n), log_f2(bz)));   // (beta zeta)^n
+    const F2 opx = ff_add(F2{1.f, 0.f}, x);
+    const double b = exp_ff(ff_to_d(ff_mul(split_d(-p.inv2n), log_f2(opx))));
+    P = ff_mul(ff_mul(ff_mul(cfa, split_d(b)), x), ff_rcp(ff_mul(zf, opx)));
     return b;
 }
 
@@ -1822,7 +1827,9 @@ __global__ void k_fastmath_eval(int fn, int64_t n, const double *x, double *y)
     case 4: y[i] = exp_ff(x[i]); break;
     case 5: y[i] = log_ff(x[i]); break;
     case 6: y[i] = rcp_ff(x[i]); break;
-    default: y[i] = rsqrt_ff(x[i]); break;
+    case 7: y[i] = rsqrt_ff(x[i]); break;
+    case 8: y[i] = ff_to_d(exp_f2(split_d(x[i]))); break;
+    default: y[i] = ff_to_d(log_f2(split_d(x[i]))); break;
     }
 }
 }  // namespace
@@ -1997,13 +2004,12 @@ int gather_blocks(int64_t N) { return N == 0 ? 1 : (int)blocks_for(N, kGatherBlo
 
 }  // namespace mdk
 
-// Diagnostics: the pair pass's table-driven fp64 exp (fn 0), log (fn 1) or Newton reciprocal
-// (fn 2) of n host values
-// on the current device (accuracy tests).  Returns 0, -1 for bad arguments, -5 on a CUDA
-// error.
+// Diagnostics: the pair passes' exp, log, reciprocal and reciprocal square root routines
+// (fn 0..9, as k_fastmath_eval lists them) on n host values, on the current device
+// (accuracy tests).  Returns 0, -1 for bad arguments, -5 on a CUDA error.
 extern "C" int md_fastmath_eval(int fn, int64_t n, const double *x, double *y)
 {
-    if (fn < 0 || fn > 7 || n < 0 || (n > 0 && (!x || !y))) return -1;
+    if (fn < 0 || fn > 9 || n < 0 || (n > 0 && (!x || !y))) return -1;
     if (n == 0) return 0;
     double *d = nullptr;
     if (cudaMalloc(&d, sizeof(double) * 2 * (size_t)n) != cudaSuccess) {

@@ -91,6 +91,21 @@ def main():
     lines.append("__device__ const double kLogTabF[256] = {")
     lines += [f"    {v}," for v in lgf]
     lines.append("};")
+    # all-fp32 routines (exp_f2, log_f2): ln2/256 and ln2 as three floats each, the head cut to
+    # few significant bits so that k * head is exact in fp32 (ln2/256: 9 bits, |k| < 2^15;
+    # ln2: 16 bits, |e| < 2^8), the middle rounded to float, the tail = the rest rounded
+    def f32(x: Decimal) -> float:
+        return struct.unpack("f", struct.pack("f", float(x)))[0]
+
+    def three(x: Decimal, head_bits: int):
+        m, e = math.frexp(float(x))
+        h = math.ldexp(math.floor(m * 2 ** head_bits) / 2 ** head_bits, e)
+        mid = f32(x - Decimal(h))
+        tail = f32(x - Decimal(h) - Decimal(mid))
+        return h, mid, tail
+    for name, val, bits, what in (("kLn2o256F3", l64, 9, "ln2/256"), ("kLn2F3", LN2, 16, "ln2")):
+        a, b, c = three(val, bits)
+        lines.append(f"constexpr float {name}[3] = {{{a.hex()}f, {b.hex()}f, {c.hex()}f}};   // {what}, head {bits} bits")
     lines += ["", "}  // namespace mdk", ""]
     with open(os.path.join(HERE, "fastmath_tables.cuh"), "w") as f:
         f.write("\n".join(lines))

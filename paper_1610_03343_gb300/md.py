@@ -339,8 +339,10 @@ def md_get_box(ctx, system=0) -> np.ndarray:
 
 def md_fastmath_eval(fn: int, x) -> np.ndarray:
     """The pair passes' fp64 routines evaluated on the GPU: all-fp64 exp (fn 0) and log
-    (fn 1), reciprocal (fn 2), reciprocal square root (fn 3), and the exp (fn 4) and log (fn 5)
-    whose correction polynomial runs as float pairs."""
+    (fn 1), reciprocal (fn 2), reciprocal square root (fn 3), the exp (fn 4) and log (fn 5)
+    whose correction polynomial runs as float pairs, the reciprocal (fn 6) and reciprocal
+    square root (fn 7) that finish in float pairs, and the all-fp32 float-pair exp (fn 8) and
+    log (fn 9) (input split to a float pair, result summed back to a double)."""
     lib = load()
     x = np.ascontiguousarray(x, dtype=np.float64)
     y = np.empty_like(x)

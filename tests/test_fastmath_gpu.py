@@ -4,7 +4,8 @@ table-driven log within an absolute 2e-16 (1 + |binary exponent|) -- both the al
 the form whose correction polynomial runs as float pairs on the fp32 pipe -- the reciprocal within 1 ulp
 (of the correctly rounded 1/x) for 1.2e-38 < |x| < 8.5e37 and the reciprocal square root
 within 1 ulp for 1.2e-38 < x < 3.4e38 (each an fp32 seed and one third-order step), including
-table and interval boundaries, powers of two, values next to 1 and the range ends."""
+table and interval boundaries, powers of two, values next to 1 and the range ends; and the
+all-fp32 float-pair exp and log of the bond-order chain."""
 import numpy as np
 import pytest
 
@@ -65,6 +66,53 @@ def test_log_absolute_error(md, fn):
     err = np.abs(y - ref)
     assert np.all(err <= bound), (x[np.argmax(err / bound)], (err / bound).max())
     assert y[-6] == 0.0 or abs(y[-6]) < 1e-17            # log(1) ~ 0
+
+
+def round_bits(x, bits=40):
+    """x rounded to `bits` significant bits: held exactly by a float pair (split_d keeps 47)."""
+    m, e = np.frexp(x)
+    return np.ldexp(np.round(m * 2.0 ** bits) / 2.0 ** bits, e)
+
+
+def test_float_pair_exp(md):
+    """exp_f2 (fn 8): relative error within 2^-45 for y in [-55, 80] (analysis: about 2^-47,
+    plus the low float of the result, up to 2^-24 of it, leaving the normal range -- which the
+    conversion back to a double flushes -- an absolute error below 2^-126: relative 2^-45 above
+    e^-55 ~ 2^-79)."""
+    rng = np.random.Generator(np.random.PCG64(5))
+    ln2_256 = np.log(2.0) / 256
+    x = round_bits(np.concatenate([
+        rng.uniform(-8.0, 2.0, 300000),                 # n log(beta zeta)
+        rng.uniform(-55.0, 80.0, 300000),
+        rng.uniform(-1e-3, 1e-3, 50000),
+        np.arange(-2000, 2000) * ln2_256 + ln2_256 / 2,  # reduction interval edges
+        [0.0, 1e-20, -1e-20, 1.0, -1.0, 80.0, -55.0],
+    ]))
+    y = md.md_fastmath_eval(8, x)
+    rel = np.abs(y - np.exp(x)) / np.exp(x)
+    assert rel.max() <= 2.0 ** -45, (x[np.argmax(rel)], rel.max())
+    lo = round_bits(rng.uniform(-80.0, -55.0, 20000))
+    assert np.abs(md.md_fastmath_eval(8, lo) - np.exp(lo)).max() <= 2.0 ** -125
+
+
+def test_float_pair_log(md):
+    """log_f2 (fn 9): absolute error within 2^-46 (1 + |log x|) (analysis: about
+    2^-47 (1 + |log x|)) for x from 2^-78 to 2^125 -- the range that the test's conversion of
+    a double to a float pair holds to 47 bits, and in which the low float stays normal."""
+    rng = np.random.Generator(np.random.PCG64(6))
+    x = round_bits(np.concatenate([
+        np.exp(rng.uniform(-30.0, 5.0, 300000)),          # beta zeta
+        1.0 + np.exp(rng.uniform(-30.0, 1.0, 300000)),    # 1 + (beta zeta)^n
+        np.exp(rng.uniform(-54.0, 86.0, 200000)),
+        2.0 ** np.arange(-78, 126, dtype=np.float64),
+        1.0 + np.arange(257) / 256.0,                     # table interval boundaries
+        [1.0, 1.0 + 2.0 ** -40, 1.0 - 2.0 ** -40],
+    ]))
+    y = md.md_fastmath_eval(9, x)
+    ref = np.log(x)
+    err = np.abs(y - ref)
+    bound = 2.0 ** -46 * (1.0 + np.abs(ref))
+    assert np.all(err <= bound), (x[np.argmax(err / bound)], (err / bound).max())
 
 
 def test_reciprocal_within_one_ulp(md):
