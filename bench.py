@@ -99,24 +99,28 @@ def gather_bytes_algorithmic(bonds: float, fused: bool = True, elem: int = 4) ->
     b = 4 + 5 * bonds + 6 * elem * bonds + 8 + 4 + 48 + 24
     return b + (72 if fused else 0)
 
-# FP64 flops of the fp64 pair pass, counted with ncu's instruction counters (DADD + DMUL +
-# 2 DFMA, which include the fp64 instruction sequences of the table-driven exp and log, the
-# Newton reciprocal and the square root), per in-cutoff bond and per ordered pair of bonds
-# (j, k != j) of one atom.  Tersoff: fit to the C sheet (3 bonds per atom, 551.449 flop/atom)
-# and Si diamond (4 bonds, 822.266 flop/atom).  SW: fit to the Si diamond lattice (4 bonds,
-# 12 ordered pairs: 620.215 flop/atom) and the same crystal after 100 fs at 300 K (5.0726
-# bonds, 21.5767 ordered pairs: 947.165 flop/atom; second-shell atoms at 3.84 A move
-# inside the 3.77 A cutoff).
-TERSOFF_FLOP_PER_BOND = 140.316
-TERSOFF_FLOP_PER_BOND_PAIR = 21.750
-SW_FLOP_PER_BOND = 79.267
-SW_FLOP_PER_BOND_PAIR = 25.262
-# DRAM bytes (read + write) of one fp64 pair pass (SW: the common-case and full-capacity
-# launches of one step at 300 K), from the ncu capture of the current kernels.
-PAIR_TRAFFIC_BYTES = {"tersoff_c_graphene_1M": 140.24e6, "tersoff_si_216k": 10.20e6, "sw_si_512k": 204.87e6}
-# DRAM bytes (read + write) of one mixed gather launch of the current kernel (ncu), by
-# workload; absent until captured
-GATHER_TRAFFIC_BYTES = {}
+# Instruction model of the fp64 pair pass, from ncu's instruction counters of the current
+# kernels (profiles/pair_tersoff_fp64_c_graphene_1M.md, profiles/pair_sw_fp64_si_512k.md):
+# per in-cutoff bond and per ordered pair of bonds (j, k != j) of one atom, solved from two
+# states each -- Tersoff: the C sheet (3 bonds, 6 ordered pairs) and Si diamond (4, 12);
+# SW: the Si lattice (4, 12) and the crystal after 100 fs at 300 K (5.1028, 21.8819; the
+# common-case and full-capacity launches together).
+#   FLOP: DADD + DMUL + 2 DFMA thread instructions (the fp64 arithmetic that is left: the
+#         bond geometry, the radial functions and the fp64 steps of exp, log, 1/r);
+#   FP64: fp64-pipe issue slots (smsp__inst_executed_pipe_fp64 x 32);
+#   ISSUE: issue slots of all instructions (smsp__inst_executed x 32), most of them the
+#         float-pair arithmetic on the fp32 pipe.
+TERSOFF_FLOP_PER_BOND, TERSOFF_FLOP_PER_BOND_PAIR = 44.505, 2.7705
+TERSOFF_FP64_PER_BOND, TERSOFF_FP64_PER_BOND_PAIR = 35.9888, 1.8984
+TERSOFF_ISSUE_PER_BOND, TERSOFF_ISSUE_PER_BOND_PAIR = 1603.424, 178.08
+SW_FLOP_PER_BOND, SW_FLOP_PER_BOND_PAIR = 47.5492, 0.50443
+SW_FP64_PER_BOND, SW_FP64_PER_BOND_PAIR = 22.0230, 6.5537
+SW_ISSUE_PER_BOND, SW_ISSUE_PER_BOND_PAIR = 387.123, 475.684
+# DRAM bytes (read + write) per launch of the current kernels at full size (ncu, one pass):
+# the fp64 pair pass (common-case launch) and the step gathers, eager launches (no fused drift)
+PAIR_TRAFFIC_BYTES = {"tersoff_c_graphene_1M": 160.13e6}
+GATHER_TRAFFIC_BYTES = {"tersoff_c_graphene_1M": 165.57e6}
+GATHER_TRAFFIC_NOTE = "ncu, full size, eager step launch (no fused drift: 72 B/atom fewer than the model)"
 
 
 def load_peaks():
@@ -206,11 +210,34 @@ def job_value(world, n_atoms, steps, ms):
 
 
 def pair_flops(kind: int, bonds: float, bond_pairs: float) -> float:
-    """Algorithmic FP64 flops per atom of the fp64 pair pass for a mean of `bonds` in-cutoff
-    neighbours and `bond_pairs` ordered bond pairs (the mean of M (M - 1)) per atom."""
+    """Counted FP64 flops (DADD + DMUL + 2 DFMA) per atom of the fp64 pair pass for a mean of
+    `bonds` in-cutoff neighbours and `bond_pairs` ordered bond pairs (the mean of M (M - 1))."""
     if kind == I.MD_TERSOFF:
         return TERSOFF_FLOP_PER_BOND * bonds + TERSOFF_FLOP_PER_BOND_PAIR * bond_pairs
     return SW_FLOP_PER_BOND * bonds + SW_FLOP_PER_BOND_PAIR * bond_pairs
+
+
+def pair_slots(kind: int, bonds: float, bond_pairs: float):
+    """(fp64-pipe issue slots, all issue slots) per atom of the fp64 pair pass."""
+    if kind == I.MD_TERSOFF:
+        return (TERSOFF_FP64_PER_BOND * bonds + TERSOFF_FP64_PER_BOND_PAIR * bond_pairs,
+                TERSOFF_ISSUE_PER_BOND * bonds + TERSOFF_ISSUE_PER_BOND_PAIR * bond_pairs)
+    return (SW_FP64_PER_BOND * bonds + SW_FP64_PER_BOND_PAIR * bond_pairs,
+            SW_ISSUE_PER_BOND * bonds + SW_ISSUE_PER_BOND_PAIR * bond_pairs)
+
+
+def pipe_model(kind: int, bonds: float, bond_pairs: float, n: int, peaks: dict) -> dict:
+    """Lower bound on one fp64 pair launch's time from its instruction mix and the measured
+    rates of this GPU: the FP64 pipe retires fp64_tflops/2 thread instructions a second (the
+    FMA-chain peak, 2 flop per FMA), and the schedulers issue fp32_tflops/64 warp
+    instructions a second (the fp32 FMA-chain peak: 32 lanes x 2 flop per issued FMA).  The
+    launch cannot be faster than the larger of the two times."""
+    s64, sall = pair_slots(kind, bonds, bond_pairs)
+    t64 = s64 * n / (peaks["fp64_tflops"] * 1e12 / 2.0)
+    tis = sall * n / 32.0 / (peaks["fp32_tflops"] * 1e12 / 64.0)
+    return {"fp64_slots_per_atom": round(s64, 3), "issue_slots_per_atom": round(sall, 2),
+            "t_fp64_pipe_us": t64 * 1e6, "t_issue_us": tis * 1e6,
+            "bound_pipe": "fp64" if t64 >= tis else "issue", "t_model_us": max(t64, tis) * 1e6}
 
 
 def bond_statistics(pos, box, pbc, rc):
@@ -636,7 +663,7 @@ def precision_vs_oracle():
     return out
 
 
-def run_sw_leg(args, steps, warmup):
+def run_sw_leg(args, steps, warmup, peaks):
     """Stillinger-Weber silicon, 40^3 cells (512,000 atoms), 300 K, dt 1 fs: fp64 and mixed
     atom-steps/s after 100 untimed steps (the crystal gains about one bond per atom as its
     second shell moves inside the cutoff), with the fp64 pair pass's roofline."""
@@ -680,6 +707,10 @@ def run_sw_leg(args, steps, warmup):
             leg["pair_tflops_algorithmic"] = pair_flops_algorithmic(sysm.kind, bonds, pairs) * n / t_pair / 1e12
             if tag == "fp64":
                 leg["pair_tflops_counted"] = pair_flops(sysm.kind, bonds, pairs) * n / t_pair / 1e12
+                pm = pipe_model(sysm.kind, bonds, pairs, n, peaks)
+                leg["pair_pipes"] = pm
+                leg["pair_frac_of_pipe_model"] = pm["t_model_us"] * 1e-6 / t_pair
+                leg["pair_launch_us"] = t_pair * 1e6
         out[tag] = leg
     return out
 
@@ -771,17 +802,29 @@ def main():
     ach_alg = flops_alg / pair_avg_s / 1e12 if pair_avg_s else None
     ach_cnt = flops_cnt / pair_avg_s / 1e12 if pair_avg_s else None
     traffic = PAIR_TRAFFIC_BYTES.get(args.workload) if primary == "fp64" else None
-    roofline = {"bound": "alu", "kernel": f"pair ({primary})", "achieved": ach_alg, "peak": fp64_peak,
-                "unit": "TFLOP/s", "frac": ach_alg / fp64_peak if ach_alg else None, "traffic": traffic,
-                "flop_per_launch": flops_alg,
+    # The fp64 pass runs the method's arithmetic partly on the FP64 pipe (what needs 53 bits)
+    # and partly as float pairs on the FP32 pipe: its roofline is the larger of the two pipe
+    # times of its instruction mix at this GPU's measured rates; `peak` expresses that bound
+    # as an algorithmic flop rate, so frac = model time / launch time.
+    pm = pipe_model(sysm.kind, bonds, bond_pairs, n, peaks) if primary == "fp64" else None
+    peak_mix = flops_alg / (pm["t_model_us"] * 1e-6) / 1e12 if pm else None
+    roofline = {"bound": "alu", "kernel": f"pair ({primary})", "achieved": ach_alg, "peak": peak_mix,
+                "unit": "TFLOP/s", "frac": ach_alg / peak_mix if (ach_alg and peak_mix) else None,
+                "traffic": traffic, "flop_per_launch": flops_alg,
                 "flop_model": "expression count of Eqs. 2-6 and dU_i/dr_ij: +,-,* 1 flop; division, "
                               "reciprocal, 1/sqrt 8; exp, log 16",
-                "peak_source": "measured on this GPU: md_peak_flops FP64 FMA chains "
-                               f"(SM clock median {peaks['clocks'].get('sm_mhz')} MHz)",
-                "peak_nominal": FP64_PEAK_NOMINAL_TFLOPS,
-                "frac_of_nominal": ach_alg / FP64_PEAK_NOMINAL_TFLOPS if ach_alg else None,
-                "counted": {"achieved": ach_cnt, "frac": ach_cnt / fp64_peak if ach_cnt else None,
-                            "flop_per_launch": flops_cnt,
+                "peak_model": "algorithmic flops / max(FP64-pipe time, issue time) of the launch's counted "
+                              "instruction mix at the measured FP64 (md_peak_flops fp64) and issue "
+                              "(md_peak_flops fp32 / 64) rates",
+                "pipes": pm,
+                "launch_us": pair_avg_s * 1e6 if pair_avg_s else None,
+                "fp64_peak": fp64_peak,
+                "vs_fp64_peak": ach_alg / fp64_peak if ach_alg else None,
+                "fp64_peak_source": "measured on this GPU: md_peak_flops FP64 FMA chains "
+                                    f"(SM clock median {peaks['clocks'].get('sm_mhz')} MHz)",
+                "fp64_peak_nominal": FP64_PEAK_NOMINAL_TFLOPS,
+                "counted": {"achieved": ach_cnt, "flop_per_launch": flops_cnt,
+                            "frac_of_fp64_peak": ach_cnt / fp64_peak if ach_cnt else None,
                             "flop_model": "DADD + DMUL + 2 DFMA thread instructions of the kernel (ncu), "
                                           "per bond and per ordered bond pair"},
                 "bonds_per_atom": [round(b[0], 4) for b in bstats],
@@ -825,7 +868,7 @@ def main():
         hbm = peaks_hw["hbm_gbs"]
         rm = {"bound": "hbm", "kernel": "gather (mixed)", "unit": "GB/s", "peak": hbm,
               "peak_source": f"{peaks_hw['_source']} HBM copy bandwidth (MEASURED_PEAKS.json)",
-              "traffic": GATHER_TRAFFIC_BYTES.get(args.workload),
+              "traffic": GATHER_TRAFFIC_BYTES.get(args.workload), "traffic_note": GATHER_TRAFFIC_NOTE,
               "bytes_per_launch": gather_bytes_algorithmic(bonds) * n,
               "bytes_model": "per atom: mask 4 + list 5M + dU/dr 12M + r 12M + U 8 + type 4 + v 48 + F 24 "
                              "+ fused drift 72 (M in-cutoff bonds)"}
@@ -850,7 +893,7 @@ def main():
     if not args.no_npt:
         out["npt"] = run_npt_leg(args, max(8, args.steps // 2), args.warmup)
     if not args.no_sw:
-        out["sw"] = run_sw_leg(args, max(20, args.steps // 2), args.warmup)
+        out["sw"] = run_sw_leg(args, max(20, args.steps // 2), args.warmup, peaks)
     if not args.no_batch:
         out["batch"] = run_batch(args, max(8, args.steps // 2), args.warmup)
     if not args.no_serve:

@@ -63,13 +63,27 @@ def test_matches_brute_force_over_images():
 
 
 def test_flop_model_reproduces_the_counted_launches():
-    """The roofline's per-bond and per-bond-pair FP64 flops are solved from ncu instruction
-    counts of two states each (profiles/pair_*_fp64_*.md); they must give those counts back."""
+    """The roofline's per-bond and per-bond-pair FP64 flops and issue slots are solved from ncu
+    instruction counts of two states each (profiles/pair_*_fp64_*.md); they must give those
+    counts back (flop = DADD + DMUL + 2 DFMA; slots = warp instructions x 32, per atom)."""
     I_T, I_S = bench.I.MD_TERSOFF, bench.I.MD_SW
-    for kind, bonds, pairs, counted in [
-        (I_T, 3.0, 6.0, 551.449),        # C sheet
-        (I_T, 4.0, 12.0, 822.266),       # Si diamond
-        (I_S, 4.0, 12.0, 620.215),       # SW lattice
-        (I_S, 5.0726, 21.5767, 947.165),  # SW after 100 fs at 300 K
+    for kind, bonds, pairs, flop, fp64, issue in [
+        (I_T, 3.0, 6.0, 150.138, 3.7299 * 32, 183.711 * 32),                       # C sheet
+        (I_T, 4.0, 12.0, 211.266, 5.2105 * 32, 267.208 * 32),                      # Si diamond
+        (I_S, 4.0, 12.0, 196.250, 5.2105 * 32, (226.354 + 0.418) * 32),            # SW lattice
+        (I_S, 5.1028, 21.8819, 253.672, (7.6748 + 0.3185) * 32, (383.923 + 3.086) * 32),  # SW, 300 K
     ]:
-        assert bench.pair_flops(kind, bonds, pairs) == pytest.approx(counted, abs=0.02)
+        assert bench.pair_flops(kind, bonds, pairs) == pytest.approx(flop, abs=0.02)
+        s64, sall = bench.pair_slots(kind, bonds, pairs)
+        assert s64 == pytest.approx(fp64, abs=0.05)
+        assert sall == pytest.approx(issue, abs=0.5)
+
+
+def test_pipe_model_takes_the_slower_pipe():
+    peaks = {"fp64_tflops": 1.0, "fp32_tflops": 64.0}
+    pm = bench.pipe_model(bench.I.MD_TERSOFF, 3.0, 6.0, 1_000_000, peaks)
+    s64, sall = bench.pair_slots(bench.I.MD_TERSOFF, 3.0, 6.0)
+    assert pm["t_fp64_pipe_us"] == pytest.approx(s64 * 1e6 / 0.5e12 * 1e6)
+    assert pm["t_issue_us"] == pytest.approx(sall * 1e6 / 32 / 1e12 * 1e6)
+    assert pm["t_model_us"] == max(pm["t_fp64_pipe_us"], pm["t_issue_us"])
+    assert pm["bound_pipe"] == ("fp64" if pm["t_fp64_pipe_us"] >= pm["t_issue_us"] else "issue")
