@@ -224,7 +224,7 @@ md_status md_get_stats(md_ctx *ctx, md_stats *out);
  * look inside graphs with conditional nodes see every kernel this way. */
 md_status md_set_graph_mode(md_ctx *ctx, int use_graphs);
 
-/* Launch tuning.  Two launch parameters are free choices that do not change any result
+/* Launch tuning.  Three launch parameters are free choices that do not change any result
  * (every atom is computed by one thread the same way whatever they are; the gather's
  * partial sums are per 128-atom chunk, not per CUDA block), only the speed:
  *   pair_block          threads per block of the pair pass's common-case launch
@@ -232,9 +232,16 @@ md_status md_set_graph_mode(md_ctx *ctx, int use_graphs);
  *                       memory, so a block covers pair_block atoms);
  *   pool_blocks_per_sm  pools: blocks per SM of the kick, pair and gather kernels that
  *                       loop over the running systems' 128-atom chunks (1..64), i.e. how
- *                       many chunks (atoms / 128) one block takes on per step.
+ *                       many chunks (atoms / 128) one block takes on per step;
+ *   pair_cap            bonds staged per atom by the common-case pass of a single-system
+ *                       fp64 Tersoff context (one element): 3 or 4 (0 = 4).  Atoms with
+ *                       more in-cutoff bonds go to the full-capacity pass, computed the same
+ *                       way; 3 leaves room for more resident warps when most atoms have 3
+ *                       bonds (the honeycomb sheet).  Other contexts stage 4 (Tersoff) or 8
+ *                       (SW) whatever it is.
  * md_autotune times each candidate on the context's current state with CUDA events on
- * its stream -- pair_block over {32, 64, 128, 256} with the pair pass alone, then (pools)
+ * its stream -- pair_block over {32, 64, 128, 256} (for each pair_cap where there is a
+ * choice) with the pair pass alone, then (pools)
  * pool_blocks_per_sm over {4, 8, 16, 32, 64} with the pair pass and a gather without the
  * half-kick -- `repeats` launches each (0: 10), keeps the fastest and stores it in the
  * context; the next md_run captures its graphs with it.  The timed launches recompute the
@@ -242,7 +249,7 @@ md_status md_set_graph_mode(md_ctx *ctx, int use_graphs);
  * Positions must be set (MD_ERR_STATE otherwise).  `out` (may be NULL) receives the
  * choice and every candidate's mean time.  md_set_tuning imposes a choice (MD_ERR_ARG for
  * values outside the sets above; pair_block 0 = the precision's default: 64 for
- * MD_FP64, 128 for MD_MIXED) and md_get_tuning reads the one in use.  The paper fixes
+ * MD_FP64, 128 for MD_MIXED; pair_cap 0 = 4) and md_get_tuning reads the one in use.  The paper fixes
  * its block size by hand (Sec. 3); this tuner has no counterpart there. */
 #define MD_TUNE_MAX 16
 typedef struct md_tuning {
@@ -252,6 +259,8 @@ typedef struct md_tuning {
     int tried_pair_block[MD_TUNE_MAX];
     int tried_blocks_per_sm[MD_TUNE_MAX];
     double tried_ms[MD_TUNE_MAX];     /* mean ms of one timed launch sequence          */
+    int pair_cap;                     /* 3 or 4 in use (read); 0, 3 or 4 (md_set_tuning) */
+    int tried_pair_cap[MD_TUNE_MAX];
 } md_tuning;
 md_status md_autotune(md_ctx *ctx, int repeats, md_tuning *out);
 md_status md_set_tuning(md_ctx *ctx, const md_tuning *t);

@@ -1638,6 +1638,9 @@ unsigned pool_grid(const Plan &p)
 }
 
 constexpr int kPairCapSmall = 4;     // Tersoff: bonds staged per atom in the common-case pass
+// single-system fp64 Tersoff: a 3-bond staging (44 -> 30 shared words a thread) for
+// three-coordinated structures (the honeycomb sheet); a tuning choice (effective_pair_cap)
+constexpr int kPairCapSmall3 = 3;
 // SW: its second shell sits just outside the cutoff, and at room temperature many atoms have
 // 5-6 bonds inside it (a 12-bond fp32 staging moved the rarer heavier atoms into the common
 // pass but cost the pools' occupancy more than it saved: serving 2.94e9 -> 2.7e9 atom-steps/s)
@@ -1671,6 +1674,9 @@ void configure_block()
 {
     set_smem<T, kPairCapSmall, B, false, BATCH>();
     set_smem<T, kPairCapSmallSW<T>, B, false, BATCH>();
+    if constexpr (sizeof(T) == 8 && !BATCH)
+        cudaFuncSetAttribute(k_pair_tersoff<T, kPairCapSmall3, B, false, false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_for<T, kPairCapSmall3, B>(1));
 }
 
 template <typename T, bool BATCH>
@@ -1730,8 +1736,17 @@ void pair_launch_b(const Plan &p, cudaStream_t s, int list, int parts)
                 return;
             }
         }
-        if (parts & PAIR_FAST)
-            k_pair_tersoff<T, kPairCapSmall, B, false, BATCH><<<nb, B, smem_for<T, kPairCapSmall, B>(1), s>>>(a, c);
+        bool fast3 = false;
+        if constexpr (sizeof(T) == 8 && !BATCH) fast3 = effective_pair_cap(p) == kPairCapSmall3;
+        if (parts & PAIR_FAST) {
+            if constexpr (sizeof(T) == 8 && !BATCH) {
+                if (fast3)
+                    k_pair_tersoff<T, kPairCapSmall3, B, false, false>
+                        <<<nb, B, smem_for<T, kPairCapSmall3, B>(1), s>>>(a, c);
+            }
+            if (!fast3)
+                k_pair_tersoff<T, kPairCapSmall, B, false, BATCH><<<nb, B, smem_for<T, kPairCapSmall, B>(1), s>>>(a, c);
+        }
         if (parts & PAIR_DEFERRED)
             k_pair_tersoff<T, FULL, kPairBlockFull, true, BATCH>
                 <<<(unsigned)nbf, kPairBlockFull, smem_for<T, FULL, kPairBlockFull>(1), s>>>(a, c);
@@ -1852,6 +1867,14 @@ int effective_pair_block(const Plan &p)
 }
 
 bool valid_pair_block(int b) { return b == 32 || b == 64 || b == 128 || b == 256; }
+
+// The 3-bond staging exists for the single-system fp64 Tersoff pass only (one element);
+// everywhere else the common-case pass stages 4 (Tersoff) or 8 (SW) bonds.
+int effective_pair_cap(const Plan &p)
+{
+    const bool can3 = p.kind == 1 && p.precision == 0 && !p.batch && !p.multi;
+    return (can3 && p.pair_cap == kPairCapSmall3) ? kPairCapSmall3 : kPairCapSmall;
+}
 
 // The shared-memory opt-in of the pair kernels is an attribute of the kernel in the
 // current device's context: it is set once per device, under a lock (contexts, servers and

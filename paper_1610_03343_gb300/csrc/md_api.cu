@@ -1641,6 +1641,7 @@ void fill_tuning(const md_ctx *ctx, md_tuning *out)
 {
     out->pair_block = effective_pair_block(ctx->p);
     out->pool_blocks_per_sm = ctx->p.pool_bps;
+    out->pair_cap = effective_pair_cap(ctx->p);
 }
 
 }  // namespace
@@ -1665,21 +1666,31 @@ md_status md_autotune(md_ctx *ctx, int repeats, md_tuning *out)
         if (s != MD_OK) return s;
         static const int blocks[] = {32, 64, 128, 256};
         double best = 0.0;
-        int best_b = effective_pair_block(ctx->p);
-        for (int b : blocks) {
-            ctx->p.pair_block = b;
-            double ms = 0.0;
-            s = time_launches(ctx, repeats, false, &ms);
-            if (s != MD_OK) return s;
-            res.tried_pair_block[res.n_tried] = b;
-            res.tried_blocks_per_sm[res.n_tried] = ctx->p.pool_bps;
-            res.tried_ms[res.n_tried++] = ms;
-            if (best == 0.0 || ms < best) {
-                best = ms;
-                best_b = b;
+        int best_b = effective_pair_block(ctx->p), best_c = ctx->p.pair_cap;
+        // bond slots of the common-case pass: 4, and 3 where that staging exists
+        int caps[2] = {4, 3};
+        ctx->p.pair_cap = 3;
+        const int n_caps = effective_pair_cap(ctx->p) == 3 ? 2 : 1;
+        for (int ci = 0; ci < n_caps; ++ci) {
+            ctx->p.pair_cap = caps[ci];
+            for (int b : blocks) {
+                ctx->p.pair_block = b;
+                double ms = 0.0;
+                s = time_launches(ctx, repeats, false, &ms);
+                if (s != MD_OK) return s;
+                res.tried_pair_block[res.n_tried] = b;
+                res.tried_blocks_per_sm[res.n_tried] = ctx->p.pool_bps;
+                res.tried_pair_cap[res.n_tried] = effective_pair_cap(ctx->p);
+                res.tried_ms[res.n_tried++] = ms;
+                if (best == 0.0 || ms < best) {
+                    best = ms;
+                    best_b = b;
+                    best_c = caps[ci];
+                }
             }
         }
         ctx->p.pair_block = best_b;
+        ctx->p.pair_cap = best_c;
         if (ctx->is_pool) {
             static const int bps[] = {4, 8, 16, 32, 64};
             best = 0.0;
@@ -1691,6 +1702,7 @@ md_status md_autotune(md_ctx *ctx, int repeats, md_tuning *out)
                 if (s != MD_OK) return s;
                 res.tried_pair_block[res.n_tried] = best_b;
                 res.tried_blocks_per_sm[res.n_tried] = g;
+                res.tried_pair_cap[res.n_tried] = effective_pair_cap(ctx->p);
                 res.tried_ms[res.n_tried++] = ms;
                 if (best == 0.0 || ms < best) {
                     best = ms;
@@ -1715,8 +1727,11 @@ md_status md_set_tuning(md_ctx *ctx, const md_tuning *t)
         return fail(ctx, MD_ERR_ARG, "pair_block must be 0, 32, 64, 128 or 256");
     if (t->pool_blocks_per_sm < 1 || t->pool_blocks_per_sm > 64)
         return fail(ctx, MD_ERR_ARG, "pool_blocks_per_sm must be in 1..64");
+    if (t->pair_cap != 0 && t->pair_cap != 3 && t->pair_cap != 4)
+        return fail(ctx, MD_ERR_ARG, "pair_cap must be 0, 3 or 4");
     ctx->p.pair_block = t->pair_block;
     ctx->p.pool_bps = t->pool_blocks_per_sm;
+    ctx->p.pair_cap = t->pair_cap;
     destroy_graph(ctx);
     return MD_OK;
 }

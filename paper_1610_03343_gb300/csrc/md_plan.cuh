@@ -25,6 +25,7 @@ struct Plan {
     // the kernels that loop over the running systems' chunks
     int pair_block = 0;
     int pool_bps = 16;
+    int pair_cap = 0;    // bond slots of the common-case Tersoff pass (0: default 4; 3)
     int n_sm = 152;
     // parameter sets (a single system uses set 0)
     int n_sets = 1;
@@ -116,6 +117,7 @@ void fill_tersoff_table(const Plan &p, void *host);
 // Pair-pass block size in use (the tuned one, else the precision's default).
 int effective_pair_block(const Plan &p);
 bool valid_pair_block(int b);
+int effective_pair_cap(const Plan &p);
 // Opt the pair kernels into their dynamic shared memory on the current device (once per
 // device); false if that failed.
 constexpr int kMaxConfigDevices = 64;

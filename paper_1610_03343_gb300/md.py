@@ -109,7 +109,8 @@ class md_tuning(ctypes.Structure):
     _fields_ = [("pair_block", ctypes.c_int), ("pool_blocks_per_sm", ctypes.c_int), ("n_tried", ctypes.c_int),
                 ("tried_pair_block", ctypes.c_int * MD_TUNE_MAX),
                 ("tried_blocks_per_sm", ctypes.c_int * MD_TUNE_MAX),
-                ("tried_ms", ctypes.c_double * MD_TUNE_MAX)]
+                ("tried_ms", ctypes.c_double * MD_TUNE_MAX),
+                ("pair_cap", ctypes.c_int), ("tried_pair_cap", ctypes.c_int * MD_TUNE_MAX)]
 
 
 _lock = threading.Lock()
@@ -398,10 +399,10 @@ def md_autotune(ctx, repeats: int = 0) -> md_tuning:
     return t
 
 
-def md_set_tuning(ctx, pair_block: int = 0, pool_blocks_per_sm: int = 16):
+def md_set_tuning(ctx, pair_block: int = 0, pool_blocks_per_sm: int = 16, pair_cap: int = 0):
     lib = load()
     t = md_tuning()
-    t.pair_block, t.pool_blocks_per_sm = int(pair_block), int(pool_blocks_per_sm)
+    t.pair_block, t.pool_blocks_per_sm, t.pair_cap = int(pair_block), int(pool_blocks_per_sm), int(pair_cap)
     _check(lib, ctx, lib.md_set_tuning(ctx, ctypes.byref(t)))
 
 
@@ -414,9 +415,9 @@ def md_get_tuning(ctx) -> md_tuning:
 
 def tuning_dict(t: md_tuning) -> dict:
     """The chosen launch parameters and every timed candidate, as plain data."""
-    return {"pair_block": t.pair_block, "pool_blocks_per_sm": t.pool_blocks_per_sm,
+    return {"pair_block": t.pair_block, "pool_blocks_per_sm": t.pool_blocks_per_sm, "pair_cap": t.pair_cap,
             "tried": [{"pair_block": t.tried_pair_block[k], "pool_blocks_per_sm": t.tried_blocks_per_sm[k],
-                       "ms": t.tried_ms[k]} for k in range(t.n_tried)]}
+                       "pair_cap": t.tried_pair_cap[k], "ms": t.tried_ms[k]} for k in range(t.n_tried)]}
 
 
 def md_batch_create(atom_capacity, max_systems, kind, param_sets, masses_by_type,

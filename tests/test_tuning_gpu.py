@@ -1,7 +1,8 @@
-"""Launch tuning: the pair pass's block size and the pools' blocks per SM change only the
-speed.  Every candidate must give bitwise the same forces, per-atom fields and
-trajectories, the autotuner must pick one of its candidates, and a run after tuning must
-equal a run without it."""
+"""Launch tuning: the pair pass's block size, the pools' blocks per SM and the bond slots of
+the fp64 Tersoff common-case pass change only the speed.  Every candidate must give bitwise
+the same forces, per-atom fields and trajectories (with 3 slots every 4-bonded Si atom goes
+to the full-capacity pass), the autotuner must pick one of its candidates, and a run after
+tuning must equal a run without it."""
 import numpy as np
 import pytest
 
@@ -53,19 +54,23 @@ def make_pool(md, precision):
 def test_pair_block_does_not_change_results(md, precision, case):
     s, dt = single_cases()[case]
     ref = None
-    for b in BLOCKS:
-        with md.from_inputs(s, precision=precision) as g:
-            md.md_set_tuning(g.ctx, pair_block=b)
-            assert md.md_get_tuning(g.ctx).pair_block == b
-            out = g.compute(want=("f", "u", "w", "j"))
-            ser = g.run(16, dt)
-            x, v = g.state()
-            got = (out["F"], out["U"], out["W"], out["J"], out["totals"], ser, x, v)
-        if ref is None:
-            ref = got
-        else:
-            for a, r in zip(got, ref):
-                assert np.array_equal(a, r), (s.name, b)
+    for cap in (0, 3):
+        for b in BLOCKS:
+            with md.from_inputs(s, precision=precision) as g:
+                md.md_set_tuning(g.ctx, pair_block=b, pair_cap=cap)
+                t = md.md_get_tuning(g.ctx)
+                assert t.pair_block == b
+                # the 3-bond staging exists for the single-system fp64 Tersoff pass only
+                assert t.pair_cap == (3 if (cap == 3 and precision == 0 and s.kind == I.MD_TERSOFF) else 4)
+                out = g.compute(want=("f", "u", "w", "j"))
+                ser = g.run(16, dt)
+                x, v = g.state()
+                got = (out["F"], out["U"], out["W"], out["J"], out["totals"], ser, x, v)
+            if ref is None:
+                ref = got
+            else:
+                for a, r in zip(got, ref):
+                    assert np.array_equal(a, r), (s.name, b, cap)
 
 
 @pytest.mark.parametrize("precision", [0, 1])
@@ -91,13 +96,16 @@ def test_autotune_single_system(md, precision):
         g0.run(5, dt)
         g1.run(5, dt)
         t = md.md_autotune(g1.ctx, 3)
-        assert t.pair_block in BLOCKS
-        assert t.n_tried == len(BLOCKS)
-        assert sorted(t.tried_pair_block[k] for k in range(t.n_tried)) == list(BLOCKS)
+        caps = (4, 3) if precision == 0 else (4,)   # Tersoff Si: both stagings for fp64
+        assert t.pair_block in BLOCKS and t.pair_cap in caps
+        assert t.n_tried == len(BLOCKS) * len(caps)
+        tried = sorted((t.tried_pair_cap[k], t.tried_pair_block[k]) for k in range(t.n_tried))
+        assert tried == sorted((c, b) for c in caps for b in BLOCKS)
         assert all(t.tried_ms[k] > 0 for k in range(t.n_tried))
-        assert t.tried_ms[list(t.tried_pair_block[:t.n_tried]).index(t.pair_block)] == \
-            min(t.tried_ms[k] for k in range(t.n_tried))
-        assert md.md_get_tuning(g1.ctx).pair_block == t.pair_block
+        k_best = [(t.tried_pair_cap[k], t.tried_pair_block[k]) for k in range(t.n_tried)].index((t.pair_cap, t.pair_block))
+        assert t.tried_ms[k_best] == min(t.tried_ms[k] for k in range(t.n_tried))
+        got = md.md_get_tuning(g1.ctx)
+        assert (got.pair_block, got.pair_cap) == (t.pair_block, t.pair_cap)
         s0, s1 = g0.run(12, dt), g1.run(12, dt)
         assert np.array_equal(s0, s1)
         for a, b in zip(g0.state(), g1.state()):
@@ -128,8 +136,13 @@ def test_set_tuning_rejects_bad_values(md):
             with pytest.raises(md.MDError) as e:
                 md.md_set_tuning(g.ctx, pair_block=b, pool_blocks_per_sm=gp)
             assert e.value.status == md.MD_ERR_ARG
+        for cap in (1, 2, 5, 8):
+            with pytest.raises(md.MDError) as e:
+                md.md_set_tuning(g.ctx, pair_block=64, pair_cap=cap)
+            assert e.value.status == md.MD_ERR_ARG
         md.md_set_tuning(g.ctx, pair_block=0)
         assert md.md_get_tuning(g.ctx).pair_block == 64
+        assert md.md_get_tuning(g.ctx).pair_cap == 4
 
 
 def test_autotune_before_positions_is_a_state_error(md):
