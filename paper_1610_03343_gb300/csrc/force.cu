@@ -1234,63 +1234,70 @@ __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, i
         constexpr bool FFG = sizeof(T) == 8;
         F2 ff[3] = {}, fw[9] = {}, fwd[3] = {};
         int k = 0;
-        // each bond's list entry and reverse slot are loaded one bond ahead, while the
-        // previous bond's loads through atom j are in flight
-        int e_nx = 0, mr_nx = 0;
-        if (mask != 0u) {
-            const int m0 = __ffs(mask) - 1;
-            e_nx = a.nl[(int64_t)m0 * N + i];
-            mr_nx = a.rev[(int64_t)m0 * N + i];
-        }
+        // bonds in groups of four: the group's list entries and reverse slots, then its
+        // partners' masks, then the partners' rows, each a batch of independent loads (three
+        // dependent round trips per group instead of two per bond)
         while (mask != 0u && k < MAXA) {
-            mask &= mask - 1u;
-            const int j = list_atom(e_nx);
-            const int mr = mr_nx;
-            if (mask != 0u) {
-                const int m1 = __ffs(mask) - 1;
-                e_nx = a.nl[(int64_t)m1 * N + i];
-                mr_nx = a.rev[(int64_t)m1 * N + i];
-            }
-            const uint32_t maskj = a.mask[j];
-            const int kr = __popc(maskj & ((1u << mr) - 1u));
-            if (FFG && kr < MAXA) {
-                const Vec4<T> dv = a.d[(int64_t)k * N + i], ev = a.d[(int64_t)kr * N + j];
-                const F2 r[3] = {ff_unpack(a.r[(int64_t)(0 * MAXA + k) * N + i]),
-                                 ff_unpack(a.r[(int64_t)(1 * MAXA + k) * N + i]),
-                                 ff_unpack(a.r[(int64_t)(2 * MAXA + k) * N + i])};
-                const F2 g[3] = {ff_add(ff_unpack(dv.x), ff_neg(ff_unpack(ev.x))),
-                                 ff_add(ff_unpack(dv.y), ff_neg(ff_unpack(ev.y))),
-                                 ff_add(ff_unpack(dv.z), ff_neg(ff_unpack(ev.z)))};   // F_ij = d_ij - d_ji
+            int jg[4], mrg[4];
+            uint32_t mjg[4];
+            int ng = 0;
 #pragma unroll
-                for (int c = 0; c < 3; ++c) ff[c] = ff_add(ff[c], g[c]);
-                if (FULL) {
-#pragma unroll
-                    for (int c = 0; c < 9; ++c) fw[c] = ff_fma(r[c / 3], g[c % 3], fw[c]);
-                }
-                if (WDIAG) {
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) fwd[c] = ff_fma(r[c], g[c], fwd[c]);
-                }
-            } else if (kr < MAXA) {
-                const Vec4<T> dv = a.d[(int64_t)k * N + i], ev = a.d[(int64_t)kr * N + j];
-                const T dx = dv.x, dy = dv.y, dz = dv.z, ex = ev.x, ey = ev.y, ez = ev.z;
-                const T rx = a.r[(int64_t)(0 * MAXA + k) * N + i], ry = a.r[(int64_t)(1 * MAXA + k) * N + i],
-                        rz = a.r[(int64_t)(2 * MAXA + k) * N + i];
-                const T gx = dx - ex, gy = dy - ey, gz = dz - ez;   // F_ij = d_ij - d_ji
-                f0 += gx; f1 += gy; f2 += gz;
-                if (FULL) {
-                    w[0] += rx * gx; w[1] += rx * gy; w[2] += rx * gz;
-                    w[3] += ry * gx; w[4] += ry * gy; w[5] += ry * gz;
-                    w[6] += rz * gx; w[7] += rz * gy; w[8] += rz * gz;
-                }
-                if (WDIAG) { wd0 += rx * gx; wd1 += ry * gy; wd2 += rz * gz; }
-                if (!JPASS) {   // M_i = sum_j r_ij (x) d_ji
-                    mj[0] += rx * ex; mj[1] += rx * ey; mj[2] += rx * ez;
-                    mj[3] += ry * ex; mj[4] += ry * ey; mj[5] += ry * ez;
-                    mj[6] += rz * ex; mj[7] += rz * ey; mj[8] += rz * ez;
+            for (int u = 0; u < 4; ++u) {
+                if (mask != 0u && k + u < MAXA) {
+                    const int m = __ffs(mask) - 1;
+                    mask &= mask - 1u;
+                    jg[u] = list_atom(a.nl[(int64_t)m * N + i]);
+                    mrg[u] = a.rev[(int64_t)m * N + i];
+                    ng = u + 1;
                 }
             }
-            ++k;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (u < ng) mjg[u] = a.mask[jg[u]];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (u >= ng) break;
+                const int j = jg[u];
+                const int kr = __popc(mjg[u] & ((1u << mrg[u]) - 1u));
+                if (FFG && kr < MAXA) {
+                    const Vec4<T> dv = a.d[(int64_t)k * N + i], ev = a.d[(int64_t)kr * N + j];
+                    const F2 r[3] = {ff_unpack(a.r[(int64_t)(0 * MAXA + k) * N + i]),
+                                     ff_unpack(a.r[(int64_t)(1 * MAXA + k) * N + i]),
+                                     ff_unpack(a.r[(int64_t)(2 * MAXA + k) * N + i])};
+                    const F2 g[3] = {ff_add(ff_unpack(dv.x), ff_neg(ff_unpack(ev.x))),
+                                     ff_add(ff_unpack(dv.y), ff_neg(ff_unpack(ev.y))),
+                                     ff_add(ff_unpack(dv.z), ff_neg(ff_unpack(ev.z)))};   // F_ij = d_ij - d_ji
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) ff[c] = ff_add(ff[c], g[c]);
+                    if (FULL) {
+#pragma unroll
+                        for (int c = 0; c < 9; ++c) fw[c] = ff_fma(r[c / 3], g[c % 3], fw[c]);
+                    }
+                    if (WDIAG) {
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) fwd[c] = ff_fma(r[c], g[c], fwd[c]);
+                    }
+                } else if (kr < MAXA) {
+                    const Vec4<T> dv = a.d[(int64_t)k * N + i], ev = a.d[(int64_t)kr * N + j];
+                    const T dx = dv.x, dy = dv.y, dz = dv.z, ex = ev.x, ey = ev.y, ez = ev.z;
+                    const T rx = a.r[(int64_t)(0 * MAXA + k) * N + i], ry = a.r[(int64_t)(1 * MAXA + k) * N + i],
+                            rz = a.r[(int64_t)(2 * MAXA + k) * N + i];
+                    const T gx = dx - ex, gy = dy - ey, gz = dz - ez;   // F_ij = d_ij - d_ji
+                    f0 += gx; f1 += gy; f2 += gz;
+                    if (FULL) {
+                        w[0] += rx * gx; w[1] += rx * gy; w[2] += rx * gz;
+                        w[3] += ry * gx; w[4] += ry * gy; w[5] += ry * gz;
+                        w[6] += rz * gx; w[7] += rz * gy; w[8] += rz * gz;
+                    }
+                    if (WDIAG) { wd0 += rx * gx; wd1 += ry * gy; wd2 += rz * gz; }
+                    if (!JPASS) {   // M_i = sum_j r_ij (x) d_ji
+                        mj[0] += rx * ex; mj[1] += rx * ey; mj[2] += rx * ez;
+                        mj[3] += ry * ex; mj[4] += ry * ey; mj[5] += ry * ez;
+                        mj[6] += rz * ex; mj[7] += rz * ey; mj[8] += rz * ez;
+                    }
+                }
+                ++k;
+            }
         }
         const double F[3] = {FFG ? ff_to_d(ff[0]) : to_d(f0), FFG ? ff_to_d(ff[1]) : to_d(f1),
                              FFG ? ff_to_d(ff[2]) : to_d(f2)};
@@ -1355,21 +1362,38 @@ __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, i
             const F2 vf[3] = {split_d(v[0]), split_d(v[1]), split_d(v[2])};
             uint32_t m2 = a.mask[i];
             int k2 = 0;
-            while (m2 != 0u && k2 < MAXA) {
-                const int m = __ffs(m2) - 1;
-                m2 &= m2 - 1u;
-                const int j = list_atom(a.nl[(int64_t)m * N + i]);
-                const int mr = a.rev[(int64_t)m * N + i];
-                const int kr = __popc(a.mask[j] & ((1u << mr) - 1u));
-                if (kr < MAXA) {
-                    const Vec4<T> ev = a.d[(int64_t)kr * N + j];
-                    F2 dv = ff_mul(ff_unpack(ev.x), vf[0]);
-                    dv = ff_fma(ff_unpack(ev.y), vf[1], dv);
-                    dv = ff_fma(ff_unpack(ev.z), vf[2], dv);
+            while (m2 != 0u && k2 < MAXA) {   // grouped as in the first walk
+                int jg[4], mrg[4];
+                uint32_t mjg[4];
+                int ng = 0;
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) fj[c] = ff_fma(ff_unpack(a.r[(int64_t)(c * MAXA + k2) * N + i]), dv, fj[c]);
+                for (int u = 0; u < 4; ++u) {
+                    if (m2 != 0u && k2 + u < MAXA) {
+                        const int m = __ffs(m2) - 1;
+                        m2 &= m2 - 1u;
+                        jg[u] = list_atom(a.nl[(int64_t)m * N + i]);
+                        mrg[u] = a.rev[(int64_t)m * N + i];
+                        ng = u + 1;
+                    }
                 }
-                ++k2;
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (u < ng) mjg[u] = a.mask[jg[u]];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (u >= ng) break;
+                    const int kr = __popc(mjg[u] & ((1u << mrg[u]) - 1u));
+                    if (kr < MAXA) {
+                        const Vec4<T> ev = a.d[(int64_t)kr * N + jg[u]];
+                        F2 dv = ff_mul(ff_unpack(ev.x), vf[0]);
+                        dv = ff_fma(ff_unpack(ev.y), vf[1], dv);
+                        dv = ff_fma(ff_unpack(ev.z), vf[2], dv);
+#pragma unroll
+                        for (int c = 0; c < 3; ++c)
+                            fj[c] = ff_fma(ff_unpack(a.r[(int64_t)(c * MAXA + k2) * N + i]), dv, fj[c]);
+                    }
+                    ++k2;
+                }
             }
         }
         const T hm = a.hm[t];
