@@ -1234,6 +1234,12 @@ __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, i
         constexpr bool FFG = sizeof(T) == 8;
         F2 ff[3] = {}, fw[9] = {}, fwd[3] = {};
         int k = 0;
+        // fp64 heat current (second walk): an atom with at most four bonds keeps its one
+        // group's partners and their rows, so the second walk needs no list, mask or
+        // reverse-slot loads
+        const bool one_group = __popc(mask) <= 4;
+        int js[4], krs[4];
+        int n1 = 0;
         // bonds in groups of four: the group's list entries and reverse slots, then its
         // partners' masks, then the partners' rows, each a batch of independent loads (three
         // dependent round trips per group instead of two per bond)
@@ -1241,6 +1247,7 @@ __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, i
             int jg[4], mrg[4];
             uint32_t mjg[4];
             int ng = 0;
+            const bool first = k == 0;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 if (mask != 0u && k + u < MAXA) {
@@ -1259,6 +1266,11 @@ __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, i
                 if (u >= ng) break;
                 const int j = jg[u];
                 const int kr = __popc(mjg[u] & ((1u << mrg[u]) - 1u));
+                if (JPASS && first) {
+                    js[u] = j;
+                    krs[u] = kr;
+                    n1 = u + 1;
+                }
                 if (FFG && kr < MAXA) {
                     const Vec4<T> dv = a.d[(int64_t)k * N + i], ev = a.d[(int64_t)kr * N + j];
                     const F2 r[3] = {ff_unpack(a.r[(int64_t)(0 * MAXA + k) * N + i]),
@@ -1305,11 +1317,24 @@ __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, i
         // NaN finite values)
         const bool f_fin = FFG ? finite_bits(ff[0].h) && finite_bits(ff[1].h) && finite_bits(ff[2].h)
                                : finite_bits(f0) && finite_bits(f1) && finite_bits(f2);
+        // the epilogue's own loads, issued as one batch before any store: the pointers may
+        // alias as far as the compiler knows, so a load placed after a store would wait for
+        // a round trip of its own (one per component of the drift)
+        const int t = a.type[i];
+        double v[3] = {a.vel[i], a.vel[N + i], a.vel[2 * N + i]};
+        const double u_i = a.u[i];
+        const bool drift = a.kick && fuse;
+        double x0[3] = {0.0, 0.0, 0.0}, xb[3] = {0.0, 0.0, 0.0};
+        if (drift) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                x0[c] = a.pos[c * N + i];
+                xb[c] = a.pos_build[c * N + i];
+            }
+        }
         a.force[i] = F[0];
         a.force[N + i] = F[1];
         a.force[2 * N + i] = F[2];
-        const int t = a.type[i];
-        double v[3] = {a.vel[i], a.vel[N + i], a.vel[2 * N + i]};
         if (a.kick) {
             const double h = a.hk[t];
             v[0] = fma(h, F[0], v[0]);
@@ -1320,15 +1345,15 @@ __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, i
                 v[0] *= f; v[1] *= f; v[2] *= f;
             }
             double vn[3] = {v[0], v[1], v[2]};
-            if (fuse) {   // the next step's half-kick and drift (k_kick_drift's arithmetic)
+            if (drift) {   // the next step's half-kick and drift (k_kick_drift's arithmetic)
                 float d2 = 0.f;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     vn[c] = fma(h, F[c], v[c]);
-                    const double x = fma(a.dt, vn[c], a.pos[c * N + i]);
+                    const double x = fma(a.dt, vn[c], x0[c]);
                     a.pos[c * N + i] = x;
                     if (a.posf) a.posf[c * N + i] = d2f_trunc(x);
-                    const float d = d2f_trunc(x - a.pos_build[c * N + i]);
+                    const float d = d2f_trunc(x - xb[c]);
                     d2 = fmaf(d, d, d2);
                 }
                 if (!(d2 <= hs2)) {
@@ -1360,7 +1385,22 @@ __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, i
         } else {
             // JPASS is the fp64 path: d and r are float pairs
             const F2 vf[3] = {split_d(v[0]), split_d(v[1]), split_d(v[2])};
-            uint32_t m2 = a.mask[i];
+            // the bonds in the first walk's order, the same sums
+            auto jbond = [&](int kb, int jb, int kr) {
+                const Vec4<T> ev = a.d[(int64_t)kr * N + jb];
+                F2 dv = ff_mul(ff_unpack(ev.x), vf[0]);
+                dv = ff_fma(ff_unpack(ev.y), vf[1], dv);
+                dv = ff_fma(ff_unpack(ev.z), vf[2], dv);
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    fj[c] = ff_fma(ff_unpack(a.r[(int64_t)(c * MAXA + kb) * N + i]), dv, fj[c]);
+            };
+            uint32_t m2 = one_group ? 0u : a.mask[i];
+            if (one_group) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (u < n1 && krs[u] < MAXA) jbond(u, js[u], krs[u]);
+            }
             int k2 = 0;
             while (m2 != 0u && k2 < MAXA) {   // grouped as in the first walk
                 int jg[4], mrg[4];
@@ -1383,15 +1423,7 @@ __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, i
                 for (int u = 0; u < 4; ++u) {
                     if (u >= ng) break;
                     const int kr = __popc(mjg[u] & ((1u << mrg[u]) - 1u));
-                    if (kr < MAXA) {
-                        const Vec4<T> ev = a.d[(int64_t)kr * N + jg[u]];
-                        F2 dv = ff_mul(ff_unpack(ev.x), vf[0]);
-                        dv = ff_fma(ff_unpack(ev.y), vf[1], dv);
-                        dv = ff_fma(ff_unpack(ev.z), vf[2], dv);
-#pragma unroll
-                        for (int c = 0; c < 3; ++c)
-                            fj[c] = ff_fma(ff_unpack(a.r[(int64_t)(c * MAXA + k2) * N + i]), dv, fj[c]);
-                    }
+                    if (kr < MAXA) jbond(k2, jg[u], kr);
                     ++k2;
                 }
             }
@@ -1400,7 +1432,7 @@ __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, i
         const T ke = hm * (vx * vx + vy * vy + vz * vz);
         // -1/2 of a float pair: both parts scaled exactly, one conversion
         auto half_neg = [](F2 x) { return ff_to_d(F2{-0.5f * x.h, -0.5f * x.l}); };
-        vals[0] = a.u[i];
+        vals[0] = u_i;
         vals[1] = to_d(ke);
         vals[2] = JPASS ? ff_to_d(fj[0]) : to_d(J0);
         vals[3] = JPASS ? ff_to_d(fj[1]) : to_d(J1);
@@ -1542,17 +1574,27 @@ __device__ __forceinline__ void kick_drift_atom(const KickDriftArgs &a, int64_t 
     const double h = a.hk[a.type[i]];
     const SysDev *sdp = NPT ? (BATCH ? &a.sys[a.sys_of[i]] : a.sys) : nullptr;
     const bool scale = NPT && sdp->npt.on && sdp->npt.pending;
+    // every load before the first store (one round trip: the compiler must assume the
+    // arrays may alias, so it cannot move a load above a store)
+    double vv[3], xx[3], bb[3], ff[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        vv[c] = a.vel[c * N + i];
+        xx[c] = a.pos[c * N + i];
+        bb[c] = a.pos_build[c * N + i];
+        ff[c] = a.force[c * N + i];
+    }
     float d2 = 0.f;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        double v0 = a.vel[c * N + i], x0 = a.pos[c * N + i], xb = a.pos_build[c * N + i];
+        double v0 = vv[c], x0 = xx[c], xb = bb[c];
         if (scale) {
             v0 *= sdp->npt.lam;
             x0 *= sdp->npt.mu[c];
             xb *= sdp->npt.mu[c];
             a.pos_build[c * N + i] = xb;
         }
-        const double v = fma(h, a.force[c * N + i], v0);
+        const double v = fma(h, ff[c], v0);
         const double x = fma(a.dt, v, x0);
         a.vel[c * N + i] = v;
         a.pos[c * N + i] = x;
