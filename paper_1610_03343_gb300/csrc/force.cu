@@ -376,10 +376,22 @@ template <typename T, bool MULTI>
 constexpr int kTersoffBondFields = sizeof(T) == 8 ? TF_FA + (MULTI ? 1 : 0) : TF_NF;
 template <typename T>
 constexpr int kTersoffTypeField = sizeof(T) == 8 ? TF_FA : TF_DX;
+// The fp64 3-bond staging (single element) keeps no f_C and f_C' fields: an atom with a bond
+// in the switching region R <= r < S goes to the full-capacity pass, like an atom with more
+// than three bonds, and the common pass's bonds all have f_C = 1, f_C' = 0.  Its r (then the
+// radial term) and zeta (then P) take the slots of f_C and f_C': six fields a bond, 24 shared
+// words a thread with the three pair slots' float pairs (32 warps per SM at 256 threads).
+template <typename T, int CAP, bool MULTI>
+constexpr bool kTersoffNoSwitch = sizeof(T) == 8 && CAP == 3 && !MULTI;
+template <bool NOSW>
+constexpr int kTfFR = NOSW ? TF_FC : TF_FR;
+template <bool NOSW>
+constexpr int kTfZ = NOSW ? TF_DFC : TF_Z;
 template <typename T, int CAP, bool MULTI = false>
 constexpr int tersoff_smem_fields()
 {
-    return kTersoffBondFields<T, MULTI> * CAP + (sizeof(T) == 8 ? 2 : 1) * (CAP * (CAP - 1) / 2);
+    return (kTersoffNoSwitch<T, CAP, MULTI> ? TF_FC + 2 : kTersoffBondFields<T, MULTI>) * CAP +
+           (sizeof(T) == 8 ? 2 : 1) * (CAP * (CAP - 1) / 2);
 }
 
 // Constants of bond k of the atom: its element pair's (MULTI: the row entry of the element
@@ -399,18 +411,21 @@ __device__ __forceinline__ const TersoffC<T> &bond_const(const TersoffC<T> &p, c
 // cos theta and h - cos theta are therefore formed in fp64 from the fp64 unit vectors (four
 // fp64 instructions per pair) and only then split.  The pair cache holds, per unordered
 // bond pair q = tri(j, k), h - cos theta and dg/dcos in slots q and NP + q.
-template <int CAP, int BLOCK>
+template <int CAP, int BLOCK, bool NOSW = false>
 __device__ __forceinline__ void tersoff_zeta_ff(const TersoffC<double> &p, const Stage<double, CAP, BLOCK> &S,
                                                 double *spair, int na)
 {
     constexpr int NP = CAP * (CAP - 1) / 2;
+    constexpr int ZF = kTfZ<NOSW>;
     double *pc = spair + threadIdx.x;
     const F2 d2 = split_d(p.d2), c2d2 = split_d(p.c2d2), m2c2 = split_d(-2.0 * p.c2);
     const F2 one{1.f, 0.f};
+    // f_C as staged: the float pair of 1.0 is (1, 0)
+    auto fc_of = [&](int k) -> F2 { return NOSW ? one : ff_unpack(S(TF_FC, k)); };
     for (int j = 0; j < na; ++j) {
         const double ujx = S(TF_UX, j), ujy = S(TF_UY, j), ujz = S(TF_UZ, j);
-        const F2 fcj = ff_unpack(S(TF_FC, j));
-        F2 zj = ff_unpack(S(TF_Z, j));
+        const F2 fcj = fc_of(j);
+        F2 zj = ff_unpack(S(ZF, j));
         for (int k = j + 1; k < na; ++k) {
             const double csd = ujx * S(TF_UX, k) + ujy * S(TF_UY, k) + ujz * S(TF_UZ, k);
             // g = 1 + (c^2/d^2) (h - cos)^2 / (d^2 + (h - cos)^2), g' = -2 c^2 (h - cos) / den^2
@@ -422,37 +437,38 @@ __device__ __forceinline__ void tersoff_zeta_ff(const TersoffC<double> &p, const
             const int q = tri(j, k);
             pc[q * BLOCK] = ff_pack(hc);
             pc[(NP + q) * BLOCK] = ff_pack(dg);
-            zj = ff_fma(ff_unpack(S(TF_FC, k)), g, zj);
-            S(TF_Z, k) = ff_pack(ff_fma(fcj, g, ff_unpack(S(TF_Z, k))));
+            zj = ff_fma(fc_of(k), g, zj);
+            S(ZF, k) = ff_pack(ff_fma(fcj, g, ff_unpack(S(ZF, k))));
         }
-        S(TF_Z, j) = ff_pack(zj);
+        S(ZF, j) = ff_pack(zj);
     }
 }
 
 // The angular loop, each bond j on its own: A_j and V_j take the terms of every pair (j, k),
 // k != j, so nothing is scattered into bond k's fields; the factor (P_j + P_k) g' of a pair
 // is formed once from each side, from the same values, so both sides see the same number.
-template <int CAP, int BLOCK>
+template <int CAP, int BLOCK, bool NOSW = false>
 __device__ __forceinline__ void tersoff_angular_ff(const PairArgs<double> &a, const TersoffC<double> &p,
                                                    const Stage<double, CAP, BLOCK> &S, const double *spair,
                                                    int na, int64_t i)
 {
     constexpr int NP = CAP * (CAP - 1) / 2;
+    constexpr int ZF = kTfZ<NOSW>, FRF = kTfFR<NOSW>;
     const double *pc = spair + threadIdx.x;
     const F2 h = split_d(p.h);
     for (int j = 0; j < na; ++j) {
-        const F2 irj = ff_unpack(S(TF_IR, j)), Pj = ff_unpack(S(TF_Z, j));
-        const bool swj = no_switch(S(TF_DFC, j));
-        F2 Aj = ff_unpack(S(TF_FR, j));
+        const F2 irj = ff_unpack(S(TF_IR, j)), Pj = ff_unpack(S(ZF, j));
+        const bool swj = NOSW || no_switch(S(TF_DFC, j));
+        F2 Aj = ff_unpack(S(FRF, j));
         F2 vx{0.f, 0.f}, vy{0.f, 0.f}, vz{0.f, 0.f};
         for (int k = 0; k < na; ++k) {
             if (k == j) continue;
             const int q = k > j ? tri(j, k) : tri(k, j);
             const F2 hc = ff_unpack(pc[q * BLOCK]), dg = ff_unpack(pc[(NP + q) * BLOCK]);
             const F2 cs = ff_add(h, ff_neg(hc));
-            const F2 Pk = ff_unpack(S(TF_Z, k));
+            const F2 Pk = ff_unpack(S(ZF, k));
             F2 qj;
-            if (swj && no_switch(S(TF_DFC, k))) {
+            if (NOSW || (swj && no_switch(S(TF_DFC, k)))) {
                 // both below R: f_C = 1, f_C' = 0
                 qj = ff_mul(ff_mul(ff_add(Pj, Pk), dg), irj);
                 Aj = ff_fma(ff_neg(qj), cs, Aj);
@@ -483,9 +499,12 @@ __device__ __forceinline__ void tersoff_atom(const PairArgs<T> &a, const Tersoff
 {
     const int64_t N = a.N;
     Stage<T, CAP, BLOCK> S{base, (int)threadIdx.x};
+    constexpr bool NOSW = kTersoffNoSwitch<T, CAP, MULTI>;
+    static_assert(!(NOSW && FULL_CAP), "the full-capacity pass stages f_C");
+    constexpr int FRF = kTfFR<NOSW>, ZF = kTfZ<NOSW>;
     // per unordered bond pair q: fp64, h - cos theta and dg/dcos from the zeta loop (float
     // pairs, two slots); fp32, 1/(d^2 + (h - cos)^2) (one slot)
-    T *spair = base + kTersoffBondFields<T, MULTI> * CAP * BLOCK;
+    T *spair = base + (NOSW ? TF_FC + 2 : kTersoffBondFields<T, MULTI>) * CAP * BLOCK;
     auto PCS = [&](int q) -> T & { return spair[q * BLOCK + threadIdx.x]; };
 
     uint32_t mask;
@@ -525,24 +544,30 @@ __device__ __forceinline__ void tersoff_atom(const PairArgs<T> &a, const Tersoff
         // x = pi (r-R)/(S-R): the half-angle form has no cancellation as f_C -> 0 near S
         T fc = T(1), dfc = T(0);
         if (!lt_nonneg(r, pk.R)) {
+            if constexpr (NOSW) {   // a bond in the switching region: the full-capacity pass
+                a.ovf_list[atomicAdd(a.ovf_count, 1)] = (int)i;
+                return;
+            }
             T sn, cn;
             M<T>::sincos_(T(0.5) * pk.pi_SR * (r - pk.R), &sn, &cn);
             fc = cn * cn;
             dfc = -pk.pi_SR * sn * cn;
         }
-        put(TF_FC, k, fc);
-        S(TF_DFC, k) = dfc;
+        if constexpr (!NOSW) {
+            put(TF_FC, k, fc);
+            S(TF_DFC, k) = dfc;
+        }
         if constexpr (FF) {
-            S(TF_FR, k) = r;
+            S(FRF, k) = r;
         } else {
             S(TF_FR, k) = pk.A * M<T>::texp_(-pk.lam * r);
             S(TF_FA, k) = pk.B * M<T>::texp_(-pk.mu * r);
         }
-        S(TF_Z, k) = T(0);   // also the float pair (0, 0)
+        S(ZF, k) = T(0);   // also the float pair (0, 0)
     }
     // zeta_ij = sum_{k != j} f_C(r_ik) g(theta_ijk), each unordered pair once
     if constexpr (FF) {
-        tersoff_zeta_ff<CAP, BLOCK>(p, S, spair, na);
+        tersoff_zeta_ff<CAP, BLOCK, NOSW>(p, S, spair, na);
     } else {
         for (int j = 0; j < na; ++j) {
             const T ujx = S(TF_UX, j), ujy = S(TF_UY, j), ujz = S(TF_UZ, j), fcj = S(TF_FC, j);
@@ -566,10 +591,10 @@ __device__ __forceinline__ void tersoff_atom(const PairArgs<T> &a, const Tersoff
     T ui = T(0);
     for (int k = 0; k < na; ++k) {
         const TersoffC<T> &pk = bond_const<MULTI>(p, row, MULTI ? S(kTersoffTypeField<T>, k) : T(0));
-        const T dfc = S(TF_DFC, k);
+        const T dfc = NOSW ? T(0) : S(TF_DFC, k);
         T fr, fa;
         if constexpr (FF) {
-            const T r = S(TF_FR, k);
+            const T r = S(FRF, k);
             fr = pk.A * M<T>::texp_(-pk.lam * r);
             fa = pk.B * M<T>::texp_(-pk.mu * r);
         } else {
@@ -577,15 +602,15 @@ __device__ __forceinline__ void tersoff_atom(const PairArgs<T> &a, const Tersoff
             fa = S(TF_FA, k);
         }
         // f_C = 1, f_C' = 0 below R: the same arithmetic without the unit factors and zero terms
-        const bool sw = !no_switch(dfc);
+        const bool sw = !NOSW && !no_switch(dfc);
         T b;
         if constexpr (FF) {
             F2 cfa = split_d(fa);
             cfa = F2{0.25f * cfa.h, 0.25f * cfa.l};
             if (sw) cfa = ff_mul(cfa, ff_unpack(S(TF_FC, k)));
             F2 P;
-            b = tersoff_b_ff(p, ff_unpack(S(TF_Z, k)), cfa, P);
-            S(TF_Z, k) = ff_pack(P);
+            b = tersoff_b_ff(p, ff_unpack(S(ZF, k)), cfa, P);
+            S(ZF, k) = ff_pack(P);
         } else {
             T db;
             tersoff_b(p, S(TF_Z, k), b, db);
@@ -602,13 +627,13 @@ __device__ __forceinline__ void tersoff_atom(const PairArgs<T> &a, const Tersoff
             const T dA = dfc * fa - pk.mu * fc * fa;    // (f_C f_A)'
             radial = T(0.5) * (dR - b * dA);
         }
-        put(TF_FR, k, radial);
+        put(FRF, k, radial);
         if constexpr (FF) {
             S(TF_UX, k) = ff_pack(split_d(S(TF_UX, k)));
             S(TF_UY, k) = ff_pack(split_d(S(TF_UY, k)));
             S(TF_UZ, k) = ff_pack(split_d(S(TF_UZ, k)));
             S(TF_IR, k) = ff_pack(split_d(S(TF_IR, k)));
-            S(TF_DFC, k) = ff_pack(split_d(dfc));   // +0 stays the all-zero pattern
+            if constexpr (!NOSW) S(TF_DFC, k) = ff_pack(split_d(dfc));   // +0 stays the all-zero pattern
         } else {
             S(TF_DX, k) = T(0);
             S(TF_DY, k) = T(0);
@@ -619,7 +644,7 @@ __device__ __forceinline__ void tersoff_atom(const PairArgs<T> &a, const Tersoff
     //   d_j += (P_j fc_k + P_k fc_j) g' dcos_j + P_k fc'_j g u_j   (and j <-> k),
     // i.e. V_j += q_j u_k and A_j += c_j - q_j cos, q_j = (P_j fc_k + P_k fc_j) g'/r_ij
     if constexpr (FF) {
-        tersoff_angular_ff<CAP, BLOCK>(a, p, S, spair, na, i);
+        tersoff_angular_ff<CAP, BLOCK, NOSW>(a, p, S, spair, na, i);
     } else {
         for (int j = 0; j < na; ++j) {
             const T ujx = S(TF_UX, j), ujy = S(TF_UY, j), ujz = S(TF_UZ, j);
@@ -1332,9 +1357,14 @@ __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, i
                 xb[c] = a.pos_build[c * N + i];
             }
         }
-        a.force[i] = F[0];
-        a.force[N + i] = F[1];
-        a.force[2 * N + i] = F[2];
+        // a step whose gather also takes the next step's kick keeps F in registers: only the
+        // next step's k_kick_drift reads the stored forces, and the last step of every graph
+        // and of every system's budget stores them (no fused drift there)
+        if (!drift) {
+            a.force[i] = F[0];
+            a.force[N + i] = F[1];
+            a.force[2 * N + i] = F[2];
+        }
         if (a.kick) {
             const double h = a.hk[t];
             v[0] = fma(h, F[0], v[0]);

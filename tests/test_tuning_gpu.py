@@ -151,3 +151,31 @@ def test_autotune_before_positions_is_a_state_error(md):
         with pytest.raises(md.MDError) as e:
             md.md_autotune(g.ctx)
         assert e.value.status == md.MD_ERR_STATE
+
+
+def test_three_bond_staging_defers_bonds_in_the_switching_region(md):
+    """The fp64 3-bond staging holds no f_C values: an atom with a bond in R <= r < S goes to
+    the full-capacity pass.  A sheet stretched so that bonds straddle R = 1.8 A (bond 1.78 A,
+    second neighbours at 3.1 A, outside S) defers some atoms and not others; its forces,
+    per-atom fields and trajectory equal the 4-bond staging's bit for bit and the oracle's
+    to 1e-12."""
+    import oracle as O
+    s = I.c_graphene_tersoff(nx=8, ny=12, a_cc=1.78, jitter_amp=0.06, seed_pos=21, seed_vel=22)
+    ref = O.compute(s.pos, s.box, s.pbc, s.kind, s.params, s.vel)
+    got = {}
+    for cap in (3, 4):
+        with md.from_inputs(s, precision=0) as g:
+            md.md_set_tuning(g.ctx, pair_block=64, pair_cap=cap)
+            assert md.md_get_tuning(g.ctx).pair_cap == cap
+            out = g.compute(want=("f", "u", "w", "j"))
+            deferred = g.stats().pair_deferred
+            ser = g.run(16, 0.5)
+            x, v = g.state()
+        got[cap] = (out["F"], out["U"], out["W"], out["J"], out["totals"], ser, x, v)
+        if cap == 3:
+            assert 0 < deferred < s.n, deferred
+            for k in ("F", "U", "W", "J"):
+                den = np.abs(ref[k]).max()
+                assert np.abs(out[k] - ref[k]).max() / den < 1e-12, k
+    for a, b in zip(got[3], got[4]):
+        assert np.array_equal(a, b)
