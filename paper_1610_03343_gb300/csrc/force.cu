@@ -91,7 +91,9 @@ struct Stage {
 // Potential constants in the pair pass's arithmetic type (no conversions in the loops).
 template <typename T>
 struct TersoffC {
-    T A, B, lam, mu, n, c2, d2, c2d2, h, R, pi_SR, n_ln_beta, inv2n;   // n_ln_beta = n log(beta)
+    // hA = A/2, hB = B/2: the pair pass forms f_R/2 and f_A/2, which is what U_i (Eq. 2's
+    // 1/2 f_C (f_R - b f_A)), the radial term and P take (exact: halving is a scaling by 2^-1)
+    T hA, hB, lam, mu, n, c2, d2, c2d2, h, R, pi_SR, n_ln_beta, inv2n;   // n_ln_beta = n log(beta)
     T beta;
     T rc2;   // S^2
     int beta_zero;
@@ -100,7 +102,7 @@ template <typename T>
 TersoffC<T> tersoff_const(const TersoffP &p)
 {
     TersoffC<T> c;
-    c.A = T(p.A); c.B = T(p.B); c.lam = T(p.lam); c.mu = T(p.mu); c.n = T(p.n);
+    c.hA = T(0.5 * p.A); c.hB = T(0.5 * p.B); c.lam = T(p.lam); c.mu = T(p.mu); c.n = T(p.n);
     c.c2 = T(p.c2); c.d2 = T(p.d2); c.c2d2 = T(p.c2d2); c.h = T(p.h); c.R = T(p.R);
     c.pi_SR = T(p.pi_SR); c.n_ln_beta = T(p.n * p.ln_beta); c.inv2n = T(p.inv2n); c.beta = T(p.beta);
     c.rc2 = T(p.S * p.S);
@@ -165,8 +167,8 @@ __device__ __noinline__ void pair_fail(const PairArgs<T> &a, int64_t i, int stat
 // The cutoff decision is symmetric in i and j: the two fp64 differences are exact
 // negatives of each other, and so are their conversions.
 // MULTI (multi-element Tersoff): the cutoff is that of the element pair, row[t_j].rc2
-// (row: atom i's row of the pair table, rc2 its largest entry), and the neighbour's element
-// is staged in field ftype.
+// (row: atom i's row of the pair table; rc2, the prefilter's radius, its largest entry),
+// and the neighbour's element is staged in field ftype.
 template <typename T, int CAP, int BLOCK, bool FULL_CAP, bool PREFILTER, bool MULTI = false, typename ST>
 __device__ __forceinline__ int collect_bonds(const PairArgs<T> &a, int64_t i, const Box &box, T rc2,
                                              uint32_t &mask, ST &S, int fx, int fy, int fz, int fr2,
@@ -491,8 +493,8 @@ __device__ __forceinline__ void tersoff_angular_ff(const PairArgs<double> &a, co
 }
 
 // Pair pass for one atom (Tersoff).  MULTI: p holds atom i's element constants (angular
-// and bond-order; rc2 = its row's largest cutoff) and row its pair-constant row; each
-// bond's radial functions take the pair's constants (chi folded into B).
+// and bond-order) and row its pair-constant row; each bond's radial functions and cutoff
+// take the pair's constants (chi folded into B).
 template <typename T, int CAP, int BLOCK, bool FULL_CAP, bool MULTI = false>
 __device__ __forceinline__ void tersoff_atom(const PairArgs<T> &a, const TersoffC<T> &p, const Box &box, T *base,
                                              int64_t i, const TersoffC<T> *row = nullptr)
@@ -508,8 +510,16 @@ __device__ __forceinline__ void tersoff_atom(const PairArgs<T> &a, const Tersoff
     auto PCS = [&](int q) -> T & { return spair[q * BLOCK + threadIdx.x]; };
 
     uint32_t mask;
-    const int na = collect_bonds<T, CAP, BLOCK, FULL_CAP, false, MULTI>(a, i, box, p.rc2, mask, S, TF_UX, TF_UY,
-                                                                        TF_UZ, TF_IR, row, kTersoffTypeField<T>);
+    // fp64: the list slots outside the cutoff are dropped by an fp32 test first, so that only
+    // bonds take the fp64 bond vector and |r|^2 (the fp64 pipe bounds this pass); MULTI tests
+    // against the largest cutoff of atom i's row
+    T rc2 = p.rc2;
+    if constexpr (MULTI) {
+#pragma unroll
+        for (int t = 0; t < kMaxTypes; ++t) rc2 = row[t].rc2 > rc2 ? row[t].rc2 : rc2;
+    }
+    const int na = collect_bonds<T, CAP, BLOCK, FULL_CAP, sizeof(T) == 8, MULTI>(
+        a, i, box, rc2, mask, S, TF_UX, TF_UY, TF_UZ, TF_IR, row, kTersoffTypeField<T>);
     if (na < 0) return;   // deferred to the full-capacity pass
 
     // fp64: after the radial loop f_C, and after the bond-order loop every value the angular
@@ -560,8 +570,8 @@ __device__ __forceinline__ void tersoff_atom(const PairArgs<T> &a, const Tersoff
         if constexpr (FF) {
             S(FRF, k) = r;
         } else {
-            S(TF_FR, k) = pk.A * M<T>::texp_(-pk.lam * r);
-            S(TF_FA, k) = pk.B * M<T>::texp_(-pk.mu * r);
+            S(TF_FR, k) = pk.hA * M<T>::texp_(-pk.lam * r);   // f_R / 2
+            S(TF_FA, k) = pk.hB * M<T>::texp_(-pk.mu * r);    // f_A / 2
         }
         S(ZF, k) = T(0);   // also the float pair (0, 0)
     }
@@ -592,11 +602,11 @@ __device__ __forceinline__ void tersoff_atom(const PairArgs<T> &a, const Tersoff
     for (int k = 0; k < na; ++k) {
         const TersoffC<T> &pk = bond_const<MULTI>(p, row, MULTI ? S(kTersoffTypeField<T>, k) : T(0));
         const T dfc = NOSW ? T(0) : S(TF_DFC, k);
-        T fr, fa;
+        T fr, fa;   // f_R / 2, f_A / 2
         if constexpr (FF) {
             const T r = S(FRF, k);
-            fr = pk.A * M<T>::texp_(-pk.lam * r);
-            fa = pk.B * M<T>::texp_(-pk.mu * r);
+            fr = pk.hA * M<T>::texp_(-pk.lam * r);
+            fa = pk.hB * M<T>::texp_(-pk.mu * r);
         } else {
             fr = S(TF_FR, k);
             fa = S(TF_FA, k);
@@ -605,8 +615,8 @@ __device__ __forceinline__ void tersoff_atom(const PairArgs<T> &a, const Tersoff
         const bool sw = !NOSW && !no_switch(dfc);
         T b;
         if constexpr (FF) {
-            F2 cfa = split_d(fa);
-            cfa = F2{0.25f * cfa.h, 0.25f * cfa.l};
+            F2 cfa = split_d(fa);   // f_C f_A / 4
+            cfa = F2{0.5f * cfa.h, 0.5f * cfa.l};
             if (sw) cfa = ff_mul(cfa, ff_unpack(S(TF_FC, k)));
             F2 P;
             b = tersoff_b_ff(p, ff_unpack(S(ZF, k)), cfa, P);
@@ -614,18 +624,18 @@ __device__ __forceinline__ void tersoff_atom(const PairArgs<T> &a, const Tersoff
         } else {
             T db;
             tersoff_b(p, S(TF_Z, k), b, db);
-            S(TF_Z, k) = sw ? T(-0.5) * S(TF_FC, k) * fa * db : T(-0.5) * fa * db;
+            S(TF_Z, k) = sw ? -(S(TF_FC, k) * fa * db) : -(fa * db);   // -1/2 f_C f_A b'
         }
         T radial;
         if (!sw) {
-            ui += T(0.5) * (fr - b * fa);
-            radial = T(0.5) * (-pk.lam * fr + b * (pk.mu * fa));
+            ui += fr - b * fa;
+            radial = -pk.lam * fr + b * (pk.mu * fa);
         } else {
             const T fc = get(TF_FC, k);
-            ui += T(0.5) * fc * (fr - b * fa);
-            const T dR = dfc * fr - pk.lam * fc * fr;   // (f_C f_R)'
-            const T dA = dfc * fa - pk.mu * fc * fa;    // (f_C f_A)'
-            radial = T(0.5) * (dR - b * dA);
+            ui += fc * (fr - b * fa);
+            const T dR = dfc * fr - pk.lam * fc * fr;   // (f_C f_R)' / 2
+            const T dA = dfc * fa - pk.mu * fc * fa;    // (f_C f_A)' / 2
+            radial = dR - b * dA;
         }
         put(FRF, k, radial);
         if constexpr (FF) {
@@ -1576,7 +1586,7 @@ struct KickDriftArgs {
     int64_t N;
     int64_t n_live;         // atoms integrated: [0, n_live) (ghosts beyond)
     float *posf;   // fp32 positions, refreshed every step only where the pair pass reads them
-                   // between list builds (the SW prefilter); null otherwise (the list build
+                   // between list builds (the SW and fp64 Tersoff prefilters); null otherwise (the list build
                    // writes its own copy)
     const int *act_count, *act_chunks;
     const int *sys_of;
@@ -1725,6 +1735,11 @@ __global__ void k_step_begin(Flags *flags, int *ovf_count, cudaGraphConditionalH
 }
 
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// The pair passes that test list slots in fp32 first (SW; fp64 Tersoff) read the fp32
+// positions every step, so the kick and drift keep them current; the others read them only
+// in the list build, which writes its own copy.
+inline bool pair_reads_posf(const Plan &p) { return p.kind == 2 || (p.kind == 1 && p.precision == 0); }
 
 // Bounded grid of the pool kernels that loop over the chunk list (tuned: blocks per SM).
 unsigned pool_grid(const Plan &p)
@@ -1903,7 +1918,7 @@ void gather_launch(const Plan &p, cudaStream_t s, const double *hk, double dt, b
     a.fuse_kick = (fuse_next && hk && !full && !p.npt) ? 1 : 0;
     a.pos = p.pos;
     a.pos_build = p.pos_build;
-    a.posf = p.kind == 2 ? p.posf : nullptr;
+    a.posf = pair_reads_posf(p) ? p.posf : nullptr;
     a.half_skin2 = (float)(0.25 * p.skin * p.skin);
     const unsigned nb = BATCH ? pool_grid(p) : blocks_for(p.N, kGatherBlock);
     if (full)
@@ -2009,7 +2024,7 @@ void launch_kick_drift(const Plan &p, cudaStream_t s, const double *hk, double d
     a.vel = p.vel;
     a.force = p.force;
     a.pos_build = p.pos_build;
-    a.posf = p.kind == 2 ? p.posf : nullptr;
+    a.posf = pair_reads_posf(p) ? p.posf : nullptr;
     a.type = p.type;
     for (int t = 0; t < kMaxTypes; ++t) a.hk[t] = hk[t];
     a.dt = dt;

@@ -67,8 +67,8 @@ __global__ void k_domain_pack(int64_t n, const int *idx, const double *pos, int6
 }
 
 // positions of atoms first .. first + n - 1 from in[3k + c], minus `offset` along the axis,
-// and their fp32 copies (the SW pair pass prefilters bonds with them, as the kick keeps them
-// for the owned atoms)
+// and their fp32 copies (the SW and fp64 Tersoff pair passes prefilter bonds with them, as
+// the kick keeps them for the owned atoms)
 __global__ void k_domain_unpack(int64_t n, int64_t first, double *pos, float *posf, int64_t N, int axis,
                                 double offset, const double *in)
 {

@@ -216,7 +216,7 @@ struct GatherArgs {
     int fuse_kick;
     double *pos;
     const double *pos_build;
-    float *posf;            // fp32 positions to refresh (SW prefilter), or null
+    float *posf;            // fp32 positions to refresh (pair-pass prefilter), or null
     float half_skin2;       // single system: (skin/2)^2
 };
 
