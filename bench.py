@@ -310,8 +310,8 @@ def run_ours(args, rank, world):
         tuning = None
         if args.pair_block:
             pb = dict(zip(("fp64", "mixed"), (int(v) for v in args.pair_block.split(","))))[tag]
-            md.md_set_tuning(g.ctx, pair_block=pb)
-            tuning = {"pair_block": pb, "imposed": True}
+            md.md_set_tuning(g.ctx, pair_block=pb, pair_cap=args.pair_cap)
+            tuning = {"pair_block": pb, "pair_cap": md.md_get_tuning(g.ctx).pair_cap, "imposed": True}
         elif not args.no_tune:
             tuning = md.tuning_dict(md.md_autotune(g.ctx, 10))
         # the warm-up captures the step graphs (the timed region replays them)
@@ -751,6 +751,8 @@ def main():
     ap.add_argument("--eager", action="store_true",
                     help="launch each kernel eagerly instead of replaying graphs (for profilers)")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shapes (no autotuner)")
+    ap.add_argument("--pair-cap", type=int, default=0, choices=[0, 3, 4],
+                    help="with --pair-block: bond slots of the fp64 Tersoff common-case pass (0 = 4)")
     ap.add_argument("--pair-block", default="",
                     help="impose the pair block size instead of autotuning: 'FP64,MIXED', e.g. 64,128")
     ap.add_argument("--pool-tuning", default="",

@@ -246,8 +246,9 @@ __device__ __forceinline__ ListFrame list_frame(const float *posf, int64_t N, in
 // One thread per atom: search the distinct neighbouring cells and keep every j != i
 // with |r_ij| < rl + margin (fp32, minimum image), in ascending index order, each with
 // the image shift it was found at.  Snapshots the build positions for the skin test.
+// Returns the number of atoms found (0 for an atom of a system that is not rebuilt).
 template <bool BATCH>
-__device__ __forceinline__ void build_list_atom(int64_t i, int64_t N, const double *pos, const float *posf,
+__device__ __forceinline__ int build_list_atom(int64_t i, int64_t N, const double *pos, const float *posf,
                                                 Box box0, int nc0, int nc1, int nc2, const int *sys_of,
                                                 SysDev *sys, const int *atom_cell, const int *cell_start,
                                                 const int *cell_count, const int *cell_atoms, float rlm2, int cap,
@@ -258,7 +259,7 @@ __device__ __forceinline__ void build_list_atom(int64_t i, int64_t N, const doub
     long long off = 0;
     if (BATCH) {
         const SysDev &sd = sys[sys_of[i]];
-        if (!sd.rebuild) return;
+        if (!sd.rebuild) return 0;
         bp = &sd.box;
         nc[0] = sd.nc[0]; nc[1] = sd.nc[1]; nc[2] = sd.nc[2];
         off = sd.cell_off;
@@ -335,7 +336,15 @@ __device__ __forceinline__ void build_list_atom(int64_t i, int64_t N, const doub
         if (BATCH) fail_system(sys[sys_of[i]], MD_ERR_NEIGH_OVERFLOW);   // this system only
         else flags->list_overflow = 1;
     }
-    atomicMax(&flags->max_nn, cnt);
+    return cnt;
+}
+
+// flags->max_nn = max(flags->max_nn, the warp's largest cnt): one atomic per warp.  Every
+// lane of the warp calls it (0 for an atom it did not build).
+__device__ __forceinline__ void warp_max_nn(int cnt, Flags *flags)
+{
+    const int wmax = __reduce_max_sync(0xffffffffu, cnt);
+    if ((threadIdx.x & 31) == 0 && wmax > 0) atomicMax(&flags->max_nn, wmax);
 }
 
 // rev[m N + i] = slot of i in the list of j = atom of nl[m N + i] (lists are symmetric).
@@ -376,9 +385,11 @@ __global__ void k_build_list(int64_t N, const double *pos, const float *posf, Bo
                              double *pos_build, Flags *flags)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int cnt = 0;
     if (i < N)
-        build_list_atom<false>(i, N, pos, posf, box, nc0, nc1, nc2, nullptr, sys1, atom_cell, cell_start,
-                               cell_count, cell_atoms, rlm2, cap, nn, nl, pos_build, flags);
+        cnt = build_list_atom<false>(i, N, pos, posf, box, nc0, nc1, nc2, nullptr, sys1, atom_cell, cell_start,
+                                     cell_count, cell_atoms, rlm2, cap, nn, nl, pos_build, flags);
+    warp_max_nn(cnt, flags);
 }
 __global__ void k_build_rev(int64_t N, const int *nn, const int *nl, uint8_t *rev, Flags *flags)
 {
@@ -525,9 +536,12 @@ __global__ void __launch_bounds__(kChunk) k_build_list_pool(const int *plan, con
                                                             const int *cell_count, const int *cell_atoms, int cap,
                                                             int *nn, int *nl, double *pos_build, Flags *flags)
 {
-    for (int k = blockIdx.x; k < plan[0]; k += gridDim.x)
-        build_list_atom<true>(chunks[k] + threadIdx.x, N, pos, posf, Box{}, 1, 1, 1, sys_of, sys, atom_cell,
-                              cell_start, cell_count, cell_atoms, 0.f, cap, nn, nl, pos_build, flags);
+    for (int k = blockIdx.x; k < plan[0]; k += gridDim.x) {
+        const int cnt = build_list_atom<true>(chunks[k] + threadIdx.x, N, pos, posf, Box{}, 1, 1, 1, sys_of, sys,
+                                              atom_cell, cell_start, cell_count, cell_atoms, 0.f, cap, nn, nl,
+                                              pos_build, flags);
+        warp_max_nn(cnt, flags);
+    }
 }
 // Reverse slots of the rebuilt systems' atoms (their chunks only; padding atoms belong to the
 // inactive sentinel, which has no atoms), then the rest of the build: every atom zeroes its
