@@ -102,7 +102,8 @@ def gather_bytes_algorithmic(bonds: float, fused: bool = True, elem: int = 4) ->
 # Instruction model of the fp64 pair pass, from ncu's instruction counters of the current
 # kernels (profiles/pair_tersoff_fp64_c_graphene_1M.md, profiles/pair_sw_fp64_si_512k.md):
 # per in-cutoff bond and per ordered pair of bonds (j, k != j) of one atom, solved from two
-# states each -- Tersoff: the C sheet (3 bonds, 6 ordered pairs) and Si diamond (4, 12);
+# states each -- Tersoff: the C sheet (3 bonds, 6 ordered pairs; the 3-bond staging the
+# autotuner picks there) and Si diamond (4, 12; the 4-bond staging);
 # SW: the Si lattice (4, 12) and the crystal after 100 fs at 300 K (5.1028, 21.8819; the
 # common-case and full-capacity launches together).
 #   FLOP: DADD + DMUL + 2 DFMA thread instructions (the fp64 arithmetic that is left: the
@@ -110,15 +111,15 @@ def gather_bytes_algorithmic(bonds: float, fused: bool = True, elem: int = 4) ->
 #   FP64: fp64-pipe issue slots (smsp__inst_executed_pipe_fp64 x 32);
 #   ISSUE: issue slots of all instructions (smsp__inst_executed x 32), most of them the
 #         float-pair arithmetic on the fp32 pipe.
-TERSOFF_FLOP_PER_BOND, TERSOFF_FLOP_PER_BOND_PAIR = 44.505, 2.7705
-TERSOFF_FP64_PER_BOND, TERSOFF_FP64_PER_BOND_PAIR = 35.9888, 1.8984
-TERSOFF_ISSUE_PER_BOND, TERSOFF_ISSUE_PER_BOND_PAIR = 1603.424, 178.08
+TERSOFF_FLOP_PER_BOND, TERSOFF_FLOP_PER_BOND_PAIR = 41.4287, 3.12099
+TERSOFF_FP64_PER_BOND, TERSOFF_FP64_PER_BOND_PAIR = 32.1030, 2.52050
+TERSOFF_ISSUE_PER_BOND, TERSOFF_ISSUE_PER_BOND_PAIR = 1348.332, 288.810
 SW_FLOP_PER_BOND, SW_FLOP_PER_BOND_PAIR = 47.5492, 0.50443
 SW_FP64_PER_BOND, SW_FP64_PER_BOND_PAIR = 22.0230, 6.5537
 SW_ISSUE_PER_BOND, SW_ISSUE_PER_BOND_PAIR = 387.123, 475.684
 # DRAM bytes (read + write) per launch of the current kernels at full size (ncu, one pass):
 # the fp64 pair pass (common-case launch) and the step gathers, eager launches (no fused drift)
-PAIR_TRAFFIC_BYTES = {"tersoff_c_graphene_1M": 160.13e6}
+PAIR_TRAFFIC_BYTES = {"tersoff_c_graphene_1M": 175.08e6}
 GATHER_TRAFFIC_BYTES = {"tersoff_c_graphene_1M": 165.57e6}
 GATHER_TRAFFIC_NOTE = "ncu, full size, eager step launch (no fused drift: 72 B/atom fewer than the model)"
 

@@ -68,8 +68,8 @@ def test_flop_model_reproduces_the_counted_launches():
     counts back (flop = DADD + DMUL + 2 DFMA; slots = warp instructions x 32, per atom)."""
     I_T, I_S = bench.I.MD_TERSOFF, bench.I.MD_SW
     for kind, bonds, pairs, flop, fp64, issue in [
-        (I_T, 3.0, 6.0, 150.138, 3.7299 * 32, 183.711 * 32),                       # C sheet
-        (I_T, 4.0, 12.0, 211.266, 5.2105 * 32, 267.208 * 32),                      # Si diamond
+        (I_T, 3.0, 6.0, 143.012, 3.482252 * 32, 180.557976 * 32),                 # C sheet
+        (I_T, 4.0, 12.0, 203.167, 4.958065 * 32, 276.845213 * 32),                # Si diamond
         (I_S, 4.0, 12.0, 196.250, 5.2105 * 32, (226.354 + 0.418) * 32),            # SW lattice
         (I_S, 5.1028, 21.8819, 253.672, (7.6748 + 0.3185) * 32, (383.923 + 3.086) * 32),  # SW, 300 K
     ]:
