@@ -185,23 +185,44 @@ __device__ __forceinline__ void cell_fill_atom(int64_t i, const int *atom_cell, 
     cell_atoms[cell_start[atom_cell[i]] + atom_rank[i]] = (int)i;
 }
 
-// distinct cell indices adjacent to c along one axis (periodic wrap or open clip)
-__device__ __forceinline__ int stencil_axis(int c, int nc, int periodic, int *out)
+// The stencil along one axis: the distinct cells c-1, c, c+1 (periodic: wrapped; open:
+// clipped) as at most two runs of consecutive indices [lo0, hi0], [lo1, hi1]; `full` when
+// they are every cell of the axis.  No integer division (the grid is not a power of two).
+struct AxisRuns {
+    int lo0, hi0, lo1, hi1, n;
+    bool full;
+};
+__device__ __forceinline__ AxisRuns axis_runs(int c, int nc, int periodic)
 {
-    int n = 0;
-#pragma unroll
-    for (int t = -1; t <= 1; ++t) {
-        int k = c + t;
-        if (periodic) {
-            k = (k + nc) % nc;
-        } else if (k < 0 || k >= nc) {
-            continue;
-        }
-        bool dup = false;
-        for (int u = 0; u < n; ++u) dup |= (out[u] == k);
-        if (!dup) out[n++] = k;
+    AxisRuns r{0, nc - 1, 0, 0, 1, true};
+    if (periodic) {
+        if (nc <= 3) return r;
+        r.full = false;
+        if (c == 0) { r.hi0 = 1; r.lo1 = r.hi1 = nc - 1; r.n = 2; }
+        else if (c == nc - 1) { r.lo0 = nc - 2; r.lo1 = r.hi1 = 0; r.n = 2; }
+        else { r.lo0 = c - 1; r.hi0 = c + 1; }
+    } else {
+        r.lo0 = c > 0 ? c - 1 : 0;
+        r.hi0 = c + 1 < nc ? c + 1 : nc - 1;
+        r.full = r.lo0 == 0 && r.hi0 == nc - 1;
     }
-    return n;
+    return r;
+}
+// Item k of an axis: one of its runs (whole runs: the axes inside it are full, so the run's
+// cells are one contiguous block of cell indices) or one of its cells.
+__device__ __forceinline__ int axis_items(const AxisRuns &r, bool whole)
+{
+    return whole ? r.n : (r.hi0 - r.lo0 + 1) + (r.n == 2 ? r.hi1 - r.lo1 + 1 : 0);
+}
+__device__ __forceinline__ void axis_item(const AxisRuns &r, bool whole, int k, int &lo, int &hi)
+{
+    if (whole) {
+        lo = k == 0 ? r.lo0 : r.lo1;
+        hi = k == 0 ? r.hi0 : r.hi1;
+    } else {
+        const int n0 = r.hi0 - r.lo0 + 1;
+        lo = hi = k < n0 ? r.lo0 + k : r.lo1 + (k - n0);
+    }
 }
 
 // fp32 candidate test of the list build for atom i (coordinates xi, yi, zi, largest
@@ -269,38 +290,62 @@ __device__ __forceinline__ int build_list_atom(int64_t i, int64_t N, const doubl
         nc[0] = sys[0].nc[0]; nc[1] = sys[0].nc[1]; nc[2] = sys[0].nc[2];
     }
     const Box &box = *bp;
-    pos_build[i] = pos[i];
-    pos_build[N + i] = pos[N + i];
-    pos_build[2 * N + i] = pos[2 * N + i];
+    const double b0 = pos[i], b1 = pos[N + i], b2 = pos[2 * N + i];
     const ListFrame fr = list_frame(posf, N, i, box, rlm2);
-    const int c = (int)(atom_cell[i] - off);
-    const int cz = c % nc[2], cy = (c / nc[2]) % nc[1], cx = c / (nc[1] * nc[2]);
-    int ox[3], oy[3], oz[3];
-    const int nx = stencil_axis(cx, nc[0], box.pbc[0], ox);
-    const int ny = stencil_axis(cy, nc[1], box.pbc[1], oy);
-    const int nz = stencil_axis(cz, nc[2], box.pbc[2], oz);
-    // the stencil cells' ranges first (independent loads), then their atoms as one
-    // sequence taken four at a time, so that four candidates' loads are in flight
-    const int ns = nx * ny * nz;
-    int cs[27], ce[27];
-    for (int l = 0; l < ns; ++l) {
-        const int a = l / (ny * nz), b = (l / nz) % ny, e = l % nz;
-        const long long cc = off + ((long long)ox[a] * nc[1] + oy[b]) * nc[2] + oz[e];
-        cs[l] = cell_start[cc];
-        ce[l] = cs[l] + cell_count[cc];
-    }
+    // the atom's cell from its fp32 coordinates, as the count pass computed it
+    const int cx = cell_coord_f(fr.xi, nc[0], (float)nc[0] * d2f_trunc(box.invL[0]));
+    const int cy = cell_coord_f(fr.yi, nc[1], (float)nc[1] * d2f_trunc(box.invL[1]));
+    const int cz = cell_coord_f(fr.zi, nc[2], (float)nc[2] * d2f_trunc(box.invL[2]));
+    // The stencil as ranges of cell indices (cell = (x nc1 + y) nc2 + z): z in runs; y in
+    // runs when z is full, else cell by cell; x likewise when y and z are full.  A range's
+    // atoms are one contiguous block of cell_atoms.  On the sheet (one cell along z) the 9
+    // cells are 3 ranges.
+    const AxisRuns rx = axis_runs(cx, nc[0], box.pbc[0]);
+    const AxisRuns ry = axis_runs(cy, nc[1], box.pbc[1]);
+    const AxisRuns rz = axis_runs(cz, nc[2], box.pbc[2]);
+    const bool wy = rz.full, wx = rz.full && ry.full;
+    const int nX = axis_items(rx, wx), nY = axis_items(ry, wy), nZ = rz.n;
+    auto range_at = [&](int ix, int iy, int iz, int &q0, int &q1) {
+        int xl, xh, yl, yh, zl, zh;
+        axis_item(rx, wx, ix, xl, xh);
+        axis_item(ry, wy, iy, yl, yh);
+        axis_item(rz, true, iz, zl, zh);
+        const long long clo = off + ((long long)xl * nc[1] + yl) * nc[2] + zl;
+        const long long chi = off + ((long long)xh * nc[1] + yh) * nc[2] + zh;
+        q0 = cell_start[clo];
+        q1 = cell_start[chi] + cell_count[chi];
+    };
+    // odometer over the ranges; the next range's bounds are loaded one range ahead
+    auto step = [&](int &ix, int &iy, int &iz) {
+        if (++iz == nZ) {
+            iz = 0;
+            if (++iy == nY) {
+                iy = 0;
+                ++ix;
+            }
+        }
+        return ix < nX;
+    };
+    int q, qe, q2 = 0, qe2 = 0;
+    range_at(0, 0, 0, q, qe);
+    int jx = 0, jy = 0, jz = 0;
+    bool more = step(jx, jy, jz);
+    if (more) range_at(jx, jy, jz, q2, qe2);
     int loc[kMaxListCap];
     int cnt = 0;
-    int cell = 0, q = ns > 0 ? cs[0] : 0;
+    // the candidates as one sequence taken four at a time, so that four candidates' loads
+    // are in flight together
     while (true) {
         int jj[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            while (cell < ns && q >= ce[cell]) {
-                ++cell;
-                if (cell < ns) q = cs[cell];
+            while (q >= qe && more) {
+                q = q2;
+                qe = qe2;
+                more = step(jx, jy, jz);
+                if (more) range_at(jx, jy, jz, q2, qe2);
             }
-            jj[u] = cell < ns ? cell_atoms[q++] : -1;
+            jj[u] = q < qe ? cell_atoms[q++] : -1;
         }
         if (jj[0] < 0) break;
         float xs[4], ys[4], zs[4];
@@ -329,6 +374,9 @@ __device__ __forceinline__ int build_list_atom(int64_t i, int64_t N, const doubl
             }
         }
     }
+    pos_build[i] = b0;
+    pos_build[N + i] = b1;
+    pos_build[2 * N + i] = b2;
     const int keep = cnt < cap ? cnt : cap;
     for (int m = 0; m < keep; ++m) nl[(int64_t)m * N + i] = loc[m];
     nn[i] = keep;
