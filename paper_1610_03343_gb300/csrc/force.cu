@@ -698,8 +698,12 @@ __device__ __forceinline__ void tersoff_atom(const PairArgs<T> &a, const Tersoff
 // ---------------------------------------------------------- Stillinger-Weber
 enum { SW_UX, SW_UY, SW_UZ, SW_IR, SW_E, SW_DE, SW_DX, SW_DY, SW_DZ, SW_NF };
 
-template <int CAP>
-constexpr int sw_smem_fields() { return SW_NF * CAP; }
+// Shared-memory words per bond: the fp32 pass stages u, 1/r, E, dE/dr and the dU/dr
+// accumulators that the three-body loop scatters into (9); the fp64 pass's three-body loop
+// sums each bond's terms itself, starting from the two-body part it left in the output row,
+// so it stages the first six only (4 blocks of 128 resident instead of 3).
+template <typename T, int CAP>
+constexpr int sw_smem_fields() { return (sizeof(T) == 8 ? SW_DX : SW_NF) * CAP; }
 
 // Per-bond SW terms from r^2 and the bond vector: the unit vector u, 1/r, E = exp(gamma
 // sigma/(r - a sigma)) and dE/dr of the three-body factor, this bond's two-body share of U_i
@@ -776,8 +780,13 @@ __device__ __forceinline__ SWBondFF sw_bond_ff(const SWC<double> &p, double r2, 
 // derivative carries the factor t = cos + 1/3 (which vanishes at the tetrahedral angle) or
 // t^2, so an absolute error e in cos is an absolute error of about 2 lambda eps E E' e /r in
 // dU_i/dr_ij -- no cancellation amplifies it -- while the two-body part, whose two terms
-// cancel at the equilibrium bond length, stays fp64.  Staged fields and the scattered
-// dU/dr accumulators are float pairs; dU_i/dr_ij is stored as float pairs (bond_out).
+// cancel at the equilibrium bond length, stays fp64.  Each bond j sums the terms of its
+// pairs (j, k), k != j, itself, onto the two-body part that the per-bond loop stored in its
+// output row, so nothing is scattered into bond k's staging: per pair (j, k) the terms of
+// phi3's derivative along r_ij are
+//   2 lambda eps t E_j E_k dcos/dr_ij + lambda eps t^2 E_j' E_k u_j,
+// with dcos/dr_ij = (u_k - cos u_j)/r_ij; phi3 itself is added once per unordered pair.
+// dU_i/dr_ij is stored as float pairs (bond_out).
 template <int CAP, int BLOCK>
 __device__ __forceinline__ void sw_three_body_ff(const PairArgs<double> &a, const SWC<double> &p,
                                                  const Stage<double, CAP, BLOCK> &S, int na, int64_t i,
@@ -788,29 +797,28 @@ __device__ __forceinline__ void sw_three_body_ff(const PairArgs<double> &a, cons
     for (int j = 0; j < na; ++j) {
         const F2 ujx = ff_unpack(S(SW_UX, j)), ujy = ff_unpack(S(SW_UY, j)), ujz = ff_unpack(S(SW_UZ, j));
         const F2 irj = ff_unpack(S(SW_IR, j)), Ej = ff_unpack(S(SW_E, j)), dEj = ff_unpack(S(SW_DE, j));
-        F2 djx = ff_unpack(S(SW_DX, j)), djy = ff_unpack(S(SW_DY, j)), djz = ff_unpack(S(SW_DZ, j));
-        for (int k = j + 1; k < na; ++k) {
+        const Vec4<double> d2 = a.d[(int64_t)j * a.N + i];   // the two-body part
+        F2 djx = ff_unpack(d2.x), djy = ff_unpack(d2.y), djz = ff_unpack(d2.z);
+        for (int k = 0; k < na; ++k) {
+            if (k == j) continue;
             const F2 ukx = ff_unpack(S(SW_UX, k)), uky = ff_unpack(S(SW_UY, k)), ukz = ff_unpack(S(SW_UZ, k));
-            const F2 irk = ff_unpack(S(SW_IR, k)), Ek = ff_unpack(S(SW_E, k)), dEk = ff_unpack(S(SW_DE, k));
+            const F2 Ek = ff_unpack(S(SW_E, k));
             F2 cs = ff_mul(ujx, ukx);
             cs = ff_fma(ujy, uky, cs);
             cs = ff_fma(ujz, ukz, cs);
             const F2 t = ff_add(cs, third);
             const F2 EE = ff_mul(Ej, Ek);
             const F2 lt = ff_mul(lameps, t), lt2 = ff_mul(lt, t);
-            u3 = ff_fma(lt2, EE, u3);
+            if (k > j) u3 = ff_fma(lt2, EE, u3);
             F2 c1 = ff_mul(lt, EE);
             c1 = F2{2.f * c1.h, 2.f * c1.l};
-            const F2 cj = ff_mul(ff_mul(lt2, dEj), Ek), ck = ff_mul(ff_mul(lt2, Ej), dEk);
-            const F2 qj = ff_mul(c1, irj), qk = ff_mul(c1, irk);
+            const F2 cj = ff_mul(ff_mul(lt2, dEj), Ek);
+            const F2 qj = ff_mul(c1, irj);
             // d_j += qj (u_k - cos u_j) + cj u_j, written as qj u_k + (cj - qj cos) u_j
-            const F2 aj = ff_fma(ff_neg(qj), cs, cj), ak = ff_fma(ff_neg(qk), cs, ck);
+            const F2 aj = ff_fma(ff_neg(qj), cs, cj);
             djx = ff_fma(qj, ukx, ff_fma(aj, ujx, djx));
             djy = ff_fma(qj, uky, ff_fma(aj, ujy, djy));
             djz = ff_fma(qj, ukz, ff_fma(aj, ujz, djz));
-            S(SW_DX, k) = ff_pack(ff_fma(qk, ujx, ff_fma(ak, ukx, ff_unpack(S(SW_DX, k)))));
-            S(SW_DY, k) = ff_pack(ff_fma(qk, ujy, ff_fma(ak, uky, ff_unpack(S(SW_DY, k)))));
-            S(SW_DZ, k) = ff_pack(ff_fma(qk, ujz, ff_fma(ak, ukz, ff_unpack(S(SW_DZ, k)))));
         }
         a.d[(int64_t)j * a.N + i] = Vec4<double>{ff_pack(djx), ff_pack(djy), ff_pack(djz), 0.0};
     }
@@ -839,9 +847,8 @@ __device__ __forceinline__ void sw_terms(const PairArgs<T> &a, const SWC<T> &p, 
             S(SW_E, k) = ff_pack(b.E);
             S(SW_DE, k) = ff_pack(b.dE);
             ui += b.u2;
-            S(SW_DX, k) = ff_pack(b.dx);
-            S(SW_DY, k) = ff_pack(b.dy);
-            S(SW_DZ, k) = ff_pack(b.dz);
+            // the two-body part, in the output row until the three-body loop adds to it
+            a.d[(int64_t)k * N + i] = Vec4<double>{ff_pack(b.dx), ff_pack(b.dy), ff_pack(b.dz), 0.0};
         } else {
             const SWBond<T> b = sw_bond(p, S(SW_IR, k), S(SW_UX, k), S(SW_UY, k), S(SW_UZ, k));
             S(SW_UX, k) = b.ux; S(SW_UY, k) = b.uy; S(SW_UZ, k) = b.uz; S(SW_IR, k) = b.ir;
@@ -1763,7 +1770,7 @@ constexpr int kGatherBlock = 128;
 template <typename T, int CAP, int BLOCK, bool MULTI = false>
 size_t smem_for(int kind)
 {
-    const int nf = kind == 1 ? tersoff_smem_fields<T, CAP, MULTI>() : sw_smem_fields<CAP>();
+    const int nf = kind == 1 ? tersoff_smem_fields<T, CAP, MULTI>() : sw_smem_fields<T, CAP>();
     return (size_t)nf * BLOCK * sizeof(T);
 }
 
