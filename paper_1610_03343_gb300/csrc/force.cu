@@ -1276,12 +1276,12 @@ __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, i
         constexpr bool FFG = sizeof(T) == 8;
         F2 ff[3] = {}, fw[9] = {}, fwd[3] = {};
         int k = 0;
-        // fp64 heat current (second walk): an atom with at most four bonds keeps its one
-        // group's partners and their rows, so the second walk needs no list, mask or
-        // reverse-slot loads
-        const bool one_group = __popc(mask) <= 4;
-        int js[4], krs[4];
-        int n1 = 0;
+        // fp64 heat current (second walk): an atom with at most eight bonds keeps its two
+        // groups' partners and their rows (j | row << kAtomBits), so the second walk needs no
+        // list, mask or reverse-slot loads
+        const bool kept = __popc(mask) <= 8;
+        int jk0[4], jk1[4];
+        int n0 = 0, n1 = 0;
         // bonds in groups of four: the group's list entries and reverse slots, then its
         // partners' masks, then the partners' rows, each a batch of independent loads (three
         // dependent round trips per group instead of two per bond)
@@ -1289,7 +1289,7 @@ __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, i
             int jg[4], mrg[4];
             uint32_t mjg[4];
             int ng = 0;
-            const bool first = k == 0;
+            const int grp = k >> 2;   // k is a multiple of 4 here
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 if (mask != 0u && k + u < MAXA) {
@@ -1308,9 +1308,11 @@ __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, i
                 if (u >= ng) break;
                 const int j = jg[u];
                 const int kr = __popc(mjg[u] & ((1u << mrg[u]) - 1u));
-                if (JPASS && first) {
-                    js[u] = j;
-                    krs[u] = kr;
+                if (JPASS && grp == 0) {
+                    jk0[u] = j | (kr << kAtomBits);
+                    n0 = u + 1;
+                } else if (JPASS && grp == 1) {
+                    jk1[u] = j | (kr << kAtomBits);
                     n1 = u + 1;
                 }
                 if (FFG && kr < MAXA) {
@@ -1442,11 +1444,18 @@ __device__ __forceinline__ void gather_atom(const GatherArgs<T> &a, int64_t i, i
                 for (int c = 0; c < 3; ++c)
                     fj[c] = ff_fma(ff_unpack(a.r[(int64_t)(c * MAXA + kb) * N + i]), dv, fj[c]);
             };
-            uint32_t m2 = one_group ? 0u : a.mask[i];
-            if (one_group) {
+            uint32_t m2 = kept ? 0u : a.mask[i];
+            if (kept) {
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (u < n1 && krs[u] < MAXA) jbond(u, js[u], krs[u]);
+                for (int u = 0; u < 4; ++u) {
+                    const int kr = (unsigned)jk0[u] >> kAtomBits;
+                    if (u < n0 && kr < MAXA) jbond(u, jk0[u] & kAtomMask, kr);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int kr = (unsigned)jk1[u] >> kAtomBits;
+                    if (u < n1 && kr < MAXA) jbond(4 + u, jk1[u] & kAtomMask, kr);
+                }
             }
             int k2 = 0;
             while (m2 != 0u && k2 < MAXA) {   // grouped as in the first walk
