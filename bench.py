@@ -105,7 +105,10 @@ def gather_bytes_algorithmic(bonds: float, fused: bool = True, elem: int = 4) ->
 # states each -- Tersoff: the C sheet (3 bonds, 6 ordered pairs; the 3-bond staging the
 # autotuner picks there) and Si diamond (4, 12; the 4-bond staging);
 # SW: the Si lattice (4, 12) and the crystal after 100 fs at 300 K (5.1028, 21.8819; the
-# common-case and full-capacity launches together).
+# common-case and full-capacity launches together, at the block of 32 the autotuner picks).
+# The SW slot coefficients interpolate the two states: they are not costs of a bond and a
+# pair (the per-bond ones come out negative), since the thermal state's warps also mix atoms
+# of different bond counts, which the lattice's do not.
 #   FLOP: DADD + DMUL + 2 DFMA thread instructions (the fp64 arithmetic that is left: the
 #         bond geometry, the radial functions and the fp64 steps of exp, log, 1/r);
 #   FP64: fp64-pipe issue slots (smsp__inst_executed_pipe_fp64 x 32);
@@ -114,13 +117,13 @@ def gather_bytes_algorithmic(bonds: float, fused: bool = True, elem: int = 4) ->
 TERSOFF_FLOP_PER_BOND, TERSOFF_FLOP_PER_BOND_PAIR = 41.4287, 3.12099
 TERSOFF_FP64_PER_BOND, TERSOFF_FP64_PER_BOND_PAIR = 32.1030, 2.52050
 TERSOFF_ISSUE_PER_BOND, TERSOFF_ISSUE_PER_BOND_PAIR = 1348.332, 288.810
-SW_FLOP_PER_BOND, SW_FLOP_PER_BOND_PAIR = 47.5492, 0.50443
-SW_FP64_PER_BOND, SW_FP64_PER_BOND_PAIR = 22.0230, 6.5537
-SW_ISSUE_PER_BOND, SW_ISSUE_PER_BOND_PAIR = 387.123, 475.684
+SW_FLOP_PER_BOND, SW_FLOP_PER_BOND_PAIR = 47.5489, 0.504533
+SW_FP64_PER_BOND, SW_FP64_PER_BOND_PAIR = -0.621724, 14.185241
+SW_ISSUE_PER_BOND, SW_ISSUE_PER_BOND_PAIR = -2076.496, 1343.6406
 # DRAM bytes (read + write) per launch of the current kernels at full size (ncu, one pass):
 # the fp64 pair pass (common-case launch) and the step gathers, eager launches (no fused drift)
 PAIR_TRAFFIC_BYTES = {"tersoff_c_graphene_1M": 175.08e6}
-GATHER_TRAFFIC_BYTES = {"tersoff_c_graphene_1M": 165.57e6}
+GATHER_TRAFFIC_BYTES = {"tersoff_c_graphene_1M": 167.58e6}
 GATHER_TRAFFIC_NOTE = "ncu, full size, eager step launch (no fused drift: 72 B/atom fewer than the model)"
 
 

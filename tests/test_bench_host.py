@@ -70,8 +70,8 @@ def test_flop_model_reproduces_the_counted_launches():
     for kind, bonds, pairs, flop, fp64, issue in [
         (I_T, 3.0, 6.0, 143.012, 3.482252 * 32, 180.557976 * 32),                 # C sheet
         (I_T, 4.0, 12.0, 203.167, 4.958065 * 32, 276.845213 * 32),                # Si diamond
-        (I_S, 4.0, 12.0, 196.250, 5.2105 * 32, (226.354 + 0.418) * 32),            # SW lattice
-        (I_S, 5.1028, 21.8819, 253.672, (7.6748 + 0.3185) * 32, (383.923 + 3.086) * 32),  # SW, 300 K
+        (I_S, 4.0, 12.0, 196.250, 5.241750 * 32, (243.885 + 0.418) * 32),          # SW lattice
+        (I_S, 5.1028, 21.8819, 253.673, (9.282328 + 0.318531) * 32, (584.584 + 3.086) * 32),  # SW, 300 K
     ]:
         assert bench.pair_flops(kind, bonds, pairs) == pytest.approx(flop, abs=0.02)
         s64, sall = bench.pair_slots(kind, bonds, pairs)
