@@ -341,6 +341,30 @@ void coarsen_sparse_axes(const double *const xyz[3], int64_t n, const Box &box, 
     }
 }
 
+// coarsen_sparse_axes for a single system's positions on the device (host or device IO):
+// one pass over the atoms flags the occupied cells of each axis (launch_axis_occupancy) and
+// the host counts them.
+md_status coarsen_sparse_axes_dev(md_ctx *ctx, int nc[3])
+{
+    Plan &p = ctx->p;
+    if (!p.occ || p.N <= 0) return MD_OK;
+    const int n0 = nc[0], n1 = nc[1], n2 = nc[2], tot = n0 + n1 + n2;
+    CK(cudaMemsetAsync(p.occ, 0, (size_t)tot, ctx->stream));
+    launch_axis_occupancy(p, ctx->stream, p.box, nc, p.occ);
+    CK(cudaGetLastError());
+    std::vector<uint8_t> h((size_t)tot);
+    CK(cudaMemcpyAsync(h.data(), p.occ, (size_t)tot, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    const int off[3] = {0, n0, n0 + n1}, len[3] = {n0, n1, n2};
+    for (int a = 0; a < 3; ++a) {
+        if (len[a] < 4) continue;
+        int used = 0;
+        for (int c = 0; c < len[a]; ++c) used += h[(size_t)(off[a] + c)] != 0;
+        if (4 * used <= len[a]) nc[a] = 1;
+    }
+    return MD_OK;
+}
+
 // half-kick factors dt/2 * acc / m per type (same expression order as the oracle)
 void half_kick(const md_ctx *ctx, double dt, double *hk)
 {
@@ -799,6 +823,7 @@ md_status ctx_alloc(md_ctx *ctx)
         if (st != MD_OK) return st;
         p.pr = v;
     }
+    if (!p.batch) AL(p.occ, (size_t)ctx->nc_full[0] + ctx->nc_full[1] + ctx->nc_full[2]);
     AL(p.cell_count, p.ncell);
     AL(p.cell_start, p.ncell);
     AL(p.cell_atoms, N1);
@@ -1218,10 +1243,7 @@ md_status md_set_positions(md_ctx *ctx, const double *x, const double *y, const 
                 const int fit = (int)std::floor(ctx->p.box.L[a] / ctx->sys_host[0].cell_edge);
                 nc[a] = std::max(1, std::min(nc[a], fit));
             }
-        if (ctx->io == MD_IO_HOST) {
-            const double *xyz[3] = {x, y, z};
-            coarsen_sparse_axes(xyz, ctx->p.N, ctx->p.box, nc);
-        }
+        if ((s = coarsen_sparse_axes_dev(ctx, nc)) != MD_OK) return s;
         if (nc[0] != ctx->p.nc[0] || nc[1] != ctx->p.nc[1] || nc[2] != ctx->p.nc[2]) {
             for (int a = 0; a < 3; ++a) ctx->p.nc[a] = nc[a];
             ctx->p.ncell = (int64_t)nc[0] * nc[1] * nc[2];

@@ -67,6 +67,7 @@ struct Plan {
     int nc[3] = {1, 1, 1};
     int64_t ncell = 1;
     int *cell_count = nullptr, *cell_start = nullptr, *cell_atoms = nullptr;
+    uint8_t *occ = nullptr;     // single system: per-axis cell occupancy (nc0 + nc1 + nc2 flags)
     int *atom_cell = nullptr, *atom_rank = nullptr, *scan_blocks = nullptr;
     int64_t nscanb = 1;
     int *rb_plan = nullptr, *rb_sys = nullptr, *rb_chunks = nullptr;   // pool rebuild work lists
@@ -108,6 +109,10 @@ int launch_rebuild(const Plan &p, cudaStream_t s);
 void launch_displacement_check(const Plan &p, cudaStream_t s);
 // dst[a N + i] = positions of atoms [a0, a0 + n) wrapped into [0, L) on periodic axes.
 void launch_wrap_copy(const Plan &p, cudaStream_t s, double *dst, int64_t a0, int64_t n);
+// Per-axis cell occupancy of the single system's positions for the grid nc in `box`:
+// occ[off_a + c] = 1 where an atom's cell coordinate along axis a is c (off_0 = 0,
+// off_1 = nc0, off_2 = nc0 + nc1); the caller clears occ first.
+void launch_axis_occupancy(const Plan &p, cudaStream_t s, const Box &box, const int nc[3], uint8_t *occ);
 
 // force.cu
 // Multi-element Tersoff: bytes of the device table of pair constants, and the table

@@ -644,6 +644,24 @@ __global__ void k_displacement(int64_t N, const double *pos, const double *pos_b
     }
 }
 
+// Per-axis cell occupancy (see launch_axis_occupancy): each atom flags the cell it falls in
+// along each axis (the same coordinate as the count pass: wrapped on periodic axes).
+__global__ void k_axis_occupancy(int64_t N, const double *pos, Box box, int nc0, int nc1, int nc2, uint8_t *occ)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int nc[3] = {nc0, nc1, nc2};
+    int off = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double x = pos[a * N + i];
+        if (box.pbc[a]) x = wrap_coord(x, box.L[a], box.invL[a]);
+        const float xf = d2f_trunc(x);
+        occ[off + cell_coord_f(xf, nc[a], (float)nc[a] * d2f_trunc(box.invL[a]))] = 1;
+        off += nc[a];
+    }
+}
+
 // Wrapped copy of the positions (for output): dst[3N] = pos wrapped into [0, L).
 template <bool BATCH>
 __global__ void k_wrap_copy(int64_t N, int64_t a0, int64_t n, const double *pos, double *dst, Box box0,
@@ -749,6 +767,12 @@ void launch_displacement_check(const Plan &p, cudaStream_t s)
     else
         k_displacement<false><<<blocks_for(p.N, T), T, 0, s>>>(p.N, p.pos, p.pos_build, (float)(hs * hs),
                                                               p.sys_of, p.sys, p.npt ? 1 : 0, p.flags);
+}
+
+void launch_axis_occupancy(const Plan &p, cudaStream_t s, const Box &box, const int nc[3], uint8_t *occ)
+{
+    if (p.N <= 0) return;
+    k_axis_occupancy<<<blocks_for(p.N, 256), 256, 0, s>>>(p.N, p.pos, box, nc[0], nc[1], nc[2], occ);
 }
 
 void launch_wrap_copy(const Plan &p, cudaStream_t s, double *dst, int64_t a0, int64_t n)
