@@ -206,8 +206,9 @@ typedef struct {
                                  half-kick fused into the previous step's gather)         */
     int kernel_launches_per_rebuild; /* extra kernels of a step that rebuilds the list */
     int pair_deferred;       /* atoms with more in-cutoff bonds than the common-case pass
-                                stages (Tersoff 4, SW 8; the fp64 3-bond staging also
-                                defers atoms with a bond in f_C's switching region) at the
+                                stages (Tersoff 4, SW 8; the fp64 single-element Tersoff
+                                stagings also defer atoms with a bond in f_C's switching
+                                region) at the
                                 last pair pass, handled by the full-capacity pass (SW: one
                                 warp per atom)                                          */
     size_t device_bytes;     /* bytes the context has allocated on the device         */
@@ -239,10 +240,10 @@ md_status md_set_graph_mode(md_ctx *ctx, int use_graphs);
  *                       fp64 Tersoff context (one element): 3 or 4 (0 = 4).  Atoms with
  *                       more in-cutoff bonds go to the full-capacity pass, computed the same
  *                       way; 3 leaves room for more resident warps when most atoms have 3
- *                       bonds (the honeycomb sheet).  The 3-bond staging keeps no f_C
- *                       values: an atom with a bond in the switching region R <= r < S
- *                       also goes to the full-capacity pass.  Other contexts stage 4
- *                       (Tersoff) or 8 (SW) whatever it is.
+ *                       bonds (the honeycomb sheet).  The fp64 single-element stagings
+ *                       (3 or 4 bonds; pools: 4) keep no f_C values: an atom with a bond
+ *                       in the switching region R <= r < S also goes to the full-capacity
+ *                       pass.  Other contexts stage 4 (Tersoff) or 8 (SW) whatever it is.
  * md_autotune times each candidate on the context's current state with CUDA events on
  * its stream -- pair_block over {32, 64, 128, 256} (for each pair_cap where there is a
  * choice) with the pair pass alone, then (pools)

@@ -378,13 +378,14 @@ template <typename T, bool MULTI>
 constexpr int kTersoffBondFields = sizeof(T) == 8 ? TF_FA + (MULTI ? 1 : 0) : TF_NF;
 template <typename T>
 constexpr int kTersoffTypeField = sizeof(T) == 8 ? TF_FA : TF_DX;
-// The fp64 3-bond staging (single element) keeps no f_C and f_C' fields: an atom with a bond
-// in the switching region R <= r < S goes to the full-capacity pass, like an atom with more
-// than three bonds, and the common pass's bonds all have f_C = 1, f_C' = 0.  Its r (then the
-// radial term) and zeta (then P) take the slots of f_C and f_C': six fields a bond, 24 shared
-// words a thread with the three pair slots' float pairs (32 warps per SM at 256 threads).
+// The fp64 common-case staging of 3 or 4 bonds (single element) keeps no f_C and f_C'
+// fields: an atom with a bond in the switching region R <= r < S goes to the full-capacity
+// pass, like an atom with more bonds than the staging holds, and the common pass's bonds all
+// have f_C = 1, f_C' = 0.  Its r (then the radial term) and zeta (then P) take the slots of
+// f_C and f_C': six fields a bond -- 24 shared words a thread with 3 bonds (32 warps per SM
+// at 256 threads), 36 with 4 (22 warps at 64 threads instead of 18).
 template <typename T, int CAP, bool MULTI>
-constexpr bool kTersoffNoSwitch = sizeof(T) == 8 && CAP == 3 && !MULTI;
+constexpr bool kTersoffNoSwitch = sizeof(T) == 8 && CAP <= 4 && !MULTI;
 template <bool NOSW>
 constexpr int kTfFR = NOSW ? TF_FC : TF_FR;
 template <bool NOSW>
