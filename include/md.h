@@ -208,9 +208,8 @@ typedef struct {
     int pair_deferred;       /* atoms with more in-cutoff bonds than the common-case pass
                                 stages (Tersoff 4, SW 8; the fp64 single-element Tersoff
                                 stagings also defer atoms with a bond in f_C's switching
-                                region) at the
-                                last pair pass, handled by the full-capacity pass (SW: one
-                                warp per atom)                                          */
+                                region) at the last pair pass, handled by the
+                                full-capacity pass (SW: one warp per atom)              */
     size_t device_bytes;     /* bytes the context has allocated on the device         */
     int64_t atoms_rebuilt;   /* atoms whose neighbour list was built, summed over builds
                                 (pools: only the systems that needed a rebuild)          */
