@@ -242,7 +242,11 @@ md_status md_set_graph_mode(md_ctx *ctx, int use_graphs);
  *                       bonds (the honeycomb sheet).  The fp64 single-element stagings
  *                       (3 or 4 bonds; pools: 4) keep no f_C values: an atom with a bond
  *                       in the switching region R <= r < S also goes to the full-capacity
- *                       pass.  Other contexts stage 4 (Tersoff) or 8 (SW) whatever it is.
+ *                       pass.  When the last pair pass of an md_run call deferred more
+ *                       than 1/16 of the atoms (a liquid, a hot amorphous state), the
+ *                       context's later calls stage 4 bonds with f_C instead, and pair_cap
+ *                       reads 4.  Other contexts stage 4 (Tersoff) or 8 (SW) whatever it
+ *                       is.
  * md_autotune times each candidate on the context's current state with CUDA events on
  * its stream -- pair_block over {32, 64, 128, 256} (for each pair_cap where there is a
  * choice) with the pair pass alone, then (pools)

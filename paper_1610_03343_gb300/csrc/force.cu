@@ -384,16 +384,18 @@ constexpr int kTersoffTypeField = sizeof(T) == 8 ? TF_FA : TF_DX;
 // have f_C = 1, f_C' = 0.  Its r (then the radial term) and zeta (then P) take the slots of
 // f_C and f_C': six fields a bond -- 24 shared words a thread with 3 bonds (32 warps per SM
 // at 256 threads), 36 with 4 (22 warps at 64 threads instead of 18).
-template <typename T, int CAP, bool MULTI>
-constexpr bool kTersoffNoSwitch = sizeof(T) == 8 && CAP <= 4 && !MULTI;
+// FC: the 4-bond staging that keeps f_C after all (a context switches to it where many atoms
+// have bonds in the switching region, which the stagings without f_C would all defer).
+template <typename T, int CAP, bool MULTI, bool FC = false>
+constexpr bool kTersoffNoSwitch = sizeof(T) == 8 && CAP <= 4 && !MULTI && !FC;
 template <bool NOSW>
 constexpr int kTfFR = NOSW ? TF_FC : TF_FR;
 template <bool NOSW>
 constexpr int kTfZ = NOSW ? TF_DFC : TF_Z;
-template <typename T, int CAP, bool MULTI = false>
+template <typename T, int CAP, bool MULTI = false, bool FC = false>
 constexpr int tersoff_smem_fields()
 {
-    return (kTersoffNoSwitch<T, CAP, MULTI> ? TF_FC + 2 : kTersoffBondFields<T, MULTI>) * CAP +
+    return (kTersoffNoSwitch<T, CAP, MULTI, FC> ? TF_FC + 2 : kTersoffBondFields<T, MULTI>) * CAP +
            (sizeof(T) == 8 ? 2 : 1) * (CAP * (CAP - 1) / 2);
 }
 
@@ -496,13 +498,13 @@ __device__ __forceinline__ void tersoff_angular_ff(const PairArgs<double> &a, co
 // Pair pass for one atom (Tersoff).  MULTI: p holds atom i's element constants (angular
 // and bond-order) and row its pair-constant row; each bond's radial functions and cutoff
 // take the pair's constants (chi folded into B).
-template <typename T, int CAP, int BLOCK, bool FULL_CAP, bool MULTI = false>
+template <typename T, int CAP, int BLOCK, bool FULL_CAP, bool MULTI = false, bool FC = false>
 __device__ __forceinline__ void tersoff_atom(const PairArgs<T> &a, const TersoffC<T> &p, const Box &box, T *base,
                                              int64_t i, const TersoffC<T> *row = nullptr)
 {
     const int64_t N = a.N;
     Stage<T, CAP, BLOCK> S{base, (int)threadIdx.x};
-    constexpr bool NOSW = kTersoffNoSwitch<T, CAP, MULTI>;
+    constexpr bool NOSW = kTersoffNoSwitch<T, CAP, MULTI, FC>;
     static_assert(!(NOSW && FULL_CAP), "the full-capacity pass stages f_C");
     constexpr int FRF = kTfFR<NOSW>, ZF = kTfZ<NOSW>;
     // per unordered bond pair q: fp64, h - cos theta and dg/dcos from the zeta loop (float
@@ -1075,7 +1077,7 @@ __device__ __forceinline__ void pair_dispatch(const PairArgs<T> &a, const Sets &
     }
 }
 
-template <typename T, int CAP, int BLOCK, bool FULL_CAP, bool BATCH, bool MULTI = false>
+template <typename T, int CAP, int BLOCK, bool FULL_CAP, bool BATCH, bool MULTI = false, bool FC = false>
 __global__ void __launch_bounds__(BLOCK) k_pair_tersoff(PairArgs<T> a, TersoffSets<T> ps)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1089,7 +1091,7 @@ __global__ void __launch_bounds__(BLOCK) k_pair_tersoff(PairArgs<T> a, TersoffSe
             const TersoffC<T> own = row[ti];
             tersoff_atom<T, CAP, BLOCK, FULL_CAP, true>(a, own, box, base, i, row);
         } else {
-            tersoff_atom<T, CAP, BLOCK, FULL_CAP>(a, p, box, base, i);
+            tersoff_atom<T, CAP, BLOCK, FULL_CAP, false, FC>(a, p, box, base, i);
         }
     });
 }
@@ -1777,10 +1779,10 @@ constexpr int kPairCapSmallSW = 8;
 constexpr int kPairBlockFull = 32;   // full-capacity pass over the deferred atoms
 constexpr int kGatherBlock = 128;
 
-template <typename T, int CAP, int BLOCK, bool MULTI = false>
+template <typename T, int CAP, int BLOCK, bool MULTI = false, bool FC = false>
 size_t smem_for(int kind)
 {
-    const int nf = kind == 1 ? tersoff_smem_fields<T, CAP, MULTI>() : sw_smem_fields<T, CAP>();
+    const int nf = kind == 1 ? tersoff_smem_fields<T, CAP, MULTI, FC>() : sw_smem_fields<T, CAP>();
     return (size_t)nf * BLOCK * sizeof(T);
 }
 
@@ -1795,6 +1797,9 @@ void set_smem()
     if constexpr (!BATCH)
         cudaFuncSetAttribute(k_pair_tersoff<T, CAP, BLOCK, FULL_CAP, false, true>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_for<T, CAP, BLOCK, true>(1));
+    if constexpr (sizeof(T) == 8 && CAP == kPairCapSmall && !FULL_CAP)
+        cudaFuncSetAttribute(k_pair_tersoff<T, CAP, BLOCK, false, BATCH, false, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_for<T, CAP, BLOCK, false, true>(1));
 }
 
 template <typename T, int B, bool BATCH>
@@ -1872,7 +1877,14 @@ void pair_launch_b(const Plan &p, cudaStream_t s, int list, int parts)
                     k_pair_tersoff<T, kPairCapSmall3, B, false, false>
                         <<<nb, B, smem_for<T, kPairCapSmall3, B>(1), s>>>(a, c);
             }
-            if (!fast3)
+            bool keep_fc = false;
+            if constexpr (sizeof(T) == 8) {
+                keep_fc = !fast3 && p.pair_fc;
+                if (keep_fc)
+                    k_pair_tersoff<T, kPairCapSmall, B, false, BATCH, false, true>
+                        <<<nb, B, smem_for<T, kPairCapSmall, B, false, true>(1), s>>>(a, c);
+            }
+            if (!fast3 && !keep_fc)
                 k_pair_tersoff<T, kPairCapSmall, B, false, BATCH><<<nb, B, smem_for<T, kPairCapSmall, B>(1), s>>>(a, c);
         }
         if (parts & PAIR_DEFERRED)
@@ -2000,7 +2012,7 @@ bool valid_pair_block(int b) { return b == 32 || b == 64 || b == 128 || b == 256
 // everywhere else the common-case pass stages 4 (Tersoff) or 8 (SW) bonds.
 int effective_pair_cap(const Plan &p)
 {
-    const bool can3 = p.kind == 1 && p.precision == 0 && !p.batch && !p.multi;
+    const bool can3 = p.kind == 1 && p.precision == 0 && !p.batch && !p.multi && !p.pair_fc;
     return (can3 && p.pair_cap == kPairCapSmall3) ? kPairCapSmall3 : kPairCapSmall;
 }
 

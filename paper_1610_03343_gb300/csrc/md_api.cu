@@ -365,6 +365,26 @@ md_status coarsen_sparse_axes_dev(md_ctx *ctx, int nc[3])
     return MD_OK;
 }
 
+// fp64 single-element Tersoff: the common-case stagings without f_C send every atom with a
+// bond in the switching region R <= r < S to the full-capacity pass, which suits crystals
+// (none at room temperature) but not liquids or hot amorphous states.  When the last pair
+// pass of a call deferred more than 1/16 of the atoms, later calls use the 4-bond staging
+// that keeps f_C.  Every staging computes each atom the same way, so results do not change.
+md_status adapt_staging(md_ctx *ctx)
+{
+    Plan &p = ctx->p;
+    if (p.kind != 1 || p.precision != MD_FP64 || p.multi || p.pair_fc || p.N <= 0) return MD_OK;
+    int deferred = 0;
+    CK(cudaMemcpyAsync(&deferred, p.ovf_count, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    const int64_t n = p.n_owned >= 0 ? p.n_owned : p.N;
+    if ((int64_t)deferred * 16 > n) {
+        p.pair_fc = true;
+        destroy_graph(ctx);
+    }
+    return MD_OK;
+}
+
 // half-kick factors dt/2 * acc / m per type (same expression order as the oracle)
 void half_kick(const md_ctx *ctx, double dt, double *hk)
 {
@@ -1371,7 +1391,7 @@ md_status md_run(md_ctx *ctx, int64_t n_steps, double dt_fs, double *series)
         ctx->forces_valid = false;
         return s;
     }
-    return MD_OK;
+    return adapt_staging(ctx);
 }
 
 md_status md_set_npt(md_ctx *ctx, int system, const md_npt *npt)

@@ -26,6 +26,9 @@ struct Plan {
     int pair_block = 0;
     int pool_bps = 16;
     int pair_cap = 0;    // bond slots of the common-case Tersoff pass (0: default 4; 3)
+    // fp64 single-element Tersoff: the common-case pass keeps f_C (4 bonds) instead of
+    // deferring every atom with a bond in the switching region (set when those are many)
+    bool pair_fc = false;
     int n_sm = 152;
     // parameter sets (a single system uses set 0)
     int n_sets = 1;

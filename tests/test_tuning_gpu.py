@@ -179,3 +179,26 @@ def test_three_bond_staging_defers_bonds_in_the_switching_region(md):
                 assert np.abs(out[k] - ref[k]).max() / den < 1e-12, k
     for a, b in zip(got[3], got[4]):
         assert np.array_equal(a, b)
+
+
+def test_many_switching_bonds_switch_to_the_staging_with_fc(md):
+    """Where most atoms have a bond in the switching region (the stretched sheet: 300 of 384),
+    the stagings without f_C defer them all; after the first md_run call the context stages
+    4 bonds with f_C, defers none, and the trajectory goes on exactly as the oracle's."""
+    import oracle as O
+    s = I.c_graphene_tersoff(nx=8, ny=12, a_cc=1.78, jitter_amp=0.06, seed_pos=21, seed_vel=22)
+    with md.from_inputs(s, precision=0) as g:
+        md.md_set_tuning(g.ctx, pair_block=64, pair_cap=3)
+        ser1 = g.run(4, 0.5)
+        assert md.md_get_tuning(g.ctx).pair_cap == 4
+        ser2 = g.run(4, 0.5)
+        assert g.stats().pair_deferred == 0
+        x, v = g.state()
+    p2, v2, ser_ref = O.run(s.pos, s.vel, s.mass, s.box, s.pbc, s.kind, s.params, 8, 0.5)
+    d = x - p2
+    d -= np.round(d / s.box) * s.box
+    assert np.abs(d).max() < 1e-10
+    assert np.abs(v - v2).max() / np.abs(v2).max() < 1e-10
+    ser = np.concatenate([ser1, ser2])
+    for c in range(5):
+        assert np.abs(ser[:, c] - ser_ref[:, c]).max() / np.abs(ser_ref[:, c]).max() < 1e-10, c
