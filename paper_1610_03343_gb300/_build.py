@@ -20,6 +20,12 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libmd.so")
 SOURCES = ["force.cu", "neigh.cu", "md_api.cu", "md_server.cu", "md_static.cu", "hcacf.cu", "peak.cu",
            "md_domain.cu"]
+# force.cu is compiled as four units (its fp64 kernels of single systems and of pools and its
+# fp32 kernels through the force_part_*.cu wrappers, and the rest) so that its large sets of
+# kernel instantiations compile in parallel
+UNITS = [("force_part_fp64.cu", [], "force_part_fp64.o"), ("force_part_fp64_pool.cu", [], "force_part_fp64_pool.o"),
+         ("force_part_fp32.cu", [], "force_part_fp32.o"), ("force.cu", ["-DMD_FORCE_PART=0"], "force.o")] + \
+        [(src, [], os.path.splitext(src)[0] + ".o") for src in SOURCES if src != "force.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -52,19 +58,20 @@ def build(force: bool = False, verbose: bool = False) -> str:
     common = [cc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
               "-I", INCLUDE, "-I", CSRC, "-Xptxas", "-v"]
 
-    def compile_one(src):
-        obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
-        cmd = common + ["-c", os.path.join(CSRC, src), "-o", obj]
+    def compile_one(unit):
+        src, defs, name = unit
+        obj = os.path.join(BUILD, name)
+        cmd = common + defs + ["-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
-            raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")
+            raise RuntimeError(f"nvcc failed for {src} {' '.join(defs)}:\n{r.stderr}")
         return obj, r.stderr
 
-    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        results = list(ex.map(compile_one, SOURCES))
+    with ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
+        results = list(ex.map(compile_one, UNITS))
     with open(os.path.join(BUILD, "ptxas.log"), "w") as f:
-        for (obj, log), src in zip(results, SOURCES):
-            f.write(f"==== {src}\n{log}\n")
+        for (obj, log), (src, defs, _) in zip(results, UNITS):
+            f.write(f"==== {src} {' '.join(defs)}\n{log}\n")
     tmp = LIB + f".{os.getpid()}.tmp"
     cmd = [cc, *ARCH, "-shared", "-cudart", "static", "-o", tmp] + [o for o, _ in results] + ["-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)

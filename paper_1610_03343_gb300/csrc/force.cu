@@ -30,7 +30,9 @@
 
 namespace mdk {
 
+#if !defined(MD_FORCE_PART) || MD_FORCE_PART == 0
 const char *kKernelClassNames[KC_COUNT] = {"kick_drift", "rebuild", "pair", "gather", "reduce"};
+#endif
 
 namespace {
 
@@ -1969,6 +1971,77 @@ void fill_table(const Plan &p, void *host)
 
 }  // namespace
 
+// The build compiles this file four times, so that its large sets of kernel instantiations
+// compile in parallel: MD_FORCE_PART 1 emits the fp64 launch code and kernels of single
+// systems, 3 those of pools, 2 the fp32 ones, 0 the rest (the entry points below, which call
+// into the others).  Without MD_FORCE_PART the file holds every part.
+void pair_dispatch_fp64(const Plan &p, cudaStream_t s, int list, int parts);
+void pair_dispatch_fp64_pool(const Plan &p, cudaStream_t s, int list, int parts);
+void pair_dispatch_fp32(const Plan &p, cudaStream_t s, int list, int parts);
+void gather_dispatch_fp64(const Plan &p, cudaStream_t s, const double *hk, double dt, bool full, bool fuse);
+void gather_dispatch_fp64_pool(const Plan &p, cudaStream_t s, const double *hk, double dt, bool full, bool fuse);
+void gather_dispatch_fp32(const Plan &p, cudaStream_t s, const double *hk, double dt, bool full, bool fuse);
+void configure_fp64();
+void configure_fp64_pool();
+void configure_fp32();
+
+#if !defined(MD_FORCE_PART) || MD_FORCE_PART == 1
+void pair_dispatch_fp64(const Plan &p, cudaStream_t s, int list, int parts)
+{
+    if (p.maxa <= 8) pair_launch<double, 8, false>(p, s, list, parts);
+    else pair_launch<double, 16, false>(p, s, list, parts);
+}
+void gather_dispatch_fp64(const Plan &p, cudaStream_t s, const double *hk, double dt, bool full, bool fuse)
+{
+    if (p.maxa <= 8) gather_launch<double, 8, false>(p, s, hk, dt, full, fuse);
+    else gather_launch<double, 16, false>(p, s, hk, dt, full, fuse);
+}
+void configure_fp64() { configure_type<double, false>(); }
+#endif
+
+#if !defined(MD_FORCE_PART) || MD_FORCE_PART == 3
+void pair_dispatch_fp64_pool(const Plan &p, cudaStream_t s, int list, int parts)
+{
+    if (p.maxa <= 8) pair_launch<double, 8, true>(p, s, list, parts);
+    else pair_launch<double, 16, true>(p, s, list, parts);
+}
+void gather_dispatch_fp64_pool(const Plan &p, cudaStream_t s, const double *hk, double dt, bool full, bool fuse)
+{
+    if (p.maxa <= 8) gather_launch<double, 8, true>(p, s, hk, dt, full, fuse);
+    else gather_launch<double, 16, true>(p, s, hk, dt, full, fuse);
+}
+void configure_fp64_pool() { configure_type<double, true>(); }
+#endif
+
+#if !defined(MD_FORCE_PART) || MD_FORCE_PART == 2
+void pair_dispatch_fp32(const Plan &p, cudaStream_t s, int list, int parts)
+{
+    if (p.batch) {
+        if (p.maxa <= 8) pair_launch<float, 8, true>(p, s, list, parts);
+        else pair_launch<float, 16, true>(p, s, list, parts);
+    } else {
+        if (p.maxa <= 8) pair_launch<float, 8, false>(p, s, list, parts);
+        else pair_launch<float, 16, false>(p, s, list, parts);
+    }
+}
+void gather_dispatch_fp32(const Plan &p, cudaStream_t s, const double *hk, double dt, bool full, bool fuse)
+{
+    if (p.batch) {
+        if (p.maxa <= 8) gather_launch<float, 8, true>(p, s, hk, dt, full, fuse);
+        else gather_launch<float, 16, true>(p, s, hk, dt, full, fuse);
+    } else {
+        if (p.maxa <= 8) gather_launch<float, 8, false>(p, s, hk, dt, full, fuse);
+        else gather_launch<float, 16, false>(p, s, hk, dt, full, fuse);
+    }
+}
+void configure_fp32()
+{
+    configure_type<float, false>();
+    configure_type<float, true>();
+}
+#endif
+
+#if !defined(MD_FORCE_PART) || MD_FORCE_PART == 0
 namespace {
 __global__ void k_fastmath_eval(int fn, int64_t n, const double *x, double *y)
 {
@@ -2032,10 +2105,9 @@ bool configure_kernels(const Plan &)
     std::lock_guard<std::mutex> lk(mu);
     if (done[dev]) return true;
     cudaGetLastError();   // a stale error of an earlier call must not count as this one's
-    configure_type<double, false>();
-    configure_type<float, false>();
-    configure_type<double, true>();
-    configure_type<float, true>();
+    configure_fp64();
+    configure_fp64_pool();
+    configure_fp32();
     if (cudaGetLastError() != cudaSuccess) return false;
     done[dev] = true;
     return true;
@@ -2097,43 +2169,22 @@ void launch_clear_fresh(const Plan &p, cudaStream_t s)
     k_clear_fresh<<<(unsigned)((p.n_sys + 255) / 256), 256, 0, s>>>(p.n_sys, p.sys, p.flags);
 }
 
-template <bool BATCH>
-void pair_dispatch_launch(const Plan &p, cudaStream_t s, int list, int parts)
-{
-    if (p.precision == 0) {
-        if (p.maxa <= 8) pair_launch<double, 8, BATCH>(p, s, list, parts);
-        else pair_launch<double, 16, BATCH>(p, s, list, parts);
-    } else {
-        if (p.maxa <= 8) pair_launch<float, 8, BATCH>(p, s, list, parts);
-        else pair_launch<float, 16, BATCH>(p, s, list, parts);
-    }
-}
-
 int launch_pair(const Plan &p, cudaStream_t s, int list, int parts)
 {
     if (p.N == 0) return 0;
-    if (p.batch) pair_dispatch_launch<true>(p, s, list, parts);
-    else pair_dispatch_launch<false>(p, s, PAIR_ALL, parts);
+    const int l = p.batch ? list : PAIR_ALL;
+    if (p.precision != 0) pair_dispatch_fp32(p, s, l, parts);
+    else if (p.batch) pair_dispatch_fp64_pool(p, s, l, parts);
+    else pair_dispatch_fp64(p, s, l, parts);
     return (parts & PAIR_FAST ? 1 : 0) + (parts & PAIR_DEFERRED ? 1 : 0);
-}
-
-template <bool BATCH>
-void gather_dispatch(const Plan &p, cudaStream_t s, const double *hk, double dt, bool full, bool fuse)
-{
-    if (p.precision == 0) {
-        if (p.maxa <= 8) gather_launch<double, 8, BATCH>(p, s, hk, dt, full, fuse);
-        else gather_launch<double, 16, BATCH>(p, s, hk, dt, full, fuse);
-    } else {
-        if (p.maxa <= 8) gather_launch<float, 8, BATCH>(p, s, hk, dt, full, fuse);
-        else gather_launch<float, 16, BATCH>(p, s, hk, dt, full, fuse);
-    }
 }
 
 void launch_gather(const Plan &p, cudaStream_t s, const double *hk, double dt, bool full, bool fuse_next)
 {
     if (p.N == 0) return;
-    if (p.batch) gather_dispatch<true>(p, s, hk, dt, full, fuse_next);
-    else gather_dispatch<false>(p, s, hk, dt, full, fuse_next);
+    if (p.precision != 0) gather_dispatch_fp32(p, s, hk, dt, full, fuse_next);
+    else if (p.batch) gather_dispatch_fp64_pool(p, s, hk, dt, full, fuse_next);
+    else gather_dispatch_fp64(p, s, hk, dt, full, fuse_next);
 }
 
 void launch_reduce(const Plan &p, cudaStream_t s, bool full, bool record_series)
@@ -2164,8 +2215,11 @@ void launch_npt_couple(const Plan &p, cudaStream_t s, double dt)
 
 int gather_block() { return kGatherBlock; }
 int gather_blocks(int64_t N) { return N == 0 ? 1 : (int)blocks_for(N, kGatherBlock); }
+#endif  // part 0
 
 }  // namespace mdk
+
+#if !defined(MD_FORCE_PART) || MD_FORCE_PART == 0
 
 // Diagnostics: the pair passes' exp, log, reciprocal and reciprocal square root routines
 // (fn 0..9, as k_fastmath_eval lists them) on n host values, on the current device
@@ -2191,4 +2245,4 @@ extern "C" int md_fastmath_eval(int fn, int64_t n, const double *x, double *y)
     }
     return 0;
 }
-
+#endif  // part 0

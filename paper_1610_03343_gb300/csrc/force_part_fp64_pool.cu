@@ -1,0 +1,5 @@
+// The fp64 pair passes and gathers of pools in force.cu, compiled as a translation unit of its
+// own (a unit of its own name, so that the kernels of force.cu's internal namespace get names
+// of their own in each object).
+#define MD_FORCE_PART 3
+#include "force.cu"
