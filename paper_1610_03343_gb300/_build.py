@@ -23,8 +23,11 @@ SOURCES = ["force.cu", "neigh.cu", "md_api.cu", "md_server.cu", "md_static.cu", 
 # force.cu is compiled as four units (its fp64 kernels of single systems and of pools and its
 # fp32 kernels through the force_part_*.cu wrappers, and the rest) so that its large sets of
 # kernel instantiations compile in parallel
-UNITS = [("force_part_fp64.cu", [], "force_part_fp64.o"), ("force_part_fp64_pool.cu", [], "force_part_fp64_pool.o"),
-         ("force_part_fp32.cu", [], "force_part_fp32.o"), ("force.cu", ["-DMD_FORCE_PART=0"], "force.o")] + \
+# (each unit leaves the other units' helpers unused: their "declared but never referenced"
+# diagnostics, number 177, are silenced for these units)
+_QUIET = ["-Xcudafe", "--diag_suppress=177"]
+UNITS = [("force_part_fp64.cu", _QUIET, "force_part_fp64.o"), ("force_part_fp64_pool.cu", _QUIET, "force_part_fp64_pool.o"),
+         ("force_part_fp32.cu", _QUIET, "force_part_fp32.o"), ("force.cu", ["-DMD_FORCE_PART=0"] + _QUIET, "force.o")] + \
         [(src, [], os.path.splitext(src)[0] + ".o") for src in SOURCES if src != "force.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
